@@ -1,0 +1,111 @@
+"""The five synthetic workloads (shapes of the paper's runs, on tetrahedra).
+
+Each config fixes the mesh (periodic box of n^3 hexahedra x 6 tetrahedra),
+the order N, the physics, the initial state recipe, the number of RK4 steps
+and the time step.  DOFs are counted per scalar field, as the paper counts
+them (§5.3): one DOF = one node of one element.
+
+The time step is a fixed number derived from a closed-form bound of the
+initial state's wave speed: dt = 0.3 h / ((N+1)^2 (|u|_max + c_max)), h the
+hexahedron edge.  Both the oracle and the GPU path receive the same dt.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .gas import IdealGas, seeded_nasa7_mixture, mixture_primitive_state
+from .mesh import box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
+from .states import isentropic_vortex, taylor_green, uniform_perturbation
+
+
+@dataclass(frozen=True)
+class Config:
+    name: str
+    n: int  # hexahedra per box side
+    N: int  # polynomial order
+    physics: str  # "euler", "ns" or "euler_mixture"
+    state: str  # "vortex", "tgv" or "mixture"
+    steps: int
+    dt: float
+    precision: str = "fp64"
+    seed: int = 0
+    gas: object = field(default=None)
+    description: str = ""
+
+    @property
+    def K(self) -> int:
+        return 6 * self.n ** 3
+
+    @property
+    def Np(self) -> int:
+        return n_nodes(self.N)
+
+    @property
+    def dofs(self) -> int:
+        return self.K * self.Np
+
+
+def _tgv_dt(n, N, gamma=1.4, mach=0.1, noise=0.01):
+    V0 = mach
+    umax = V0 * (1 + noise) * math.sqrt(2.0)
+    p0 = 1.0 / gamma
+    pmax = p0 + V0 * V0 / 16.0 * 2.0 * 3.0
+    cmax = math.sqrt(gamma * pmax / 1.0)
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (umax + cmax))
+
+
+_NS_GAS = IdealGas(gamma=1.4, R=1.0, mu=1.0e-3, Pr=0.71)
+
+CONFIGS = {
+    "euler_small": Config(
+        name="euler_small", n=4, N=2, physics="euler", state="vortex", steps=1, dt=1.0e-3,
+        gas=IdealGas(gamma=1.4, R=1.0),
+        description="single-species Euler, 4^3 hexes x 6 = 384 tets, N=2, isentropic vortex + U(+-1e-3), "
+                    "one RK4 step, dt=1e-3"),
+    "ns_viscous": Config(
+        name="ns_viscous", n=24, N=3, physics="ns", state="tgv", steps=10, dt=_tgv_dt(24, 3),
+        gas=_NS_GAS,
+        description="Navier-Stokes with BR1, mu=1e-3, Pr=0.71, 24^3 hexes x 6 = 82,944 tets, N=3, "
+                    "Taylor-Green Mach 0.1 + 1% noise, 10 RK4 steps"),
+    "ns_precision": Config(
+        name="ns_precision", n=32, N=4, physics="ns", state="tgv", steps=10, dt=_tgv_dt(32, 4),
+        gas=_NS_GAS, precision="mixed",
+        description="as ns_viscous at 32^3 hexes x 6 = 196,608 tets, N=4; split-product tensor-core D/LIFT"),
+    "mixture_learned": Config(
+        name="mixture_learned", n=32, N=2, physics="euler_mixture", state="mixture", steps=1, dt=5.0e-6,
+        description="7-species Euler mixture, seeded NASA-7, 32^3 hexes x 6 = 196,608 tets, N=2; "
+                    "temperature Newton seeded by an MLP"),
+}
+
+
+def get_config(name: str) -> Config:
+    return CONFIGS[name]
+
+
+def build_case(cfg: Config, n=None, N=None):
+    """Mesh and initial state of a config (optionally at another size/order).
+
+    Returns dict(vertices, period, ref_nodes, xyz, q or mixture primitives).
+    """
+    n = cfg.n if n is None else n
+    N = cfg.N if N is None else N
+    verts, period = box_mesh(n, 1.0)
+    rst = equispaced_tet_nodes(N)
+    xyz = physical_nodes(verts, rst)
+    out = dict(vertices=verts, period=period, ref_nodes=rst, xyz=xyz, N=N, n=n)
+    if cfg.state == "vortex":
+        q = isentropic_vortex(xyz, 0.0, gamma=cfg.gas.gamma, period=period)
+        out["q"] = uniform_perturbation(q, 1.0e-3, seed=cfg.seed)
+    elif cfg.state == "tgv":
+        out["q"] = taylor_green(xyz, gamma=cfg.gas.gamma, mach=0.1, noise=0.01, seed=cfg.seed)
+    elif cfg.state == "mixture":
+        mix = seeded_nasa7_mixture(7, seed=cfg.seed)
+        Y, T, vel, p0 = mixture_primitive_state(xyz, 7, seed=cfg.seed)
+        out.update(mixture=mix, Y=Y, T=T, vel=vel, p0=p0)
+    else:
+        raise ValueError(cfg.state)
+    return out
