@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the nodal DG hot path: LSRK4-stage DOF-updates/s on GB300.
+
+A step is one full low-storage RK4 step (five fused right-hand-side + stage
+updates) of the workload, through libdg's C ABI.  The default workload is the
+viscous configuration: compressible Navier-Stokes with BR1, mu = 1e-3,
+Pr = 0.71, periodic box of 24^3 hexahedra x 6 = 82,944 tetrahedra, order N = 3
+(20 nodes each), Taylor-Green vortex at Mach 0.1 with 1% seeded noise, FP64.
+A DOF is one node of one element (per scalar field, as the paper counts them);
+one stage updates K*Np DOFs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--config NAME]
+
+One JSON line is printed by rank 0.  --impl reference times the FP64 CPU oracle
+on the host cores instead (the reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK4 stage DOF-updates/s on 1 GB300: mixed/learned vs plain FP64 at fixed error"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (the pool's recipe table); an FMA-loop probe measured 1.198
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture, keyed by the
+# sha256 of the kernel source they were taken on; a changed kernel reports null traffic.
+TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu"):
+        with open(os.path.join(ROOT, "paper_2512_17101_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ---- algorithmic work per launch (documented in the design doc) --------------------------------------
+
+def rhs_flops_per_element(Np, NF, V, viscous):
+    """FP64 flops the fused right-hand side + stage update needs per element."""
+    f = 2 * 3 * Np * Np * V          # -sum_a D_a F_a
+    f += 2 * NF * Np * V             # LIFT g
+    f += Np * V * 3 * 5              # contravariant fluxes
+    f += Np * 30                     # pressure, velocity, Euler fluxes
+    f += NF * (56 + 4 + 5 * V)       # both traces' p, c, u.n, n.F; lambda; LF flux and Fscale
+    f += Np * V * 4                  # k <- a k + dt rhs, q <- q + b k
+    if viscous:
+        f += Np * 12 + NF * 48       # subtract viscous flux; central viscous normal flux
+    return f
+
+
+def viscous_flops_per_element(Np, NF):
+    f = 2 * 3 * Np * Np * 5          # reference derivatives of (rho, rho u, T)
+    f += Np * 5 * 3 * 5              # to physical gradients
+    f += 2 * NF * Np * 5 + Np * 4 * 3 * 5 * 2  # lifted central jumps, per-face normals
+    f += NF * 30 + Np * 15           # traces and T at own nodes
+    f += Np * 60                     # velocity gradient, stress, heat flux
+    return f
+
+
+def rhs_bytes_per_element(Np, NF, V, viscous):
+    b = Np * 8 * 4 * V + 26 * 8 + 4 * NF  # q, k in; q_out, k out; geometry; neighbour map
+    if viscous:
+        b += Np * 8 * 9                    # viscous flux in
+    return b
+
+
+def viscous_bytes_per_element(Np, NF):
+    return Np * 8 * (5 + 9) + 26 * 8 + 4 * NF
+
+
+# ---- clocks ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- distributed plumbing ------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- oracle timing (the reference arm and the cpu_baseline leg) ------------------------------------
+
+def oracle_stage_runner(cfg, n=None):
+    """Returns (run_one_stage, dofs_per_stage, description) for the oracle on the config."""
+    import numpy as np
+    from oracle.euler import rhs_strong
+    from oracle.geometry import connect, geometric_factors
+    from oracle.lsrk import lsrk4_stage
+    from oracle.ns import rhs_ns
+    from oracle.refelem import build_reference
+    from oracle.thermo import PerfectGas
+    from workloads.configs import build_case
+    case = build_case(cfg, n=n)
+    ref = build_reference(cfg.N, case["ref_nodes"])
+    geo = geometric_factors(case["vertices"])
+    conn = connect(case["vertices"], case["period"], ref)
+    gas = PerfectGas(cfg.gas.gamma, cfg.gas.R)
+    if cfg.physics == "ns":
+        f = lambda u: rhs_ns(ref, geo, conn, u, gas, cfg.gas.mu, cfg.gas.Pr)
+    elif cfg.physics == "euler":
+        f = lambda u: rhs_strong(ref, geo, conn, u, gas)
+    else:
+        raise ValueError(f"no oracle timing for {cfg.physics}")
+    state = {"q": case["q"], "k": np.zeros_like(case["q"]), "s": 0}
+
+    def run():
+        state["q"], state["k"] = lsrk4_stage(state["q"], state["k"], state["s"], cfg.dt, f)
+        state["s"] = (state["s"] + 1) % 5
+
+    K = case["vertices"].shape[0]
+    return run, K * ref.Np, f"one LSRK4 stage on {K} tets (box {case['n']}^3 x 6), N={cfg.N}"
+
+
+def time_oracle(cfg, stages, n=None):
+    run, dofs, desc = oracle_stage_runner(cfg, n)
+    t0 = time.perf_counter()
+    for _ in range(stages):
+        run()
+    dt = time.perf_counter() - t0
+    return dofs * stages / dt, desc, dt
+
+
+def reference_arm(args, cfg, world, rank):
+    if rank != 0:
+        return
+    sub_n = max(2, cfg.n // 2)
+    run, dofs, desc = oracle_stage_runner(cfg, n=sub_n)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    el = time.perf_counter() - t0
+    value = dofs * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(cfg),
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {desc} (half-size box of the workload); numpy, single thread"},
+        "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(cfg):
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": cfg.Np,
+            "V": 5, "physics": cfg.physics, "dofs_per_stage": cfg.dofs, "stages_per_step": 5,
+            "dt": cfg.dt, "precision": cfg.precision,
+            "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
+# ---- GPU arm -------------------------------------------------------------------------------------
+
+def gpu_arm(args, cfg, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2512_17101_gb300 import capi, dg
+    from workloads.configs import build_case
+
+    if not os.path.exists(capi.LIB_PATH):
+        raise SystemExit("libdg.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    g = cfg.gas
+    gas = dg.Gas(model="perfect", gamma=g.gamma, R=g.R, mu=g.mu, Pr=g.Pr)
+    q0 = torch.tensor(case["q"], device=dev)
+    q = q0.clone()
+    work = (torch.empty_like(q), torch.zeros_like(q))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(qbuf):
+        dg.lsrk4_step(mesh, gas, qbuf, cfg.dt, steps=1, work=work)
+
+    for _ in range(args.warmup):
+        step(q)
+    torch.cuda.synchronize()
+    mesh.kernel_times(reset=True)
+
+    # device-timed region: inputs resident in HBM
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    mesh.set_timing(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev0[i].record(stream)
+        step(q)
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_info = clocks.stop()
+    mesh.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ktimes = mesh.kernel_times(reset=True)
+    if mesh.status() != 0:
+        raise SystemExit("device status flags set during the benchmark (non-physical state)")
+    launches = sum(n for _, n in ktimes.values())
+
+    ms_per_step = total_ms / args.steps
+    dofs_step = cfg.dofs * 5
+    value = world * dofs_step / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel
+    Np, NF = cfg.Np, 4 * ((cfg.N + 1) * (cfg.N + 2) // 2)
+    viscous = g.mu > 0
+    per_kernel = {}
+    for name, (ms, n) in ktimes.items():
+        if n:
+            per_kernel[name] = {"avg_ms": ms / n, "launches": n, "share": None}
+    tot = sum(v["avg_ms"] * v["launches"] for v in per_kernel.values())
+    for v in per_kernel.values():
+        v["share"] = v["avg_ms"] * v["launches"] / tot
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["avg_ms"] * per_kernel[k]["launches"])
+    if dom == "rhs":
+        flops = rhs_flops_per_element(Np, NF, 5, viscous) * cfg.K
+        nbytes = rhs_bytes_per_element(Np, NF, 5, viscous) * cfg.K
+    else:
+        flops = viscous_flops_per_element(Np, NF) * cfg.K
+        nbytes = viscous_bytes_per_element(Np, NF) * cfg.K
+    avg_s = per_kernel[dom]["avg_ms"] * 1e-3
+    achieved = flops / avg_s / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    src = kernel_source_hash()
+    traffic = TRAFFIC.get((src, dom))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak, "kernels": per_kernel,
+                "peak_note": "FP64 nominal 1.25 TFLOP/s (pool recipe); HBM peak of measured copy"}
+
+    # end to end through the public API: pinned host state in, stages, state back to host
+    host_in = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(q0.cpu())
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0[i].record(stream)
+        q.copy_(host_in, non_blocking=True)
+        step(q)
+        host_out.copy_(q, non_blocking=True)
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e0, e1)), world) / args.steps
+    state_bytes = q.numel() * 8
+    e2e = {"value": world * dofs_step / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes, "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, desc, secs = time_oracle(cfg, 1)
+        cpu = {"value": val, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{desc}: the full workload's mesh; numpy, single thread; {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(cfg),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clock_info, "kernel_src": src, "impl": "gpu",
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--config", default="ns_viscous")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    from workloads.configs import get_config
+    cfg = get_config(args.config)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, cfg, world, rank)
+    else:
+        gpu_arm(args, cfg, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * dg.h - C ABI of libdg: the nodal discontinuous-Galerkin right-hand side and
+ * low-storage RK4 stage for compressible (multi-species, viscous) flow on
+ * tetrahedral meshes, on one GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 2512.17101, MIRGE-Com):
+ *   - DOFs are local to each element and stored as an array per field, the
+ *     element-major nodal layout of Sec. 1, Fig. 1;
+ *   - nodal DG on tetrahedra (Sec. 1) with full assembly of the reference
+ *     operators (Sec. 5.2); Euler equations with a Lax-Friedrichs flux
+ *     (Sec. 5.2); compressible Navier-Stokes (Sec. 5.3) with BR1 gradients;
+ *     perfect gas gamma = 1.4 (Sec. 5.3) or a multi-species NASA-7 mixture
+ *     (Sec. 4, Sec. 5) whose temperature comes from a per-node Newton solve;
+ *   - explicit fourth-order Runge-Kutta (Sec. 5.2), here the five-stage
+ *     2N-storage scheme of Carpenter & Kennedy.
+ * The paper names these pieces without formulas; the library implements the
+ * textbook forms (Hesthaven & Warburton) that its Sec. 1 cites.
+ *
+ * Conventions shared by all calls
+ *   - State q is float64 [V][K][Np], node index fastest ("field, element,
+ *     node"), with V = 5 + nspecies: rho, rho u, rho v, rho w, rho E, rho Y_k.
+ *     The right-hand side, the RK register k and the stage output use the
+ *     same layout.  Temperature fields are float64 [K][Np].
+ *   - Reference tetrahedron: vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1),
+ *     (-1,-1,1); element vertex m is the image of reference vertex m.
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees or retains them beyond the call.  Pointers named
+ *     *_host are host pointers read during the call only.
+ *   - Calls that take a stream enqueue work asynchronously on it (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream) and
+ *     return after launching.  Errors found on the device (non-physical
+ *     state, Newton without convergence) are recorded in a status word of
+ *     the handle and read with dg_mesh_status / dg_gas_status.
+ *   - Every call returns DG_OK (0) or a negative DG_ERR_* code; the message
+ *     of the last error on the calling thread is dg_last_error().  The
+ *     library never prints, exits or traps.
+ */
+#ifndef DG_H_
+#define DG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DG_OK 0
+#define DG_ERR_INVALID_ARG (-1)
+#define DG_ERR_CUDA (-2)
+#define DG_ERR_NO_CONVERGENCE (-3)
+#define DG_ERR_NONPHYSICAL (-4)
+#define DG_ERR_TIMEOUT (-5)
+#define DG_ERR_OOM (-6)
+#define DG_ERR_UNSUPPORTED (-7)
+
+/* bits of the device status word (dg_mesh_status / dg_gas_status) */
+#define DG_STATUS_NONPHYSICAL 1u      /* rho <= 0 or p <= 0 met at some node */
+#define DG_STATUS_NO_CONVERGENCE 2u   /* a Newton temperature solve hit its cap */
+
+/* ---- limits -------------------------------------------------------------- */
+#define DG_MAX_ORDER 4
+#define DG_MAX_SPECIES 8
+
+typedef struct dg_mesh_s* dg_mesh;
+typedef struct dg_gas_s* dg_gas;
+
+/* ---- mesh ---------------------------------------------------------------- */
+typedef struct {
+  int32_t K;                 /* number of tetrahedra, >= 1                        */
+  int32_t N;                 /* polynomial order, 1..DG_MAX_ORDER                 */
+  const double* ref_nodes;   /* host [Np][3]: (r,s,t) of the reference nodes; the  */
+                             /* face nodes of each face must match those of the   */
+                             /* neighbouring face (e.g. equispaced lattice)        */
+  const double* vertices;    /* host [K][4][3]: vertex coordinates per element,   */
+                             /* unwrapped across periodic seams; positive volume  */
+  double period[3];          /* periodic box lengths; 0 = not periodic along it    */
+  int32_t flags;             /* DG_MESH_* bits                                     */
+} dg_mesh_desc;
+
+/* Build the host-side tables only (no device memory, no CUDA call).  Such a
+ * mesh answers dg_mesh_info / dg_mesh_operators / dg_mesh_connectivity and is
+ * rejected by the compute calls.  Lets the host logic be checked without a GPU. */
+#define DG_MESH_HOST_ONLY 1
+
+/* Builds the reference operators (Dr, Ds, Dt, LIFT = M^-1 E, Fmask) from the
+ * reference nodes, the affine geometric factors (inverse Jacobian, unit outward
+ * normals, Fscale = face area / (2 J)) and the face connectivity (faces paired
+ * by centroid modulo the period, face nodes by coordinates under the face
+ * pair's periodic shift), then copies them to the current device together with
+ * a scratch buffer for the viscous flux (9 doubles per node).  Sec. 1 Fig. 1
+ * (element-local arrays), Sec. 4.1.2 / Sec. 4.3 (connectivity, indirect gather).
+ * Every face must find exactly one partner (closed periodic meshes): otherwise
+ * DG_ERR_INVALID_ARG.  Allocates device memory (cudaMalloc); *out owns it. */
+int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out);
+int dg_mesh_free(dg_mesh mesh);
+
+/* Sizes of an uploaded mesh. Any pointer may be NULL. */
+int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp);
+
+/* Copies the library's reference operators to host buffers (any may be NULL):
+ * Dr/Ds/Dt [Np][Np] row-major, LIFT [Np][4 Nfp], Fmask [4][Nfp]. Test aid. */
+int dg_mesh_operators(dg_mesh mesh, double* Dr_host, double* Ds_host, double* Dt_host,
+                      double* LIFT_host, int32_t* Fmask_host);
+
+/* Copies the neighbour map vmapP [K][4 Nfp] (flat node index k2 Np + n2 of the
+ * partner of each face node) and per-element geometry to host buffers (any may
+ * be NULL).  geo_host is [K][DG_GEO_STRIDE]. Test aid. */
+#define DG_GEO_STRIDE 26 /* rx ry rz sx sy sz tx ty tz | (nx ny nz Fscale) x 4 faces | J */
+int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP_host, double* geo_host);
+
+/* Reads (and with reset != 0 clears) the device status word of the mesh, after
+ * synchronising the device.  *bits receives DG_STATUS_* bits. */
+int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset);
+
+/* ---- per-kernel timing (CUDA events on the launch stream) ------------------ */
+#define DG_KERNEL_VISCOUS 0     /* BR1 gradient + viscous flux pass            */
+#define DG_KERNEL_RHS 1         /* fused right-hand side (+ RK stage)          */
+#define DG_KERNEL_TEMPERATURE 2 /* Newton temperature solve inside dg_rhs/stage */
+#define DG_NUM_KERNELS 3
+
+/* With enable != 0, every later dg_rhs / dg_rk_stage on this mesh brackets each
+ * of its kernel launches with CUDA events recorded on the launch stream (the
+ * events are created by the library).  Timing adds two event records per
+ * launch and nothing else. */
+int dg_mesh_set_timing(dg_mesh mesh, int enable);
+
+/* Waits for the recorded events and returns, per DG_KERNEL_* id, the summed
+ * device time in milliseconds (ms_host[DG_NUM_KERNELS]) and the number of
+ * launches (launches_host[DG_NUM_KERNELS]) since the last reset; reset != 0
+ * clears the totals. */
+int dg_mesh_kernel_times(dg_mesh mesh, double* ms_host, int64_t* launches_host, int reset);
+
+/* ---- gas ----------------------------------------------------------------- */
+#define DG_GAS_PERFECT 0
+#define DG_GAS_NASA7 1
+
+typedef struct {
+  int32_t model;             /* DG_GAS_PERFECT or DG_GAS_NASA7                     */
+  double gamma;              /* perfect gas: ratio of specific heats               */
+  double R;                  /* perfect gas: gas constant (T = p / (rho R))       */
+  double mu;                 /* dynamic viscosity; 0 = inviscid (Euler)            */
+  double Pr;                 /* Prandtl number: kappa = mu cp / Pr                 */
+  int32_t nspecies;          /* NASA-7: 1..DG_MAX_SPECIES (state V = 5 + nspecies) */
+  const double* W;           /* NASA-7: host [nspecies] molar masses               */
+  const double* nasa7;       /* NASA-7: host [nspecies][7] coefficients a1..a7     */
+  double R_universal;        /* NASA-7: R_k = R_universal / W_k                    */
+  double newton_tol;         /* NASA-7: stop at |dT| < tol (K), e.g. 1e-10         */
+  int32_t newton_max_it;     /* NASA-7: iteration cap, e.g. 50                     */
+} dg_gas_desc;
+
+/* Perfect gas (Sec. 5.3): p = (gamma-1)(rho E - rho |u|^2 / 2).
+ * NASA-7 mixture (Sec. 4, Sec. 5 multi-species): cp_k/R_k = a1 + a2 T + ... + a5 T^4,
+ * h_k/R_k = a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6, e = sum_k Y_k (h_k - R_k T),
+ * p = rho R_mix T, c^2 = (cp/cv) p / rho.  Viscous mixtures are unsupported. */
+int dg_gas_create(const dg_gas_desc* desc, dg_gas* out);
+int dg_gas_free(dg_gas gas);
+int dg_gas_status(dg_gas gas, uint32_t* bits, int reset);
+
+/* ---- options --------------------------------------------------------------- */
+#define DG_PREC_FP64 0   /* every step in float64                                   */
+#define DG_TSEED_INPUT 0 /* Newton starts from T_io                                  */
+#define DG_TSEED_CONST 1 /* Newton starts from opts.t_const                           */
+
+typedef struct {
+  int32_t precision;  /* DG_PREC_*                                                   */
+  int32_t t_seed;     /* DG_TSEED_*                                                  */
+  double t_const;     /* constant Newton seed for DG_TSEED_CONST                     */
+  int32_t reserved[8];
+} dg_opts;            /* NULL = defaults: DG_PREC_FP64, DG_TSEED_INPUT              */
+
+/* ---- the hot path ------------------------------------------------------------ */
+
+/* Semi-discrete right-hand side rhs = dq/dt (strong form):
+ *   rhs = -sum_d dG_d/dx_d + LIFT( Fscale * (n.G(q-) - G*) ),  G = F_euler - F_viscous,
+ * with the pointwise Lax-Friedrichs flux for F_euler and, when mu > 0, BR1
+ * central fluxes for the gradients of (rho, rho u, T) and for F_viscous.
+ * q_dev, rhs_dev: [V][K][Np]; they must not overlap.  T_io_dev: [K][Np],
+ * required for a NASA-7 gas (Newton seed in, temperature out), ignored (may be
+ * NULL) for a perfect gas.  The mesh's scratch buffer is used for the viscous
+ * flux, so calls on one mesh must not overlap in time. */
+int dg_rhs(dg_mesh mesh, dg_gas gas, const double* q_dev, double* rhs_dev, double* T_io_dev,
+           const dg_opts* opts, void* stream);
+
+/* Stage s (0..4) of the five-stage 2N-storage RK4 (Carpenter & Kennedy 1994):
+ *   k <- a_s k + dt rhs(q_in),   q_out <- q_in + b_s k.
+ * The right-hand side and the update are fused; k_dev is updated in place
+ * (a_0 = 0, so its content is ignored at s = 0).  q_out_dev must not overlap
+ * q_in_dev (neighbour traces of q_in are read while q_out is written). */
+int dg_rk_stage(dg_mesh mesh, dg_gas gas, int32_t stage, double dt, const double* q_in_dev,
+                double* q_out_dev, double* k_dev, double* T_io_dev, const dg_opts* opts, void* stream);
+
+/* The coefficients a_s, b_s (s = 0..4) used by dg_rk_stage (host arrays of 5). */
+int dg_lsrk4_coefficients(double* a_host, double* b_host);
+
+/* Per-node temperature of a NASA-7 mixture from the conserved state:
+ * e = rho E / rho - |u|^2/2, Y_k = rho Y_k / rho, Newton T <- T - (e(T) - e)/cv(T)
+ * from the seed (T_io or opts.t_const) until |dT| < newton_tol.  n nodes;
+ * q_dev: [V][n] (V = 5 + nspecies); T_io_dev: [n]; iters_dev (nullable):
+ * int32 [n] Newton updates taken.  Nodes that reach newton_max_it set
+ * DG_STATUS_NO_CONVERGENCE in the gas status. */
+int dg_temperature(dg_gas gas, int64_t n, const double* q_dev, double* T_io_dev, int32_t* iters_dev,
+                   const dg_opts* opts, void* stream);
+
+/* Mixture internal energy e(T, Y) per node (the inverse of dg_temperature's
+ * solve): n nodes, T_dev [n], Y_dev [nspecies][n], e_dev [n]. */
+int dg_mixture_energy(dg_gas gas, int64_t n, const double* T_dev, const double* Y_dev, double* e_dev,
+                      void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H_ */

@@ -1,0 +1,110 @@
+"""ctypes declarations of libdg's C ABI (include/dg.h).
+
+Loading fails loudly if libdg.so has not been built: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdg.so")
+
+DG_OK = 0
+DG_ERR_INVALID_ARG = -1
+DG_ERR_CUDA = -2
+DG_ERR_NO_CONVERGENCE = -3
+DG_ERR_NONPHYSICAL = -4
+DG_ERR_TIMEOUT = -5
+DG_ERR_OOM = -6
+DG_ERR_UNSUPPORTED = -7
+DG_STATUS_NONPHYSICAL = 1
+DG_STATUS_NO_CONVERGENCE = 2
+DG_MAX_ORDER = 4
+DG_MAX_SPECIES = 8
+DG_GEO_STRIDE = 26
+DG_GAS_PERFECT = 0
+DG_GAS_NASA7 = 1
+DG_PREC_FP64 = 0
+DG_TSEED_INPUT = 0
+DG_TSEED_CONST = 1
+DG_MESH_HOST_ONLY = 1
+DG_KERNEL_VISCOUS = 0
+DG_KERNEL_RHS = 1
+DG_KERNEL_TEMPERATURE = 2
+DG_NUM_KERNELS = 3
+KERNEL_NAMES = ('viscous', 'rhs', 'temperature')
+
+c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, \
+    ctypes.c_void_p
+
+
+class dg_mesh_desc(ctypes.Structure):
+    _fields_ = [("K", c_int32), ("N", c_int32), ("ref_nodes", c_void_p), ("vertices", c_void_p),
+                ("period", c_double * 3), ("flags", c_int32)]
+
+
+class dg_gas_desc(ctypes.Structure):
+    _fields_ = [("model", c_int32), ("gamma", c_double), ("R", c_double), ("mu", c_double), ("Pr", c_double),
+                ("nspecies", c_int32), ("W", c_void_p), ("nasa7", c_void_p), ("R_universal", c_double),
+                ("newton_tol", c_double), ("newton_max_it", c_int32)]
+
+
+class dg_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("reserved", c_int32 * 8)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/dg.h
+SIGNATURES = {
+    "dg_mesh_upload": (c_int32, [ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(c_void_p)]),
+    "dg_mesh_free": (c_int32, [c_void_p]),
+    "dg_mesh_info": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                               ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "dg_mesh_operators": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_connectivity": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
+    "dg_mesh_set_timing": (c_int32, [c_void_p, c_int32]),
+    "dg_mesh_kernel_times": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "dg_gas_create": (c_int32, [ctypes.POINTER(dg_gas_desc), ctypes.POINTER(c_void_p)]),
+    "dg_gas_free": (c_int32, [c_void_p]),
+    "dg_gas_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
+    "dg_rhs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(dg_opts), c_void_p]),
+    "dg_rk_stage": (c_int32, [c_void_p, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                              ctypes.POINTER(dg_opts), c_void_p]),
+    "dg_lsrk4_coefficients": (c_int32, [c_void_p, c_void_p]),
+    "dg_temperature": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.POINTER(dg_opts),
+                                 c_void_p]),
+    "dg_mixture_energy": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_last_error": (ctypes.c_char_p, []),
+}
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdg.so (once) and declare its signatures; raises ImportError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(code: int) -> None:
+    if code != DG_OK:
+        msg = load().dg_last_error()
+        raise DGError(code, msg.decode() if msg else "")

@@ -1,0 +1,388 @@
+// C ABI of libdg: argument checks, handle management and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(DG_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  return fail(DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme.
+const double kRK4A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                         -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRK4B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+
+}  // namespace dg
+
+using dg::fail;
+using dg::cuda_fail;
+
+namespace {
+
+void free_mesh_device(dg::MeshDev& d) {
+  cudaFree(d.ops);
+  cudaFree(d.fmask);
+  cudaFree(d.geo);
+  cudaFree(d.vmapP);
+  cudaFree(d.scratch);
+  cudaFree(d.status);
+  d = dg::MeshDev();
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int check_opts(const dg_opts* o) {
+  if (!o) return DG_OK;
+  if (o->precision != DG_PREC_FP64) return fail(DG_ERR_UNSUPPORTED, "unsupported precision mode");
+  if (o->t_seed != DG_TSEED_INPUT && o->t_seed != DG_TSEED_CONST)
+    return fail(DG_ERR_INVALID_ARG, "unknown temperature seed mode");
+  if (o->t_seed == DG_TSEED_CONST && !(o->t_const > 0)) return fail(DG_ERR_INVALID_ARG, "t_const must be > 0");
+  return DG_OK;
+}
+
+int read_status(unsigned* dev, uint32_t* bits, int reset) {
+  if (!bits) return fail(DG_ERR_INVALID_ARG, "bits is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  unsigned v = 0;
+  e = cudaMemcpy(&v, dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  *bits = v;
+  if (reset) {
+    e = cudaMemset(dev, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "reset status");
+  }
+  return DG_OK;
+}
+
+cudaEvent_t take_event(dg::KernelTimer& t) {
+  if (!t.pool.empty()) {
+    cudaEvent_t e = t.pool.back();
+    t.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Records an event pair around launch() on stream s when timing is enabled.
+template <typename F>
+cudaError_t timed(dg_mesh mesh, int id, cudaStream_t s, F launch) {
+  dg::KernelTimer& t = mesh->timer;
+  if (!t.enabled) return launch();
+  cudaEvent_t a = take_event(t), b = take_event(t);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, s);
+  cudaError_t e = launch();
+  cudaEventRecord(b, s);
+  t.pending[id].push_back({a, b});
+  return e;
+}
+
+int resolve_timer(dg::KernelTimer& t) {
+  for (int id = 0; id < DG_NUM_KERNELS; ++id) {
+    for (auto& pr : t.pending[id]) {
+      cudaError_t e = cudaEventSynchronize(pr.second);
+      if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+      float ms = 0;
+      e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      if (e != cudaSuccess) return cuda_fail(e, "event elapsed time");
+      t.ms[id] += ms;
+      t.count[id] += 1;
+      t.pool.push_back(pr.first);
+      t.pool.push_back(pr.second);
+    }
+    t.pending[id].clear();
+  }
+  return DG_OK;
+}
+
+// Shared front end of dg_rhs and dg_rk_stage.
+int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, double* T_io, const dg_opts* opts,
+            void* stream, bool rk, int stage, double dt) {
+  if (!mesh || !gas) return fail(DG_ERR_INVALID_ARG, "NULL mesh or gas handle");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  if (!q || !out) return fail(DG_ERR_INVALID_ARG, "NULL state or output pointer");
+  if (rk && !k) return fail(DG_ERR_INVALID_ARG, "NULL RK register k");
+  if (rk && (stage < 0 || stage > 4)) return fail(DG_ERR_INVALID_ARG, "stage must be in 0..4");
+  if (rk && !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite");
+  if (int rc = check_opts(opts)) return rc;
+  const dg::MeshDev& m = mesh->d;
+  const dg::GasParams& g = gas->p;
+  const int V = 5 + g.ns;
+  const size_t bytes = sizeof(double) * (size_t)V * m.K * m.Np;
+  if (q == out || (q < out + bytes / sizeof(double) && out < q + bytes / sizeof(double)))
+    return fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const double* T = nullptr;
+  if (g.model == DG_GAS_NASA7) {
+    if (!T_io) return fail(DG_ERR_INVALID_ARG, "a NASA-7 gas needs the temperature buffer T_io");
+    const int mode = opts ? opts->t_seed : DG_TSEED_INPUT;
+    const double tc = opts ? opts->t_const : 0.0;
+    e = timed(mesh, DG_KERNEL_TEMPERATURE, s, [&] {
+      return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, tc, gas->status, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
+    T = T_io;
+  }
+  if (g.mu > 0) {
+    e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
+  }
+  const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
+  e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs(m, g, q, out, k, T, rk, a, b, dt, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(void) { return dg::g_last_error.c_str(); }
+
+int dg_lsrk4_coefficients(double* a_host, double* b_host) {
+  if (!a_host || !b_host) return fail(DG_ERR_INVALID_ARG, "NULL output");
+  for (int s = 0; s < 5; ++s) {
+    a_host[s] = dg::kRK4A[s];
+    b_host[s] = dg::kRK4B[s];
+  }
+  return DG_OK;
+}
+
+int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
+  if (!desc || !out) return fail(DG_ERR_INVALID_ARG, "NULL descriptor or output handle");
+  *out = nullptr;
+  if (desc->K < 1) return fail(DG_ERR_INVALID_ARG, "K must be >= 1");
+  if (desc->N < 1 || desc->N > DG_MAX_ORDER) return fail(DG_ERR_INVALID_ARG, "N must be in 1..4");
+  if (!desc->ref_nodes || !desc->vertices) return fail(DG_ERR_INVALID_ARG, "NULL ref_nodes or vertices");
+  for (int x = 0; x < 3; ++x)
+    if (!(desc->period[x] >= 0) || !std::isfinite(desc->period[x]))
+      return fail(DG_ERR_INVALID_ARG, "period must be finite and >= 0");
+  dg_mesh m = new (std::nothrow) dg_mesh_s();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  std::string err;
+  if (!dg::build_ref_ops(desc->N, desc->ref_nodes, m->ops, err) ||
+      !dg::build_geometry(desc->K, desc->vertices, m->geo, err) ||
+      !dg::build_connectivity(desc->K, desc->vertices, desc->period, m->ops, desc->ref_nodes, m->vmapP, err)) {
+    delete m;
+    return fail(DG_ERR_INVALID_ARG, err);
+  }
+  dg::MeshDev& d = m->d;
+  d.K = desc->K;
+  d.N = desc->N;
+  d.Np = m->ops.Np;
+  d.Nfp = m->ops.Nfp;
+  if (desc->flags & DG_MESH_HOST_ONLY) {
+    *out = m;
+    return DG_OK;
+  }
+  cudaGetDevice(&m->device);
+  const int Np = d.Np, NF = 4 * d.Nfp;
+  std::vector<double> ops;
+  ops.reserve(3 * Np * Np + Np * NF);
+  ops.insert(ops.end(), m->ops.Dr.begin(), m->ops.Dr.end());
+  ops.insert(ops.end(), m->ops.Ds.begin(), m->ops.Ds.end());
+  ops.insert(ops.end(), m->ops.Dt.begin(), m->ops.Dt.end());
+  ops.insert(ops.end(), m->ops.LIFT.begin(), m->ops.LIFT.end());
+  cudaError_t e = upload(&d.ops, ops.data(), ops.size());
+  if (e == cudaSuccess) e = upload(&d.fmask, m->ops.Fmask.data(), m->ops.Fmask.size());
+  if (e == cudaSuccess) e = upload(&d.geo, m->geo.data(), m->geo.size());
+  if (e == cudaSuccess) e = upload(&d.vmapP, m->vmapP.data(), m->vmapP.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 9 * (size_t)d.K * Np);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    free_mesh_device(d);
+    delete m;
+    return cuda_fail(e, "mesh upload");
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_set_timing(dg_mesh mesh, int enable) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  mesh->timer.enabled = enable != 0;
+  return DG_OK;
+}
+
+int dg_mesh_kernel_times(dg_mesh mesh, double* ms, int64_t* launches, int reset) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (int rc = resolve_timer(mesh->timer)) return rc;
+  for (int id = 0; id < DG_NUM_KERNELS; ++id) {
+    if (ms) ms[id] = mesh->timer.ms[id];
+    if (launches) launches[id] = mesh->timer.count[id];
+    if (reset) {
+      mesh->timer.ms[id] = 0;
+      mesh->timer.count[id] = 0;
+    }
+  }
+  return DG_OK;
+}
+
+int dg_mesh_free(dg_mesh mesh) {
+  if (!mesh) return DG_OK;
+  resolve_timer(mesh->timer);
+  for (cudaEvent_t e : mesh->timer.pool) cudaEventDestroy(e);
+  free_mesh_device(mesh->d);
+  delete mesh;
+  return DG_OK;
+}
+
+int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (K) *K = mesh->d.K;
+  if (N) *N = mesh->d.N;
+  if (Np) *Np = mesh->d.Np;
+  if (Nfp) *Nfp = mesh->d.Nfp;
+  return DG_OK;
+}
+
+int dg_mesh_operators(dg_mesh mesh, double* Dr, double* Ds, double* Dt, double* LIFT, int32_t* Fmask) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  const dg::RefOps& o = mesh->ops;
+  if (Dr) std::memcpy(Dr, o.Dr.data(), sizeof(double) * o.Dr.size());
+  if (Ds) std::memcpy(Ds, o.Ds.data(), sizeof(double) * o.Ds.size());
+  if (Dt) std::memcpy(Dt, o.Dt.data(), sizeof(double) * o.Dt.size());
+  if (LIFT) std::memcpy(LIFT, o.LIFT.data(), sizeof(double) * o.LIFT.size());
+  if (Fmask) std::memcpy(Fmask, o.Fmask.data(), sizeof(int32_t) * o.Fmask.size());
+  return DG_OK;
+}
+
+int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP, double* geo) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (vmapP) std::memcpy(vmapP, mesh->vmapP.data(), sizeof(int32_t) * mesh->vmapP.size());
+  if (geo) std::memcpy(geo, mesh->geo.data(), sizeof(double) * mesh->geo.size());
+  return DG_OK;
+}
+
+int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (!mesh->d.status) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  return read_status(mesh->d.status, bits, reset);
+}
+
+int dg_gas_create(const dg_gas_desc* desc, dg_gas* out) {
+  if (!desc || !out) return fail(DG_ERR_INVALID_ARG, "NULL descriptor or output handle");
+  *out = nullptr;
+  dg::GasParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.model = desc->model;
+  p.mu = desc->mu;
+  p.Pr = desc->Pr;
+  if (!(desc->mu >= 0) || !std::isfinite(desc->mu)) return fail(DG_ERR_INVALID_ARG, "mu must be >= 0");
+  if (desc->mu > 0 && !(desc->Pr > 0)) return fail(DG_ERR_INVALID_ARG, "Pr must be > 0 when mu > 0");
+  if (desc->model == DG_GAS_PERFECT) {
+    if (!(desc->gamma > 1) || !(desc->R > 0)) return fail(DG_ERR_INVALID_ARG, "need gamma > 1 and R > 0");
+    p.gamma = desc->gamma;
+    p.R = desc->R;
+    p.cp = desc->gamma * desc->R / (desc->gamma - 1);
+    p.kappa = desc->mu > 0 ? desc->mu * p.cp / desc->Pr : 0.0;
+  } else if (desc->model == DG_GAS_NASA7) {
+    if (desc->nspecies < 1 || desc->nspecies > DG_MAX_SPECIES)
+      return fail(DG_ERR_INVALID_ARG, "nspecies must be in 1..8");
+    if (!desc->W || !desc->nasa7) return fail(DG_ERR_INVALID_ARG, "NULL W or nasa7");
+    if (desc->mu > 0) return fail(DG_ERR_UNSUPPORTED, "viscous mixtures are not supported");
+    if (!(desc->R_universal > 0)) return fail(DG_ERR_INVALID_ARG, "R_universal must be > 0");
+    if (!(desc->newton_tol > 0) || desc->newton_max_it < 1)
+      return fail(DG_ERR_INVALID_ARG, "need newton_tol > 0 and newton_max_it >= 1");
+    p.ns = desc->nspecies;
+    for (int k = 0; k < p.ns; ++k) {
+      if (!(desc->W[k] > 0)) return fail(DG_ERR_INVALID_ARG, "molar masses must be > 0");
+      p.Rk[k] = desc->R_universal / desc->W[k];
+      for (int i = 0; i < 7; ++i) p.a[k][i] = desc->nasa7[7 * k + i];
+    }
+    p.newton_tol = desc->newton_tol;
+    p.newton_max_it = desc->newton_max_it;
+  } else {
+    return fail(DG_ERR_INVALID_ARG, "unknown gas model");
+  }
+  dg_gas g = new (std::nothrow) dg_gas_s();
+  if (!g) return fail(DG_ERR_OOM, "host allocation failed");
+  g->p = p;
+  cudaGetDevice(&g->device);
+  cudaError_t e = cudaMalloc((void**)&g->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaFree(g->status);
+    delete g;
+    return cuda_fail(e, "gas status allocation");
+  }
+  *out = g;
+  return DG_OK;
+}
+
+int dg_gas_free(dg_gas gas) {
+  if (!gas) return DG_OK;
+  cudaFree(gas->status);
+  delete gas;
+  return DG_OK;
+}
+
+int dg_gas_status(dg_gas gas, uint32_t* bits, int reset) {
+  if (!gas) return fail(DG_ERR_INVALID_ARG, "NULL gas");
+  return read_status(gas->status, bits, reset);
+}
+
+int dg_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* rhs, double* T_io, const dg_opts* opts,
+           void* stream) {
+  return run_rhs(mesh, gas, q, rhs, nullptr, T_io, opts, stream, false, 0, 0.0);
+}
+
+int dg_rk_stage(dg_mesh mesh, dg_gas gas, int32_t stage, double dt, const double* q_in, double* q_out,
+                double* k, double* T_io, const dg_opts* opts, void* stream) {
+  return run_rhs(mesh, gas, q_in, q_out, k, T_io, opts, stream, true, stage, dt);
+}
+
+int dg_temperature(dg_gas gas, int64_t n, const double* q, double* T_io, int32_t* iters, const dg_opts* opts,
+                   void* stream) {
+  if (!gas) return fail(DG_ERR_INVALID_ARG, "NULL gas");
+  if (gas->p.model != DG_GAS_NASA7) return fail(DG_ERR_INVALID_ARG, "dg_temperature needs a NASA-7 gas");
+  if (n < 0) return fail(DG_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DG_OK;
+  if (!q || !T_io) return fail(DG_ERR_INVALID_ARG, "NULL state or temperature");
+  if (int rc = check_opts(opts)) return rc;
+  const int mode = opts ? opts->t_seed : DG_TSEED_INPUT;
+  const double tc = opts ? opts->t_const : 0.0;
+  cudaError_t e = dg::launch_temperature(gas->p, n, q, T_io, iters, mode, tc, gas->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
+  return DG_OK;
+}
+
+int dg_mixture_energy(dg_gas gas, int64_t n, const double* T, const double* Y, double* e_out, void* stream) {
+  if (!gas) return fail(DG_ERR_INVALID_ARG, "NULL gas");
+  if (gas->p.model != DG_GAS_NASA7) return fail(DG_ERR_INVALID_ARG, "dg_mixture_energy needs a NASA-7 gas");
+  if (n < 0) return fail(DG_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DG_OK;
+  if (!T || !Y || !e_out) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
+  cudaError_t e = dg::launch_mixture_energy(gas->p, n, T, Y, e_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mixture energy kernel");
+  return DG_OK;
+}
+
+}  // extern "C"

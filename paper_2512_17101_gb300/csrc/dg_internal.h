@@ -1,0 +1,101 @@
+// Internal declarations of libdg (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dg.h"
+
+namespace dg {
+
+// ---- errors (thread-local message, see dg_last_error) -----------------------
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// ---- host-side builders -----------------------------------------------------
+struct RefOps {
+  int N = 0, Np = 0, Nfp = 0;
+  std::vector<double> Dr, Ds, Dt;  // [Np][Np] row-major
+  std::vector<double> LIFT;        // [Np][4 Nfp]
+  std::vector<int32_t> Fmask;      // [4][Nfp]
+};
+
+// Reference operators of order N on the given nodes (refops.cpp).
+bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err);
+
+// Affine geometric factors, geo[K][DG_GEO_STRIDE] (mesh.cpp).
+bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::string& err);
+
+// Periodic face-node connectivity vmapP[K][4 Nfp] (mesh.cpp).
+bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
+                        const double* ref_nodes, std::vector<int32_t>& vmapP, std::string& err);
+
+// ---- device-side parameter blocks -------------------------------------------
+struct GasParams {  // passed to kernels by value
+  int model;        // DG_GAS_PERFECT / DG_GAS_NASA7
+  int ns;           // species (NASA-7), 0 for a perfect gas
+  double gamma, R, mu, Pr, kappa, cp;
+  double Rk[DG_MAX_SPECIES];
+  double a[DG_MAX_SPECIES][7];
+  double newton_tol;
+  int newton_max_it;
+};
+
+struct MeshDev {
+  int K = 0, N = 0, Np = 0, Nfp = 0;
+  double* ops = nullptr;       // Dr | Ds | Dt | LIFT, row-major
+  int32_t* fmask = nullptr;    // [4][Nfp]
+  double* geo = nullptr;       // [K][DG_GEO_STRIDE]
+  int32_t* vmapP = nullptr;    // [K][4 Nfp]
+  double* scratch = nullptr;   // [9][K][Np] viscous flux (BR1 pass 1 output)
+  unsigned* status = nullptr;  // device status word
+};
+
+// LSRK4 coefficients (Carpenter & Kennedy 1994, five stages, 2N storage).
+extern const double kRK4A[5];
+extern const double kRK4B[5];
+
+// ---- kernel launchers (kernels_dg.cu, kernels_thermo.cu) ------------------------
+// Right-hand side (rk == false: out = rhs) or fused RK stage (rk == true:
+// k <- a k + dt rhs, out = q + b k).  T (may be null for a perfect gas) holds
+// the node temperatures of a mixture.
+cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                       const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
+// BR1 pass 1: viscous flux of a perfect gas into m.scratch.
+cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// Mixture temperature (Newton).  seed_mode: DG_TSEED_*; nvar = 5 + ns; q is [nvar][n].
+cudaError_t launch_temperature(const GasParams& g, int64_t n, const double* q, double* T, int32_t* iters,
+                               int seed_mode, double t_const, unsigned* status, cudaStream_t s);
+cudaError_t launch_mixture_energy(const GasParams& g, int64_t n, const double* T, const double* Y, double* e,
+                                  cudaStream_t s);
+
+}  // namespace dg
+
+namespace dg {
+// Event pairs bracketing kernel launches, resolved lazily (dg_mesh_kernel_times).
+struct KernelTimer {
+  bool enabled = false;
+  std::vector<cudaEvent_t> pool;                                // idle events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[DG_NUM_KERNELS];
+  double ms[DG_NUM_KERNELS] = {0, 0, 0};
+  int64_t count[DG_NUM_KERNELS] = {0, 0, 0};
+};
+}  // namespace dg
+
+struct dg_mesh_s {
+  dg::MeshDev d;
+  dg::KernelTimer timer;
+  dg::RefOps ops;
+  std::vector<int32_t> vmapP;
+  std::vector<double> geo;
+  int device = 0;
+};
+
+struct dg_gas_s {
+  dg::GasParams p;
+  unsigned* status = nullptr;
+  int device = 0;
+};

@@ -1,0 +1,464 @@
+// FP64 nodal-DG kernels for sm_103a: fused volume flux + Lax-Friedrichs surface
+// flux + LIFT (+ optional low-storage RK4 stage update), and the BR1 gradient /
+// viscous-flux pass.
+//
+// Data layout (element-major nodal arrays, Sec. 1 Fig. 1): state [V][K][Np],
+// node index fastest, so the Np*EPB nodes of a block's EPB consecutive
+// elements are one contiguous, coalesced run per variable.  Each block owns EPB
+// elements: it stages the reference operators (Dr|Ds|Dt|LIFT), the elements'
+// geometric factors and their state in shared memory, then runs three phases
+//   1. node-parallel   : pointwise fluxes, contravariant components -> smem
+//   2. face-node-par.  : neighbour gather q+ = q[vmapP], numerical flux -> smem
+//   3. node-parallel   : -sum_a D_a F_a + LIFT g, then the RK update, -> HBM
+// so that no intermediate ever goes to HBM.  On GB300 FP64 runs at 1/64 of the
+// FP32 rate, so these kernels are bound by the FP64 pipe, not by HBM.
+#pragma once
+
+#include "dg_internal.h"
+
+namespace dg {
+namespace kern {
+
+constexpr int GS = DG_GEO_STRIDE;
+
+template <int N>
+struct Ord {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int EPB = N == 1 ? 32 : N == 2 ? 16 : 8;  // elements per block
+  static constexpr int NODES = EPB * Np;                     // node slots per block
+  static constexpr int NT = (NODES + 31) / 32 * 32;          // threads per block
+  static constexpr int OPS = 3 * Np * Np + Np * NF;          // doubles in Dr|Ds|Dt|LIFT
+};
+
+enum Phys { EULER = 0, NAVIER_STOKES = 1, MIXTURE = 2 };
+
+// index of tau_ij in the stored symmetric viscous stress (xx yy zz xy xz yz)
+__device__ __forceinline__ int tau_index(int i, int j) {
+  return i == j ? i : (i + j == 1 ? 3 : (i + j == 2 ? 4 : 5));
+}
+
+// Mixture: R_mix and cp_mix at temperature T from mass fractions Y (nasa-7).
+__device__ __forceinline__ void mixture_cp_R(const GasParams& g, const double* Y, double T, double& cp,
+                                             double& Rmix) {
+  cp = 0.0;
+  Rmix = 0.0;
+#pragma unroll
+  for (int k = 0; k < DG_MAX_SPECIES; ++k) {
+    if (k >= g.ns) break;
+    const double* a = g.a[k];
+    const double cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    cp = fma(Y[k] * g.Rk[k], cpk, cp);
+    Rmix = fma(Y[k], g.Rk[k], Rmix);
+  }
+}
+
+// Pressure and sound speed of state qv (V values) at temperature T (mixture only).
+template <int PHYS, int V>
+__device__ __forceinline__ void thermo(const GasParams& g, const double* qv, double ir, double T, double& p,
+                                       double& c) {
+  const double ke = 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
+  if (PHYS != MIXTURE) {
+    p = (g.gamma - 1.0) * (qv[4] - ke);
+    c = sqrt(g.gamma * p * ir);
+  } else {
+    double Y[DG_MAX_SPECIES];
+#pragma unroll
+    for (int k = 0; k < DG_MAX_SPECIES; ++k) Y[k] = (5 + k < V && k < g.ns) ? qv[5 + k] * ir : 0.0;
+    double cp, Rmix;
+    mixture_cp_R(g, Y, T, cp, Rmix);
+    p = qv[0] * Rmix * T;
+    c = sqrt(cp / (cp - Rmix) * p * ir);
+  }
+}
+
+// Normal Euler flux n.F(q) for velocity normal component un = u.n.
+template <int V>
+__device__ __forceinline__ void normal_flux(const double* qv, double un, double p, double nx, double ny, double nz,
+                                            int nvar, double* fn) {
+  fn[0] = qv[0] * un;
+  fn[1] = fma(qv[1], un, p * nx);
+  fn[2] = fma(qv[2], un, p * ny);
+  fn[3] = fma(qv[3], un, p * nz);
+  fn[4] = (qv[4] + p) * un;
+#pragma unroll
+  for (int v = 5; v < V; ++v)
+    if (v < nvar) fn[v] = qv[v] * un;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Right-hand side, optionally fused with the LSRK4 stage update.
+//   RK == false: out = rhs
+//   RK == true : k <- a k + dt rhs (k read only if a != 0), out = q + b k
+// V is the compile-time maximum of variables; nvar (runtime) <= V are used.
+// ---------------------------------------------------------------------------------------------
+template <int N, int V, int PHYS, bool RK>
+__global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
+    const double* __restrict__ q, double* __restrict__ out, double* __restrict__ kreg,
+    const double* __restrict__ Tg, const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g,
+    const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
+    unsigned* __restrict__ status, const GasParams gp, const int K, const int nvar, const double a,
+    const double b, const double dt) {
+  using O = Ord<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
+  extern __shared__ double smem[];
+  double* sOps = smem;
+  double* sGeo = sOps + O::OPS;
+  double* sQ = sGeo + EPB * GS;
+  double* sF = sQ + V * NODES;
+  double* sG = sF + 3 * V * NODES;
+  double* sFv = sG + V * EPB * NF;
+  double* sT = sFv + (PHYS == NAVIER_STOKES ? 9 * NODES : 0);
+  int* sFm = reinterpret_cast<int*>(sT + (PHYS == MIXTURE ? NODES : 0));
+
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+
+  for (int i = tid; i < O::OPS; i += blockDim.x) sOps[i] = ops_g[i];
+  for (int i = tid; i < NF; i += blockDim.x) sFm[i] = fmask_g[i];
+  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)e0 * GS + i];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+    if (v < nvar)
+      for (int i = tid; i < nn; i += blockDim.x) sQ[v * NODES + i] = q[v * KNp + base + i];
+  if (PHYS == NAVIER_STOKES)
+    for (int c = 0; c < 9; ++c)
+      for (int i = tid; i < nn; i += blockDim.x) sFv[c * NODES + i] = fv_g[c * KNp + base + i];
+  if (PHYS == MIXTURE)
+    for (int i = tid; i < nn; i += blockDim.x) sT[i] = Tg[base + i];
+  __syncthreads();
+
+  // ---- phase 1: pointwise fluxes, contravariant components ----
+  if (tid < nn) {
+    const int e = tid / Np;
+    const double* G = sGeo + e * GS;
+    double qv[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) qv[v] = v < nvar ? sQ[v * NODES + tid] : 0.0;
+    const double ir = 1.0 / qv[0];
+    double p, c;
+    thermo<PHYS, V>(gp, qv, ir, PHYS == MIXTURE ? sT[tid] : 0.0, p, c);
+    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    const double vel[3] = {qv[1] * ir, qv[2] * ir, qv[3] * ir};
+    double F[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      F[d][0] = qv[1 + d];
+      F[d][1] = qv[1] * vel[d];
+      F[d][2] = qv[2] * vel[d];
+      F[d][3] = qv[3] * vel[d];
+      F[d][1 + d] += p;
+      F[d][4] = vel[d] * (qv[4] + p);
+#pragma unroll
+      for (int v = 5; v < V; ++v) F[d][v] = qv[v] * vel[d];
+      if (PHYS == NAVIER_STOKES) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) F[d][1 + i] -= sFv[tau_index(i, d) * NODES + tid];
+        F[d][4] -= sFv[(6 + d) * NODES + tid];
+      }
+    }
+#pragma unroll
+    for (int ra = 0; ra < 3; ++ra) {
+      const double gx = G[3 * ra], gy = G[3 * ra + 1], gz = G[3 * ra + 2];
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (v < nvar) sF[(ra * V + v) * NODES + tid] = fma(gx, F[0][v], fma(gy, F[1][v], gz * F[2][v]));
+    }
+  }
+
+  // ---- phase 2: surface terms g = Fscale (n.G- - G*) at the block's face nodes ----
+  for (int j = tid; j < nel * NF; j += blockDim.x) {
+    const int e = j / NF, m = j - e * NF, f = m / Nfp;
+    const double* G = sGeo + e * GS;
+    const double nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
+    const int own = e * Np + sFm[m];
+    const int P = vmapP[(size_t)(e0 + e) * NF + m];
+    double qm[V], qp[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      qm[v] = v < nvar ? sQ[v * NODES + own] : 0.0;
+      qp[v] = v < nvar ? q[v * KNp + P] : 0.0;
+    }
+    const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
+    double pm, cm, pp, cp;
+    thermo<PHYS, V>(gp, qm, irm, PHYS == MIXTURE ? sT[own] : 0.0, pm, cm);
+    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? Tg[P] : 0.0, pp, cp);
+    const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
+    const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
+    const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
+    double fm[V], fp[V];
+    normal_flux<V>(qm, unm, pm, nx, ny, nz, nvar, fm);
+    normal_flux<V>(qp, unp, pp, nx, ny, nz, nvar, fp);
+    double g[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) g[v] = 0.5 * ((fm[v] - fp[v]) - lam * (qm[v] - qp[v]));
+    if (PHYS == NAVIER_STOKES) {
+      // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2
+      const double nn3[3] = {nx, ny, nz};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double dm = 0.0, dp = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int c = tau_index(i, d);
+          dm = fma(nn3[d], sFv[c * NODES + own], dm);
+          dp = fma(nn3[d], fv_g[c * KNp + P], dp);
+        }
+        g[1 + i] -= 0.5 * (dm - dp);
+      }
+      double em = 0.0, ep = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        em = fma(nn3[d], sFv[(6 + d) * NODES + own], em);
+        ep = fma(nn3[d], fv_g[(6 + d) * KNp + P], ep);
+      }
+      g[4] -= 0.5 * (em - ep);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (v < nvar) sG[v * EPB * NF + j] = fs * g[v];
+  }
+  __syncthreads();
+
+  // ---- phase 3: rhs = -sum_a D_a F_a + LIFT g, then output / RK update ----
+  if (tid < nn) {
+    const int e = tid / Np, i = tid - e * Np;
+    const double* Dr = sOps + i * Np;
+    const double* Ds = sOps + Np * Np + i * Np;
+    const double* Dt = sOps + 2 * Np * Np + i * Np;
+    const double* L = sOps + 3 * Np * Np + i * NF;
+    double acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+#pragma unroll 4
+    for (int jn = 0; jn < Np; ++jn) {
+      const double dr = Dr[jn], ds = Ds[jn], dtt = Dt[jn];
+      const int col = e * Np + jn;
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (v < nvar)
+          acc[v] = fma(dr, sF[(0 * V + v) * NODES + col],
+                       fma(ds, sF[(1 * V + v) * NODES + col], fma(dtt, sF[(2 * V + v) * NODES + col], acc[v])));
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = -acc[v];
+#pragma unroll 4
+    for (int mm = 0; mm < NF; ++mm) {
+      const double l = L[mm];
+      const int col = e * NF + mm;
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (v < nvar) acc[v] = fma(l, sG[v * EPB * NF + col], acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (v >= nvar) break;
+      const size_t gi = v * KNp + base + tid;
+      if (RK) {
+        const double kk = (a != 0.0 ? a * kreg[gi] : 0.0) + dt * acc[v];
+        kreg[gi] = kk;
+        out[gi] = fma(b, kk, sQ[v * NODES + tid]);
+      } else {
+        out[gi] = acc[v];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// BR1 pass 1 for a perfect gas: gradients of w = (rho, rho u, rho v, rho w, T) with
+// the central flux, then the viscous stress and energy flux per node:
+//   grad_d w = sum_a (dr_a/dx_d) D_a w + sum_f n_d,f LIFT_f (Fscale (w+ - w-)/2)
+//   out[9][K][Np] = (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, Q_x, Q_y, Q_z),
+//   Q_d = sum_i u_i tau_id + kappa dT/dx_d.
+// ---------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
+    const double* __restrict__ q, double* __restrict__ fv_out, const double* __restrict__ ops_g,
+    const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP,
+    unsigned* __restrict__ status, const GasParams gp, const int K) {
+  using O = Ord<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
+  constexpr int W = 5;
+  extern __shared__ double smem[];
+  double* sOps = smem;
+  double* sGeo = sOps + O::OPS;
+  double* sW = sGeo + EPB * GS;
+  double* sJ = sW + W * NODES;
+  int* sFm = reinterpret_cast<int*>(sJ + W * EPB * NF);
+
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+
+  for (int i = tid; i < O::OPS; i += blockDim.x) sOps[i] = ops_g[i];
+  for (int i = tid; i < NF; i += blockDim.x) sFm[i] = fmask_g[i];
+  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)e0 * GS + i];
+  const double gm1 = gp.gamma - 1.0, iR = 1.0 / gp.R;
+  if (tid < nn) {
+    double qv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
+    const double ir = 1.0 / qv[0];
+    const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
+    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sW[v * NODES + tid] = qv[v];
+    sW[4 * NODES + tid] = p * ir * iR;
+  }
+  __syncthreads();
+
+  for (int j = tid; j < nel * NF; j += blockDim.x) {
+    const int e = j / NF, m = j - e * NF, f = m / Nfp;
+    const double fs = sGeo[e * GS + 12 + 4 * f];
+    const int own = e * Np + sFm[m];
+    const int P = vmapP[(size_t)(e0 + e) * NF + m];
+    double qp[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + P];
+    const double irp = 1.0 / qp[0];
+    const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+    const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
+    const double hf = 0.5 * fs;
+#pragma unroll
+    for (int v = 0; v < W; ++v) sJ[v * EPB * NF + j] = hf * (wp[v] - sW[v * NODES + own]);
+  }
+  __syncthreads();
+
+  if (tid < nn) {
+    const int e = tid / Np, i = tid - e * Np;
+    const double* G = sGeo + e * GS;
+    const double* Dr = sOps + i * Np;
+    const double* Ds = sOps + Np * Np + i * Np;
+    const double* Dt = sOps + 2 * Np * Np + i * Np;
+    const double* L = sOps + 3 * Np * Np + i * NF;
+    double dref[3][W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) dref[0][v] = dref[1][v] = dref[2][v] = 0.0;
+#pragma unroll 4
+    for (int jn = 0; jn < Np; ++jn) {
+      const double dr = Dr[jn], ds = Ds[jn], dtt = Dt[jn];
+#pragma unroll
+      for (int v = 0; v < W; ++v) {
+        const double w = sW[v * NODES + e * Np + jn];
+        dref[0][v] = fma(dr, w, dref[0][v]);
+        dref[1][v] = fma(ds, w, dref[1][v]);
+        dref[2][v] = fma(dtt, w, dref[2][v]);
+      }
+    }
+    double grad[3][W];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < W; ++v)
+        grad[d][v] = fma(G[d], dref[0][v], fma(G[3 + d], dref[1][v], G[6 + d] * dref[2][v]));
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      double lf[W];
+#pragma unroll
+      for (int v = 0; v < W; ++v) lf[v] = 0.0;
+#pragma unroll 5
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const double l = L[f * Nfp + jj];
+        const int col = e * NF + f * Nfp + jj;
+#pragma unroll
+        for (int v = 0; v < W; ++v) lf[v] = fma(l, sJ[v * EPB * NF + col], lf[v]);
+      }
+      const double nf[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < W; ++v) grad[d][v] = fma(nf[d], lf[v], grad[d][v]);
+    }
+    const double rho = sW[tid], ir = 1.0 / rho;
+    const double u[3] = {sW[NODES + tid] * ir, sW[2 * NODES + tid] * ir, sW[3 * NODES + tid] * ir};
+    double du[3][3];  // du[i][d] = d u_i / d x_d
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) du[ii][d] = (grad[d][1 + ii] - u[ii] * grad[d][0]) * ir;
+    const double mu = gp.mu;
+    const double divu = du[0][0] + du[1][1] + du[2][2];
+    double tau[3][3];
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) tau[ii][jj] = mu * (du[ii][jj] + du[jj][ii]);
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii) tau[ii][ii] -= (2.0 / 3.0) * mu * divu;
+    const size_t gi = base + tid;
+    fv_out[0 * KNp + gi] = tau[0][0];
+    fv_out[1 * KNp + gi] = tau[1][1];
+    fv_out[2 * KNp + gi] = tau[2][2];
+    fv_out[3 * KNp + gi] = tau[0][1];
+    fv_out[4 * KNp + gi] = tau[0][2];
+    fv_out[5 * KNp + gi] = tau[1][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      fv_out[(6 + d) * KNp + gi] =
+          fma(u[0], tau[0][d], fma(u[1], tau[1][d], fma(u[2], tau[2][d], gp.kappa * grad[d][4])));
+  }
+}
+
+// Dynamic shared memory of rhs_kernel / viscous_kernel, in bytes.
+template <int N, int V, int PHYS>
+constexpr size_t rhs_smem() {
+  using O = Ord<N>;
+  return sizeof(double) * (O::OPS + O::EPB * GS + V * O::NODES + 3 * V * O::NODES + V * O::EPB * O::NF +
+                           (PHYS == NAVIER_STOKES ? 9 * O::NODES : 0) + (PHYS == MIXTURE ? O::NODES : 0)) +
+         sizeof(int) * O::NF;
+}
+
+template <int N>
+constexpr size_t viscous_smem() {
+  using O = Ord<N>;
+  return sizeof(double) * (O::OPS + O::EPB * GS + 5 * O::NODES + 5 * O::EPB * O::NF) + sizeof(int) * O::NF;
+}
+
+template <int N, int V, int PHYS, bool RK>
+cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                         const double* T, int nvar, double a, double b, double dt, cudaStream_t s) {
+  using O = Ord<N>;
+  constexpr size_t smem = rhs_smem<N, V, PHYS>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(rhs_kernel<N, V, PHYS, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int blocks = (m.K + O::EPB - 1) / O::EPB;
+  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP, m.scratch,
+                                                           m.status, g, m.K, nvar, a, b, dt);
+  return cudaGetLastError();
+}
+
+template <int V, int PHYS>
+cudaError_t dispatch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                         const double* T, bool rk, double a, double b, double dt, cudaStream_t s) {
+  const int nvar = 5 + g.ns;
+  switch (m.N) {
+#define DG_CASE(NN)                                                                         \
+  case NN:                                                                                  \
+    return rk ? launch_rhs_t<NN, V, PHYS, true>(m, g, q, out, k, T, nvar, a, b, dt, s)      \
+              : launch_rhs_t<NN, V, PHYS, false>(m, g, q, out, k, T, nvar, a, b, dt, s);
+    DG_CASE(1)
+    DG_CASE(2)
+    DG_CASE(3)
+    DG_CASE(4)
+#undef DG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace kern
+}  // namespace dg

@@ -1,0 +1,247 @@
+// Reference-tetrahedron operators of nodal DG (the element-local operators
+// that the paper's DG layout, Sec. 1 Fig. 1, applies to every element; "full
+// assembly of all DG operators", Sec. 5.2).
+//
+// Built from the nodal basis l_i (degree <= N, l_i(x_j) = delta_ij), in long
+// double with Gauss-Jordan elimination:
+//   Dr = Vr V^-1 (likewise Ds, Dt) with the monomial Vandermonde V of
+//        r^a s^b t^c, whose derivatives are exact;
+//   M^-1 = Vo Vo^T with the Vandermonde Vo of an orthonormal basis of the
+//        degree-N polynomials on the reference tetrahedron
+//        {r,s,t >= -1, r+s+t <= -1} (collapsed-coordinate products of
+//        normalised Jacobi polynomials), which needs no ill-conditioned Gram
+//        matrix or inversion;
+//   E_f = face mass of face f in its parameter coordinates (parameter triangle
+//        of area 2), (Wo Wo^T)^-1 with the orthonormal triangle basis Wo at the
+//        face nodes, placed on the rows of the face's nodes;
+//   LIFT = M^-1 [E_0 | E_1 | E_2 | E_3].
+// Orthonormal bases: with normalised Jacobi polynomials P~_n^(al,be),
+//   triangle {x,y >= -1, x+y <= 0}: a = 2(1+x)/(1-y) - 1, b = y,
+//     psi_ij = sqrt(2) P~_i^(0,0)(a) P~_j^(2i+1,0)(b) (1-b)^i;
+//   tetrahedron: a = -2(1+r)/(s+t) - 1, b = 2(1+s)/(1-t) - 1, c = t,
+//     psi_ijk = 2 sqrt(2) P~_i^(0,0)(a) P~_j^(2i+1,0)(b) (1-b)^i P~_k^(2i+2j+2,0)(c) (1-c)^(i+j)
+// (the powers of (1-b)/2, (1-c)/2 that the collapse's Jacobian
+// (1-b)/2 ((1-c)/2)^2 needs for orthogonality, with the factors of 2 folded
+// into the constants); a and b are set to -1 where the collapse is singular.
+// Faces: 0: t = -1 (params r,s), 1: s = -1 (r,t), 2: r+s+t = -1 (s,t),
+// 3: r = -1 (s,t); face nodes are listed in increasing volume-node order.
+#include <cmath>
+
+#include "dg_internal.h"
+
+namespace dg {
+namespace {
+
+typedef long double ld;
+
+ld ipow(ld x, int n) {
+  ld r = 1;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+ld factorial(int n) {
+  ld r = 1;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+// In-place inverse of the n x n row-major matrix A; false if singular.
+bool invert(std::vector<ld>& A, int n) {
+  std::vector<ld> I(n * n, 0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(A[r * n + c]) > fabsl(A[piv * n + c])) piv = r;
+    if (fabsl(A[piv * n + c]) < 1e-300L) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[c * n + j], A[piv * n + j]);
+        std::swap(I[c * n + j], I[piv * n + j]);
+      }
+    ld inv = 1 / A[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[c * n + j] *= inv;
+      I[c * n + j] *= inv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      ld f = A[r * n + c];
+      if (f == 0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[r * n + j] -= f * A[c * n + j];
+        I[r * n + j] -= f * I[c * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// C = A (n x m) * B (m x p)
+std::vector<ld> matmul(const std::vector<ld>& A, const std::vector<ld>& B, int n, int m, int p) {
+  std::vector<ld> C(n * p, 0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < m; ++k) {
+      ld a = A[i * m + k];
+      for (int j = 0; j < p; ++j) C[i * p + j] += a * B[k * p + j];
+    }
+  return C;
+}
+
+std::vector<ld> transpose(const std::vector<ld>& A, int n, int m) {
+  std::vector<ld> T(m * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) T[j * n + i] = A[i * m + j];
+  return T;
+}
+
+ld face_residual(int f, ld r, ld s, ld t) {
+  switch (f) {
+    case 0: return 1 + t;
+    case 1: return 1 + s;
+    case 2: return 1 + r + s + t;
+    default: return 1 + r;
+  }
+}
+
+void face_params(int f, ld r, ld s, ld t, ld& x, ld& y) {
+  switch (f) {
+    case 0: x = r; y = s; break;
+    case 1: x = r; y = t; break;
+    default: x = s; y = t; break;
+  }
+}
+
+// Normalised Jacobi polynomial P~_n^(al,be)(x): the three-term recurrence of
+// the classical P_n^(al,be), divided by sqrt of
+// gamma_n = 2^(al+be+1) / (2n+al+be+1) * (n+al)! (n+be)! / ((n+al+be)! n!).
+ld jacobi(ld x, int al, int be, int n) {
+  ld p0 = 1, p1 = 0.5L * ((al + be + 2) * x + (al - be));
+  ld pn = n == 0 ? p0 : p1;
+  for (int k = 2; k <= n; ++k) {
+    const ld s = 2 * k + al + be;
+    const ld a1 = 2.0L * k * (k + al + be) * (s - 2);
+    const ld a2 = (s - 1) * (ld)(al * al - be * be);
+    const ld a3 = (s - 2) * (s - 1) * s;
+    const ld a4 = 2.0L * (k + al - 1) * (k + be - 1) * s;
+    pn = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+    p0 = p1;
+    p1 = pn;
+  }
+  const ld gam = ipow(2, al + be + 1) / (2 * n + al + be + 1) * factorial(n + al) * factorial(n + be) /
+                 (factorial(n + al + be) * factorial(n));
+  return pn / sqrtl(gam);
+}
+
+ld ortho_tri(int i, int j, ld x, ld y) {
+  const ld a = fabsl(1 - y) > 1e-13L ? 2 * (1 + x) / (1 - y) - 1 : -1;
+  const ld b = y;
+  return sqrtl(2.0L) * jacobi(a, 0, 0, i) * jacobi(b, 2 * i + 1, 0, j) * ipow(1 - b, i);
+}
+
+ld ortho_tet(int i, int j, int k, ld r, ld s, ld t) {
+  const ld a = fabsl(s + t) > 1e-13L ? -2 * (1 + r) / (s + t) - 1 : -1;
+  const ld b = fabsl(1 - t) > 1e-13L ? 2 * (1 + s) / (1 - t) - 1 : -1;
+  const ld c = t;
+  return 2 * sqrtl(2.0L) * jacobi(a, 0, 0, i) * jacobi(b, 2 * i + 1, 0, j) * ipow(1 - b, i) *
+         jacobi(c, 2 * i + 2 * j + 2, 0, k) * ipow(1 - c, i + j);
+}
+
+}  // namespace
+
+bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err) {
+  if (N < 1 || N > DG_MAX_ORDER) {
+    err = "order must be in 1.." + std::to_string(DG_MAX_ORDER);
+    return false;
+  }
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  const int Nfp = (N + 1) * (N + 2) / 2;
+  std::vector<int> ea, eb, ec;
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; a + b <= N; ++b)
+      for (int c = 0; a + b + c <= N; ++c) {
+        ea.push_back(a);
+        eb.push_back(b);
+        ec.push_back(c);
+      }
+  std::vector<ld> V(Np * Np), Vr(Np * Np, 0), Vs(Np * Np, 0), Vt(Np * Np, 0);
+  for (int i = 0; i < Np; ++i) {
+    ld r = nodes[3 * i], s = nodes[3 * i + 1], t = nodes[3 * i + 2];
+    for (int m = 0; m < Np; ++m) {
+      int a = ea[m], b = eb[m], c = ec[m];
+      V[i * Np + m] = ipow(r, a) * ipow(s, b) * ipow(t, c);
+      if (a) Vr[i * Np + m] = a * ipow(r, a - 1) * ipow(s, b) * ipow(t, c);
+      if (b) Vs[i * Np + m] = b * ipow(r, a) * ipow(s, b - 1) * ipow(t, c);
+      if (c) Vt[i * Np + m] = c * ipow(r, a) * ipow(s, b) * ipow(t, c - 1);
+    }
+  }
+  std::vector<ld> Vinv = V;
+  if (!invert(Vinv, Np)) {
+    err = "reference nodes are not unisolvent for this order";
+    return false;
+  }
+  // M^-1 = Vo Vo^T from the orthonormal basis
+  std::vector<ld> Vo(Np * Np);
+  for (int n = 0; n < Np; ++n) {
+    const ld r = nodes[3 * n], s = nodes[3 * n + 1], t = nodes[3 * n + 2];
+    int m = 0;
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; a + b <= N; ++b)
+        for (int c = 0; a + b + c <= N; ++c) Vo[n * Np + m++] = ortho_tet(a, b, c, r, s, t);
+  }
+  std::vector<ld> Minv = matmul(Vo, transpose(Vo, Np, Np), Np, Np, Np);
+
+  // face nodes and face mass matrices
+  std::vector<int32_t> Fmask(4 * Nfp);
+  std::vector<ld> E(Np * 4 * Nfp, 0);
+  for (int f = 0; f < 4; ++f) {
+    int cnt = 0;
+    for (int i = 0; i < Np; ++i) {
+      ld res = face_residual(f, nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2]);
+      if (fabsl(res) < 1e-10L) {
+        if (cnt >= Nfp) {
+          err = "too many nodes on a reference face";
+          return false;
+        }
+        Fmask[f * Nfp + cnt++] = i;
+      }
+    }
+    if (cnt != Nfp) {
+      err = "reference face " + std::to_string(f) + " holds " + std::to_string(cnt) + " nodes, expected " +
+            std::to_string(Nfp);
+      return false;
+    }
+    std::vector<ld> W2(Nfp * Nfp);
+    for (int a = 0; a < Nfp; ++a) {
+      int i = Fmask[f * Nfp + a];
+      ld x, y;
+      face_params(f, nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2], x, y);
+      int m = 0;
+      for (int p = 0; p <= N; ++p)
+        for (int q = 0; p + q <= N; ++q) W2[a * Nfp + m++] = ortho_tri(p, q, x, y);
+    }
+    std::vector<ld> Mf = matmul(W2, transpose(W2, Nfp, Nfp), Nfp, Nfp, Nfp);
+    if (!invert(Mf, Nfp)) {
+      err = "face nodes are not unisolvent";
+      return false;
+    }
+    for (int a = 0; a < Nfp; ++a)
+      for (int b = 0; b < Nfp; ++b) E[Fmask[f * Nfp + a] * 4 * Nfp + f * Nfp + b] = Mf[a * Nfp + b];
+  }
+  std::vector<ld> LIFT = matmul(Minv, E, Np, Np, 4 * Nfp);
+  std::vector<ld> Dr = matmul(Vr, Vinv, Np, Np, Np), Ds = matmul(Vs, Vinv, Np, Np, Np),
+                  Dt = matmul(Vt, Vinv, Np, Np, Np);
+  out.N = N;
+  out.Np = Np;
+  out.Nfp = Nfp;
+  out.Dr.assign(Dr.begin(), Dr.end());
+  out.Ds.assign(Ds.begin(), Ds.end());
+  out.Dt.assign(Dt.begin(), Dt.end());
+  out.LIFT.assign(LIFT.begin(), LIFT.end());
+  out.Fmask = Fmask;
+  return true;
+}
+
+}  // namespace dg

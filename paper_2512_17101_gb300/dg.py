@@ -1,0 +1,237 @@
+"""Python binding of libdg: same names as the C ABI, argument marshalling only.
+
+Device arrays are torch CUDA tensors (float64 / int32, contiguous); torch is
+used for device memory and streams, every computation runs in libdg's CUDA
+kernels.  Host arrays are numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+from .capi import check, load
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0):
+    o = capi.dg_opts()
+    o.precision = precision
+    o.t_seed = t_seed
+    o.t_const = t_const
+    return o
+
+
+# ---- mesh -------------------------------------------------------------------------------
+
+class Mesh:
+    """An uploaded mesh (dg_mesh handle)."""
+
+    def __init__(self, vertices, period, N, ref_nodes, host_only=False):
+        lib = load()
+        self._v = np.ascontiguousarray(vertices, dtype=np.float64)
+        self._r = np.ascontiguousarray(ref_nodes, dtype=np.float64)
+        if self._v.ndim != 3 or self._v.shape[1:] != (4, 3):
+            raise ValueError("vertices must be [K][4][3]")
+        d = capi.dg_mesh_desc()
+        d.K = self._v.shape[0]
+        d.N = int(N)
+        d.ref_nodes = _hptr(self._r)
+        d.vertices = _hptr(self._v)
+        for i in range(3):
+            d.period[i] = float(period[i])
+        d.flags = capi.DG_MESH_HOST_ONLY if host_only else 0
+        h = ctypes.c_void_p()
+        check(lib.dg_mesh_upload(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        K, N_, Np, Nfp = (ctypes.c_int32() for _ in range(4))
+        check(lib.dg_mesh_info(h, ctypes.byref(K), ctypes.byref(N_), ctypes.byref(Np), ctypes.byref(Nfp)))
+        self.K, self.N, self.Np, self.Nfp = K.value, N_.value, Np.value, Nfp.value
+
+    def operators(self):
+        Np, NF = self.Np, 4 * self.Nfp
+        Dr, Ds, Dt = (np.zeros((Np, Np)) for _ in range(3))
+        LIFT = np.zeros((Np, NF))
+        Fm = np.zeros((4, self.Nfp), dtype=np.int32)
+        check(load().dg_mesh_operators(self.handle, _hptr(Dr), _hptr(Ds), _hptr(Dt), _hptr(LIFT), _hptr(Fm)))
+        return dict(Dr=Dr, Ds=Ds, Dt=Dt, LIFT=LIFT, Fmask=Fm)
+
+    def connectivity(self):
+        vmapP = np.zeros((self.K, 4 * self.Nfp), dtype=np.int32)
+        geo = np.zeros((self.K, capi.DG_GEO_STRIDE))
+        check(load().dg_mesh_connectivity(self.handle, _hptr(vmapP), _hptr(geo)))
+        return vmapP, geo
+
+    def set_timing(self, enable=True):
+        check(load().dg_mesh_set_timing(self.handle, int(enable)))
+
+    def kernel_times(self, reset=True):
+        """{kernel name: (total ms, launches)} of the event-timed launches since the last reset."""
+        ms = np.zeros(capi.DG_NUM_KERNELS)
+        n = np.zeros(capi.DG_NUM_KERNELS, dtype=np.int64)
+        check(load().dg_mesh_kernel_times(self.handle, _hptr(ms), _hptr(n), int(reset)))
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(capi.KERNEL_NAMES)}
+
+    def status(self, reset=True):
+        bits = ctypes.c_uint32()
+        check(load().dg_mesh_status(self.handle, ctypes.byref(bits), int(reset)))
+        return bits.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().dg_mesh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dg_mesh_upload(vertices, period, N, ref_nodes, host_only=False) -> Mesh:
+    return Mesh(vertices, period, N, ref_nodes, host_only=host_only)
+
+
+def dg_mesh_free(mesh: Mesh) -> None:
+    mesh.close()
+
+
+# ---- gas ----------------------------------------------------------------------------------
+
+class Gas:
+    """A gas model (dg_gas handle): perfect gas or NASA-7 mixture."""
+
+    def __init__(self, *, model="perfect", gamma=1.4, R=1.0, mu=0.0, Pr=0.71, W=None, nasa7=None,
+                 R_universal=8314.462618, newton_tol=1e-10, newton_max_it=50):
+        lib = load()
+        d = capi.dg_gas_desc()
+        d.mu = mu
+        d.Pr = Pr
+        if model == "perfect":
+            d.model = capi.DG_GAS_PERFECT
+            d.gamma = gamma
+            d.R = R
+            self.nspecies = 0
+        elif model == "nasa7":
+            d.model = capi.DG_GAS_NASA7
+            self._W = np.ascontiguousarray(W, dtype=np.float64)
+            self._a = np.ascontiguousarray(nasa7, dtype=np.float64)
+            d.nspecies = self._W.shape[0]
+            d.W = _hptr(self._W)
+            d.nasa7 = _hptr(self._a)
+            d.R_universal = R_universal
+            d.newton_tol = newton_tol
+            d.newton_max_it = newton_max_it
+            self.nspecies = int(self._W.shape[0])
+        else:
+            raise ValueError(model)
+        h = ctypes.c_void_p()
+        check(lib.dg_gas_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.nvar = 5 + self.nspecies
+        self.model = model
+
+    def status(self, reset=True):
+        bits = ctypes.c_uint32()
+        check(load().dg_gas_status(self.handle, ctypes.byref(bits), int(reset)))
+        return bits.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().dg_gas_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dg_gas_create(**kw) -> Gas:
+    return Gas(**kw)
+
+
+# ---- hot path -------------------------------------------------------------------------------
+
+def dg_rhs(mesh: Mesh, gas: Gas, q, rhs, T_io=None, opts=None, stream=None):
+    """rhs <- dq/dt for q [V][K][Np] (CUDA float64)."""
+    import torch
+    o = opts if opts is not None else _opts()
+    check(load().dg_rhs(mesh.handle, gas.handle, _dptr(q, torch.float64, "q"), _dptr(rhs, torch.float64, "rhs"),
+                        _dptr(T_io, torch.float64, "T_io"), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def dg_rk_stage(mesh: Mesh, gas: Gas, stage, dt, q_in, q_out, k, T_io=None, opts=None, stream=None):
+    """LSRK4 stage: k <- a_s k + dt rhs(q_in); q_out <- q_in + b_s k."""
+    import torch
+    o = opts if opts is not None else _opts()
+    check(load().dg_rk_stage(mesh.handle, gas.handle, int(stage), float(dt), _dptr(q_in, torch.float64, "q_in"),
+                             _dptr(q_out, torch.float64, "q_out"), _dptr(k, torch.float64, "k"),
+                             _dptr(T_io, torch.float64, "T_io"), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def dg_lsrk4_coefficients():
+    a = np.zeros(5)
+    b = np.zeros(5)
+    check(load().dg_lsrk4_coefficients(_hptr(a), _hptr(b)))
+    return a, b
+
+
+def dg_temperature(gas: Gas, q, T_io, iters=None, opts=None, stream=None):
+    """Newton temperature of a NASA-7 mixture, q [V][n] (or [V][K][Np]), T_io [n]."""
+    import torch
+    n = T_io.numel()
+    o = opts if opts is not None else _opts()
+    check(load().dg_temperature(gas.handle, n, _dptr(q, torch.float64, "q"), _dptr(T_io, torch.float64, "T_io"),
+                                _dptr(iters, torch.int32, "iters"), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def dg_mixture_energy(gas: Gas, T, Y, e, stream=None):
+    """e(T, Y) per node; T [n], Y [nspecies][n], e [n]."""
+    import torch
+    check(load().dg_mixture_energy(gas.handle, T.numel(), _dptr(T, torch.float64, "T"), _dptr(Y, torch.float64, "Y"),
+                                   _dptr(e, torch.float64, "e"), _stream_ptr(stream)))
+
+
+def lsrk4_step(mesh, gas, q, dt, steps=1, T_io=None, opts=None, stream=None, work=None):
+    """Advance q in place by ``steps`` LSRK4 steps (5 stages each) with ping-pong buffers."""
+    import torch
+    if work is None:
+        work = (torch.empty_like(q), torch.zeros_like(q))
+    qb, k = work
+    cur, nxt = q, qb
+    for _ in range(steps):
+        for s in range(5):
+            dg_rk_stage(mesh, gas, s, dt, cur, nxt, k, T_io=T_io, opts=opts, stream=stream)
+            cur, nxt = nxt, cur
+    if cur is not q:
+        q.copy_(cur)
+    return q

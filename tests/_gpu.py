@@ -1,0 +1,27 @@
+"""Helpers for the GPU parity tests (CUDA path through the C ABI vs the oracle)."""
+
+import numpy as np
+import pytest
+
+
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    from paper_2512_17101_gb300 import capi
+    import os
+    if not os.path.exists(capi.LIB_PATH):
+        __graft_entry__.build()
+    return torch
+
+
+def rel_err(got, want):
+    """Max over variables of max|got_v - want_v| / max|want_v| (max-norm per conserved variable)."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    errs = []
+    for v in range(want.shape[0]):
+        scale = np.abs(want[v]).max()
+        errs.append(np.abs(got[v] - want[v]).max() / (scale if scale > 0 else 1.0))
+    return max(errs)
