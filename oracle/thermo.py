@@ -120,7 +120,10 @@ class Nasa7Gas:
         """Per-node Newton; returns (T, iterations, converged)."""
         tol = self.newton_tol if tol is None else tol
         max_it = self.newton_max_it if max_it is None else max_it
-        T = np.array(T0, dtype=np.float64, copy=True)
+        shape = np.shape(e)
+        e = np.asarray(e, dtype=np.float64).reshape(-1)
+        Y = np.asarray(Y, dtype=np.float64).reshape(self.nspecies, -1)
+        T = np.array(T0, dtype=np.float64, copy=True).reshape(-1)
         iters = np.zeros(T.shape, dtype=np.int64)
         active = np.ones(T.shape, dtype=bool)
         for _ in range(max_it):
@@ -134,7 +137,7 @@ class Nasa7Gas:
             done = np.abs(dT) < tol
             idx = np.flatnonzero(active)
             active[idx[done]] = False
-        return T, iters, ~active
+        return T.reshape(shape), iters.reshape(shape), ~active.reshape(shape)
 
     def bisect_temperature(self, e, Y, lo=300.0, hi=3000.0, tol=1e-12):
         """Bisection on [lo, hi] (e(T) is increasing there); independent check of Newton."""

@@ -62,7 +62,7 @@ def test_euler_small_config_one_rk4_step():
     dg.lsrk4_step(mesh, gas, q, 1e-3, steps=1)
     want = lsrk4_step(q0, 1e-3, f)
     assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL  # the step's increment, not the state
-    assert rel_err(q.cpu().numpy(), want) <= 1e-14
+    assert rel_err(q.cpu().numpy(), want) <= 1e-13
 
 
 def test_rk_stage_semantics():
