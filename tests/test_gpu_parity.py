@@ -186,7 +186,9 @@ def test_mixture_energy_inverts_temperature():
 
 @pytest.mark.parametrize("N", [1, 2, 3])
 def test_mixture_rhs(N):
-    torch, dg, d, mesh, gas, gas_o, q0, T_true = _mixture_setup((3, 2, 2), N, seed=1)
+    # a 3^3 box: on a 2-cell lattice sin(2 pi y) vanishes at every N=1 node and the x/y-momentum
+    # right-hand side degenerates to rounding noise of the uniform pressure
+    torch, dg, d, mesh, gas, gas_o, q0, T_true = _mixture_setup(3, N, seed=1)
     q = torch.tensor(q0, device="cuda")
     rhs = torch.empty_like(q)
     T = torch.full(q0.shape[1:], 1650.0, device="cuda", dtype=torch.float64)
@@ -196,7 +198,10 @@ def test_mixture_rhs(N):
     want = rhs_strong(d.ref, d.geo, d.conn, q0, gas_o, T=Tw)
     assert ok.all()
     assert np.abs(T.cpu().numpy() - Tw).max() < 1e-9
-    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    got = rhs.cpu().numpy()
+    per_var = [float(np.abs(got[v] - want[v]).max() / np.abs(want[v]).max()) for v in range(want.shape[0])]
+    worst = np.unravel_index(np.argmax(np.abs(got[4] - want[4])), want[4].shape)
+    assert rel_err(got, want) <= TOL, (per_var, worst, got[:, worst[0], worst[1]], want[:, worst[0], worst[1]])
 
 
 def test_status_flags_without_fault():
