@@ -207,6 +207,43 @@ int dg_temperature(dg_gas gas, int64_t n, const double* q_dev, double* T_io_dev,
 int dg_mixture_energy(dg_gas gas, int64_t n, const double* T_dev, const double* Y_dev, double* e_dev,
                       void* stream);
 
+/* ---- allocation-free stage (no counterpart in the paper) --------------------------
+ * For callers that cannot call cudaMalloc: code whose device memory is owned by
+ * another allocator (a host framework's memory pool that has reserved the
+ * device, an arena with a fixed budget), or loops where an allocation's implicit
+ * device synchronisation is not acceptable.  Such a caller allocates the tables
+ * and buffers itself, fills the tables from a DG_MESH_HOST_ONLY mesh
+ * (dg_mesh_operators, dg_mesh_connectivity; no CUDA call is made to build it),
+ * and calls dg_rk_stage_noalloc, which allocates nothing: the viscous-flux
+ * scratch of the BR1 pass lives in a static device array of
+ * DG_STATIC_SCRATCH_NODES * 9 doubles (36 MiB) that every GPU which loads the
+ * library holds until the process exits. */
+#define DG_STATIC_SCRATCH_NODES (1 << 19) /* largest K * Np accepted */
+
+typedef struct {
+  int32_t K;                 /* tetrahedra                                            */
+  int32_t N;                 /* order, 1..DG_MAX_ORDER                                 */
+  const double* ops_dev;     /* [3 Np Np + Np 4 Nfp]: Dr | Ds | Dt | LIFT, row-major  */
+  const int32_t* fmask_dev;  /* [4][Nfp]                                               */
+  const double* geo_dev;     /* [K][DG_GEO_STRIDE]                                     */
+  const int32_t* vmapP_dev;  /* [K][4 Nfp]                                             */
+} dg_mesh_tables;
+
+/* Same stage as dg_rk_stage for a viscous perfect gas (gas->model ==
+ * DG_GAS_PERFECT, gas->mu > 0): k <- a_s k + dt rhs(q_in), q_out <- q_in + b_s k,
+ * with the same kernels, on caller-owned tables and buffers.  status_dev: one
+ * uint32 in device memory that receives DG_STATUS_* bits (atomic OR; the
+ * caller clears it).  Rejects K * Np > DG_STATIC_SCRATCH_NODES with
+ * DG_ERR_INVALID_ARG.  The first call on a device looks up the device address
+ * of the static array (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call shares the one array
+ * and leaves its content behind; the stage writes all of it that it reads, so
+ * nothing needs clearing, but calls that overlap in time on the GPU (other
+ * streams, other host threads) race on it and must be serialised. */
+int dg_rk_stage_noalloc(const dg_mesh_tables* tables, const dg_gas_desc* gas, int32_t stage, double dt,
+                        const double* q_in_dev, double* q_out_dev, double* k_dev, uint32_t* status_dev,
+                        void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dg_last_error(void);
 

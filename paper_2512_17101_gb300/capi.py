@@ -29,6 +29,7 @@ DG_PREC_FP64 = 0
 DG_TSEED_INPUT = 0
 DG_TSEED_CONST = 1
 DG_MESH_HOST_ONLY = 1
+DG_STATIC_SCRATCH_NODES = 1 << 19
 DG_KERNEL_VISCOUS = 0
 DG_KERNEL_RHS = 1
 DG_KERNEL_TEMPERATURE = 2
@@ -48,6 +49,11 @@ class dg_gas_desc(ctypes.Structure):
     _fields_ = [("model", c_int32), ("gamma", c_double), ("R", c_double), ("mu", c_double), ("Pr", c_double),
                 ("nspecies", c_int32), ("W", c_void_p), ("nasa7", c_void_p), ("R_universal", c_double),
                 ("newton_tol", c_double), ("newton_max_it", c_int32)]
+
+
+class dg_mesh_tables(ctypes.Structure):
+    _fields_ = [("K", c_int32), ("N", c_int32), ("ops_dev", c_void_p), ("fmask_dev", c_void_p),
+                ("geo_dev", c_void_p), ("vmapP_dev", c_void_p)]
 
 
 class dg_opts(ctypes.Structure):
@@ -75,6 +81,8 @@ SIGNATURES = {
     "dg_temperature": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.POINTER(dg_opts),
                                  c_void_p]),
     "dg_mixture_energy": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_rk_stage_noalloc": (c_int32, [ctypes.POINTER(dg_mesh_tables), ctypes.POINTER(dg_gas_desc), c_int32,
+                                      c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_last_error": (ctypes.c_char_p, []),
 }
 

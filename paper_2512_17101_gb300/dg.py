@@ -235,3 +235,25 @@ def lsrk4_step(mesh, gas, q, dt, steps=1, T_io=None, opts=None, stream=None, wor
     if cur is not q:
         q.copy_(cur)
     return q
+
+
+def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, stream=None):
+    """Allocation-free viscous stage on caller-owned tables.
+
+    tables: dict(K, N, ops, fmask, geo, vmapP) of CUDA tensors (float64 ops/geo, int32 fmask/vmapP);
+    gas_desc: dict(gamma, R, mu, Pr); status: CUDA int32 tensor of one element.
+    """
+    import torch
+    t = capi.dg_mesh_tables()
+    t.K, t.N = int(tables["K"]), int(tables["N"])
+    t.ops_dev = _dptr(tables["ops"], torch.float64, "ops")
+    t.fmask_dev = _dptr(tables["fmask"], torch.int32, "fmask")
+    t.geo_dev = _dptr(tables["geo"], torch.float64, "geo")
+    t.vmapP_dev = _dptr(tables["vmapP"], torch.int32, "vmapP")
+    g = capi.dg_gas_desc()
+    g.model = capi.DG_GAS_PERFECT
+    g.gamma, g.R, g.mu, g.Pr = (float(gas_desc[x]) for x in ("gamma", "R", "mu", "Pr"))
+    check(load().dg_rk_stage_noalloc(ctypes.byref(t), ctypes.byref(g), int(stage), float(dt),
+                                     _dptr(q_in, torch.float64, "q_in"), _dptr(q_out, torch.float64, "q_out"),
+                                     _dptr(k, torch.float64, "k"), _dptr(status, torch.int32, "status"),
+                                     _stream_ptr(stream)))
