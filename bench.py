@@ -252,6 +252,25 @@ def workload_config(cfg):
 
 # ---- GPU arm -------------------------------------------------------------------------------------
 
+def mixed_rhs_bytes_per_element(Np, NF, viscous):
+    b = Np * 8 * 20 + 26 * 8 + 4 * NF       # q in; k in/out; q_out; geometry; neighbour map
+    if viscous:
+        b += Np * 4 * 9                      # fp32 viscous flux in
+    return b
+
+
+def mixed_viscous_bytes_per_element(Np, NF):
+    return Np * (8 * 5 + 4 * 9) + 26 * 8 + 4 * NF
+
+
+def mixed_tensor_flops_per_element(Np, NF, viscous):
+    """Tensor-core flops of the split products (3 products per contraction)."""
+    f = 3 * 2 * 5 * Np * (3 * Np + NF)                        # [-D | LIFT] contraction
+    if viscous:
+        f += 3 * 2 * (5 * 3 * Np * Np + 15 * Np * NF)         # BR1 volume + surface contractions
+    return f
+
+
 def gpu_arm(args, cfg, world, rank, local):
     import numpy as np
     import torch
@@ -267,66 +286,58 @@ def gpu_arm(args, cfg, world, rank, local):
     g = cfg.gas
     gas = dg.Gas(model="perfect", gamma=g.gamma, R=g.R, mu=g.mu, Pr=g.Pr)
     q0 = torch.tensor(case["q"], device=dev)
-    q = q0.clone()
-    work = (torch.empty_like(q), torch.zeros_like(q))
+    work = (torch.empty_like(q0), torch.zeros_like(q0))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    forms = {"fp64": dg._opts(precision=capi.DG_PREC_FP64), "mixed": dg._opts(precision=capi.DG_PREC_MIXED)}
 
-    def step(qbuf):
-        dg.lsrk4_step(mesh, gas, qbuf, cfg.dt, steps=1, work=work)
+    def step(qbuf, form):
+        dg.lsrk4_step(mesh, gas, qbuf, cfg.dt, steps=1, work=work, opts=forms[form])
 
-    for _ in range(args.warmup):
-        step(q)
-    torch.cuda.synchronize()
-    mesh.kernel_times(reset=True)
+    def timed_run(form, with_clocks):
+        q = q0.clone()
+        for _ in range(args.warmup):
+            step(q, form)
+        q.copy_(q0)
+        torch.cuda.synchronize()
+        mesh.kernel_times(reset=True)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local) if with_clocks else None
+        mesh.set_timing(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+            step(q, form)
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clock_info = clocks.stop() if clocks else None
+        mesh.set_timing(False)
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), world)
+        ktimes = mesh.kernel_times(reset=True)
+        if mesh.status() != 0:
+            raise SystemExit(f"device status flags set during the {form} run (non-physical state)")
+        return dict(ms=total_ms / args.steps, ktimes=ktimes, clocks=clock_info, q=q)
 
-    # device-timed region: inputs resident in HBM
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    mesh.set_timing(True)
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev0[i].record(stream)
-        step(q)
-        ev1[i].record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clock_info = clocks.stop()
-    mesh.set_timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = max_over_ranks(sum(step_ms), world)
-    ktimes = mesh.kernel_times(reset=True)
-    if mesh.status() != 0:
-        raise SystemExit("device status flags set during the benchmark (non-physical state)")
-    launches = sum(n for _, n in ktimes.values())
-
-    ms_per_step = total_ms / args.steps
+    head = args.precision
+    other = "mixed" if head == "fp64" else "fp64"
+    runs = {head: timed_run(head, True), other: timed_run(other, False)}
     dofs_step = cfg.dofs * 5
-    value = world * dofs_step / (ms_per_step * 1e-3)
-
-    # roofline of the dominant kernel
     Np, NF = cfg.Np, 4 * ((cfg.N + 1) * (cfg.N + 2) // 2)
     viscous = g.mu > 0
-    per_kernel = {}
-    for name, (ms, n) in ktimes.items():
-        if n:
-            per_kernel[name] = {"avg_ms": ms / n, "launches": n, "share": None}
-    tot = sum(v["avg_ms"] * v["launches"] for v in per_kernel.values())
-    for v in per_kernel.values():
-        v["share"] = v["avg_ms"] * v["launches"] / tot
-    dom = max(per_kernel, key=lambda k: per_kernel[k]["avg_ms"] * per_kernel[k]["launches"])
-    if dom == "rhs":
-        flops = rhs_flops_per_element(Np, NF, 5, viscous) * cfg.K
-        nbytes = rhs_bytes_per_element(Np, NF, 5, viscous) * cfg.K
-    else:
-        flops = viscous_flops_per_element(Np, NF) * cfg.K
-        nbytes = viscous_bytes_per_element(Np, NF) * cfg.K
-    avg_s = per_kernel[dom]["avg_ms"] * 1e-3
-    achieved = flops / avg_s / 1e12
+
+    def kernel_table(ktimes):
+        per = {name: {"avg_ms": ms / n, "launches": n} for name, (ms, n) in ktimes.items() if n}
+        tot = sum(v["avg_ms"] * v["launches"] for v in per.values())
+        for v in per.values():
+            v["share"] = v["avg_ms"] * v["launches"] / tot
+        return per
+
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -335,15 +346,51 @@ def gpu_arm(args, cfg, world, rank, local):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     src = kernel_source_hash()
-    traffic = TRAFFIC.get((src, dom))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
-                "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
-                "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak, "kernels": per_kernel,
-                "peak_note": "FP64 nominal 1.25 TFLOP/s (pool recipe); HBM peak of measured copy"}
 
-    # end to end through the public API: pinned host state in, stages, state back to host
+    def roofline(form, per):
+        dom = max(per, key=lambda k: per[k]["avg_ms"] * per[k]["launches"])
+        avg_s = per[dom]["avg_ms"] * 1e-3
+        if form == "fp64":
+            if dom == "rhs":
+                flops = rhs_flops_per_element(Np, NF, 5, viscous) * cfg.K
+                nbytes = rhs_bytes_per_element(Np, NF, 5, viscous) * cfg.K
+            else:
+                flops = viscous_flops_per_element(Np, NF) * cfg.K
+                nbytes = viscous_bytes_per_element(Np, NF) * cfg.K
+            ach = flops / avg_s / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((src, dom)), "kernel": dom,
+                    "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                    "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                    "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak, "kernels": per,
+                    "peak_note": "FP64 nominal 1.25 TFLOP/s (pool recipe table); HBM: measured copy"}
+        nbytes = (mixed_rhs_bytes_per_element(Np, NF, viscous) if dom == "rhs"
+                  else mixed_viscous_bytes_per_element(Np, NF)) * cfg.K
+        ach = nbytes / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": TRAFFIC.get((src, "mixed_" + dom)), "kernel": dom, "algorithmic_bytes_per_launch": nbytes,
+                "tensor_flops_per_step": mixed_tensor_flops_per_element(Np, NF, viscous) * cfg.K * 5,
+                "kernels": per, "peak_note": "HBM: measured copy (MEASURED_PEAKS.json)"}
+
+    # mixed form's error against the fp64 form after the same steps from the same state
+    qa, qb = runs["fp64"]["q"], runs["mixed"]["q"]
+    comp = [float(((qb[v] - qa[v]).abs().max() / qa[v].abs().max()).item()) for v in range(5)]
+    mom = float((qb[1:4] - qa[1:4]).abs().max().item() / qa[1:4].abs().max().item())
+    field = max(comp[0], mom, comp[4])
+
+    per_head = kernel_table(runs[head]["ktimes"])
+    per_other = kernel_table(runs[other]["ktimes"])
+    ms_per_step = runs[head]["ms"]
+    value = world * dofs_step / (ms_per_step * 1e-3)
+    other_line = {"precision": other, "value": world * dofs_step / (runs[other]["ms"] * 1e-3),
+                  "unit": "DOF-updates/s", "ms_per_step": runs[other]["ms"],
+                  "roofline": roofline(other, per_other)}
+    mixed_err = {"vs": "fp64 form on the same state (the fp64 form matches the oracle to 1e-11, tests/test_gpu_parity.py)",
+                 "steps": args.steps, "per_field_max": field, "per_component": comp,
+                 "fields": "rho, momentum (vector), rho E"}
+
+    # end to end through the public API: pinned host state in, one RK4 step, state back to host
+    q = q0.clone()
     host_in = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
     host_in.copy_(q0.cpu())
     host_out = torch.empty_like(host_in, pin_memory=True)
@@ -355,7 +402,7 @@ def gpu_arm(args, cfg, world, rank, local):
         flush.fill_(float(i))
         e0[i].record(stream)
         q.copy_(host_in, non_blocking=True)
-        step(q)
+        step(q, head)
         host_out.copy_(q, non_blocking=True)
         e1[i].record(stream)
     torch.cuda.synchronize()
@@ -371,13 +418,16 @@ def gpu_arm(args, cfg, world, rank, local):
         cpu = {"value": val, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{desc}: the full workload's mesh; numpy, single thread; {secs:.1f} s"}
 
+    launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(cfg),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clock_info, "kernel_src": src, "impl": "gpu",
+            "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f64 state; fp16x2 tensor / fp32 flux",
+            "data": "synthetic", "config": dict(workload_config(cfg), precision=head),
+            "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
+            "kernel_src": src, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -390,6 +440,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--config", default="ns_viscous")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -117,7 +117,8 @@ int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset);
 #define DG_KERNEL_VISCOUS 0     /* BR1 gradient + viscous flux pass            */
 #define DG_KERNEL_RHS 1         /* fused right-hand side (+ RK stage)          */
 #define DG_KERNEL_TEMPERATURE 2 /* Newton temperature solve inside dg_rhs/stage */
-#define DG_NUM_KERNELS 3
+#define DG_KERNEL_PRIMS 3       /* per-node pressure / temperature pass (mixed form) */
+#define DG_NUM_KERNELS 4
 
 /* With enable != 0, every later dg_rhs / dg_rk_stage on this mesh brackets each
  * of its kernel launches with CUDA events recorded on the launch stream (the
@@ -159,8 +160,14 @@ int dg_gas_status(dg_gas gas, uint32_t* bits, int reset);
 
 /* ---- options --------------------------------------------------------------- */
 #define DG_PREC_FP64 0   /* every step in float64                                   */
+/* D and LIFT contractions on tensor cores as split-fp16 products (x = hi + lo,
+ * three products, fp32 accumulation), pointwise fluxes in fp32; pressure,
+ * pressure/state differences that would cancel, and the RK update in fp64.
+ * Perfect gas only; error vs the fp64 form is reported by the tests. */
+#define DG_PREC_MIXED 1
 #define DG_TSEED_INPUT 0 /* Newton starts from T_io                                  */
 #define DG_TSEED_CONST 1 /* Newton starts from opts.t_const                           */
+#define DG_TSEED_MLP 2   /* Newton starts from the gas's trained MLP guess            */
 
 typedef struct {
   int32_t precision;  /* DG_PREC_*                                                   */
@@ -206,6 +213,51 @@ int dg_temperature(dg_gas gas, int64_t n, const double* q_dev, double* T_io_dev,
  * solve): n nodes, T_dev [n], Y_dev [nspecies][n], e_dev [n]. */
 int dg_mixture_energy(dg_gas gas, int64_t n, const double* T_dev, const double* Y_dev, double* e_dev,
                       void* stream);
+
+/* ---- learned temperature guess (no counterpart in the paper) ------------------------
+ * An 8 -> 64 -> 64 -> 1 tanh MLP maps x = ((e - e_mean)/e_scale, Y_1..Y_7) to
+ * (T - T_mean)/T_scale; its guess (clamped to [T_min, T_max]) seeds the FP64
+ * Newton solve, which stays the judge of the result (same |dT| < tol) and its
+ * fallback.  Inference uses FP16 operands with FP32 accumulation on the tensor
+ * cores; training runs the library's own FP32 forward/backward and Adam kernels.
+ * Parameters, float, flat: W1 [64][8] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64] | b3. */
+#define DG_MLP_PARAMS 4801
+
+typedef struct {
+  double e_mean, e_scale;    /* input 0 = (e - e_mean) / e_scale                    */
+  double T_mean, T_scale;    /* T = T_mean + T_scale * output                        */
+  double T_min, T_max;       /* clamp of the guess                                   */
+} dg_mlp_norm;
+
+typedef struct {
+  int32_t epochs;            /* passes over the samples                              */
+  int32_t batch;             /* samples per Adam step (full batches are used)        */
+  float lr;                  /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8)    */
+  float lr_decay;            /* step size multiplier per epoch                        */
+} dg_mlp_train_opts;
+
+/* Attach (or replace) the gas's MLP: params_host [DG_MLP_PARAMS] and its normalisation. */
+int dg_mlp_set(dg_gas gas, const float* params_host, const dg_mlp_norm* norm);
+/* Copy the gas's MLP parameters and normalisation to the host (either may be NULL). */
+int dg_mlp_get(dg_gas gas, float* params_host, dg_mlp_norm* norm);
+
+/* Batch loss and gradient: loss += mean_i (y_i - t_i)^2 and grad += its gradient
+ * with respect to params_dev, for x_dev [n][8], t_dev [n] (normalised), all float
+ * device arrays; grad_dev [DG_MLP_PARAMS] and loss_dev [1] accumulate (the caller
+ * zeroes them).  The training step's kernel, exposed for gradient checks. */
+int dg_mlp_loss_grad(int64_t n, const float* params_dev, const float* x_dev, const float* t_dev, float* grad_dev,
+                     float* loss_dev, void* stream);
+
+/* Train the gas's MLP on n samples (e_dev [n], Y_dev [nspecies][n], T_dev [n],
+ * float64 device arrays; T typically from dg_temperature), starting from
+ * init_params_host, with the normalisation taken from the samples' means and
+ * standard deviations.  Synchronous; allocates its work buffers.  The mean loss
+ * of each epoch goes to loss_history_host [epochs] (nullable). */
+int dg_mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* Y_dev, const double* T_dev,
+                 const float* init_params_host, const dg_mlp_train_opts* opts, float* loss_history_host);
+
+/* The MLP's temperature guess alone (no Newton) for the state q_dev [V][n]. */
+int dg_mlp_guess(dg_gas gas, int64_t n, const double* q_dev, double* T_dev, void* stream);
 
 /* ---- allocation-free stage (no counterpart in the paper) --------------------------
  * For callers that cannot call cudaMalloc: code whose device memory is owned by

@@ -26,15 +26,19 @@ DG_GEO_STRIDE = 26
 DG_GAS_PERFECT = 0
 DG_GAS_NASA7 = 1
 DG_PREC_FP64 = 0
+DG_PREC_MIXED = 1
 DG_TSEED_INPUT = 0
 DG_TSEED_CONST = 1
+DG_TSEED_MLP = 2
+DG_MLP_PARAMS = 4801
 DG_MESH_HOST_ONLY = 1
 DG_STATIC_SCRATCH_NODES = 1 << 19
 DG_KERNEL_VISCOUS = 0
 DG_KERNEL_RHS = 1
 DG_KERNEL_TEMPERATURE = 2
-DG_NUM_KERNELS = 3
-KERNEL_NAMES = ('viscous', 'rhs', 'temperature')
+DG_KERNEL_PRIMS = 3
+DG_NUM_KERNELS = 4
+KERNEL_NAMES = ('viscous', 'rhs', 'temperature', 'prims')
 
 c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, \
     ctypes.c_void_p
@@ -54,6 +58,15 @@ class dg_gas_desc(ctypes.Structure):
 class dg_mesh_tables(ctypes.Structure):
     _fields_ = [("K", c_int32), ("N", c_int32), ("ops_dev", c_void_p), ("fmask_dev", c_void_p),
                 ("geo_dev", c_void_p), ("vmapP_dev", c_void_p)]
+
+
+class dg_mlp_norm(ctypes.Structure):
+    _fields_ = [("e_mean", c_double), ("e_scale", c_double), ("T_mean", c_double), ("T_scale", c_double),
+                ("T_min", c_double), ("T_max", c_double)]
+
+
+class dg_mlp_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", c_int32), ("batch", c_int32), ("lr", ctypes.c_float), ("lr_decay", ctypes.c_float)]
 
 
 class dg_opts(ctypes.Structure):
@@ -81,6 +94,12 @@ SIGNATURES = {
     "dg_temperature": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.POINTER(dg_opts),
                                  c_void_p]),
     "dg_mixture_energy": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_set": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(dg_mlp_norm)]),
+    "dg_mlp_get": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(dg_mlp_norm)]),
+    "dg_mlp_loss_grad": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_train": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                               ctypes.POINTER(dg_mlp_train_opts), c_void_p]),
+    "dg_mlp_guess": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "dg_rk_stage_noalloc": (c_int32, [ctypes.POINTER(dg_mesh_tables), ctypes.POINTER(dg_gas_desc), c_int32,
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_last_error": (ctypes.c_char_p, []),

@@ -36,11 +36,13 @@ using dg::cuda_fail;
 namespace {
 
 void free_mesh_device(dg::MeshDev& d) {
+  dg::free_mixed_ops(d);
   cudaFree(d.ops);
   cudaFree(d.fmask);
   cudaFree(d.geo);
   cudaFree(d.vmapP);
   cudaFree(d.scratch);
+  cudaFree(d.geo32);
   cudaFree(d.status);
   d = dg::MeshDev();
 }
@@ -54,8 +56,9 @@ cudaError_t upload(T** dst, const T* src, size_t count) {
 
 int check_opts(const dg_opts* o) {
   if (!o) return DG_OK;
-  if (o->precision != DG_PREC_FP64) return fail(DG_ERR_UNSUPPORTED, "unsupported precision mode");
-  if (o->t_seed != DG_TSEED_INPUT && o->t_seed != DG_TSEED_CONST)
+  if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED)
+    return fail(DG_ERR_UNSUPPORTED, "unsupported precision mode");
+  if (o->t_seed != DG_TSEED_INPUT && o->t_seed != DG_TSEED_CONST && o->t_seed != DG_TSEED_MLP)
     return fail(DG_ERR_INVALID_ARG, "unknown temperature seed mode");
   if (o->t_seed == DG_TSEED_CONST && !(o->t_const > 0)) return fail(DG_ERR_INVALID_ARG, "t_const must be > 0");
   return DG_OK;
@@ -137,12 +140,27 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     return fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
+  if (opts && opts->precision == DG_PREC_MIXED) {
+    if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "the mixed-precision form needs a perfect gas");
+    e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_mixed(m, g, q, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "mixed primitives kernel");
+    if (g.mu > 0) {
+      e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_mixed(m, g, q, s); });
+      if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
+    }
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_mixed(m, g, q, out, k, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "mixed right-hand-side kernel");
+    return DG_OK;
+  }
   const double* T = nullptr;
   if (g.model == DG_GAS_NASA7) {
     if (!T_io) return fail(DG_ERR_INVALID_ARG, "a NASA-7 gas needs the temperature buffer T_io");
     const int mode = opts ? opts->t_seed : DG_TSEED_INPUT;
     const double tc = opts ? opts->t_const : 0.0;
+    if (mode == DG_TSEED_MLP && !gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "DG_TSEED_MLP needs a trained MLP");
     e = timed(mesh, DG_KERNEL_TEMPERATURE, s, [&] {
+      if (mode == DG_TSEED_MLP) return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s);
       return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, tc, gas->status, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
@@ -152,7 +170,6 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
   }
-  const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
   e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs(m, g, q, out, k, T, rk, a, b, dt, s); });
   if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
   return DG_OK;
@@ -212,9 +229,14 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   if (e == cudaSuccess) e = upload(&d.fmask, m->ops.Fmask.data(), m->ops.Fmask.size());
   if (e == cudaSuccess) e = upload(&d.geo, m->geo.data(), m->geo.size());
   if (e == cudaSuccess) e = upload(&d.vmapP, m->vmapP.data(), m->vmapP.size());
+  if (e == cudaSuccess) {
+    std::vector<float> g32(m->geo.begin(), m->geo.end());
+    e = upload(&d.geo32, g32.data(), g32.size());
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 9 * (size_t)d.K * Np);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = dg::build_mixed_ops(d, m->ops);
   if (e != cudaSuccess) {
     free_mesh_device(d);
     delete m;
@@ -340,6 +362,9 @@ int dg_gas_create(const dg_gas_desc* desc, dg_gas* out) {
 int dg_gas_free(dg_gas gas) {
   if (!gas) return DG_OK;
   cudaFree(gas->status);
+  cudaFree(gas->mlp_theta);
+  cudaFree(gas->mlp_w1h);
+  cudaFree(gas->mlp_w2h);
   delete gas;
   return DG_OK;
 }
@@ -369,7 +394,10 @@ int dg_temperature(dg_gas gas, int64_t n, const double* q, double* T_io, int32_t
   if (int rc = check_opts(opts)) return rc;
   const int mode = opts ? opts->t_seed : DG_TSEED_INPUT;
   const double tc = opts ? opts->t_const : 0.0;
-  cudaError_t e = dg::launch_temperature(gas->p, n, q, T_io, iters, mode, tc, gas->status, (cudaStream_t)stream);
+  if (mode == DG_TSEED_MLP && !gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "DG_TSEED_MLP needs a trained MLP");
+  cudaError_t e = mode == DG_TSEED_MLP
+                      ? dg::launch_temperature_mlp(gas, n, q, T_io, iters, 0, (cudaStream_t)stream)
+                      : dg::launch_temperature(gas->p, n, q, T_io, iters, mode, tc, gas->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
   return DG_OK;
 }
@@ -382,6 +410,61 @@ int dg_mixture_energy(dg_gas gas, int64_t n, const double* T, const double* Y, d
   if (!T || !Y || !e_out) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
   cudaError_t e = dg::launch_mixture_energy(gas->p, n, T, Y, e_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "mixture energy kernel");
+  return DG_OK;
+}
+
+int dg_mlp_set(dg_gas gas, const float* params, const dg_mlp_norm* norm) {
+  if (!gas || !params || !norm) return fail(DG_ERR_INVALID_ARG, "NULL gas, params or norm");
+  if (gas->p.model != DG_GAS_NASA7) return fail(DG_ERR_INVALID_ARG, "the MLP guess needs a NASA-7 gas");
+  if (!(norm->e_scale > 0) || !(norm->T_scale > 0) || !(norm->T_max >= norm->T_min))
+    return fail(DG_ERR_INVALID_ARG, "need e_scale > 0, T_scale > 0 and T_max >= T_min");
+  cudaError_t e = dg::mlp_set_params(gas, params, *norm);
+  if (e != cudaSuccess) return cuda_fail(e, "MLP upload");
+  return DG_OK;
+}
+
+int dg_mlp_get(dg_gas gas, float* params, dg_mlp_norm* norm) {
+  if (!gas) return fail(DG_ERR_INVALID_ARG, "NULL gas");
+  if (!gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "the gas has no MLP");
+  if (params) {
+    cudaError_t e = cudaMemcpy(params, gas->mlp_theta, sizeof(float) * DG_MLP_PARAMS, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "MLP download");
+  }
+  if (norm) *norm = gas->mlp_norm;
+  return DG_OK;
+}
+
+int dg_mlp_loss_grad(int64_t n, const float* params, const float* x, const float* t, float* grad, float* loss,
+                     void* stream) {
+  if (n < 0) return fail(DG_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DG_OK;
+  if (!params || !x || !t || !grad || !loss) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
+  cudaError_t e = dg::mlp_loss_grad(n, params, x, t, grad, loss, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "MLP gradient kernel");
+  return DG_OK;
+}
+
+int dg_mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* Y_dev, const double* T_dev,
+                 const float* init, const dg_mlp_train_opts* o, float* history) {
+  if (!gas || !o || !init) return fail(DG_ERR_INVALID_ARG, "NULL gas, options or initial parameters");
+  if (gas->p.model != DG_GAS_NASA7) return fail(DG_ERR_INVALID_ARG, "the MLP guess needs a NASA-7 gas");
+  if (gas->p.ns > 7) return fail(DG_ERR_UNSUPPORTED, "the MLP takes at most 7 mass fractions");
+  if (!e_dev || !Y_dev || !T_dev) return fail(DG_ERR_INVALID_ARG, "NULL sample array");
+  if (o->epochs < 1 || o->batch < 1 || !(o->lr > 0) || !(o->lr_decay > 0) || n < o->batch)
+    return fail(DG_ERR_INVALID_ARG, "need epochs >= 1, 1 <= batch <= n, lr > 0, lr_decay > 0");
+  cudaError_t e = dg::mlp_train(gas, n, e_dev, Y_dev, T_dev, *o, init, history);
+  if (e != cudaSuccess) return cuda_fail(e, "MLP training");
+  return DG_OK;
+}
+
+int dg_mlp_guess(dg_gas gas, int64_t n, const double* q, double* T, void* stream) {
+  if (!gas) return fail(DG_ERR_INVALID_ARG, "NULL gas");
+  if (!gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "the gas has no MLP");
+  if (n < 0) return fail(DG_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DG_OK;
+  if (!q || !T) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
+  cudaError_t e = dg::launch_temperature_mlp(gas, n, q, T, nullptr, 1, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "MLP guess kernel");
   return DG_OK;
 }
 

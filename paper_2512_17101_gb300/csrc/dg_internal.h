@@ -44,13 +44,28 @@ struct GasParams {  // passed to kernels by value
   int newton_max_it;
 };
 
+// Split-FP16 operator tables of the mixed-precision path (built at upload).
+// Each is a row-major [rows][words] array of 32-bit words, a word holding two
+// consecutive k entries (k, k+1) as fp16; "hi" = fp16(x), "lo" = fp16(x - hi).
+struct MixedOps {
+  uint32_t* rhs_hi = nullptr;  // [NPAD][KR/2]: row i = [-Dr_i | -Ds_i | -Dt_i | LIFT_i]
+  uint32_t* rhs_lo = nullptr;
+  uint32_t* d_hi = nullptr;    // [3Np pad 8][KW/2]: row (a, i) = D_a[i][:]
+  uint32_t* d_lo = nullptr;
+  uint32_t* l_hi = nullptr;    // [NPAD][KJ/2]: row i = LIFT[i][:]
+  uint32_t* l_lo = nullptr;
+};
+
 struct MeshDev {
   int K = 0, N = 0, Np = 0, Nfp = 0;
+  MixedOps mx;
   double* ops = nullptr;       // Dr | Ds | Dt | LIFT, row-major
   int32_t* fmask = nullptr;    // [4][Nfp]
   double* geo = nullptr;       // [K][DG_GEO_STRIDE]
   int32_t* vmapP = nullptr;    // [K][4 Nfp]
-  double* scratch = nullptr;   // [9][K][Np] viscous flux (BR1 pass 1 output)
+  double* scratch = nullptr;   // 72 B per node: FP64 form [9][K][Np] viscous flux (BR1 pass 1 output);
+                               // mixed form float Fv [9] | float q [5] | double p | double T, each [K][Np]
+  float* geo32 = nullptr;      // [K][DG_GEO_STRIDE] float copy of geo (mixed form)
   unsigned* status = nullptr;  // device status word
 };
 
@@ -64,6 +79,14 @@ extern const double kRK4B[5];
 // the node temperatures of a mixture.
 cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                        const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
+// Mixed-precision path (k_mixed.cu): split operator tables, and the tensor-core
+// right-hand side / RK stage with its BR1 pass.
+cudaError_t build_mixed_ops(MeshDev& m, const RefOps& ops);
+void free_mixed_ops(MeshDev& m);
+cudaError_t launch_rhs_mixed(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                             double a, double b, double dt, cudaStream_t s);
+cudaError_t launch_viscous_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture temperature (Newton).  seed_mode: DG_TSEED_*; nvar = 5 + ns; q is [nvar][n].
@@ -80,8 +103,8 @@ struct KernelTimer {
   bool enabled = false;
   std::vector<cudaEvent_t> pool;                                // idle events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[DG_NUM_KERNELS];
-  double ms[DG_NUM_KERNELS] = {0, 0, 0};
-  int64_t count[DG_NUM_KERNELS] = {0, 0, 0};
+  double ms[DG_NUM_KERNELS] = {};
+  int64_t count[DG_NUM_KERNELS] = {};
 };
 }  // namespace dg
 
@@ -98,4 +121,21 @@ struct dg_gas_s {
   dg::GasParams p;
   unsigned* status = nullptr;
   int device = 0;
+  // learned temperature guess
+  bool has_mlp = false;
+  float* mlp_theta = nullptr;  // [DG_MLP_PARAMS] fp32
+  void* mlp_w1h = nullptr;     // fp16 [64][16]
+  void* mlp_w2h = nullptr;     // fp16 [64][64]
+  dg_mlp_norm mlp_norm{};
 };
+
+namespace dg {
+// k_mlp.cu
+cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, double* T, int32_t* iters, int guess_only,
+                                   cudaStream_t s);
+cudaError_t mlp_set_params(dg_gas gas, const float* theta_host, const dg_mlp_norm& nrm);
+cudaError_t mlp_loss_grad(int64_t n, const float* theta, const float* X, const float* t, float* grad, float* loss,
+                          cudaStream_t s);
+cudaError_t mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* Y_dev, const double* T_dev,
+                      const dg_mlp_train_opts& o, const float* init_host, float* history);
+}  // namespace dg

@@ -221,7 +221,7 @@ def dg_mixture_energy(gas: Gas, T, Y, e, stream=None):
                                    _dptr(e, torch.float64, "e"), _stream_ptr(stream)))
 
 
-def lsrk4_step(mesh, gas, q, dt, steps=1, T_io=None, opts=None, stream=None, work=None):
+def lsrk4_step(mesh, gas, q, dt, steps=1, T_io=None, opts=None, stream=None, work=None):  # noqa: D401
     """Advance q in place by ``steps`` LSRK4 steps (5 stages each) with ping-pong buffers."""
     import torch
     if work is None:
@@ -257,3 +257,42 @@ def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, str
                                      _dptr(q_in, torch.float64, "q_in"), _dptr(q_out, torch.float64, "q_out"),
                                      _dptr(k, torch.float64, "k"), _dptr(status, torch.int32, "status"),
                                      _stream_ptr(stream)))
+
+
+# ---- learned temperature guess -------------------------------------------------------------
+
+def dg_mlp_set(gas: Gas, params, norm: dict):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    n = capi.dg_mlp_norm(**{k: float(v) for k, v in norm.items()})
+    check(load().dg_mlp_set(gas.handle, _hptr(params), ctypes.byref(n)))
+
+
+def dg_mlp_get(gas: Gas):
+    params = np.zeros(capi.DG_MLP_PARAMS, dtype=np.float32)
+    n = capi.dg_mlp_norm()
+    check(load().dg_mlp_get(gas.handle, _hptr(params), ctypes.byref(n)))
+    return params, {k: getattr(n, k) for k, _ in capi.dg_mlp_norm._fields_}
+
+
+def dg_mlp_loss_grad(params, x, t, grad, loss, stream=None):
+    import torch
+    check(load().dg_mlp_loss_grad(t.numel(), _dptr(params, torch.float32, "params"), _dptr(x, torch.float32, "x"),
+                                  _dptr(t, torch.float32, "t"), _dptr(grad, torch.float32, "grad"),
+                                  _dptr(loss, torch.float32, "loss"), _stream_ptr(stream)))
+
+
+def dg_mlp_train(gas: Gas, e, Y, T, init_params, epochs=20, batch=4096, lr=3e-3, lr_decay=0.9):
+    """Train the gas's MLP on device samples (float64 tensors); returns the per-epoch loss history."""
+    import torch
+    o = capi.dg_mlp_train_opts(epochs=int(epochs), batch=int(batch), lr=float(lr), lr_decay=float(lr_decay))
+    init = np.ascontiguousarray(init_params, dtype=np.float32)
+    hist = np.zeros(int(epochs), dtype=np.float32)
+    check(load().dg_mlp_train(gas.handle, e.numel(), _dptr(e, torch.float64, "e"), _dptr(Y, torch.float64, "Y"),
+                              _dptr(T, torch.float64, "T"), _hptr(init), ctypes.byref(o), _hptr(hist)))
+    return hist
+
+
+def dg_mlp_guess(gas: Gas, q, T, stream=None):
+    import torch
+    check(load().dg_mlp_guess(gas.handle, T.numel(), _dptr(q, torch.float64, "q"), _dptr(T, torch.float64, "T"),
+                              _stream_ptr(stream)))

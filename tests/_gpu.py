@@ -25,3 +25,17 @@ def rel_err(got, want):
         scale = np.abs(want[v]).max()
         errs.append(np.abs(got[v] - want[v]).max() / (scale if scale > 0 else 1.0))
     return max(errs)
+
+
+def field_err(got, want):
+    """Max over conserved fields of max|got - want| / max|want|, with the momentum components
+    taken together as one vector field (rho, rho u, rho E, species); the error measure of the
+    mixed-precision form."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    groups = [[0], [1, 2, 3], [4]] + [[v] for v in range(5, want.shape[0])]
+    errs = []
+    for g in groups:
+        scale = max(np.abs(want[v]).max() for v in g)
+        errs.append(max(np.abs(got[v] - want[v]).max() for v in g) / (scale if scale > 0 else 1.0))
+    return max(errs)
