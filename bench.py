@@ -418,6 +418,12 @@ def gpu_arm(args, cfg, world, rank, local):
         cpu = {"value": val, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{desc}: the full workload's mesh; numpy, single thread; {secs:.1f} s"}
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_form(args, local)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_form(args, local)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -427,9 +433,155 @@ def gpu_arm(args, cfg, world, rank, local):
             "data": "synthetic", "config": dict(workload_config(cfg), precision=head),
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
+            "learned_form": learned, "batched_form": batched,
             "kernel_src": src, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
+
+
+def learned_form(args, local):
+    """The learned form's workload (7-species Euler mixture, 32^3 x 6 tets, N = 2): RK4 steps with the
+    Newton temperature solve seeded by a constant, by the previous stage's T, and by the trained MLP."""
+    import numpy as np
+    import torch
+    from paper_2512_17101_gb300 import capi, dg
+    from workloads.configs import build_case, get_config
+    from workloads.mlp import glorot_params, temperature_samples
+
+    cfg = get_config("mixture_learned")
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    mix = case["mixture"]
+    gas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs, newton_tol=1e-10, newton_max_it=50)
+    K, Np = case["vertices"].shape[0], case["ref_nodes"].shape[0]
+    n = K * Np
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    # conserved state from (Y, T, u, p0): density from the mixture gas constant, energy from the library's EOS
+    Y = np.ascontiguousarray(case["Y"].reshape(7, n))
+    T = np.ascontiguousarray(case["T"].reshape(n))
+    vel = np.ascontiguousarray(case["vel"].reshape(3, n))
+    Rmix = (Y * (mix.R_universal / mix.W)[:, None]).sum(axis=0)
+    rho = case["p0"] / (Rmix * T)
+    Yd, Td = torch.tensor(Y, device=dev), torch.tensor(T, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev)
+    dg.dg_mixture_energy(gas, Td, Yd, e)
+    rho_d, vel_d = torch.tensor(rho, device=dev), torch.tensor(vel, device=dev)
+    q0 = torch.empty((12, n), dtype=torch.float64, device=dev)
+    q0[0] = rho_d
+    q0[1:4] = rho_d * vel_d
+    q0[4] = rho_d * (e + 0.5 * (vel_d * vel_d).sum(dim=0))
+    q0[5:] = rho_d * Yd
+    q0 = q0.reshape(12, K, Np).contiguous()
+
+    # training data: uniform T, Dirichlet Y -> e (library EOS) -> Newton labels from a constant seed
+    t0 = time.perf_counter()
+    Ts, Ys = temperature_samples(1_000_000, 7, seed=7)
+    Tsd, Ysd = torch.tensor(Ts, device=dev), torch.tensor(Ys, device=dev)
+    es = torch.empty_like(Tsd)
+    dg.dg_mixture_energy(gas, Tsd, Ysd, es)
+    qs = torch.zeros((12, Ts.size), dtype=torch.float64, device=dev)
+    qs[0], qs[4], qs[5:] = 1.0, es, Ysd
+    Tl = torch.full_like(Tsd, 1650.0)
+    dg.dg_temperature(gas, qs, Tl)
+    torch.cuda.synchronize()
+    hist = dg.dg_mlp_train(gas, es, Ysd, Tl, glorot_params(0), epochs=30, batch=1024, lr=3e-3, lr_decay=0.9)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    seeds = {"constant_1650K": dg._opts(t_seed=capi.DG_TSEED_CONST, t_const=1650.0),
+             "previous_stage_T": dg._opts(t_seed=capi.DG_TSEED_INPUT),
+             "mlp": dg._opts(t_seed=capi.DG_TSEED_MLP)}
+    out = {}
+    steps = max(2, min(args.steps, 5))
+    for name, opts in seeds.items():
+        q = q0.clone()
+        Tio = torch.full((K, Np), 1650.0, dtype=torch.float64, device=dev)
+        work = (torch.empty_like(q), torch.zeros_like(q))
+        for _ in range(2):
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, T_io=Tio, opts=opts, work=work)
+        q.copy_(q0)
+        torch.cuda.synchronize()
+        mesh.kernel_times(reset=True)
+        mesh.set_timing(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=steps, T_io=Tio, opts=opts, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        mesh.set_timing(False)
+        kt = mesh.kernel_times(reset=True)
+        ms = a.elapsed_time(b) / steps
+        # Newton iterations of one solve on the final state from this seed
+        it = torch.zeros(n, dtype=torch.int32, device=dev)
+        Tt = Tio.reshape(n).clone() if name == "previous_stage_T" else torch.empty(n, dtype=torch.float64, device=dev)
+        dg.dg_temperature(gas, q.reshape(12, n), Tt, it, opts=opts)
+        out[name] = {"ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
+                     "temperature_ms_per_stage": kt["temperature"][0] / max(kt["temperature"][1], 1),
+                     "rhs_ms_per_stage": kt["rhs"][0] / max(kt["rhs"][1], 1),
+                     "newton_iterations_mean": float(it.double().mean().item()), "q": q}
+        if gas.status() != 0 or mesh.status() != 0:
+            raise SystemExit(f"status flags set in the learned-form run ({name})")
+    ref_q = out["constant_1650K"].pop("q")
+    for name in out:
+        if "q" in out[name]:
+            qq = out[name].pop("q")
+            out[name]["state_diff_vs_constant_seed"] = float(((qq - ref_q).abs().max() / ref_q.abs().max()).item())
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": K, "N": cfg.N, "V": 12, "steps": steps,
+            "training": {"samples": int(Ts.size), "epochs": 30, "seconds_incl_sampling": train_s,
+                         "loss_first_last": [float(hist[0]), float(hist[-1])]},
+            "seeds": out}
+
+
+def batched_form(args, local):
+    """The batched workload (64 uneven cases, orders 1..4, half Euler / half NS, mixed precision):
+    one graph launch per RK4 step, against stepping the same cases one by one."""
+    import torch
+    from paper_2512_17101_gb300 import capi, dg
+    from workloads.configs import batched_cases
+
+    dev = torch.device("cuda", local)
+    cases = batched_cases(64, seed=0)
+    hs = []
+    for c in cases:
+        mesh = dg.Mesh(c["vertices"], c["period"], c["N"], c["ref_nodes"])
+        g = c["gas"]
+        gas = dg.Gas(model="perfect", gamma=g.gamma, R=g.R, mu=g.mu, Pr=g.Pr)
+        hs.append((mesh, gas, c["dt"], torch.tensor(c["q"], device=dev)))
+    t0 = time.perf_counter()
+    batch = dg.Batch(hs, autotune=True)
+    setup_s = time.perf_counter() - t0
+    dofs = sum(c["K"] * c["Np"] for c in cases)
+    steps = max(2, min(args.steps, 10))
+    batch.step(2)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    batch.step(steps)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    if batch.status() != 0:
+        raise SystemExit("status flags set in the batched run")
+    # the same cases stepped one by one (one call per case and stage)
+    opts = dg._opts(precision=capi.DG_PREC_MIXED)
+    works = [(torch.empty_like(q), torch.zeros_like(q)) for (_, _, _, q) in hs]
+    for (mesh, gas, dt, q), w in zip(hs, works):
+        dg.lsrk4_step(mesh, gas, q, dt, steps=1, opts=opts, work=w)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        for (mesh, gas, dt, q), w in zip(hs, works):
+            dg.lsrk4_step(mesh, gas, q, dt, steps=1, opts=opts, work=w)
+    b.record()
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(b) / steps
+    rt, vt, tune = batch.tiles()
+    return {"workload": "64 cases, periodic n^3 x 6 tets with n ~ U{2..20}, N ~ U{1..4}, half Euler vortex / half "
+                        "NS Taylor-Green, seed 0; mixed precision",
+            "dofs_per_stage": dofs, "steps": steps, "ms_per_step": ms, "value": dofs * 5 / (ms * 1e-3),
+            "unit": "DOF-updates/s", "graph_launches_per_step": 1, "setup_s_incl_autotune": setup_s,
+            "one_by_one_ms_per_step": ms_seq, "one_by_one_value": dofs * 5 / (ms_seq * 1e-3),
+            "tiles_rhs_by_order_euler_ns": rt.tolist(), "tiles_br1_by_order": vt.tolist()}
 
 
 def main():
@@ -440,6 +592,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--config", default="ns_viscous")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()

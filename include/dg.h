@@ -296,6 +296,45 @@ int dg_rk_stage_noalloc(const dg_mesh_tables* tables, const dg_gas_desc* gas, in
                         const double* q_in_dev, double* q_out_dev, double* k_dev, uint32_t* status_dev,
                         void* stream);
 
+/* ---- batched form: many uneven cases, one graph launch per RK4 step --------------------
+ * Cases of orders 1..4, Euler or Navier-Stokes (perfect gas), any sizes, advanced
+ * together in the mixed-precision form (DG_PREC_MIXED).  Cases are grouped by
+ * (order, physics); each group's kernels are persistent over a device work list of
+ * (case, element tile) items, so a stage costs one launch per group and pass, and
+ * a whole RK4 step (5 stages, then each case's result copied back into its state)
+ * is captured once into a CUDA graph.  With DG_BATCH_AUTOTUNE the tile size of
+ * each group (elements per block) is chosen at creation by timing the compiled
+ * candidates on the batch's own cases.  The paper's nearest counterpart is its
+ * concatenation of outlined calls into fewer kernels (Sec. 4.2.4) and the
+ * launch-overhead floor of small cases (Sec. 5.2). */
+typedef struct dg_batch_s* dg_batch;
+
+typedef struct {
+  dg_mesh mesh;    /* uploaded mesh (its tables and scratch are used by the batch)     */
+  dg_gas gas;      /* perfect gas, inviscid or viscous                                  */
+  double dt;       /* the case's time step                                              */
+  double* q_dev;   /* [5][K][Np] state, advanced in place by dg_batch_step               */
+} dg_batch_case;
+
+#define DG_BATCH_AUTOTUNE 1
+
+/* Creates the batch: allocates a work state and an RK register per case, builds the
+ * work lists, tunes the tiles (flag), and captures the step graph.  Meshes of one
+ * order must share their reference operators; each mesh belongs to one case, and
+ * the meshes, gases and states must outlive the batch.  Synchronous. */
+int dg_batch_create(const dg_batch_case* cases, int32_t ncases, int32_t flags, dg_batch* out);
+
+/* Advances every case by `steps` RK4 steps: `steps` graph launches on `stream`. */
+int dg_batch_step(dg_batch batch, int32_t steps, void* stream);
+
+/* Chosen tiles: rhs_tiles_host [4][2] (order, physics 0 = Euler / 1 = NS; 0 where the
+ * batch has no such group), viscous_tiles_host [4]; rhs_tune_ms_host [4][2][4] the
+ * timings of the candidates (any pointer may be NULL). */
+int dg_batch_tiles(dg_batch batch, int32_t* rhs_tiles_host, int32_t* viscous_tiles_host, double* rhs_tune_ms_host);
+
+int dg_batch_status(dg_batch batch, uint32_t* bits, int reset);
+int dg_batch_free(dg_batch batch);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dg_last_error(void);
 

@@ -32,6 +32,7 @@ DG_TSEED_CONST = 1
 DG_TSEED_MLP = 2
 DG_MLP_PARAMS = 4801
 DG_MESH_HOST_ONLY = 1
+DG_BATCH_AUTOTUNE = 1
 DG_STATIC_SCRATCH_NODES = 1 << 19
 DG_KERNEL_VISCOUS = 0
 DG_KERNEL_RHS = 1
@@ -69,6 +70,10 @@ class dg_mlp_train_opts(ctypes.Structure):
     _fields_ = [("epochs", c_int32), ("batch", c_int32), ("lr", ctypes.c_float), ("lr_decay", ctypes.c_float)]
 
 
+class dg_batch_case(ctypes.Structure):
+    _fields_ = [("mesh", c_void_p), ("gas", c_void_p), ("dt", c_double), ("q_dev", c_void_p)]
+
+
 class dg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("reserved", c_int32 * 8)]
 
@@ -100,6 +105,11 @@ SIGNATURES = {
     "dg_mlp_train": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                ctypes.POINTER(dg_mlp_train_opts), c_void_p]),
     "dg_mlp_guess": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "dg_batch_create": (c_int32, [ctypes.POINTER(dg_batch_case), c_int32, c_int32, ctypes.POINTER(c_void_p)]),
+    "dg_batch_step": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "dg_batch_tiles": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_batch_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
+    "dg_batch_free": (c_int32, [c_void_p]),
     "dg_rk_stage_noalloc": (c_int32, [ctypes.POINTER(dg_mesh_tables), ctypes.POINTER(dg_gas_desc), c_int32,
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_last_error": (ctypes.c_char_p, []),

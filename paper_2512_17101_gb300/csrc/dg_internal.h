@@ -44,16 +44,13 @@ struct GasParams {  // passed to kernels by value
   int newton_max_it;
 };
 
-// Split-FP16 operator tables of the mixed-precision path (built at upload).
-// Each is a row-major [rows][words] array of 32-bit words, a word holding two
-// consecutive k entries (k, k+1) as fp16; "hi" = fp16(x), "lo" = fp16(x - hi).
+// Split-BF16 operator tables of the mixed-precision path (built at upload).  Each
+// is [3][rows][words] (terms hi, mid, lo; x = hi + mid + lo, each bf16), a 32-bit
+// word holding two consecutive k.
 struct MixedOps {
-  uint32_t* rhs_hi = nullptr;  // [NPAD][KR/2]: row i = [-Dr_i | -Ds_i | -Dt_i | LIFT_i]
-  uint32_t* rhs_lo = nullptr;
-  uint32_t* d_hi = nullptr;    // [3Np pad 8][KW/2]: row (a, i) = D_a[i][:]
-  uint32_t* d_lo = nullptr;
-  uint32_t* l_hi = nullptr;    // [NPAD][KJ/2]: row i = LIFT[i][:]
-  uint32_t* l_lo = nullptr;
+  uint32_t* rhs = nullptr;  // rows i < NPAD: [-Dr_i | -Ds_i | -Dt_i | LIFT_i], KR columns
+  uint32_t* d = nullptr;    // rows (a, i) < 3Np pad 8: D_a[i][:], KW columns
+  uint32_t* l = nullptr;    // rows (face, i), 4 x NPAD: LIFT[i][face block], KF columns
 };
 
 struct MeshDev {

@@ -7,29 +7,35 @@
 namespace dg {
 namespace {
 
-// words[r][c] = (fp16(x) | fp16(y) << 16) for (x, y) = M[r][2c], M[r][2c+1]; lo = residuals.
-__global__ void split_table_kernel(const double* __restrict__ M, int rows, int cols, uint32_t* __restrict__ hi,
-                                   uint32_t* __restrict__ lo) {
+// table[term][r][c] = (t(x) | t(y) << 16) for (x, y) = M[r][2c], M[r][2c+1], t the bf16
+// term: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid) (residuals in FP64).
+__global__ void split_table_kernel(const double* __restrict__ M, int rows, int cols, uint32_t* __restrict__ out) {
   const int half = cols / 2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * half; i += gridDim.x * blockDim.x) {
     const int r = i / half, c = i - r * half;
-    const double x = M[r * cols + 2 * c], y = M[r * cols + 2 * c + 1];
-    const __half hx = __double2half(x), hy = __double2half(y);
-    const __half lx = __double2half(x - (double)__half2float(hx)), ly = __double2half(y - (double)__half2float(hy));
-    hi[i] = (uint32_t)__half_as_ushort(hx) | ((uint32_t)__half_as_ushort(hy) << 16);
-    lo[i] = (uint32_t)__half_as_ushort(lx) | ((uint32_t)__half_as_ushort(ly) << 16);
+    double x[2] = {M[r * cols + 2 * c], M[r * cols + 2 * c + 1]};
+    unsigned short t[3][2];
+    for (int j = 0; j < 2; ++j) {
+      double rem = x[j];
+      for (int term = 0; term < 3; ++term) {
+        const __nv_bfloat16 h = __double2bfloat16(rem);
+        t[term][j] = __bfloat16_as_ushort(h);
+        rem -= (double)__bfloat162float(h);
+      }
+    }
+    for (int term = 0; term < 3; ++term)
+      out[(size_t)term * rows * half + i] = (uint32_t)t[term][0] | ((uint32_t)t[term][1] << 16);
   }
 }
 
-cudaError_t split_table(const std::vector<double>& host, int rows, int cols, uint32_t** hi, uint32_t** lo) {
+cudaError_t split_table(const std::vector<double>& host, int rows, int cols, uint32_t** out) {
   double* dM = nullptr;
   const size_t words = (size_t)rows * cols / 2;
   cudaError_t e = cudaMalloc((void**)&dM, sizeof(double) * host.size());
   if (e == cudaSuccess) e = cudaMemcpy(dM, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)hi, sizeof(uint32_t) * words);
-  if (e == cudaSuccess) e = cudaMalloc((void**)lo, sizeof(uint32_t) * words);
+  if (e == cudaSuccess) e = cudaMalloc((void**)out, sizeof(uint32_t) * 3 * words);
   if (e == cudaSuccess) {
-    split_table_kernel<<<64, 256>>>(dM, rows, cols, *hi, *lo);
+    split_table_kernel<<<64, 256>>>(dM, rows, cols, *out);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -40,7 +46,7 @@ cudaError_t split_table(const std::vector<double>& host, int rows, int cols, uin
 template <int N>
 cudaError_t build_t(MeshDev& m, const RefOps& o) {
   using M = mixk::MOrd<N>;
-  const int Np = M::Np, NF = M::NF;
+  const int Np = M::Np, NF = M::NF, Nfp = M::Nfp;
   const std::vector<double>* D[3] = {&o.Dr, &o.Ds, &o.Dt};
   std::vector<double> R((size_t)M::NPAD * M::KR, 0.0);
   for (int i = 0; i < Np; ++i) {
@@ -52,20 +58,20 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
   for (int a = 0; a < 3; ++a)
     for (int i = 0; i < Np; ++i)
       for (int j = 0; j < Np; ++j) Dm[(size_t)(a * Np + i) * M::KW + j] = (*D[a])[i * Np + j];
-  std::vector<double> L((size_t)M::NPAD * M::KJ, 0.0);
-  for (int i = 0; i < Np; ++i)
-    for (int k = 0; k < NF; ++k) L[(size_t)i * M::KJ + k] = o.LIFT[i * NF + k];
-  cudaError_t e = split_table(R, M::NPAD, M::KR, &m.mx.rhs_hi, &m.mx.rhs_lo);
-  if (e == cudaSuccess) e = split_table(Dm, M::ND, M::KW, &m.mx.d_hi, &m.mx.d_lo);
-  if (e == cudaSuccess) e = split_table(L, M::NPAD, M::KJ, &m.mx.l_hi, &m.mx.l_lo);
+  std::vector<double> L((size_t)4 * M::NPAD * M::KF, 0.0);
+  for (int f = 0; f < 4; ++f)
+    for (int i = 0; i < Np; ++i)
+      for (int jj = 0; jj < Nfp; ++jj) L[((size_t)f * M::NPAD + i) * M::KF + jj] = o.LIFT[i * NF + f * Nfp + jj];
+  cudaError_t e = split_table(R, M::NPAD, M::KR, &m.mx.rhs);
+  if (e == cudaSuccess) e = split_table(Dm, M::ND, M::KW, &m.mx.d);
+  if (e == cudaSuccess) e = split_table(L, 4 * M::NPAD, M::KF, &m.mx.l);
   return e;
 }
 
 template <int N, int PHYS, bool RK>
-cudaError_t launch_rhs_mixed_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
-                               double a, double b, double dt, cudaStream_t s) {
-  using M = mixk::MOrd<N>;
-  constexpr size_t smem = mixk::rhs_mixed_smem<N, PHYS>();
+cudaError_t launch_rhs_mixed_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
+  using T = mixk::RT<N, mixk::MOrd<N>::EPB>;
+  const size_t smem = T::smem(PHYS == kern::NAVIER_STOKES);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mixk::rhs_mixed_kernel<N, PHYS, RK>,
@@ -73,22 +79,18 @@ cudaError_t launch_rhs_mixed_t(const MeshDev& m, const GasParams& g, const doubl
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int blocks = (m.K + M::EPB - 1) / M::EPB;
-  const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * M::Np);
-  mixk::rhs_mixed_kernel<N, PHYS, RK><<<blocks, M::NT, smem, s>>>(q, out, k, m.mx.rhs_hi, m.mx.rhs_lo, m.fmask,
-                                                                    m.geo32, m.vmapP, sc.qf, sc.p, sc.fv, g, m.K,
-                                                                    a, b, (float)dt);
+  const int blocks = (m.K + T::EPB - 1) / T::EPB;
+  mixk::rhs_mixed_kernel<N, PHYS, RK><<<blocks, T::NT, smem, s>>>(c, m.mx.rhs, m.fmask, a, b);
   return cudaGetLastError();
 }
 
 template <int PHYS>
-cudaError_t dispatch_mixed(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
-                           double a, double b, double dt, cudaStream_t s) {
+cudaError_t dispatch_mixed(const MeshDev& m, const mixk::MixedCase& c, bool rk, double a, double b,
+                           cudaStream_t s) {
   switch (m.N) {
-#define DG_CASE(NN)                                                                     \
-  case NN:                                                                              \
-    return rk ? launch_rhs_mixed_t<NN, PHYS, true>(m, g, q, out, k, a, b, dt, s)        \
-              : launch_rhs_mixed_t<NN, PHYS, false>(m, g, q, out, k, a, b, dt, s);
+#define DG_CASE(NN)                                                                           \
+  case NN:                                                                                    \
+    return rk ? launch_rhs_mixed_t<NN, PHYS, true>(m, c, a, b, s) : launch_rhs_mixed_t<NN, PHYS, false>(m, c, a, b, s);
     DG_CASE(1)
     DG_CASE(2)
     DG_CASE(3)
@@ -100,9 +102,9 @@ cudaError_t dispatch_mixed(const MeshDev& m, const GasParams& g, const double* q
 }
 
 template <int N>
-cudaError_t launch_viscous_mixed_t(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
-  using M = mixk::MOrd<N>;
-  constexpr size_t smem = mixk::viscous_mixed_smem<N>();
+cudaError_t launch_viscous_mixed_t(const MeshDev& m, const mixk::MixedCase& c, cudaStream_t s) {
+  using T = mixk::VT<N, mixk::MOrd<N>::EPBV>;
+  const size_t smem = T::smem();
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
@@ -110,11 +112,8 @@ cudaError_t launch_viscous_mixed_t(const MeshDev& m, const GasParams& g, const d
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int blocks = (m.K + M::EPBV - 1) / M::EPBV;
-  const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * M::Np);
-  mixk::viscous_mixed_kernel<N><<<blocks, M::NTV, smem, s>>>(q, sc.qf, sc.T, sc.fv, m.mx.d_hi, m.mx.d_lo,
-                                                             m.mx.l_hi, m.mx.l_lo, m.fmask, m.geo32, m.vmapP, g,
-                                                             m.K);
+  const int blocks = (m.K + T::EPB - 1) / T::EPB;
+  mixk::viscous_mixed_kernel<N><<<blocks, T::NT, smem, s>>>(c, m.mx.d, m.mx.l, m.fmask);
   return cudaGetLastError();
 }
 
@@ -131,42 +130,58 @@ cudaError_t build_mixed_ops(MeshDev& m, const RefOps& ops) {
 }
 
 void free_mixed_ops(MeshDev& m) {
-  cudaFree(m.mx.rhs_hi);
-  cudaFree(m.mx.rhs_lo);
-  cudaFree(m.mx.d_hi);
-  cudaFree(m.mx.d_lo);
-  cudaFree(m.mx.l_hi);
-  cudaFree(m.mx.l_lo);
+  cudaFree(m.mx.rhs);
+  cudaFree(m.mx.d);
+  cudaFree(m.mx.l);
   m.mx = MixedOps();
+}
+
+mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const double* qin, double* out, double* k,
+                                double dt) {
+  const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * m.Np);
+  mixk::MixedCase c;
+  c.q[0] = const_cast<double*>(qin);
+  c.q[1] = out;
+  c.k = k;
+  c.qf = sc.qf;
+  c.p = sc.p;
+  c.T = sc.T;
+  c.fv = sc.fv;
+  c.geo = m.geo32;
+  c.vmapP = m.vmapP;
+  c.K = m.K;
+  c.Np = m.Np;
+  c.dt = dt;
+  c.gas = mixk::MixedGas{g.gamma, g.R, g.mu, g.kappa};
+  return c;
 }
 
 cudaError_t launch_rhs_mixed(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                              double a, double b, double dt, cudaStream_t s) {
-  if (g.mu > 0) return dispatch_mixed<kern::NAVIER_STOKES>(m, g, q, out, k, rk, a, b, dt, s);
-  return dispatch_mixed<kern::EULER>(m, g, q, out, k, rk, a, b, dt, s);
+  const mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
+  if (g.mu > 0) return dispatch_mixed<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
+  return dispatch_mixed<kern::EULER>(m, c, rk, a, b, s);
 }
 
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
   const size_t KNp = (size_t)m.K * m.Np;
-  const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, KNp);
+  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t want = (KNp + 255) / 256;
   const int blocks = (int)(want < (size_t)sms * 16 ? want : (size_t)sms * 16);
-  if (g.mu > 0)
-    mixk::prims_kernel<true><<<blocks, 256, 0, s>>>(q, sc.qf, sc.p, sc.T, m.status, g, KNp);
-  else
-    mixk::prims_kernel<false><<<blocks, 256, 0, s>>>(q, sc.qf, sc.p, sc.T, m.status, g, KNp);
+  mixk::prims_kernel<<<blocks, 256, 0, s>>>(c, q, KNp, m.status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_viscous_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
+  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
   switch (m.N) {
-    case 1: return launch_viscous_mixed_t<1>(m, g, q, s);
-    case 2: return launch_viscous_mixed_t<2>(m, g, q, s);
-    case 3: return launch_viscous_mixed_t<3>(m, g, q, s);
-    case 4: return launch_viscous_mixed_t<4>(m, g, q, s);
+    case 1: return launch_viscous_mixed_t<1>(m, c, s);
+    case 2: return launch_viscous_mixed_t<2>(m, c, s);
+    case 3: return launch_viscous_mixed_t<3>(m, c, s);
+    case 4: return launch_viscous_mixed_t<4>(m, c, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -296,3 +296,53 @@ def dg_mlp_guess(gas: Gas, q, T, stream=None):
     import torch
     check(load().dg_mlp_guess(gas.handle, T.numel(), _dptr(q, torch.float64, "q"), _dptr(T, torch.float64, "T"),
                               _stream_ptr(stream)))
+
+
+# ---- batched form ----------------------------------------------------------------------------
+
+class Batch:
+    """Cases (mesh, gas, dt, CUDA state tensor) advanced together, one graph launch per RK4 step."""
+
+    def __init__(self, cases, autotune=True):
+        lib = load()
+        arr = (capi.dg_batch_case * len(cases))()
+        self._keep = []
+        for i, (mesh, gas, dt, q) in enumerate(cases):
+            arr[i].mesh = mesh.handle
+            arr[i].gas = gas.handle
+            arr[i].dt = float(dt)
+            arr[i].q_dev = _dptr(q, None, "q")
+            self._keep.append((mesh, gas, q))
+        h = ctypes.c_void_p()
+        check(lib.dg_batch_create(arr, len(cases), capi.DG_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, steps=1, stream=None):
+        check(load().dg_batch_step(self.handle, int(steps), _stream_ptr(stream)))
+
+    def tiles(self):
+        r = np.zeros((4, 2), dtype=np.int32)
+        v = np.zeros(4, dtype=np.int32)
+        t = np.zeros((4, 2, 4))
+        check(load().dg_batch_tiles(self.handle, _hptr(r), _hptr(v), _hptr(t)))
+        return r, v, t
+
+    def status(self, reset=True):
+        bits = ctypes.c_uint32()
+        check(load().dg_batch_status(self.handle, ctypes.byref(bits), int(reset)))
+        return bits.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().dg_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dg_batch_create(cases, autotune=True) -> Batch:
+    return Batch(cases, autotune)

@@ -65,6 +65,25 @@ def test_mixed_navier_stokes_rhs(N):
     assert err <= RHS_TOL, err
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_mixed_navier_stokes_rhs_viscous_dominated(N):
+    """mu = 0.05 on a noisy state: the lifted BR1 jumps carry a large share of the gradient,
+    so an error in the surface contraction of the viscous pass shows at O(1)."""
+    torch, dg, d, mesh = _setup((3, 3, 2), N)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=0.05, Pr=0.71)
+    q0 = uniform_perturbation(taylor_green(d.xyz, mach=0.1, noise=0.01, seed=2), 2e-2, seed=3)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs, opts=_mixed_opts())
+    want = rhs_ns(d.ref, d.geo, d.conn, q0, PerfectGas(1.4, 1.0), 0.05, 0.71)
+    err = field_err(rhs.cpu().numpy(), want)
+    assert err <= RHS_TOL, err
+    assert mesh.status() == 0
+    rhs2 = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs2, opts=_mixed_opts())
+    assert torch.equal(rhs, rhs2)  # deterministic: no read of unwritten shared memory
+
+
 def test_mixed_precision_config_state_error_reduced_mesh():
     """The precision config (NS, mu = 1e-3, Pr = 0.71, TGV Mach 0.1 + 1% noise, N = 4, 10 RK4 steps) on 6^3 x 6 tets."""
     from workloads.configs import _tgv_dt

@@ -58,6 +58,13 @@ def _tgv_dt(n, N, gamma=1.4, mach=0.1, noise=0.01):
     return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (umax + cmax))
 
 
+def _mixture_dt(n, N):
+    """Bound for the seeded 7-species mixture: R_mix <= R_u / W_min with W >= 2 kg/kmol,
+    gamma <= 5/3 (cp/R > 2 keeps cv/R > 1.5), T <= 3000 K, |u| <= 10*sqrt(3) m/s."""
+    cmax = math.sqrt(5.0 / 3.0 * 8314.462618 / 2.0 * 3000.0)
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (cmax + 10.0 * math.sqrt(3.0)))
+
+
 _NS_GAS = IdealGas(gamma=1.4, R=1.0, mu=1.0e-3, Pr=0.71)
 
 CONFIGS = {
@@ -76,7 +83,7 @@ CONFIGS = {
         gas=_NS_GAS, precision="mixed",
         description="as ns_viscous at 32^3 hexes x 6 = 196,608 tets, N=4; split-product tensor-core D/LIFT"),
     "mixture_learned": Config(
-        name="mixture_learned", n=32, N=2, physics="euler_mixture", state="mixture", steps=1, dt=5.0e-6,
+        name="mixture_learned", n=32, N=2, physics="euler_mixture", state="mixture", steps=1, dt=_mixture_dt(32, 2),
         description="7-species Euler mixture, seeded NASA-7, 32^3 hexes x 6 = 196,608 tets, N=2; "
                     "temperature Newton seeded by an MLP"),
 }
@@ -108,4 +115,35 @@ def build_case(cfg: Config, n=None, N=None):
         out.update(mixture=mix, Y=Y, T=T, vel=vel, p0=p0)
     else:
         raise ValueError(cfg.state)
+    return out
+
+
+def batched_cases(ncases=64, seed=0, n_min=2, n_max=20):
+    """The batched workload: ncases independent periodic boxes of n^3 hexahedra x 6
+    tetrahedra, n ~ U{n_min..n_max}, order N ~ U{1..4}, half of them Euler (isentropic
+    vortex + U(+-1e-3)) and half Navier-Stokes (Taylor-Green Mach 0.1 + 1% noise, mu = 1e-3,
+    Pr = 0.71), assigned by a seeded permutation.  Returns a list of dicts with the
+    mesh, nodes, state, gas and a CFL time step per case (PCG64, ``seed``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.integers(n_min, n_max + 1, size=ncases)
+    Ns = rng.integers(1, 5, size=ncases)
+    viscous = np.zeros(ncases, dtype=bool)
+    viscous[rng.permutation(ncases)[: ncases // 2]] = True
+    out = []
+    for i in range(ncases):
+        n, N = int(ns[i]), int(Ns[i])
+        verts, period = box_mesh(n, 1.0)
+        rst = equispaced_tet_nodes(N)
+        xyz = physical_nodes(verts, rst)
+        if viscous[i]:
+            q = taylor_green(xyz, gamma=1.4, mach=0.1, noise=0.01, seed=seed + i)
+            gas = _NS_GAS
+            dt = _tgv_dt(n, N)
+        else:
+            q = uniform_perturbation(isentropic_vortex(xyz, 0.0, gamma=1.4, period=period), 1.0e-3, seed=seed + i)
+            gas = IdealGas(gamma=1.4, R=1.0)
+            # |u| <= 1 + beta/(2 pi) e^(1/2) ~ 2.31, c <= sqrt(1.4) ~ 1.18 for the vortex
+            dt = 0.3 * (1.0 / n) / ((N + 1) ** 2 * (2.31 + 1.19))
+        out.append(dict(n=n, N=N, viscous=bool(viscous[i]), vertices=verts, period=period, ref_nodes=rst, q=q,
+                        gas=gas, dt=dt, K=verts.shape[0], Np=rst.shape[0]))
     return out
