@@ -320,6 +320,17 @@ __device__ __forceinline__ void rhs_tile(const RhsSmem<T, PHYS>& S, const MixedC
       for (int i = tid; i < nn; i += blockDim.x) S.sFv[cc * NODES + i] = fv_g[cc * KNp + base + i];
   __syncthreads();
 
+  // the RK inputs of this thread's node, loaded now so that their latency hides behind the fluxes
+  double k_old[5], q_old[5];
+  if (RK && tid < nn) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const size_t gi = v * KNp + base + tid;
+      k_old[v] = a != 0.0 ? c.k[gi] : 0.0;
+      q_old[v] = qin[gi];
+    }
+  }
+
   // volume fluxes (FP32; pressure relative to the element's first node, in FP64)
   if (tid < nn) {
     const int e = tid / Np, i = tid - e * Np;
@@ -421,9 +432,9 @@ __device__ __forceinline__ void rhs_tile(const RhsSmem<T, PHYS>& S, const MixedC
       const float r = S.sC[(e * 5 + v) * NPAD + i];
       const size_t gi = v * KNp + base + tid;
       if (RK) {
-        const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, (double)(dtf * r));
+        const double kk = fma(a, k_old[v], (double)(dtf * r));
         c.k[gi] = kk;
-        out[gi] = fma(b, kk, qin[gi]);
+        out[gi] = fma(b, kk, q_old[v]);
       } else {
         out[gi] = (double)r;
       }
@@ -587,7 +598,7 @@ __device__ __forceinline__ void vis_tile(const VisSmem<T>& S, const MixedCase& c
   __syncthreads();
 }
 
-// ---- kernels: one case (dg_rhs / dg_rk_stage) -------------------------------------------------
+// ---- kernels: one case (dg_rhs / dg_rk_stage), persistent over its element tiles -----------------
 template <int N, int PHYS, bool RK>
 __global__ void __launch_bounds__(RT<N, MOrd<N>::EPB>::NT) rhs_mixed_kernel(
     const MixedCase c, const uint32_t* __restrict__ b_g, const int32_t* __restrict__ fmask_g, const double a,
@@ -596,7 +607,8 @@ __global__ void __launch_bounds__(RT<N, MOrd<N>::EPB>::NT) rhs_mixed_kernel(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RhsSmem<T, PHYS> S(smem_raw);
   rhs_block_setup<T, PHYS>(S, b_g, fmask_g);
-  rhs_tile<T, PHYS, RK>(S, c, c.q[0], c.q[1], blockIdx.x * T::EPB, a, b);
+  for (int e0 = blockIdx.x * T::EPB; e0 < c.K; e0 += gridDim.x * T::EPB)
+    rhs_tile<T, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b);
 }
 
 template <int N>
@@ -607,7 +619,7 @@ __global__ void __launch_bounds__(VT<N, MOrd<N>::EPBV>::NT) viscous_mixed_kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const VisSmem<T> S(smem_raw);
   vis_block_setup<T>(S, d_g, l_g, fmask_g);
-  vis_tile<T>(S, c, c.q[0], blockIdx.x * T::EPB);
+  for (int e0 = blockIdx.x * T::EPB; e0 < c.K; e0 += gridDim.x * T::EPB) vis_tile<T>(S, c, c.q[0], e0);
 }
 
 // ---- kernels: a batch of cases, persistent over a work list of (case, first element) ----------

@@ -1,5 +1,6 @@
-// Mixed-precision path: split-FP16 operator tables (built once at upload) and the
+// Mixed-precision path: split-BF16 operator tables (built once at upload) and the
 // launchers of the tensor-core right-hand side / RK stage and its BR1 pass.
+#include <algorithm>
 #include <vector>
 
 #include "dg_mixed.cuh"
@@ -68,6 +69,17 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
   return e;
 }
 
+// Resident blocks per SM x SMs: the grid of a persistent kernel.
+template <typename K>
+int persistent_cap(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, per_sm * sms);
+}
+
 template <int N, int PHYS, bool RK>
 cudaError_t launch_rhs_mixed_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
   using T = mixk::RT<N, mixk::MOrd<N>::EPB>;
@@ -79,8 +91,10 @@ cudaError_t launch_rhs_mixed_t(const MeshDev& m, const mixk::MixedCase& c, doubl
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int blocks = (m.K + T::EPB - 1) / T::EPB;
-  mixk::rhs_mixed_kernel<N, PHYS, RK><<<blocks, T::NT, smem, s>>>(c, m.mx.rhs, m.fmask, a, b);
+  static int grid_cap = 0;
+  if (!grid_cap) grid_cap = persistent_cap(mixk::rhs_mixed_kernel<N, PHYS, RK>, T::NT, smem);
+  const int tiles = (m.K + T::EPB - 1) / T::EPB;
+  mixk::rhs_mixed_kernel<N, PHYS, RK><<<std::min(tiles, grid_cap), T::NT, smem, s>>>(c, m.mx.rhs, m.fmask, a, b);
   return cudaGetLastError();
 }
 
@@ -112,8 +126,10 @@ cudaError_t launch_viscous_mixed_t(const MeshDev& m, const mixk::MixedCase& c, c
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int blocks = (m.K + T::EPB - 1) / T::EPB;
-  mixk::viscous_mixed_kernel<N><<<blocks, T::NT, smem, s>>>(c, m.mx.d, m.mx.l, m.fmask);
+  static int grid_cap = 0;
+  if (!grid_cap) grid_cap = persistent_cap(mixk::viscous_mixed_kernel<N>, T::NT, smem);
+  const int tiles = (m.K + T::EPB - 1) / T::EPB;
+  mixk::viscous_mixed_kernel<N><<<std::min(tiles, grid_cap), T::NT, smem, s>>>(c, m.mx.d, m.mx.l, m.fmask);
   return cudaGetLastError();
 }
 
