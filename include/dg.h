@@ -57,6 +57,9 @@ extern "C" {
 /* bits of the device status word (dg_mesh_status / dg_gas_status) */
 #define DG_STATUS_NONPHYSICAL 1u      /* rho <= 0 or p <= 0 met at some node */
 #define DG_STATUS_NO_CONVERGENCE 2u   /* a Newton temperature solve hit its cap */
+#define DG_STATUS_TIMEOUT 4u          /* a tensor-core kernel's wait on its own MMA completion hit
+                                         its iteration bound; that kernel stopped early and its
+                                         output is incomplete */
 
 /* ---- limits -------------------------------------------------------------- */
 #define DG_MAX_ORDER 4

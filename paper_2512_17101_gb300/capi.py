@@ -20,6 +20,7 @@ DG_ERR_OOM = -6
 DG_ERR_UNSUPPORTED = -7
 DG_STATUS_NONPHYSICAL = 1
 DG_STATUS_NO_CONVERGENCE = 2
+DG_STATUS_TIMEOUT = 4
 DG_MAX_ORDER = 4
 DG_MAX_SPECIES = 8
 DG_GEO_STRIDE = 26

@@ -149,7 +149,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_mixed(m, g, q, s); });
       if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
     }
-    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_mixed(m, g, q, out, k, rk, a, b, dt, s); });
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_tc(m, g, q, out, k, rk, a, b, dt, s); });
     if (e != cudaSuccess) return cuda_fail(e, "mixed right-hand-side kernel");
     return DG_OK;
   }
@@ -237,6 +237,7 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dg::build_mixed_ops(d, m->ops);
+  if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);
   if (e != cudaSuccess) {
     free_mesh_device(d);
     delete m;

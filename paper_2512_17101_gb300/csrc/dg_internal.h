@@ -51,6 +51,8 @@ struct MixedOps {
   uint32_t* rhs = nullptr;  // rows i < NPAD: [-Dr_i | -Ds_i | -Dt_i | LIFT_i], KR columns
   uint32_t* d = nullptr;    // rows (a, i) < 3Np pad 8: D_a[i][:], KW columns
   uint32_t* l = nullptr;    // rows (face, i), 4 x NPAD: LIFT[i][face block], KF columns
+  unsigned char* tc_rhs = nullptr;  // tcgen05 operator table: 3 BF16 terms of [-Dr | -Ds | -Dt | LIFT]
+                                    // in the UMMA K-major layout (chunks of round16(Np) columns)
 };
 
 struct MeshDev {
@@ -84,6 +86,9 @@ cudaError_t launch_rhs_mixed(const MeshDev& m, const GasParams& g, const double*
                              double a, double b, double dt, cudaStream_t s);
 cudaError_t launch_viscous_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
+cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                          double a, double b, double dt, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture temperature (Newton).  seed_mode: DG_TSEED_*; nvar = 5 + ns; q is [nvar][n].

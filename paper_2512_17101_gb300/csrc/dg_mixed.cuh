@@ -228,6 +228,71 @@ static __global__ void prims_batched(const MixedCase* __restrict__ cases, const 
   }
 }
 
+// ---- pointwise FP32 fluxes shared by the mma.sync and tcgen05 tiles ------------------------------
+// Volume flux of one node, F[d][v] = (rho u_d, rho u u_d + dp e_d, u_d (rho E + p)) minus the
+// viscous flux (NS); dp is the pressure relative to the element's first node (an FP64 difference
+// rounded to FP32), pf the pressure itself.  Viscous flux layout: tau_xx, tau_yy, tau_zz, tau_xy,
+// tau_xz, tau_yz, then (u . tau - q_heat)_d.
+template <bool NS>
+__device__ __forceinline__ void node_flux(const float q[5], float dp, float pf, const float fv[9], float F[3][5]) {
+  const float ir = 1.0f / q[0];
+  const float u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = q[1 + d];
+    F[d][1] = q[1] * u[d];
+    F[d][2] = q[2] * u[d];
+    F[d][3] = q[3] * u[d];
+    F[d][1 + d] += dp;
+    F[d][4] = u[d] * (q[4] + pf);
+    if (NS) {
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) F[d][1 + ii] -= fv[kern::tau_index(ii, d)];
+      F[d][4] -= fv[6 + d];
+    }
+  }
+}
+
+// Surface term of one face node before the Fscale factor: g = n.F(q-) - F*, with the local
+// Lax-Friedrichs flux F* (pointwise lambda) and, for NS, the central viscous flux; dpn = p- - p+
+// as an FP64 difference rounded to FP32.
+template <bool NS>
+__device__ __forceinline__ void face_term(const float qm[5], const float qp[5], float pm, float pp, float dpn,
+                                          const float fvm[9], const float fvp[9], const float n[3], float gam,
+                                          float g[5]) {
+  const float irm = 1.0f / qm[0], irp = 1.0f / qp[0];
+  const float unm = (qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2]) * irm;
+  const float unp = (qp[1] * n[0] + qp[2] * n[1] + qp[3] * n[2]) * irp;
+  const float cm = sqrtf(gam * pm * irm), cp = sqrtf(gam * pp * irp);
+  const float lam = fmaxf(fabsf(unm) + cm, fabsf(unp) + cp);
+  float dq[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dq[v] = qm[v] - qp[v];
+  float dF[5];
+  dF[0] = dq[1] * n[0] + dq[2] * n[1] + dq[3] * n[2];
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii) dF[1 + ii] = qm[1 + ii] * unm - qp[1 + ii] * unp + dpn * n[ii];
+  dF[4] = unm * (qm[4] + pm) - unp * (qp[4] + pp);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) g[v] = 0.5f * (dF[v] - lam * dq[v]);
+  if (NS) {
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii) {
+      float dv = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int cc = kern::tau_index(ii, d);
+        dv = fmaf(n[d], fvm[cc] - fvp[cc], dv);
+      }
+      g[1 + ii] -= 0.5f * dv;
+    }
+    float de = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) de = fmaf(n[d], fvm[6 + d] - fvp[6 + d], de);
+    g[4] -= 0.5f * de;
+  }
+}
+
 // ---- tile configurations -------------------------------------------------------------------
 template <int N, int EPB_>
 struct RT {  // right-hand side: EPB elements per block
@@ -335,27 +400,12 @@ __device__ __forceinline__ void rhs_tile(const RhsSmem<T, PHYS>& S, const MixedC
   if (tid < nn) {
     const int e = tid / Np, i = tid - e * Np;
     const float* G = S.sGeo + e * GS;
-    const float m[3] = {S.sQ[NODES + tid], S.sQ[2 * NODES + tid], S.sQ[3 * NODES + tid]};
-    const float E = S.sQ[4 * NODES + tid];
-    const float dp = (float)(S.sP[tid] - S.sP[e * Np]);
-    const float pf = (float)S.sP[tid];
-    const float ir = 1.0f / S.sQ[tid];
-    const float u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
-    float F[3][5];
+    float qv[5], fv[9], F[3][5];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      F[d][0] = m[d];
-      F[d][1] = m[0] * u[d];
-      F[d][2] = m[1] * u[d];
-      F[d][3] = m[2] * u[d];
-      F[d][1 + d] += dp;
-      F[d][4] = u[d] * (E + pf);
-      if (NS) {
+    for (int v = 0; v < 5; ++v) qv[v] = S.sQ[v * NODES + tid];
 #pragma unroll
-        for (int ii = 0; ii < 3; ++ii) F[d][1 + ii] -= S.sFv[kern::tau_index(ii, d) * NODES + tid];
-        F[d][4] -= S.sFv[(6 + d) * NODES + tid];
-      }
-    }
+    for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? S.sFv[cc * NODES + tid] : 0.0f;
+    node_flux<NS>(qv, (float)(S.sP[tid] - S.sP[e * Np]), (float)S.sP[tid], fv, F);
 #pragma unroll
     for (int ra = 0; ra < 3; ++ra) {
       const float gx = G[3 * ra], gy = G[3 * ra + 1], gz = G[3 * ra + 2];
@@ -370,51 +420,24 @@ __device__ __forceinline__ void rhs_tile(const RhsSmem<T, PHYS>& S, const MixedC
   for (int j = tid; j < nel * NF; j += blockDim.x) {
     const int e = j / NF, mm = j - e * NF, f = mm / Nfp;
     const float* G = S.sGeo + e * GS;
-    const float nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
+    const float n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+    const float fs = G[12 + 4 * f];
     const int own = e * Np + S.sFm[mm];
     const int P = vmapP[(size_t)(e0 + e) * NF + mm];
-    float qm[5], qp[5];
+    float qm[5], qp[5], fvm[9], fvp[9];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       qm[v] = S.sQ[v * NODES + own];
       qp[v] = qf_g[v * KNp + P];
     }
-    const double pp64 = p_g[P];
-    const float dpn = (float)(S.sP[own] - pp64);
-    const float pm = (float)S.sP[own], pp = (float)pp64;
-    const float irm = 1.0f / qm[0], irp = 1.0f / qp[0];
-    const float unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
-    const float unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
-    const float cm = sqrtf(gam * pm * irm), cp = sqrtf(gam * pp * irp);
-    const float lam = fmaxf(fabsf(unm) + cm, fabsf(unp) + cp);
-    const float nn3[3] = {nx, ny, nz};
-    float dq[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) dq[v] = qm[v] - qp[v];
-    float dF[5];
-    dF[0] = dq[1] * nx + dq[2] * ny + dq[3] * nz;
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii) dF[1 + ii] = qm[1 + ii] * unm - qp[1 + ii] * unp + dpn * nn3[ii];
-    dF[4] = unm * (qm[4] + pm) - unp * (qp[4] + pp);
-    float g[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) g[v] = 0.5f * (dF[v] - lam * dq[v]);
-    if (NS) {
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii) {
-        float dv = 0.0f;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const int cc = kern::tau_index(ii, d);
-          dv = fmaf(nn3[d], S.sFv[cc * NODES + own] - fv_g[cc * KNp + P], dv);
-        }
-        g[1 + ii] -= 0.5f * dv;
-      }
-      float de = 0.0f;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) de = fmaf(nn3[d], S.sFv[(6 + d) * NODES + own] - fv_g[(6 + d) * KNp + P], de);
-      g[4] -= 0.5f * de;
+    for (int cc = 0; cc < 9; ++cc) {
+      fvm[cc] = NS ? S.sFv[cc * NODES + own] : 0.0f;
+      fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
     }
+    const double pp64 = p_g[P];
+    float g[5];
+    face_term<NS>(qm, qp, (float)S.sP[own], (float)pp64, (float)(S.sP[own] - pp64), fvm, fvp, n3, gam, g);
 #pragma unroll
     for (int v = 0; v < 5; ++v) put3(S.sA, AS, AT, e * 5 + v, 3 * Np + mm, fs * g[v]);
   }
@@ -657,4 +680,9 @@ __global__ void __launch_bounds__(VT<N, EPB>::NT) viscous_mixed_batched(
 }
 
 }  // namespace mixk
+
+// The mixed-form view of one mesh and state (k_mixed.cu).
+mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const double* qin, double* out, double* k,
+                                double dt);
+
 }  // namespace dg

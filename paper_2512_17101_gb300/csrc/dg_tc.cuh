@@ -1,0 +1,416 @@
+// Mixed-precision right-hand side with the D and LIFT contraction on the fifth-generation
+// tensor cores (tcgen05): operands in shared memory in the UMMA K-major layout, the
+// accumulator in tensor memory (TMEM), MMAs issued by one thread and completed through an
+// mbarrier, and the FP64 RK update from a shared-memory copy of the accumulator.
+//
+// Tile: 25 elements, rows r = 5 e + v (125 of the MMA's M = 128 rows; rows 125..127 are never
+// read), columns = output nodes i (N = NPAD = Np rounded up to 16).  The reduction runs over
+// chunks of KV = NPAD columns: three volume chunks (reference directions r, s, t: the
+// contravariant fluxes against -D_r, -D_s, -D_t) and one or two surface chunks (Fscale g
+// against LIFT).  Each chunk is produced by all threads into one shared-memory slot, then
+// contracted by KV/16 k-steps of the six split-BF16 products while nothing else may touch
+// the slot; two or three blocks per SM overlap one block's production with another's MMAs.
+// Operand columns past Np (volume) or past the face-node count (last surface chunk) hold
+// zeros or stale finite values from an earlier chunk; the operator table is zero there, so
+// they contribute nothing.
+#pragma once
+
+#include "dg_mixed.cuh"
+
+namespace dg {
+namespace tc {
+
+using mixk::MixedCase;
+using kern::GS;
+
+// ---- tcgen05 / mbarrier primitives (inline PTX) ------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address, the byte distance
+// between core matrices adjacent in K (lbo) and between 8-row groups (sbo), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B both BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// The mbarrier receives one arrival once every MMA this thread issued before has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;\n");
+}
+
+// Bounded wait for the phase with the given parity to complete; false when the bound is hit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Generic-proxy writes to shared memory become visible to the tensor core (async proxy).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: lane = warp's quarter + lane id).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(r[j]);
+}
+
+// ---- tile configuration --------------------------------------------------------------------
+constexpr int round16(int x) { return (x + 15) / 16 * 16; }
+
+template <int N>
+struct Cfg {
+  using O = kern::Ord<N>;
+  static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
+  static constexpr int E = 25, ROWS = 128;
+  static constexpr int KV = round16(Np), NPAD = KV;
+  static constexpr int NSURF = (NF + KV - 1) / KV, NCHUNK = 3 + NSURF, KB = NCHUNK * KV;
+  // operand slot: 3 terms x 128 rows x KV columns; core matrices adjacent in K are 144 B apart
+  // (not 128) so that the 16 B rows written by consecutive node threads fall in distinct banks
+  static constexpr int A_LBO = 144, A_SBO = (KV / 8) * A_LBO, A_TERM = 16 * A_SBO;
+  // operator table: 3 terms x NPAD rows x KB columns
+  static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NPAD / 8) * B_SBO;
+  static constexpr int CS = NPAD + 1;  // row stride (floats) of the accumulator copy
+  static constexpr int TMEM_COLS = NPAD <= 32 ? 32 : 64;
+  static constexpr int NT = N == 1 ? 128 : (N == 2 ? 256 : (N == 3 ? 256 : 448));
+  static constexpr int MINB = N == 4 ? 2 : (N == 3 ? 3 : 4);  // resident blocks per SM aimed at
+  static constexpr int NODES = E * Np, NPT = (NODES + NT - 1) / NT;
+  static constexpr uint32_t IDESC = idesc_bf16(ROWS, NPAD);
+  // shared-memory layout (bytes)
+  static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
+  static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
+  static constexpr int SMEM = OFF_BAR + 16;
+  static_assert(ROWS * CS * 4 <= 3 * A_TERM, "the accumulator copy must fit in the operand slot");
+  static_assert(ROWS * CS % 4 == 0, "the accumulator copy is cleared in 16 B words");
+  static_assert(NPAD <= TMEM_COLS, "TMEM columns");
+  static_assert(OFF_A % 16 == 0 && A_TERM % 16 == 0 && B_TERM % 16 == 0, "UMMA operands need 16 B alignment");
+};
+
+// Byte offset of (row, k) in a K-major no-swizzle operand.
+__device__ __forceinline__ int umma_off(int row, int k, int lbo, int sbo) {
+  return (row >> 3) * sbo + (k >> 3) * lbo + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Split FP32 value v into three BF16 terms (v = hi + mid + lo to 24 bits) stored at `off` of
+// the three term arrays (term stride ts bytes).
+__device__ __forceinline__ void put3_umma(unsigned char* A, int ts, int off, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  *reinterpret_cast<__nv_bfloat16*>(A + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(A + ts + off) = m;
+  *reinterpret_cast<__nv_bfloat16*>(A + 2 * ts + off) = l;
+}
+
+template <int N>
+struct Smem {
+  unsigned char* B;
+  unsigned char* A;
+  float* C;  // accumulator copy, aliases the operand slot once the tile's MMAs are done
+  float* geo;
+  int* fm;
+  uint64_t* bar;
+  uint32_t* tmem;
+  int* abort;
+  __device__ explicit Smem(unsigned char* raw) {
+    using C_ = Cfg<N>;
+    B = raw + C_::OFF_B;
+    A = raw + C_::OFF_A;
+    C = reinterpret_cast<float*>(A);
+    geo = reinterpret_cast<float*>(raw + C_::OFF_GEO);
+    fm = reinterpret_cast<int*>(raw + C_::OFF_FM);
+    bar = reinterpret_cast<uint64_t*>(raw + C_::OFF_BAR);
+    tmem = reinterpret_cast<uint32_t*>(raw + C_::OFF_BAR + 8);
+    abort = reinterpret_cast<int*>(raw + C_::OFF_BAR + 12);
+  }
+};
+
+// Block set-up: operator table, face map, a zeroed operand slot (no NaN patterns in columns
+// that no chunk writes), the mbarrier and the TMEM accumulator.
+template <int N>
+__device__ __forceinline__ void block_setup(const Smem<N>& S, const uint4* __restrict__ b_g,
+                                            const int32_t* __restrict__ fmask_g) {
+  using C_ = Cfg<N>;
+  const int tid = threadIdx.x;
+  uint4* Bs = reinterpret_cast<uint4*>(S.B);
+  for (int i = tid; i < 3 * C_::B_TERM / 16; i += blockDim.x) Bs[i] = b_g[i];
+  uint4* As = reinterpret_cast<uint4*>(S.A);
+  for (int i = tid; i < 3 * C_::A_TERM / 16; i += blockDim.x) As[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < C_::NF; i += blockDim.x) S.fm[i] = fmask_g[i];
+  if (tid == 0) {
+    mbar_init(smem_u32(S.bar), 1);
+    *S.abort = 0;
+  }
+  if (tid < 32) tmem_alloc(smem_u32(S.tmem), C_::TMEM_COLS);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+template <int N>
+__device__ __forceinline__ void block_teardown(const Smem<N>& S, uint32_t phase) {
+  using C_ = Cfg<N>;
+  // after an abort the MMA group whose wait timed out (parity phase ^ 1) may still be in
+  // flight: give it one more bounded wait before the accumulator is released
+  if (*S.abort && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), phase ^ 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(*S.tmem, C_::TMEM_COLS);
+}
+
+// Issue the MMAs of chunk c (KV/16 k-steps x 6 split products) and commit them to the mbarrier.
+template <int N>
+__device__ __forceinline__ void issue_chunk(const Smem<N>& S, int c) {
+  using C_ = Cfg<N>;
+  const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B), tmem = *S.tmem;
+  // products (A term, B term) whose term orders add up to at most 2
+  constexpr int PA[6] = {0, 0, 1, 0, 1, 2}, PB[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+  for (int ks = 0; ks < C_::KV / 16; ++ks)
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const uint64_t ad = umma_desc(a0 + PA[p] * C_::A_TERM + ks * 2 * C_::A_LBO, C_::A_LBO, C_::A_SBO);
+      const uint64_t bd =
+          umma_desc(b0 + PB[p] * C_::B_TERM + (c * (C_::KV / 8) + 2 * ks) * C_::B_LBO, C_::B_LBO, C_::B_SBO);
+      mma_bf16(tmem, ad, bd, C_::IDESC, (c > 0 || ks > 0 || p > 0) ? 1u : 0u);
+    }
+  mma_commit(smem_u32(S.bar));
+}
+
+// After a chunk's operand is in the slot: make it visible to the tensor core, issue its MMAs
+// and wait for them (the slot is rewritten next).  Returns false once any wait has timed out
+// (uniform across the block).
+template <int N>
+__device__ __forceinline__ bool run_chunk(const Smem<N>& S, int c, uint32_t& phase, unsigned* status) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (*S.abort) return false;
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue_chunk<N>(S, c);
+  }
+  if (!mbar_wait(smem_u32(S.bar), phase)) {
+    *S.abort = 1;
+    atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+  }
+  phase ^= 1u;
+  tc_fence_after();
+  return true;
+}
+
+// Elements [e0, e0 + 25) of case c: right-hand side (RK = false: out = rhs) or the LSRK stage
+// (k <- a k + dt rhs, out <- qin + b k).  Returns false when the block must stop (timeout).
+template <int N, int PHYS, bool RK>
+__device__ __forceinline__ bool rhs_tile(const Smem<N>& S, const MixedCase& c, const double* __restrict__ qin,
+                                         double* __restrict__ out, const int e0, const double a, const double b,
+                                         uint32_t& phase, unsigned* status) {
+  using C_ = Cfg<N>;
+  constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
+  constexpr bool NS = PHYS == kern::NAVIER_STOKES;
+  const int tid = threadIdx.x;
+  const int nel = min(C_::E, c.K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)c.K * Np;
+  const size_t base = (size_t)e0 * Np;
+  const float* __restrict__ qf_g = c.qf;
+  const double* __restrict__ p_g = c.p;
+  const float* __restrict__ fv_g = c.fv;
+
+  for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
+
+  // volume fluxes of this thread's nodes (FP32; pressure relative to the element's first node in FP64)
+  float F[NPT][3][5];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int n = tid + s * NT;
+    if (n < nn) {
+      const int e = n / Np;
+      const size_t gn = base + n;
+      float qv[5], fv[9];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qv[v] = qf_g[v * KNp + gn];
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? fv_g[cc * KNp + gn] : 0.0f;
+      const double p = p_g[gn];
+      mixk::node_flux<NS>(qv, (float)(p - p_g[base + (size_t)e * Np]), (float)p, fv, F[s]);
+    }
+  }
+  __syncthreads();  // geometry in place; the previous tile's accumulator copy has been read
+
+  // three volume chunks: contravariant flux sum_d (dr_a/dx_d) F_d at column i
+#pragma unroll
+  for (int ra = 0; ra < 3; ++ra) {
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int n = tid + s * NT;
+      if (n < nn) {
+        const int e = n / Np, i = n - e * Np;
+        const float* G = S.geo + e * GS;
+        const float gx = G[3 * ra], gy = G[3 * ra + 1], gz = G[3 * ra + 2];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + v, i, C_::A_LBO, C_::A_SBO),
+                    fmaf(gx, F[s][0][v], fmaf(gy, F[s][1][v], gz * F[s][2][v])));
+      }
+    }
+    if (!run_chunk<N>(S, ra, phase, status)) return false;
+  }
+
+  // surface chunks: face nodes [sc KV, sc KV + KV) of every element
+  const float gam = (float)c.gas.gamma;
+#pragma unroll 1
+  for (int sc = 0; sc < C_::NSURF; ++sc) {
+    const int m0 = sc * KV, w = min(KV, NF - m0);
+    for (int j = tid; j < nel * w; j += NT) {
+      const int e = j / w, mm = m0 + (j - e * w), f = mm / Nfp;
+      const float* G = S.geo + e * GS;
+      const float n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+      const float fs = G[12 + 4 * f];
+      const size_t own = base + (size_t)e * Np + S.fm[mm];
+      const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
+      float qm[5], qp[5], fvm[9], fvp[9];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = qf_g[v * KNp + own];
+        qp[v] = qf_g[v * KNp + P];
+      }
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) {
+        fvm[cc] = NS ? fv_g[cc * KNp + own] : 0.0f;
+        fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
+      }
+      const double pm64 = p_g[own], pp64 = p_g[P];
+      float g[5];
+      mixk::face_term<NS>(qm, qp, (float)pm64, (float)pp64, (float)(pm64 - pp64), fvm, fvp, n3, gam, g);
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
+    }
+    if (!run_chunk<N>(S, 3 + sc, phase, status)) return false;
+  }
+
+  // accumulator -> shared memory (warps 0..3 own TMEM lanes 0..127), then the node-parallel update
+  if (tid < 128) {
+    const int warp = tid >> 5, row = tid;
+    float* Crow = S.C + row * C_::CS;
+#pragma unroll
+    for (int c0 = 0; c0 < C_::NPAD; c0 += 16) {
+      float r[16];
+      tmem_ld16(*S.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) Crow[c0 + j] = r[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  const float dtf = (float)c.dt;
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int n = tid + s * NT;
+    if (n < nn) {
+      const int e = n / Np, i = n - e * Np;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float r = S.C[(e * 5 + v) * C_::CS + i];
+        const size_t gi = v * KNp + base + n;
+        if (RK) {
+          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, (double)(dtf * r));
+          c.k[gi] = kk;
+          out[gi] = fma(b, kk, qin[gi]);
+        } else {
+          out[gi] = (double)r;
+        }
+      }
+    }
+  }
+  // the accumulator copy overwrote operand columns that no chunk rewrites (padding whose
+  // operator entries are zero): clear it, so that they hold zeros rather than FP32 bit
+  // patterns read as BF16 (possibly NaN, and 0 x NaN = NaN)
+  __syncthreads();
+  uint4* Cz = reinterpret_cast<uint4*>(S.C);
+  for (int i = tid; i < C_::ROWS * C_::CS / 4; i += NT) Cz[i] = make_uint4(0u, 0u, 0u, 0u);
+  return true;
+}
+
+// ---- kernels ---------------------------------------------------------------------------------
+template <int N, int PHYS, bool RK>
+__global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_kernel(const MixedCase c, const uint4* __restrict__ b_g,
+                                                             const int32_t* __restrict__ fmask_g, const double a,
+                                                             const double b, unsigned* __restrict__ status) {
+  using C_ = Cfg<N>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const Smem<N> S(smem_raw);
+  block_setup<N>(S, b_g, fmask_g);
+  uint32_t phase = 0;
+  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
+    if (!rhs_tile<N, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status)) break;
+  block_teardown<N>(S, phase);
+}
+
+// A batch of cases: persistent over a work list of (case, first element) tiles; the stage's
+// parity picks input and output among each case's two state buffers.
+template <int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_batched(const MixedCase* __restrict__ cases,
+                                                              const int2* __restrict__ work, const int nwork,
+                                                              const uint4* __restrict__ b_g,
+                                                              const int32_t* __restrict__ fmask_g, const int stage,
+                                                              const double a, const double b,
+                                                              unsigned* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const Smem<N> S(smem_raw);
+  block_setup<N>(S, b_g, fmask_g);
+  uint32_t phase = 0;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 it = work[w];
+    const MixedCase& c = cases[it.x];
+    if (!rhs_tile<N, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status)) break;
+  }
+  block_teardown<N>(S, phase);
+}
+
+}  // namespace tc
+}  // namespace dg

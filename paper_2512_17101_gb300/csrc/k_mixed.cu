@@ -149,6 +149,7 @@ void free_mixed_ops(MeshDev& m) {
   cudaFree(m.mx.rhs);
   cudaFree(m.mx.d);
   cudaFree(m.mx.l);
+  cudaFree(m.mx.tc_rhs);
   m.mx = MixedOps();
 }
 

@@ -1,0 +1,113 @@
+// tcgen05 path of the mixed-precision right-hand side: the operator table in the UMMA layout
+// (built once at upload) and the launchers.
+#include <algorithm>
+#include <vector>
+
+#include "dg_tc.cuh"
+
+namespace dg {
+namespace {
+
+// out[term] = UMMA K-major image (core matrices 128 B apart in K, sbo between 8-row groups)
+// of the term-th BF16 part of M[rows][cols]: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid).
+__global__ void umma_table_kernel(const double* __restrict__ M, int rows, int cols, int sbo, int term_bytes,
+                                  unsigned char* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.x * blockDim.x) {
+    const int r = i / cols, k = i - r * cols;
+    const int off = (r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+    double rem = M[i];
+    for (int term = 0; term < 3; ++term) {
+      const __nv_bfloat16 h = __double2bfloat16(rem);
+      *reinterpret_cast<__nv_bfloat16*>(out + (size_t)term * term_bytes + off) = h;
+      rem -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+template <int N>
+cudaError_t build_t(MeshDev& m, const RefOps& o) {
+  using C = tc::Cfg<N>;
+  const int Np = C::Np, NF = C::NF, KV = C::KV;
+  const std::vector<double>* D[3] = {&o.Dr, &o.Ds, &o.Dt};
+  std::vector<double> R((size_t)C::NPAD * C::KB, 0.0);
+  for (int i = 0; i < Np; ++i) {
+    for (int a = 0; a < 3; ++a)
+      for (int j = 0; j < Np; ++j) R[(size_t)i * C::KB + a * KV + j] = -(*D[a])[i * Np + j];
+    for (int mm = 0; mm < NF; ++mm) R[(size_t)i * C::KB + 3 * KV + mm] = o.LIFT[i * NF + mm];
+  }
+  double* dM = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dM, sizeof(double) * R.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dM, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m.mx.tc_rhs, 3 * (size_t)C::B_TERM);
+  if (e == cudaSuccess) e = cudaMemset(m.mx.tc_rhs, 0, 3 * (size_t)C::B_TERM);
+  if (e == cudaSuccess) {
+    umma_table_kernel<<<64, 256>>>(dM, C::NPAD, C::KB, C::B_SBO, C::B_TERM, m.mx.tc_rhs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dM);
+  return e;
+}
+
+template <typename K>
+int persistent_cap(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, per_sm * sms);
+}
+
+template <int N, int PHYS, bool RK>
+cudaError_t launch_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
+  using C = tc::Cfg<N>;
+  auto kern_fn = tc::rhs_tc_kernel<N, PHYS, RK>;
+  static int grid_cap = 0;
+  if (!grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    grid_cap = persistent_cap(kern_fn, C::NT, C::SMEM);
+  }
+  const int tiles = (m.K + C::E - 1) / C::E;
+  kern_fn<<<std::min(tiles, grid_cap), C::NT, C::SMEM, s>>>(c, reinterpret_cast<const uint4*>(m.mx.tc_rhs),
+                                                              m.fmask, a, b, m.status);
+  return cudaGetLastError();
+}
+
+template <int PHYS>
+cudaError_t dispatch(const MeshDev& m, const mixk::MixedCase& c, bool rk, double a, double b, cudaStream_t s) {
+  switch (m.N) {
+#define DG_CASE(NN) \
+  case NN:          \
+    return rk ? launch_t<NN, PHYS, true>(m, c, a, b, s) : launch_t<NN, PHYS, false>(m, c, a, b, s);
+    DG_CASE(1)
+    DG_CASE(2)
+    DG_CASE(3)
+    DG_CASE(4)
+#undef DG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops) {
+  switch (m.N) {
+    case 1: return build_t<1>(m, ops);
+    case 2: return build_t<2>(m, ops);
+    case 3: return build_t<3>(m, ops);
+    case 4: return build_t<4>(m, ops);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                          double a, double b, double dt, cudaStream_t s) {
+  const mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
+  if (g.mu > 0) return dispatch<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
+  return dispatch<kern::EULER>(m, c, rk, a, b, s);
+}
+
+}  // namespace dg

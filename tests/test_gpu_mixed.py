@@ -102,6 +102,27 @@ def test_mixed_precision_config_state_error_reduced_mesh():
     assert mesh.status() == 0
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_mixed_many_tiles_per_block_against_fp64_path(N):
+    """14^3 x 6 = 16,464 tets: more element tiles than resident blocks, so every persistent block
+    runs several tiles in a row (state carried from tile to tile must not leak).  Mixed RHS and
+    two RK4 steps against the FP64 GPU path, which matches the oracle to 1e-11."""
+    from workloads.configs import _tgv_dt
+    torch, dg, d, mesh = _setup(14, N)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=1e-3, Pr=0.71)
+    q0 = torch.tensor(taylor_green(d.xyz, mach=0.1, noise=0.01, seed=4), device="cuda")
+    r64, rmx = torch.empty_like(q0), torch.empty_like(q0)
+    dg.dg_rhs(mesh, gas, q0, r64)
+    dg.dg_rhs(mesh, gas, q0, rmx, opts=_mixed_opts())
+    assert field_err(rmx.cpu().numpy(), r64.cpu().numpy()) <= RHS_TOL
+    q64, qmx = q0.clone(), q0.clone()
+    dt = _tgv_dt(14, N)
+    dg.lsrk4_step(mesh, gas, q64, dt, steps=2)
+    dg.lsrk4_step(mesh, gas, qmx, dt, steps=2, opts=_mixed_opts())
+    assert field_err(qmx.cpu().numpy(), q64.cpu().numpy()) <= STATE_TOL
+    assert mesh.status() == 0
+
+
 @pytest.mark.slow
 def test_mixed_precision_config_full_size_against_fp64_path():
     """Full precision config (32^3 x 6 = 196,608 tets, N = 4, 10 RK4 steps): mixed vs the FP64 path,
