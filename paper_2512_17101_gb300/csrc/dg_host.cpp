@@ -1,4 +1,5 @@
 // C ABI of libdg: argument checks, handle management and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -470,3 +471,37 @@ int dg_mlp_guess(dg_gas gas, int64_t n, const double* q, double* T, void* stream
 }
 
 }  // extern "C"
+
+namespace dg {
+
+int device_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+int resident_blocks(const void* fn, int threads, size_t dyn_smem) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+  int n = blk_sm > 0 ? blk_sm : 1;
+  if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+  n = std::min(n, smem_sm / (int)(dyn_smem + fa.sharedSizeBytes + (size_t)reserved));
+  n = std::min(n, thr_sm / (warps * 32));
+  return std::max(n, 1);
+}
+
+}  // namespace dg

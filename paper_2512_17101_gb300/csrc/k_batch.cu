@@ -16,7 +16,7 @@
 #include <map>
 #include <vector>
 
-#include "dg_mixed.cuh"
+#include "dg_tc.cuh"
 
 namespace dg {
 namespace {
@@ -30,32 +30,23 @@ struct Group {
   std::vector<int> cases;
 };
 
-int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms;
-}
-
 // Persistent grid of a kernel: resident blocks per SM x SMs, at most one block per work item.
 template <typename K>
 int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  return std::max(1, std::min(nwork, per_sm * sm_count()));
+  return std::max(1, std::min(nwork, resident_blocks((const void*)kernel, threads, smem) * device_sms()));
 }
 
-template <int N, int EPB, int PHYS>
+// Right-hand side + RK stage of a group on the tensor cores (tcgen05), tiles of 25 elements.
+template <int N, int PHYS>
 cudaError_t rhs_batched_t(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask, int stage,
-                          double a, double b, cudaStream_t s) {
-  using T = mixk::RT<N, EPB>;
-  const size_t smem = T::smem(PHYS == kern::NAVIER_STOKES);
-  auto kern_fn = mixk::rhs_mixed_batched<N, EPB, PHYS>;
-  cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                          double a, double b, unsigned* status, cudaStream_t s) {
+  using C = tc::Cfg<N>;
+  auto kern_fn = tc::rhs_tc_batched<N, PHYS>;
+  cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(kern_fn, T::NT, smem, g.nwork);
-  kern_fn<<<grid, T::NT, smem, s>>>(cases, g.work, g.nwork, mx.rhs, fmask, stage, a, b);
+  const int grid = persistent_grid(kern_fn, C::NT, C::SMEM, g.nwork);
+  kern_fn<<<grid, C::NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_rhs), fmask,
+                                       stage, a, b, status);
   return cudaGetLastError();
 }
 
@@ -72,10 +63,11 @@ cudaError_t vis_batched_t(const Group& g, const MixedCase* cases, const MixedOps
   return cudaGetLastError();
 }
 
-// Candidate tiles (elements per block) per order; the first is the single-case default.
-const std::vector<int>& rhs_candidates(int N) {
-  static const std::vector<int> c1{32, 64}, c2{16, 32}, c3{16, 32}, c4{16};
-  return N == 1 ? c1 : N == 2 ? c2 : N == 3 ? c3 : c4;
+// Candidate tiles (elements per block) per order; the first is the single-case default.  The
+// right-hand side runs in tensor-core tiles of 128 rows = 25 elements x 5 variables.
+const std::vector<int>& rhs_candidates(int) {
+  static const std::vector<int> c{tc::Cfg<1>::E};
+  return c;
 }
 const std::vector<int>& vis_candidates(int N) {
   static const std::vector<int> c1{32, 16}, c2{16, 8}, c3{8, 16}, c4{8};
@@ -83,21 +75,21 @@ const std::vector<int>& vis_candidates(int N) {
 }
 
 cudaError_t launch_rhs_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
-                             int stage, double a, double b, cudaStream_t s) {
+                             int stage, double a, double b, unsigned* status, cudaStream_t s) {
   const bool ns = g.phys == kern::NAVIER_STOKES;
-#define DG_RHS(NN, EE)                                                                                      \
-  if (g.N == NN && g.epb == EE)                                                                            \
-    return ns ? rhs_batched_t<NN, EE, kern::NAVIER_STOKES>(g, cases, mx, fmask, stage, a, b, s)            \
-              : rhs_batched_t<NN, EE, kern::EULER>(g, cases, mx, fmask, stage, a, b, s);
-  DG_RHS(1, 32)
-  DG_RHS(1, 64)
-  DG_RHS(2, 16)
-  DG_RHS(2, 32)
-  DG_RHS(3, 16)
-  DG_RHS(3, 32)
-  DG_RHS(4, 16)
+  switch (g.N) {
+#define DG_RHS(NN)                                                                                 \
+  case NN:                                                                                         \
+    return ns ? rhs_batched_t<NN, kern::NAVIER_STOKES>(g, cases, mx, fmask, stage, a, b, status, s) \
+              : rhs_batched_t<NN, kern::EULER>(g, cases, mx, fmask, stage, a, b, status, s);
+    DG_RHS(1)
+    DG_RHS(2)
+    DG_RHS(3)
+    DG_RHS(4)
 #undef DG_RHS
-  return cudaErrorInvalidValue;
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_vis_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
@@ -158,7 +150,7 @@ cudaError_t build_work(dg::Group& g, const dg_batch_s* b) {
 }
 
 cudaError_t launch_prims(dg_batch_s* b, int stage, cudaStream_t s) {
-  const int grid = std::min(b->prims_nwork, dg::sm_count() * 8);
+  const int grid = std::min(b->prims_nwork, dg::device_sms() * 8);
   dg::mixk::prims_batched<<<std::max(grid, 1), 256, 0, s>>>(b->dcases, b->prims_work, b->prims_nwork, stage,
                                                              b->status);
   return cudaGetLastError();
@@ -174,7 +166,7 @@ cudaError_t launch_stage(dg_batch_s* b, int stage, cudaStream_t s) {
   for (const dg::Group& g : b->rhs)
     if (e == cudaSuccess) {
       const dg::MeshDev& m = mdev(b, g.N);
-      e = dg::launch_rhs_group(g, b->dcases, m.mx, m.fmask, stage, dg::kRK4A[stage], dg::kRK4B[stage], s);
+      e = dg::launch_rhs_group(g, b->dcases, m.mx, m.fmask, stage, dg::kRK4A[stage], dg::kRK4B[stage], b->status, s);
     }
   return e;
 }
@@ -332,7 +324,7 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
         const dg::MeshDev& m = mdev(b, g.N);
         const double ms = time_launches(
             [&] {
-              return dg::launch_rhs_group(g, b->dcases, m.mx, m.fmask, 0, dg::kRK4A[0], dg::kRK4B[0], b->cap);
+              return dg::launch_rhs_group(g, b->dcases, m.mx, m.fmask, 0, dg::kRK4A[0], dg::kRK4B[0], b->status, b->cap);
             },
             b->cap);
         b->tune_ms[g.N - 1][g.phys == dg::kern::NAVIER_STOKES][ci] = ms;

@@ -69,17 +69,6 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
   return e;
 }
 
-// Resident blocks per SM x SMs: the grid of a persistent kernel.
-template <typename K>
-int persistent_cap(K kernel, int threads, size_t smem) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  return std::max(1, per_sm * sms);
-}
-
 template <int N, int PHYS, bool RK>
 cudaError_t launch_rhs_mixed_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
   using T = mixk::RT<N, mixk::MOrd<N>::EPB>;
@@ -92,7 +81,7 @@ cudaError_t launch_rhs_mixed_t(const MeshDev& m, const mixk::MixedCase& c, doubl
     configured = true;
   }
   static int grid_cap = 0;
-  if (!grid_cap) grid_cap = persistent_cap(mixk::rhs_mixed_kernel<N, PHYS, RK>, T::NT, smem);
+  if (!grid_cap) grid_cap = resident_blocks((const void*)mixk::rhs_mixed_kernel<N, PHYS, RK>, T::NT, smem) * device_sms();
   const int tiles = (m.K + T::EPB - 1) / T::EPB;
   mixk::rhs_mixed_kernel<N, PHYS, RK><<<std::min(tiles, grid_cap), T::NT, smem, s>>>(c, m.mx.rhs, m.fmask, a, b);
   return cudaGetLastError();
@@ -127,7 +116,7 @@ cudaError_t launch_viscous_mixed_t(const MeshDev& m, const mixk::MixedCase& c, c
     configured = true;
   }
   static int grid_cap = 0;
-  if (!grid_cap) grid_cap = persistent_cap(mixk::viscous_mixed_kernel<N>, T::NT, smem);
+  if (!grid_cap) grid_cap = resident_blocks((const void*)mixk::viscous_mixed_kernel<N>, T::NT, smem) * device_sms();
   const int tiles = (m.K + T::EPB - 1) / T::EPB;
   mixk::viscous_mixed_kernel<N><<<std::min(tiles, grid_cap), T::NT, smem, s>>>(c, m.mx.d, m.mx.l, m.fmask);
   return cudaGetLastError();

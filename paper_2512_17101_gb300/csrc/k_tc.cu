@@ -49,16 +49,6 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
   return e;
 }
 
-template <typename K>
-int persistent_cap(K kernel, int threads, size_t smem) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  return std::max(1, per_sm * sms);
-}
-
 template <int N, int PHYS, bool RK>
 cudaError_t launch_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
   using C = tc::Cfg<N>;
@@ -67,7 +57,7 @@ cudaError_t launch_t(const MeshDev& m, const mixk::MixedCase& c, double a, doubl
   if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    grid_cap = persistent_cap(kern_fn, C::NT, C::SMEM);
+    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM) * device_sms();
   }
   const int tiles = (m.K + C::E - 1) / C::E;
   kern_fn<<<std::min(tiles, grid_cap), C::NT, C::SMEM, s>>>(c, reinterpret_cast<const uint4*>(m.mx.tc_rhs),
