@@ -147,7 +147,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_mixed(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "mixed primitives kernel");
     if (g.mu > 0) {
-      e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_mixed(m, g, q, s); });
+      e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_tc(m, g, q, s); });
       if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
     }
     e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_tc(m, g, q, out, k, rk, a, b, dt, s); });

@@ -53,6 +53,7 @@ struct MixedOps {
   uint32_t* l = nullptr;    // rows (face, i), 4 x NPAD: LIFT[i][face block], KF columns
   unsigned char* tc_rhs = nullptr;  // tcgen05 operator table: 3 BF16 terms of [-Dr | -Ds | -Dt | LIFT]
                                     // in the UMMA K-major layout (chunks of round16(Np) columns)
+  unsigned char* tc_vis = nullptr;  // tcgen05 BR1 table: rows (a, i), [D_a | 1/2 sum_f c_fa LIFT_f]
 };
 
 struct MeshDev {
@@ -89,6 +90,7 @@ cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const doubl
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                           double a, double b, double dt, cudaStream_t s);
+cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture temperature (Newton).  seed_mode: DG_TSEED_*; nvar = 5 + ns; q is [nvar][n].

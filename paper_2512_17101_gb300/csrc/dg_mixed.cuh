@@ -293,6 +293,36 @@ __device__ __forceinline__ void face_term(const float qm[5], const float qp[5], 
   }
 }
 
+// Viscous flux of one node from the gradients grad[d][w] of w = (rho, rho u, rho v, rho w, T)
+// (velocity gradient by the product rule), Stokes hypothesis: fv = (tau_xx, tau_yy, tau_zz,
+// tau_xy, tau_xz, tau_yz, (u . tau + kappa grad T)_x, _y, _z).
+__device__ __forceinline__ void viscous_flux_node(float rho, const float m[3], const float grad[3][5], float mu,
+                                                  float kap, float fv[9]) {
+  const float ir = 1.0f / rho;
+  const float u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+  float du[3][3];
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) du[ii][d] = (grad[d][1 + ii] - u[ii] * grad[d][0]) * ir;
+  const float divu = du[0][0] + du[1][1] + du[2][2];
+  float tau[3][3];
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) tau[ii][jj] = mu * (du[ii][jj] + du[jj][ii]);
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii) tau[ii][ii] -= (2.0f / 3.0f) * mu * divu;
+  fv[0] = tau[0][0];
+  fv[1] = tau[1][1];
+  fv[2] = tau[2][2];
+  fv[3] = tau[0][1];
+  fv[4] = tau[0][2];
+  fv[5] = tau[1][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) fv[6 + d] = fmaf(u[0], tau[0][d], fmaf(u[1], tau[1][d], fmaf(u[2], tau[2][d], kap * grad[d][4])));
+}
+
 // ---- tile configurations -------------------------------------------------------------------
 template <int N, int EPB_>
 struct RT {  // right-hand side: EPB elements per block
@@ -590,33 +620,12 @@ __device__ __forceinline__ void vis_tile(const VisSmem<T>& S, const MixedCase& c
         for (int d = 0; d < 3; ++d) grad[d][v] = fmaf(G[9 + 4 * f + d], l, grad[d][v]);
       }
     }
-    const float rho = (float)S.sRho[tid], ir = 1.0f / rho;
-    const float u[3] = {S.sM[tid] * ir, S.sM[NODES + tid] * ir, S.sM[2 * NODES + tid] * ir};
-    float du[3][3];
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) du[ii][d] = (grad[d][1 + ii] - u[ii] * grad[d][0]) * ir;
-    const float mu = (float)c.gas.mu, kap = (float)c.gas.kappa;
-    const float divu = du[0][0] + du[1][1] + du[2][2];
-    float tau[3][3];
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) tau[ii][jj] = mu * (du[ii][jj] + du[jj][ii]);
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii) tau[ii][ii] -= (2.0f / 3.0f) * mu * divu;
-    float* fv = c.fv;
+    const float m3[3] = {S.sM[tid], S.sM[NODES + tid], S.sM[2 * NODES + tid]};
+    float f9[9];
+    viscous_flux_node((float)S.sRho[tid], m3, grad, (float)c.gas.mu, (float)c.gas.kappa, f9);
     const size_t gi = base + tid;
-    fv[0 * KNp + gi] = tau[0][0];
-    fv[1 * KNp + gi] = tau[1][1];
-    fv[2 * KNp + gi] = tau[2][2];
-    fv[3 * KNp + gi] = tau[0][1];
-    fv[4 * KNp + gi] = tau[0][2];
-    fv[5 * KNp + gi] = tau[1][2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      fv[(6 + d) * KNp + gi] = fmaf(u[0], tau[0][d], fmaf(u[1], tau[1][d], fmaf(u[2], tau[2][d], kap * grad[d][4])));
+    for (int cc = 0; cc < 9; ++cc) c.fv[cc * KNp + gi] = f9[cc];
   }
   __syncthreads();
 }

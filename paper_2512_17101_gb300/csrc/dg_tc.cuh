@@ -143,7 +143,7 @@ __device__ __forceinline__ void put3_umma(unsigned char* A, int ts, int off, flo
   *reinterpret_cast<__nv_bfloat16*>(A + 2 * ts + off) = l;
 }
 
-template <int N>
+template <class C_>
 struct Smem {
   unsigned char* B;
   unsigned char* A;
@@ -154,7 +154,6 @@ struct Smem {
   uint32_t* tmem;
   int* abort;
   __device__ explicit Smem(unsigned char* raw) {
-    using C_ = Cfg<N>;
     B = raw + C_::OFF_B;
     A = raw + C_::OFF_A;
     C = reinterpret_cast<float*>(A);
@@ -168,10 +167,9 @@ struct Smem {
 
 // Block set-up: operator table, face map, a zeroed operand slot (no NaN patterns in columns
 // that no chunk writes), the mbarrier and the TMEM accumulator.
-template <int N>
-__device__ __forceinline__ void block_setup(const Smem<N>& S, const uint4* __restrict__ b_g,
+template <class C_>
+__device__ __forceinline__ void block_setup(const Smem<C_>& S, const uint4* __restrict__ b_g,
                                             const int32_t* __restrict__ fmask_g) {
-  using C_ = Cfg<N>;
   const int tid = threadIdx.x;
   uint4* Bs = reinterpret_cast<uint4*>(S.B);
   for (int i = tid; i < 3 * C_::B_TERM / 16; i += blockDim.x) Bs[i] = b_g[i];
@@ -189,9 +187,8 @@ __device__ __forceinline__ void block_setup(const Smem<N>& S, const uint4* __res
   tc_fence_after();
 }
 
-template <int N>
-__device__ __forceinline__ void block_teardown(const Smem<N>& S, uint32_t phase) {
-  using C_ = Cfg<N>;
+template <class C_>
+__device__ __forceinline__ void block_teardown(const Smem<C_>& S, uint32_t phase) {
   // after an abort the MMA group whose wait timed out (parity phase ^ 1) may still be in
   // flight: give it one more bounded wait before the accumulator is released
   if (*S.abort && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), phase ^ 1u);
@@ -202,9 +199,8 @@ __device__ __forceinline__ void block_teardown(const Smem<N>& S, uint32_t phase)
 }
 
 // Issue the MMAs of chunk c (KV/16 k-steps x 6 split products) and commit them to the mbarrier.
-template <int N>
-__device__ __forceinline__ void issue_chunk(const Smem<N>& S, int c) {
-  using C_ = Cfg<N>;
+template <class C_>
+__device__ __forceinline__ void issue_chunk(const Smem<C_>& S, int c) {
   const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B), tmem = *S.tmem;
   // products (A term, B term) whose term orders add up to at most 2
   constexpr int PA[6] = {0, 0, 1, 0, 1, 2}, PB[6] = {0, 1, 0, 2, 1, 0};
@@ -223,15 +219,15 @@ __device__ __forceinline__ void issue_chunk(const Smem<N>& S, int c) {
 // After a chunk's operand is in the slot: make it visible to the tensor core, issue its MMAs
 // and wait for them (the slot is rewritten next).  Returns false once any wait has timed out
 // (uniform across the block).
-template <int N>
-__device__ __forceinline__ bool run_chunk(const Smem<N>& S, int c, uint32_t& phase, unsigned* status) {
+template <class C_>
+__device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& phase, unsigned* status) {
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   if (*S.abort) return false;
   if (threadIdx.x == 0) {
     tc_fence_after();
-    issue_chunk<N>(S, c);
+    issue_chunk<C_>(S, c);
   }
   if (!mbar_wait(smem_u32(S.bar), phase)) {
     *S.abort = 1;
@@ -245,7 +241,7 @@ __device__ __forceinline__ bool run_chunk(const Smem<N>& S, int c, uint32_t& pha
 // Elements [e0, e0 + 25) of case c: right-hand side (RK = false: out = rhs) or the LSRK stage
 // (k <- a k + dt rhs, out <- qin + b k).  Returns false when the block must stop (timeout).
 template <int N, int PHYS, bool RK>
-__device__ __forceinline__ bool rhs_tile(const Smem<N>& S, const MixedCase& c, const double* __restrict__ qin,
+__device__ __forceinline__ bool rhs_tile(const Smem<Cfg<N>>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
                                          uint32_t& phase, unsigned* status) {
   using C_ = Cfg<N>;
@@ -279,7 +275,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<N>& S, const MixedCase& c, c
       mixk::node_flux<NS>(qv, (float)(p - p_g[base + (size_t)e * Np]), (float)p, fv, F[s]);
     }
   }
-  __syncthreads();  // geometry in place; the previous tile's accumulator copy has been read
+  __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
 
   // three volume chunks: contravariant flux sum_d (dr_a/dx_d) F_d at column i
 #pragma unroll
@@ -297,7 +293,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<N>& S, const MixedCase& c, c
                     fmaf(gx, F[s][0][v], fmaf(gy, F[s][1][v], gz * F[s][2][v])));
       }
     }
-    if (!run_chunk<N>(S, ra, phase, status)) return false;
+    if (!run_chunk<C_>(S, ra, phase, status)) return false;
   }
 
   // surface chunks: face nodes [sc KV, sc KV + KV) of every element
@@ -330,7 +326,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<N>& S, const MixedCase& c, c
       for (int v = 0; v < 5; ++v)
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
     }
-    if (!run_chunk<N>(S, 3 + sc, phase, status)) return false;
+    if (!run_chunk<C_>(S, 3 + sc, phase, status)) return false;
   }
 
   // accumulator -> shared memory (warps 0..3 own TMEM lanes 0..127), then the node-parallel update
@@ -383,12 +379,12 @@ __global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_kernel(const 
                                                              const double b, unsigned* __restrict__ status) {
   using C_ = Cfg<N>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const Smem<N> S(smem_raw);
-  block_setup<N>(S, b_g, fmask_g);
+  const Smem<C_> S(smem_raw);
+  block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
     if (!rhs_tile<N, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status)) break;
-  block_teardown<N>(S, phase);
+  block_teardown<C_>(S, phase);
 }
 
 // A batch of cases: persistent over a work list of (case, first element) tiles; the stage's
@@ -400,16 +396,210 @@ __global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_batched(const
                                                               const int32_t* __restrict__ fmask_g, const int stage,
                                                               const double a, const double b,
                                                               unsigned* __restrict__ status) {
+  using C_ = Cfg<N>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const Smem<N> S(smem_raw);
-  block_setup<N>(S, b_g, fmask_g);
+  const Smem<C_> S(smem_raw);
+  block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
     if (!rhs_tile<N, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status)) break;
   }
-  block_teardown<N>(S, phase);
+  block_teardown<C_>(S, phase);
+}
+
+// ==== BR1 pass on the tensor cores ===============================================================
+// For affine tetrahedra the outward normal times Fscale of face f is a fixed combination of the
+// rows of dr/dx (Nanson's relation): n_f Fscale_f = sum_a c_{f,a} grad r_a with c = (0,0,-1),
+// (0,-1,0), (1,1,1), (-1,0,0) for faces 0..3.  The lifted central-flux jump of BR1 therefore
+// folds into element-independent operators:
+//   grad_d w = sum_a (dr_a/dx_d) ( D_a w + Lhat_a jump ),  Lhat_a = 1/2 sum_f c_{f,a} LIFT_f,
+// with jump = w+ - w- at the face nodes.  One contraction of [w | jump] (rows (element, field))
+// against [D_a | Lhat_a] for a = r, s, t (N = 3 NPAD output columns) gives the three reference
+// derivatives; the geometric factors and the stress follow per node.
+template <int N>
+struct VCfg {
+  using O = kern::Ord<N>;
+  static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
+  static constexpr int E = 25, ROWS = 128;
+  static constexpr int KV = round16(Np), NPAD = KV, NOUT = 3 * NPAD;
+  static constexpr int NSURF = (NF + KV - 1) / KV, NCHUNK = 1 + NSURF, KB = NCHUNK * KV;
+  static constexpr int A_LBO = 144, A_SBO = (KV / 8) * A_LBO, A_TERM = 16 * A_SBO;
+  static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NOUT / 8) * B_SBO;
+  static constexpr int CS = NPAD + 1;  // one reference direction's columns are copied at a time
+  static constexpr int TMEM_COLS = NOUT <= 64 ? 64 : (NOUT <= 128 ? 128 : 256);
+  static constexpr int NT = N == 1 ? 128 : (N == 4 ? 448 : 256);
+  static constexpr int MINB = N == 4 ? 1 : 2;
+  static constexpr int NODES = E * Np, NPT = (NODES + NT - 1) / NT;
+  static constexpr uint32_t IDESC = idesc_bf16(ROWS, NOUT);
+  static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
+  static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
+  static constexpr int SMEM = OFF_BAR + 16;
+  static_assert(NOUT <= 256 && NOUT % 16 == 0, "MMA N");
+  static_assert(ROWS * CS * 4 <= 3 * A_TERM && ROWS * CS % 4 == 0, "accumulator copy in the operand slot");
+  static_assert(NOUT <= TMEM_COLS, "TMEM columns");
+};
+
+// Elements [e0, e0 + 25) of case c: viscous flux fv[9][K][Np] from the state qin (rho in FP64),
+// the float state copy (momentum) and the FP64 temperature.
+template <int N>
+__device__ __forceinline__ bool vis_tile(const Smem<VCfg<N>>& S, const MixedCase& c, const double* __restrict__ qin,
+                                         const int e0, uint32_t& phase, unsigned* status) {
+  using C_ = VCfg<N>;
+  constexpr int Np = C_::Np, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
+  const int tid = threadIdx.x;
+  const int nel = min(C_::E, c.K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)c.K * Np;
+  const size_t base = (size_t)e0 * Np;
+  const float* __restrict__ qf_g = c.qf;
+  const double* __restrict__ T_g = c.T;
+
+  for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
+
+  // volume chunk: (rho - rho_1, m, T - T_1) per node, differences to the element's first node in FP64
+  float rho_n[NPT], m_n[NPT][3], w_n[NPT][5];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int n = tid + s * NT;
+    if (n < nn) {
+      const int e = n / Np;
+      const size_t gn = base + n, g1 = base + (size_t)e * Np;
+      const double rho = qin[gn];
+      rho_n[s] = (float)rho;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) m_n[s][d] = qf_g[(1 + d) * KNp + gn];
+      w_n[s][0] = (float)(rho - qin[g1]);
+      w_n[s][1] = m_n[s][0];
+      w_n[s][2] = m_n[s][1];
+      w_n[s][3] = m_n[s][2];
+      w_n[s][4] = (float)(T_g[gn] - T_g[g1]);
+    }
+  }
+  __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int n = tid + s * NT;
+    if (n < nn) {
+      const int e = n / Np, i = n - e * Np;
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, i, C_::A_LBO, C_::A_SBO), w_n[s][f]);
+    }
+  }
+  if (!run_chunk<C_>(S, 0, phase, status)) return false;
+
+  // surface chunks: jumps w+ - w- at face nodes [sc KV, sc KV + KV)
+#pragma unroll 1
+  for (int sc = 0; sc < C_::NSURF; ++sc) {
+    const int m0 = sc * KV, w = min(KV, NF - m0);
+    for (int j = tid; j < nel * w; j += NT) {
+      const int e = j / w, mm = m0 + (j - e * w);
+      const size_t own = base + (size_t)e * Np + S.fm[mm];
+      const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
+      float jv[5];
+      jv[0] = (float)(qin[P] - qin[own]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) jv[1 + d] = qf_g[(1 + d) * KNp + P] - qf_g[(1 + d) * KNp + own];
+      jv[4] = (float)(T_g[P] - T_g[own]);
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, mm - m0, C_::A_LBO, C_::A_SBO), jv[f]);
+    }
+    if (!run_chunk<C_>(S, 1 + sc, phase, status)) return false;
+  }
+
+  // reference derivatives -> gradients, one reference direction at a time through shared memory
+  float grad[NPT][3][5];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int f = 0; f < 5; ++f) grad[s][d][f] = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {
+    if (tid < 128) {
+      const int warp = tid >> 5;
+      float* Crow = S.C + tid * C_::CS;
+#pragma unroll
+      for (int c0 = 0; c0 < C_::NPAD; c0 += 16) {
+        float r[16];
+        tmem_ld16(*S.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * C_::NPAD + c0), r);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) Crow[c0 + jj] = r[jj];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int n = tid + s * NT;
+      if (n < nn) {
+        const int e = n / Np, i = n - e * Np;
+        const float* G = S.geo + e * GS + 3 * a;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          const float cv = S.C[(e * 5 + f) * C_::CS + i];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) grad[s][d][f] = fmaf(G[d], cv, grad[s][d][f]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const float mu = (float)c.gas.mu, kap = (float)c.gas.kappa;
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int n = tid + s * NT;
+    if (n < nn) {
+      float f9[9];
+      mixk::viscous_flux_node(rho_n[s], m_n[s], grad[s], mu, kap, f9);
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) c.fv[cc * KNp + base + n] = f9[cc];
+    }
+  }
+  // clear the accumulator copy (see rhs_tile); the last barrier above ordered its reads
+  uint4* Cz = reinterpret_cast<uint4*>(S.C);
+  for (int i = tid; i < C_::ROWS * C_::CS / 4; i += NT) Cz[i] = make_uint4(0u, 0u, 0u, 0u);
+  return true;
+}
+
+template <int N>
+__global__ void __launch_bounds__(VCfg<N>::NT, VCfg<N>::MINB) vis_tc_kernel(const MixedCase c,
+                                                                             const uint4* __restrict__ b_g,
+                                                                             const int32_t* __restrict__ fmask_g,
+                                                                             unsigned* __restrict__ status) {
+  using C_ = VCfg<N>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const Smem<C_> S(smem_raw);
+  block_setup<C_>(S, b_g, fmask_g);
+  uint32_t phase = 0;
+  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
+    if (!vis_tile<N>(S, c, c.q[0], e0, phase, status)) break;
+  block_teardown<C_>(S, phase);
+}
+
+template <int N>
+__global__ void __launch_bounds__(VCfg<N>::NT, VCfg<N>::MINB) vis_tc_batched(const MixedCase* __restrict__ cases,
+                                                                              const int2* __restrict__ work,
+                                                                              const int nwork,
+                                                                              const uint4* __restrict__ b_g,
+                                                                              const int32_t* __restrict__ fmask_g,
+                                                                              const int stage,
+                                                                              unsigned* __restrict__ status) {
+  using C_ = VCfg<N>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const Smem<C_> S(smem_raw);
+  block_setup<C_>(S, b_g, fmask_g);
+  uint32_t phase = 0;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 it = work[w];
+    const MixedCase& c = cases[it.x];
+    if (!vis_tile<N>(S, c, c.q[stage & 1], it.y, phase, status)) break;
+  }
+  block_teardown<C_>(S, phase);
 }
 
 }  // namespace tc

@@ -50,16 +50,17 @@ cudaError_t rhs_batched_t(const Group& g, const MixedCase* cases, const MixedOps
   return cudaGetLastError();
 }
 
-template <int N, int EPB>
+// BR1 pass of a group on the tensor cores (tcgen05), tiles of 25 elements.
+template <int N>
 cudaError_t vis_batched_t(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask, int stage,
-                          cudaStream_t s) {
-  using T = mixk::VT<N, EPB>;
-  const size_t smem = T::smem();
-  auto kern_fn = mixk::viscous_mixed_batched<N, EPB>;
-  cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                          unsigned* status, cudaStream_t s) {
+  using C = tc::VCfg<N>;
+  auto kern_fn = tc::vis_tc_batched<N>;
+  cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(kern_fn, T::NT, smem, g.nwork);
-  kern_fn<<<grid, T::NT, smem, s>>>(cases, g.work, g.nwork, mx.d, mx.l, fmask, stage);
+  const int grid = persistent_grid(kern_fn, C::NT, C::SMEM, g.nwork);
+  kern_fn<<<grid, C::NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_vis), fmask,
+                                       stage, status);
   return cudaGetLastError();
 }
 
@@ -69,9 +70,9 @@ const std::vector<int>& rhs_candidates(int) {
   static const std::vector<int> c{tc::Cfg<1>::E};
   return c;
 }
-const std::vector<int>& vis_candidates(int N) {
-  static const std::vector<int> c1{32, 16}, c2{16, 8}, c3{8, 16}, c4{8};
-  return N == 1 ? c1 : N == 2 ? c2 : N == 3 ? c3 : c4;
+const std::vector<int>& vis_candidates(int) {
+  static const std::vector<int> c{tc::VCfg<1>::E};
+  return c;
 }
 
 cudaError_t launch_rhs_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
@@ -93,18 +94,14 @@ cudaError_t launch_rhs_group(const Group& g, const MixedCase* cases, const Mixed
 }
 
 cudaError_t launch_vis_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
-                             int stage, cudaStream_t s) {
-#define DG_VIS(NN, EE) \
-  if (g.N == NN && g.epb == EE) return vis_batched_t<NN, EE>(g, cases, mx, fmask, stage, s);
-  DG_VIS(1, 16)
-  DG_VIS(1, 32)
-  DG_VIS(2, 8)
-  DG_VIS(2, 16)
-  DG_VIS(3, 8)
-  DG_VIS(3, 16)
-  DG_VIS(4, 8)
-#undef DG_VIS
-  return cudaErrorInvalidValue;
+                             int stage, unsigned* status, cudaStream_t s) {
+  switch (g.N) {
+    case 1: return vis_batched_t<1>(g, cases, mx, fmask, stage, status, s);
+    case 2: return vis_batched_t<2>(g, cases, mx, fmask, stage, status, s);
+    case 3: return vis_batched_t<3>(g, cases, mx, fmask, stage, status, s);
+    case 4: return vis_batched_t<4>(g, cases, mx, fmask, stage, status, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -161,7 +158,7 @@ cudaError_t launch_stage(dg_batch_s* b, int stage, cudaStream_t s) {
   for (const dg::Group& g : b->vis)
     if (e == cudaSuccess) {
       const dg::MeshDev& m = mdev(b, g.N);
-      e = dg::launch_vis_group(g, b->dcases, m.mx, m.fmask, stage, s);
+      e = dg::launch_vis_group(g, b->dcases, m.mx, m.fmask, stage, b->status, s);
     }
   for (const dg::Group& g : b->rhs)
     if (e == cudaSuccess) {
@@ -304,7 +301,7 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
         e = build_work(g, b);
         const dg::MeshDev& m = mdev(b, g.N);
         const double ms =
-            time_launches([&] { return dg::launch_vis_group(g, b->dcases, m.mx, m.fmask, 0, b->cap); }, b->cap);
+            time_launches([&] { return dg::launch_vis_group(g, b->dcases, m.mx, m.fmask, 0, b->status, b->cap); }, b->cap);
         b->tune_vis_ms[g.N - 1][ci] = ms;
         if (ms < best) {
           best = ms;

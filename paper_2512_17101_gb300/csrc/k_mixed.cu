@@ -139,6 +139,7 @@ void free_mixed_ops(MeshDev& m) {
   cudaFree(m.mx.d);
   cudaFree(m.mx.l);
   cudaFree(m.mx.tc_rhs);
+  cudaFree(m.mx.tc_vis);
   m.mx = MixedOps();
 }
 

@@ -24,6 +24,23 @@ __global__ void umma_table_kernel(const double* __restrict__ M, int rows, int co
   }
 }
 
+// Device copy of the three-term UMMA image of a row-major double matrix.
+cudaError_t upload_table(const std::vector<double>& host, int rows, int cols, int sbo, int term_bytes,
+                         unsigned char** out) {
+  double* dM = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dM, sizeof(double) * host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dM, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)out, 3 * (size_t)term_bytes);
+  if (e == cudaSuccess) e = cudaMemset(*out, 0, 3 * (size_t)term_bytes);
+  if (e == cudaSuccess) {
+    umma_table_kernel<<<64, 256>>>(dM, rows, cols, sbo, term_bytes, *out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dM);
+  return e;
+}
+
 template <int N>
 cudaError_t build_t(MeshDev& m, const RefOps& o) {
   using C = tc::Cfg<N>;
@@ -35,18 +52,20 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
       for (int j = 0; j < Np; ++j) R[(size_t)i * C::KB + a * KV + j] = -(*D[a])[i * Np + j];
     for (int mm = 0; mm < NF; ++mm) R[(size_t)i * C::KB + 3 * KV + mm] = o.LIFT[i * NF + mm];
   }
-  double* dM = nullptr;
-  cudaError_t e = cudaMalloc((void**)&dM, sizeof(double) * R.size());
-  if (e == cudaSuccess) e = cudaMemcpy(dM, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&m.mx.tc_rhs, 3 * (size_t)C::B_TERM);
-  if (e == cudaSuccess) e = cudaMemset(m.mx.tc_rhs, 0, 3 * (size_t)C::B_TERM);
-  if (e == cudaSuccess) {
-    umma_table_kernel<<<64, 256>>>(dM, C::NPAD, C::KB, C::B_SBO, C::B_TERM, m.mx.tc_rhs);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(dM);
-  return e;
+  cudaError_t e = upload_table(R, C::NPAD, C::KB, C::B_SBO, C::B_TERM, &m.mx.tc_rhs);
+  if (e != cudaSuccess) return e;
+  // BR1: rows (a, i) = [D_a[i][:] | 1/2 sum_f c_{f,a} LIFT[i][face f block]], c the reference
+  // outward normals of faces t = -1, s = -1, r + s + t = -1, r = -1 (Nanson's relation)
+  using V = tc::VCfg<N>;
+  constexpr double cfa[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1}, {-1, 0, 0}};
+  std::vector<double> Rv((size_t)V::NOUT * V::KB, 0.0);
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < Np; ++i) {
+      double* row = &Rv[(size_t)(a * V::NPAD + i) * V::KB];
+      for (int j = 0; j < Np; ++j) row[j] = (*D[a])[i * Np + j];
+      for (int mm = 0; mm < NF; ++mm) row[V::KV + mm] = 0.5 * cfa[mm / C::Nfp][a] * o.LIFT[i * NF + mm];
+    }
+  return upload_table(Rv, V::NOUT, V::KB, V::B_SBO, V::B_TERM, &m.mx.tc_vis);
 }
 
 template <int N, int PHYS, bool RK>
@@ -81,7 +100,34 @@ cudaError_t dispatch(const MeshDev& m, const mixk::MixedCase& c, bool rk, double
   }
 }
 
+template <int N>
+cudaError_t launch_vis_t(const MeshDev& m, const mixk::MixedCase& c, cudaStream_t s) {
+  using C = tc::VCfg<N>;
+  auto kern_fn = tc::vis_tc_kernel<N>;
+  static int grid_cap = 0;
+  if (!grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM) * device_sms();
+  }
+  const int tiles = (m.K + C::E - 1) / C::E;
+  kern_fn<<<std::min(tiles, grid_cap), C::NT, C::SMEM, s>>>(c, reinterpret_cast<const uint4*>(m.mx.tc_vis), m.fmask,
+                                                              m.status);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
+  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
+  switch (m.N) {
+    case 1: return launch_vis_t<1>(m, c, s);
+    case 2: return launch_vis_t<2>(m, c, s);
+    case 3: return launch_vis_t<3>(m, c, s);
+    case 4: return launch_vis_t<4>(m, c, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops) {
   switch (m.N) {
