@@ -237,7 +237,6 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 9 * (size_t)d.K * Np);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
-  if (e == cudaSuccess) e = dg::build_mixed_ops(d, m->ops);
   if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);
   if (e != cudaSuccess) {
     free_mesh_device(d);

@@ -44,13 +44,10 @@ struct GasParams {  // passed to kernels by value
   int newton_max_it;
 };
 
-// Split-BF16 operator tables of the mixed-precision path (built at upload).  Each
-// is [3][rows][words] (terms hi, mid, lo; x = hi + mid + lo, each bf16), a 32-bit
-// word holding two consecutive k.
+// Split-BF16 operator tables of the mixed-precision path (built at upload): three terms
+// (x = hi + mid + lo, each bf16), each the image of the operator in the UMMA K-major
+// shared-memory layout that the tcgen05 kernels copy in as is.
 struct MixedOps {
-  uint32_t* rhs = nullptr;  // rows i < NPAD: [-Dr_i | -Ds_i | -Dt_i | LIFT_i], KR columns
-  uint32_t* d = nullptr;    // rows (a, i) < 3Np pad 8: D_a[i][:], KW columns
-  uint32_t* l = nullptr;    // rows (face, i), 4 x NPAD: LIFT[i][face block], KF columns
   unsigned char* tc_rhs = nullptr;  // tcgen05 operator table: 3 BF16 terms of [-Dr | -Ds | -Dt | LIFT]
                                     // in the UMMA K-major layout (chunks of round16(Np) columns)
   unsigned char* tc_vis = nullptr;  // tcgen05 BR1 table: rows (a, i), [D_a | 1/2 sum_f c_fa LIFT_f]
@@ -79,13 +76,9 @@ extern const double kRK4B[5];
 // the node temperatures of a mixture.
 cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                        const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
-// Mixed-precision path (k_mixed.cu): split operator tables, and the tensor-core
-// right-hand side / RK stage with its BR1 pass.
-cudaError_t build_mixed_ops(MeshDev& m, const RefOps& ops);
+// Mixed-precision path: primitives pass (k_mixed.cu); operator tables, tensor-core right-hand
+// side / RK stage and its BR1 pass (k_tc.cu).
 void free_mixed_ops(MeshDev& m);
-cudaError_t launch_rhs_mixed(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
-                             double a, double b, double dt, cudaStream_t s);
-cudaError_t launch_viscous_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,

@@ -243,7 +243,7 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
     c.K = m.K;
     c.Np = m.Np;
     c.dt = in[i].dt;
-    c.gas = dg::mixk::MixedGas{gp.gamma, gp.R, gp.mu, gp.kappa};
+    c.gas = dg::mixk::MixedGas{gp.gamma, gp.R, gp.mu, gp.kappa, 1.0 / gp.R};
     b->cases.push_back(c);
     b->meshes.push_back(in[i].mesh);
   }
