@@ -35,15 +35,21 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (the pool's recipe table); an
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture, keyed by the
-# sha256 of the kernel source they were taken on; a changed kernel reports null traffic.
+# sha256 of the kernel sources they were taken on; a changed kernel reports null traffic.
+FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
+MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     ("7ae1f260473cc60c", "rhs"): 290.224896e6 + 105.554176e6,  # profiles/ns_N3_K82944_fp64.md
+    # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
+    ("e72d02e6201aa1be", "mixed_rhs"): 202.015232e6 + 114.677248e6,
+    ("e72d02e6201aa1be", "mixed_viscous"): 70.391808e6 + 19.945728e6,
+    ("e72d02e6201aa1be", "mixed_prims"): 66.373888e6 + 16.406272e6,
 }
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=FP64_SOURCES):
     h = hashlib.sha256()
-    for f in ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2512_17101_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -252,22 +258,29 @@ def workload_config(cfg):
 
 # ---- GPU arm -------------------------------------------------------------------------------------
 
+def mixed_prims_bytes_per_element(Np, viscous):
+    """q in (FP64); float state copy, FP64 pressure (and temperature) out."""
+    return Np * (40 + 20 + 8 + (8 if viscous else 0))
+
+
 def mixed_rhs_bytes_per_element(Np, NF, viscous):
-    b = Np * 8 * 20 + 26 * 8 + 4 * NF       # q in; k in/out; q_out; geometry; neighbour map
+    """float state copy + FP64 pressure in; q in, k in/out, q_out (FP64); fp32 geometry; neighbour map."""
+    b = Np * (20 + 8 + 4 * 40) + 26 * 4 + 4 * NF
     if viscous:
         b += Np * 4 * 9                      # fp32 viscous flux in
     return b
 
 
 def mixed_viscous_bytes_per_element(Np, NF):
-    return Np * (8 * 5 + 4 * 9) + 26 * 8 + 4 * NF
+    """rho, T (FP64) and momentum (fp32) in; fp32 viscous flux out; fp32 geometry; neighbour map."""
+    return Np * (8 + 8 + 12 + 36) + 26 * 4 + 4 * NF
 
 
 def mixed_tensor_flops_per_element(Np, NF, viscous):
-    """Tensor-core flops of the split products (3 products per contraction)."""
-    f = 3 * 2 * 5 * Np * (3 * Np + NF)                        # [-D | LIFT] contraction
+    """Tensor-core flops of the split-BF16 products (6 products per contraction, real rows and columns)."""
+    f = 6 * 2 * 5 * Np * (3 * Np + NF)                        # [-D_r -D_s -D_t | LIFT] contraction
     if viscous:
-        f += 3 * 2 * (5 * 3 * Np * Np + 15 * Np * NF)         # BR1 volume + surface contractions
+        f += 6 * 2 * 5 * 3 * Np * (Np + NF)                   # BR1: [D_a | Lhat_a], a = r, s, t
     return f
 
 
@@ -345,7 +358,8 @@ def gpu_arm(args, cfg, world, rank, local):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    src = kernel_source_hash()
+    src = kernel_source_hash(FP64_SOURCES)
+    src_mixed = kernel_source_hash(MIXED_SOURCES)
 
     def roofline(form, per):
         dom = max(per, key=lambda k: per[k]["avg_ms"] * per[k]["launches"])
@@ -364,11 +378,18 @@ def gpu_arm(args, cfg, world, rank, local):
                     "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
                     "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak, "kernels": per,
                     "peak_note": "FP64 nominal 1.25 TFLOP/s (pool recipe table); HBM: measured copy"}
-        nbytes = (mixed_rhs_bytes_per_element(Np, NF, viscous) if dom == "rhs"
-                  else mixed_viscous_bytes_per_element(Np, NF)) * cfg.K
+        per_el = {"rhs": mixed_rhs_bytes_per_element(Np, NF, viscous),
+                  "viscous": mixed_viscous_bytes_per_element(Np, NF),
+                  "prims": mixed_prims_bytes_per_element(Np, viscous)}
+        for name, v in per.items():
+            if name in per_el:
+                v["algorithmic_bytes"] = per_el[name] * cfg.K
+                v["hbm_frac"] = per_el[name] * cfg.K / (v["avg_ms"] * 1e-3) / 1e9 / hbm_peak
+        nbytes = per_el[dom] * cfg.K
         ach = nbytes / avg_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": TRAFFIC.get((src, "mixed_" + dom)), "kernel": dom, "algorithmic_bytes_per_launch": nbytes,
+                "traffic": TRAFFIC.get((src_mixed, "mixed_" + dom)), "kernel": dom,
+                "algorithmic_bytes_per_launch": nbytes,
                 "tensor_flops_per_step": mixed_tensor_flops_per_element(Np, NF, viscous) * cfg.K * 5,
                 "kernels": per, "peak_note": "HBM: measured copy (MEASURED_PEAKS.json)"}
 
@@ -434,7 +455,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched,
-            "kernel_src": src, "impl": "gpu",
+            "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
