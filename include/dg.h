@@ -330,9 +330,10 @@ int dg_batch_create(const dg_batch_case* cases, int32_t ncases, int32_t flags, d
 /* Advances every case by `steps` RK4 steps: `steps` graph launches on `stream`. */
 int dg_batch_step(dg_batch batch, int32_t steps, void* stream);
 
-/* Chosen tiles: rhs_tiles_host [4][2] (order, physics 0 = Euler / 1 = NS; 0 where the
- * batch has no such group), viscous_tiles_host [4]; rhs_tune_ms_host [4][2][4] the
- * timings of the candidates (any pointer may be NULL). */
+/* Chosen block sizes (threads per 25-element tensor-core tile): rhs_tiles_host [4][2]
+ * (order, physics 0 = Euler / 1 = NS; 0 where the batch has no such group),
+ * viscous_tiles_host [4]; rhs_tune_ms_host [4][2][4] the timings of the candidates (any
+ * pointer may be NULL). */
 int dg_batch_tiles(dg_batch batch, int32_t* rhs_tiles_host, int32_t* viscous_tiles_host, double* rhs_tune_ms_host);
 
 int dg_batch_status(dg_batch batch, uint32_t* bits, int reset);

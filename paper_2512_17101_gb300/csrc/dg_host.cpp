@@ -480,7 +480,7 @@ int device_sms() {
   return n > 0 ? n : 1;
 }
 
-int resident_blocks(const void* fn, int threads, size_t dyn_smem) {
+int resident_blocks(const void* fn, int threads, size_t dyn_smem, int tmem_cols) {
   cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
@@ -500,6 +500,7 @@ int resident_blocks(const void* fn, int threads, size_t dyn_smem) {
   if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
   n = std::min(n, smem_sm / (int)(dyn_smem + fa.sharedSizeBytes + (size_t)reserved));
   n = std::min(n, thr_sm / (warps * 32));
+  if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
   return std::max(n, 1);
 }
 

@@ -94,10 +94,11 @@ cudaError_t launch_mixture_energy(const GasParams& g, int64_t n, const double* T
 
 // SMs of the current device.
 int device_sms();
-// Blocks of kernel fn (threads per block, dynamic shared memory) resident on one SM at once, from
-// its registers, shared memory and threads against the SM's limits; sets the kernel's shared
-// memory carveout to the maximum.  A persistent kernel's grid is this times device_sms().
-int resident_blocks(const void* fn, int threads, size_t dyn_smem);
+// Blocks of kernel fn (threads per block, dynamic shared memory, TMEM columns allocated per
+// block) resident on one SM at once, from its registers, shared memory, threads and tensor
+// memory (512 columns per SM) against the SM's limits; sets the kernel's shared memory
+// carveout to the maximum.  A persistent kernel's grid is this times device_sms().
+int resident_blocks(const void* fn, int threads, size_t dyn_smem, int tmem_cols = 0);
 
 }  // namespace dg
 

@@ -98,9 +98,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
 // ---- tile configuration --------------------------------------------------------------------
 constexpr int round16(int x) { return (x + 15) / 16 * 16; }
 
-template <int N>
+// Single-case threads per tile (the batched form's autotuner picks among two compiled
+// candidates per order; these are its choices on the benchmark workloads).
+__host__ __device__ constexpr int default_nt(int N) { return N == 1 ? 128 : (N == 4 ? 448 : 256); }
+__host__ __device__ constexpr int default_vis_nt(int N) { return N == 1 ? 128 : (N == 2 ? 128 : (N == 3 ? 512 : 896)); }
+
+// Blocks per SM that the compiler's register budget aims at: the shared-memory limit, the
+// thread limit, and no fewer than 64 registers per thread.
+__host__ __device__ constexpr int aim_blocks(int smem, int nt) {
+  const int by_smem = (228 * 1024) / (smem + 1024), by_thr = 2048 / nt, by_reg = 65536 / (nt * 64);
+  const int m = by_smem < by_thr ? by_smem : by_thr;
+  const int r = m < by_reg ? m : by_reg;
+  return r < 1 ? 1 : r;
+}
+
+template <int N, int NT_ = default_nt(N)>
 struct Cfg {
   using O = kern::Ord<N>;
+  static constexpr int ORDER = N;
   static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
   static constexpr int E = 25, ROWS = 128;
   static constexpr int KV = round16(Np), NPAD = KV;
@@ -112,18 +127,19 @@ struct Cfg {
   static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NPAD / 8) * B_SBO;
   static constexpr int CS = NPAD + 1;  // row stride (floats) of the accumulator copy
   static constexpr int TMEM_COLS = NPAD <= 32 ? 32 : 64;
-  static constexpr int NT = N == 1 ? 128 : (N == 2 ? 256 : (N == 3 ? 256 : 448));
-  static constexpr int MINB = N == 4 ? 2 : (N == 3 ? 3 : 4);  // resident blocks per SM aimed at
+  static constexpr int NT = NT_;
   static constexpr int NODES = E * Np, NPT = (NODES + NT - 1) / NT;
   static constexpr uint32_t IDESC = idesc_bf16(ROWS, NPAD);
   // shared-memory layout (bytes)
   static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
   static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
   static constexpr int SMEM = OFF_BAR + 16;
+  static constexpr int MINB = aim_blocks(SMEM, NT);
   static_assert(ROWS * CS * 4 <= 3 * A_TERM, "the accumulator copy must fit in the operand slot");
   static_assert(ROWS * CS % 4 == 0, "the accumulator copy is cleared in 16 B words");
   static_assert(NPAD <= TMEM_COLS, "TMEM columns");
   static_assert(OFF_A % 16 == 0 && A_TERM % 16 == 0 && B_TERM % 16 == 0, "UMMA operands need 16 B alignment");
+  static_assert(NT % 32 == 0 && NT >= 128 && NT <= 1024, "whole warps, at least the four TMEM lane quarters");
 };
 
 // Byte offset of (row, k) in a K-major no-swizzle operand.
@@ -240,11 +256,10 @@ __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& ph
 
 // Elements [e0, e0 + 25) of case c: right-hand side (RK = false: out = rhs) or the LSRK stage
 // (k <- a k + dt rhs, out <- qin + b k).  Returns false when the block must stop (timeout).
-template <int N, int PHYS, bool RK>
-__device__ __forceinline__ bool rhs_tile(const Smem<Cfg<N>>& S, const MixedCase& c, const double* __restrict__ qin,
+template <class C_, int PHYS, bool RK>
+__device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
                                          uint32_t& phase, unsigned* status) {
-  using C_ = Cfg<N>;
   constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
   constexpr bool NS = PHYS == kern::NAVIER_STOKES;
   const int tid = threadIdx.x;
@@ -373,30 +388,30 @@ __device__ __forceinline__ bool rhs_tile(const Smem<Cfg<N>>& S, const MixedCase&
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-template <int N, int PHYS, bool RK>
-__global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_kernel(const MixedCase c, const uint4* __restrict__ b_g,
+template <int N, int NT, int PHYS, bool RK>
+__global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_kernel(const MixedCase c, const uint4* __restrict__ b_g,
                                                              const int32_t* __restrict__ fmask_g, const double a,
                                                              const double b, unsigned* __restrict__ status) {
-  using C_ = Cfg<N>;
+  using C_ = Cfg<N, NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
-    if (!rhs_tile<N, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status)) break;
+    if (!rhs_tile<C_, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status)) break;
   block_teardown<C_>(S, phase);
 }
 
 // A batch of cases: persistent over a work list of (case, first element) tiles; the stage's
 // parity picks input and output among each case's two state buffers.
-template <int N, int PHYS>
-__global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_batched(const MixedCase* __restrict__ cases,
+template <int N, int NT, int PHYS>
+__global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const MixedCase* __restrict__ cases,
                                                               const int2* __restrict__ work, const int nwork,
                                                               const uint4* __restrict__ b_g,
                                                               const int32_t* __restrict__ fmask_g, const int stage,
                                                               const double a, const double b,
                                                               unsigned* __restrict__ status) {
-  using C_ = Cfg<N>;
+  using C_ = Cfg<N, NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
@@ -404,7 +419,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_batched(const
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
-    if (!rhs_tile<N, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status)) break;
+    if (!rhs_tile<C_, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status)) break;
   }
   block_teardown<C_>(S, phase);
 }
@@ -418,9 +433,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, Cfg<N>::MINB) rhs_tc_batched(const
 // with jump = w+ - w- at the face nodes.  One contraction of [w | jump] (rows (element, field))
 // against [D_a | Lhat_a] for a = r, s, t (N = 3 NPAD output columns) gives the three reference
 // derivatives; the geometric factors and the stress follow per node.
-template <int N>
+template <int N, int NT_ = default_vis_nt(N)>
 struct VCfg {
   using O = kern::Ord<N>;
+  static constexpr int ORDER = N;
   static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
   static constexpr int E = 25, ROWS = 128;
   static constexpr int KV = round16(Np), NPAD = KV, NOUT = 3 * NPAD;
@@ -429,13 +445,14 @@ struct VCfg {
   static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NOUT / 8) * B_SBO;
   static constexpr int CS = NPAD + 1;  // one reference direction's columns are copied at a time
   static constexpr int TMEM_COLS = NOUT <= 64 ? 64 : (NOUT <= 128 ? 128 : 256);
-  static constexpr int NT = N == 1 ? 128 : (N == 4 ? 448 : 256);
-  static constexpr int MINB = N == 4 ? 1 : 2;
+  static constexpr int NT = NT_;
   static constexpr int NODES = E * Np, NPT = (NODES + NT - 1) / NT;
   static constexpr uint32_t IDESC = idesc_bf16(ROWS, NOUT);
   static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
   static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
   static constexpr int SMEM = OFF_BAR + 16;
+  static constexpr int MINB = aim_blocks(SMEM, NT);
+  static_assert(NT % 32 == 0 && NT >= 128 && NT <= 1024, "whole warps, at least the four TMEM lane quarters");
   static_assert(NOUT <= 256 && NOUT % 16 == 0, "MMA N");
   static_assert(ROWS * CS * 4 <= 3 * A_TERM && ROWS * CS % 4 == 0, "accumulator copy in the operand slot");
   static_assert(NOUT <= TMEM_COLS, "TMEM columns");
@@ -443,10 +460,9 @@ struct VCfg {
 
 // Elements [e0, e0 + 25) of case c: viscous flux fv[9][K][Np] from the state qin (rho in FP64),
 // the float state copy (momentum) and the FP64 temperature.
-template <int N>
-__device__ __forceinline__ bool vis_tile(const Smem<VCfg<N>>& S, const MixedCase& c, const double* __restrict__ qin,
+template <class C_>
+__device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          const int e0, uint32_t& phase, unsigned* status) {
-  using C_ = VCfg<N>;
   constexpr int Np = C_::Np, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
   const int tid = threadIdx.x;
   const int nel = min(C_::E, c.K - e0);
@@ -566,30 +582,30 @@ __device__ __forceinline__ bool vis_tile(const Smem<VCfg<N>>& S, const MixedCase
   return true;
 }
 
-template <int N>
-__global__ void __launch_bounds__(VCfg<N>::NT, VCfg<N>::MINB) vis_tc_kernel(const MixedCase c,
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_kernel(const MixedCase c,
                                                                              const uint4* __restrict__ b_g,
                                                                              const int32_t* __restrict__ fmask_g,
                                                                              unsigned* __restrict__ status) {
-  using C_ = VCfg<N>;
+  using C_ = VCfg<N, NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
-    if (!vis_tile<N>(S, c, c.q[0], e0, phase, status)) break;
+    if (!vis_tile<C_>(S, c, c.q[0], e0, phase, status)) break;
   block_teardown<C_>(S, phase);
 }
 
-template <int N>
-__global__ void __launch_bounds__(VCfg<N>::NT, VCfg<N>::MINB) vis_tc_batched(const MixedCase* __restrict__ cases,
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_batched(const MixedCase* __restrict__ cases,
                                                                               const int2* __restrict__ work,
                                                                               const int nwork,
                                                                               const uint4* __restrict__ b_g,
                                                                               const int32_t* __restrict__ fmask_g,
                                                                               const int stage,
                                                                               unsigned* __restrict__ status) {
-  using C_ = VCfg<N>;
+  using C_ = VCfg<N, NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
@@ -597,7 +613,7 @@ __global__ void __launch_bounds__(VCfg<N>::NT, VCfg<N>::MINB) vis_tc_batched(con
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
-    if (!vis_tile<N>(S, c, c.q[stage & 1], it.y, phase, status)) break;
+    if (!vis_tile<C_>(S, c, c.q[stage & 1], it.y, phase, status)) break;
   }
   block_teardown<C_>(S, phase);
 }

@@ -2,11 +2,12 @@
 // one CUDA-graph launch per RK4 step.
 //
 // The cases are grouped by (order, physics).  Each group's kernels are persistent
-// over a device work list of (case, first element) tiles, so one launch per group and
-// pass serves all its cases; a step is 5 stages x (primitives pass, BR1 pass per
-// viscous group, right-hand side per group) plus a copy of each case's result back
-// into its state buffer, captured once into a graph.  The tile size of each group
-// (elements per block) is chosen at creation by timing the compiled candidates on the
+// over a device work list of (case, first element) tiles of 25 elements (the 128 rows of
+// one tensor-core tile), so one launch per group and pass serves all its cases; a step is
+// 5 stages x (primitives pass, BR1 pass per viscous group, right-hand side per group) plus
+// a copy of each case's result back into its state buffer, captured once into a graph.
+// The block size of each group's kernels (threads per tile, i.e. nodes per thread against
+// resident blocks per SM) is chosen at creation by timing the compiled candidates on the
 // batch's own cases (the autotuner).  The paper's nearest counterpart is its
 // concatenation of outlined calls into fewer, larger kernels (Sec. 4.2.4) and the
 // launch-overhead floor it reports (Sec. 5.2).
@@ -24,7 +25,7 @@ namespace {
 using mixk::MixedCase;
 
 struct Group {
-  int N = 0, phys = 0, epb = 0;
+  int N = 0, phys = 0, epb = 0, nt = 0;  // elements per work item (25), threads per block
   int2* work = nullptr;
   int nwork = 0;
   std::vector<int> cases;
@@ -32,76 +33,80 @@ struct Group {
 
 // Persistent grid of a kernel: resident blocks per SM x SMs, at most one block per work item.
 template <typename K>
-int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
-  return std::max(1, std::min(nwork, resident_blocks((const void*)kernel, threads, smem) * device_sms()));
+int persistent_grid(K kernel, int threads, size_t smem, int tmem_cols, int nwork) {
+  return std::max(1, std::min(nwork, resident_blocks((const void*)kernel, threads, smem, tmem_cols) * device_sms()));
 }
 
-// Right-hand side + RK stage of a group on the tensor cores (tcgen05), tiles of 25 elements.
-template <int N, int PHYS>
+// Right-hand side + RK stage of a group on the tensor cores (tcgen05), tiles of 25 elements,
+// NT threads per block.
+template <int N, int NT, int PHYS>
 cudaError_t rhs_batched_t(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask, int stage,
                           double a, double b, unsigned* status, cudaStream_t s) {
-  using C = tc::Cfg<N>;
-  auto kern_fn = tc::rhs_tc_batched<N, PHYS>;
+  using C = tc::Cfg<N, NT>;
+  auto kern_fn = tc::rhs_tc_batched<N, NT, PHYS>;
   cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(kern_fn, C::NT, C::SMEM, g.nwork);
-  kern_fn<<<grid, C::NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_rhs), fmask,
-                                       stage, a, b, status);
+  const int grid = persistent_grid(kern_fn, NT, C::SMEM, C::TMEM_COLS, g.nwork);
+  kern_fn<<<grid, NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_rhs), fmask, stage,
+                                    a, b, status);
   return cudaGetLastError();
 }
 
-// BR1 pass of a group on the tensor cores (tcgen05), tiles of 25 elements.
-template <int N>
+// BR1 pass of a group on the tensor cores (tcgen05), tiles of 25 elements, NT threads per block.
+template <int N, int NT>
 cudaError_t vis_batched_t(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask, int stage,
                           unsigned* status, cudaStream_t s) {
-  using C = tc::VCfg<N>;
-  auto kern_fn = tc::vis_tc_batched<N>;
+  using C = tc::VCfg<N, NT>;
+  auto kern_fn = tc::vis_tc_batched<N, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(kern_fn, C::NT, C::SMEM, g.nwork);
-  kern_fn<<<grid, C::NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_vis), fmask,
-                                       stage, status);
+  const int grid = persistent_grid(kern_fn, NT, C::SMEM, C::TMEM_COLS, g.nwork);
+  kern_fn<<<grid, NT, C::SMEM, s>>>(cases, g.work, g.nwork, reinterpret_cast<const uint4*>(mx.tc_vis), fmask, stage,
+                                    status);
   return cudaGetLastError();
 }
 
-// Candidate tiles (elements per block) per order; the first is the single-case default.  The
-// right-hand side runs in tensor-core tiles of 128 rows = 25 elements x 5 variables.
-const std::vector<int>& rhs_candidates(int) {
-  static const std::vector<int> c{tc::Cfg<1>::E};
-  return c;
-}
-const std::vector<int>& vis_candidates(int) {
-  static const std::vector<int> c{tc::VCfg<1>::E};
-  return c;
+// Compiled candidates (threads per 25-element tile) per order; the first is the single-case
+// default.  Fewer threads: more resident blocks, more nodes per thread; more threads: one
+// node (or face node) per thread and fewer blocks.  Both passes use the same lists.
+const std::vector<int>& nt_candidates(int N) {
+  static const std::vector<int> c1{128, 256}, c2{256, 128}, c3{256, 512}, c4{448, 896};
+  return N == 1 ? c1 : N == 2 ? c2 : N == 3 ? c3 : c4;
 }
 
 cudaError_t launch_rhs_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
                              int stage, double a, double b, unsigned* status, cudaStream_t s) {
   const bool ns = g.phys == kern::NAVIER_STOKES;
-  switch (g.N) {
-#define DG_RHS(NN)                                                                                 \
-  case NN:                                                                                         \
-    return ns ? rhs_batched_t<NN, kern::NAVIER_STOKES>(g, cases, mx, fmask, stage, a, b, status, s) \
-              : rhs_batched_t<NN, kern::EULER>(g, cases, mx, fmask, stage, a, b, status, s);
-    DG_RHS(1)
-    DG_RHS(2)
-    DG_RHS(3)
-    DG_RHS(4)
+#define DG_RHS(NN, TT)                                                                                \
+  if (g.N == NN && g.nt == TT)                                                                        \
+    return ns ? rhs_batched_t<NN, TT, kern::NAVIER_STOKES>(g, cases, mx, fmask, stage, a, b, status, s) \
+              : rhs_batched_t<NN, TT, kern::EULER>(g, cases, mx, fmask, stage, a, b, status, s);
+  DG_RHS(1, 128)
+  DG_RHS(1, 256)
+  DG_RHS(2, 256)
+  DG_RHS(2, 128)
+  DG_RHS(3, 256)
+  DG_RHS(3, 512)
+  DG_RHS(4, 448)
+  DG_RHS(4, 896)
 #undef DG_RHS
-    default:
-      return cudaErrorInvalidValue;
-  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_vis_group(const Group& g, const MixedCase* cases, const MixedOps& mx, const int32_t* fmask,
                              int stage, unsigned* status, cudaStream_t s) {
-  switch (g.N) {
-    case 1: return vis_batched_t<1>(g, cases, mx, fmask, stage, status, s);
-    case 2: return vis_batched_t<2>(g, cases, mx, fmask, stage, status, s);
-    case 3: return vis_batched_t<3>(g, cases, mx, fmask, stage, status, s);
-    case 4: return vis_batched_t<4>(g, cases, mx, fmask, stage, status, s);
-    default: return cudaErrorInvalidValue;
-  }
+#define DG_VIS(NN, TT) \
+  if (g.N == NN && g.nt == TT) return vis_batched_t<NN, TT>(g, cases, mx, fmask, stage, status, s);
+  DG_VIS(1, 128)
+  DG_VIS(1, 256)
+  DG_VIS(2, 256)
+  DG_VIS(2, 128)
+  DG_VIS(3, 256)
+  DG_VIS(3, 512)
+  DG_VIS(4, 448)
+  DG_VIS(4, 896)
+#undef DG_VIS
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -271,13 +276,15 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
       dg::Group& g = rg[{N, phys}];
       g.N = N;
       g.phys = phys;
-      g.epb = dg::rhs_candidates(N)[0];
+      g.epb = dg::tc::Cfg<1>::E;
+      g.nt = dg::nt_candidates(N)[0];
       g.cases.push_back(i);
       if (phys == dg::kern::NAVIER_STOKES) {
         dg::Group& v = vg[N];
         v.N = N;
         v.phys = phys;
-        v.epb = dg::vis_candidates(N)[0];
+        v.epb = dg::tc::VCfg<1>::E;
+        v.nt = dg::nt_candidates(N)[0];
         v.cases.push_back(i);
       }
     }
@@ -289,35 +296,33 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
       if (e == cudaSuccess) e = build_work(g, b);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  // autotune: time each group's candidate tiles on stage 0 (reads the cases' states, writes only work buffers)
+  // autotune: time each group's compiled block sizes on stage 0 (reads the cases' states, writes
+  // only work buffers) and keep the fastest
   if (e == cudaSuccess && (flags & DG_BATCH_AUTOTUNE)) {
     e = launch_stage(b, 0, b->cap);
     for (auto& g : b->vis) {
       double best = 1e300;
-      int best_epb = g.epb;
-      const auto& cand = dg::vis_candidates(g.N);
+      int best_nt = g.nt;
+      const auto& cand = dg::nt_candidates(g.N);
       for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
-        g.epb = cand[ci];
-        e = build_work(g, b);
+        g.nt = cand[ci];
         const dg::MeshDev& m = mdev(b, g.N);
         const double ms =
             time_launches([&] { return dg::launch_vis_group(g, b->dcases, m.mx, m.fmask, 0, b->status, b->cap); }, b->cap);
         b->tune_vis_ms[g.N - 1][ci] = ms;
         if (ms < best) {
           best = ms;
-          best_epb = cand[ci];
+          best_nt = cand[ci];
         }
       }
-      g.epb = best_epb;
-      if (e == cudaSuccess) e = build_work(g, b);
+      g.nt = best_nt;
     }
     for (auto& g : b->rhs) {
       double best = 1e300;
-      int best_epb = g.epb;
-      const auto& cand = dg::rhs_candidates(g.N);
+      int best_nt = g.nt;
+      const auto& cand = dg::nt_candidates(g.N);
       for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
-        g.epb = cand[ci];
-        e = build_work(g, b);
+        g.nt = cand[ci];
         const dg::MeshDev& m = mdev(b, g.N);
         const double ms = time_launches(
             [&] {
@@ -327,11 +332,10 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
         b->tune_ms[g.N - 1][g.phys == dg::kern::NAVIER_STOKES][ci] = ms;
         if (ms < best) {
           best = ms;
-          best_epb = cand[ci];
+          best_nt = cand[ci];
         }
       }
-      g.epb = best_epb;
-      if (e == cudaSuccess) e = build_work(g, b);
+      g.nt = best_nt;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
     if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(unsigned));
@@ -375,9 +379,9 @@ int dg_batch_tiles(dg_batch b, int32_t* rhs_tiles, int32_t* viscous_tiles, doubl
   if (viscous_tiles)
     for (int i = 0; i < 4; ++i) viscous_tiles[i] = 0;
   for (const auto& g : b->rhs)
-    if (rhs_tiles) rhs_tiles[(g.N - 1) * 2 + (g.phys == dg::kern::NAVIER_STOKES)] = g.epb;
+    if (rhs_tiles) rhs_tiles[(g.N - 1) * 2 + (g.phys == dg::kern::NAVIER_STOKES)] = g.nt;
   for (const auto& g : b->vis)
-    if (viscous_tiles) viscous_tiles[g.N - 1] = g.epb;
+    if (viscous_tiles) viscous_tiles[g.N - 1] = g.nt;
   if (rhs_tune_ms) std::memcpy(rhs_tune_ms, b->tune_ms, sizeof(b->tune_ms));
   return DG_OK;
 }

@@ -71,12 +71,12 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
 template <int N, int PHYS, bool RK>
 cudaError_t launch_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
   using C = tc::Cfg<N>;
-  auto kern_fn = tc::rhs_tc_kernel<N, PHYS, RK>;
+  auto kern_fn = tc::rhs_tc_kernel<N, C::NT, PHYS, RK>;
   static int grid_cap = 0;
   if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM) * device_sms();
+    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM, C::TMEM_COLS) * device_sms();
   }
   const int tiles = (m.K + C::E - 1) / C::E;
   kern_fn<<<std::min(tiles, grid_cap), C::NT, C::SMEM, s>>>(c, reinterpret_cast<const uint4*>(m.mx.tc_rhs),
@@ -103,12 +103,12 @@ cudaError_t dispatch(const MeshDev& m, const mixk::MixedCase& c, bool rk, double
 template <int N>
 cudaError_t launch_vis_t(const MeshDev& m, const mixk::MixedCase& c, cudaStream_t s) {
   using C = tc::VCfg<N>;
-  auto kern_fn = tc::vis_tc_kernel<N>;
+  auto kern_fn = tc::vis_tc_kernel<N, C::NT>;
   static int grid_cap = 0;
   if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM) * device_sms();
+    grid_cap = resident_blocks((const void*)kern_fn, C::NT, C::SMEM, C::TMEM_COLS) * device_sms();
   }
   const int tiles = (m.K + C::E - 1) / C::E;
   kern_fn<<<std::min(tiles, grid_cap), C::NT, C::SMEM, s>>>(c, reinterpret_cast<const uint4*>(m.mx.tc_vis), m.fmask,
