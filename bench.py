@@ -509,48 +509,76 @@ def learned_form(args, local):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
 
-    seeds = {"constant_1650K": dg._opts(t_seed=capi.DG_TSEED_CONST, t_const=1650.0),
-             "previous_stage_T": dg._opts(t_seed=capi.DG_TSEED_INPUT),
-             "mlp": dg._opts(t_seed=capi.DG_TSEED_MLP)}
-    out = {}
+    seed_modes = {"constant_1650K": (capi.DG_TSEED_CONST, 1650.0), "previous_stage_T": (capi.DG_TSEED_INPUT, 0.0),
+                  "mlp": (capi.DG_TSEED_MLP, 0.0)}
+    precisions = {"fp64": capi.DG_PREC_FP64, "mixed": capi.DG_PREC_MIXED}
+    out = {"fp64": {}, "mixed": {}}
     steps = max(2, min(args.steps, 5))
-    for name, opts in seeds.items():
-        q = q0.clone()
-        Tio = torch.full((K, Np), 1650.0, dtype=torch.float64, device=dev)
-        work = (torch.empty_like(q), torch.zeros_like(q))
-        for _ in range(2):
-            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, T_io=Tio, opts=opts, work=work)
-        q.copy_(q0)
-        torch.cuda.synchronize()
-        mesh.kernel_times(reset=True)
-        mesh.set_timing(True)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=steps, T_io=Tio, opts=opts, work=work)
-        b.record()
-        torch.cuda.synchronize()
-        mesh.set_timing(False)
-        kt = mesh.kernel_times(reset=True)
-        ms = a.elapsed_time(b) / steps
-        # Newton iterations of one solve on the final state from this seed
-        it = torch.zeros(n, dtype=torch.int32, device=dev)
-        Tt = Tio.reshape(n).clone() if name == "previous_stage_T" else torch.empty(n, dtype=torch.float64, device=dev)
-        dg.dg_temperature(gas, q.reshape(12, n), Tt, it, opts=opts)
-        out[name] = {"ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
-                     "temperature_ms_per_stage": kt["temperature"][0] / max(kt["temperature"][1], 1),
-                     "rhs_ms_per_stage": kt["rhs"][0] / max(kt["rhs"][1], 1),
-                     "newton_iterations_mean": float(it.double().mean().item()), "q": q}
-        if gas.status() != 0 or mesh.status() != 0:
-            raise SystemExit(f"status flags set in the learned-form run ({name})")
-    ref_q = out["constant_1650K"].pop("q")
-    for name in out:
-        if "q" in out[name]:
-            qq = out[name].pop("q")
-            out[name]["state_diff_vs_constant_seed"] = float(((qq - ref_q).abs().max() / ref_q.abs().max()).item())
+    for pname, prec in precisions.items():
+        for name, (mode, tc) in seed_modes.items():
+            opts = dg._opts(precision=prec, t_seed=mode, t_const=tc)
+            q = q0.clone()
+            Tio = torch.full((K, Np), 1650.0, dtype=torch.float64, device=dev)
+            work = (torch.empty_like(q), torch.zeros_like(q))
+            for _ in range(2):
+                dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, T_io=Tio, opts=opts, work=work)
+            q.copy_(q0)
+            Tio.fill_(1650.0)
+            torch.cuda.synchronize()
+            mesh.kernel_times(reset=True)
+            mesh.set_timing(True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=steps, T_io=Tio, opts=opts, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            mesh.set_timing(False)
+            kt = mesh.kernel_times(reset=True)
+            ms = a.elapsed_time(b) / steps
+            # Newton iterations of one solve on the final state from this seed
+            it = torch.zeros(n, dtype=torch.int32, device=dev)
+            Tt = Tio.reshape(n).clone() if name == "previous_stage_T" else torch.empty(n, dtype=torch.float64, device=dev)
+            dg.dg_temperature(gas, q.reshape(12, n), Tt, it, opts=dg._opts(t_seed=mode, t_const=tc))
+            # the state after the workload's own step count, for the error bar
+            q1 = q0.clone()
+            T1 = torch.full((K, Np), 1650.0, dtype=torch.float64, device=dev)
+            dg.lsrk4_step(mesh, gas, q1, cfg.dt, steps=cfg.steps, T_io=T1, opts=opts, work=work)
+            r = {"ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
+                 "newton_iterations_mean": float(it.double().mean().item()), "q": q, "q1": q1}
+            for kname in ("temperature", "prims", "rhs"):
+                if kt[kname][1]:
+                    r[kname + "_ms_per_stage"] = kt[kname][0] / kt[kname][1]
+            out[pname][name] = r
+            if gas.status() != 0 or mesh.status() != 0:
+                raise SystemExit(f"status flags set in the learned-form run ({pname}, {name})")
+    ref_q, ref_q1 = out["fp64"]["constant_1650K"]["q"], out["fp64"]["constant_1650K"]["q1"]
+
+    def field_err(a_, b_):
+        groups = [[0], [1, 2, 3], [4]] + [[v] for v in range(5, 12)]
+        return max(float((a_[g] - b_[g]).abs().max().item() / b_[g].abs().max().item()) for g in groups)
+
+    for pname in out:
+        for name in out[pname]:
+            out[pname][name][f"state_err_vs_fp64_after_{cfg.steps}_step"] = field_err(out[pname][name]["q1"], ref_q1)
+            out[pname][name][f"state_err_vs_fp64_after_{steps}_steps"] = field_err(out[pname][name]["q"], ref_q)
+    for pname in out:
+        for name in out[pname]:
+            out[pname][name].pop("q")
+            out[pname][name].pop("q1")
+    plain, combined = out["fp64"]["constant_1650K"], out["mixed"]["mlp"]
     return {"workload": f"{cfg.name}: {cfg.description}", "K": K, "N": cfg.N, "V": 12, "steps": steps,
             "training": {"samples": int(Ts.size), "epochs": 30, "seconds_incl_sampling": train_s,
                          "loss_first_last": [float(hist[0]), float(hist[-1])]},
-            "seeds": out}
+            "mixed_plus_learned": {"value": combined["value"], "unit": "DOF-updates/s",
+                                   "vs_plain_fp64_constant_seed": combined["value"] / plain["value"],
+                                   "state_err_per_field": combined[f"state_err_vs_fp64_after_{cfg.steps}_step"],
+                                   "state_err_per_field_after_timed_steps": combined[f"state_err_vs_fp64_after_{steps}_steps"],
+                                   "error_measure": f"max over fields (rho, momentum vector, rho E, each rho Y_k) of "
+                                                    f"max|q - q_fp64| / max|q_fp64| after the workload's {cfg.steps} RK4 "
+                                                    f"step(s) from the same state; the per-node random mass fractions "
+                                                    f"make the state move ~7 % per step, so the error grows ~linearly "
+                                                    f"with the steps taken"},
+            "seeds": out["fp64"], "mixed_precision_seeds": out["mixed"]}
 
 
 def batched_form(args, local):

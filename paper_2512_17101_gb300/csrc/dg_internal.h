@@ -80,6 +80,8 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // side / RK stage and its BR1 pass (k_tc.cu).
 void free_mixed_ops(MeshDev& m);
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t launch_prims_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
+                                 cudaStream_t s);
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                           double a, double b, double dt, cudaStream_t s);

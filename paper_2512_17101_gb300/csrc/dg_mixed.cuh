@@ -64,13 +64,27 @@ struct MixedCase {
   double* p;
   double* T;
   float* fv;
+  float* cs;  // sound speed per node (mixtures; a perfect gas computes it from p and rho)
   const float* geo;
   const int32_t* vmapP;
   int K;
   int Np;
+  int nvar;   // conserved variables: 5, or 5 + species for a mixture
   double dt;
   MixedGas gas;
 };
+
+// Per-node tables of the mixed form for a mixture (64 of the scratch's 72 bytes per node):
+// float state copy [MIX_V][KNp], float sound speed [KNp], FP64 pressure [KNp].
+constexpr int MIX_V = 5 + DG_MAX_SPECIES;
+__host__ __device__ inline void mixed_scratch_mixture(double* base, size_t KNp, float** qf, float** cs, double** p) {
+  float* f = reinterpret_cast<float*>(base);
+  *qf = f;
+  *cs = f + MIX_V * KNp;
+  *p = reinterpret_cast<double*>(f + (MIX_V + 1) * KNp);
+}
+static_assert((MIX_V + 1) % 2 == 0, "the FP64 pressure must start on an 8-byte boundary");
+static_assert((MIX_V + 1) * 4 + 8 <= 72, "the mixture tables must fit the 72-byte scratch");
 
 // ---- pass 0: per node, FP64 pressure (and temperature) and a float copy of the state,
 // so that the later kernels read traces without recomputing or converting them.
@@ -109,6 +123,37 @@ static __global__ void prims_batched(const MixedCase* __restrict__ cases, const 
       const size_t i = (size_t)it.y + j;
       if (i < KNp) prims_node(c, qin, KNp, i, status);
     }
+  }
+}
+
+// ---- mixture primitives: FP64 pressure p = rho R_mix T at the Newton temperature, the sound
+// speed c = sqrt(cp/(cp - R_mix) p/rho), and a float copy of the state.
+static __global__ void prims_mixture_kernel(const MixedCase c, const GasParams g, const double* __restrict__ qin,
+                                            const double* __restrict__ T, const size_t KNp,
+                                            unsigned* __restrict__ status) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < KNp; i += (size_t)gridDim.x * blockDim.x) {
+    double qv[MIX_V];
+#pragma unroll
+    for (int v = 0; v < MIX_V; ++v) qv[v] = v < c.nvar ? qin[v * KNp + i] : 0.0;
+    float ir32;
+    const double ir = recip64(qv[0], ir32);
+    double Y[DG_MAX_SPECIES];
+#pragma unroll
+    for (int k = 0; k < DG_MAX_SPECIES; ++k) Y[k] = qv[5 + k] * ir;
+    const double Ti = T[i];
+    double cp, Rmix;
+    kern::mixture_cp_R(g, Y, Ti, cp, Rmix);
+    const double p = qv[0] * Rmix * Ti;
+    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+#pragma unroll
+    for (int v = 0; v < MIX_V; ++v)
+      if (v < c.nvar) c.qf[v * KNp + i] = (float)qv[v];
+    c.p[i] = p;
+    // c^2 = cp/(cp - R_mix) p/rho formed in FP64 and rounded once: the sound speed sets the
+    // Lax-Friedrichs dissipation, the largest surface term on rough mixture states
+    float r32;
+    const double c2 = cp * p * ir * recip64(cp - Rmix, r32);
+    c.cs[i] = sqrtf((float)c2);
   }
 }
 
@@ -175,6 +220,48 @@ __device__ __forceinline__ void face_term(const float qm[5], const float qp[5], 
     for (int d = 0; d < 3; ++d) de = fmaf(n[d], fvm[6 + d] - fvp[6 + d], de);
     g[4] -= 0.5f * de;
   }
+}
+
+// Mixture volume flux of one node (nvar <= V variables): the Euler part as node_flux<false>,
+// and the passive species rho Y_k u_d.
+template <int V>
+__device__ __forceinline__ void node_flux_mix(const float q[V], int nvar, float dp, float pf, float F[3][V]) {
+  const float ir = 1.0f / q[0];
+  const float u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = q[1 + d];
+    F[d][1] = q[1] * u[d];
+    F[d][2] = q[2] * u[d];
+    F[d][3] = q[3] * u[d];
+    F[d][1 + d] += dp;
+    F[d][4] = u[d] * (q[4] + pf);
+#pragma unroll
+    for (int v = 5; v < V; ++v) F[d][v] = v < nvar ? q[v] * u[d] : 0.0f;
+  }
+}
+
+// Mixture surface term of one face node before Fscale: local Lax-Friedrichs with the sound
+// speeds of both traces (from the primitives pass).
+template <int V>
+__device__ __forceinline__ void face_term_mix(const float qm[V], const float qp[V], int nvar, float pm, float pp,
+                                              float dpn, float cm, float cp, const float n[3], float g[V]) {
+  const float irm = 1.0f / qm[0], irp = 1.0f / qp[0];
+  const float unm = (qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2]) * irm;
+  const float unp = (qp[1] * n[0] + qp[2] * n[1] + qp[3] * n[2]) * irp;
+  const float lam = fmaxf(fabsf(unm) + cm, fabsf(unp) + cp);
+  float dq[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) dq[v] = qm[v] - qp[v];
+  float dF[V];
+  dF[0] = dq[1] * n[0] + dq[2] * n[1] + dq[3] * n[2];
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii) dF[1 + ii] = qm[1 + ii] * unm - qp[1 + ii] * unp + dpn * n[ii];
+  dF[4] = unm * (qm[4] + pm) - unp * (qp[4] + pp);
+#pragma unroll
+  for (int v = 5; v < V; ++v) dF[v] = qm[v] * unm - qp[v] * unp;
+#pragma unroll
+  for (int v = 0; v < V; ++v) g[v] = v < nvar ? 0.5f * (dF[v] - lam * dq[v]) : 0.0f;
 }
 
 // Viscous flux of one node from the gradients grad[d][w] of w = (rho, rho u, rho v, rho w, T)

@@ -104,20 +104,23 @@ __host__ __device__ constexpr int default_nt(int N) { return N == 1 ? 128 : (N =
 __host__ __device__ constexpr int default_vis_nt(int N) { return N == 1 ? 128 : (N == 2 ? 128 : (N == 3 ? 512 : 896)); }
 
 // Blocks per SM that the compiler's register budget aims at: the shared-memory limit, the
-// thread limit, and no fewer than 64 registers per thread.
-__host__ __device__ constexpr int aim_blocks(int smem, int nt) {
-  const int by_smem = (228 * 1024) / (smem + 1024), by_thr = 2048 / nt, by_reg = 65536 / (nt * 64);
+// thread limit, and no fewer than min_regs registers per thread.
+__host__ __device__ constexpr int aim_blocks(int smem, int nt, int min_regs = 64) {
+  const int by_smem = (228 * 1024) / (smem + 1024), by_thr = 2048 / nt, by_reg = 65536 / (nt * min_regs);
   const int m = by_smem < by_thr ? by_smem : by_thr;
   const int r = m < by_reg ? m : by_reg;
   return r < 1 ? 1 : r;
 }
 
-template <int N, int NT_ = default_nt(N)>
+// Threads per tile of a mixture (13 rows per element, 9 elements per tile): about one node per thread.
+__host__ __device__ constexpr int mixture_nt(int N) { return N <= 2 ? 128 : (N == 3 ? 192 : 320); }
+
+template <int N, int NT_ = default_nt(N), int V_ = 5>
 struct Cfg {
   using O = kern::Ord<N>;
-  static constexpr int ORDER = N;
+  static constexpr int ORDER = N, V = V_;
   static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
-  static constexpr int E = 25, ROWS = 128;
+  static constexpr int E = 128 / V, ROWS = 128;  // rows (element, variable) of one MMA tile
   static constexpr int KV = round16(Np), NPAD = KV;
   static constexpr int NSURF = (NF + KV - 1) / KV, NCHUNK = 3 + NSURF, KB = NCHUNK * KV;
   // operand slot: 3 terms x 128 rows x KV columns; core matrices adjacent in K are 144 B apart
@@ -134,7 +137,7 @@ struct Cfg {
   static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
   static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
   static constexpr int SMEM = OFF_BAR + 16;
-  static constexpr int MINB = aim_blocks(SMEM, NT);
+  static constexpr int MINB = aim_blocks(SMEM, NT, V > 5 ? 96 : 64);  // a mixture node holds 3 x 13 fluxes
   static_assert(ROWS * CS * 4 <= 3 * A_TERM, "the accumulator copy must fit in the operand slot");
   static_assert(ROWS * CS % 4 == 0, "the accumulator copy is cleared in 16 B words");
   static_assert(NPAD <= TMEM_COLS, "TMEM columns");
@@ -260,9 +263,11 @@ template <class C_, int PHYS, bool RK>
 __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
                                          uint32_t& phase, unsigned* status) {
-  constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
-  constexpr bool NS = PHYS == kern::NAVIER_STOKES;
+  constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT, V = C_::V;
+  constexpr bool NS = PHYS == kern::NAVIER_STOKES, MIX = PHYS == kern::MIXTURE;
+  static_assert(MIX || V == 5, "a perfect gas has 5 conserved variables");
   const int tid = threadIdx.x;
+  const int nvar = MIX ? c.nvar : 5;
   const int nel = min(C_::E, c.K - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)c.K * Np;
@@ -274,20 +279,26 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
   for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
 
   // volume fluxes of this thread's nodes (FP32; pressure relative to the element's first node in FP64)
-  float F[NPT][3][5];
+  float F[NPT][3][V];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int n = tid + s * NT;
     if (n < nn) {
       const int e = n / Np;
       const size_t gn = base + n;
-      float qv[5], fv[9];
+      float qv[V];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) qv[v] = qf_g[v * KNp + gn];
-#pragma unroll
-      for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? fv_g[cc * KNp + gn] : 0.0f;
+      for (int v = 0; v < V; ++v) qv[v] = v < nvar ? qf_g[v * KNp + gn] : 0.0f;
       const double p = p_g[gn];
-      mixk::node_flux<NS>(qv, (float)(p - p_g[base + (size_t)e * Np]), (float)p, fv, F[s]);
+      const float dp = (float)(p - p_g[base + (size_t)e * Np]);
+      if constexpr (MIX) {
+        mixk::node_flux_mix<V>(qv, nvar, dp, (float)p, F[s]);
+      } else {
+        float fv[9];
+#pragma unroll
+        for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? fv_g[cc * KNp + gn] : 0.0f;
+        mixk::node_flux<NS>(qv, dp, (float)p, fv, F[s]);
+      }
     }
   }
   __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
@@ -303,8 +314,8 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         const float* G = S.geo + e * GS;
         const float gx = G[3 * ra], gy = G[3 * ra + 1], gz = G[3 * ra + 2];
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + v, i, C_::A_LBO, C_::A_SBO),
+        for (int v = 0; v < V; ++v)
+          put3_umma(S.A, C_::A_TERM, umma_off(e * V + v, i, C_::A_LBO, C_::A_SBO),
                     fmaf(gx, F[s][0][v], fmaf(gy, F[s][1][v], gz * F[s][2][v])));
       }
     }
@@ -323,23 +334,27 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       const float fs = G[12 + 4 * f];
       const size_t own = base + (size_t)e * Np + S.fm[mm];
       const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
-      float qm[5], qp[5], fvm[9], fvp[9];
+      float qm[V], qp[V], g[V];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        qm[v] = qf_g[v * KNp + own];
-        qp[v] = qf_g[v * KNp + P];
-      }
-#pragma unroll
-      for (int cc = 0; cc < 9; ++cc) {
-        fvm[cc] = NS ? fv_g[cc * KNp + own] : 0.0f;
-        fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
+      for (int v = 0; v < V; ++v) {
+        qm[v] = v < nvar ? qf_g[v * KNp + own] : 0.0f;
+        qp[v] = v < nvar ? qf_g[v * KNp + P] : 0.0f;
       }
       const double pm64 = p_g[own], pp64 = p_g[P];
-      float g[5];
-      mixk::face_term<NS>(qm, qp, (float)pm64, (float)pp64, (float)(pm64 - pp64), fvm, fvp, n3, gam, g);
+      if constexpr (MIX) {
+        mixk::face_term_mix<V>(qm, qp, nvar, (float)pm64, (float)pp64, (float)(pm64 - pp64), c.cs[own], c.cs[P], n3, g);
+      } else {
+        float fvm[9], fvp[9];
 #pragma unroll
-      for (int v = 0; v < 5; ++v)
-        put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
+        for (int cc = 0; cc < 9; ++cc) {
+          fvm[cc] = NS ? fv_g[cc * KNp + own] : 0.0f;
+          fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
+        }
+        mixk::face_term<NS>(qm, qp, (float)pm64, (float)pp64, (float)(pm64 - pp64), fvm, fvp, n3, gam, g);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        put3_umma(S.A, C_::A_TERM, umma_off(e * V + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
     }
     if (!run_chunk<C_>(S, 3 + sc, phase, status)) return false;
   }
@@ -358,18 +373,18 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
   }
   tc_fence_before();
   __syncthreads();
-  const float dtf = (float)c.dt;
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int n = tid + s * NT;
     if (n < nn) {
       const int e = n / Np, i = n - e * Np;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const float r = S.C[(e * 5 + v) * C_::CS + i];
+      for (int v = 0; v < V; ++v) {
+        if (v >= nvar) break;
+        const float r = S.C[(e * V + v) * C_::CS + i];
         const size_t gi = v * KNp + base + n;
         if (RK) {
-          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, (double)(dtf * r));
+          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, c.dt * (double)r);
           c.k[gi] = kk;
           out[gi] = fma(b, kk, qin[gi]);
         } else {
@@ -388,11 +403,14 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
+// Variables per element row block: 5, or 5 + DG_MAX_SPECIES for a mixture.
+__host__ __device__ constexpr int tile_v(int PHYS) { return PHYS == kern::MIXTURE ? mixk::MIX_V : 5; }
+
 template <int N, int NT, int PHYS, bool RK>
-__global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_kernel(const MixedCase c, const uint4* __restrict__ b_g,
+__global__ void __launch_bounds__(NT, (Cfg<N, NT, tile_v(PHYS)>::MINB)) rhs_tc_kernel(const MixedCase c, const uint4* __restrict__ b_g,
                                                              const int32_t* __restrict__ fmask_g, const double a,
                                                              const double b, unsigned* __restrict__ status) {
-  using C_ = Cfg<N, NT>;
+  using C_ = Cfg<N, NT, tile_v(PHYS)>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);

@@ -15,15 +15,23 @@ void free_mixed_ops(MeshDev& m) {
 
 mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const double* qin, double* out, double* k,
                                 double dt) {
-  const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * m.Np);
   mixk::MixedCase c;
   c.q[0] = const_cast<double*>(qin);
   c.q[1] = out;
   c.k = k;
-  c.qf = sc.qf;
-  c.p = sc.p;
-  c.T = sc.T;
-  c.fv = sc.fv;
+  if (g.model == DG_GAS_NASA7) {
+    mixk::mixed_scratch_mixture(m.scratch, (size_t)m.K * m.Np, &c.qf, &c.cs, &c.p);
+    c.T = nullptr;
+    c.fv = nullptr;
+  } else {
+    const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * m.Np);
+    c.qf = sc.qf;
+    c.p = sc.p;
+    c.T = sc.T;
+    c.fv = sc.fv;
+    c.cs = nullptr;
+  }
+  c.nvar = 5 + g.ns;
   c.geo = m.geo32;
   c.vmapP = m.vmapP;
   c.K = m.K;
@@ -42,6 +50,16 @@ cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const doubl
   const size_t want = (KNp + 255) / 256;
   const int blocks = (int)(want < (size_t)sms * 16 ? want : (size_t)sms * 16);
   mixk::prims_kernel<<<blocks, 256, 0, s>>>(c, q, KNp, m.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prims_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
+                                 cudaStream_t s) {
+  const size_t KNp = (size_t)m.K * m.Np;
+  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
+  const size_t want = (KNp + 255) / 256;
+  const int blocks = (int)std::min(want, (size_t)device_sms() * 16);
+  mixk::prims_mixture_kernel<<<blocks, 256, 0, s>>>(c, g, q, T, KNp, m.status);
   return cudaGetLastError();
 }
 

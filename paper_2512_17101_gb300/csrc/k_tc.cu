@@ -70,8 +70,9 @@ cudaError_t build_t(MeshDev& m, const RefOps& o) {
 
 template <int N, int PHYS, bool RK>
 cudaError_t launch_t(const MeshDev& m, const mixk::MixedCase& c, double a, double b, cudaStream_t s) {
-  using C = tc::Cfg<N>;
-  auto kern_fn = tc::rhs_tc_kernel<N, C::NT, PHYS, RK>;
+  constexpr int NT = PHYS == kern::MIXTURE ? tc::mixture_nt(N) : tc::default_nt(N);
+  using C = tc::Cfg<N, NT, tc::tile_v(PHYS)>;
+  auto kern_fn = tc::rhs_tc_kernel<N, NT, PHYS, RK>;
   static int grid_cap = 0;
   if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -142,6 +143,7 @@ cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops) {
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                           double a, double b, double dt, cudaStream_t s) {
   const mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
+  if (g.model == DG_GAS_NASA7) return dispatch<kern::MIXTURE>(m, c, rk, a, b, s);
   if (g.mu > 0) return dispatch<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
   return dispatch<kern::EULER>(m, c, rk, a, b, s);
 }

@@ -16,10 +16,12 @@ import pytest
 from oracle.euler import rhs_strong
 from oracle.lsrk import lsrk4_step
 from oracle.ns import rhs_ns
-from oracle.thermo import PerfectGas
+from oracle.thermo import Nasa7Gas, PerfectGas
 from tests._gpu import field_err, torch_cuda
 from tests._oracle_case import Disc
 from workloads import box_mesh, equispaced_tet_nodes, isentropic_vortex, taylor_green, uniform_perturbation
+from workloads.gas import mixture_primitive_state, seeded_nasa7_mixture
+from workloads.mlp import glorot_params, temperature_samples
 
 pytestmark = pytest.mark.gpu
 RHS_TOL = 1e-4     # right-hand side, relative per variable
@@ -141,3 +143,70 @@ def test_mixed_precision_config_full_size_against_fp64_path():
     err = field_err(qmx.cpu().numpy(), q64.cpu().numpy())
     assert err <= STATE_TOL, err
     assert mesh.status() == 0
+
+
+# ---- mixture: FP64 Newton temperature, tensor-core right-hand side -------------------------
+
+def _mixture(n, N, seed):
+    torch, dg, d, mesh = _setup(n, N)
+    mix = seeded_nasa7_mixture(7, seed=seed)
+    gas_o = Nasa7Gas(W=mix.W, coeffs=mix.coeffs)
+    gas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs, newton_tol=1e-10, newton_max_it=50)
+    Y, T, vel, p0 = mixture_primitive_state(d.xyz, 7, seed=seed)
+    rho = p0 / (gas_o.R_mix(Y) * T)
+    return torch, dg, d, mesh, gas, gas_o, mix, gas_o.conserved(rho, vel, Y, T)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_mixed_mixture_rhs(N):
+    """7 passive species, seeded NASA-7: 13-row element blocks (9 elements per tensor-core tile)."""
+    torch, dg, d, mesh, gas, gas_o, mix, q0 = _mixture(3, N, seed=1)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    T = torch.full(q0.shape[1:], 1650.0, device="cuda", dtype=torch.float64)
+    from paper_2512_17101_gb300 import capi
+    dg.dg_rhs(mesh, gas, q, rhs, T_io=T, opts=dg._opts(precision=capi.DG_PREC_MIXED))
+    rho, vel, Y, e = gas_o.split_state(q0)
+    Tw, _, ok = gas_o.newton_temperature(e, Y, np.full(e.shape, 1650.0))
+    want = rhs_strong(d.ref, d.geo, d.conn, q0, gas_o, T=Tw)
+    assert ok.all()
+    assert np.abs(T.cpu().numpy() - Tw).max() < 1e-9  # the temperature stays FP64 Newton
+    assert field_err(rhs.cpu().numpy(), want) <= RHS_TOL
+    assert mesh.status() == 0 and gas.status() == 0
+
+
+def test_mixed_precision_plus_learned_guess_step():
+    """The mixed-precision plus learned-guess path: MLP-seeded FP64 Newton and the tensor-core
+    mixture right-hand side, two RK4 steps on 4^3 x 6 tets at N = 2 against the oracle."""
+    from workloads.configs import _mixture_dt
+    torch, dg, d, mesh, gas, gas_o, mix, q0 = _mixture(4, 2, seed=0)
+    from paper_2512_17101_gb300 import capi
+    # a small training run: the network only seeds Newton, which stays the judge of T
+    T, Y = temperature_samples(50_000, 7, seed=11)
+    Td, Yd = torch.tensor(T, device="cuda"), torch.tensor(Y, device="cuda")
+    e = torch.empty_like(Td)
+    dg.dg_mixture_energy(gas, Td, Yd, e)
+    qs = torch.zeros((12, T.size), device="cuda", dtype=torch.float64)
+    qs[0] = 1.0
+    qs[4] = e
+    qs[5:] = Yd
+    Tn = torch.full_like(Td, 1650.0)
+    dg.dg_temperature(gas, qs, Tn)
+    dg.dg_mlp_train(gas, e, Yd, Tn, glorot_params(0), epochs=5, batch=1024, lr=3e-3, lr_decay=0.9)
+    dt = _mixture_dt(4, 2)
+    q = torch.tensor(q0, device="cuda")
+    Tio = torch.full(q0.shape[1:], 1650.0, device="cuda", dtype=torch.float64)
+    opts = dg._opts(precision=capi.DG_PREC_MIXED, t_seed=capi.DG_TSEED_MLP)
+    dg.lsrk4_step(mesh, gas, q, dt, steps=2, T_io=Tio, opts=opts)
+
+    def f(u):
+        rho, vel, Yk, ek = gas_o.split_state(u)
+        Tw, _, ok = gas_o.newton_temperature(ek, Yk, np.full(ek.shape, 1650.0))
+        assert ok.all()
+        return rhs_strong(d.ref, d.geo, d.conn, u, gas_o, T=Tw)
+
+    want = q0
+    for _ in range(2):
+        want = lsrk4_step(want, dt, f)
+    assert field_err(q.cpu().numpy(), want) <= STATE_TOL
+    assert mesh.status() == 0 and gas.status() == 0
