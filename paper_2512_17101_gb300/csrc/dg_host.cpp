@@ -144,19 +144,21 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
   if (opts && opts->precision == DG_PREC_MIXED) {
     if (g.model == DG_GAS_NASA7) {
-      // FP64 Newton temperature (seeded as opts says), FP64 pressure and FP32 sound speed per
-      // node, then the tensor-core right-hand side of the mixture
+      // FP64 Newton temperature (seeded as opts says), which at the converged temperature also
+      // writes the FP64 pressure, the sound speed and the float state copy; then the
+      // tensor-core right-hand side of the mixture
       if (!T_io) return fail(DG_ERR_INVALID_ARG, "a NASA-7 gas needs the temperature buffer T_io");
       if (g.mu > 0) return fail(DG_ERR_UNSUPPORTED, "the mixed-precision mixture path is inviscid");
       const int mode = opts->t_seed;
       if (mode == DG_TSEED_MLP && !gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "DG_TSEED_MLP needs a trained MLP");
+      const dg::MixturePrims mp = dg::mixture_prims_out(m);
       e = timed(mesh, DG_KERNEL_TEMPERATURE, s, [&] {
-        if (mode == DG_TSEED_MLP) return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s);
-        return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, opts->t_const, gas->status, s);
+        if (mode == DG_TSEED_MLP)
+          return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s, mp);
+        return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, opts->t_const, gas->status, s,
+                                      mp);
       });
       if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
-      e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_mixture(m, g, q, T_io, s); });
-      if (e != cudaSuccess) return cuda_fail(e, "mixture primitives kernel");
     } else {
       e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_mixed(m, g, q, s); });
       if (e != cudaSuccess) return cuda_fail(e, "mixed primitives kernel");

@@ -80,17 +80,27 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // side / RK stage and its BR1 pass (k_tc.cu).
 void free_mixed_ops(MeshDev& m);
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
-cudaError_t launch_prims_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
-                                 cudaStream_t s);
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                           double a, double b, double dt, cudaStream_t s);
 cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// Outputs of the mixed-precision form that the temperature solve also writes (all null: none):
+// float state copy [5 + ns][n], FP64 pressure [n], float sound speed [n]; rho <= 0 or p <= 0
+// sets DG_STATUS_NONPHYSICAL in *status.
+struct MixturePrims {
+  float* qf = nullptr;
+  double* p = nullptr;
+  float* cs = nullptr;
+  unsigned* status = nullptr;
+};
+// The mesh scratch's mixture tables (k_mixed.cu).
+MixturePrims mixture_prims_out(const MeshDev& m);
 // Mixture temperature (Newton).  seed_mode: DG_TSEED_*; nvar = 5 + ns; q is [nvar][n].
 cudaError_t launch_temperature(const GasParams& g, int64_t n, const double* q, double* T, int32_t* iters,
-                               int seed_mode, double t_const, unsigned* status, cudaStream_t s);
+                               int seed_mode, double t_const, unsigned* status, cudaStream_t s,
+                               const MixturePrims& mp = MixturePrims());
 cudaError_t launch_mixture_energy(const GasParams& g, int64_t n, const double* T, const double* Y, double* e,
                                   cudaStream_t s);
 
@@ -139,7 +149,7 @@ struct dg_gas_s {
 namespace dg {
 // k_mlp.cu
 cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, double* T, int32_t* iters, int guess_only,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const MixturePrims& mp = MixturePrims());
 cudaError_t mlp_set_params(dg_gas gas, const float* theta_host, const dg_mlp_norm& nrm);
 cudaError_t mlp_loss_grad(int64_t n, const float* theta, const float* X, const float* t, float* grad, float* loss,
                           cudaStream_t s);

@@ -75,7 +75,8 @@ struct MixedCase {
 };
 
 // Per-node tables of the mixed form for a mixture (64 of the scratch's 72 bytes per node):
-// float state copy [MIX_V][KNp], float sound speed [KNp], FP64 pressure [KNp].
+// float state copy [MIX_V][KNp], float sound speed [KNp], FP64 pressure [KNp]; written by the
+// temperature Newton kernels at the converged temperature (dg_newton.cuh).
 constexpr int MIX_V = 5 + DG_MAX_SPECIES;
 __host__ __device__ inline void mixed_scratch_mixture(double* base, size_t KNp, float** qf, float** cs, double** p) {
   float* f = reinterpret_cast<float*>(base);
@@ -123,37 +124,6 @@ static __global__ void prims_batched(const MixedCase* __restrict__ cases, const 
       const size_t i = (size_t)it.y + j;
       if (i < KNp) prims_node(c, qin, KNp, i, status);
     }
-  }
-}
-
-// ---- mixture primitives: FP64 pressure p = rho R_mix T at the Newton temperature, the sound
-// speed c = sqrt(cp/(cp - R_mix) p/rho), and a float copy of the state.
-static __global__ void prims_mixture_kernel(const MixedCase c, const GasParams g, const double* __restrict__ qin,
-                                            const double* __restrict__ T, const size_t KNp,
-                                            unsigned* __restrict__ status) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < KNp; i += (size_t)gridDim.x * blockDim.x) {
-    double qv[MIX_V];
-#pragma unroll
-    for (int v = 0; v < MIX_V; ++v) qv[v] = v < c.nvar ? qin[v * KNp + i] : 0.0;
-    float ir32;
-    const double ir = recip64(qv[0], ir32);
-    double Y[DG_MAX_SPECIES];
-#pragma unroll
-    for (int k = 0; k < DG_MAX_SPECIES; ++k) Y[k] = qv[5 + k] * ir;
-    const double Ti = T[i];
-    double cp, Rmix;
-    kern::mixture_cp_R(g, Y, Ti, cp, Rmix);
-    const double p = qv[0] * Rmix * Ti;
-    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-#pragma unroll
-    for (int v = 0; v < MIX_V; ++v)
-      if (v < c.nvar) c.qf[v * KNp + i] = (float)qv[v];
-    c.p[i] = p;
-    // c^2 = cp/(cp - R_mix) p/rho formed in FP64 and rounded once: the sound speed sets the
-    // Lax-Friedrichs dissipation, the largest surface term on rough mixture states
-    float r32;
-    const double c2 = cp * p * ir * recip64(cp - Rmix, r32);
-    c.cs[i] = sqrtf((float)c2);
   }
 }
 

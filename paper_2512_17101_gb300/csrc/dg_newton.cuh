@@ -1,0 +1,75 @@
+// Per-node temperature Newton solve of a NASA-7 mixture, shared by the seeded kernel
+// (k_thermo.cu) and the MLP-seeded kernel (k_mlp.cu), and the mixed-precision form's
+// per-node outputs that the converged solve yields almost for free.
+//
+// For fixed Y the mixture internal energy is a quintic in T whose coefficients c[0..5]
+// fold the species sums (sum_k Y_k R_k a_kj / (j+1), the -R_mix T of e = h - R T included);
+// each Newton update evaluates e(T) and cv(T) = de/dT by Horner and takes
+// T <- T - (e(T) - e) / cv(T) until |dT| < tol (capped).
+// At the converged T: cp = cv + R_mix, p = rho R_mix T, c^2 = cp/cv p/rho = R_mix T (cv + R_mix)/cv.
+#pragma once
+
+#include "dg_internal.h"
+
+namespace dg {
+namespace newton {
+
+// FP64 reciprocal from an FP32 seed and one Newton step (relative error ~1e-14).
+__device__ __forceinline__ double rcp64(double x) {
+  const double r = (double)(1.0f / (float)x);
+  return r * fma(-x, r, 2.0);
+}
+
+// Fold the species polynomials into the quintic e(T) = c0 + c1 T + ... + c5 T^5 (J/kg).
+__device__ __forceinline__ void fold(const GasParams& g, const double* Y, double c[6], double& Rmix) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) c[j] = 0.0;
+  Rmix = 0.0;
+#pragma unroll
+  for (int k = 0; k < DG_MAX_SPECIES; ++k) {
+    if (k >= g.ns) break;
+    const double yr = Y[k] * g.Rk[k];
+    const double* a = g.a[k];
+    Rmix += yr;
+    c[0] = fma(yr, a[5], c[0]);
+    c[1] = fma(yr, a[0] - 1.0, c[1]);
+    c[2] = fma(yr, a[1] * 0.5, c[2]);
+    c[3] = fma(yr, a[2] * (1.0 / 3.0), c[3]);
+    c[4] = fma(yr, a[3] * 0.25, c[4]);
+    c[5] = fma(yr, a[4] * 0.2, c[5]);
+  }
+}
+
+// Newton from seed t; returns true when |dT| < tol was met within max_it updates.  On return
+// t is the solution, it the updates taken and cv the heat capacity at the last iterate.
+__device__ __forceinline__ bool solve(const double c[6], double e, double& t, int max_it, double tol, int& it,
+                                      double& cv) {
+  it = 0;
+  cv = 1.0;
+  while (it < max_it) {
+    const double eT = c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * (c[4] + t * c[5]))));
+    cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
+    const double dT = (eT - e) * rcp64(cv);
+    t -= dT;
+    ++it;
+    if (fabs(dT) < tol) return true;
+  }
+  return false;
+}
+
+// The mixed-precision form's node outputs from the converged temperature t (cv at the last
+// iterate): float copy of the state, FP64 p = rho R_mix t, sound speed from c^2 formed in FP64
+// and rounded once.
+__device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasParams& g, const double* __restrict__ q,
+                                            int64_t n, int64_t node, double rho, double Rmix, double t, double cv) {
+  const int nvar = 5 + g.ns;
+  for (int v = 0; v < nvar; ++v) mp.qf[v * n + node] = (float)q[v * n + node];
+  const double p = rho * Rmix * t;
+  if (!(rho > 0.0) || !(p > 0.0)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
+  mp.p[node] = p;
+  const double c2 = Rmix * t * fma(Rmix, rcp64(cv), 1.0);
+  mp.cs[node] = sqrtf((float)c2);
+}
+
+}  // namespace newton
+}  // namespace dg

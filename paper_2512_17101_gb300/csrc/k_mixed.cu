@@ -53,14 +53,11 @@ cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_prims_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
-                                 cudaStream_t s) {
-  const size_t KNp = (size_t)m.K * m.Np;
-  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
-  const size_t want = (KNp + 255) / 256;
-  const int blocks = (int)std::min(want, (size_t)device_sms() * 16);
-  mixk::prims_mixture_kernel<<<blocks, 256, 0, s>>>(c, g, q, T, KNp, m.status);
-  return cudaGetLastError();
+MixturePrims mixture_prims_out(const MeshDev& m) {
+  MixturePrims mp;
+  mixk::mixed_scratch_mixture(m.scratch, (size_t)m.K * m.Np, &mp.qf, &mp.cs, &mp.p);
+  mp.status = m.status;
+  return mp;
 }
 
 }  // namespace dg

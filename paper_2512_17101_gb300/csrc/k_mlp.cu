@@ -17,7 +17,7 @@
 #include <cstring>
 #include <vector>
 
-#include "dg_internal.h"
+#include "dg_newton.cuh"
 
 namespace dg {
 namespace {
@@ -174,6 +174,14 @@ __device__ __forceinline__ void mma16816h(float* c, const uint32_t* a, uint32_t 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Hardware tanh (tanh.approx.f32, about 11 correct bits): the inference only seeds Newton,
+// which stays the judge of T; training uses the precise tanhf.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
   return (uint32_t)__half_as_ushort(__float2half_rn(lo)) | ((uint32_t)__half_as_ushort(__float2half_rn(hi)) << 16);
 }
@@ -194,7 +202,8 @@ struct MlpDev {
 __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g, const int64_t n,
                                                               const double* __restrict__ q, double* __restrict__ T,
                                                               int32_t* __restrict__ iters, const MlpDev mlp,
-                                                              const int guess_only, unsigned* __restrict__ status) {
+                                                              const int guess_only, unsigned* __restrict__ status,
+                                                              const MixturePrims mp) {
   __shared__ uint32_t sW1[NH * W1S];
   __shared__ uint32_t sW2[NH * W2S];
   __shared__ float sb1[NH], sb2[NH], sW3[NH];
@@ -215,27 +224,21 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
   for (int64_t g0 = ((int64_t)blockIdx.x * 4 + warp) * 32; g0 < n; g0 += stride) {
     const int64_t node = g0 + lane;
     const bool valid = node < n;
-    double e = 0.0, c[6] = {0, 0, 0, 0, 0, 0};
+    double e = 0.0, rho = 1.0, Rmix = 0.0, c[6] = {0, 0, 0, 0, 0, 0};
     float feat[NI] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid) {
-      const double rho = q[node], ir = 1.0 / rho;
+      rho = q[node];
+      const double ir = newton::rcp64(rho);
       const double mx = q[n + node], my = q[2 * n + node], mz = q[3 * n + node];
       e = q[4 * n + node] * ir - 0.5 * ir * ir * (mx * mx + my * my + mz * mz);
       feat[0] = (float)((e - mlp.nrm.e_mean) / mlp.nrm.e_scale);
+      double Y[DG_MAX_SPECIES];
 #pragma unroll
       for (int k = 0; k < DG_MAX_SPECIES; ++k) {
-        if (k >= g.ns) break;
-        const double Yk = q[(5 + k) * n + node] * ir;
-        if (k < NI - 1) feat[1 + k] = (float)Yk;
-        const double yr = Yk * g.Rk[k];
-        const double* a = g.a[k];
-        c[0] = fma(yr, a[5], c[0]);
-        c[1] = fma(yr, a[0] - 1.0, c[1]);
-        c[2] = fma(yr, a[1] * 0.5, c[2]);
-        c[3] = fma(yr, a[2] * (1.0 / 3.0), c[3]);
-        c[4] = fma(yr, a[3] * 0.25, c[4]);
-        c[5] = fma(yr, a[4] * 0.2, c[5]);
+        Y[k] = k < g.ns ? q[(5 + k) * n + node] * ir : 0.0;
+        if (k < NI - 1) feat[1 + k] = (float)Y[k];
       }
+      newton::fold(g, Y, c, Rmix);
     }
     uint32_t* xr = sX[warp] + lane * XS;
 #pragma unroll
@@ -255,8 +258,8 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
         const uint32_t* w = sW1 + (nt * 8 + gq) * W1S;
         mma16816h(cc, a1, w[tq], w[4 + tq]);
         const int col = nt * 8 + 2 * tq;
-        const float h0 = tanhf(cc[0] + sb1[col]), h1 = tanhf(cc[1] + sb1[col + 1]);
-        const float h2 = tanhf(cc[2] + sb1[col]), h3 = tanhf(cc[3] + sb1[col + 1]);
+        const float h0 = tanh_fast(cc[0] + sb1[col]), h1 = tanh_fast(cc[1] + sb1[col + 1]);
+        const float h2 = tanh_fast(cc[2] + sb1[col]), h3 = tanh_fast(cc[3] + sb1[col + 1]);
         // accumulator tile nt becomes half of the A fragment of layer-2 k-tile nt/2
         const int kt = nt >> 1, hi = nt & 1;
         a2[kt][hi ? 2 : 0] = pack_half2(h0, h1);
@@ -270,8 +273,8 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma16816h(cc, a2[kt], w[kt * 8 + tq], w[kt * 8 + 4 + tq]);
         const int col = nt * 8 + 2 * tq;
-        y0 = fmaf(sW3[col], tanhf(cc[0] + sb2[col]), fmaf(sW3[col + 1], tanhf(cc[1] + sb2[col + 1]), y0));
-        y1 = fmaf(sW3[col], tanhf(cc[2] + sb2[col]), fmaf(sW3[col + 1], tanhf(cc[3] + sb2[col + 1]), y1));
+        y0 = fmaf(sW3[col], tanh_fast(cc[0] + sb2[col]), fmaf(sW3[col + 1], tanh_fast(cc[1] + sb2[col + 1]), y0));
+        y1 = fmaf(sW3[col], tanh_fast(cc[2] + sb2[col]), fmaf(sW3[col + 1], tanh_fast(cc[3] + sb2[col + 1]), y1));
       }
       y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
       y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
@@ -291,22 +294,12 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
       T[node] = t;
       continue;
     }
-    int it = 0;
-    bool done = false;
-    while (it < g.newton_max_it) {
-      const double eT = c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * (c[4] + t * c[5]))));
-      const double cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
-      const double dT = (eT - e) / cv;
-      t -= dT;
-      ++it;
-      if (fabs(dT) < g.newton_tol) {
-        done = true;
-        break;
-      }
-    }
-    if (!done) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+    int it;
+    double cv;
+    if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
     T[node] = t;
     if (iters) iters[node] = it;
+    if (mp.qf) newton::store_prims(mp, g, q, n, node, rho, Rmix, t, cv);
   }
 }
 
@@ -332,12 +325,12 @@ cudaError_t ensure_half_weights(dg_gas gas) {
 }  // namespace
 
 cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, double* T, int32_t* iters, int guess_only,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const MixturePrims& mp) {
   if (n <= 0) return cudaSuccess;
   MlpDev m{(const uint32_t*)gas->mlp_w1h, (const uint32_t*)gas->mlp_w2h, gas->mlp_theta, gas->mlp_norm};
   const int64_t groups = (n + 31) / 32;
   int blocks = (int)std::min<int64_t>((groups + 3) / 4, (int64_t)sm_count() * 16);
-  temperature_mlp_kernel<<<blocks, 128, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status);
+  temperature_mlp_kernel<<<blocks, 128, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status, mp);
   return cudaGetLastError();
 }
 

@@ -5,48 +5,33 @@
 // For fixed Y the mixture energy is a quintic in T,
 //   e(T) = sum_k Y_k R_k (a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5 + a6 - T),
 // so each node first folds the species sums into six coefficients; every
-// Newton update then costs two Horner evaluations and a division:
-//   T <- T - (e(T) - e) / cv(T),  cv = de/dT,  until |dT| < tol (capped).
-#include "dg_internal.h"
+// Newton update then costs two Horner evaluations and a reciprocal:
+//   T <- T - (e(T) - e) / cv(T),  cv = de/dT,  until |dT| < tol (capped)
+// (dg_newton.cuh).  In the mixed-precision form the same kernel also writes the
+// node's pressure, sound speed and float state copy.
+#include "dg_newton.cuh"
 
 namespace dg {
 namespace {
 
 __global__ void temperature_kernel(const GasParams g, const int64_t n, const double* __restrict__ q,
                                    double* __restrict__ T, int32_t* __restrict__ iters, const int mode,
-                                   const double t_const, unsigned* __restrict__ status) {
+                                   const double t_const, unsigned* __restrict__ status, const MixturePrims mp) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double rho = q[i], ir = 1.0 / rho;
+    const double rho = q[i], ir = newton::rcp64(rho);
     const double mx = q[n + i], my = q[2 * n + i], mz = q[3 * n + i];
     const double e = q[4 * n + i] * ir - 0.5 * ir * ir * (mx * mx + my * my + mz * mz);
-    double c[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < g.ns; ++k) {
-      const double yr = q[(5 + k) * n + i] * ir * g.Rk[k];
-      const double* a = g.a[k];
-      c[0] = fma(yr, a[5], c[0]);
-      c[1] = fma(yr, a[0] - 1.0, c[1]);
-      c[2] = fma(yr, a[1] * 0.5, c[2]);
-      c[3] = fma(yr, a[2] * (1.0 / 3.0), c[3]);
-      c[4] = fma(yr, a[3] * 0.25, c[4]);
-      c[5] = fma(yr, a[4] * 0.2, c[5]);
-    }
+    double Y[DG_MAX_SPECIES];
+#pragma unroll
+    for (int k = 0; k < DG_MAX_SPECIES; ++k) Y[k] = k < g.ns ? q[(5 + k) * n + i] * ir : 0.0;
+    double c[6], Rmix, cv;
+    newton::fold(g, Y, c, Rmix);
     double t = mode == DG_TSEED_CONST ? t_const : T[i];
-    int it = 0;
-    bool done = false;
-    while (it < g.newton_max_it) {
-      const double eT = c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * (c[4] + t * c[5]))));
-      const double cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
-      const double dT = (eT - e) / cv;
-      t -= dT;
-      ++it;
-      if (fabs(dT) < g.newton_tol) {
-        done = true;
-        break;
-      }
-    }
-    if (!done) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+    int it;
+    if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
     T[i] = t;
     if (iters) iters[i] = it;
+    if (mp.qf) newton::store_prims(mp, g, q, n, i, rho, Rmix, t, cv);
   }
 }
 
@@ -77,9 +62,10 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_temperature(const GasParams& g, int64_t n, const double* q, double* T, int32_t* iters,
-                               int seed_mode, double t_const, unsigned* status, cudaStream_t s) {
+                               int seed_mode, double t_const, unsigned* status, cudaStream_t s,
+                               const MixturePrims& mp) {
   if (n <= 0) return cudaSuccess;
-  temperature_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status);
+  temperature_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
   return cudaGetLastError();
 }
 
