@@ -95,6 +95,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
   for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(r[j]);
 }
 
+// Bulk prefetch of [ptr, ptr + bytes) into L2 by the TMA engine, clamped inward to 16-byte
+// boundaries (cp.async.bulk.prefetch needs a 16-byte aligned start and size), so that it never
+// touches memory outside the range.
+__device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
+  const uintptr_t lo = ((uintptr_t)ptr + 15) & ~(uintptr_t)15;
+  const uintptr_t hi = ((uintptr_t)ptr + bytes) & ~(uintptr_t)15;
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
+// One thread's L2 prefetch of a tile's contiguous inputs: the float state copy and FP64 pressure
+// (and, for Navier-Stokes, the viscous flux), geometry and neighbour map of elements [e0, e0+nel).
+__device__ __forceinline__ void prefetch_tile_inputs(const MixedCase& c, int e0, int nel, int Np, int NF, int nvar,
+                                                     bool ns) {
+  const size_t KNp = (size_t)c.K * Np, base = (size_t)e0 * Np, nn = (size_t)nel * Np;
+  for (int v = 0; v < nvar; ++v) prefetch_l2(c.qf + v * KNp + base, nn * 4);
+  prefetch_l2(c.p + base, nn * 8);
+  if (ns)
+    for (int cc = 0; cc < 9; ++cc) prefetch_l2(c.fv + cc * KNp + base, nn * 4);
+  prefetch_l2(c.geo + (size_t)e0 * GS, (size_t)nel * GS * 4);
+  prefetch_l2(c.vmapP + (size_t)e0 * NF, (size_t)nel * NF * 4);
+}
+
 // ---- tile configuration --------------------------------------------------------------------
 constexpr int round16(int x) { return (x + 15) / 16 * 16; }
 
@@ -262,7 +285,7 @@ __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& ph
 template <class C_, int PHYS, bool RK>
 __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
-                                         uint32_t& phase, unsigned* status) {
+                                         uint32_t& phase, unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT, V = C_::V;
   constexpr bool NS = PHYS == kern::NAVIER_STOKES, MIX = PHYS == kern::MIXTURE;
   static_assert(MIX || V == 5, "a perfect gas has 5 conserved variables");
@@ -276,6 +299,18 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
   const double* __restrict__ p_g = c.p;
   const float* __restrict__ fv_g = c.fv;
 
+  if (tid == 0) {
+    // this tile's RK inputs (read only in the epilogue) and the next tile's inputs, into L2
+    if (RK)
+      for (int v = 0; v < nvar; ++v) {
+        if (a != 0.0) prefetch_l2(c.k + v * KNp + base, (size_t)nn * 8);
+        prefetch_l2(qin + v * KNp + base, (size_t)nn * 8);
+      }
+    if (next) {
+      const int nnel = min(C_::E, next->K - next_e0);
+      prefetch_tile_inputs(*next, next_e0, nnel, Np, NF, nvar, NS);
+    }
+  }
   for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
 
   // volume fluxes of this thread's nodes (FP32; pressure relative to the element's first node in FP64)
@@ -415,8 +450,11 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT, tile_v(PHYS)>::MINB)) rhs_tc_k
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
-  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
-    if (!rhs_tile<C_, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status)) break;
+  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
+    const int ne0 = e0 + gridDim.x * C_::E;
+    if (!rhs_tile<C_, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status, ne0 < c.K ? &c : nullptr, ne0))
+      break;
+  }
   block_teardown<C_>(S, phase);
 }
 
@@ -437,7 +475,11 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const M
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
-    if (!rhs_tile<C_, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status)) break;
+    const int wn = w + gridDim.x;
+    const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
+    if (!rhs_tile<C_, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status,
+                                  wn < nwork ? &cases[nx.x] : nullptr, nx.y))
+      break;
   }
   block_teardown<C_>(S, phase);
 }
@@ -480,7 +522,8 @@ struct VCfg {
 // the float state copy (momentum) and the FP64 temperature.
 template <class C_>
 __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
-                                         const int e0, uint32_t& phase, unsigned* status) {
+                                         const int e0, uint32_t& phase, unsigned* status, const MixedCase* next,
+                                         const double* next_q, int next_e0) {
   constexpr int Np = C_::Np, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
   const int tid = threadIdx.x;
   const int nel = min(C_::E, c.K - e0);
@@ -490,6 +533,16 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
   const float* __restrict__ qf_g = c.qf;
   const double* __restrict__ T_g = c.T;
 
+  if (tid == 0 && next) {
+    // the next tile's inputs into L2: rho (FP64 state), T, momentum copy, geometry, neighbour map
+    const int nnel = min(C_::E, next->K - next_e0);
+    const size_t nK = (size_t)next->K * Np, nb = (size_t)next_e0 * Np, nnn = (size_t)nnel * Np;
+    prefetch_l2(next_q + nb, nnn * 8);
+    prefetch_l2(next->T + nb, nnn * 8);
+    for (int d = 1; d < 4; ++d) prefetch_l2(next->qf + d * nK + nb, nnn * 4);
+    prefetch_l2(next->geo + (size_t)next_e0 * GS, (size_t)nnel * GS * 4);
+    prefetch_l2(next->vmapP + (size_t)next_e0 * NF, (size_t)nnel * NF * 4);
+  }
   for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
 
   // volume chunk: (rho - rho_1, m, T - T_1) per node, differences to the element's first node in FP64
@@ -610,8 +663,10 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_kernel(const M
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   uint32_t phase = 0;
-  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E)
-    if (!vis_tile<C_>(S, c, c.q[0], e0, phase, status)) break;
+  for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
+    const int ne0 = e0 + gridDim.x * C_::E;
+    if (!vis_tile<C_>(S, c, c.q[0], e0, phase, status, ne0 < c.K ? &c : nullptr, c.q[0], ne0)) break;
+  }
   block_teardown<C_>(S, phase);
 }
 
@@ -631,7 +686,10 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_batched(const 
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
-    if (!vis_tile<C_>(S, c, c.q[stage & 1], it.y, phase, status)) break;
+    const int wn = w + gridDim.x;
+    const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
+    const MixedCase* nc = wn < nwork ? &cases[nx.x] : nullptr;
+    if (!vis_tile<C_>(S, c, c.q[stage & 1], it.y, phase, status, nc, nc ? nc->q[stage & 1] : nullptr, nx.y)) break;
   }
   block_teardown<C_>(S, phase);
 }
