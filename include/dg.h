@@ -339,6 +339,19 @@ int dg_batch_tiles(dg_batch batch, int32_t* rhs_tiles_host, int32_t* viscous_til
 int dg_batch_status(dg_batch batch, uint32_t* bits, int reset);
 int dg_batch_free(dg_batch batch);
 
+/* ---- precision conversions ------------------------------------------------------------------
+ * The FP64 -> FP32 and FP32 -> FP64 conversions that the mixed-precision kernels use, done with
+ * integer operations on the IEEE-754 bit patterns (the FP64 pipe, which runs the hardware
+ * conversions, is the scarce unit on this GPU).  The paper has no counterpart; exposed so that
+ * the conversions can be checked against the hardware's.
+ *   dg_round_to_float: y[i] = x[i] rounded to nearest, ties to even (as the hardware for all
+ *     inputs; normal and zero results on the integer path, the rest by the hardware).
+ *   dg_widen_to_double: y[i] = x[i] exactly for finite, infinite and NaN inputs; float
+ *     subnormals become signed zero.
+ * x, y: device arrays of n elements (n >= 0), asynchronous on stream. */
+int dg_round_to_float(const double* x_dev, float* y_dev, int64_t n, void* stream);
+int dg_widen_to_double(const float* x_dev, double* y_dev, int64_t n, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dg_last_error(void);
 

@@ -113,6 +113,8 @@ SIGNATURES = {
     "dg_batch_free": (c_int32, [c_void_p]),
     "dg_rk_stage_noalloc": (c_int32, [ctypes.POINTER(dg_mesh_tables), ctypes.POINTER(dg_gas_desc), c_int32,
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_round_to_float": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "dg_widen_to_double": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, []),
 }
 

@@ -18,6 +18,7 @@
 
 #include <cuda_bf16.h>
 
+#include "dg_cvt.cuh"
 #include "dg_kernels.cuh"
 
 namespace dg {
@@ -25,10 +26,11 @@ namespace mixk {
 
 using kern::GS;
 
-// FP64 reciprocal from an FP32 seed plus one Newton step (relative error ~1e-14).
+// FP64 reciprocal from an FP32 seed plus one Newton step (relative error ~1e-14); the seed's
+// conversions run on the integer pipe.
 __device__ __forceinline__ double recip64(double x, float& r32) {
-  r32 = 1.0f / (float)x;
-  double r = (double)r32;
+  r32 = 1.0f / cvt::narrow(x);
+  const double r = cvt::widen(r32);
   return r * fma(-x, r, 2.0);
 }
 
@@ -97,9 +99,12 @@ __device__ __forceinline__ void prims_node(const MixedCase& c, const double* __r
   float ir32;
   const double ir = recip64(qv[0], ir32);
   const double p = (c.gas.gamma - 1.0) * (qv[4] - 0.5 * ir * fma(qv[1], qv[1], fma(qv[2], qv[2], qv[3] * qv[3])));
-  if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+  float qf[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) c.qf[v * KNp + i] = (float)qv[v];
+  for (int v = 0; v < 5; ++v) qf[v] = cvt::narrow(qv[v]);
+  if (!(qf[0] > 0.0f) || !(cvt::narrow(p) > 0.0f)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) c.qf[v * KNp + i] = qf[v];
   c.p[i] = p;
   if (c.gas.mu > 0.0) c.T[i] = p * ir * c.gas.inv_R;  // T = p / (rho R), no FP64 division
 }

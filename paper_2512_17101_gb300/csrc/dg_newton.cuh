@@ -9,14 +9,16 @@
 // At the converged T: cp = cv + R_mix, p = rho R_mix T, c^2 = cp/cv p/rho = R_mix T (cv + R_mix)/cv.
 #pragma once
 
+#include "dg_cvt.cuh"
 #include "dg_internal.h"
 
 namespace dg {
 namespace newton {
 
-// FP64 reciprocal from an FP32 seed and one Newton step (relative error ~1e-14).
+// FP64 reciprocal from an FP32 seed and one Newton step (relative error ~1e-14); the seed's
+// conversions run on the integer pipe.
 __device__ __forceinline__ double rcp64(double x) {
-  const double r = (double)(1.0f / (float)x);
+  const double r = cvt::widen(1.0f / cvt::narrow(x));
   return r * fma(-x, r, 2.0);
 }
 
@@ -63,12 +65,12 @@ __device__ __forceinline__ bool solve(const double c[6], double e, double& t, in
 __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasParams& g, const double* __restrict__ q,
                                             int64_t n, int64_t node, double rho, double Rmix, double t, double cv) {
   const int nvar = 5 + g.ns;
-  for (int v = 0; v < nvar; ++v) mp.qf[v * n + node] = (float)q[v * n + node];
+  for (int v = 0; v < nvar; ++v) mp.qf[v * n + node] = cvt::narrow(q[v * n + node]);
   const double p = rho * Rmix * t;
-  if (!(rho > 0.0) || !(p > 0.0)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
+  if (!(cvt::narrow(rho) > 0.0f) || !(cvt::narrow(p) > 0.0f)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
   mp.p[node] = p;
   const double c2 = Rmix * t * fma(Rmix, rcp64(cv), 1.0);
-  mp.cs[node] = sqrtf((float)c2);
+  mp.cs[node] = sqrtf(cvt::narrow(c2));
 }
 
 }  // namespace newton

@@ -325,14 +325,14 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
 #pragma unroll
       for (int v = 0; v < V; ++v) qv[v] = v < nvar ? qf_g[v * KNp + gn] : 0.0f;
       const double p = p_g[gn];
-      const float dp = (float)(p - p_g[base + (size_t)e * Np]);
+      const float dp = cvt::narrow(p - p_g[base + (size_t)e * Np]), pf = cvt::narrow(p);
       if constexpr (MIX) {
-        mixk::node_flux_mix<V>(qv, nvar, dp, (float)p, F[s]);
+        mixk::node_flux_mix<V>(qv, nvar, dp, pf, F[s]);
       } else {
         float fv[9];
 #pragma unroll
         for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? fv_g[cc * KNp + gn] : 0.0f;
-        mixk::node_flux<NS>(qv, dp, (float)p, fv, F[s]);
+        mixk::node_flux<NS>(qv, dp, pf, fv, F[s]);
       }
     }
   }
@@ -376,8 +376,9 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         qp[v] = v < nvar ? qf_g[v * KNp + P] : 0.0f;
       }
       const double pm64 = p_g[own], pp64 = p_g[P];
+      const float pm = cvt::narrow(pm64), pp = cvt::narrow(pp64), dpn = cvt::narrow(pm64 - pp64);
       if constexpr (MIX) {
-        mixk::face_term_mix<V>(qm, qp, nvar, (float)pm64, (float)pp64, (float)(pm64 - pp64), c.cs[own], c.cs[P], n3, g);
+        mixk::face_term_mix<V>(qm, qp, nvar, pm, pp, dpn, c.cs[own], c.cs[P], n3, g);
       } else {
         float fvm[9], fvp[9];
 #pragma unroll
@@ -385,7 +386,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
           fvm[cc] = NS ? fv_g[cc * KNp + own] : 0.0f;
           fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
         }
-        mixk::face_term<NS>(qm, qp, (float)pm64, (float)pp64, (float)(pm64 - pp64), fvm, fvp, n3, gam, g);
+        mixk::face_term<NS>(qm, qp, pm, pp, dpn, fvm, fvp, n3, gam, g);
       }
 #pragma unroll
       for (int v = 0; v < V; ++v)
@@ -408,6 +409,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
   }
   tc_fence_before();
   __syncthreads();
+  const float dtf = (float)c.dt;
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int n = tid + s * NT;
@@ -419,11 +421,13 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         const float r = S.C[(e * V + v) * C_::CS + i];
         const size_t gi = v * KNp + base + n;
         if (RK) {
-          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, c.dt * (double)r);
+          // dt rhs formed in FP32 (the right-hand side carries FP32-level error already) and
+          // widened on the integer pipe; the accumulation is FP64
+          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, cvt::widen(dtf * r));
           c.k[gi] = kk;
           out[gi] = fma(b, kk, qin[gi]);
         } else {
-          out[gi] = (double)r;
+          out[gi] = cvt::widen(r);
         }
       }
     }
@@ -554,14 +558,14 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       const int e = n / Np;
       const size_t gn = base + n, g1 = base + (size_t)e * Np;
       const double rho = qin[gn];
-      rho_n[s] = (float)rho;
+      rho_n[s] = cvt::narrow(rho);
 #pragma unroll
       for (int d = 0; d < 3; ++d) m_n[s][d] = qf_g[(1 + d) * KNp + gn];
-      w_n[s][0] = (float)(rho - qin[g1]);
+      w_n[s][0] = cvt::narrow(rho - qin[g1]);
       w_n[s][1] = m_n[s][0];
       w_n[s][2] = m_n[s][1];
       w_n[s][3] = m_n[s][2];
-      w_n[s][4] = (float)(T_g[gn] - T_g[g1]);
+      w_n[s][4] = cvt::narrow(T_g[gn] - T_g[g1]);
     }
   }
   __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
@@ -586,10 +590,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       const size_t own = base + (size_t)e * Np + S.fm[mm];
       const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
       float jv[5];
-      jv[0] = (float)(qin[P] - qin[own]);
+      jv[0] = cvt::narrow(qin[P] - qin[own]);
 #pragma unroll
       for (int d = 0; d < 3; ++d) jv[1 + d] = qf_g[(1 + d) * KNp + P] - qf_g[(1 + d) * KNp + own];
-      jv[4] = (float)(T_g[P] - T_g[own]);
+      jv[4] = cvt::narrow(T_g[P] - T_g[own]);
 #pragma unroll
       for (int f = 0; f < 5; ++f)
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, mm - m0, C_::A_LBO, C_::A_SBO), jv[f]);

@@ -237,6 +237,20 @@ def lsrk4_step(mesh, gas, q, dt, steps=1, T_io=None, opts=None, stream=None, wor
     return q
 
 
+def dg_round_to_float(x, y, stream=None):
+    """y = x rounded to FP32 by the library's integer-pipe conversion (float64 -> float32 CUDA tensors)."""
+    import torch
+    check(load().dg_round_to_float(_dptr(x, torch.float64, "x"), _dptr(y, torch.float32, "y"), x.numel(),
+                                   _stream_ptr(stream)))
+
+
+def dg_widen_to_double(x, y, stream=None):
+    """y = x widened to FP64 by the library's integer-pipe conversion (float32 -> float64 CUDA tensors)."""
+    import torch
+    check(load().dg_widen_to_double(_dptr(x, torch.float32, "x"), _dptr(y, torch.float64, "y"), x.numel(),
+                                    _stream_ptr(stream)))
+
+
 def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, stream=None):
     """Allocation-free viscous stage on caller-owned tables.
 
