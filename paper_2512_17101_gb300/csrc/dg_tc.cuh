@@ -415,19 +415,28 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
     const int n = tid + s * NT;
     if (n < nn) {
       const int e = n / Np, i = n - e * Np;
+      // all of this node's RK inputs first, so that their loads overlap
+      double k_old[V], q_old[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        if (v >= nvar) break;
-        const float r = S.C[(e * V + v) * C_::CS + i];
         const size_t gi = v * KNp + base + n;
-        if (RK) {
-          // dt rhs formed in FP32 (the right-hand side carries FP32-level error already) and
-          // widened on the integer pipe; the accumulation is FP64
-          const double kk = fma(a, a != 0.0 ? c.k[gi] : 0.0, cvt::widen(dtf * r));
-          c.k[gi] = kk;
-          out[gi] = fma(b, kk, qin[gi]);
-        } else {
-          out[gi] = cvt::widen(r);
+        k_old[v] = (RK && v < nvar && a != 0.0) ? c.k[gi] : 0.0;
+        q_old[v] = (RK && v < nvar) ? qin[gi] : 0.0;
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (v < nvar) {
+          const float r = S.C[(e * V + v) * C_::CS + i];
+          const size_t gi = v * KNp + base + n;
+          if (RK) {
+            // dt rhs formed in FP32 (the right-hand side carries FP32-level error already) and
+            // widened on the integer pipe; the accumulation is FP64
+            const double kk = fma(a, k_old[v], cvt::widen(dtf * r));
+            c.k[gi] = kk;
+            out[gi] = fma(b, kk, q_old[v]);
+          } else {
+            out[gi] = cvt::widen(r);
+          }
         }
       }
     }
