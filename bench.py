@@ -259,21 +259,22 @@ def workload_config(cfg):
 # ---- GPU arm -------------------------------------------------------------------------------------
 
 def mixed_prims_bytes_per_element(Np, viscous):
-    """q in (FP64); float state copy, FP64 pressure (and temperature) out."""
-    return Np * (40 + 20 + 8 + (8 if viscous else 0))
+    """q in (FP64); the 32-byte node record (float state, pressure and density as hi/lo pairs) and,
+    for Navier-Stokes, the temperature pair out."""
+    return Np * (40 + 32 + (8 if viscous else 0))
 
 
 def mixed_rhs_bytes_per_element(Np, NF, viscous):
-    """float state copy + FP64 pressure in; q in, k in/out, q_out (FP64); fp32 geometry; neighbour map."""
-    b = Np * (20 + 8 + 4 * 40) + 26 * 4 + 4 * NF
+    """node records in; q in, k in/out, q_out (FP64); fp32 geometry; neighbour map."""
+    b = Np * (32 + 4 * 40) + 26 * 4 + 4 * NF
     if viscous:
-        b += Np * 4 * 9                      # fp32 viscous flux in
+        b += Np * 4 * 9                      # fp32 viscous-flux record in
     return b
 
 
 def mixed_viscous_bytes_per_element(Np, NF):
-    """rho, T (FP64) and momentum (fp32) in; fp32 viscous flux out; fp32 geometry; neighbour map."""
-    return Np * (8 + 8 + 12 + 36) + 26 * 4 + 4 * NF
+    """node records and temperature pairs in; fp32 viscous-flux record out; fp32 geometry; neighbour map."""
+    return Np * (32 + 8 + 36) + 26 * 4 + 4 * NF
 
 
 def mixed_tensor_flops_per_element(Np, NF, viscous):

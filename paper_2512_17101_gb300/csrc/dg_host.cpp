@@ -251,7 +251,7 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
     std::vector<float> g32(m->geo.begin(), m->geo.end());
     e = upload(&d.geo32, g32.data(), g32.size());
   }
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 9 * (size_t)d.K * Np);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 10 * (size_t)d.K * Np);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);

@@ -60,8 +60,8 @@ struct MeshDev {
   int32_t* fmask = nullptr;    // [4][Nfp]
   double* geo = nullptr;       // [K][DG_GEO_STRIDE]
   int32_t* vmapP = nullptr;    // [K][4 Nfp]
-  double* scratch = nullptr;   // 72 B per node: FP64 form [9][K][Np] viscous flux (BR1 pass 1 output);
-                               // mixed form float Fv [9] | float q [5] | double p | double T, each [K][Np]
+  double* scratch = nullptr;   // 80 B per node: FP64 form [9][K][Np] viscous flux (BR1 pass 1 output);
+                               // mixed form node records (dg_mixed.cuh NodeTables) or mixture tables
   float* geo32 = nullptr;      // [K][DG_GEO_STRIDE] float copy of geo (mixed form)
   unsigned* status = nullptr;  // device status word
 };

@@ -34,22 +34,36 @@ __device__ __forceinline__ double recip64(double x, float& r32) {
   return r * fma(-x, r, 2.0);
 }
 
-// Per-node tables of the mixed form, in the mesh's scratch (72 bytes per node).
-struct MixedScratch {
-  float* fv;   // [9][KNp] viscous flux (BR1 output)
-  float* qf;   // [5][KNp] float copy of the state
-  double* p;   // [KNp] pressure (FP64)
-  double* T;   // [KNp] temperature (FP64, viscous only)
+// Per-node tables of the mixed form for a perfect gas, in the mesh's scratch (76 of its 80 bytes
+// per node), as records so that a node's values come in a few wide loads:
+//   node [KNp][2] float4: {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, rho_lo}
+//   fv4  [KNp][2] float4: {tau_xx, tau_yy, tau_zz, tau_xy}, {tau_xz, tau_yz, Q_x, Q_y};  fvz [KNp]: Q_z
+//   temp [KNp] float2: {T_hi, T_lo}
+// rho, p and T are float pairs hi + lo (hi = the FP64 value rounded to FP32, lo = the rounded rest:
+// about 48 significant bits), so the differences that would cancel (p against the element's first
+// node, p- - p+, rho and T against a reference and their jumps) are formed as (hi - hi') + (lo - lo')
+// in FP32, whose hi part is exact for values within a factor of two of each other.
+struct NodeTables {
+  float4* node;
+  float4* fv4;
+  float* fvz;
+  float2* temp;
 };
 
-__host__ __device__ inline MixedScratch mixed_scratch(double* base, size_t KNp) {
+__host__ __device__ inline NodeTables node_tables(double* base, size_t KNp) {
   float* f = reinterpret_cast<float*>(base);
-  MixedScratch m;
-  m.fv = f;
-  m.qf = f + 9 * KNp;
-  m.p = reinterpret_cast<double*>(f + 14 * KNp);
-  m.T = m.p + KNp;
-  return m;
+  NodeTables t;
+  t.node = reinterpret_cast<float4*>(f);
+  t.fv4 = reinterpret_cast<float4*>(f + 8 * KNp);
+  t.temp = reinterpret_cast<float2*>(f + 16 * KNp);
+  t.fvz = f + 18 * KNp;
+  return t;
+}
+
+// x = hi + lo with hi = x rounded to FP32 and lo the rest rounded to FP32 (integer-pipe conversions).
+__device__ __forceinline__ float2 split2(double x) {
+  const float hi = cvt::narrow(x);
+  return make_float2(hi, cvt::narrow(x - cvt::widen(hi)));
 }
 
 // One case of the mixed form: its state buffers (q[0] in, q[1] out for a single
@@ -62,11 +76,15 @@ struct MixedGas {
 struct MixedCase {
   double* q[2];
   double* k;
+  // perfect gas: node records (see NodeTables)
+  float4* node;
+  float4* fv4;
+  float* fvz;
+  float2* temp;
+  // mixture: float state copy [nvar][KNp], FP64 pressure, sound speed
   float* qf;
   double* p;
-  double* T;
-  float* fv;
-  float* cs;  // sound speed per node (mixtures; a perfect gas computes it from p and rho)
+  float* cs;
   const float* geo;
   const int32_t* vmapP;
   int K;
@@ -76,7 +94,7 @@ struct MixedCase {
   MixedGas gas;
 };
 
-// Per-node tables of the mixed form for a mixture (64 of the scratch's 72 bytes per node):
+// Per-node tables of the mixed form for a mixture (64 of the scratch's 80 bytes per node):
 // float state copy [MIX_V][KNp], float sound speed [KNp], FP64 pressure [KNp]; written by the
 // temperature Newton kernels at the converged temperature (dg_newton.cuh).
 constexpr int MIX_V = 5 + DG_MAX_SPECIES;
@@ -87,10 +105,10 @@ __host__ __device__ inline void mixed_scratch_mixture(double* base, size_t KNp, 
   *p = reinterpret_cast<double*>(f + (MIX_V + 1) * KNp);
 }
 static_assert((MIX_V + 1) % 2 == 0, "the FP64 pressure must start on an 8-byte boundary");
-static_assert((MIX_V + 1) * 4 + 8 <= 72, "the mixture tables must fit the 72-byte scratch");
+static_assert((MIX_V + 1) * 4 + 8 <= 80, "the mixture tables must fit the 80-byte scratch");
 
-// ---- pass 0: per node, FP64 pressure (and temperature) and a float copy of the state,
-// so that the later kernels read traces without recomputing or converting them.
+// ---- pass 0: per node, FP64 pressure (and temperature) and the node record, so that the later
+// kernels read traces without recomputing or converting them.
 __device__ __forceinline__ void prims_node(const MixedCase& c, const double* __restrict__ qin, size_t KNp, size_t i,
                                            unsigned* status) {
   double qv[5];
@@ -99,14 +117,11 @@ __device__ __forceinline__ void prims_node(const MixedCase& c, const double* __r
   float ir32;
   const double ir = recip64(qv[0], ir32);
   const double p = (c.gas.gamma - 1.0) * (qv[4] - 0.5 * ir * fma(qv[1], qv[1], fma(qv[2], qv[2], qv[3] * qv[3])));
-  float qf[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) qf[v] = cvt::narrow(qv[v]);
-  if (!(qf[0] > 0.0f) || !(cvt::narrow(p) > 0.0f)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) c.qf[v * KNp + i] = qf[v];
-  c.p[i] = p;
-  if (c.gas.mu > 0.0) c.T[i] = p * ir * c.gas.inv_R;  // T = p / (rho R), no FP64 division
+  const float2 rho2 = split2(qv[0]), p2 = split2(p);
+  if (!(rho2.x > 0.0f) || !(p2.x > 0.0f)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+  c.node[2 * i] = make_float4(rho2.x, cvt::narrow(qv[1]), cvt::narrow(qv[2]), cvt::narrow(qv[3]));
+  c.node[2 * i + 1] = make_float4(cvt::narrow(qv[4]), p2.x, p2.y, rho2.y);
+  if (c.gas.mu > 0.0) c.temp[i] = split2(p * ir * c.gas.inv_R);  // T = p / (rho R), no FP64 division
 }
 
 static __global__ void prims_kernel(const MixedCase c, const double* __restrict__ qin, const size_t KNp,

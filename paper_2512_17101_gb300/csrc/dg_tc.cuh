@@ -105,15 +105,23 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
 }
 
-// One thread's L2 prefetch of a tile's contiguous inputs: the float state copy and FP64 pressure
-// (and, for Navier-Stokes, the viscous flux), geometry and neighbour map of elements [e0, e0+nel).
-__device__ __forceinline__ void prefetch_tile_inputs(const MixedCase& c, int e0, int nel, int Np, int NF, int nvar,
+// One thread's L2 prefetch of a tile's contiguous inputs (the node records or, for a mixture,
+// the float state copy, pressure and sound speed; the viscous-flux records for Navier-Stokes),
+// geometry and neighbour map of elements [e0, e0 + nel).
+__device__ __forceinline__ void prefetch_tile_inputs(const MixedCase& c, int e0, int nel, int Np, int NF, bool mix,
                                                      bool ns) {
   const size_t KNp = (size_t)c.K * Np, base = (size_t)e0 * Np, nn = (size_t)nel * Np;
-  for (int v = 0; v < nvar; ++v) prefetch_l2(c.qf + v * KNp + base, nn * 4);
-  prefetch_l2(c.p + base, nn * 8);
-  if (ns)
-    for (int cc = 0; cc < 9; ++cc) prefetch_l2(c.fv + cc * KNp + base, nn * 4);
+  if (mix) {
+    for (int v = 0; v < c.nvar; ++v) prefetch_l2(c.qf + v * KNp + base, nn * 4);
+    prefetch_l2(c.p + base, nn * 8);
+    prefetch_l2(c.cs + base, nn * 4);
+  } else {
+    prefetch_l2(c.node + 2 * base, nn * 32);
+    if (ns) {
+      prefetch_l2(c.fv4 + 2 * base, nn * 32);
+      prefetch_l2(c.fvz + base, nn * 4);
+    }
+  }
   prefetch_l2(c.geo + (size_t)e0 * GS, (size_t)nel * GS * 4);
   prefetch_l2(c.vmapP + (size_t)e0 * NF, (size_t)nel * NF * 4);
 }
@@ -295,9 +303,8 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
   const int nn = nel * Np;
   const size_t KNp = (size_t)c.K * Np;
   const size_t base = (size_t)e0 * Np;
-  const float* __restrict__ qf_g = c.qf;
+  const float* __restrict__ qf_g = c.qf;  // mixture tables
   const double* __restrict__ p_g = c.p;
-  const float* __restrict__ fv_g = c.fv;
 
   if (tid == 0) {
     // this tile's RK inputs (read only in the epilogue) and the next tile's inputs, into L2
@@ -308,7 +315,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       }
     if (next) {
       const int nnel = min(C_::E, next->K - next_e0);
-      prefetch_tile_inputs(*next, next_e0, nnel, Np, NF, nvar, NS);
+      prefetch_tile_inputs(*next, next_e0, nnel, Np, NF, MIX, NS);
     }
   }
   for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
@@ -320,19 +327,25 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
     const int n = tid + s * NT;
     if (n < nn) {
       const int e = n / Np;
-      const size_t gn = base + n;
-      float qv[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) qv[v] = v < nvar ? qf_g[v * KNp + gn] : 0.0f;
-      const double p = p_g[gn];
-      const float dp = cvt::narrow(p - p_g[base + (size_t)e * Np]), pf = cvt::narrow(p);
+      const size_t gn = base + n, g1 = base + (size_t)e * Np;
       if constexpr (MIX) {
-        mixk::node_flux_mix<V>(qv, nvar, dp, pf, F[s]);
-      } else {
-        float fv[9];
+        float qv[V];
 #pragma unroll
-        for (int cc = 0; cc < 9; ++cc) fv[cc] = NS ? fv_g[cc * KNp + gn] : 0.0f;
-        mixk::node_flux<NS>(qv, dp, pf, fv, F[s]);
+        for (int v = 0; v < V; ++v) qv[v] = v < nvar ? qf_g[v * KNp + gn] : 0.0f;
+        const double p = p_g[gn];
+        mixk::node_flux_mix<V>(qv, nvar, cvt::narrow(p - p_g[g1]), cvt::narrow(p), F[s]);
+      } else {
+        const float4 a0 = c.node[2 * gn], a1 = c.node[2 * gn + 1], r1 = c.node[2 * g1 + 1];
+        const float qv[5] = {a0.x, a0.y, a0.z, a0.w, a1.x};
+        float fv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if constexpr (NS) {
+          const float4 f0 = c.fv4[2 * gn], f1 = c.fv4[2 * gn + 1];
+          fv[0] = f0.x; fv[1] = f0.y; fv[2] = f0.z; fv[3] = f0.w;
+          fv[4] = f1.x; fv[5] = f1.y; fv[6] = f1.z; fv[7] = f1.w;
+          fv[8] = c.fvz[gn];
+        }
+        // p - p_1 from the hi/lo pairs; p itself (energy flux) as its FP32 rounding
+        mixk::node_flux<NS>(qv, (a1.y - r1.y) + (a1.z - r1.z), a1.y, fv, F[s]);
       }
     }
   }
@@ -369,24 +382,31 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       const float fs = G[12 + 4 * f];
       const size_t own = base + (size_t)e * Np + S.fm[mm];
       const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
-      float qm[V], qp[V], g[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        qm[v] = v < nvar ? qf_g[v * KNp + own] : 0.0f;
-        qp[v] = v < nvar ? qf_g[v * KNp + P] : 0.0f;
-      }
-      const double pm64 = p_g[own], pp64 = p_g[P];
-      const float pm = cvt::narrow(pm64), pp = cvt::narrow(pp64), dpn = cvt::narrow(pm64 - pp64);
+      float g[V];
       if constexpr (MIX) {
-        mixk::face_term_mix<V>(qm, qp, nvar, pm, pp, dpn, c.cs[own], c.cs[P], n3, g);
-      } else {
-        float fvm[9], fvp[9];
+        float qm[V], qp[V];
 #pragma unroll
-        for (int cc = 0; cc < 9; ++cc) {
-          fvm[cc] = NS ? fv_g[cc * KNp + own] : 0.0f;
-          fvp[cc] = NS ? fv_g[cc * KNp + P] : 0.0f;
+        for (int v = 0; v < V; ++v) {
+          qm[v] = v < nvar ? qf_g[v * KNp + own] : 0.0f;
+          qp[v] = v < nvar ? qf_g[v * KNp + P] : 0.0f;
         }
-        mixk::face_term<NS>(qm, qp, pm, pp, dpn, fvm, fvp, n3, gam, g);
+        const double pm64 = p_g[own], pp64 = p_g[P];
+        mixk::face_term_mix<V>(qm, qp, nvar, cvt::narrow(pm64), cvt::narrow(pp64), cvt::narrow(pm64 - pp64),
+                               c.cs[own], c.cs[P], n3, g);
+      } else {
+        const float4 m0r = c.node[2 * own], m1r = c.node[2 * own + 1];
+        const float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];
+        const float qm[5] = {m0r.x, m0r.y, m0r.z, m0r.w, m1r.x}, qp[5] = {p0r.x, p0r.y, p0r.z, p0r.w, p1r.x};
+        const float dpn = (m1r.y - p1r.y) + (m1r.z - p1r.z);  // p- - p+ from the hi/lo pairs
+        float fvm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, fvp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if constexpr (NS) {
+          const float4 a = c.fv4[2 * own], b2 = c.fv4[2 * own + 1], cc4 = c.fv4[2 * P], d4 = c.fv4[2 * P + 1];
+          fvm[0] = a.x; fvm[1] = a.y; fvm[2] = a.z; fvm[3] = a.w;
+          fvm[4] = b2.x; fvm[5] = b2.y; fvm[6] = b2.z; fvm[7] = b2.w; fvm[8] = c.fvz[own];
+          fvp[0] = cc4.x; fvp[1] = cc4.y; fvp[2] = cc4.z; fvp[3] = cc4.w;
+          fvp[4] = d4.x; fvp[5] = d4.y; fvp[6] = d4.z; fvp[7] = d4.w; fvp[8] = c.fvz[P];
+        }
+        mixk::face_term<NS>(qm, qp, m1r.y, p1r.y, dpn, fvm, fvp, n3, gam, g);
       }
 #pragma unroll
       for (int v = 0; v < V; ++v)
@@ -531,34 +551,31 @@ struct VCfg {
   static_assert(NOUT <= TMEM_COLS, "TMEM columns");
 };
 
-// Elements [e0, e0 + 25) of case c: viscous flux fv[9][K][Np] from the state qin (rho in FP64),
-// the float state copy (momentum) and the FP64 temperature.
+// Elements [e0, e0 + 25) of case c: the viscous-flux records from the node records (rho and T as
+// hi/lo pairs, momentum) and the temperature pairs.
 template <class C_>
-__device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
-                                         const int e0, uint32_t& phase, unsigned* status, const MixedCase* next,
-                                         const double* next_q, int next_e0) {
+__device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const int e0, uint32_t& phase,
+                                         unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
   const int tid = threadIdx.x;
   const int nel = min(C_::E, c.K - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)c.K * Np;
   const size_t base = (size_t)e0 * Np;
-  const float* __restrict__ qf_g = c.qf;
-  const double* __restrict__ T_g = c.T;
 
   if (tid == 0 && next) {
-    // the next tile's inputs into L2: rho (FP64 state), T, momentum copy, geometry, neighbour map
+    // the next tile's inputs into L2: node records, temperature pairs, geometry, neighbour map
     const int nnel = min(C_::E, next->K - next_e0);
-    const size_t nK = (size_t)next->K * Np, nb = (size_t)next_e0 * Np, nnn = (size_t)nnel * Np;
-    prefetch_l2(next_q + nb, nnn * 8);
-    prefetch_l2(next->T + nb, nnn * 8);
-    for (int d = 1; d < 4; ++d) prefetch_l2(next->qf + d * nK + nb, nnn * 4);
+    const size_t nb = (size_t)next_e0 * Np, nnn = (size_t)nnel * Np;
+    prefetch_l2(next->node + 2 * nb, nnn * 32);
+    prefetch_l2(next->temp + nb, nnn * 8);
     prefetch_l2(next->geo + (size_t)next_e0 * GS, (size_t)nnel * GS * 4);
     prefetch_l2(next->vmapP + (size_t)next_e0 * NF, (size_t)nnel * NF * 4);
   }
   for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
 
-  // volume chunk: (rho - rho_1, m, T - T_1) per node, differences to the element's first node in FP64
+  // volume chunk: (rho - rho_1, m, T - T_1) per node; the differences to the element's first node
+  // from the hi/lo pairs
   float rho_n[NPT], m_n[NPT][3], w_n[NPT][5];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
@@ -566,15 +583,18 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     if (n < nn) {
       const int e = n / Np;
       const size_t gn = base + n, g1 = base + (size_t)e * Np;
-      const double rho = qin[gn];
-      rho_n[s] = cvt::narrow(rho);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) m_n[s][d] = qf_g[(1 + d) * KNp + gn];
-      w_n[s][0] = cvt::narrow(rho - qin[g1]);
-      w_n[s][1] = m_n[s][0];
-      w_n[s][2] = m_n[s][1];
-      w_n[s][3] = m_n[s][2];
-      w_n[s][4] = cvt::narrow(T_g[gn] - T_g[g1]);
+      const float4 a0 = c.node[2 * gn], a1 = c.node[2 * gn + 1];
+      const float4 r0 = c.node[2 * g1], r1 = c.node[2 * g1 + 1];
+      const float2 t = c.temp[gn], t1 = c.temp[g1];
+      rho_n[s] = a0.x;
+      m_n[s][0] = a0.y;
+      m_n[s][1] = a0.z;
+      m_n[s][2] = a0.w;
+      w_n[s][0] = (a0.x - r0.x) + (a1.w - r1.w);
+      w_n[s][1] = a0.y;
+      w_n[s][2] = a0.z;
+      w_n[s][3] = a0.w;
+      w_n[s][4] = (t.x - t1.x) + (t.y - t1.y);
     }
   }
   __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
@@ -598,11 +618,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       const int e = j / w, mm = m0 + (j - e * w);
       const size_t own = base + (size_t)e * Np + S.fm[mm];
       const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
-      float jv[5];
-      jv[0] = cvt::narrow(qin[P] - qin[own]);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) jv[1 + d] = qf_g[(1 + d) * KNp + P] - qf_g[(1 + d) * KNp + own];
-      jv[4] = cvt::narrow(T_g[P] - T_g[own]);
+      const float4 o0 = c.node[2 * own], o1 = c.node[2 * own + 1], q0 = c.node[2 * P], q1 = c.node[2 * P + 1];
+      const float2 to = c.temp[own], tp = c.temp[P];
+      const float jv[5] = {(q0.x - o0.x) + (q1.w - o1.w), q0.y - o0.y, q0.z - o0.z, q0.w - o0.w,
+                           (tp.x - to.x) + (tp.y - to.y)};
 #pragma unroll
       for (int f = 0; f < 5; ++f)
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, mm - m0, C_::A_LBO, C_::A_SBO), jv[f]);
@@ -656,8 +675,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     if (n < nn) {
       float f9[9];
       mixk::viscous_flux_node(rho_n[s], m_n[s], grad[s], mu, kap, f9);
-#pragma unroll
-      for (int cc = 0; cc < 9; ++cc) c.fv[cc * KNp + base + n] = f9[cc];
+      const size_t gn = base + n;
+      c.fv4[2 * gn] = make_float4(f9[0], f9[1], f9[2], f9[3]);
+      c.fv4[2 * gn + 1] = make_float4(f9[4], f9[5], f9[6], f9[7]);
+      c.fvz[gn] = f9[8];
     }
   }
   // clear the accumulator copy (see rhs_tile); the last barrier above ordered its reads
@@ -678,7 +699,7 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_kernel(const M
   uint32_t phase = 0;
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
     const int ne0 = e0 + gridDim.x * C_::E;
-    if (!vis_tile<C_>(S, c, c.q[0], e0, phase, status, ne0 < c.K ? &c : nullptr, c.q[0], ne0)) break;
+    if (!vis_tile<C_>(S, c, e0, phase, status, ne0 < c.K ? &c : nullptr, ne0)) break;
   }
   block_teardown<C_>(S, phase);
 }
@@ -701,8 +722,7 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_batched(const 
     const MixedCase& c = cases[it.x];
     const int wn = w + gridDim.x;
     const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
-    const MixedCase* nc = wn < nwork ? &cases[nx.x] : nullptr;
-    if (!vis_tile<C_>(S, c, c.q[stage & 1], it.y, phase, status, nc, nc ? nc->q[stage & 1] : nullptr, nx.y)) break;
+    if (!vis_tile<C_>(S, c, it.y, phase, status, wn < nwork ? &cases[nx.x] : nullptr, nx.y)) break;
   }
   block_teardown<C_>(S, phase);
 }

@@ -234,21 +234,7 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
     if (e == cudaSuccess) e = cudaMalloc((void**)&k, sizeof(double) * n);
     if (e == cudaSuccess) b->owned.push_back(k);
     if (e != cudaSuccess) break;
-    const dg::mixk::MixedScratch sc = dg::mixk::mixed_scratch(m.scratch, (size_t)m.K * m.Np);
-    dg::mixk::MixedCase c;
-    c.q[0] = in[i].q_dev;
-    c.q[1] = work;
-    c.k = k;
-    c.qf = sc.qf;
-    c.p = sc.p;
-    c.T = sc.T;
-    c.fv = sc.fv;
-    c.geo = m.geo32;
-    c.vmapP = m.vmapP;
-    c.K = m.K;
-    c.Np = m.Np;
-    c.dt = in[i].dt;
-    c.gas = dg::mixk::MixedGas{gp.gamma, gp.R, gp.mu, gp.kappa, 1.0 / gp.R};
+    dg::mixk::MixedCase c = dg::make_mixed_case(m, gp, in[i].q_dev, work, k, in[i].dt);
     b->cases.push_back(c);
     b->meshes.push_back(in[i].mesh);
   }

@@ -15,21 +15,18 @@ void free_mixed_ops(MeshDev& m) {
 
 mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const double* qin, double* out, double* k,
                                 double dt) {
-  mixk::MixedCase c;
+  mixk::MixedCase c{};
   c.q[0] = const_cast<double*>(qin);
   c.q[1] = out;
   c.k = k;
   if (g.model == DG_GAS_NASA7) {
     mixk::mixed_scratch_mixture(m.scratch, (size_t)m.K * m.Np, &c.qf, &c.cs, &c.p);
-    c.T = nullptr;
-    c.fv = nullptr;
   } else {
-    const mixk::MixedScratch sc = mixk::mixed_scratch(m.scratch, (size_t)m.K * m.Np);
-    c.qf = sc.qf;
-    c.p = sc.p;
-    c.T = sc.T;
-    c.fv = sc.fv;
-    c.cs = nullptr;
+    const mixk::NodeTables t = mixk::node_tables(m.scratch, (size_t)m.K * m.Np);
+    c.node = t.node;
+    c.fv4 = t.fv4;
+    c.fvz = t.fvz;
+    c.temp = t.temp;
   }
   c.nvar = 5 + g.ns;
   c.geo = m.geo32;
