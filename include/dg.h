@@ -351,6 +351,10 @@ int dg_batch_free(dg_batch batch);
  * x, y: device arrays of n elements (n >= 0), asynchronous on stream. */
 int dg_round_to_float(const double* x_dev, float* y_dev, int64_t n, void* stream);
 int dg_widen_to_double(const float* x_dev, double* y_dev, int64_t n, void* stream);
+/* hi[i] = x[i] rounded to FP32 as dg_round_to_float, lo[i] = (x[i] - hi[i]) rounded to FP32 (the
+ * float pair, ~48 significant bits, in which the mixed form keeps density, pressure and
+ * temperature); hi, lo: device arrays of n floats. */
+int dg_split_to_float_pair(const double* x_dev, float* hi_dev, float* lo_dev, int64_t n, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* dg_last_error(void);

@@ -115,6 +115,8 @@ SIGNATURES = {
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_round_to_float": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "dg_widen_to_double": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "dg_split_to_float_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, []),
 }
 

@@ -48,5 +48,24 @@ __device__ __forceinline__ float narrow(double x) {
   return __double2float_rn(x);             // subnormal results, overflow, infinities, NaN
 }
 
+// x = hi + lo with hi = narrow(x) and lo = the residual x - hi rounded to nearest: about 48
+// significant bits as a float pair.  The residual is exact in binary64 and is, in units of x's
+// last place, the 29 fraction bits that narrowing dropped (less 2^29 when it rounded up); it is
+// formed from them with integer operations, converted to FP32 (the rounding of the residual) and
+// scaled by a power of two.  Exponents outside [2^-74, 2^127) use the FP64 subtraction and the
+// hardware widening.
+__device__ __forceinline__ float2 split(double x) {
+  const float hi = narrow(x);
+  const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+  const uint32_t e = (xh >> 20) & 0x7ffu;
+  if (e - 949u > 1150u - 949u) return make_float2(hi, narrow(x - (double)hi));  // hi may be subnormal here
+  const uint32_t low = xl & 0x1fffffffu;                                   // dropped fraction bits
+  const uint32_t up = ((xl >> 28) & 1u) & (((xl & 0x0fffffffu) != 0u) | ((xl >> 29) & 1u));
+  const int r = up ? (int)low - (1 << 29) : (int)low;                       // residual / ulp(x), exact
+  const float scale = __uint_as_float((e - 1075u + 127u) << 23);          // 2^(e - 1075), a normal float
+  const float lo = __int2float_rn(r) * scale;
+  return make_float2(hi, (xh >> 31) ? -lo : lo);
+}
+
 }  // namespace cvt
 }  // namespace dg

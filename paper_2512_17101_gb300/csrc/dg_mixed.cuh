@@ -60,11 +60,8 @@ __host__ __device__ inline NodeTables node_tables(double* base, size_t KNp) {
   return t;
 }
 
-// x = hi + lo with hi = x rounded to FP32 and lo the rest rounded to FP32 (integer-pipe conversions).
-__device__ __forceinline__ float2 split2(double x) {
-  const float hi = cvt::narrow(x);
-  return make_float2(hi, cvt::narrow(x - cvt::widen(hi)));
-}
+// x = hi + lo with hi = x rounded to FP32 and lo the rest rounded to FP32 (integer pipe, dg_cvt.cuh).
+__device__ __forceinline__ float2 split2(double x) { return cvt::split(x); }
 
 // One case of the mixed form: its state buffers (q[0] in, q[1] out for a single
 // stage; the two alternate over the stages of a batched step), RK register,

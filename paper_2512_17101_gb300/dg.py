@@ -251,6 +251,13 @@ def dg_widen_to_double(x, y, stream=None):
                                     _stream_ptr(stream)))
 
 
+def dg_split_to_float_pair(x, hi, lo, stream=None):
+    """hi, lo = the library's float-pair representation of x (float64 -> two float32 CUDA tensors)."""
+    import torch
+    check(load().dg_split_to_float_pair(_dptr(x, torch.float64, "x"), _dptr(hi, torch.float32, "hi"),
+                                        _dptr(lo, torch.float32, "lo"), x.numel(), _stream_ptr(stream)))
+
+
 def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, stream=None):
     """Allocation-free viscous stage on caller-owned tables.
 

@@ -58,3 +58,21 @@ def test_widen_to_double_matches_hardware():
     keep = ~nan & ~sub
     assert bool(torch.equal(y.view(torch.int64)[keep], want.view(torch.int64)[keep]))
     assert bool((y[sub] == 0).all()) and bool(torch.equal(torch.signbit(y[sub]), torch.signbit(x[sub])))
+
+
+def test_split_to_float_pair_matches_fp64_residual():
+    """hi = x rounded to FP32, lo = (x - hi) rounded to FP32, the residual taken in FP64."""
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    x = torch.tensor(_doubles(), device="cuda")
+    keep = torch.isfinite(x) & (x.float().abs() < 3.0e38)
+    x = x[keep].contiguous()
+    hi = torch.empty(x.numel(), device="cuda", dtype=torch.float32)
+    lo = torch.empty_like(hi)
+    dg.dg_split_to_float_pair(x, hi, lo)
+    want_hi = x.float()
+    want_lo = (x - want_hi.double()).float()
+    assert bool(torch.equal(hi.view(torch.int32), want_hi.view(torch.int32)))
+    # signed zeros of the residual may differ; compare values
+    bad = lo != want_lo
+    assert not bool(bad.any()), (x[bad][:5].tolist(), lo[bad][:5].tolist(), want_lo[bad][:5].tolist())
