@@ -86,13 +86,11 @@ cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q,
 cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
-// Outputs of the mixed-precision form that the temperature solve also writes (all null: none):
-// float state copy [5 + ns][n], FP64 pressure [n], float sound speed [n]; rho <= 0 or p <= 0
-// sets DG_STATUS_NONPHYSICAL in *status.
+// Outputs of the mixed-precision form that the temperature solve also writes (rec null: none):
+// the node records [n][4] float4 {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, c},
+// {rho Y_1..4}, {rho Y_5..8}; rho <= 0 or p <= 0 sets DG_STATUS_NONPHYSICAL in *status.
 struct MixturePrims {
-  float* qf = nullptr;
-  double* p = nullptr;
-  float* cs = nullptr;
+  float4* rec = nullptr;
   unsigned* status = nullptr;
 };
 // The mesh scratch's mixture tables (k_mixed.cu).

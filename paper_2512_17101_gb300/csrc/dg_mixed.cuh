@@ -78,10 +78,8 @@ struct MixedCase {
   float4* fv4;
   float* fvz;
   float2* temp;
-  // mixture: float state copy [nvar][KNp], FP64 pressure, sound speed
-  float* qf;
-  double* p;
-  float* cs;
+  // mixture: node records (see mixture_records)
+  float4* mrec;
   const float* geo;
   const int32_t* vmapP;
   int K;
@@ -91,18 +89,13 @@ struct MixedCase {
   MixedGas gas;
 };
 
-// Per-node tables of the mixed form for a mixture (64 of the scratch's 80 bytes per node):
-// float state copy [MIX_V][KNp], float sound speed [KNp], FP64 pressure [KNp]; written by the
-// temperature Newton kernels at the converged temperature (dg_newton.cuh).
+// Per-node record of the mixed form for a mixture (64 of the scratch's 80 bytes per node), written
+// by the temperature Newton kernels at the converged temperature (dg_newton.cuh):
+//   [KNp][4] float4: {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, c},
+//                    {rho Y_1 .. rho Y_4}, {rho Y_5 .. rho Y_8}   (absent species 0)
 constexpr int MIX_V = 5 + DG_MAX_SPECIES;
-__host__ __device__ inline void mixed_scratch_mixture(double* base, size_t KNp, float** qf, float** cs, double** p) {
-  float* f = reinterpret_cast<float*>(base);
-  *qf = f;
-  *cs = f + MIX_V * KNp;
-  *p = reinterpret_cast<double*>(f + (MIX_V + 1) * KNp);
-}
-static_assert((MIX_V + 1) % 2 == 0, "the FP64 pressure must start on an 8-byte boundary");
-static_assert((MIX_V + 1) * 4 + 8 <= 80, "the mixture tables must fit the 80-byte scratch");
+static_assert(MIX_V <= 13, "the mixture record holds up to 8 species");
+__host__ __device__ inline float4* mixture_records(double* base) { return reinterpret_cast<float4*>(base); }
 
 // ---- pass 0: per node, FP64 pressure (and temperature) and the node record, so that the later
 // kernels read traces without recomputing or converting them.

@@ -59,18 +59,32 @@ __device__ __forceinline__ bool solve(const double c[6], double e, double& t, in
   return false;
 }
 
-// The mixed-precision form's node outputs from the converged temperature t (cv at the last
-// iterate): float copy of the state, FP64 p = rho R_mix t, sound speed from c^2 formed in FP64
-// and rounded once.
+// The mixed-precision form's node record from the converged temperature t (cv at the last
+// iterate): the float state, p = rho R_mix t as a float pair, and the sound speed from c^2 formed
+// in FP64 and rounded once.
 __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasParams& g, const double* __restrict__ q,
                                             int64_t n, int64_t node, double rho, double Rmix, double t, double cv) {
   const int nvar = 5 + g.ns;
-  for (int v = 0; v < nvar; ++v) mp.qf[v * n + node] = cvt::narrow(q[v * n + node]);
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+  const float2 rho2 = cvt::split(rho);
   const double p = rho * Rmix * t;
-  if (!(cvt::narrow(rho) > 0.0f) || !(cvt::narrow(p) > 0.0f)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
-  mp.p[node] = p;
+  const float2 p2 = cvt::split(p);
+  if (!(rho2.x > 0.0f) || !(p2.x > 0.0f)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
+  v[0] = rho2.x;
+  for (int j = 1; j < 4; ++j) v[j] = cvt::narrow(q[j * n + node]);
+  v[4] = cvt::narrow(q[4 * n + node]);
+  v[5] = p2.x;
+  v[6] = p2.y;
   const double c2 = Rmix * t * fma(Rmix, rcp64(cv), 1.0);
-  mp.cs[node] = sqrtf(cvt::narrow(c2));
+  v[7] = sqrtf(cvt::narrow(c2));
+  for (int k = 0; k < nvar - 5; ++k) v[8 + k] = cvt::narrow(q[(5 + k) * n + node]);
+  float4* r = mp.rec + 4 * node;
+  r[0] = make_float4(v[0], v[1], v[2], v[3]);
+  r[1] = make_float4(v[4], v[5], v[6], v[7]);
+  r[2] = make_float4(v[8], v[9], v[10], v[11]);
+  r[3] = make_float4(v[12], v[13], v[14], v[15]);
 }
 
 }  // namespace newton

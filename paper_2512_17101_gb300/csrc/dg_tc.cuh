@@ -112,9 +112,7 @@ __device__ __forceinline__ void prefetch_tile_inputs(const MixedCase& c, int e0,
                                                      bool ns) {
   const size_t KNp = (size_t)c.K * Np, base = (size_t)e0 * Np, nn = (size_t)nel * Np;
   if (mix) {
-    for (int v = 0; v < c.nvar; ++v) prefetch_l2(c.qf + v * KNp + base, nn * 4);
-    prefetch_l2(c.p + base, nn * 8);
-    prefetch_l2(c.cs + base, nn * 4);
+    prefetch_l2(c.mrec + 4 * base, nn * 64);
   } else {
     prefetch_l2(c.node + 2 * base, nn * 32);
     if (ns) {
@@ -290,21 +288,28 @@ __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& ph
 
 // Elements [e0, e0 + 25) of case c: right-hand side (RK = false: out = rhs) or the LSRK stage
 // (k <- a k + dt rhs, out <- qin + b k).  Returns false when the block must stop (timeout).
+// A mixture node's float state (13 values, absent species 0) from its record; returns p_hi.
+__device__ __forceinline__ float load_mix_record(const float4* r, float* q) {
+  const float4 a = r[0], b = r[1], c = r[2], d = r[3];
+  q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w; q[4] = b.x;
+  q[5] = c.x; q[6] = c.y; q[7] = c.z; q[8] = c.w;
+  q[9] = d.x; q[10] = d.y; q[11] = d.z; q[12] = d.w;
+  return b.y;
+}
+
 template <class C_, int PHYS, bool RK>
 __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
                                          uint32_t& phase, unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT, V = C_::V;
   constexpr bool NS = PHYS == kern::NAVIER_STOKES, MIX = PHYS == kern::MIXTURE;
-  static_assert(MIX || V == 5, "a perfect gas has 5 conserved variables");
+  static_assert(MIX ? V == mixk::MIX_V : V == 5, "5 conserved variables, or the 13 of a mixture record");
   const int tid = threadIdx.x;
   const int nvar = MIX ? c.nvar : 5;
   const int nel = min(C_::E, c.K - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)c.K * Np;
   const size_t base = (size_t)e0 * Np;
-  const float* __restrict__ qf_g = c.qf;  // mixture tables
-  const double* __restrict__ p_g = c.p;
 
   if (tid == 0) {
     // this tile's RK inputs (read only in the epilogue) and the next tile's inputs, into L2
@@ -330,10 +335,10 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       const size_t gn = base + n, g1 = base + (size_t)e * Np;
       if constexpr (MIX) {
         float qv[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) qv[v] = v < nvar ? qf_g[v * KNp + gn] : 0.0f;
-        const double p = p_g[gn];
-        mixk::node_flux_mix<V>(qv, nvar, cvt::narrow(p - p_g[g1]), cvt::narrow(p), F[s]);
+        const float4 ref = c.mrec[4 * g1 + 1];
+        const float p1 = load_mix_record(c.mrec + 4 * gn, qv);
+        const float p_lo = c.mrec[4 * gn + 1].z;
+        mixk::node_flux_mix<V>(qv, nvar, (p1 - ref.y) + (p_lo - ref.z), p1, F[s]);
       } else {
         const float4 a0 = c.node[2 * gn], a1 = c.node[2 * gn + 1], r1 = c.node[2 * g1 + 1];
         const float qv[5] = {a0.x, a0.y, a0.z, a0.w, a1.x};
@@ -385,14 +390,10 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       float g[V];
       if constexpr (MIX) {
         float qm[V], qp[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          qm[v] = v < nvar ? qf_g[v * KNp + own] : 0.0f;
-          qp[v] = v < nvar ? qf_g[v * KNp + P] : 0.0f;
-        }
-        const double pm64 = p_g[own], pp64 = p_g[P];
-        mixk::face_term_mix<V>(qm, qp, nvar, cvt::narrow(pm64), cvt::narrow(pp64), cvt::narrow(pm64 - pp64),
-                               c.cs[own], c.cs[P], n3, g);
+        const float4 am = c.mrec[4 * own + 1], ap = c.mrec[4 * P + 1];  // {rho E, p_hi, p_lo, c}
+        load_mix_record(c.mrec + 4 * own, qm);
+        load_mix_record(c.mrec + 4 * P, qp);
+        mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, g);
       } else {
         const float4 m0r = c.node[2 * own], m1r = c.node[2 * own + 1];
         const float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];

@@ -20,7 +20,7 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
   c.q[1] = out;
   c.k = k;
   if (g.model == DG_GAS_NASA7) {
-    mixk::mixed_scratch_mixture(m.scratch, (size_t)m.K * m.Np, &c.qf, &c.cs, &c.p);
+    c.mrec = mixk::mixture_records(m.scratch);
   } else {
     const mixk::NodeTables t = mixk::node_tables(m.scratch, (size_t)m.K * m.Np);
     c.node = t.node;
@@ -52,7 +52,7 @@ cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const doubl
 
 MixturePrims mixture_prims_out(const MeshDev& m) {
   MixturePrims mp;
-  mixk::mixed_scratch_mixture(m.scratch, (size_t)m.K * m.Np, &mp.qf, &mp.cs, &mp.p);
+  mp.rec = mixk::mixture_records(m.scratch);
   mp.status = m.status;
   return mp;
 }

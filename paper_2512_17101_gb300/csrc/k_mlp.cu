@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
     if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
     T[node] = t;
     if (iters) iters[node] = it;
-    if (mp.qf) newton::store_prims(mp, g, q, n, node, rho, Rmix, t, cv);
+    if (mp.rec) newton::store_prims(mp, g, q, n, node, rho, Rmix, t, cv);
   }
 }
 

@@ -31,7 +31,7 @@ __global__ void temperature_kernel(const GasParams g, const int64_t n, const dou
     if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
     T[i] = t;
     if (iters) iters[i] = it;
-    if (mp.qf) newton::store_prims(mp, g, q, n, i, rho, Rmix, t, cv);
+    if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, Rmix, t, cv);
   }
 }
 
