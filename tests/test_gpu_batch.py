@@ -78,3 +78,25 @@ def test_batch_against_oracle():
             f = lambda u: rhs_strong(d.ref, d.geo, d.conn, u, PerfectGas(g.gamma, g.R))
         want = lsrk4_step(c["q"], dt, f)
         assert field_err(q.cpu().numpy(), want) <= 1e-6
+
+
+@pytest.mark.slow
+def test_full_batched_workload_equals_single_case_stages():
+    """The benchmark's batch (64 cases, n ~ U{2..20}, N ~ U{1..4}, seed 0), autotuned: one graph
+    launch per RK4 step equals the same mixed stages case by case."""
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import capi, dg
+    cases = batched_cases(ncases=64, seed=0)
+    hs = _handles(torch, dg, cases)
+    batch = dg.Batch(hs, autotune=True)
+    opts = dg._opts(precision=capi.DG_PREC_MIXED)
+    refs = []
+    for (mesh, gas, dt, q), c in zip(hs, cases):
+        qr = torch.tensor(c["q"], device="cuda")
+        dg.lsrk4_step(mesh, gas, qr, dt, steps=1, opts=opts)
+        refs.append(qr)
+    batch.step(1)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for (mesh, gas, dt, q), qr in zip(hs, refs):
+        assert float((q - qr).abs().max()) <= 1e-12 * float(qr.abs().max())

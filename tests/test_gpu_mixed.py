@@ -210,3 +210,38 @@ def test_mixed_precision_plus_learned_guess_step():
         want = lsrk4_step(want, dt, f)
     assert field_err(q.cpu().numpy(), want) <= STATE_TOL
     assert mesh.status() == 0 and gas.status() == 0
+
+
+@pytest.mark.slow
+def test_mixed_plus_learned_full_size_against_fp64_path():
+    """Full-size learned-form workload: one RK4 step of the mixed-precision plus learned-guess path
+    against the FP64 path (which matches the oracle, test_gpu_parity), per field."""
+    from workloads.configs import build_case, get_config
+    cfg = get_config("mixture_learned")
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import capi, dg
+    case = build_case(cfg)
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    mix = case["mixture"]
+    gas_o = Nasa7Gas(W=mix.W, coeffs=mix.coeffs)
+    gas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs, newton_tol=1e-10, newton_max_it=50)
+    T, Y = temperature_samples(50_000, 7, seed=11)
+    Td, Yd = torch.tensor(T, device="cuda"), torch.tensor(Y, device="cuda")
+    e = torch.empty_like(Td)
+    dg.dg_mixture_energy(gas, Td, Yd, e)
+    qs = torch.zeros((12, T.size), device="cuda", dtype=torch.float64)
+    qs[0], qs[4], qs[5:] = 1.0, e, Yd
+    Tn = torch.full_like(Td, 1650.0)
+    dg.dg_temperature(gas, qs, Tn)
+    dg.dg_mlp_train(gas, e, Yd, Tn, glorot_params(0), epochs=5, batch=1024, lr=3e-3, lr_decay=0.9)
+    rho = case["p0"] / (gas_o.R_mix(case["Y"]) * case["T"])
+    q0 = gas_o.conserved(rho, case["vel"], case["Y"], case["T"])
+    q64, qmx = torch.tensor(q0, device="cuda"), torch.tensor(q0, device="cuda")
+    T64 = torch.full(q0.shape[1:], 1650.0, device="cuda", dtype=torch.float64)
+    Tmx = T64.clone()
+    dg.lsrk4_step(mesh, gas, q64, cfg.dt, steps=cfg.steps, T_io=T64,
+                  opts=dg._opts(t_seed=capi.DG_TSEED_CONST, t_const=1650.0))
+    dg.lsrk4_step(mesh, gas, qmx, cfg.dt, steps=cfg.steps, T_io=Tmx,
+                  opts=dg._opts(precision=capi.DG_PREC_MIXED, t_seed=capi.DG_TSEED_MLP))
+    assert field_err(qmx.cpu().numpy(), q64.cpu().numpy()) <= STATE_TOL
+    assert mesh.status() == 0 and gas.status() == 0

@@ -254,3 +254,31 @@ def test_discrete_conservation_on_gpu():
     dg.dg_rhs(mesh, gas, q, rhs)
     r = rhs.cpu().numpy()
     assert np.all(np.abs(d.integrate(r)) <= 1e-12 * d.abs_integral(r))
+
+
+@pytest.mark.slow
+def test_mixture_learned_full_size_stage():
+    """Full-size learned-form workload (32^3 x 6 = 196,608 tets, N = 2, 7 species): the FP64 stage
+    against the oracle, temperatures from Newton on both sides."""
+    from workloads.configs import build_case, get_config
+    cfg = get_config("mixture_learned")
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    case = build_case(cfg)
+    d = Disc(case["vertices"], case["period"], cfg.N)
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    mix = case["mixture"]
+    gas_o = Nasa7Gas(W=mix.W, coeffs=mix.coeffs)
+    gas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs, newton_tol=1e-10, newton_max_it=50)
+    rho = case["p0"] / (gas_o.R_mix(case["Y"]) * case["T"])
+    q0 = gas_o.conserved(rho, case["vel"], case["Y"], case["T"])
+    q_in = torch.tensor(q0, device="cuda")
+    q_out, k = torch.empty_like(q_in), torch.zeros_like(q_in)
+    T = torch.full(q0.shape[1:], 1650.0, device="cuda", dtype=torch.float64)
+    dg.dg_rk_stage(mesh, gas, 0, cfg.dt, q_in, q_out, k, T_io=T)
+    _, _, Y, e = gas_o.split_state(q0)
+    Tw, _, ok = gas_o.newton_temperature(e, Y, np.full(e.shape, 1650.0))
+    assert ok.all()
+    rhs_want = rhs_strong(d.ref, d.geo, d.conn, q0, gas_o, T=Tw)
+    assert rel_err(k.cpu().numpy(), cfg.dt * rhs_want) <= TOL
+    assert mesh.status() == 0 and gas.status() == 0
