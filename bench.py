@@ -41,9 +41,9 @@ MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     ("7ae1f260473cc60c", "rhs"): 290.224896e6 + 105.554176e6,  # profiles/ns_N3_K82944_fp64.md
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("a3ea87baf3de95b6", "mixed_rhs"): 250.168320e6 + 118.326016e6,
-    ("a3ea87baf3de95b6", "mixed_viscous"): 70.415360e6 + 19.955456e6,
-    ("a3ea87baf3de95b6", "mixed_prims"): 66.374656e6 + 16.314112e6,
+    ("2ba9f488305c1d84", "mixed_rhs"): 256.088320e6 + 119.813376e6,
+    ("2ba9f488305c1d84", "mixed_viscous"): 90.063616e6 + 26.145024e6,
+    ("2ba9f488305c1d84", "mixed_prims"): 66.374912e6 + 14.992128e6,
 }
 
 
