@@ -1,0 +1,162 @@
+"""Oracle of nodal DG on tensor-product hexahedra (the paper's element type in its timed runs,
+§5.2-§5.4: "tensor product elements"), Euler equations of a perfect gas.  Test infrastructure
+only: imported by tests/, __graft_entry__.smoke() and bench.py's CPU legs, never by the library.
+
+The paper prints none of the discretisation; this follows the collocated nodal spectral-element
+DG on Gauss-Lobatto-Legendre points, written from its definitions:
+
+* 1-D nodal basis l_i through the given node set x_0 < ... < x_N on [-1, 1];
+  quadrature weights w_i = integral of l_i over [-1, 1] (exact polynomial integration);
+  differentiation matrix D[i][j] = l_j'(x_i).  Evaluated in 40-digit arithmetic (mpmath) and
+  rounded once.
+* element [x0, x0 + h_x] x ... mapped from [-1, 1]^3: d/dx = (2 / h_x) d/dr; mass matrix
+  collocated (diagonal J w_i w_j w_k); face integrals collocated at the face nodes.
+* strong form, per conserved variable:
+    dq/dt = - sum_d (2/h_d) D_d F_d(q) + sum over the faces f the node lies on of
+            (2/h_d(f)) / w_end (n_f . F(q-) - F*_f),
+  with the local Lax-Friedrichs flux n.F* = (n.F(q-) + n.F(q+))/2 + lambda (q- - q+)/2,
+  lambda = max(|u-.n| + c-, |u+.n| + c+) at the face node; q+ is the neighbour's node at the
+  same position on the shared face (periodic box).
+* weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
+  with the summation-by-parts identity W D + D^T W = diag(-1, 0, ..., 0, 1) it equals the
+  strong form up to rounding.
+
+Arrays: q[V][K][Np], node index n = i + (N+1)(j + (N+1)k); element index ex + nx(ey + ny ez).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import mpmath
+import numpy as np
+
+from .euler import euler_flux
+
+
+@dataclass
+class HexRef:
+    N: int
+    nodes: np.ndarray  # [N+1]
+    w: np.ndarray      # [N+1] quadrature weights
+    D: np.ndarray      # [N+1][N+1], D[i][j] = l_j'(x_i)
+
+
+def hex_reference(x1d) -> HexRef:
+    x1d = np.asarray(x1d, dtype=np.float64)
+    m = x1d.size
+    with mpmath.workdps(40):
+        xs = [mpmath.mpf(float(v)) for v in x1d]
+        w = []
+        D = [[mpmath.mpf(0)] * m for _ in range(m)]
+        for j in range(m):
+            # l_j as a polynomial: coefficients (ascending) of prod_{k != j} (x - x_k) / (x_j - x_k)
+            coeff = [mpmath.mpf(1)]
+            den = mpmath.mpf(1)
+            for k in range(m):
+                if k == j:
+                    continue
+                coeff = [mpmath.mpf(0)] + coeff  # multiply by x
+                for a in range(len(coeff) - 1):
+                    coeff[a] -= xs[k] * coeff[a + 1]
+                den *= xs[j] - xs[k]
+            coeff = [c / den for c in coeff]
+            # integral over [-1, 1]: sum c_a (1 - (-1)^(a+1)) / (a+1)
+            w.append(sum(c * (1 - (-1) ** (a + 1)) / (a + 1) for a, c in enumerate(coeff)))
+            dcoeff = [a * coeff[a] for a in range(1, len(coeff))]
+            for i in range(m):
+                D[i][j] = sum(c * xs[i] ** a for a, c in enumerate(dcoeff))
+        w = np.array([float(v) for v in w])
+        D = np.array([[float(D[i][j]) for j in range(m)] for i in range(m)])
+    return HexRef(N=m - 1, nodes=x1d, w=w, D=D)
+
+
+def _along(M, a, axis):
+    """Apply the 1-D matrix M along tensor axis `axis` (0 = i/x, 1 = j/y, 2 = k/z) of a[..., k, j, i]."""
+    ax = {0: -1, 1: -2, 2: -3}[axis]
+    a = np.moveaxis(a, ax, -1)
+    out = a @ M.T
+    return np.moveaxis(out, -1, ax)
+
+
+def _shape(q, N):
+    V, K = q.shape[:2]
+    return q.reshape(V, K, N + 1, N + 1, N + 1)  # [V][K][k][j][i]
+
+
+def _neighbour(box, axis, step):
+    """Element index of the periodic neighbour of every element along axis (step = +-1)."""
+    nx, ny, nz = box["n"]
+    e = np.arange(nx * ny * nz)
+    ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+    c = [ex, ey, ez]
+    c[axis] = (c[axis] + step) % box["n"][axis]
+    return c[0] + nx * (c[1] + ny * c[2])
+
+
+def _face_slices(N, axis, end):
+    """Index tuple selecting the face (axis, end) of a [..., k, j, i] array; end 0 = minus face."""
+    idx = [slice(None)] * 3
+    idx[2 - axis] = 0 if end == 0 else N
+    return (Ellipsis,) + tuple(idx)
+
+
+def _surface_terms(ref, box, q5, gas):
+    """Per face (axis, end): (selector, lifting factor, n.F(q-), n.F*) at the face nodes."""
+    N = ref.N
+    out = []
+    for axis in range(3):
+        for end in (0, 1):
+            sign = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, axis, -1 if end == 0 else 1)
+            qm = q5[_face_slices(N, axis, end)]             # [V][K][face]
+            qp = q5[:, nb][_face_slices(N, axis, 1 - end)]  # the neighbour's opposite face
+            pm, cm = gas.pressure_sound_speed(qm)
+            pp, cp = gas.pressure_sound_speed(qp)
+            fm = sign * euler_flux(qm, pm)[axis]
+            fp = sign * euler_flux(qp, pp)[axis]
+            lam = np.maximum(np.abs(sign * qm[1 + axis] / qm[0]) + cm, np.abs(sign * qp[1 + axis] / qp[0]) + cp)
+            fstar = 0.5 * (fm + fp) + 0.5 * lam[None] * (qm - qp)
+            lift = (2.0 / box["h"][axis]) / ref.w[0 if end == 0 else N]
+            out.append((_face_slices(N, axis, end), lift, fm, fstar))
+    return out
+
+
+def _volume_fluxes(q5, gas):
+    return list(euler_flux(q5, gas.pressure(q5)))
+
+
+def hex_rhs_strong(ref, box, q, gas):
+    """Strong-form right-hand side, q[5][K][Np] -> rhs[5][K][Np]."""
+    N = ref.N
+    q5 = _shape(np.asarray(q, dtype=np.float64), N)
+    F = _volume_fluxes(q5, gas)
+    rhs = np.zeros_like(q5)
+    for d in range(3):
+        rhs -= (2.0 / box["h"][d]) * _along(ref.D, F[d], d)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+        rhs[sel] += lift * (fm - fstar)
+    return rhs.reshape(q.shape)
+
+
+def hex_rhs_weak(ref, box, q, gas):
+    """Weak-form right-hand side (the cross-check of the strong form)."""
+    N = ref.N
+    q5 = _shape(np.asarray(q, dtype=np.float64), N)
+    F = _volume_fluxes(q5, gas)
+    Wi = np.diag(1.0 / ref.w)
+    Mt = Wi @ ref.D.T @ np.diag(ref.w)
+    rhs = np.zeros_like(q5)
+    for d in range(3):
+        rhs += (2.0 / box["h"][d]) * _along(Mt, F[d], d)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+        rhs[sel] -= lift * fstar
+    return rhs.reshape(q.shape)
+
+
+def hex_integrate(ref, box, u):
+    """sum over elements of J sum_nodes w_i w_j w_k u, for u[..., K, Np]."""
+    N = ref.N
+    w3 = (ref.w[None, None, :] * ref.w[None, :, None] * ref.w[:, None, None]).ravel()  # [Np] with k, j, i
+    J = np.prod(box["h"]) / 8.0
+    return J * np.tensordot(u, w3, axes=([-1], [0])).sum(axis=-1)
