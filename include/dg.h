@@ -339,6 +339,40 @@ int dg_batch_tiles(dg_batch batch, int32_t* rhs_tiles_host, int32_t* viscous_til
 int dg_batch_status(dg_batch batch, uint32_t* bits, int reset);
 int dg_batch_free(dg_batch batch);
 
+/* ---- tensor-product hexahedra ---------------------------------------------------------------
+ * Nodal DG on a periodic box of axis-aligned hexahedra with tensor-product nodes, the element
+ * type of the paper's timed runs (Sec. 5.2-5.4, "tensor product elements"); Euler equations of a
+ * perfect gas in FP64, the same local Lax-Friedrichs flux and fused LSRK4 stage as the
+ * tetrahedral path.  Collocated nodal spectral-element DG: quadrature weights w_i = integral of the
+ * 1-D Lagrange basis through the node set, D[i][j] = l_j'(x_i), diagonal mass,
+ *   rhs = - sum_d (2/h_d) D_d F_d + sum over the faces of a node (2/h_d) / w_end (n.F- - n.F*),
+ * applied by sum factorisation.  State layout [5][K][(N+1)^3], node index i + (N+1)(j + (N+1)k)
+ * (i along x fastest), element index ex + nx (ey + ny ez); element (ex, ey, ez) spans
+ * [ex h_x, (ex+1) h_x] x ... with h = L / n. */
+typedef struct dg_hex_mesh_s* dg_hex_mesh;
+typedef struct {
+  int32_t n[3];            /* hexahedra per direction, >= 1                                   */
+  double L[3];             /* box lengths, > 0                                                */
+  int32_t N;               /* order, 1..DG_MAX_ORDER                                          */
+  const double* nodes1d;   /* host [N+1]: the 1-D node set, ascending, first -1 and last 1
+                              (copied; Gauss-Lobatto-Legendre points in the workloads)        */
+} dg_hex_desc;
+/* Builds the 1-D operators on the host and uploads them.  Errors: DG_ERR_INVALID_ARG (sizes,
+ * node set), DG_ERR_CUDA. */
+int dg_hex_mesh_create(const dg_hex_desc* desc, dg_hex_mesh* out);
+int dg_hex_mesh_free(dg_hex_mesh mesh);
+/* Host copies of the library's 1-D operators: D_host [N+1][N+1] row-major, w_host [N+1]
+ * (either may be NULL). */
+int dg_hex_operators(dg_hex_mesh mesh, double* D_host, double* w_host);
+/* rhs = right-hand side of q (device arrays [5][K][Np], caller-owned, not overlapping); the gas
+ * must be a perfect gas with mu = 0 (else DG_ERR_UNSUPPORTED).  Asynchronous on stream. */
+int dg_hex_rhs(dg_hex_mesh mesh, dg_gas gas, const double* q_dev, double* rhs_dev, void* stream);
+/* LSRK4 stage (as dg_rk_stage): k <- a_s k + dt rhs(q_in); q_out <- q_in + b_s k. */
+int dg_hex_rk_stage(dg_hex_mesh mesh, dg_gas gas, int32_t stage, double dt, const double* q_in_dev,
+                    double* q_out_dev, double* k_dev, void* stream);
+/* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
+int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);
+
 /* ---- precision conversions ------------------------------------------------------------------
  * The FP64 -> FP32 and FP32 -> FP64 conversions that the mixed-precision kernels use, done with
  * integer operations on the IEEE-754 bit patterns (the FP64 pipe, which runs the hardware

@@ -80,6 +80,11 @@ class dg_opts(ctypes.Structure):
 
 
 # name -> (restype, argtypes); every entry point declared in include/dg.h
+class dg_hex_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("L", ctypes.c_double * 3), ("N", ctypes.c_int32),
+                ("nodes1d", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "dg_mesh_upload": (c_int32, [ctypes.POINTER(dg_mesh_desc), ctypes.POINTER(c_void_p)]),
     "dg_mesh_free": (c_int32, [c_void_p]),
@@ -113,6 +118,13 @@ SIGNATURES = {
     "dg_batch_free": (c_int32, [c_void_p]),
     "dg_rk_stage_noalloc": (c_int32, [ctypes.POINTER(dg_mesh_tables), ctypes.POINTER(dg_gas_desc), c_int32,
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_hex_mesh_create": (ctypes.c_int, [ctypes.POINTER(dg_hex_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_hex_mesh_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "dg_hex_operators": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "dg_hex_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "dg_hex_rk_stage": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "dg_hex_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
     "dg_round_to_float": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "dg_widen_to_double": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "dg_split_to_float_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,

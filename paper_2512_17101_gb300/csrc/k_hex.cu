@@ -1,0 +1,367 @@
+// Nodal DG on tensor-product hexahedra (the element type of the paper's timed runs, Sec. 5.2-5.4):
+// Euler equations of a perfect gas on a periodic box of axis-aligned hexahedra, FP64, fused with
+// the low-storage RK4 stage like the tetrahedral path.
+//
+// Discretisation (collocated nodal spectral-element DG): tensor-product nodes from a 1-D node
+// set x_0 = -1 < ... < x_N = 1 (Gauss-Lobatto-Legendre in the workloads), quadrature weights
+// w_i = integral of the Lagrange basis l_i, D[i][j] = l_j'(x_i); diagonal collocated mass;
+//   rhs = - sum_d (2/h_d) D_d F_d + sum over the faces f a node lies on (2/h_d(f)) / w_end (n.F- - n.F*),
+// local Lax-Friedrichs n.F*.  Sum factorisation: the derivative along d at node (i, j, k) reads the
+// N+1 fluxes on the line through the node, 3 (N+1) products per variable instead of (N+1)^3.
+//
+// Kernel layout: one thread per node, EPB elements per block (whole elements, so that the lines
+// are in the block's shared memory); fluxes and the state staged in shared memory; the
+// neighbour's face node (same position on the shared face, mirrored index along the face normal)
+// read from global memory.  Neighbours come from the box structure: no geometry or map arrays.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+struct dg_hex_mesh_s {
+  int n[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0};
+  int N = 0, M = 0, Np = 0;
+  int64_t K = 0;
+  std::vector<double> nodes, w, D;  // host copies
+  double* D_dev = nullptr;          // [M][M]
+  unsigned* status = nullptr;
+};
+
+namespace dg {
+namespace hexk {
+
+template <int N>
+struct HexCfg {
+  static constexpr int M = N + 1, Np = M * M * M;
+  static constexpr int EPB = N == 1 ? 32 : (N == 2 ? 8 : (N == 3 ? 4 : 2));
+  static constexpr int NODES = EPB * Np, NT = (NODES + 31) / 32 * 32;
+};
+
+struct HexGeo {
+  int n[3];
+  double two_h[3];  // 2 / h_d
+  double lift[2];   // 1 / w_0, 1 / w_N
+};
+
+// Pressure and sound speed of a perfect gas.
+__device__ __forceinline__ void pc(double gamma, const double* q, double& p, double& c) {
+  const double ir = 1.0 / q[0];
+  p = (gamma - 1.0) * (q[4] - 0.5 * ir * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]));
+  c = sqrt(gamma * p * ir);
+}
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __restrict__ q, double* __restrict__ out,
+                                                                 double* __restrict__ kreg,
+                                                                 const double* __restrict__ D_g, const HexGeo geo,
+                                                                 const int64_t K, const double gamma, const double a,
+                                                                 const double b, const double dt,
+                                                                 unsigned* __restrict__ status) {
+  using C = HexCfg<N>;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES;
+  __shared__ double sD[M * M];
+  __shared__ double sF[3][5][NODES];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < M * M; i += blockDim.x) sD[i] = D_g[i];
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+  double qv[5] = {0, 0, 0, 0, 0};
+  double pm = 0, cm = 0;
+  if (tid < nn) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
+    pc(gamma, qv, pm, cm);
+    if (!(qv[0] > 0.0) || !(pm > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    const double ir = 1.0 / qv[0];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double ud = qv[1 + d] * ir;
+      sF[d][0][tid] = qv[1 + d];
+      sF[d][1][tid] = qv[1] * ud;
+      sF[d][2][tid] = qv[2] * ud;
+      sF[d][3][tid] = qv[3] * ud;
+      sF[d][1 + d][tid] += pm;
+      sF[d][4][tid] = ud * (qv[4] + pm);
+    }
+  }
+  __syncthreads();
+  if (tid >= nn) return;
+
+  const int el = tid / Np, node = tid - el * Np;
+  const int idx[3] = {node % M, (node / M) % M, node / (M * M)};
+  const int stride[3] = {1, M, M * M};
+  double acc[5] = {0, 0, 0, 0, 0};
+  // volume: - sum_d (2/h_d) sum_l D[idx_d][l] F_d(line node l)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int line0 = el * Np + node - idx[d] * stride[d];
+    const double* Drow = sD + idx[d] * M;
+    double s[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const double dl = Drow[l];
+      const int src = line0 + l * stride[d];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] = fma(dl, sF[d][v][src], s[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = fma(-geo.two_h[d], s[v], acc[v]);
+  }
+
+  // surface: every face the node lies on
+  const int64_t e = e0 + el;
+  const int64_t nx = geo.n[0], ny = geo.n[1], nz = geo.n[2];
+  const int64_t ec[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int end = 0; end < 2; ++end) {
+      if (idx[d] != (end ? N : 0)) continue;
+      int64_t c3[3] = {ec[0], ec[1], ec[2]};
+      c3[d] = (c3[d] + (end ? 1 : geo.n[d] - 1)) % geo.n[d];
+      const int64_t enb = c3[0] + nx * (c3[1] + ny * c3[2]);
+      const int nnode = node + ((end ? 0 : N) - idx[d]) * stride[d];  // mirrored index along d
+      const size_t gP = (size_t)enb * Np + nnode;
+      double qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
+      double pp, cp;
+      pc(gamma, qp, pp, cp);
+      const double sgn = end ? 1.0 : -1.0;
+      const double unm = sgn * qv[1 + d] / qv[0], unp = sgn * qp[1 + d] / qp[0];
+      const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
+      // n.F for both traces: n = sgn e_d
+      double fm[5], fp[5];
+      fm[0] = sgn * qv[1 + d];
+      fp[0] = sgn * qp[1 + d];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        fm[1 + i] = qv[1 + i] * unm;
+        fp[1 + i] = qp[1 + i] * unp;
+      }
+      fm[1 + d] += sgn * pm;
+      fp[1 + d] += sgn * pp;
+      fm[4] = unm * (qv[4] + pm);
+      fp[4] = unp * (qp[4] + pp);
+      const double lf = geo.two_h[d] * geo.lift[end];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] = fma(lf, 0.5 * ((fm[v] - fp[v]) - lam * (qv[v] - qp[v])), acc[v]);
+    }
+  }
+
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const size_t gi = v * KNp + base + tid;
+    if (RK) {
+      const double kk = fma(a, a != 0.0 ? kreg[gi] : 0.0, dt * acc[v]);
+      kreg[gi] = kk;
+      out[gi] = fma(b, kk, qv[v]);
+    } else {
+      out[gi] = acc[v];
+    }
+  }
+}
+
+template <int N, bool RK>
+cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a, double b,
+                     double dt, cudaStream_t s) {
+  using C = HexCfg<N>;
+  HexGeo geo;
+  for (int d = 0; d < 3; ++d) {
+    geo.n[d] = m.n[d];
+    geo.two_h[d] = 2.0 / (m.L[d] / m.n[d]);
+  }
+  geo.lift[0] = 1.0 / m.w[0];
+  geo.lift[1] = 1.0 / m.w[N];
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_rhs_kernel<N, RK><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b, dt, m.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, bool rk, double a,
+                   double b, double dt, cudaStream_t s) {
+  switch (m.N) {
+#define DG_CASE(NN) \
+  case NN:          \
+    return rk ? launch_t<NN, true>(m, gamma, q, out, k, a, b, dt, s) : launch_t<NN, false>(m, gamma, q, out, k, a, b, dt, s);
+    DG_CASE(1)
+    DG_CASE(2)
+    DG_CASE(3)
+    DG_CASE(4)
+#undef DG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// Quadrature weights and differentiation matrix of the Lagrange basis through the nodes, in long
+// double: barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k); D[i][j] = (lambda_j /
+// lambda_i) / (x_i - x_j) off the diagonal, the diagonal from D 1 = 0; w_j = integral of l_j by
+// (N+2)-point Gauss-Legendre quadrature (exact for degree <= 2N+3) of the barycentric l_j.
+bool build_operators(const std::vector<double>& x, std::vector<double>& w, std::vector<double>& D, std::string& err) {
+  const int m = (int)x.size();
+  typedef long double ld;
+  std::vector<ld> lam(m, 1.0L);
+  for (int j = 0; j < m; ++j)
+    for (int k = 0; k < m; ++k)
+      if (k != j) {
+        const ld dx = (ld)x[j] - (ld)x[k];
+        if (!(dx != 0.0L)) {
+          err = "repeated node in the 1-D node set";
+          return false;
+        }
+        lam[j] /= dx;
+      }
+  D.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    ld diag = 0.0L;
+    for (int j = 0; j < m; ++j)
+      if (j != i) {
+        const ld dij = (lam[j] / lam[i]) / ((ld)x[i] - (ld)x[j]);
+        D[(size_t)i * m + j] = (double)dij;
+        diag -= dij;
+      }
+    D[(size_t)i * m + i] = (double)diag;
+  }
+  // Gauss-Legendre points and weights of order G by Newton on P_G (recurrence in long double)
+  const int G = m + 1;
+  std::vector<ld> gx(G), gw(G);
+  const ld pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < G; ++i) {
+    ld z = cosl(pi * (i + 0.75L) / (G + 0.5L));
+    ld dp = 1.0L;
+    for (int it = 0; it < 100; ++it) {
+      ld p0 = 1.0L, p1 = z;
+      for (int n = 2; n <= G; ++n) {
+        const ld p2 = ((2 * n - 1) * z * p1 - (n - 1) * p0) / n;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = G * (z * p1 - p0) / (z * z - 1.0L);
+      const ld dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-19L) break;
+    }
+    gx[i] = z;
+    gw[i] = 2.0L / ((1.0L - z * z) * dp * dp);
+  }
+  w.assign(m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    ld s = 0.0L;
+    for (int g = 0; g < G; ++g) {
+      ld l = 1.0L;
+      for (int k = 0; k < m; ++k)
+        if (k != j) l *= (gx[g] - (ld)x[k]) / ((ld)x[j] - (ld)x[k]);
+      s += gw[g] * l;
+    }
+    w[j] = (double)s;
+  }
+  return true;
+}
+
+}  // namespace hexk
+}  // namespace dg
+
+extern "C" {
+
+int dg_hex_mesh_create(const dg_hex_desc* d, dg_hex_mesh* out) {
+  if (!d || !out) return dg::fail(DG_ERR_INVALID_ARG, "NULL descriptor or output handle");
+  *out = nullptr;
+  if (d->N < 1 || d->N > DG_MAX_ORDER) return dg::fail(DG_ERR_INVALID_ARG, "N must be in 1..4");
+  if (!d->nodes1d) return dg::fail(DG_ERR_INVALID_ARG, "NULL 1-D node set");
+  for (int k = 0; k < 3; ++k) {
+    if (d->n[k] < 1) return dg::fail(DG_ERR_INVALID_ARG, "need at least one hexahedron per direction");
+    if (!(d->L[k] > 0.0)) return dg::fail(DG_ERR_INVALID_ARG, "box lengths must be positive");
+  }
+  const int M = d->N + 1;
+  std::vector<double> x(d->nodes1d, d->nodes1d + M);
+  if (x[0] != -1.0 || x[M - 1] != 1.0) return dg::fail(DG_ERR_INVALID_ARG, "the node set must start at -1 and end at 1");
+  for (int i = 1; i < M; ++i)
+    if (!(x[i] > x[i - 1])) return dg::fail(DG_ERR_INVALID_ARG, "the node set must be ascending");
+  dg_hex_mesh_s* m = new dg_hex_mesh_s();
+  for (int k = 0; k < 3; ++k) {
+    m->n[k] = d->n[k];
+    m->L[k] = d->L[k];
+  }
+  m->N = d->N;
+  m->M = M;
+  m->Np = M * M * M;
+  m->K = (int64_t)d->n[0] * d->n[1] * d->n[2];
+  m->nodes = x;
+  std::string err;
+  if (!dg::hexk::build_operators(x, m->w, m->D, err)) {
+    delete m;
+    return dg::fail(DG_ERR_INVALID_ARG, err);
+  }
+  cudaError_t e = cudaMalloc((void**)&m->D_dev, sizeof(double) * M * M);
+  if (e == cudaSuccess) e = cudaMemcpy(m->D_dev, m->D.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaFree(m->D_dev);
+    cudaFree(m->status);
+    delete m;
+    return dg::cuda_fail(e, "hexahedral mesh upload");
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_hex_mesh_free(dg_hex_mesh m) {
+  if (!m) return DG_OK;
+  cudaFree(m->D_dev);
+  cudaFree(m->status);
+  delete m;
+  return DG_OK;
+}
+
+int dg_hex_operators(dg_hex_mesh m, double* D_host, double* w_host) {
+  if (!m) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (D_host) std::copy(m->D.begin(), m->D.end(), D_host);
+  if (w_host) std::copy(m->w.begin(), m->w.end(), w_host);
+  return DG_OK;
+}
+
+static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, double* k, bool rk, int stage, double dt,
+                   void* stream) {
+  if (!m || !gas) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh or gas");
+  if (!q || !out) return dg::fail(DG_ERR_INVALID_ARG, "NULL state or output");
+  if (rk && !k) return dg::fail(DG_ERR_INVALID_ARG, "NULL RK register k");
+  if (rk && (stage < 0 || stage > 4)) return dg::fail(DG_ERR_INVALID_ARG, "stage must be in 0..4");
+  if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
+  if (gas->p.model != DG_GAS_PERFECT || gas->p.mu > 0)
+    return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path solves the Euler equations of a perfect gas");
+  const size_t n = (size_t)5 * m->K * m->Np;
+  if (q == out || (q < out + n && out < q + n)) return dg::fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
+  const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
+  const cudaError_t e = dg::hexk::launch(*m, gas->p.gamma, q, out, k, rk, a, b, dt, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral right-hand-side kernel");
+}
+
+int dg_hex_rhs(dg_hex_mesh m, dg_gas gas, const double* q, double* rhs, void* stream) {
+  return hex_run(m, gas, q, rhs, nullptr, false, 0, 0.0, stream);
+}
+
+int dg_hex_rk_stage(dg_hex_mesh m, dg_gas gas, int32_t stage, double dt, const double* q_in, double* q_out, double* k,
+                    void* stream) {
+  return hex_run(m, gas, q_in, q_out, k, true, stage, dt, stream);
+}
+
+int dg_hex_status(dg_hex_mesh m, uint32_t* bits, int reset) {
+  if (!m || !bits) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh or bits");
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, m->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(m->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return dg::cuda_fail(e, "hexahedral mesh status");
+  *bits = v;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -280,6 +280,79 @@ def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, str
                                      _stream_ptr(stream)))
 
 
+# ---- tensor-product hexahedra -------------------------------------------------------------------
+
+class HexMesh:
+    """A periodic box of axis-aligned hexahedra with tensor-product nodes (dg_hex_mesh handle)."""
+
+    def __init__(self, n, L, N, nodes1d):
+        n3 = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+        L3 = (L, L, L) if np.isscalar(L) else tuple(float(v) for v in L)
+        self.N = int(N)
+        self._nodes = np.ascontiguousarray(nodes1d, dtype=np.float64)
+        d = capi.dg_hex_desc()
+        d.n = (ctypes.c_int32 * 3)(*n3)
+        d.L = (ctypes.c_double * 3)(*L3)
+        d.N = self.N
+        d.nodes1d = self._nodes.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        check(load().dg_hex_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.K = n3[0] * n3[1] * n3[2]
+        self.Np = (self.N + 1) ** 3
+
+    def operators(self):
+        M = self.N + 1
+        D, w = np.zeros((M, M)), np.zeros(M)
+        check(load().dg_hex_operators(self.handle, _hptr(D), _hptr(w)))
+        return D, w
+
+    def status(self, reset=True):
+        bits = ctypes.c_uint32()
+        check(load().dg_hex_status(self.handle, ctypes.byref(bits), int(reset)))
+        return bits.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().dg_hex_mesh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dg_hex_rhs(mesh: HexMesh, gas: Gas, q, rhs, stream=None):
+    import torch
+    check(load().dg_hex_rhs(mesh.handle, gas.handle, _dptr(q, torch.float64, "q"), _dptr(rhs, torch.float64, "rhs"),
+                            _stream_ptr(stream)))
+
+
+def dg_hex_rk_stage(mesh: HexMesh, gas: Gas, stage, dt, q_in, q_out, k, stream=None):
+    import torch
+    check(load().dg_hex_rk_stage(mesh.handle, gas.handle, int(stage), float(dt), _dptr(q_in, torch.float64, "q_in"),
+                                 _dptr(q_out, torch.float64, "q_out"), _dptr(k, torch.float64, "k"),
+                                 _stream_ptr(stream)))
+
+
+def hex_lsrk4_step(mesh: HexMesh, gas: Gas, q, dt, steps=1, stream=None, work=None):
+    """Advance q in place by ``steps`` LSRK4 steps on the hexahedral mesh (ping-pong buffers)."""
+    import torch
+    if work is None:
+        work = (torch.empty_like(q), torch.zeros_like(q))
+    qb, k = work
+    cur, nxt = q, qb
+    for _ in range(steps):
+        for s in range(5):
+            dg_hex_rk_stage(mesh, gas, s, dt, cur, nxt, k, stream=stream)
+            cur, nxt = nxt, cur
+    if cur is not q:
+        q.copy_(cur)
+    return q
+
+
 # ---- learned temperature guess -------------------------------------------------------------
 
 def dg_mlp_set(gas: Gas, params, norm: dict):

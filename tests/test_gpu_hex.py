@@ -1,0 +1,103 @@
+"""Tensor-product hexahedra: the CUDA path through the C ABI against the hexahedron oracle
+(FP64, 1e-11 relative per conserved variable)."""
+
+import numpy as np
+import pytest
+
+import oracle.hex as hx
+from oracle.lsrk import lsrk4_step
+from oracle.thermo import PerfectGas
+from tests._gpu import rel_err, torch_cuda
+from workloads import isentropic_vortex, uniform_perturbation
+from workloads.hexmesh import gll_nodes, hex_box, hex_nodes
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+GAS = PerfectGas(1.4, 1.0)
+
+
+def _setup(n, N, L=1.0, noise=1e-3, seed=0):
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    box = hex_box(n, L)
+    x = gll_nodes(N)
+    ref = hx.hex_reference(x)
+    q0 = isentropic_vortex(hex_nodes(box, x), 0.0, center=(0.45, 0.55), radius=0.15, period=box["L"])
+    q0 = uniform_perturbation(q0, noise, seed=seed)
+    mesh = dg.HexMesh(box["n"], box["L"], N, x)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    return torch, dg, box, ref, q0, mesh, gas
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_hex_operators_match_oracle(N):
+    torch, dg, box, ref, q0, mesh, gas = _setup(1, N)
+    D, w = mesh.operators()
+    assert np.abs(D - ref.D).max() <= 1e-13 * max(1.0, np.abs(ref.D).max())
+    assert np.abs(w - ref.w).max() <= 1e-15
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, (3, 2, 2), (5, 1, 3)])
+def test_hex_rhs(n, N):
+    torch, dg, box, ref, q0, mesh, gas = _setup(n, N)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, gas, q, rhs)
+    want = hx.hex_rhs_strong(ref, box, q0, GAS)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_two_rk4_steps():
+    torch, dg, box, ref, q0, mesh, gas = _setup((4, 3, 2), 3)
+    dt = 2e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.hex_lsrk4_step(mesh, gas, q, dt, steps=2)
+    f = lambda u: hx.hex_rhs_strong(ref, box, u, GAS)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+
+
+def test_hex_rejects_what_it_does_not_solve():
+    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
+    from paper_2512_17101_gb300 import capi
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=1e-3, Pr=0.71)
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_rhs(mesh, ns, q, rhs)
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_rhs(mesh, gas, q, q)
+    with pytest.raises(capi.DGError):
+        dg.HexMesh(2, 1.0, 2, np.array([-1.0, 0.5, 0.2]))
+
+
+def test_hex_status_flags_without_fault():
+    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
+    q0 = q0.copy()
+    q0[0, 3, 1] = -1.0
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, gas, q, rhs)
+    from paper_2512_17101_gb300 import capi
+    assert mesh.status() & capi.DG_STATUS_NONPHYSICAL
+
+
+@pytest.mark.slow
+def test_hex_vortex_full_size_stage():
+    """The hexahedral benchmark workload (32^3 hexahedra, N = 4): the stage the benchmark times."""
+    from workloads.configs import build_hex_case, get_config
+    cfg = get_config("hex_vortex")
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    case = build_hex_case(cfg)
+    ref = hx.hex_reference(case["nodes1d"])
+    mesh = dg.HexMesh(case["box"]["n"], case["box"]["L"], cfg.N, case["nodes1d"])
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    q_in = torch.tensor(case["q"], device="cuda")
+    q_out, k = torch.empty_like(q_in), torch.zeros_like(q_in)
+    dg.dg_hex_rk_stage(mesh, gas, 0, cfg.dt, q_in, q_out, k)
+    want = hx.hex_rhs_strong(ref, case["box"], case["q"], GAS)
+    assert rel_err(k.cpu().numpy(), cfg.dt * want) <= TOL
+    assert mesh.status() == 0

@@ -18,6 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .gas import IdealGas, seeded_nasa7_mixture, mixture_primitive_state
+from .hexmesh import gll_nodes, hex_box, hex_nodes
 from .mesh import box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
 from .states import isentropic_vortex, taylor_green, uniform_perturbation
 
@@ -37,12 +38,16 @@ class Config:
     description: str = ""
 
     @property
+    def hexahedral(self) -> bool:
+        return self.physics.endswith("_hex")
+
+    @property
     def K(self) -> int:
-        return 6 * self.n ** 3
+        return self.n ** 3 if self.hexahedral else 6 * self.n ** 3
 
     @property
     def Np(self) -> int:
-        return n_nodes(self.N)
+        return (self.N + 1) ** 3 if self.hexahedral else n_nodes(self.N)
 
     @property
     def dofs(self) -> int:
@@ -56,6 +61,11 @@ def _tgv_dt(n, N, gamma=1.4, mach=0.1, noise=0.01):
     pmax = p0 + V0 * V0 / 16.0 * 2.0 * 3.0
     cmax = math.sqrt(gamma * pmax / 1.0)
     return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (umax + cmax))
+
+
+def _vortex_dt(n, N):
+    """|u| <= 1 + beta/(2 pi) e^(1/2) ~ 2.31 and c <= sqrt(1.4) ~ 1.19 for the vortex of the workloads."""
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (2.31 + 1.19))
 
 
 def _mixture_dt(n, N):
@@ -82,6 +92,12 @@ CONFIGS = {
         name="ns_precision", n=32, N=4, physics="ns", state="tgv", steps=10, dt=_tgv_dt(32, 4),
         gas=_NS_GAS, precision="mixed",
         description="as ns_viscous at 32^3 hexes x 6 = 196,608 tets, N=4; split-product tensor-core D/LIFT"),
+    "hex_vortex": Config(
+        name="hex_vortex", n=32, N=4, physics="euler_hex", state="vortex", steps=10, dt=_vortex_dt(32, 4),
+        gas=IdealGas(gamma=1.4, R=1.0),
+        description="Euler on tensor-product hexahedra (the paper's element type), periodic box of 32^3 "
+                    "hexahedra, N=4 (125 GLL nodes each, 4,096,000 DOFs), isentropic vortex + U(+-1e-3), "
+                    "10 RK4 steps"),
     "mixture_learned": Config(
         name="mixture_learned", n=32, N=2, physics="euler_mixture", state="mixture", steps=1, dt=_mixture_dt(32, 2),
         description="7-species Euler mixture, seeded NASA-7, 32^3 hexes x 6 = 196,608 tets, N=2; "
@@ -116,6 +132,18 @@ def build_case(cfg: Config, n=None, N=None):
     else:
         raise ValueError(cfg.state)
     return out
+
+
+def build_hex_case(cfg: Config, n=None, N=None):
+    """Mesh, node set and initial state of a hexahedral config: dict(box, nodes1d, xyz, q)."""
+    n = cfg.n if n is None else n
+    N = cfg.N if N is None else N
+    box = hex_box(n, 1.0)
+    x = gll_nodes(N)
+    xyz = hex_nodes(box, x)
+    q = isentropic_vortex(xyz, 0.0, gamma=cfg.gas.gamma, period=box["L"])
+    q = uniform_perturbation(q, 1.0e-3, seed=cfg.seed)
+    return dict(box=box, nodes1d=x, xyz=xyz, q=q, n=n, N=N)
 
 
 def batched_cases(ncases=64, seed=0, n_min=2, n_max=20):
