@@ -446,16 +446,19 @@ def gpu_arm(args, cfg, world, rank, local):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_form(args, local)
+    hexf = None
+    if rank == 0 and not args.no_hex:
+        hexf = hex_form(args, local)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f64 state; fp16x2 tensor / fp32 flux",
+            "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f64 state; bf16x3 tensor / fp32 flux",
             "data": "synthetic", "config": dict(workload_config(cfg), precision=head),
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
-            "learned_form": learned, "batched_form": batched,
+            "learned_form": learned, "batched_form": batched, "hex_form": hexf,
             "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
@@ -582,6 +585,82 @@ def learned_form(args, local):
             "seeds": out["fp64"], "mixed_precision_seeds": out["mixed"]}
 
 
+def hex_flops_per_element(M):
+    """FP64 flops of the sum-factorised hexahedral right-hand side + stage update per element (M = N+1)."""
+    per_node = 8 + 21 + 2 * 3 * 5 * M + 15 + 4 * 5   # pressure, fluxes, 3 line derivatives x 5 vars, RK
+    per_face_node = 60                              # neighbour p, c, u.n, n.F of both traces, lambda, LF
+    return M ** 3 * per_node + 6 * M * M * per_face_node
+
+
+def hex_bytes_per_element(M):
+    """q in, k in/out, q_out (FP64, 5 variables); neighbour traces assumed L2-resident."""
+    return M ** 3 * 5 * 8 * 4
+
+
+def hex_form(args, local):
+    """The tensor-product hexahedron workload (Euler, isentropic vortex, 32^3 hexahedra, N = 4):
+    FP64 RK4 steps with CUDA events, its FP64 roofline, and the oracle's stage on a 16^3 box."""
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads.configs import build_hex_case, get_config
+
+    cfg = get_config("hex_vortex")
+    dev = torch.device("cuda", local)
+    case = build_hex_case(cfg)
+    mesh = dg.HexMesh(case["box"]["n"], case["box"]["L"], cfg.N, case["nodes1d"])
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    q0 = torch.tensor(case["q"], device=dev)
+    q = q0.clone()
+    work = (torch.empty_like(q), torch.zeros_like(q))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        dg.hex_lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+    q.copy_(q0)
+    steps = max(1, args.steps)
+    total = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.hex_lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    if mesh.status() != 0:
+        raise SystemExit("status flags set in the hexahedral run")
+    ms = total / steps
+    M = cfg.N + 1
+    stage_s = ms * 1e-3 / 5
+    flops, nbytes = hex_flops_per_element(M) * cfg.K, hex_bytes_per_element(M) * cfg.K
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # the oracle's stage on a 16^3 box (one core), for context
+    import numpy as np
+    import oracle.hex as hx
+    from oracle.thermo import PerfectGas
+    small = build_hex_case(cfg, n=16)
+    ref = hx.hex_reference(small["nodes1d"])
+    t0 = time.perf_counter()
+    hx.hex_rhs_strong(ref, small["box"], small["q"], PerfectGas(1.4, 1.0))
+    cpu_s = time.perf_counter() - t0
+    cpu_dofs = 16 ** 3 * M ** 3
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
+            "steps": steps, "ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
+            "roofline": {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / stage_s / 1e12 / FP64_PEAK_TFLOPS,
+                         "flops_per_stage": flops, "algorithmic_bytes_per_stage": nbytes,
+                         "hbm_achieved_gbs": nbytes / stage_s / 1e9, "hbm_frac": nbytes / stage_s / 1e9 / hbm},
+            "cpu_oracle_stage": {"value": cpu_dofs / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+                                 "sample": f"one right-hand side of the oracle on 16^3 hexahedra, N = {cfg.N} "
+                                           f"(numpy, single thread), {cpu_s:.2f} s"},
+            "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
 def batched_form(args, local):
     """The batched workload (64 uneven cases, orders 1..4, half Euler / half NS, mixed precision):
     one graph launch per RK4 step, against stepping the same cases one by one."""
@@ -644,6 +723,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
+    ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "dg_cvt.cuh"
 #include "dg_internal.h"
 
 struct dg_hex_mesh_s {
@@ -46,11 +47,25 @@ struct HexGeo {
   double lift[2];   // 1 / w_0, 1 / w_N
 };
 
-// Pressure and sound speed of a perfect gas.
-__device__ __forceinline__ void pc(double gamma, const double* q, double& p, double& c) {
-  const double ir = 1.0 / q[0];
+// FP64 reciprocal and square root from FP32 seeds (conversions on the integer pipe) and one
+// Newton step each, relative error a few 1e-14: the IEEE FP64 division and square root are long
+// instruction sequences on the FP64 pipe, which bounds this kernel, and every face incidence
+// needs a trace's 1/rho and sound speed.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double r = cvt::widen(1.0f / cvt::narrow(x));
+  return r * fma(-x, r, 2.0);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  const double y = cvt::widen(rsqrtf(cvt::narrow(x)));  // ~ x^-1/2
+  const double s = x * y;                                // ~ x^1/2
+  return fma(0.5 * y, fma(-s, s, x), s);                 // s + (x - s^2) / (2 sqrt x)
+}
+
+// 1/rho, pressure and sound speed of a perfect gas.
+__device__ __forceinline__ void pc(double gamma, const double* q, double& ir, double& p, double& c) {
+  ir = rcp_nr(q[0]);
   p = (gamma - 1.0) * (q[4] - 0.5 * ir * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]));
-  c = sqrt(gamma * p * ir);
+  c = sqrt_nr(gamma * p * ir);
 }
 
 template <int N, bool RK>
@@ -72,13 +87,13 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
   double qv[5] = {0, 0, 0, 0, 0};
-  double pm = 0, cm = 0;
+  double pm = 0, cm = 0, irm = 0;
   if (tid < nn) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
-    pc(gamma, qv, pm, cm);
+    pc(gamma, qv, irm, pm, cm);
     if (!(qv[0] > 0.0) || !(pm > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-    const double ir = 1.0 / qv[0];
+    const double ir = irm;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double ud = qv[1 + d] * ir;
@@ -131,10 +146,10 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       double qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
-      double pp, cp;
-      pc(gamma, qp, pp, cp);
+      double irp, pp, cp;
+      pc(gamma, qp, irp, pp, cp);
       const double sgn = end ? 1.0 : -1.0;
-      const double unm = sgn * qv[1 + d] / qv[0], unp = sgn * qp[1 + d] / qp[0];
+      const double unm = sgn * qv[1 + d] * irm, unp = sgn * qp[1 + d] * irp;
       const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
       // n.F for both traces: n = sgn e_d
       double fm[5], fp[5];
