@@ -9,10 +9,13 @@
 // local Lax-Friedrichs n.F*.  Sum factorisation: the derivative along d at node (i, j, k) reads the
 // N+1 fluxes on the line through the node, 3 (N+1) products per variable instead of (N+1)^3.
 //
-// Kernel layout: one thread per node, EPB elements per block (whole elements, so that the lines
-// are in the block's shared memory); fluxes and the state staged in shared memory; the
-// neighbour's face node (same position on the shared face, mirrored index along the face normal)
-// read from global memory.  Neighbours come from the box structure: no geometry or map arrays.
+// Kernel layout: EPB whole elements per block (so that the lines are in the block's shared
+// memory).  Node-parallel: fluxes, 1/rho, p and c into shared memory, then the line derivatives.
+// Face-node-parallel: the Lax-Friedrichs terms, one axis at a time so that no two face nodes of a
+// pass add into the same node (no warp of consecutive nodes steps through faces only some of its
+// lanes lie on); the neighbour's face node (same position on the shared face, mirrored index along
+// the face normal) read from global memory.  Neighbours come from the box structure: no geometry
+// or map arrays.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -76,24 +79,28 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
                                                                  const double b, const double dt,
                                                                  unsigned* __restrict__ status) {
   using C = HexCfg<N>;
-  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
   __shared__ double sD[M * M];
-  __shared__ double sF[3][5][NODES];
+  __shared__ double sF[3][5][NODES];  // volume fluxes
+  __shared__ double sS[5][NODES];     // lifted surface terms
+  __shared__ double sPC[3][NODES];    // 1/rho, p, c of the block's nodes
   const int tid = threadIdx.x;
-  for (int i = tid; i < M * M; i += blockDim.x) sD[i] = D_g[i];
+  for (int i = tid; i < M * M; i += NT) sD[i] = D_g[i];
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int nel = (int)min((int64_t)EPB, K - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
   double qv[5] = {0, 0, 0, 0, 0};
-  double pm = 0, cm = 0, irm = 0;
   if (tid < nn) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
-    pc(gamma, qv, irm, pm, cm);
-    if (!(qv[0] > 0.0) || !(pm > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-    const double ir = irm;
+    double ir, p, c;
+    pc(gamma, qv, ir, p, c);
+    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    sPC[0][tid] = ir;
+    sPC[1][tid] = p;
+    sPC[2][tid] = c;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double ud = qv[1 + d] * ir;
@@ -101,73 +108,87 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       sF[d][1][tid] = qv[1] * ud;
       sF[d][2][tid] = qv[2] * ud;
       sF[d][3][tid] = qv[3] * ud;
-      sF[d][1 + d][tid] += pm;
-      sF[d][4][tid] = ud * (qv[4] + pm);
+      sF[d][1 + d][tid] += p;
+      sF[d][4][tid] = ud * (qv[4] + p);
     }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sS[v][tid] = 0.0;
   }
   __syncthreads();
+
+  // surface: face-node-parallel, one axis at a time (a node lies on at most one face of an axis,
+  // so within a pass no two face nodes add into the same node)
+  const int64_t nx = geo.n[0], ny = geo.n[1];
+  constexpr int FPA = 2 * M * M;  // face nodes of one element on the two faces of an axis
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int s1 = stride[(d + 1) % 3], s2 = stride[(d + 2) % 3];
+    for (int w = tid; w < nel * FPA; w += NT) {
+      const int el = w / FPA, rem = w - el * FPA, end = rem / (M * M), ab = rem - end * M * M;
+      const int ia = ab % M, ib = ab / M;
+      const int node = (end ? N : 0) * stride[d] + ia * s1 + ib * s2;
+      const int loc = el * Np + node;
+      const int64_t e = e0 + el;
+      int64_t c3[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
+      c3[d] = (c3[d] + (end ? 1 : geo.n[d] - 1)) % geo.n[d];
+      const int64_t enb = c3[0] + nx * (c3[1] + ny * c3[2]);
+      const int nnode = node + (end ? -N : N) * stride[d];  // mirrored index along d
+      const size_t gP = (size_t)enb * Np + nnode, gM = base + loc;
+      double qm[5], qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = q[v * KNp + gM];
+        qp[v] = q[v * KNp + gP];
+      }
+      const double irm = sPC[0][loc], pm = sPC[1][loc], cm = sPC[2][loc];
+      double irp, pp, cp;
+      pc(gamma, qp, irp, pp, cp);
+      // n = +-e_d: n.F(q) = +-(F_d(q)); the sign folded into the lifted term
+      const double um = qm[1 + d] * irm, up = qp[1 + d] * irp;
+      const double lam = fmax(fabs(um) + cm, fabs(up) + cp);
+      double fm[5], fp[5];
+      fm[0] = qm[1 + d];
+      fp[0] = qp[1 + d];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        fm[1 + i] = qm[1 + i] * um;
+        fp[1 + i] = qp[1 + i] * up;
+      }
+      fm[1 + d] += pm;
+      fp[1 + d] += pp;
+      fm[4] = um * (qm[4] + pm);
+      fp[4] = up * (qp[4] + pp);
+      // n.F- - n.F* = (sgn (F_d- - F_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end
+      const double lf = 0.5 * geo.two_h[d] * (end ? geo.lift[1] : geo.lift[0]);
+      const double sgnlf = end ? lf : -lf;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sS[v][loc] += fma(sgnlf, fm[v] - fp[v], -lf * lam * (qm[v] - qp[v]));
+    }
+    __syncthreads();
+  }
   if (tid >= nn) return;
 
   const int el = tid / Np, node = tid - el * Np;
   const int idx[3] = {node % M, (node / M) % M, node / (M * M)};
-  const int stride[3] = {1, M, M * M};
-  double acc[5] = {0, 0, 0, 0, 0};
+  double acc[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) acc[v] = sS[v][tid];
   // volume: - sum_d (2/h_d) sum_l D[idx_d][l] F_d(line node l)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int line0 = el * Np + node - idx[d] * stride[d];
     const double* Drow = sD + idx[d] * M;
-    double s[5] = {0, 0, 0, 0, 0};
+    double sv[5] = {0, 0, 0, 0, 0};
 #pragma unroll
     for (int l = 0; l < M; ++l) {
       const double dl = Drow[l];
       const int src = line0 + l * stride[d];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s[v] = fma(dl, sF[d][v][src], s[v]);
+      for (int v = 0; v < 5; ++v) sv[v] = fma(dl, sF[d][v][src], sv[v]);
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = fma(-geo.two_h[d], s[v], acc[v]);
-  }
-
-  // surface: every face the node lies on
-  const int64_t e = e0 + el;
-  const int64_t nx = geo.n[0], ny = geo.n[1], nz = geo.n[2];
-  const int64_t ec[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int end = 0; end < 2; ++end) {
-      if (idx[d] != (end ? N : 0)) continue;
-      int64_t c3[3] = {ec[0], ec[1], ec[2]};
-      c3[d] = (c3[d] + (end ? 1 : geo.n[d] - 1)) % geo.n[d];
-      const int64_t enb = c3[0] + nx * (c3[1] + ny * c3[2]);
-      const int nnode = node + ((end ? 0 : N) - idx[d]) * stride[d];  // mirrored index along d
-      const size_t gP = (size_t)enb * Np + nnode;
-      double qp[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
-      double irp, pp, cp;
-      pc(gamma, qp, irp, pp, cp);
-      const double sgn = end ? 1.0 : -1.0;
-      const double unm = sgn * qv[1 + d] * irm, unp = sgn * qp[1 + d] * irp;
-      const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
-      // n.F for both traces: n = sgn e_d
-      double fm[5], fp[5];
-      fm[0] = sgn * qv[1 + d];
-      fp[0] = sgn * qp[1 + d];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        fm[1 + i] = qv[1 + i] * unm;
-        fp[1 + i] = qp[1 + i] * unp;
-      }
-      fm[1 + d] += sgn * pm;
-      fp[1 + d] += sgn * pp;
-      fm[4] = unm * (qv[4] + pm);
-      fp[4] = unp * (qp[4] + pp);
-      const double lf = geo.two_h[d] * geo.lift[end];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] = fma(lf, 0.5 * ((fm[v] - fp[v]) - lam * (qv[v] - qp[v])), acc[v]);
-    }
+    for (int v = 0; v < 5; ++v) acc[v] = fma(-geo.two_h[d], sv[v], acc[v]);
   }
 
 #pragma unroll
