@@ -20,6 +20,10 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
 * weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
   with the summation-by-parts identity W D + D^T W = diag(-1, 0, ..., 0, 1) it equals the
   strong form up to rounding.
+* scalar advection du/dt + a . grad u = 0, a constant (the paper's GPU comparison workload,
+  section 5.2, on p = 1 tensor-product elements): the same strong and weak forms with the flux
+  F_d = a_d u and the Lax-Friedrichs flux with lambda = |a . n|, which is the upwind flux
+  n.F* = (a.n) u_upwind.
 
 Arrays: q[V][K][Np], node index n = i + (N+1)(j + (N+1)k); element index ex + nx(ey + ny ez).
 """
@@ -152,6 +156,57 @@ def hex_rhs_weak(ref, box, q, gas):
     for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
         rhs[sel] -= lift * fstar
     return rhs.reshape(q.shape)
+
+
+def _advection_lambda(an):
+    """Lax-Friedrichs dissipation coefficient of the flux a u across a face with a.n = an."""
+    return abs(an)
+
+
+def _advection_surface_terms(ref, box, u5, a):
+    """Per face (axis, end): (selector, lifting factor, n.F(u-), n.F*) for F = a u."""
+    N = ref.N
+    out = []
+    for axis in range(3):
+        for end in (0, 1):
+            an = (-1.0 if end == 0 else 1.0) * a[axis]
+            nb = _neighbour(box, axis, -1 if end == 0 else 1)
+            um = u5[_face_slices(N, axis, end)]
+            up = u5[nb][_face_slices(N, axis, 1 - end)]
+            fm, fp = an * um, an * up
+            fstar = 0.5 * (fm + fp) + 0.5 * _advection_lambda(an) * (um - up)
+            lift = (2.0 / box["h"][axis]) / ref.w[0 if end == 0 else N]
+            out.append((_face_slices(N, axis, end), lift, fm, fstar))
+    return out
+
+
+def _scalar_shape(u, N):
+    u = np.asarray(u, dtype=np.float64)
+    return u.reshape(u.shape[-2], N + 1, N + 1, N + 1)  # [K][k][j][i]
+
+
+def hex_advection_rhs_strong(ref, box, u, a):
+    """Strong-form right-hand side of scalar advection with constant velocity a[3]:
+    u[K][Np] (or [1][K][Np]) -> rhs of the same shape."""
+    u5 = _scalar_shape(u, ref.N)
+    rhs = np.zeros_like(u5)
+    for d in range(3):
+        rhs -= (2.0 / box["h"][d]) * _along(ref.D, a[d] * u5, d)
+    for sel, lift, fm, fstar in _advection_surface_terms(ref, box, u5, a):
+        rhs[sel] += lift * (fm - fstar)
+    return rhs.reshape(np.shape(u))
+
+
+def hex_advection_rhs_weak(ref, box, u, a):
+    """Weak-form right-hand side of scalar advection (the cross-check of the strong form)."""
+    u5 = _scalar_shape(u, ref.N)
+    Mt = np.diag(1.0 / ref.w) @ ref.D.T @ np.diag(ref.w)
+    rhs = np.zeros_like(u5)
+    for d in range(3):
+        rhs += (2.0 / box["h"][d]) * _along(Mt, a[d] * u5, d)
+    for sel, lift, fm, fstar in _advection_surface_terms(ref, box, u5, a):
+        rhs[sel] -= lift * fstar
+    return rhs.reshape(np.shape(u))
 
 
 def hex_integrate(ref, box, u):
