@@ -446,9 +446,10 @@ def gpu_arm(args, cfg, world, rank, local):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_form(args, local)
-    hexf = None
+    hexf = hexadv = None
     if rank == 0 and not args.no_hex:
         hexf = hex_form(args, local)
+        hexadv = hex_advection_form(args, local)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -459,7 +460,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
-            "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "hex_advection_form": hexadv, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -587,7 +588,8 @@ def learned_form(args, local):
 
 def hex_flops_per_element(M):
     """FP64 flops of the sum-factorised hexahedral right-hand side + stage update per element (M = N+1)."""
-    per_node = 8 + 21 + 2 * 3 * 5 * M + 15 + 4 * 5   # pressure, fluxes, 3 line derivatives x 5 vars, RK
+    per_node = 8 + 21 + 2 * 3 * 5 * M + 4 * 5   # pressure, fluxes, 3 line derivatives x 5 vars (the
+    #                                             -(2/h_d) dt factor folded into D), RK update
     per_face_node = 60                              # neighbour p, c, u.n, n.F of both traces, lambda, LF
     return M ** 3 * per_node + 6 * M * M * per_face_node
 
@@ -657,6 +659,74 @@ def hex_form(args, local):
                          "hbm_achieved_gbs": nbytes / stage_s / 1e9, "hbm_frac": nbytes / stage_s / 1e9 / hbm},
             "cpu_oracle_stage": {"value": cpu_dofs / cpu_s, "unit": "DOF-updates/s", "cores": 1,
                                  "sample": f"one right-hand side of the oracle on 16^3 hexahedra, N = {cfg.N} "
+                                           f"(numpy, single thread), {cpu_s:.2f} s"},
+            "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
+def hex_advection_flops_per_element(M, velocity):
+    """FP64 flops of the advection right-hand side + stage update per element (M = N+1): per node
+    3 line derivatives of M FMAs (the factor -a_d (2/h_d) dt folded into D) and the 2 FMAs of the
+    update; per node of an inflow face (one per axis with a_d != 0) a difference and an FMA."""
+    inflow = sum(1 for v in velocity if v != 0.0)
+    return M ** 3 * (2 * 3 * M + 2 * 2) + inflow * M * M * 3
+
+
+def hex_advection_form(args, local):
+    """Scalar advection on p = 1 hexahedra (the paper's GPU comparison workload), 128^3 hexahedra:
+    FP64 RK4 steps with CUDA events, the FP64 and HBM rooflines, and the oracle's stage on 32^3."""
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads.configs import build_hex_advection_case, get_config
+
+    cfg = get_config("hex_advection")
+    dev = torch.device("cuda", local)
+    case = build_hex_advection_case(cfg)
+    vel = case["velocity"]
+    mesh = dg.HexMesh(case["box"]["n"], case["box"]["L"], cfg.N, case["nodes1d"])
+    u0 = torch.tensor(case["u"], device=dev)
+    u = u0.clone()
+    work = (torch.empty_like(u), torch.zeros_like(u))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        dg.hex_advection_lsrk4_step(mesh, vel, u, cfg.dt, steps=1, work=work)
+    u.copy_(u0)
+    steps = max(1, args.steps)
+    total = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.hex_advection_lsrk4_step(mesh, vel, u, cfg.dt, steps=1, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    ms = total / steps
+    M = cfg.N + 1
+    stage_s = ms * 1e-3 / 5
+    flops = hex_advection_flops_per_element(M, vel) * cfg.K
+    nbytes = M ** 3 * 8 * 4 * cfg.K  # u in, k in and out, u_out
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    import oracle.hex as hx
+    small = build_hex_advection_case(cfg, n=32)
+    ref = hx.hex_reference(small["nodes1d"])
+    t0 = time.perf_counter()
+    hx.hex_advection_rhs_strong(ref, small["box"], small["u"], vel)
+    cpu_s = time.perf_counter() - t0
+    cpu_dofs = 32 ** 3 * M ** 3
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
+            "steps": steps, "ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
+            "roofline": {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / stage_s / 1e12 / FP64_PEAK_TFLOPS,
+                         "flops_per_stage": flops, "algorithmic_bytes_per_stage": nbytes,
+                         "hbm_achieved_gbs": nbytes / stage_s / 1e9, "hbm_frac": nbytes / stage_s / 1e9 / hbm},
+            "cpu_oracle_stage": {"value": cpu_dofs / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+                                 "sample": f"one right-hand side of the oracle on 32^3 hexahedra, N = {cfg.N} "
                                            f"(numpy, single thread), {cpu_s:.2f} s"},
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 

@@ -370,6 +370,17 @@ int dg_hex_rhs(dg_hex_mesh mesh, dg_gas gas, const double* q_dev, double* rhs_de
 /* LSRK4 stage (as dg_rk_stage): k <- a_s k + dt rhs(q_in); q_out <- q_in + b_s k. */
 int dg_hex_rk_stage(dg_hex_mesh mesh, dg_gas gas, int32_t stage, double dt, const double* q_in_dev,
                     double* q_out_dev, double* k_dev, void* stream);
+/* Scalar advection du/dt + a . grad u = 0 with a constant velocity (the paper's GPU comparison
+ * workload, Sec. 5.2, run there on p = 1 tensor-product elements): flux F_d = a_d u, local
+ * Lax-Friedrichs flux with lambda = |a . n| (the upwind flux), the same strong form and lifting.
+ * velocity: host [3]; u, rhs: device [K][Np], caller-owned, not overlapping.  Errors:
+ * DG_ERR_INVALID_ARG (NULL, overlap, non-finite velocity or dt, stage outside 0..4), DG_ERR_CUDA.
+ * Asynchronous on stream. */
+int dg_hex_advection_rhs(dg_hex_mesh mesh, const double* velocity, const double* u_dev, double* rhs_dev,
+                         void* stream);
+/* LSRK4 stage of the advection: k <- a_s k + dt rhs(u_in); u_out <- u_in + b_s k. */
+int dg_hex_advection_rk_stage(dg_hex_mesh mesh, const double* velocity, int32_t stage, double dt,
+                              const double* u_in_dev, double* u_out_dev, double* k_dev, void* stream);
 /* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
 int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);
 

@@ -1,6 +1,6 @@
 // Nodal DG on tensor-product hexahedra (the element type of the paper's timed runs, Sec. 5.2-5.4):
-// Euler equations of a perfect gas on a periodic box of axis-aligned hexahedra, FP64, fused with
-// the low-storage RK4 stage like the tetrahedral path.
+// Euler equations of a perfect gas, and scalar advection, on a periodic box of axis-aligned
+// hexahedra, FP64, fused with the low-storage RK4 stage like the tetrahedral path.
 //
 // Discretisation (collocated nodal spectral-element DG): tensor-product nodes from a 1-D node
 // set x_0 = -1 < ... < x_N = 1 (Gauss-Lobatto-Legendre in the workloads), quadrature weights
@@ -44,10 +44,12 @@ struct HexCfg {
   static constexpr int NODES = EPB * Np, NT = (NODES + 31) / 32 * 32;
 };
 
+// Coefficients with the stage's dt folded in (s = dt in an RK stage, 1 for the right-hand side), so
+// that the kernel accumulates dt * rhs directly: the volume term uses D_d = -(2/h_d) s D.
 struct HexGeo {
   int n[3];
-  double two_h[3];  // 2 / h_d
-  double lift[2];   // 1 / w_0, 1 / w_N
+  double dsc[3];    // -(2/h_d) s
+  double lf[3][2];  // (2/h_d) / w_end s / 2
 };
 
 // FP64 reciprocal and square root from FP32 seeds (conversions on the integer pipe) and one
@@ -71,27 +73,46 @@ __device__ __forceinline__ void pc(double gamma, const double* q, double& ir, do
   c = sqrt_nr(gamma * p * ir);
 }
 
+// The six periodic neighbours of element e, slot 2d + end (end 0: the -x_d side), in 32-bit
+// arithmetic (K < 2^31 is checked on the host): the 64-bit integer division is a long sequence
+// whose conversions compete for the FP64 pipe that bounds these kernels.  Computed once per
+// element, not per face node.
+__device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* nb) {
+  const unsigned nx = n[0], ny = n[1], nz = n[2], nxy = nx * ny;
+  const unsigned t = e / nx, ex = e - t * nx, ez = t / ny, ey = t - ez * ny;
+  nb[0] = (int)(ex == 0 ? e + (nx - 1) : e - 1);
+  nb[1] = (int)(ex == nx - 1 ? e - (nx - 1) : e + 1);
+  nb[2] = (int)(ey == 0 ? e + (ny - 1) * nx : e - nx);
+  nb[3] = (int)(ey == ny - 1 ? e - (ny - 1) * nx : e + nx);
+  nb[4] = (int)(ez == 0 ? e + (nz - 1) * nxy : e - nxy);
+  nb[5] = (int)(ez == nz - 1 ? e - (nz - 1) * nxy : e + nxy);
+}
+
 template <int N, bool RK>
 __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                                  double* __restrict__ kreg,
                                                                  const double* __restrict__ D_g, const HexGeo geo,
                                                                  const int64_t K, const double gamma, const double a,
-                                                                 const double b, const double dt,
+                                                                 const double b, const int accumulate,
                                                                  unsigned* __restrict__ status) {
   using C = HexCfg<N>;
   constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
-  __shared__ double sD[M * M];
+  __shared__ double sD[3][M * M];     // -(2/h_d) s D per axis
   __shared__ double sF[3][5][NODES];  // volume fluxes
   __shared__ double sS[5][NODES];     // lifted surface terms
   __shared__ double sPC[3][NODES];    // 1/rho, p, c of the block's nodes
+  __shared__ int sNb[EPB][6];
   const int tid = threadIdx.x;
-  for (int i = tid; i < M * M; i += NT) sD[i] = D_g[i];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int i = tid; i < M * M; i += NT) sD[d][i] = geo.dsc[d] * D_g[i];
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int nel = (int)min((int64_t)EPB, K - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
   double qv[5] = {0, 0, 0, 0, 0};
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid]);
   if (tid < nn) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
@@ -118,7 +139,6 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
 
   // surface: face-node-parallel, one axis at a time (a node lies on at most one face of an axis,
   // so within a pass no two face nodes add into the same node)
-  const int64_t nx = geo.n[0], ny = geo.n[1];
   constexpr int FPA = 2 * M * M;  // face nodes of one element on the two faces of an axis
   constexpr int stride[3] = {1, M, M * M};
 #pragma unroll
@@ -129,12 +149,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       const int ia = ab % M, ib = ab / M;
       const int node = (end ? N : 0) * stride[d] + ia * s1 + ib * s2;
       const int loc = el * Np + node;
-      const int64_t e = e0 + el;
-      int64_t c3[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
-      c3[d] = (c3[d] + (end ? 1 : geo.n[d] - 1)) % geo.n[d];
-      const int64_t enb = c3[0] + nx * (c3[1] + ny * c3[2]);
       const int nnode = node + (end ? -N : N) * stride[d];  // mirrored index along d
-      const size_t gP = (size_t)enb * Np + nnode, gM = base + loc;
+      const size_t gP = (size_t)sNb[el][2 * d + end] * Np + nnode, gM = base + loc;
       double qm[5], qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -159,8 +175,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       fp[1 + d] += pp;
       fm[4] = um * (qm[4] + pm);
       fp[4] = up * (qp[4] + pp);
-      // n.F- - n.F* = (sgn (F_d- - F_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end
-      const double lf = 0.5 * geo.two_h[d] * (end ? geo.lift[1] : geo.lift[0]);
+      // n.F- - n.F* = (sgn (F_d- - F_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end (times s)
+      const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
       const double sgnlf = end ? lf : -lf;
 #pragma unroll
       for (int v = 0; v < 5; ++v) sS[v][loc] += fma(sgnlf, fm[v] - fp[v], -lf * lam * (qm[v] - qp[v]));
@@ -174,28 +190,25 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   double acc[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) acc[v] = sS[v][tid];
-  // volume: - sum_d (2/h_d) sum_l D[idx_d][l] F_d(line node l)
+  // volume: - sum_d (2/h_d) s sum_l D[idx_d][l] F_d(line node l)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int line0 = el * Np + node - idx[d] * stride[d];
-    const double* Drow = sD + idx[d] * M;
-    double sv[5] = {0, 0, 0, 0, 0};
+    const double* Drow = sD[d] + idx[d] * M;
 #pragma unroll
     for (int l = 0; l < M; ++l) {
       const double dl = Drow[l];
       const int src = line0 + l * stride[d];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sv[v] = fma(dl, sF[d][v][src], sv[v]);
+      for (int v = 0; v < 5; ++v) acc[v] = fma(dl, sF[d][v][src], acc[v]);
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = fma(-geo.two_h[d], sv[v], acc[v]);
   }
 
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const size_t gi = v * KNp + base + tid;
     if (RK) {
-      const double kk = fma(a, a != 0.0 ? kreg[gi] : 0.0, dt * acc[v]);
+      const double kk = accumulate ? fma(a, kreg[gi], acc[v]) : acc[v];  // acc = dt rhs
       kreg[gi] = kk;
       out[gi] = fma(b, kk, qv[v]);
     } else {
@@ -204,19 +217,142 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   }
 }
 
+// Scalar advection du/dt + a . grad u = 0 (the paper's GPU comparison workload, Sec. 5.2): F_d = a_d u
+// and the Lax-Friedrichs flux with lambda = |a . n|, i.e. the upwind flux, so that a face adds
+//   (2/h_d)/w_end (n.F- - n.F*) = (2/h_d)/w_end (s a_d - |a_d|)/2 (u- - u+),  s = -1 (end 0), +1 (end 1),
+// which vanishes on outflow faces: per axis only the inflow face of an element contributes.
+// As for the Euler kernel, the stage's dt (s) is folded into the coefficients.
+struct AdvCoef {
+  int n[3];
+  int inflow;         // bit 2d + end set where face[d][end] != 0 (tested on the integer pipe)
+  double dsc[3];      // -a_d (2/h_d) s
+  double face[3][2];  // (2/h_d)/w_end (sgn a_d - |a_d|) s / 2, sgn = -1 (end 0), +1 (end 1)
+};
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(HexCfg<N>::NT) hex_adv_kernel(const double* __restrict__ u, double* __restrict__ out,
+                                                                 double* __restrict__ kreg,
+                                                                 const double* __restrict__ D_g, const AdvCoef cf,
+                                                                 const int64_t K, const double a, const double b,
+                                                                 const int accumulate) {
+  using C = HexCfg<N>;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
+  __shared__ double sD[3][M * M];  // -a_d (2/h_d) s D per axis
+  __shared__ double sU[NODES];
+  __shared__ double sS[NODES];
+  __shared__ int sNb[EPB][6];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int i = tid; i < M * M; i += NT) sD[d][i] = cf.dsc[d] * D_g[i];
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t base = (size_t)e0 * Np;
+  double uv = 0.0;
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), cf.n, sNb[tid]);
+  if (tid < nn) {
+    uv = u[base + tid];
+    sU[tid] = uv;
+    sS[tid] = 0.0;
+  }
+  __syncthreads();
+
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int s1 = stride[(d + 1) % 3], s2 = stride[(d + 2) % 3];
+#pragma unroll
+    for (int end = 0; end < 2; ++end) {
+      if (!(cf.inflow >> (2 * d + end) & 1)) continue;  // outflow face (or a_d = 0): uniform
+      const double c = cf.face[d][end];
+      for (int w = tid; w < nel * M * M; w += NT) {
+        const int el = w / (M * M), ab = w - el * M * M;
+        const int node = (end ? N : 0) * stride[d] + (ab % M) * s1 + (ab / M) * s2;
+        const int loc = el * Np + node;
+        const int nnode = node + (end ? -N : N) * stride[d];
+        sS[loc] = fma(c, sU[loc] - u[(size_t)sNb[el][2 * d + end] * Np + nnode], sS[loc]);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid >= nn) return;
+
+  const int el = tid / Np, node = tid - el * Np;
+  const int idx[3] = {node % M, (node / M) % M, node / (M * M)};
+  double acc = sS[tid];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int line0 = el * Np + node - idx[d] * stride[d];
+    const double* Drow = sD[d] + idx[d] * M;
+#pragma unroll
+    for (int l = 0; l < M; ++l) acc = fma(Drow[l], sU[line0 + l * stride[d]], acc);
+  }
+  const size_t gi = base + tid;
+  if (RK) {
+    const double kk = accumulate ? fma(a, kreg[gi], acc) : acc;  // acc = dt rhs
+    kreg[gi] = kk;
+    out[gi] = fma(b, kk, uv);
+  } else {
+    out[gi] = acc;
+  }
+}
+
+template <int N, bool RK>
+cudaError_t launch_adv_t(const dg_hex_mesh_s& m, const double* vel, const double* u, double* out, double* k, double a,
+                         double b, double dt, cudaStream_t s) {
+  using C = HexCfg<N>;
+  const double sc = RK ? dt : 1.0;
+  AdvCoef cf;
+  for (int d = 0; d < 3; ++d) {
+    cf.n[d] = m.n[d];
+    const double two_h = 2.0 / (m.L[d] / m.n[d]);
+    cf.dsc[d] = -vel[d] * two_h * sc;
+    cf.face[d][0] = two_h / m.w[0] * 0.5 * (-vel[d] - std::fabs(vel[d])) * sc;
+    cf.face[d][1] = two_h / m.w[N] * 0.5 * (vel[d] - std::fabs(vel[d])) * sc;
+  }
+  cf.inflow = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int end = 0; end < 2; ++end)
+      if (cf.face[d][end] != 0.0) cf.inflow |= 1 << (2 * d + end);
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_adv_kernel<N, RK><<<(unsigned)blocks, C::NT, 0, s>>>(u, out, k, m.D_dev, cf, m.K, a, b, a != 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adv(const dg_hex_mesh_s& m, const double* vel, const double* u, double* out, double* k, bool rk,
+                       double a, double b, double dt, cudaStream_t s) {
+  switch (m.N) {
+#define DG_CASE(NN)                                                         \
+  case NN:                                                                  \
+    return rk ? launch_adv_t<NN, true>(m, vel, u, out, k, a, b, dt, s)      \
+              : launch_adv_t<NN, false>(m, vel, u, out, k, a, b, dt, s);
+    DG_CASE(1)
+    DG_CASE(2)
+    DG_CASE(3)
+    DG_CASE(4)
+#undef DG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <int N, bool RK>
 cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a, double b,
                      double dt, cudaStream_t s) {
   using C = HexCfg<N>;
+  const double sc = RK ? dt : 1.0;
   HexGeo geo;
   for (int d = 0; d < 3; ++d) {
     geo.n[d] = m.n[d];
-    geo.two_h[d] = 2.0 / (m.L[d] / m.n[d]);
+    const double two_h = 2.0 / (m.L[d] / m.n[d]);
+    geo.dsc[d] = -two_h * sc;
+    geo.lf[d][0] = 0.5 * two_h / m.w[0] * sc;
+    geo.lf[d][1] = 0.5 * two_h / m.w[N] * sc;
   }
-  geo.lift[0] = 1.0 / m.w[0];
-  geo.lift[1] = 1.0 / m.w[N];
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
-  hex_rhs_kernel<N, RK><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b, dt, m.status);
+  hex_rhs_kernel<N, RK><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b, a != 0.0,
+                                                           m.status);
   return cudaGetLastError();
 }
 
@@ -329,6 +465,10 @@ int dg_hex_mesh_create(const dg_hex_desc* d, dg_hex_mesh* out) {
   m->M = M;
   m->Np = M * M * M;
   m->K = (int64_t)d->n[0] * d->n[1] * d->n[2];
+  if (m->K > INT32_MAX) {
+    delete m;
+    return dg::fail(DG_ERR_INVALID_ARG, "at most 2^31 - 1 hexahedra");
+  }
   m->nodes = x;
   std::string err;
   if (!dg::hexk::build_operators(x, m->w, m->D, err)) {
@@ -387,6 +527,31 @@ int dg_hex_rhs(dg_hex_mesh m, dg_gas gas, const double* q, double* rhs, void* st
 int dg_hex_rk_stage(dg_hex_mesh m, dg_gas gas, int32_t stage, double dt, const double* q_in, double* q_out, double* k,
                     void* stream) {
   return hex_run(m, gas, q_in, q_out, k, true, stage, dt, stream);
+}
+
+static int hex_adv_run(dg_hex_mesh m, const double* vel, const double* u, double* out, double* k, bool rk, int stage,
+                       double dt, void* stream) {
+  if (!m || !vel) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh or velocity");
+  if (!u || !out) return dg::fail(DG_ERR_INVALID_ARG, "NULL state or output");
+  if (rk && !k) return dg::fail(DG_ERR_INVALID_ARG, "NULL RK register k");
+  if (rk && (stage < 0 || stage > 4)) return dg::fail(DG_ERR_INVALID_ARG, "stage must be in 0..4");
+  if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(vel[d])) return dg::fail(DG_ERR_INVALID_ARG, "the velocity must be finite");
+  const size_t n = (size_t)m->K * m->Np;
+  if (u == out || (u < out + n && out < u + n)) return dg::fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
+  const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
+  const cudaError_t e = dg::hexk::launch_adv(*m, vel, u, out, k, rk, a, b, dt, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral advection kernel");
+}
+
+int dg_hex_advection_rhs(dg_hex_mesh m, const double* velocity, const double* u, double* rhs, void* stream) {
+  return hex_adv_run(m, velocity, u, rhs, nullptr, false, 0, 0.0, stream);
+}
+
+int dg_hex_advection_rk_stage(dg_hex_mesh m, const double* velocity, int32_t stage, double dt, const double* u_in,
+                              double* u_out, double* k, void* stream) {
+  return hex_adv_run(m, velocity, u_in, u_out, k, true, stage, dt, stream);
 }
 
 int dg_hex_status(dg_hex_mesh m, uint32_t* bits, int reset) {

@@ -324,14 +324,22 @@ class HexMesh:
             pass
 
 
+def _hex_sized(mesh: HexMesh, nvar, **tensors):
+    for name, t in tensors.items():
+        if t is not None and t.numel() != nvar * mesh.K * mesh.Np:
+            raise ValueError(f"{name} must hold {nvar} x {mesh.K} x {mesh.Np} values, got {t.numel()}")
+
+
 def dg_hex_rhs(mesh: HexMesh, gas: Gas, q, rhs, stream=None):
     import torch
+    _hex_sized(mesh, 5, q=q, rhs=rhs)
     check(load().dg_hex_rhs(mesh.handle, gas.handle, _dptr(q, torch.float64, "q"), _dptr(rhs, torch.float64, "rhs"),
                             _stream_ptr(stream)))
 
 
 def dg_hex_rk_stage(mesh: HexMesh, gas: Gas, stage, dt, q_in, q_out, k, stream=None):
     import torch
+    _hex_sized(mesh, 5, q_in=q_in, q_out=q_out, k=k)
     check(load().dg_hex_rk_stage(mesh.handle, gas.handle, int(stage), float(dt), _dptr(q_in, torch.float64, "q_in"),
                                  _dptr(q_out, torch.float64, "q_out"), _dptr(k, torch.float64, "k"),
                                  _stream_ptr(stream)))
@@ -351,6 +359,47 @@ def hex_lsrk4_step(mesh: HexMesh, gas: Gas, q, dt, steps=1, stream=None, work=No
     if cur is not q:
         q.copy_(cur)
     return q
+
+
+def _velocity(a):
+    v = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if v.size != 3:
+        raise ValueError("the advection velocity has 3 components")
+    return v
+
+
+def dg_hex_advection_rhs(mesh: HexMesh, velocity, u, rhs, stream=None):
+    """rhs = right-hand side of scalar advection of u[K][Np] with the constant velocity[3]."""
+    import torch
+    _hex_sized(mesh, 1, u=u, rhs=rhs)
+    v = _velocity(velocity)
+    check(load().dg_hex_advection_rhs(mesh.handle, _hptr(v), _dptr(u, torch.float64, "u"),
+                                      _dptr(rhs, torch.float64, "rhs"), _stream_ptr(stream)))
+
+
+def dg_hex_advection_rk_stage(mesh: HexMesh, velocity, stage, dt, u_in, u_out, k, stream=None):
+    import torch
+    _hex_sized(mesh, 1, u_in=u_in, u_out=u_out, k=k)
+    v = _velocity(velocity)
+    check(load().dg_hex_advection_rk_stage(mesh.handle, _hptr(v), int(stage), float(dt),
+                                           _dptr(u_in, torch.float64, "u_in"), _dptr(u_out, torch.float64, "u_out"),
+                                           _dptr(k, torch.float64, "k"), _stream_ptr(stream)))
+
+
+def hex_advection_lsrk4_step(mesh: HexMesh, velocity, u, dt, steps=1, stream=None, work=None):
+    """Advance u in place by ``steps`` LSRK4 steps of scalar advection (ping-pong buffers)."""
+    import torch
+    if work is None:
+        work = (torch.empty_like(u), torch.zeros_like(u))
+    ub, k = work
+    cur, nxt = u, ub
+    for _ in range(steps):
+        for s in range(5):
+            dg_hex_advection_rk_stage(mesh, velocity, s, dt, cur, nxt, k, stream=stream)
+            cur, nxt = nxt, cur
+    if cur is not u:
+        u.copy_(cur)
+    return u
 
 
 # ---- learned temperature guess -------------------------------------------------------------

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle.hex as hx
-from oracle.lsrk import lsrk4_step
+from oracle.lsrk import lsrk4_stage, lsrk4_step
 from oracle.thermo import PerfectGas
 from tests._gpu import rel_err, torch_cuda
 from workloads import isentropic_vortex, uniform_perturbation
@@ -101,3 +101,90 @@ def test_hex_vortex_full_size_stage():
     want = hx.hex_rhs_strong(ref, case["box"], case["q"], GAS)
     assert rel_err(k.cpu().numpy(), cfg.dt * want) <= TOL
     assert mesh.status() == 0
+
+
+# --- scalar advection -------------------------------------------------------------------------------
+
+VELOCITIES = [(1.0, -0.5, 0.25), (0.0, 0.0, -2.0), (-1.0, 0.3, 0.0)]
+
+
+def _adv_setup(n, N, noise=1e-3, seed=0):
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    from workloads import advected_wave
+    box = hex_box(n, 1.0)
+    x = gll_nodes(N)
+    ref = hx.hex_reference(x)
+    u0 = advected_wave(hex_nodes(box, x))
+    u0 = u0 + noise * np.random.default_rng(seed).uniform(-1.0, 1.0, u0.shape)
+    mesh = dg.HexMesh(box["n"], box["L"], N, x)
+    return torch, dg, box, ref, u0, mesh
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, (3, 2, 2), (5, 1, 3)])
+@pytest.mark.parametrize("vel", VELOCITIES)
+def test_hex_advection_rhs(n, N, vel):
+    torch, dg, box, ref, u0, mesh = _adv_setup(n, N)
+    u = torch.tensor(u0, device="cuda")
+    rhs = torch.empty_like(u)
+    dg.dg_hex_advection_rhs(mesh, vel, u, rhs)
+    want = hx.hex_advection_rhs_strong(ref, box, u0, vel)
+    assert _rel(rhs.cpu().numpy(), want) <= TOL
+
+
+def test_hex_advection_many_blocks_ragged():
+    """More elements than one block holds, with a ragged last block (5 x 7 x 3 = 105 elements)."""
+    torch, dg, box, ref, u0, mesh = _adv_setup((5, 7, 3), 1)
+    u = torch.tensor(u0, device="cuda")
+    rhs = torch.empty_like(u)
+    dg.dg_hex_advection_rhs(mesh, VELOCITIES[0], u, rhs)
+    assert _rel(rhs.cpu().numpy(), hx.hex_advection_rhs_strong(ref, box, u0, VELOCITIES[0])) <= TOL
+
+
+def test_hex_advection_two_rk4_steps():
+    torch, dg, box, ref, u0, mesh = _adv_setup((4, 3, 2), 2)
+    dt, vel = 2e-3, VELOCITIES[0]
+    u = torch.tensor(u0, device="cuda")
+    dg.hex_advection_lsrk4_step(mesh, vel, u, dt, steps=2)
+    f = lambda v: hx.hex_advection_rhs_strong(ref, box, v, vel)
+    want = lsrk4_step(lsrk4_step(u0, dt, f), dt, f)
+    assert _rel(u.cpu().numpy() - u0, want - u0) <= TOL
+
+
+def test_hex_advection_rejects_bad_arguments():
+    torch, dg, box, ref, u0, mesh = _adv_setup(2, 2)
+    from paper_2512_17101_gb300 import capi
+    u = torch.tensor(u0, device="cuda")
+    rhs = torch.empty_like(u)
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_advection_rhs(mesh, (np.nan, 0.0, 0.0), u, rhs)
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_advection_rhs(mesh, VELOCITIES[0], u, u)
+    with pytest.raises(ValueError):
+        dg.dg_hex_advection_rhs(mesh, VELOCITIES[0], u[:-1], rhs[:-1])
+    with pytest.raises(ValueError):
+        dg.dg_hex_advection_rhs(mesh, (1.0, 0.0), u, rhs)
+
+
+@pytest.mark.slow
+def test_hex_advection_full_size_stage():
+    """The advection benchmark workload (128^3 hexahedra, N = 1): the stage the benchmark times."""
+    from workloads.configs import build_hex_advection_case, get_config
+    cfg = get_config("hex_advection")
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    case = build_hex_advection_case(cfg)
+    ref = hx.hex_reference(case["nodes1d"])
+    mesh = dg.HexMesh(case["box"]["n"], case["box"]["L"], cfg.N, case["nodes1d"])
+    u_in = torch.tensor(case["u"], device="cuda")
+    u_out, k = torch.empty_like(u_in), torch.zeros_like(u_in)
+    dg.dg_hex_advection_rk_stage(mesh, case["velocity"], 0, cfg.dt, u_in, u_out, k)
+    f = lambda v: hx.hex_advection_rhs_strong(ref, case["box"], v, case["velocity"])
+    want_u, want_k = lsrk4_stage(case["u"], np.zeros_like(case["u"]), 0, cfg.dt, f)
+    assert _rel(k.cpu().numpy(), want_k) <= TOL
+    assert _rel(u_out.cpu().numpy() - case["u"], want_u - case["u"]) <= TOL

@@ -19,6 +19,7 @@ from .states import (
     uniform_perturbation,
     freestream,
     sin_shear,
+    advected_wave,
 )
 from .gas import IdealGas, Nasa7Mixture, seeded_nasa7_mixture
 from .configs import CONFIGS, get_config

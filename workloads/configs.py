@@ -20,7 +20,7 @@ import numpy as np
 from .gas import IdealGas, seeded_nasa7_mixture, mixture_primitive_state
 from .hexmesh import gll_nodes, hex_box, hex_nodes
 from .mesh import box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
-from .states import isentropic_vortex, taylor_green, uniform_perturbation
+from .states import advected_wave, isentropic_vortex, taylor_green, uniform_perturbation
 
 
 @dataclass(frozen=True)
@@ -75,6 +75,13 @@ def _mixture_dt(n, N):
     return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (cmax + 10.0 * math.sqrt(3.0)))
 
 
+ADVECTION_VELOCITY = (1.0, 0.5, 0.25)
+
+
+def _advection_dt(n, N, velocity=ADVECTION_VELOCITY):
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * sum(abs(v) for v in velocity))
+
+
 _NS_GAS = IdealGas(gamma=1.4, R=1.0, mu=1.0e-3, Pr=0.71)
 
 CONFIGS = {
@@ -98,6 +105,12 @@ CONFIGS = {
         description="Euler on tensor-product hexahedra (the paper's element type), periodic box of 32^3 "
                     "hexahedra, N=4 (125 GLL nodes each, 4,096,000 DOFs), isentropic vortex + U(+-1e-3), "
                     "10 RK4 steps"),
+    "hex_advection": Config(
+        name="hex_advection", n=128, N=1, physics="advection_hex", state="wave", steps=10,
+        dt=_advection_dt(128, 1),
+        description="scalar advection on tensor-product hexahedra, p = 1 (the paper's GPU comparison "
+                    "workload), periodic box of 128^3 hexahedra (8 GLL nodes each, 16,777,216 DOFs), "
+                    "velocity (1, 0.5, 0.25), smooth wave + U(+-1e-3), 10 RK4 steps"),
     "mixture_learned": Config(
         name="mixture_learned", n=32, N=2, physics="euler_mixture", state="mixture", steps=1, dt=_mixture_dt(32, 2),
         description="7-species Euler mixture, seeded NASA-7, 32^3 hexes x 6 = 196,608 tets, N=2; "
@@ -144,6 +157,18 @@ def build_hex_case(cfg: Config, n=None, N=None):
     q = isentropic_vortex(xyz, 0.0, gamma=cfg.gas.gamma, period=box["L"])
     q = uniform_perturbation(q, 1.0e-3, seed=cfg.seed)
     return dict(box=box, nodes1d=x, xyz=xyz, q=q, n=n, N=N)
+
+
+def build_hex_advection_case(cfg: Config, n=None, N=None):
+    """Mesh, node set, velocity and initial scalar u[K][Np] of the advection config."""
+    n = cfg.n if n is None else n
+    N = cfg.N if N is None else N
+    box = hex_box(n, 1.0)
+    x = gll_nodes(N)
+    xyz = hex_nodes(box, x)
+    u = advected_wave(xyz, 0.0, velocity=ADVECTION_VELOCITY)
+    u = uniform_perturbation(u[None], 1.0e-3, seed=cfg.seed)[0]
+    return dict(box=box, nodes1d=x, xyz=xyz, u=u, velocity=ADVECTION_VELOCITY, n=n, N=N)
 
 
 def batched_cases(ncases=64, seed=0, n_min=2, n_max=20):

@@ -100,6 +100,14 @@ def sin_shear(xyz, *, gamma=1.4, amp=0.1, L=1.0, rho=1.0, p=1.0):
     return _conserved_perfect_gas(rho + z, u, z, z, p + z, gamma)
 
 
+def advected_wave(xyz, t=0.0, *, velocity=(1.0, 0.5, 0.25), L=1.0):
+    """Smooth periodic scalar on the box [0, L]^3 translated by velocity t: the exact solution of
+    du/dt + a . grad u = 0 for u(x, 0) = sin(2 pi x/L) cos(2 pi y/L) + 0.3 sin(2 pi z/L)."""
+    k = 2.0 * np.pi / L
+    x, y, z = (xyz[..., d] - velocity[d] * t for d in range(3))
+    return np.sin(k * x) * np.cos(k * y) + 0.3 * np.sin(k * z)
+
+
 def uniform_perturbation(q, amplitude, seed=0):
     """q + U(-amplitude, amplitude), drawn per conserved variable per node (PCG64, ``seed``)."""
     rng = np.random.Generator(np.random.PCG64(seed))
