@@ -16,7 +16,10 @@ definitions here:
 * faces of a periodic mesh are paired by their centroids modulo the box
   lengths; the two centroids fix the periodic shift between the faces (a
   whole number of box lengths) and face nodes are paired by coordinates under
-  that shift.
+  that shift;
+* a face that finds no partner is a boundary face, allowed only where the
+  caller's face_bc[k][f] names a boundary condition (oracle/boundary.py); its
+  face nodes point at themselves in vmapP and carry that code in ``bc``.
 """
 
 from __future__ import annotations
@@ -91,7 +94,8 @@ class Connectivity:
     EToE: np.ndarray  # [K][4]
     EToF: np.ndarray  # [K][4]
     vmapM: np.ndarray  # [K][4 Nfp] flat node index (k Np + n) of each own face node
-    vmapP: np.ndarray  # [K][4 Nfp] flat node index of the matching neighbour node
+    vmapP: np.ndarray  # [K][4 Nfp] flat node index of the matching neighbour node (own node on a boundary face)
+    bc: np.ndarray = None  # [K][4 Nfp] boundary-condition code of each face node, 0 on interior faces
 
 
 def _wrap(x, period):
@@ -105,11 +109,13 @@ def _wrap(x, period):
 
 
 
-def connect(vertices: np.ndarray, period, ref: RefElement, tol_rel: float = 1e-8) -> Connectivity:
+def connect(vertices: np.ndarray, period, ref: RefElement, tol_rel: float = 1e-8, face_bc=None) -> Connectivity:
     """Pair every face with its neighbour and every face node with its partner.
 
-    Raises ValueError if some face or face node has no unique partner (the
-    mesh must be closed under the periodic identification).
+    Without face_bc, raises ValueError if some face or face node has no unique
+    partner (the mesh must be closed under the periodic identification).  With
+    face_bc [K][4], a face without a partner must carry a non-zero code there
+    and a paired face must carry 0.
     """
     v = np.asarray(vertices, dtype=np.float64)
     period = np.asarray(period, dtype=np.float64)
@@ -126,15 +132,23 @@ def connect(vertices: np.ndarray, period, ref: RefElement, tol_rel: float = 1e-8
             table.setdefault(tuple(keys[k, f]), []).append((k, f))
     EToE = np.full((K, 4), -1, dtype=np.int64)
     EToF = np.full((K, 4), -1, dtype=np.int64)
+    fbc = np.zeros((K, 4), dtype=np.int64) if face_bc is None else np.asarray(face_bc, dtype=np.int64).reshape(K, 4)
     for key, lst in table.items():
+        if len(lst) == 1 and fbc[lst[0]] != 0:
+            continue  # boundary face
         if len(lst) != 2:
             raise ValueError(f"face with centroid key {key} has {len(lst)} occurrences (expected 2)")
+        if fbc[lst[0]] != 0 or fbc[lst[1]] != 0:
+            raise ValueError(f"interior face with centroid key {key} carries a boundary condition")
         (k1, f1), (k2, f2) = lst
         EToE[k1, f1], EToF[k1, f1] = k2, f2
         EToE[k2, f2], EToF[k2, f2] = k1, f1
     xyz = affine_nodes(v, ref.nodes)  # [K][Np][3]
     vmapM = (np.arange(K)[:, None, None] * Np + ref.Fmask[None, :, :]).reshape(K, 4 * Nfp)
     vmapP = np.zeros((K, 4, Nfp), dtype=np.int64)
+    bnd = EToE < 0
+    EToE = np.where(bnd, np.arange(K)[:, None], EToE)  # boundary faces point at themselves
+    EToF = np.where(bnd, np.arange(4)[None, :], EToF)
     for f in range(4):
         own = xyz[:, ref.Fmask[f]]  # [K][Nfp][3]
         nb = xyz[EToE[:, f][:, None], ref.Fmask[EToF[:, f]]]  # [K][Nfp][3]
@@ -151,4 +165,7 @@ def connect(vertices: np.ndarray, period, ref: RefElement, tol_rel: float = 1e-8
         if np.any(np.sort(j, axis=1) != np.arange(Nfp)[None, :]):
             raise ValueError("face node matching is not one-to-one")
         vmapP[:, f] = EToE[:, f][:, None] * Np + ref.Fmask[EToF[:, f][:, None], j]
-    return Connectivity(EToE=EToE, EToF=EToF, vmapM=vmapM, vmapP=vmapP.reshape(K, 4 * Nfp))
+    bc = np.repeat(np.where(bnd, fbc, 0), Nfp, axis=1)  # [K][4 Nfp]
+    EToE = np.where(bnd, -1, EToE)
+    EToF = np.where(bnd, -1, EToF)
+    return Connectivity(EToE=EToE, EToF=EToF, vmapM=vmapM, vmapP=vmapP.reshape(K, 4 * Nfp), bc=bc)

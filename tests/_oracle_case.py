@@ -7,6 +7,7 @@ import numpy as np
 from oracle.geometry import connect, geometric_factors, affine_nodes
 from oracle.refelem import build_reference
 from workloads import box_mesh, equispaced_tet_nodes
+from workloads.mesh import box_face_bc
 
 
 @functools.lru_cache(maxsize=None)
@@ -15,13 +16,14 @@ def reference(N):
 
 
 class Disc:
-    def __init__(self, vertices, period, N):
+    def __init__(self, vertices, period, N, face_bc=None):
         self.N = N
         self.vertices = vertices
         self.period = np.asarray(period, float)
+        self.face_bc = face_bc
         self.ref = reference(N)
         self.geo = geometric_factors(vertices)
-        self.conn = connect(vertices, period, self.ref)
+        self.conn = connect(vertices, period, self.ref, face_bc=face_bc)
         self.xyz = affine_nodes(vertices, self.ref.nodes)
         self.K = vertices.shape[0]
 
@@ -42,3 +44,13 @@ class Disc:
 def box_disc(n, N, L=1.0):
     v, per = box_mesh(n, L)
     return Disc(v, per, N)
+
+
+def bc_disc(n, N, sides, L=1.0):
+    """Box mesh with boundary conditions sides[(axis, end)] = code; the axes that carry codes are
+    not periodic."""
+    v, per = box_mesh(n, L)
+    per = np.array(per, dtype=float)
+    for axis, _ in sides:
+        per[axis] = 0.0
+    return Disc(v, per, N, face_bc=box_face_bc(v, L, sides=sides))

@@ -74,6 +74,27 @@ def box_mesh(n, L=1.0, origin=(0.0, 0.0, 0.0)):
     return np.ascontiguousarray(verts), np.array([Lx, Ly, Lz], dtype=np.float64)
 
 
+# vertex triples of the four faces of a tetrahedron, in the library's face order
+TET_FACES = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
+
+
+def box_face_bc(vertices, L=1.0, origin=(0.0, 0.0, 0.0), sides=None):
+    """Boundary-condition codes face_bc [K][4] (int32) of a box mesh: the code sides[(axis, end)]
+    (end 0 = the plane x_axis = origin, 1 = origin + L) on faces lying in that plane, 0 elsewhere.
+    Axes whose planes carry codes must be meshed without periodicity along them."""
+    v = np.asarray(vertices, dtype=np.float64)
+    Ls = np.asarray(_as3(L, float))
+    o = np.asarray(origin, dtype=np.float64)
+    out = np.zeros((v.shape[0], 4), dtype=np.int32)
+    tol = 1e-9 * Ls.max()
+    for (axis, end), code in (sides or {}).items():
+        plane = o[axis] + (Ls[axis] if end else 0.0)
+        for f, tri in enumerate(TET_FACES):
+            on = np.all(np.abs(v[:, list(tri), axis] - plane) <= tol, axis=1)
+            out[on, f] = code
+    return out
+
+
 def equispaced_tet_nodes(N: int) -> np.ndarray:
     """Equispaced (barycentric-lattice) nodes of the reference tetrahedron.
 
