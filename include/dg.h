@@ -79,7 +79,29 @@ typedef struct {
                              /* unwrapped across periodic seams; positive volume  */
   double period[3];          /* periodic box lengths; 0 = not periodic along it    */
   int32_t flags;             /* DG_MESH_* bits                                     */
+  const int32_t* face_bc;    /* host [K][4] or NULL: DG_BC_* code of each face that */
+                             /* has no partner, 0 on paired faces (face f has the   */
+                             /* vertex triple 012, 013, 123, 023 for f = 0..3)      */
 } dg_mesh_desc;
+
+/* Boundary conditions of faces without a partner (Sec. 5.3-5.4 run wall-bounded and inflow /
+ * outflow cases; the paper does not write out their treatment).  Ghost-state reading: at a
+ * boundary face node the exterior trace q+ is built from the interior trace q- and the outward
+ * unit normal n and fed to the same numerical fluxes as an interior face:
+ *   DG_BC_SLIP_WALL   q+ = (rho, m - 2 (m.n) n, rho E): mirror state; with viscosity the wall
+ *                     is shear-free and adiabatic: traction t+ = 2 (n.t-) n - t-, energy flux
+ *                     e+ = -e- (t = tau n, e = n.(u.tau + kappa grad T));
+ *   DG_BC_NOSLIP_WALL q+ = (rho, -m, rho E); viscous t+ = t-, e+ = -e- (adiabatic, no work);
+ *   DG_BC_INFLOW      q+ = the state set by dg_mesh_set_inflow (supersonic inflow);
+ *   DG_BC_OUTFLOW     q+ = q- (supersonic outflow).
+ * BR1 exterior values are w(q+); away from walls the viscous exterior flux is the interior one.
+ * Meshes with boundary faces run in the FP64 form with a perfect gas (Euler or Navier-Stokes);
+ * the mixed-precision form, the mixture and the batched form reject them (DG_ERR_UNSUPPORTED).
+ * In the vmapP of dg_mesh_connectivity a boundary face node holds -code. */
+#define DG_BC_SLIP_WALL 1
+#define DG_BC_NOSLIP_WALL 2
+#define DG_BC_INFLOW 3
+#define DG_BC_OUTFLOW 4
 
 /* Build the host-side tables only (no device memory, no CUDA call).  Such a
  * mesh answers dg_mesh_info / dg_mesh_operators / dg_mesh_connectivity and is
@@ -93,10 +115,17 @@ typedef struct {
  * pair's periodic shift), then copies them to the current device together with
  * a scratch buffer for the viscous flux (9 doubles per node).  Sec. 1 Fig. 1
  * (element-local arrays), Sec. 4.1.2 / Sec. 4.3 (connectivity, indirect gather).
- * Every face must find exactly one partner (closed periodic meshes): otherwise
- * DG_ERR_INVALID_ARG.  Allocates device memory (cudaMalloc); *out owns it. */
+ * Every face must find exactly one partner, or carry a DG_BC_* code in face_bc;
+ * a paired face must carry 0; otherwise DG_ERR_INVALID_ARG.  Allocates device
+ * memory (cudaMalloc); *out owns it. */
 int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out);
 int dg_mesh_free(dg_mesh mesh);
+
+/* Sets the conserved state q_in[nvar] (host; nvar = 5 for a perfect gas) that DG_BC_INFLOW
+ * faces impose.  Required before a right-hand side on a mesh with inflow faces
+ * (DG_ERR_INVALID_ARG otherwise, or when nvar differs from the gas's).  Errors:
+ * DG_ERR_INVALID_ARG (NULL, nvar outside 5..5+DG_MAX_SPECIES, rho <= 0 or non-finite). */
+int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar);
 
 /* Sizes of an uploaded mesh. Any pointer may be NULL. */
 int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp);

@@ -21,6 +21,7 @@ DG_ERR_UNSUPPORTED = -7
 DG_STATUS_NONPHYSICAL = 1
 DG_STATUS_NO_CONVERGENCE = 2
 DG_STATUS_TIMEOUT = 4
+DG_BC_SLIP_WALL, DG_BC_NOSLIP_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW = 1, 2, 3, 4
 DG_MAX_ORDER = 4
 DG_MAX_SPECIES = 8
 DG_GEO_STRIDE = 26
@@ -48,7 +49,7 @@ c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64,
 
 class dg_mesh_desc(ctypes.Structure):
     _fields_ = [("K", c_int32), ("N", c_int32), ("ref_nodes", c_void_p), ("vertices", c_void_p),
-                ("period", c_double * 3), ("flags", c_int32)]
+                ("period", c_double * 3), ("flags", c_int32), ("face_bc", c_void_p)]
 
 
 class dg_gas_desc(ctypes.Structure):
@@ -92,6 +93,7 @@ SIGNATURES = {
                                ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "dg_mesh_operators": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_connectivity": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_set_inflow": (c_int32, [c_void_p, c_void_p, c_int32]),
     "dg_mesh_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
     "dg_mesh_set_timing": (c_int32, [c_void_p, c_int32]),
     "dg_mesh_kernel_times": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),

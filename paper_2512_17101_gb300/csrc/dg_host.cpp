@@ -136,6 +136,14 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const dg::MeshDev& m = mesh->d;
   const dg::GasParams& g = gas->p;
   const int V = 5 + g.ns;
+  if (m.boundary_faces > 0) {
+    if (opts && opts->precision == DG_PREC_MIXED)
+      return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces run in the FP64 form only");
+    if (g.model != DG_GAS_PERFECT)
+      return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces need a perfect gas");
+    if (m.inflow_faces > 0 && m.inflow_nvar != V)
+      return fail(DG_ERR_INVALID_ARG, "the mesh has inflow faces: set the inflow state with dg_mesh_set_inflow");
+  }
   const size_t bytes = sizeof(double) * (size_t)V * m.K * m.Np;
   if (q == out || (q < out + bytes / sizeof(double) && out < q + bytes / sizeof(double)))
     return fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
@@ -222,7 +230,8 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   std::string err;
   if (!dg::build_ref_ops(desc->N, desc->ref_nodes, m->ops, err) ||
       !dg::build_geometry(desc->K, desc->vertices, m->geo, err) ||
-      !dg::build_connectivity(desc->K, desc->vertices, desc->period, m->ops, desc->ref_nodes, m->vmapP, err)) {
+      !dg::build_connectivity(desc->K, desc->vertices, desc->period, m->ops, desc->ref_nodes, desc->face_bc,
+                              m->vmapP, err)) {
     delete m;
     return fail(DG_ERR_INVALID_ARG, err);
   }
@@ -231,6 +240,12 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   d.N = desc->N;
   d.Np = m->ops.Np;
   d.Nfp = m->ops.Nfp;
+  for (int k = 0; k < d.K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      const int32_t v = m->vmapP[(size_t)k * 4 * d.Nfp + f * d.Nfp];
+      d.boundary_faces += v < 0;
+      d.inflow_faces += v == -DG_BC_INFLOW;
+    }
   if (desc->flags & DG_MESH_HOST_ONLY) {
     *out = m;
     return DG_OK;
@@ -311,6 +326,17 @@ int dg_mesh_operators(dg_mesh mesh, double* Dr, double* Ds, double* Dt, double* 
   if (Dt) std::memcpy(Dt, o.Dt.data(), sizeof(double) * o.Dt.size());
   if (LIFT) std::memcpy(LIFT, o.LIFT.data(), sizeof(double) * o.LIFT.size());
   if (Fmask) std::memcpy(Fmask, o.Fmask.data(), sizeof(int32_t) * o.Fmask.size());
+  return DG_OK;
+}
+
+int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar) {
+  if (!mesh || !q_in) return fail(DG_ERR_INVALID_ARG, "NULL mesh or inflow state");
+  if (nvar < 5 || nvar > 5 + DG_MAX_SPECIES) return fail(DG_ERR_INVALID_ARG, "nvar must be in 5..5+DG_MAX_SPECIES");
+  for (int v = 0; v < nvar; ++v)
+    if (!std::isfinite(q_in[v])) return fail(DG_ERR_INVALID_ARG, "the inflow state must be finite");
+  if (!(q_in[0] > 0)) return fail(DG_ERR_INVALID_ARG, "the inflow density must be positive");
+  for (int v = 0; v < 5 + DG_MAX_SPECIES; ++v) mesh->d.bc.q_in[v] = v < nvar ? q_in[v] : 0.0;
+  mesh->d.inflow_nvar = nvar;
   return DG_OK;
 }
 

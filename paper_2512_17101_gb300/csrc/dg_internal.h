@@ -30,8 +30,11 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err);
 bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::string& err);
 
 // Periodic face-node connectivity vmapP[K][4 Nfp] (mesh.cpp).
+// face_bc [K][4] (may be null): DG_BC_* code of the faces without a partner; their face nodes
+// get vmapP = -code.
 bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
-                        const double* ref_nodes, std::vector<int32_t>& vmapP, std::string& err);
+                        const double* ref_nodes, const int32_t* face_bc, std::vector<int32_t>& vmapP,
+                        std::string& err);
 
 // ---- device-side parameter blocks -------------------------------------------
 struct GasParams {  // passed to kernels by value
@@ -53,8 +56,17 @@ struct MixedOps {
   unsigned char* tc_vis = nullptr;  // tcgen05 BR1 table: rows (a, i), [D_a | 1/2 sum_f c_fa LIFT_f]
 };
 
+// Boundary data passed to the FP64 kernels by value: the conserved state of DG_BC_INFLOW faces.
+struct BcParams {
+  double q_in[5 + DG_MAX_SPECIES];
+};
+
 struct MeshDev {
   int K = 0, N = 0, Np = 0, Nfp = 0;
+  int boundary_faces = 0;     // faces carrying a DG_BC_* code
+  int inflow_faces = 0;       // of which DG_BC_INFLOW
+  int inflow_nvar = 0;        // 0 until dg_mesh_set_inflow
+  BcParams bc{};
   MixedOps mx;
   double* ops = nullptr;       // Dr | Ds | Dt | LIFT, row-major
   int32_t* fmask = nullptr;    // [4][Nfp]

@@ -87,6 +87,30 @@ __device__ __forceinline__ void normal_flux(const double* qv, double un, double 
     if (v < nvar) fn[v] = qv[v] * un;
 }
 
+// Exterior trace q+ at a boundary face node with code = -vmapP (DG_BC_*): the ghost states of the
+// slip wall (mirror state), the no-slip wall (momentum reversed), supersonic inflow (the mesh's
+// prescribed state) and supersonic outflow (the interior state).
+template <int V>
+__device__ __forceinline__ void ghost_state(int code, const double* qm, double nx, double ny, double nz,
+                                            const BcParams& bc, int nvar, double* qp) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) qp[v] = qm[v];
+  if (code == DG_BC_SLIP_WALL) {
+    const double mn2 = 2.0 * (qm[1] * nx + qm[2] * ny + qm[3] * nz);
+    qp[1] = qm[1] - mn2 * nx;
+    qp[2] = qm[2] - mn2 * ny;
+    qp[3] = qm[3] - mn2 * nz;
+  } else if (code == DG_BC_NOSLIP_WALL) {
+    qp[1] = -qm[1];
+    qp[2] = -qm[2];
+    qp[3] = -qm[3];
+  } else if (code == DG_BC_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (v < nvar) qp[v] = bc.q_in[v];
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Right-hand side, optionally fused with the LSRK4 stage update.
 //   RK == false: out = rhs
@@ -98,8 +122,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* __restrict__ q, double* __restrict__ out, double* __restrict__ kreg,
     const double* __restrict__ Tg, const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g,
     const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
-    unsigned* __restrict__ status, const GasParams gp, const int K, const int nvar, const double a,
-    const double b, const double dt) {
+    unsigned* __restrict__ status, const GasParams gp, const BcParams bc, const int K, const int nvar,
+    const double a, const double b, const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   extern __shared__ double smem[];
@@ -177,17 +201,21 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* G = sGeo + e * GS;
     const double nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
     const int own = e * Np + sFm[m];
-    const int P = vmapP[(size_t)(e0 + e) * NF + m];
+    const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
     double qm[V], qp[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      qm[v] = v < nvar ? sQ[v * NODES + own] : 0.0;
-      qp[v] = v < nvar ? q[v * KNp + P] : 0.0;
+    for (int v = 0; v < V; ++v) qm[v] = v < nvar ? sQ[v * NODES + own] : 0.0;
+    if (P >= 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) qp[v] = v < nvar ? q[v * KNp + P] : 0.0;
+    } else {
+      ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
     }
     const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
     double pm, cm, pp, cp;
     thermo<PHYS, V>(gp, qm, irm, PHYS == MIXTURE ? sT[own] : 0.0, pm, cm);
-    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? Tg[P] : 0.0, pp, cp);
+    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? (P >= 0 ? Tg[P] : sT[own]) : 0.0, pp, cp);
+    if (P < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
     const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
     const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
     const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
@@ -198,8 +226,10 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.5 * ((fm[v] - fp[v]) - lam * (qm[v] - qp[v]));
     if (PHYS == NAVIER_STOKES) {
-      // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2
+      // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2; at a boundary node the
+      // exterior normal flux (traction t+, energy flux e+) follows the face's condition
       const double nn3[3] = {nx, ny, nz};
+      double tm[3], tp[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         double dm = 0.0, dp = 0.0;
@@ -207,16 +237,25 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
         for (int d = 0; d < 3; ++d) {
           const int c = tau_index(i, d);
           dm = fma(nn3[d], sFv[c * NODES + own], dm);
-          dp = fma(nn3[d], fv_g[c * KNp + P], dp);
+          if (P >= 0) dp = fma(nn3[d], fv_g[c * KNp + P], dp);
         }
-        g[1 + i] -= 0.5 * (dm - dp);
+        tm[i] = dm;
+        tp[i] = P >= 0 ? dp : dm;
       }
+      if (P == -DG_BC_SLIP_WALL) {  // shear-free: t+ = 2 (n.t-) n - t-
+        const double tn2 = 2.0 * (tm[0] * nx + tm[1] * ny + tm[2] * nz);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tp[i] = tn2 * nn3[i] - tm[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) g[1 + i] -= 0.5 * (tm[i] - tp[i]);
       double em = 0.0, ep = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         em = fma(nn3[d], sFv[(6 + d) * NODES + own], em);
-        ep = fma(nn3[d], fv_g[(6 + d) * KNp + P], ep);
+        if (P >= 0) ep = fma(nn3[d], fv_g[(6 + d) * KNp + P], ep);
       }
+      if (P < 0) ep = (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) ? -em : em;  // adiabatic walls
       g[4] -= 0.5 * (em - ep);
     }
 #pragma unroll
@@ -281,7 +320,7 @@ template <int N>
 __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
     const double* __restrict__ q, double* __restrict__ fv_out, const double* __restrict__ ops_g,
     const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP,
-    unsigned* __restrict__ status, const GasParams gp, const int K) {
+    unsigned* __restrict__ status, const GasParams gp, const BcParams bc, const int K) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   constexpr int W = 5;
@@ -318,12 +357,20 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
 
   for (int j = tid; j < nel * NF; j += blockDim.x) {
     const int e = j / NF, m = j - e * NF, f = m / Nfp;
-    const double fs = sGeo[e * GS + 12 + 4 * f];
+    const double* G = sGeo + e * GS;
+    const double fs = G[12 + 4 * f];
     const int own = e * Np + sFm[m];
-    const int P = vmapP[(size_t)(e0 + e) * NF + m];
+    const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
     double qp[5];
+    if (P >= 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + P];
+      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + P];
+    } else {  // exterior values w(q+) of the face's ghost state
+      double qm[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qm[v] = q[v * KNp + base + own];
+      ghost_state<5>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, 5, qp);
+    }
     const double irp = 1.0 / qp[0];
     const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
     const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
@@ -437,7 +484,7 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
   rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP, m.scratch,
-                                                           m.status, g, m.K, nvar, a, b, dt);
+                                                           m.status, g, m.bc, m.K, nvar, a, b, dt);
   return cudaGetLastError();
 }
 

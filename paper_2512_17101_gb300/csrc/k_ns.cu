@@ -22,7 +22,7 @@ cudaError_t launch_viscous_t(const MeshDev& m, const GasParams& g, const double*
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  kern::viscous_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.scratch, m.ops, m.fmask, m.geo, m.vmapP, m.status, g,
+  kern::viscous_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.scratch, m.ops, m.fmask, m.geo, m.vmapP, m.status, g, m.bc,
                                                       m.K);
   return cudaGetLastError();
 }

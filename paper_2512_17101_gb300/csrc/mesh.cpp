@@ -11,7 +11,8 @@
 //   triangles of area 2).
 // Faces are paired by centroid modulo the period; the centroid difference of a
 // pair gives its periodic shift (whole box lengths), under which face nodes are
-// paired by coordinates.
+// paired by coordinates.  A face without a partner must carry a boundary-condition
+// code (face_bc), which its face nodes keep in vmapP as -code.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -107,7 +108,8 @@ bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::s
 }
 
 bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
-                        const double* ref_nodes, std::vector<int32_t>& vmapP, std::string& err) {
+                        const double* ref_nodes, const int32_t* face_bc, std::vector<int32_t>& vmapP,
+                        std::string& err) {
   const int Np = ops.Np, Nfp = ops.Nfp, NF = 4 * Nfp;
   if ((int64_t)K * Np >= (int64_t)INT32_MAX) {
     err = "K * Np exceeds the int32 node index range";
@@ -137,6 +139,21 @@ bool build_connectivity(int K, const double* verts, const double period[3], cons
   for (size_t i = 0; i < order.size();) {
     size_t j = i + 1;
     while (j < order.size() && key[order[j]] == key[order[i]]) ++j;
+    if (j - i == 1 && face_bc && face_bc[order[i]] != 0) {  // boundary face
+      const int code = face_bc[order[i]];
+      if (code < DG_BC_SLIP_WALL || code > DG_BC_OUTFLOW) {
+        err = "face_bc holds an unknown boundary-condition code " + std::to_string(code);
+        return false;
+      }
+      i = j;
+      continue;
+    }
+    if (j - i == 2 && face_bc && (face_bc[order[i]] != 0 || face_bc[order[i + 1]] != 0)) {
+      const int kf = face_bc[order[i]] != 0 ? order[i] : order[i + 1];
+      err = "face " + std::to_string(kf % 4) + " of element " + std::to_string(kf / 4) +
+            " has a partner but carries a boundary condition";
+      return false;
+    }
     if (j - i != 2) {
       int kf = order[i];
       err = "face " + std::to_string(kf % 4) + " of element " + std::to_string(kf / 4) + " has " +
@@ -162,6 +179,10 @@ bool build_connectivity(int K, const double* verts, const double period[3], cons
   for (int k = 0; k < K; ++k)
     for (int f = 0; f < 4; ++f) {
       const int pf = partner[4 * k + f];
+      if (pf < 0) {  // boundary face: every face node holds -code
+        for (int i = 0; i < Nfp; ++i) vmapP[(size_t)k * NF + f * Nfp + i] = -face_bc[4 * k + f];
+        continue;
+      }
       const int k2 = pf / 4, f2 = pf % 4;
       double shift[3];
       for (int x = 0; x < 3; ++x) {

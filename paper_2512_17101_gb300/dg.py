@@ -53,12 +53,18 @@ def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0):
 class Mesh:
     """An uploaded mesh (dg_mesh handle)."""
 
-    def __init__(self, vertices, period, N, ref_nodes, host_only=False):
+    def __init__(self, vertices, period, N, ref_nodes, host_only=False, face_bc=None):
+        """face_bc: optional [K][4] DG_BC_* codes of the faces without a partner (0 elsewhere)."""
         lib = load()
         self._v = np.ascontiguousarray(vertices, dtype=np.float64)
         self._r = np.ascontiguousarray(ref_nodes, dtype=np.float64)
         if self._v.ndim != 3 or self._v.shape[1:] != (4, 3):
             raise ValueError("vertices must be [K][4][3]")
+        self._bc = None
+        if face_bc is not None:
+            self._bc = np.ascontiguousarray(face_bc, dtype=np.int32)
+            if self._bc.shape != (self._v.shape[0], 4):
+                raise ValueError("face_bc must be [K][4]")
         d = capi.dg_mesh_desc()
         d.K = self._v.shape[0]
         d.N = int(N)
@@ -67,6 +73,7 @@ class Mesh:
         for i in range(3):
             d.period[i] = float(period[i])
         d.flags = capi.DG_MESH_HOST_ONLY if host_only else 0
+        d.face_bc = None if self._bc is None else _hptr(self._bc)
         h = ctypes.c_void_p()
         check(lib.dg_mesh_upload(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -87,6 +94,11 @@ class Mesh:
         geo = np.zeros((self.K, capi.DG_GEO_STRIDE))
         check(load().dg_mesh_connectivity(self.handle, _hptr(vmapP), _hptr(geo)))
         return vmapP, geo
+
+    def set_inflow(self, q_in):
+        """Conserved state imposed on DG_BC_INFLOW faces (5 values for a perfect gas)."""
+        v = np.ascontiguousarray(q_in, dtype=np.float64).reshape(-1)
+        check(load().dg_mesh_set_inflow(self.handle, _hptr(v), int(v.size)))
 
     def set_timing(self, enable=True):
         check(load().dg_mesh_set_timing(self.handle, int(enable)))

@@ -61,6 +61,51 @@ def test_host_tables_match_oracle(lib, N):
     assert np.abs(geo - expect).max() <= 1e-13 * np.abs(expect).max()
 
 
+BC_SIDES = [
+    {(1, 0): 1, (1, 1): 2},
+    {(0, 0): 3, (0, 1): 4, (2, 0): 1, (2, 1): 1},
+    {(a, e): 2 for a in range(3) for e in (0, 1)},
+]
+
+
+@pytest.mark.parametrize("sides", BC_SIDES)
+@pytest.mark.parametrize("N", [1, 3])
+def test_boundary_connectivity_matches_oracle(lib, sides, N):
+    """Faces without a partner keep -code in vmapP; the paired ones match the oracle's pairing."""
+    from paper_2512_17101_gb300 import dg
+    from tests._oracle_case import bc_disc
+    from workloads import equispaced_tet_nodes
+    d = bc_disc((3, 2, 2), N, sides)
+    m = dg.Mesh(d.vertices, d.period, N, equispaced_tet_nodes(N), host_only=True, face_bc=d.face_bc)
+    vmapP, _ = m.connectivity()
+    want = np.where(d.conn.bc != 0, -d.conn.bc, d.conn.vmapP)
+    assert np.array_equal(vmapP, want)
+
+
+def test_boundary_faces_are_checked(lib):
+    from paper_2512_17101_gb300 import capi, dg
+    from workloads import box_mesh, equispaced_tet_nodes
+    from workloads.mesh import box_face_bc
+    v, per = box_mesh((2, 2, 2), 1.0)
+    open_per = np.array([per[0], 0.0, per[2]])
+    nodes = equispaced_tet_nodes(1)
+    fb = box_face_bc(v, 1.0, sides={(1, 0): 1, (1, 1): 1})
+    dg.Mesh(v, open_per, 1, nodes, host_only=True, face_bc=fb)  # closed by walls: fine
+    with pytest.raises(capi.DGError):  # open faces without a code
+        dg.Mesh(v, open_per, 1, nodes, host_only=True)
+    with pytest.raises(capi.DGError):  # a code on faces that have partners
+        dg.Mesh(v, per, 1, nodes, host_only=True, face_bc=fb)
+    bad = fb.copy()
+    bad[bad != 0] = 9
+    with pytest.raises(capi.DGError):  # unknown code
+        dg.Mesh(v, open_per, 1, nodes, host_only=True, face_bc=bad)
+    m = dg.Mesh(v, open_per, 1, nodes, host_only=True, face_bc=fb)
+    with pytest.raises(capi.DGError):
+        m.set_inflow([0.0, 0.0, 0.0, 0.0, 1.0])  # rho <= 0
+    with pytest.raises(capi.DGError):
+        m.set_inflow([1.0, 0.0, 0.0])  # too few variables
+
+
 def test_lsrk_coefficients_match_oracle(lib):
     from paper_2512_17101_gb300 import dg
     from oracle.lsrk import RK4A, RK4B

@@ -20,6 +20,7 @@ from .states import (
     freestream,
     sin_shear,
     advected_wave,
+    channel_flow,
 )
 from .gas import IdealGas, Nasa7Mixture, seeded_nasa7_mixture
 from .configs import CONFIGS, get_config

@@ -19,8 +19,8 @@ import numpy as np
 
 from .gas import IdealGas, seeded_nasa7_mixture, mixture_primitive_state
 from .hexmesh import gll_nodes, hex_box, hex_nodes
-from .mesh import box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
-from .states import advected_wave, isentropic_vortex, taylor_green, uniform_perturbation
+from .mesh import box_face_bc, box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
+from .states import advected_wave, channel_flow, isentropic_vortex, taylor_green, uniform_perturbation
 
 
 @dataclass(frozen=True)
@@ -36,6 +36,7 @@ class Config:
     seed: int = 0
     gas: object = field(default=None)
     description: str = ""
+    walls: tuple = ()  # ((axis, end, DG_BC_* code), ...): boundary faces instead of periodicity
 
     @property
     def hexahedral(self) -> bool:
@@ -75,6 +76,10 @@ def _mixture_dt(n, N):
     return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (cmax + 10.0 * math.sqrt(3.0)))
 
 
+def _channel_dt(n, N, mach=0.3, noise=0.01):
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (mach * (1 + noise) + 1.0))
+
+
 ADVECTION_VELOCITY = (1.0, 0.5, 0.25)
 
 
@@ -105,6 +110,12 @@ CONFIGS = {
         description="Euler on tensor-product hexahedra (the paper's element type), periodic box of 32^3 "
                     "hexahedra, N=4 (125 GLL nodes each, 4,096,000 DOFs), isentropic vortex + U(+-1e-3), "
                     "10 RK4 steps"),
+    "ns_channel": Config(
+        name="ns_channel", n=24, N=3, physics="ns", state="channel", steps=1, dt=_channel_dt(24, 3),
+        gas=_NS_GAS, walls=((1, 0, 2), (1, 1, 2)),
+        description="Navier-Stokes with BR1, mu=1e-3, Pr=0.71, 24^3 hexes x 6 = 82,944 tets, N=3, "
+                    "no-slip adiabatic walls at y = 0 and y = 1, periodic in x and z; parabolic "
+                    "Mach 0.3 channel profile with 1% noise; 1 RK4 step"),
     "hex_advection": Config(
         name="hex_advection", n=128, N=1, physics="advection_hex", state="wave", steps=10,
         dt=_advection_dt(128, 1),
@@ -132,10 +143,18 @@ def build_case(cfg: Config, n=None, N=None):
     verts, period = box_mesh(n, 1.0)
     rst = equispaced_tet_nodes(N)
     xyz = physical_nodes(verts, rst)
-    out = dict(vertices=verts, period=period, ref_nodes=rst, xyz=xyz, N=N, n=n)
+    out = dict(vertices=verts, period=period, ref_nodes=rst, xyz=xyz, N=N, n=n, face_bc=None)
+    if cfg.walls:
+        period = np.array(period, dtype=np.float64)
+        for axis, _, _ in cfg.walls:
+            period[axis] = 0.0
+        out["period"] = period
+        out["face_bc"] = box_face_bc(verts, 1.0, sides={(a, e): c for a, e, c in cfg.walls})
     if cfg.state == "vortex":
         q = isentropic_vortex(xyz, 0.0, gamma=cfg.gas.gamma, period=period)
         out["q"] = uniform_perturbation(q, 1.0e-3, seed=cfg.seed)
+    elif cfg.state == "channel":
+        out["q"] = channel_flow(xyz, gamma=cfg.gas.gamma, mach=0.3, noise=0.01, seed=cfg.seed)
     elif cfg.state == "tgv":
         out["q"] = taylor_green(xyz, gamma=cfg.gas.gamma, mach=0.1, noise=0.01, seed=cfg.seed)
     elif cfg.state == "mixture":

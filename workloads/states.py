@@ -100,6 +100,19 @@ def sin_shear(xyz, *, gamma=1.4, amp=0.1, L=1.0, rho=1.0, p=1.0):
     return _conserved_perfect_gas(rho + z, u, z, z, p + z, gamma)
 
 
+def channel_flow(xyz, *, gamma=1.4, mach=0.3, noise=0.01, seed=0, height=1.0):
+    """Parabolic channel profile between walls at y = 0 and y = height: rho = 1, p = 1/gamma
+    (c = 1), u = 4 M y (h - y) / h^2, times (1 + noise U(-1, 1)) per node; v = w = noise M U(-1, 1)
+    / 10 (PCG64, ``seed``).  Conserved variables [5][...]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    y = xyz[..., 1]
+    shape = y.shape
+    u = 4.0 * mach * y * (height - y) / height ** 2 * (1.0 + noise * rng.uniform(-1, 1, shape))
+    v = 0.1 * noise * mach * rng.uniform(-1, 1, shape)
+    w = 0.1 * noise * mach * rng.uniform(-1, 1, shape)
+    return _conserved_perfect_gas(np.ones(shape), u, v, w, np.full(shape, 1.0 / gamma), gamma)
+
+
 def advected_wave(xyz, t=0.0, *, velocity=(1.0, 0.5, 0.25), L=1.0):
     """Smooth periodic scalar on the box [0, L]^3 translated by velocity t: the exact solution of
     du/dt + a . grad u = 0 for u(x, 0) = sin(2 pi x/L) cos(2 pi y/L) + 0.3 sin(2 pi z/L)."""
