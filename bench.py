@@ -450,6 +450,10 @@ def gpu_arm(args, cfg, world, rank, local):
     if rank == 0 and not args.no_hex:
         hexf = hex_form(args, local)
         hexadv = hex_advection_form(args, local)
+    bnd = None
+    if rank == 0 and not args.no_boundary:
+        periodic = value if (head == "fp64" and cfg.name == "ns_viscous") else None
+        bnd = boundary_form(args, local, periodic)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -460,7 +464,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
-            "hex_advection_form": hexadv, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "hex_advection_form": hexadv, "boundary_form": bnd, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -641,25 +645,89 @@ def hex_form(args, local):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # the oracle's stage on a 16^3 box (one core), for context
-    import numpy as np
-    import oracle.hex as hx
-    from oracle.thermo import PerfectGas
-    small = build_hex_case(cfg, n=16)
-    ref = hx.hex_reference(small["nodes1d"])
-    t0 = time.perf_counter()
-    hx.hex_rhs_strong(ref, small["box"], small["q"], PerfectGas(1.4, 1.0))
-    cpu_s = time.perf_counter() - t0
-    cpu_dofs = 16 ** 3 * M ** 3
+    cpu = None
+    if not args.no_cpu_baseline:  # the oracle's stage on a 16^3 box (one core), for context
+        import oracle.hex as hx
+        from oracle.thermo import PerfectGas
+        small = build_hex_case(cfg, n=16)
+        ref = hx.hex_reference(small["nodes1d"])
+        t0 = time.perf_counter()
+        hx.hex_rhs_strong(ref, small["box"], small["q"], PerfectGas(1.4, 1.0))
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": 16 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+               "sample": f"one right-hand side of the oracle on 16^3 hexahedra, N = {cfg.N} "
+                         f"(numpy, single thread), {cpu_s:.2f} s"}
     return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
             "steps": steps, "ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
             "roofline": {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": flops / stage_s / 1e12 / FP64_PEAK_TFLOPS,
                          "flops_per_stage": flops, "algorithmic_bytes_per_stage": nbytes,
                          "hbm_achieved_gbs": nbytes / stage_s / 1e9, "hbm_frac": nbytes / stage_s / 1e9 / hbm},
-            "cpu_oracle_stage": {"value": cpu_dofs / cpu_s, "unit": "DOF-updates/s", "cores": 1,
-                                 "sample": f"one right-hand side of the oracle on 16^3 hexahedra, N = {cfg.N} "
-                                           f"(numpy, single thread), {cpu_s:.2f} s"},
+            "cpu_oracle_stage": cpu,
+            "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
+def boundary_form(args, local, periodic_fp64=None):
+    """The wall-bounded workload (Navier-Stokes channel, no-slip adiabatic walls at y = 0, 1,
+    24^3 x 6 tets, N = 3): FP64 RK4 steps with CUDA events, the kernel split, against the
+    periodic workload of the same size and order (the main line's FP64 value)."""
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads.configs import build_case, get_config
+
+    cfg = get_config("ns_channel")
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"], face_bc=case["face_bc"])
+    g = cfg.gas
+    gas = dg.Gas(model="perfect", gamma=g.gamma, R=g.R, mu=g.mu, Pr=g.Pr)
+    q0 = torch.tensor(case["q"], device=dev)
+    q = q0.clone()
+    work = (torch.empty_like(q), torch.zeros_like(q))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+    q.copy_(q0)
+    steps = max(1, args.steps)
+    total = 0.0
+    mesh.kernel_times(reset=True)
+    mesh.set_timing(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    mesh.set_timing(False)
+    kt = {name: {"avg_ms": ms / n, "launches": n} for name, (ms, n) in mesh.kernel_times(reset=True).items() if n}
+    if mesh.status() != 0:
+        raise SystemExit("status flags set in the wall-bounded run")
+    ms = total / steps
+    value = cfg.dofs * 5 / (ms * 1e-3)
+    nbnd = int((case["face_bc"] != 0).sum())
+    cpu = None
+    if not args.no_cpu_baseline:  # the oracle's right-hand side on the channel at 6^3 x 6 tets (one core)
+        import oracle.boundary as bd
+        from oracle.geometry import connect, geometric_factors
+        from oracle.refelem import build_reference
+        from oracle.thermo import PerfectGas
+        small = build_case(cfg, n=6)
+        ref = build_reference(cfg.N, small["ref_nodes"])
+        geo = geometric_factors(small["vertices"])
+        conn = connect(small["vertices"], small["period"], ref, face_bc=small["face_bc"])
+        t0 = time.perf_counter()
+        bd.rhs_ns_bc(ref, geo, conn, small["q"], PerfectGas(g.gamma, g.R), g.mu, g.Pr)
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": small["q"].shape[1] * small["q"].shape[2] / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+               "sample": f"one right-hand side of the oracle on the channel at 6^3 x 6 tets, N = {cfg.N} "
+                         f"(numpy, single thread), {cpu_s:.2f} s"}
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": cfg.Np, "dtype": "f64",
+            "boundary_faces": nbnd, "steps": steps, "ms_per_step": ms, "value": value, "unit": "DOF-updates/s",
+            "vs_periodic_same_size": None if not periodic_fp64 else value / periodic_fp64,
+            "kernels": kt,
+            "cpu_oracle_stage": cpu,
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
@@ -712,22 +780,24 @@ def hex_advection_form(args, local):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    import oracle.hex as hx
-    small = build_hex_advection_case(cfg, n=32)
-    ref = hx.hex_reference(small["nodes1d"])
-    t0 = time.perf_counter()
-    hx.hex_advection_rhs_strong(ref, small["box"], small["u"], vel)
-    cpu_s = time.perf_counter() - t0
-    cpu_dofs = 32 ** 3 * M ** 3
+    cpu = None
+    if not args.no_cpu_baseline:  # the oracle's stage on a 32^3 box (one core), for context
+        import oracle.hex as hx
+        small = build_hex_advection_case(cfg, n=32)
+        ref = hx.hex_reference(small["nodes1d"])
+        t0 = time.perf_counter()
+        hx.hex_advection_rhs_strong(ref, small["box"], small["u"], vel)
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": 32 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+               "sample": f"one right-hand side of the oracle on 32^3 hexahedra, N = {cfg.N} "
+                         f"(numpy, single thread), {cpu_s:.2f} s"}
     return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
             "steps": steps, "ms_per_step": ms, "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s",
             "roofline": {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": flops / stage_s / 1e12 / FP64_PEAK_TFLOPS,
                          "flops_per_stage": flops, "algorithmic_bytes_per_stage": nbytes,
                          "hbm_achieved_gbs": nbytes / stage_s / 1e9, "hbm_frac": nbytes / stage_s / 1e9 / hbm},
-            "cpu_oracle_stage": {"value": cpu_dofs / cpu_s, "unit": "DOF-updates/s", "cores": 1,
-                                 "sample": f"one right-hand side of the oracle on 32^3 hexahedra, N = {cfg.N} "
-                                           f"(numpy, single thread), {cpu_s:.2f} s"},
+            "cpu_oracle_stage": cpu,
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
@@ -794,6 +864,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
+    ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel section")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()
