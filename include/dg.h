@@ -127,6 +127,30 @@ int dg_mesh_free(dg_mesh mesh);
  * DG_ERR_INVALID_ARG (NULL, nvar outside 5..5+DG_MAX_SPECIES, rho <= 0 or non-finite). */
 int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar);
 
+/* ---- shock capturing: artificial viscosity ------------------------------------------------
+ * Sec. 5.3 stabilises its shock cases with artificial viscosity (among others) without writing
+ * it out; the method here is the sub-cell shock capturing of Persson and Peraire (2006).  Per
+ * element, the smoothness indicator of the density, S = (energy of its orthonormal modes of total
+ * degree N) / (its total energy), s = log10 S, sets the viscosity eps = 0 (s < s0 - kappa),
+ * eps0 (s > s0 + kappa), eps0/2 (1 + sin(pi (s - s0) / (2 kappa))) in between; the right-hand
+ * side gains div(eps grad q) on every conserved variable with BR1 central fluxes in both passes
+ * (at boundary faces the gradient pass takes the ghost state and the exterior flux is the
+ * interior one).  FP64 form with a perfect gas (Euler or Navier-Stokes); the mixed-precision and
+ * batched forms and the mixture reject a mesh with it on (DG_ERR_UNSUPPORTED). */
+typedef struct {
+  double eps0;   /* maximum viscosity, >= 0; 0 turns the term off                            */
+  double s0;     /* indicator threshold, log10 scale (e.g. -4 log10 N)                       */
+  double kappa;  /* half width of the ramp, > 0                                              */
+} dg_av_params;
+/* Turns artificial viscosity on (params->eps0 > 0) or off (NULL or eps0 = 0) for later dg_rhs /
+ * dg_rk_stage calls on the mesh; the first call that turns it on allocates 15 doubles per node
+ * and one per element of device scratch (cudaMalloc; the mesh owns it).  Errors:
+ * DG_ERR_INVALID_ARG (host-only mesh, eps0 < 0, kappa <= 0, non-finite), DG_ERR_CUDA, DG_ERR_OOM. */
+int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* params);
+/* eps_dev [K] (device, caller-owned) <- the element viscosities of the state q_dev (device
+ * [V][K][Np]; its density is read) under the mesh's parameters.  Asynchronous on stream. */
+int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* stream);
+
 /* Sizes of an uploaded mesh. Any pointer may be NULL. */
 int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp);
 
@@ -150,7 +174,8 @@ int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset);
 #define DG_KERNEL_RHS 1         /* fused right-hand side (+ RK stage)          */
 #define DG_KERNEL_TEMPERATURE 2 /* Newton temperature solve inside dg_rhs/stage */
 #define DG_KERNEL_PRIMS 3       /* per-node pressure / temperature pass (mixed form) */
-#define DG_NUM_KERNELS 4
+#define DG_KERNEL_AV 4          /* artificial viscosity: indicator + flux passes  */
+#define DG_NUM_KERNELS 5
 
 /* With enable != 0, every later dg_rhs / dg_rk_stage on this mesh brackets each
  * of its kernel launches with CUDA events recorded on the launch stream (the

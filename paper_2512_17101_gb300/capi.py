@@ -40,8 +40,8 @@ DG_KERNEL_VISCOUS = 0
 DG_KERNEL_RHS = 1
 DG_KERNEL_TEMPERATURE = 2
 DG_KERNEL_PRIMS = 3
-DG_NUM_KERNELS = 4
-KERNEL_NAMES = ('viscous', 'rhs', 'temperature', 'prims')
+DG_NUM_KERNELS = 5
+KERNEL_NAMES = ('viscous', 'rhs', 'temperature', 'prims', 'av')
 
 c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, \
     ctypes.c_void_p
@@ -50,6 +50,10 @@ c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64,
 class dg_mesh_desc(ctypes.Structure):
     _fields_ = [("K", c_int32), ("N", c_int32), ("ref_nodes", c_void_p), ("vertices", c_void_p),
                 ("period", c_double * 3), ("flags", c_int32), ("face_bc", c_void_p)]
+
+
+class dg_av_params(ctypes.Structure):
+    _fields_ = [("eps0", c_double), ("s0", c_double), ("kappa", c_double)]
 
 
 class dg_gas_desc(ctypes.Structure):
@@ -94,6 +98,8 @@ SIGNATURES = {
     "dg_mesh_operators": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_connectivity": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "dg_mesh_set_inflow": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "dg_mesh_set_av": (c_int32, [c_void_p, c_void_p]),
+    "dg_av_viscosity": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
     "dg_mesh_set_timing": (c_int32, [c_void_p, c_int32]),
     "dg_mesh_kernel_times": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),

@@ -45,6 +45,9 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.scratch);
   cudaFree(d.geo32);
   cudaFree(d.status);
+  cudaFree(d.modal);
+  cudaFree(d.av_eps);
+  cudaFree(d.av_sig);
   d = dg::MeshDev();
 }
 
@@ -136,6 +139,12 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const dg::MeshDev& m = mesh->d;
   const dg::GasParams& g = gas->p;
   const int V = 5 + g.ns;
+  const bool av = m.av.eps0 > 0;
+  if (av) {
+    if (opts && opts->precision == DG_PREC_MIXED)
+      return fail(DG_ERR_UNSUPPORTED, "artificial viscosity runs in the FP64 form only");
+    if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
+  }
   if (m.boundary_faces > 0) {
     if (opts && opts->precision == DG_PREC_MIXED)
       return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces run in the FP64 form only");
@@ -195,6 +204,16 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   if (g.mu > 0) {
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
+  }
+  if (av) {
+    e = timed(mesh, DG_KERNEL_AV, s, [&] {
+      cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s);
+      return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_av(m, g, q, out, k, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
+    return DG_OK;
   }
   e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs(m, g, q, out, k, T, rk, a, b, dt, s); });
   if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
@@ -270,6 +289,8 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);
+  if (e == cudaSuccess) e = upload(&d.modal, m->ops.modal.data(), m->ops.modal.size());
+  d.ntop = m->ops.ntop;
   if (e != cudaSuccess) {
     free_mesh_device(d);
     delete m;
@@ -338,6 +359,38 @@ int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar) {
   for (int v = 0; v < 5 + DG_MAX_SPECIES; ++v) mesh->d.bc.q_in[v] = v < nvar ? q_in[v] : 0.0;
   mesh->d.inflow_nvar = nvar;
   return DG_OK;
+}
+
+int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* p) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  dg::MeshDev& d = mesh->d;
+  if (!p || p->eps0 == 0.0) {
+    d.av = dg::AvParams{0.0, 0.0, 1.0};
+    return DG_OK;
+  }
+  if (!(p->eps0 > 0) || !std::isfinite(p->eps0) || !std::isfinite(p->s0) || !(p->kappa > 0) ||
+      !std::isfinite(p->kappa))
+    return fail(DG_ERR_INVALID_ARG, "need eps0 >= 0, kappa > 0, all finite");
+  if (!d.av_eps) {
+    cudaError_t e = cudaMalloc((void**)&d.av_eps, sizeof(double) * (size_t)d.K);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.av_sig, sizeof(double) * 15 * (size_t)d.K * d.Np);
+    if (e != cudaSuccess) {
+      cudaFree(d.av_eps);
+      cudaFree(d.av_sig);
+      d.av_eps = d.av_sig = nullptr;
+      return cuda_fail(e, "artificial-viscosity scratch");
+    }
+  }
+  d.av = dg::AvParams{p->eps0, p->s0, p->kappa};
+  return DG_OK;
+}
+
+int dg_av_viscosity(dg_mesh mesh, const double* q, double* eps, void* stream) {
+  if (!mesh || !q || !eps) return fail(DG_ERR_INVALID_ARG, "NULL mesh, state or output");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  const cudaError_t e = dg::launch_av_sensor(mesh->d, q, eps, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "smoothness-indicator kernel");
 }
 
 int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP, double* geo) {

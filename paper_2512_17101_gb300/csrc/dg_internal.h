@@ -21,6 +21,9 @@ struct RefOps {
   std::vector<double> Dr, Ds, Dt;  // [Np][Np] row-major
   std::vector<double> LIFT;        // [Np][4 Nfp]
   std::vector<int32_t> Fmask;      // [4][Nfp]
+  std::vector<double> modal;       // [Np][Np]: orthonormal (PKDO) coefficients from nodal values,
+                                   // the ntop modes of total degree N in the last rows
+  int ntop = 0;
 };
 
 // Reference operators of order N on the given nodes (refops.cpp).
@@ -56,6 +59,11 @@ struct MixedOps {
   unsigned char* tc_vis = nullptr;  // tcgen05 BR1 table: rows (a, i), [D_a | 1/2 sum_f c_fa LIFT_f]
 };
 
+// Artificial-viscosity parameters (eps0 > 0: on).
+struct AvParams {
+  double eps0, s0, kappa;
+};
+
 // Boundary data passed to the FP64 kernels by value: the conserved state of DG_BC_INFLOW faces.
 struct BcParams {
   double q_in[5 + DG_MAX_SPECIES];
@@ -67,6 +75,13 @@ struct MeshDev {
   int inflow_faces = 0;       // of which DG_BC_INFLOW
   int inflow_nvar = 0;        // 0 until dg_mesh_set_inflow
   BcParams bc{};
+  // artificial viscosity (dg_mesh_set_av): parameters, modal-analysis matrix, element viscosity
+  // [K] and the flux eps grad q_v along x_d, [(5 d + v)][K][Np]
+  AvParams av{};
+  int ntop = 0;
+  double* modal = nullptr;
+  double* av_eps = nullptr;
+  double* av_sig = nullptr;
   MixedOps mx;
   double* ops = nullptr;       // Dr | Ds | Dt | LIFT, row-major
   int32_t* fmask = nullptr;    // [4][Nfp]
@@ -88,6 +103,12 @@ extern const double kRK4B[5];
 // the node temperatures of a mixture.
 cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                        const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
+// Artificial viscosity (k_av.cu): element viscosities of q into eps [K]; the flux eps grad q into
+// m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
+cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
+cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t launch_rhs_av(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                          double a, double b, double dt, cudaStream_t s);
 // Mixed-precision path: primitives pass (k_mixed.cu); operator tables, tensor-core right-hand
 // side / RK stage and its BR1 pass (k_tc.cu).
 void free_mixed_ops(MeshDev& m);

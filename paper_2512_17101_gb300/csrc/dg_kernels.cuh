@@ -32,7 +32,10 @@ struct Ord {
   static constexpr int OPS = 3 * Np * Np + Np * NF;          // doubles in Dr|Ds|Dt|LIFT
 };
 
-enum Phys { EULER = 0, NAVIER_STOKES = 1, MIXTURE = 2 };
+// EULER_AV / NS_AV: the perfect-gas right-hand sides with the artificial-viscosity flux added.
+enum Phys { EULER = 0, NAVIER_STOKES = 1, MIXTURE = 2, EULER_AV = 3, NS_AV = 4 };
+__host__ __device__ constexpr bool has_visc(int PHYS) { return PHYS == NAVIER_STOKES || PHYS == NS_AV; }
+__host__ __device__ constexpr bool has_av(int PHYS) { return PHYS == EULER_AV || PHYS == NS_AV; }
 
 // index of tau_ij in the stored symmetric viscous stress (xx yy zz xy xz yz)
 __device__ __forceinline__ int tau_index(int i, int j) {
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* __restrict__ q, double* __restrict__ out, double* __restrict__ kreg,
     const double* __restrict__ Tg, const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g,
     const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
-    unsigned* __restrict__ status, const GasParams gp, const BcParams bc, const int K, const int nvar,
-    const double a, const double b, const double dt) {
+    const double* __restrict__ av_g, unsigned* __restrict__ status, const GasParams gp, const BcParams bc,
+    const int K, const int nvar, const double a, const double b, const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   extern __shared__ double smem[];
@@ -133,7 +136,9 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   double* sF = sQ + V * NODES;
   double* sG = sF + 3 * V * NODES;
   double* sFv = sG + V * EPB * NF;
-  double* sT = sFv + (PHYS == NAVIER_STOKES ? 9 * NODES : 0);
+  constexpr bool VISC = has_visc(PHYS), AV = has_av(PHYS);
+  double* sAv = sFv + (VISC ? 9 * NODES : 0);
+  double* sT = sAv + (AV ? 15 * NODES : 0);
   int* sFm = reinterpret_cast<int*>(sT + (PHYS == MIXTURE ? NODES : 0));
 
   const int tid = threadIdx.x;
@@ -150,7 +155,10 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   for (int v = 0; v < V; ++v)
     if (v < nvar)
       for (int i = tid; i < nn; i += blockDim.x) sQ[v * NODES + i] = q[v * KNp + base + i];
-  if (PHYS == NAVIER_STOKES)
+  if (AV)  // artificial-viscosity flux eps grad q_v along x_d at [(5 d + v)][K][Np]
+    for (int c = 0; c < 15; ++c)
+      for (int i = tid; i < nn; i += blockDim.x) sAv[c * NODES + i] = av_g[c * KNp + base + i];
+  if (VISC)
     for (int c = 0; c < 9; ++c)
       for (int i = tid; i < nn; i += blockDim.x) sFv[c * NODES + i] = fv_g[c * KNp + base + i];
   if (PHYS == MIXTURE)
@@ -180,10 +188,14 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
       F[d][4] = vel[d] * (qv[4] + p);
 #pragma unroll
       for (int v = 5; v < V; ++v) F[d][v] = qv[v] * vel[d];
-      if (PHYS == NAVIER_STOKES) {
+      if (VISC) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) F[d][1 + i] -= sFv[tau_index(i, d) * NODES + tid];
         F[d][4] -= sFv[(6 + d) * NODES + tid];
+      }
+      if (AV) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[d][v] -= sAv[(5 * d + v) * NODES + tid];
       }
     }
 #pragma unroll
@@ -225,7 +237,21 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     double g[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.5 * ((fm[v] - fp[v]) - lam * (qm[v] - qp[v]));
-    if (PHYS == NAVIER_STOKES) {
+    if (AV) {
+      // central artificial-viscosity flux: n.(G- - G*) gains -(n.s- - n.s+)/2; the exterior flux
+      // at a boundary node is the interior one
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double sm = 0.0, sp = 0.0;
+        sm = fma(nx, sAv[(0 + v) * NODES + own], fma(ny, sAv[(5 + v) * NODES + own], nz * sAv[(10 + v) * NODES + own]));
+        if (P >= 0)
+          sp = fma(nx, av_g[(0 + v) * KNp + P], fma(ny, av_g[(5 + v) * KNp + P], nz * av_g[(10 + v) * KNp + P]));
+        else
+          sp = sm;
+        g[v] -= 0.5 * (sm - sp);
+      }
+    }
+    if (VISC) {
       // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2; at a boundary node the
       // exterior normal flux (traction t+, energy flux e+) follows the face's condition
       const double nn3[3] = {nx, ny, nz};
@@ -460,7 +486,8 @@ template <int N, int V, int PHYS>
 constexpr size_t rhs_smem() {
   using O = Ord<N>;
   return sizeof(double) * (O::OPS + O::EPB * GS + V * O::NODES + 3 * V * O::NODES + V * O::EPB * O::NF +
-                           (PHYS == NAVIER_STOKES ? 9 * O::NODES : 0) + (PHYS == MIXTURE ? O::NODES : 0)) +
+                           (has_visc(PHYS) ? 9 * O::NODES : 0) + (has_av(PHYS) ? 15 * O::NODES : 0) +
+                           (PHYS == MIXTURE ? O::NODES : 0)) +
          sizeof(int) * O::NF;
 }
 
@@ -484,7 +511,7 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
   rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP, m.scratch,
-                                                           m.status, g, m.bc, m.K, nvar, a, b, dt);
+                                                           m.av_sig, m.status, g, m.bc, m.K, nvar, a, b, dt);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,222 @@
+// Shock capturing by artificial viscosity on the FP64 tetrahedral path (the paper names
+// artificial viscosity among the stabilisations of its shock cases, Sec. 5.3; the method here is
+// the sub-cell shock capturing of Persson and Peraire, 2006):
+//   * smoothness indicator of the density per element, S = (energy of its orthonormal modes of
+//     total degree N) / (its total energy), s = log10 S;
+//   * eps = 0 (s < s0 - kappa), eps0 (s > s0 + kappa), eps0/2 (1 + sin(pi (s - s0) / (2 kappa)));
+//   * flux sigma_v = eps grad q_v for every conserved variable, BR1 gradient with the central
+//     flux (exterior values from the ghost states at boundary faces), added to the right-hand
+//     side through the central flux (rhs_kernel<EULER_AV / NS_AV>).
+#include <cmath>
+
+#include "dg_kernels.cuh"
+
+namespace dg {
+namespace kern {
+
+// One thread per (element, mode): the mode's coefficient from the element's nodal densities;
+// then one thread per element sums the energies.
+template <int N>
+__global__ void __launch_bounds__(Ord<N>::NT) av_sensor_kernel(const double* __restrict__ q,
+                                                               const double* __restrict__ modal_g, const int ntop,
+                                                               const AvParams av, const int K,
+                                                               double* __restrict__ eps) {
+  using O = Ord<N>;
+  constexpr int Np = O::Np, EPB = O::EPB, NODES = O::NODES;
+  __shared__ double sH[Np * Np];
+  __shared__ double sU[NODES];
+  __shared__ double sC[NODES];
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t base = (size_t)e0 * Np;
+  for (int i = tid; i < Np * Np; i += blockDim.x) sH[i] = modal_g[i];
+  if (tid < nn) sU[tid] = q[base + tid];  // density, variable 0
+  __syncthreads();
+  if (tid < nn) {
+    const int e = tid / Np, m = tid - e * Np;
+    double c = 0.0;
+#pragma unroll 5
+    for (int j = 0; j < Np; ++j) c = fma(sH[m * Np + j], sU[e * Np + j], c);
+    sC[tid] = c * c;
+  }
+  __syncthreads();
+  if (tid < nel) {
+    double den = 0.0, num = 0.0;
+    for (int m = 0; m < Np; ++m) {
+      const double c2 = sC[tid * Np + m];
+      den += c2;
+      if (m >= Np - ntop) num += c2;
+    }
+    double e = 0.0;
+    if (num > 0.0 && den > 0.0) {
+      const double sv = log10(num / den);
+      if (sv > av.s0 + av.kappa)
+        e = av.eps0;
+      else if (sv >= av.s0 - av.kappa)
+        e = 0.5 * av.eps0 * (1.0 + sin(3.141592653589793 * (sv - av.s0) / (2.0 * av.kappa)));
+    }
+    eps[e0 + tid] = e;
+  }
+}
+
+// BR1 gradient of the five conserved variables, times the element viscosity:
+//   grad_d q = sum_a (dr_a/dx_d) D_a q + sum_f n_d,f LIFT_f (Fscale (q+ - q-)/2),
+//   sig[(5 d + v)][K][Np] = eps_e grad_d q_v.
+template <int N>
+__global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
+    const double* __restrict__ q, const double* __restrict__ eps, double* __restrict__ sig,
+    const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g,
+    const int32_t* __restrict__ vmapP, const BcParams bc, const int K) {
+  using O = Ord<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
+  constexpr int W = 5;
+  extern __shared__ double smem[];
+  double* sOps = smem;
+  double* sGeo = sOps + O::OPS;
+  double* sW = sGeo + EPB * GS;
+  double* sJ = sW + W * NODES;
+  int* sFm = reinterpret_cast<int*>(sJ + W * EPB * NF);
+
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+
+  for (int i = tid; i < O::OPS; i += blockDim.x) sOps[i] = ops_g[i];
+  for (int i = tid; i < NF; i += blockDim.x) sFm[i] = fmask_g[i];
+  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)e0 * GS + i];
+#pragma unroll
+  for (int v = 0; v < W; ++v)
+    for (int i = tid; i < nn; i += blockDim.x) sW[v * NODES + i] = q[v * KNp + base + i];
+  __syncthreads();
+
+  for (int j = tid; j < nel * NF; j += blockDim.x) {
+    const int e = j / NF, m = j - e * NF, f = m / Nfp;
+    const double* G = sGeo + e * GS;
+    const double hf = 0.5 * G[12 + 4 * f];
+    const int own = e * Np + sFm[m];
+    const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    double qm[W], qp[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) qm[v] = sW[v * NODES + own];
+    if (P >= 0) {
+#pragma unroll
+      for (int v = 0; v < W; ++v) qp[v] = q[v * KNp + P];
+    } else {
+      ghost_state<W>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, W, qp);
+    }
+#pragma unroll
+    for (int v = 0; v < W; ++v) sJ[v * EPB * NF + j] = hf * (qp[v] - qm[v]);
+  }
+  __syncthreads();
+
+  if (tid < nn) {
+    const int e = tid / Np, i = tid - e * Np;
+    const double* G = sGeo + e * GS;
+    const double* Dr = sOps + i * Np;
+    const double* Ds = sOps + Np * Np + i * Np;
+    const double* Dt = sOps + 2 * Np * Np + i * Np;
+    const double* L = sOps + 3 * Np * Np + i * NF;
+    double dref[3][W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) dref[0][v] = dref[1][v] = dref[2][v] = 0.0;
+#pragma unroll 4
+    for (int jn = 0; jn < Np; ++jn) {
+      const double dr = Dr[jn], ds = Ds[jn], dtt = Dt[jn];
+#pragma unroll
+      for (int v = 0; v < W; ++v) {
+        const double w = sW[v * NODES + e * Np + jn];
+        dref[0][v] = fma(dr, w, dref[0][v]);
+        dref[1][v] = fma(ds, w, dref[1][v]);
+        dref[2][v] = fma(dtt, w, dref[2][v]);
+      }
+    }
+    double grad[3][W];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < W; ++v)
+        grad[d][v] = fma(G[d], dref[0][v], fma(G[3 + d], dref[1][v], G[6 + d] * dref[2][v]));
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      double lf[W];
+#pragma unroll
+      for (int v = 0; v < W; ++v) lf[v] = 0.0;
+#pragma unroll 5
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const double l = L[f * Nfp + jj];
+        const int col = e * NF + f * Nfp + jj;
+#pragma unroll
+        for (int v = 0; v < W; ++v) lf[v] = fma(l, sJ[v * EPB * NF + col], lf[v]);
+      }
+      const double nf[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < W; ++v) grad[d][v] = fma(nf[d], lf[v], grad[d][v]);
+    }
+    const double ee = eps[e0 + e];
+    const size_t gi = base + tid;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * grad[d][v];
+  }
+}
+
+template <int N>
+cudaError_t launch_sensor_t(const MeshDev& m, const double* q, double* eps, cudaStream_t s) {
+  using O = Ord<N>;
+  const int blocks = (m.K + O::EPB - 1) / O::EPB;
+  av_sensor_kernel<N><<<blocks, O::NT, 0, s>>>(q, m.modal, m.ntop, m.av, m.K, eps);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_flux_t(const MeshDev& m, const double* q, cudaStream_t s) {
+  using O = Ord<N>;
+  constexpr size_t smem = viscous_smem<N>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(av_flux_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int blocks = (m.K + O::EPB - 1) / O::EPB;
+  av_flux_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.av_eps, m.av_sig, m.ops, m.fmask, m.geo, m.vmapP, m.bc, m.K);
+  return cudaGetLastError();
+}
+
+}  // namespace kern
+
+cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s) {
+  switch (m.N) {
+    case 1: return kern::launch_sensor_t<1>(m, q, eps, s);
+    case 2: return kern::launch_sensor_t<2>(m, q, eps, s);
+    case 3: return kern::launch_sensor_t<3>(m, q, eps, s);
+    case 4: return kern::launch_sensor_t<4>(m, q, eps, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_av_flux(const MeshDev& m, const GasParams&, const double* q, cudaStream_t s) {
+  switch (m.N) {
+    case 1: return kern::launch_flux_t<1>(m, q, s);
+    case 2: return kern::launch_flux_t<2>(m, q, s);
+    case 3: return kern::launch_flux_t<3>(m, q, s);
+    case 4: return kern::launch_flux_t<4>(m, q, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_rhs_av(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                          double a, double b, double dt, cudaStream_t s) {
+  if (g.mu > 0) return kern::dispatch_rhs<5, kern::NS_AV>(m, g, q, out, k, nullptr, rk, a, b, dt, s);
+  return kern::dispatch_rhs<5, kern::EULER_AV>(m, g, q, out, k, nullptr, rk, a, b, dt, s);
+}
+
+}  // namespace dg

@@ -214,6 +214,8 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
     const dg_batch_case& c = in[i];
     if (!c.mesh || !c.gas || !c.q_dev) return fail(DG_ERR_INVALID_ARG, "case " + std::to_string(i) + ": NULL field");
     if (!c.mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "case " + std::to_string(i) + ": host-only mesh");
+    if (c.mesh->d.av.eps0 > 0)
+      return fail(DG_ERR_UNSUPPORTED, "case " + std::to_string(i) + ": artificial viscosity runs in the FP64 form");
     if (c.mesh->d.boundary_faces > 0)
       return fail(DG_ERR_UNSUPPORTED, "case " + std::to_string(i) + ": the batched form needs periodic meshes");
     if (c.gas->p.model != DG_GAS_PERFECT)

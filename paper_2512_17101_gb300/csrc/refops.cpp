@@ -241,6 +241,25 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err) {
   out.Dt.assign(Dt.begin(), Dt.end());
   out.LIFT.assign(LIFT.begin(), LIFT.end());
   out.Fmask = Fmask;
+  // modal analysis for the smoothness indicator: rows of Vo^-1 (nodal values -> orthonormal
+  // coefficients), the modes of total degree N last
+  std::vector<ld> Voi = Vo;
+  if (!invert(Voi, Np)) {
+    err = "orthonormal Vandermonde matrix is singular";
+    return false;
+  }
+  std::vector<int> deg;
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; a + b <= N; ++b)
+      for (int c = 0; a + b + c <= N; ++c) deg.push_back(a + b + c);
+  out.modal.clear();
+  out.ntop = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int m = 0; m < Np; ++m)
+      if ((deg[m] == N) == (pass == 1)) {
+        for (int j = 0; j < Np; ++j) out.modal.push_back((double)Voi[m * Np + j]);
+        out.ntop += pass;
+      }
   return true;
 }
 
