@@ -450,10 +450,11 @@ def gpu_arm(args, cfg, world, rank, local):
     if rank == 0 and not args.no_hex:
         hexf = hex_form(args, local)
         hexadv = hex_advection_form(args, local)
-    bnd = None
+    bnd = avf = None
     if rank == 0 and not args.no_boundary:
         periodic = value if (head == "fp64" and cfg.name == "ns_viscous") else None
         bnd = boundary_form(args, local, periodic)
+        avf = av_form(args, local)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -464,7 +465,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
-            "hex_advection_form": hexadv, "boundary_form": bnd, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "hex_advection_form": hexadv, "boundary_form": bnd, "av_form": avf, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -731,6 +732,62 @@ def boundary_form(args, local, periodic_fp64=None):
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
+def av_form(args, local):
+    """Shock capturing: Euler with artificial viscosity on two smoothed Sod fronts (24^3 x 6 tets,
+    N = 3), FP64 RK4 steps with CUDA events and the kernel split, against the same steps with
+    the artificial viscosity off."""
+    import numpy as np
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads.configs import build_case, get_config
+
+    cfg = get_config("euler_shock_av")
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    gas = dg.Gas(model="perfect", gamma=cfg.gas.gamma, R=cfg.gas.R)
+    q0 = torch.tensor(case["q"], device=dev)
+    work = (torch.empty_like(q0), torch.zeros_like(q0))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    params = dict(eps0=5e-3, s0=-4.0 * np.log10(cfg.N), kappa=1.0)
+
+    def run(on):
+        mesh.set_av(params["eps0"] if on else 0.0, params["s0"], params["kappa"])
+        q = q0.clone()
+        for _ in range(max(3, args.warmup)):
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+        q.copy_(q0)
+        mesh.kernel_times(reset=True)
+        mesh.set_timing(True)
+        total = 0.0
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        mesh.set_timing(False)
+        kt = {n: {"avg_ms": ms / c, "launches": c} for n, (ms, c) in mesh.kernel_times(reset=True).items() if c}
+        if mesh.status() != 0:
+            raise SystemExit("status flags set in the artificial-viscosity run")
+        return total / max(1, args.steps), kt
+
+    ms_on, kt_on = run(True)
+    ms_off, _ = run(False)
+    mesh.set_av(params["eps0"], params["s0"], params["kappa"])
+    eps = torch.empty(cfg.K, dtype=torch.float64, device=dev)
+    mesh.av_viscosity(q0, eps)
+    e = eps.cpu().numpy()
+    return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "dtype": "f64",
+            "steps": max(1, args.steps), "ms_per_step": ms_on, "value": cfg.dofs * 5 / (ms_on * 1e-3),
+            "unit": "DOF-updates/s", "ms_per_step_without_av": ms_off, "av_overhead": ms_on / ms_off - 1.0,
+            "kernels": kt_on, "elements_with_eps": {"zero": int((e == 0).sum()), "ramp": int(((e > 0) & (e < 5e-3)).sum()),
+                                                      "eps0": int((e == 5e-3).sum())},
+            "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
 def hex_advection_flops_per_element(M, velocity):
     """FP64 flops of the advection right-hand side + stage update per element (M = N+1): per node
     3 line derivatives of M FMAs (the factor -a_d (2/h_d) dt folded into D) and the 2 FMAs of the
@@ -864,7 +921,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
-    ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel section")
+    ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel and artificial-viscosity sections")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()

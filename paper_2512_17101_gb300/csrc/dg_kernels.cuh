@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* __restrict__ q, double* __restrict__ out, double* __restrict__ kreg,
     const double* __restrict__ Tg, const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g,
     const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
-    const double* __restrict__ av_g, unsigned* __restrict__ status, const GasParams gp, const BcParams bc,
-    const int K, const int nvar, const double a, const double b, const double dt) {
+    const double* __restrict__ av_g, const double* __restrict__ av_eps, unsigned* __restrict__ status,
+    const GasParams gp, const BcParams bc, const int K, const int nvar, const double a, const double b,
+    const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   extern __shared__ double smem[];
@@ -137,8 +138,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   double* sG = sF + 3 * V * NODES;
   double* sFv = sG + V * EPB * NF;
   constexpr bool VISC = has_visc(PHYS), AV = has_av(PHYS);
-  double* sAv = sFv + (VISC ? 9 * NODES : 0);
-  double* sT = sAv + (AV ? 15 * NODES : 0);
+  double* sT = sFv + (VISC ? 9 * NODES : 0);
   int* sFm = reinterpret_cast<int*>(sT + (PHYS == MIXTURE ? NODES : 0));
 
   const int tid = threadIdx.x;
@@ -155,9 +155,6 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   for (int v = 0; v < V; ++v)
     if (v < nvar)
       for (int i = tid; i < nn; i += blockDim.x) sQ[v * NODES + i] = q[v * KNp + base + i];
-  if (AV)  // artificial-viscosity flux eps grad q_v along x_d at [(5 d + v)][K][Np]
-    for (int c = 0; c < 15; ++c)
-      for (int i = tid; i < nn; i += blockDim.x) sAv[c * NODES + i] = av_g[c * KNp + base + i];
   if (VISC)
     for (int c = 0; c < 9; ++c)
       for (int i = tid; i < nn; i += blockDim.x) sFv[c * NODES + i] = fv_g[c * KNp + base + i];
@@ -193,9 +190,11 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
         for (int i = 0; i < 3; ++i) F[d][1 + i] -= sFv[tau_index(i, d) * NODES + tid];
         F[d][4] -= sFv[(6 + d) * NODES + tid];
       }
-      if (AV) {
+      // artificial-viscosity flux eps grad q_v along x_d at av_g[(5 d + v)][K][Np]: zero, and not
+      // stored, in elements with eps = 0 (most of them), so it is read from HBM only where eps > 0
+      if (AV && av_eps[e0 + e] > 0.0) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) F[d][v] -= sAv[(5 * d + v) * NODES + tid];
+        for (int v = 0; v < 5; ++v) F[d][v] -= av_g[(5 * d + v) * KNp + base + tid];
       }
     }
 #pragma unroll
@@ -240,15 +239,20 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     if (AV) {
       // central artificial-viscosity flux: n.(G- - G*) gains -(n.s- - n.s+)/2; the exterior flux
       // at a boundary node is the interior one
+      const size_t gM = base + own;
+      const bool onM = av_eps[e0 + e] > 0.0, onP = P >= 0 && av_eps[P / Np] > 0.0;
+      if (onM || onP) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        double sm = 0.0, sp = 0.0;
-        sm = fma(nx, sAv[(0 + v) * NODES + own], fma(ny, sAv[(5 + v) * NODES + own], nz * sAv[(10 + v) * NODES + own]));
-        if (P >= 0)
-          sp = fma(nx, av_g[(0 + v) * KNp + P], fma(ny, av_g[(5 + v) * KNp + P], nz * av_g[(10 + v) * KNp + P]));
-        else
-          sp = sm;
-        g[v] -= 0.5 * (sm - sp);
+        for (int v = 0; v < 5; ++v) {
+          double sm = 0.0, sp = 0.0;
+          if (onM)
+            sm = fma(nx, av_g[(0 + v) * KNp + gM], fma(ny, av_g[(5 + v) * KNp + gM], nz * av_g[(10 + v) * KNp + gM]));
+          if (P < 0)
+            sp = sm;
+          else if (onP)
+            sp = fma(nx, av_g[(0 + v) * KNp + P], fma(ny, av_g[(5 + v) * KNp + P], nz * av_g[(10 + v) * KNp + P]));
+          g[v] -= 0.5 * (sm - sp);
+        }
       }
     }
     if (VISC) {
@@ -486,8 +490,7 @@ template <int N, int V, int PHYS>
 constexpr size_t rhs_smem() {
   using O = Ord<N>;
   return sizeof(double) * (O::OPS + O::EPB * GS + V * O::NODES + 3 * V * O::NODES + V * O::EPB * O::NF +
-                           (has_visc(PHYS) ? 9 * O::NODES : 0) + (has_av(PHYS) ? 15 * O::NODES : 0) +
-                           (PHYS == MIXTURE ? O::NODES : 0)) +
+                           (has_visc(PHYS) ? 9 * O::NODES : 0) + (PHYS == MIXTURE ? O::NODES : 0)) +
          sizeof(int) * O::NF;
 }
 
@@ -511,7 +514,8 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
   rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP, m.scratch,
-                                                           m.av_sig, m.status, g, m.bc, m.K, nvar, a, b, dt);
+                                                           m.av_sig, m.av_eps, m.status, g, m.bc, m.K, nvar, a, b,
+                                                           dt);
   return cudaGetLastError();
 }
 

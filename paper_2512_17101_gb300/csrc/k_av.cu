@@ -85,6 +85,9 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
   const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
+  // sigma = 0 wherever eps = 0, and the right-hand side reads sigma only where eps > 0: a block
+  // whose elements all have eps = 0 has nothing to do
+  if (!__syncthreads_or(tid < nel && eps[e0 + tid] > 0.0)) return;
 
   for (int i = tid; i < O::OPS; i += blockDim.x) sOps[i] = ops_g[i];
   for (int i = tid; i < NF; i += blockDim.x) sFm[i] = fmask_g[i];
@@ -161,10 +164,11 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
     }
     const double ee = eps[e0 + e];
     const size_t gi = base + tid;
+    if (ee > 0.0)
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * grad[d][v];
+        for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * grad[d][v];
   }
 }
 

@@ -52,7 +52,7 @@ cudaError_t stage_t(const dg::MeshDev& m, const dg::GasParams& g, const double* 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dg::kern::rhs_kernel<N, 5, dg::kern::NAVIER_STOKES, true><<<blocks, O::NT, rs, s>>>(
-      q, out, k, nullptr, m.ops, m.fmask, m.geo, m.vmapP, m.scratch, nullptr, m.status, g, m.bc, m.K, 5, a, b, dt);
+      q, out, k, nullptr, m.ops, m.fmask, m.geo, m.vmapP, m.scratch, nullptr, nullptr, m.status, g, m.bc, m.K, 5, a, b, dt);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ from .states import (
     sin_shear,
     advected_wave,
     channel_flow,
+    sod_fronts,
 )
 from .gas import IdealGas, Nasa7Mixture, seeded_nasa7_mixture
 from .configs import CONFIGS, get_config

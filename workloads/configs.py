@@ -20,7 +20,7 @@ import numpy as np
 from .gas import IdealGas, seeded_nasa7_mixture, mixture_primitive_state
 from .hexmesh import gll_nodes, hex_box, hex_nodes
 from .mesh import box_face_bc, box_mesh, equispaced_tet_nodes, physical_nodes, n_nodes
-from .states import advected_wave, channel_flow, isentropic_vortex, taylor_green, uniform_perturbation
+from .states import advected_wave, channel_flow, sod_fronts, isentropic_vortex, taylor_green, uniform_perturbation
 
 
 @dataclass(frozen=True)
@@ -80,6 +80,11 @@ def _channel_dt(n, N, mach=0.3, noise=0.01):
     return 0.3 * (1.0 / n) / ((N + 1) ** 2 * (mach * (1 + noise) + 1.0))
 
 
+def _sod_dt(n, N):
+    """|u| + c <= 2.2 for the Sod states (c <= sqrt(1.4), |u| below the Sod contact speed 0.93)."""
+    return 0.3 * (1.0 / n) / ((N + 1) ** 2 * 2.2)
+
+
 ADVECTION_VELOCITY = (1.0, 0.5, 0.25)
 
 
@@ -116,6 +121,13 @@ CONFIGS = {
         description="Navier-Stokes with BR1, mu=1e-3, Pr=0.71, 24^3 hexes x 6 = 82,944 tets, N=3, "
                     "no-slip adiabatic walls at y = 0 and y = 1, periodic in x and z; parabolic "
                     "Mach 0.3 channel profile with 1% noise; 1 RK4 step"),
+    "euler_shock_av": Config(
+        name="euler_shock_av", n=24, N=3, physics="euler", state="fronts", steps=1,
+        dt=_sod_dt(24, 3),
+        gas=IdealGas(gamma=1.4, R=1.0),
+        description="Euler with artificial viscosity (eps0 = 5e-3, s0 = -4 log10 N, kappa = 1), "
+                    "24^3 hexes x 6 = 82,944 tets, N=3, two smoothed Sod fronts (width 0.01) in a "
+                    "periodic box; 1 RK4 step"),
     "hex_advection": Config(
         name="hex_advection", n=128, N=1, physics="advection_hex", state="wave", steps=10,
         dt=_advection_dt(128, 1),
@@ -153,6 +165,8 @@ def build_case(cfg: Config, n=None, N=None):
     if cfg.state == "vortex":
         q = isentropic_vortex(xyz, 0.0, gamma=cfg.gas.gamma, period=period)
         out["q"] = uniform_perturbation(q, 1.0e-3, seed=cfg.seed)
+    elif cfg.state == "fronts":
+        out["q"] = sod_fronts(xyz, gamma=cfg.gas.gamma, width=0.01)
     elif cfg.state == "channel":
         out["q"] = channel_flow(xyz, gamma=cfg.gas.gamma, mach=0.3, noise=0.01, seed=cfg.seed)
     elif cfg.state == "tgv":

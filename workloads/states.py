@@ -113,6 +113,17 @@ def channel_flow(xyz, *, gamma=1.4, mach=0.3, noise=0.01, seed=0, height=1.0):
     return _conserved_perfect_gas(np.ones(shape), u, v, w, np.full(shape, 1.0 / gamma), gamma)
 
 
+def sod_fronts(xyz, *, gamma=1.4, width=0.01, L=1.0):
+    """Two smoothed Sod shock-tube states on a periodic box: (rho, p) = (1, 1) for x in
+    [L/4, 3L/4] and (0.125, 0.1) outside, joined by tanh profiles of the given width; at rest."""
+    x = xyz[..., 0]
+    S = 0.5 * (np.tanh((x - 0.25 * L) / width) - np.tanh((x - 0.75 * L) / width))
+    rho = 0.125 + 0.875 * S
+    p = 0.1 + 0.9 * S
+    zero = np.zeros_like(x)
+    return _conserved_perfect_gas(rho, zero, zero, zero, p, gamma)
+
+
 def advected_wave(xyz, t=0.0, *, velocity=(1.0, 0.5, 0.25), L=1.0):
     """Smooth periodic scalar on the box [0, L]^3 translated by velocity t: the exact solution of
     du/dt + a . grad u = 0 for u(x, 0) = sin(2 pi x/L) cos(2 pi y/L) + 0.3 sin(2 pi z/L)."""
