@@ -213,19 +213,21 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
     const int own = e * Np + sFm[m];
     const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    // a boundary node gathers its own trace, so that interior and boundary nodes run the same
+    // code; the ghost state and the exterior viscous fluxes of its condition are applied in the
+    // branch below, which interior faces never take
+    const size_t Pn = P >= 0 ? (size_t)P : base + own;
     double qm[V], qp[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) qm[v] = v < nvar ? sQ[v * NODES + own] : 0.0;
-    if (P >= 0) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) qp[v] = v < nvar ? q[v * KNp + P] : 0.0;
-    } else {
-      ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
+    for (int v = 0; v < V; ++v) {
+      qm[v] = v < nvar ? sQ[v * NODES + own] : 0.0;
+      qp[v] = v < nvar ? q[v * KNp + Pn] : 0.0;
     }
+    if (P < 0) ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
     const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
     double pm, cm, pp, cp;
     thermo<PHYS, V>(gp, qm, irm, PHYS == MIXTURE ? sT[own] : 0.0, pm, cm);
-    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? (P >= 0 ? Tg[P] : sT[own]) : 0.0, pp, cp);
+    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? Tg[Pn] : 0.0, pp, cp);
     if (P < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
     const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
     const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
@@ -237,29 +239,25 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.5 * ((fm[v] - fp[v]) - lam * (qm[v] - qp[v]));
     if (AV) {
-      // central artificial-viscosity flux: n.(G- - G*) gains -(n.s- - n.s+)/2; the exterior flux
-      // at a boundary node is the interior one
+      // central artificial-viscosity flux: n.(G- - G*) gains -(n.s- - n.s+)/2; at a boundary node
+      // the exterior flux is the interior one (Pn is the node itself)
       const size_t gM = base + own;
-      const bool onM = av_eps[e0 + e] > 0.0, onP = P >= 0 && av_eps[P / Np] > 0.0;
+      const bool onM = av_eps[e0 + e] > 0.0, onP = av_eps[Pn / Np] > 0.0;
       if (onM || onP) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           double sm = 0.0, sp = 0.0;
           if (onM)
             sm = fma(nx, av_g[(0 + v) * KNp + gM], fma(ny, av_g[(5 + v) * KNp + gM], nz * av_g[(10 + v) * KNp + gM]));
-          if (P < 0)
-            sp = sm;
-          else if (onP)
-            sp = fma(nx, av_g[(0 + v) * KNp + P], fma(ny, av_g[(5 + v) * KNp + P], nz * av_g[(10 + v) * KNp + P]));
+          if (onP)
+            sp = fma(nx, av_g[(0 + v) * KNp + Pn], fma(ny, av_g[(5 + v) * KNp + Pn], nz * av_g[(10 + v) * KNp + Pn]));
           g[v] -= 0.5 * (sm - sp);
         }
       }
     }
     if (VISC) {
-      // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2; at a boundary node the
-      // exterior normal flux (traction t+, energy flux e+) follows the face's condition
+      // central viscous flux: n.(G- - G*) gains -(n.Fv- - n.Fv+)/2
       const double nn3[3] = {nx, ny, nz};
-      double tm[3], tp[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         double dm = 0.0, dp = 0.0;
@@ -267,26 +265,35 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
         for (int d = 0; d < 3; ++d) {
           const int c = tau_index(i, d);
           dm = fma(nn3[d], sFv[c * NODES + own], dm);
-          if (P >= 0) dp = fma(nn3[d], fv_g[c * KNp + P], dp);
+          dp = fma(nn3[d], fv_g[c * KNp + Pn], dp);
         }
-        tm[i] = dm;
-        tp[i] = P >= 0 ? dp : dm;
+        g[1 + i] -= 0.5 * (dm - dp);
       }
-      if (P == -DG_BC_SLIP_WALL) {  // shear-free: t+ = 2 (n.t-) n - t-
-        const double tn2 = 2.0 * (tm[0] * nx + tm[1] * ny + tm[2] * nz);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) tp[i] = tn2 * nn3[i] - tm[i];
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) g[1 + i] -= 0.5 * (tm[i] - tp[i]);
       double em = 0.0, ep = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         em = fma(nn3[d], sFv[(6 + d) * NODES + own], em);
-        if (P >= 0) ep = fma(nn3[d], fv_g[(6 + d) * KNp + P], ep);
+        ep = fma(nn3[d], fv_g[(6 + d) * KNp + Pn], ep);
       }
-      if (P < 0) ep = (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) ? -em : em;  // adiabatic walls
       g[4] -= 0.5 * (em - ep);
+      // at a boundary node the terms above cancel (exterior = interior flux); walls are adiabatic
+      // (e+ = -e-: g gains -e-) and a slip wall is shear-free (t+ = 2 (n.t-) n - t-: g gains
+      // -(t- - (n.t-) n))
+      if (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) {
+        g[4] -= em;
+        if (P == -DG_BC_SLIP_WALL) {
+          double tm[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            tm[i] = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) tm[i] = fma(nn3[d], sFv[tau_index(i, d) * NODES + own], tm[i]);
+          }
+          const double tn = tm[0] * nx + tm[1] * ny + tm[2] * nz;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) g[1 + i] -= tm[i] - tn * nn3[i];
+        }
+      }
     }
 #pragma unroll
     for (int v = 0; v < V; ++v)
@@ -391,14 +398,14 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
     const double fs = G[12 + 4 * f];
     const int own = e * Np + sFm[m];
     const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    const size_t Pn = P >= 0 ? (size_t)P : base + own;  // a boundary node gathers its own trace
     double qp[5];
-    if (P >= 0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + P];
-    } else {  // exterior values w(q+) of the face's ghost state
+    for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + Pn];
+    if (P < 0) {  // exterior values w(q+) of the face's ghost state
       double qm[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) qm[v] = q[v * KNp + base + own];
+      for (int v = 0; v < 5; ++v) qm[v] = qp[v];
       ghost_state<5>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, 5, qp);
     }
     const double irp = 1.0 / qp[0];

@@ -103,15 +103,14 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
     const double hf = 0.5 * G[12 + 4 * f];
     const int own = e * Np + sFm[m];
     const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    const size_t Pn = P >= 0 ? (size_t)P : base + own;  // a boundary node gathers its own trace
     double qm[W], qp[W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) qm[v] = sW[v * NODES + own];
-    if (P >= 0) {
-#pragma unroll
-      for (int v = 0; v < W; ++v) qp[v] = q[v * KNp + P];
-    } else {
-      ghost_state<W>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, W, qp);
+    for (int v = 0; v < W; ++v) {
+      qm[v] = sW[v * NODES + own];
+      qp[v] = q[v * KNp + Pn];
     }
+    if (P < 0) ghost_state<W>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, W, qp);
 #pragma unroll
     for (int v = 0; v < W; ++v) sJ[v * EPB * NF + j] = hf * (qp[v] - qm[v]);
   }
