@@ -39,7 +39,9 @@ L2_FLUSH_BYTES = 256 << 20
 FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
-    ("7ae1f260473cc60c", "rhs"): 290.224896e6 + 105.554176e6,  # profiles/ns_N3_K82944_fp64.md
+    # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
+    ("46bd0c832d9bb35a", "rhs"): 289.528320e6 + 105.552384e6,
+    ("46bd0c832d9bb35a", "viscous"): 99.328000e6 + 74.704128e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
     ("2ba9f488305c1d84", "mixed_rhs"): 256.088320e6 + 119.813376e6,
     ("2ba9f488305c1d84", "mixed_viscous"): 90.063616e6 + 26.145024e6,
