@@ -190,6 +190,13 @@ int dg_mesh_set_timing(dg_mesh mesh, int enable);
 int dg_mesh_kernel_times(dg_mesh mesh, double* ms_host, int64_t* launches_host, int reset);
 
 /* ---- gas ----------------------------------------------------------------- */
+/* A NASA-7 mixture with mu > 0 (FP64 form, periodic meshes) carries viscosity, heat conduction
+ * and species diffusion (the paper's viscous multi-species flows, Sec. 4-5, name no transport
+ * model; reading): constant mu, Stokes hypothesis; kappa = mu cp_mix(T, Y) / Pr; Fickian
+ * diffusion at the Schmidt number Sc with the zero-sum correction,
+ * J_k = -(mu / Sc) (grad Y_k - Y_k sum_j grad Y_j); heat flux q = -kappa grad T + sum_k h_k J_k;
+ * BR1 central fluxes on (rho, rho u, T, Y_k).  The mesh allocates 33 doubles per node for its
+ * viscous flux on the first such call. */
 #define DG_GAS_PERFECT 0
 #define DG_GAS_NASA7 1
 
@@ -205,6 +212,8 @@ typedef struct {
   double R_universal;        /* NASA-7: R_k = R_universal / W_k                    */
   double newton_tol;         /* NASA-7: stop at |dT| < tol (K), e.g. 1e-10         */
   int32_t newton_max_it;     /* NASA-7: iteration cap, e.g. 50                     */
+  double Sc;                 /* NASA-7 with mu > 0: Schmidt number of the species  */
+                             /* diffusion, rho D = mu / Sc (> 0)                   */
 } dg_gas_desc;
 
 /* Perfect gas (Sec. 5.3): p = (gamma-1)(rho E - rho |u|^2 / 2).

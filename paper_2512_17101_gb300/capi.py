@@ -59,7 +59,7 @@ class dg_av_params(ctypes.Structure):
 class dg_gas_desc(ctypes.Structure):
     _fields_ = [("model", c_int32), ("gamma", c_double), ("R", c_double), ("mu", c_double), ("Pr", c_double),
                 ("nspecies", c_int32), ("W", c_void_p), ("nasa7", c_void_p), ("R_universal", c_double),
-                ("newton_tol", c_double), ("newton_max_it", c_int32)]
+                ("newton_tol", c_double), ("newton_max_it", c_int32), ("Sc", c_double)]
 
 
 class dg_mesh_tables(ctypes.Structure):

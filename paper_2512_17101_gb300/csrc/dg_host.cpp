@@ -48,6 +48,7 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.modal);
   cudaFree(d.av_eps);
   cudaFree(d.av_sig);
+  cudaFree(d.mix_fv);
   d = dg::MeshDev();
 }
 
@@ -200,6 +201,19 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     });
     if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
     T = T_io;
+  }
+  const bool mix_ns = g.model == DG_GAS_NASA7 && g.mu > 0;
+  if (mix_ns) {
+    if (!m.mix_fv) {  // first viscous-mixture call on this mesh: its flux buffer
+      e = cudaMalloc((void**)&mesh->d.mix_fv, sizeof(double) * (9 + 3 * DG_MAX_SPECIES) * (size_t)m.K * m.Np);
+      if (e != cudaSuccess) return cuda_fail(e, "mixture viscous-flux buffer");
+    }
+    e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_mixture(m, g, q, T, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "mixture viscous flux kernel");
+    e = timed(mesh, DG_KERNEL_RHS, s,
+              [&] { return dg::launch_rhs_mixture_ns(m, g, q, out, k, T, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
+    return DG_OK;
   }
   if (g.mu > 0) {
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
@@ -426,7 +440,8 @@ int dg_gas_create(const dg_gas_desc* desc, dg_gas* out) {
     if (desc->nspecies < 1 || desc->nspecies > DG_MAX_SPECIES)
       return fail(DG_ERR_INVALID_ARG, "nspecies must be in 1..8");
     if (!desc->W || !desc->nasa7) return fail(DG_ERR_INVALID_ARG, "NULL W or nasa7");
-    if (desc->mu > 0) return fail(DG_ERR_UNSUPPORTED, "viscous mixtures are not supported");
+    if (desc->mu > 0 && !(desc->Sc > 0)) return fail(DG_ERR_INVALID_ARG, "a viscous mixture needs Sc > 0");
+    p.Sc = desc->Sc;
     if (!(desc->R_universal > 0)) return fail(DG_ERR_INVALID_ARG, "R_universal must be > 0");
     if (!(desc->newton_tol > 0) || desc->newton_max_it < 1)
       return fail(DG_ERR_INVALID_ARG, "need newton_tol > 0 and newton_max_it >= 1");

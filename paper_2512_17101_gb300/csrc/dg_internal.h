@@ -48,6 +48,7 @@ struct GasParams {  // passed to kernels by value
   double a[DG_MAX_SPECIES][7];
   double newton_tol;
   int newton_max_it;
+  double Sc;        // NASA-7 with viscosity: Schmidt number, rho D = mu / Sc
 };
 
 // Split-BF16 operator tables of the mixed-precision path (built at upload): three terms
@@ -82,6 +83,7 @@ struct MeshDev {
   double* modal = nullptr;
   double* av_eps = nullptr;
   double* av_sig = nullptr;
+  double* mix_fv = nullptr;  // viscous flux of a mixture, [9 + 3 DG_MAX_SPECIES][K][Np] (on first use)
   MixedOps mx;
   double* ops = nullptr;       // Dr | Ds | Dt | LIFT, row-major
   int32_t* fmask = nullptr;    // [4][Nfp]
@@ -107,6 +109,12 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
 cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
 cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
+// flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.
+cudaError_t launch_viscous_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
+                                   cudaStream_t s);
+cudaError_t launch_rhs_mixture_ns(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                                  const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
 cudaError_t launch_rhs_av(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                           double a, double b, double dt, cudaStream_t s);
 // Mixed-precision path: primitives pass (k_mixed.cu); operator tables, tensor-core right-hand

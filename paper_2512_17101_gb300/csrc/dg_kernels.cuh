@@ -33,7 +33,10 @@ struct Ord {
 };
 
 // EULER_AV / NS_AV: the perfect-gas right-hand sides with the artificial-viscosity flux added.
-enum Phys { EULER = 0, NAVIER_STOKES = 1, MIXTURE = 2, EULER_AV = 3, NS_AV = 4 };
+// MIXTURE_NS: the NASA-7 mixture with viscosity, heat conduction and species diffusion (its
+// viscous flux, [9 + 3 ns][K][Np], read from global memory).
+enum Phys { EULER = 0, NAVIER_STOKES = 1, MIXTURE = 2, EULER_AV = 3, NS_AV = 4, MIXTURE_NS = 5 };
+__host__ __device__ constexpr bool is_mix(int PHYS) { return PHYS == MIXTURE || PHYS == MIXTURE_NS; }
 __host__ __device__ constexpr bool has_visc(int PHYS) { return PHYS == NAVIER_STOKES || PHYS == NS_AV; }
 __host__ __device__ constexpr bool has_av(int PHYS) { return PHYS == EULER_AV || PHYS == NS_AV; }
 
@@ -62,7 +65,7 @@ template <int PHYS, int V>
 __device__ __forceinline__ void thermo(const GasParams& g, const double* qv, double ir, double T, double& p,
                                        double& c) {
   const double ke = 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
-  if (PHYS != MIXTURE) {
+  if (!is_mix(PHYS)) {
     p = (g.gamma - 1.0) * (qv[4] - ke);
     c = sqrt(g.gamma * p * ir);
   } else {
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   double* sFv = sG + V * EPB * NF;
   constexpr bool VISC = has_visc(PHYS), AV = has_av(PHYS);
   double* sT = sFv + (VISC ? 9 * NODES : 0);
-  int* sFm = reinterpret_cast<int*>(sT + (PHYS == MIXTURE ? NODES : 0));
+  int* sFm = reinterpret_cast<int*>(sT + (is_mix(PHYS) ? NODES : 0));
 
   const int tid = threadIdx.x;
   const int e0 = blockIdx.x * EPB;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   if (VISC)
     for (int c = 0; c < 9; ++c)
       for (int i = tid; i < nn; i += blockDim.x) sFv[c * NODES + i] = fv_g[c * KNp + base + i];
-  if (PHYS == MIXTURE)
+  if (is_mix(PHYS))
     for (int i = tid; i < nn; i += blockDim.x) sT[i] = Tg[base + i];
   __syncthreads();
 
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     for (int v = 0; v < V; ++v) qv[v] = v < nvar ? sQ[v * NODES + tid] : 0.0;
     const double ir = 1.0 / qv[0];
     double p, c;
-    thermo<PHYS, V>(gp, qv, ir, PHYS == MIXTURE ? sT[tid] : 0.0, p, c);
+    thermo<PHYS, V>(gp, qv, ir, is_mix(PHYS) ? sT[tid] : 0.0, p, c);
     if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
     const double vel[3] = {qv[1] * ir, qv[2] * ir, qv[3] * ir};
     double F[3][V];
@@ -189,6 +192,15 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
 #pragma unroll
         for (int i = 0; i < 3; ++i) F[d][1 + i] -= sFv[tau_index(i, d) * NODES + tid];
         F[d][4] -= sFv[(6 + d) * NODES + tid];
+      }
+      if (PHYS == MIXTURE_NS) {  // viscous flux of the mixture, [9 + 3 ns][K][Np]
+        const size_t gi = base + tid;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) F[d][1 + i] -= fv_g[tau_index(i, d) * KNp + gi];
+        F[d][4] -= fv_g[(6 + d) * KNp + gi];
+#pragma unroll
+        for (int v = 5; v < V; ++v)
+          if (v < nvar) F[d][v] -= fv_g[(9 + 3 * (v - 5) + d) * KNp + gi];
       }
       // artificial-viscosity flux eps grad q_v along x_d at av_g[(5 d + v)][K][Np]: zero, and not
       // stored, in elements with eps = 0 (most of them), so it is read from HBM only where eps > 0
@@ -226,8 +238,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     if (P < 0) ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
     const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
     double pm, cm, pp, cp;
-    thermo<PHYS, V>(gp, qm, irm, PHYS == MIXTURE ? sT[own] : 0.0, pm, cm);
-    thermo<PHYS, V>(gp, qp, irp, PHYS == MIXTURE ? Tg[Pn] : 0.0, pp, cp);
+    thermo<PHYS, V>(gp, qm, irm, is_mix(PHYS) ? sT[own] : 0.0, pm, cm);
+    thermo<PHYS, V>(gp, qp, irp, is_mix(PHYS) ? Tg[Pn] : 0.0, pp, cp);
     if (P < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
     const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
     const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
@@ -253,6 +265,33 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
             sp = fma(nx, av_g[(0 + v) * KNp + Pn], fma(ny, av_g[(5 + v) * KNp + Pn], nz * av_g[(10 + v) * KNp + Pn]));
           g[v] -= 0.5 * (sm - sp);
         }
+      }
+    }
+    if (PHYS == MIXTURE_NS) {  // central viscous flux of the mixture (periodic meshes only)
+      const size_t gM = base + own;
+      const double nn3[3] = {nx, ny, nz};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double dm = 0.0, dp = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int c = tau_index(i, d);
+          dm = fma(nn3[d], fv_g[c * KNp + gM], dm);
+          dp = fma(nn3[d], fv_g[c * KNp + Pn], dp);
+        }
+        g[1 + i] -= 0.5 * (dm - dp);
+      }
+#pragma unroll
+      for (int v = 4; v < V; ++v) {
+        if (v >= nvar) break;
+        const int c0 = v == 4 ? 6 : 9 + 3 * (v - 5);
+        double dm = 0.0, dp = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          dm = fma(nn3[d], fv_g[(c0 + d) * KNp + gM], dm);
+          dp = fma(nn3[d], fv_g[(c0 + d) * KNp + Pn], dp);
+        }
+        g[v] -= 0.5 * (dm - dp);
       }
     }
     if (VISC) {
@@ -497,7 +536,7 @@ template <int N, int V, int PHYS>
 constexpr size_t rhs_smem() {
   using O = Ord<N>;
   return sizeof(double) * (O::OPS + O::EPB * GS + V * O::NODES + 3 * V * O::NODES + V * O::EPB * O::NF +
-                           (has_visc(PHYS) ? 9 * O::NODES : 0) + (PHYS == MIXTURE ? O::NODES : 0)) +
+                           (has_visc(PHYS) ? 9 * O::NODES : 0) + (is_mix(PHYS) ? O::NODES : 0)) +
          sizeof(int) * O::NF;
 }
 
@@ -520,7 +559,8 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP, m.scratch,
+  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP,
+                                                           PHYS == MIXTURE_NS ? m.mix_fv : m.scratch,
                                                            m.av_sig, m.av_eps, m.status, g, m.bc, m.K, nvar, a, b,
                                                            dt);
   return cudaGetLastError();

@@ -158,11 +158,13 @@ class Gas:
     """A gas model (dg_gas handle): perfect gas or NASA-7 mixture."""
 
     def __init__(self, *, model="perfect", gamma=1.4, R=1.0, mu=0.0, Pr=0.71, W=None, nasa7=None,
-                 R_universal=8314.462618, newton_tol=1e-10, newton_max_it=50):
+                 R_universal=8314.462618, newton_tol=1e-10, newton_max_it=50, Sc=0.0):
+        """Sc: Schmidt number of the species diffusion of a viscous NASA-7 mixture."""
         lib = load()
         d = capi.dg_gas_desc()
         d.mu = mu
         d.Pr = Pr
+        d.Sc = Sc
         if model == "perfect":
             d.model = capi.DG_GAS_PERFECT
             d.gamma = gamma
