@@ -452,11 +452,12 @@ def gpu_arm(args, cfg, world, rank, local):
     if rank == 0 and not args.no_hex:
         hexf = hex_form(args, local)
         hexadv = hex_advection_form(args, local)
-    bnd = avf = None
+    bnd = avf = mixns = None
     if rank == 0 and not args.no_boundary:
         periodic = value if (head == "fp64" and cfg.name == "ns_viscous") else None
         bnd = boundary_form(args, local, periodic)
         avf = av_form(args, local)
+        mixns = mixture_ns_form(args, local)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -467,7 +468,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
-            "hex_advection_form": hexadv, "boundary_form": bnd, "av_form": avf, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "hex_advection_form": hexadv, "boundary_form": bnd, "av_form": avf, "mixture_ns_form": mixns, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -790,6 +791,67 @@ def av_form(args, local):
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
+def mixture_ns_form(args, local):
+    """The viscous mixture with species diffusion (7 species, the mixture workload's mesh and
+    state: 32^3 x 6 tets, N = 2), FP64 RK4 steps with CUDA events and the kernel split, against
+    the same steps without viscosity."""
+    import numpy as np
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads.configs import build_case, get_config
+
+    cfg = get_config("mixture_learned")
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    mix = case["mixture"]
+    mesh = dg.Mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"])
+    Rk = 8314.462618 / np.asarray(mix.W)
+    Rmix = np.einsum("k,k...->...", Rk, case["Y"])
+    rho = case["p0"] / (Rmix * case["T"])
+    # conserved state from (rho, u, Y, T) with the library's own energy evaluation
+    e = torch.empty(case["T"].size, dtype=torch.float64, device=dev)
+    out = {}
+    for visc in (True, False):
+        gas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs, newton_tol=1e-10, newton_max_it=50,
+                     mu=1.8e-5 if visc else 0.0, Pr=0.71, Sc=0.7)
+        dg.dg_mixture_energy(gas, torch.tensor(np.ascontiguousarray(case["T"].ravel()), device=dev),
+                             torch.tensor(np.ascontiguousarray(case["Y"].reshape(case["Y"].shape[0], -1)),
+                                          device=dev).contiguous(), e)
+        ee = e.cpu().numpy().reshape(case["T"].shape)
+        vel = case["vel"]
+        E = rho * (ee + 0.5 * np.sum(vel ** 2, axis=0))
+        q0 = torch.tensor(np.concatenate([rho[None], rho[None] * vel, E[None], rho[None] * case["Y"]]), device=dev)
+        q = q0.clone()
+        T = torch.tensor(case["T"], device=dev)
+        work = (torch.empty_like(q), torch.zeros_like(q))
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, T_io=T, work=work)
+        q.copy_(q0)
+        mesh.kernel_times(reset=True)
+        mesh.set_timing(True)
+        total = 0.0
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, T_io=T, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        mesh.set_timing(False)
+        kt = {n: {"avg_ms": ms / c, "launches": c} for n, (ms, c) in mesh.kernel_times(reset=True).items() if c}
+        if mesh.status() != 0 or gas.status() != 0:
+            raise SystemExit("status flags set in the viscous-mixture run")
+        out[visc] = (total / max(1, args.steps), kt)
+    ms, kt = out[True]
+    return {"workload": f"{cfg.name} mesh and state with viscosity (mu = 1.8e-5, Pr = 0.71, Sc = 0.7): 7-species "
+                        f"NASA-7 mixture, 32^3 x 6 = 196,608 tets, N = 2, species and enthalpy diffusion",
+            "K": cfg.K, "N": cfg.N, "V": 12, "dtype": "f64", "steps": max(1, args.steps), "ms_per_step": ms,
+            "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step_inviscid": out[False][0],
+            "kernels": kt, "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+
+
 def hex_advection_flops_per_element(M, velocity):
     """FP64 flops of the advection right-hand side + stage update per element (M = N+1): per node
     3 line derivatives of M FMAs (the factor -a_d (2/h_d) dt folded into D) and the 2 FMAs of the
@@ -923,7 +985,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
-    ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel and artificial-viscosity sections")
+    ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel, artificial-viscosity and viscous-mixture sections")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()
