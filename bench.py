@@ -710,6 +710,25 @@ def boundary_form(args, local, periodic_fp64=None):
         raise SystemExit("status flags set in the wall-bounded run")
     ms = total / steps
     value = cfg.dofs * 5 / (ms * 1e-3)
+    # the same steps in the mixed-precision form
+    from paper_2512_17101_gb300 import capi
+    mixed = dg._opts(precision=capi.DG_PREC_MIXED)
+    qm = q0.clone()
+    for _ in range(max(3, args.warmup)):
+        dg.lsrk4_step(mesh, gas, qm, cfg.dt, steps=1, work=work, opts=mixed)
+    qm.copy_(q0)
+    total_m = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.lsrk4_step(mesh, gas, qm, cfg.dt, steps=1, work=work, opts=mixed)
+        b.record()
+        torch.cuda.synchronize()
+        total_m += a.elapsed_time(b)
+    if mesh.status() != 0:
+        raise SystemExit("status flags set in the wall-bounded mixed-form run")
+    ms_m = total_m / steps
     nbnd = int((case["face_bc"] != 0).sum())
     cpu = None
     if not args.no_cpu_baseline:  # the oracle's right-hand side on the channel at 6^3 x 6 tets (one core)
@@ -731,6 +750,8 @@ def boundary_form(args, local, periodic_fp64=None):
             "boundary_faces": nbnd, "steps": steps, "ms_per_step": ms, "value": value, "unit": "DOF-updates/s",
             "vs_periodic_same_size": None if not periodic_fp64 else value / periodic_fp64,
             "kernels": kt,
+            "mixed_form": {"ms_per_step": ms_m, "value": cfg.dofs * 5 / (ms_m * 1e-3), "unit": "DOF-updates/s",
+                           "vs_fp64": ms / ms_m},
             "cpu_oracle_stage": cpu,
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 

@@ -147,8 +147,6 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
   }
   if (m.boundary_faces > 0) {
-    if (opts && opts->precision == DG_PREC_MIXED)
-      return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces run in the FP64 form only");
     if (g.model != DG_GAS_PERFECT)
       return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces need a perfect gas");
     if (m.inflow_faces > 0 && m.inflow_nvar != V)

@@ -87,7 +87,55 @@ struct MixedCase {
   int nvar;   // conserved variables: 5, or 5 + species for a mixture
   double dt;
   MixedGas gas;
+  // DG_BC_INFLOW state as a node record and a temperature pair (perfect gas)
+  float4 in_node[2];
+  float2 in_temp;
 };
+
+// Exterior record of a boundary face node (code = -vmapP; r0, r1 hold the node's own record on
+// entry): the ghost states of the FP64 path in record form: slip wall (momentum mirrored), no-slip
+// wall (momentum reversed), inflow (the prescribed state), outflow (the node's own).
+__device__ __forceinline__ void ghost_record(int code, const float n[3], const MixedCase& c, float4& r0, float4& r1) {
+  if (code == DG_BC_SLIP_WALL) {
+    const float mn2 = 2.0f * (r0.y * n[0] + r0.z * n[1] + r0.w * n[2]);
+    r0.y -= mn2 * n[0];
+    r0.z -= mn2 * n[1];
+    r0.w -= mn2 * n[2];
+  } else if (code == DG_BC_NOSLIP_WALL) {
+    r0.y = -r0.y;
+    r0.z = -r0.z;
+    r0.w = -r0.w;
+  } else if (code == DG_BC_INFLOW) {
+    r0 = c.in_node[0];
+    r1 = c.in_node[1];
+  }
+}
+
+// Exterior viscous flux {tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, Q_x, Q_y, Q_z} of a
+// boundary face node (fv holds the node's own on entry): walls are adiabatic (Q+ = -Q-); a slip
+// wall is shear-free, tau+ = -tau- + 2 (n.tau- n) n n^T, so that tau+ n = 2 (n.tau- n) n - tau- n.
+__device__ __forceinline__ void ghost_viscous(int code, const float n[3], float fv[9]) {
+  if (code != DG_BC_SLIP_WALL && code != DG_BC_NOSLIP_WALL) return;
+  fv[6] = -fv[6];
+  fv[7] = -fv[7];
+  fv[8] = -fv[8];
+  if (code == DG_BC_SLIP_WALL) {
+    float tn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tn[i] = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) tn[i] = fmaf(n[d], fv[kern::tau_index(i, d)], tn[i]);
+    }
+    const float tnn2 = 2.0f * (tn[0] * n[0] + tn[1] * n[1] + tn[2] * n[2]);
+    fv[0] = fmaf(tnn2, n[0] * n[0], -fv[0]);
+    fv[1] = fmaf(tnn2, n[1] * n[1], -fv[1]);
+    fv[2] = fmaf(tnn2, n[2] * n[2], -fv[2]);
+    fv[3] = fmaf(tnn2, n[0] * n[1], -fv[3]);
+    fv[4] = fmaf(tnn2, n[0] * n[2], -fv[4]);
+    fv[5] = fmaf(tnn2, n[1] * n[2], -fv[5]);
+  }
+}
 
 // Per-node record of the mixed form for a mixture (64 of the scratch's 80 bytes per node), written
 // by the temperature Newton kernels at the converged temperature (dg_newton.cuh):

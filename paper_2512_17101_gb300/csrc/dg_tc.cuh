@@ -386,7 +386,8 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       const float n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
       const float fs = G[12 + 4 * f];
       const size_t own = base + (size_t)e * Np + S.fm[mm];
-      const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
+      const int Pi = c.vmapP[(size_t)(e0 + e) * NF + mm];  // < 0: boundary face node, -DG_BC_* code
+      const size_t P = Pi >= 0 ? (size_t)Pi : own;          // a boundary node gathers its own record
       float g[V];
       if constexpr (MIX) {
         float qm[V], qp[V];
@@ -396,7 +397,8 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, g);
       } else {
         const float4 m0r = c.node[2 * own], m1r = c.node[2 * own + 1];
-        const float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];
+        float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];
+        if (Pi < 0) mixk::ghost_record(-Pi, n3, c, p0r, p1r);
         const float qm[5] = {m0r.x, m0r.y, m0r.z, m0r.w, m1r.x}, qp[5] = {p0r.x, p0r.y, p0r.z, p0r.w, p1r.x};
         const float dpn = (m1r.y - p1r.y) + (m1r.z - p1r.z);  // p- - p+ from the hi/lo pairs
         float fvm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, fvp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -406,6 +408,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
           fvm[4] = b2.x; fvm[5] = b2.y; fvm[6] = b2.z; fvm[7] = b2.w; fvm[8] = c.fvz[own];
           fvp[0] = cc4.x; fvp[1] = cc4.y; fvp[2] = cc4.z; fvp[3] = cc4.w;
           fvp[4] = d4.x; fvp[5] = d4.y; fvp[6] = d4.z; fvp[7] = d4.w; fvp[8] = c.fvz[P];
+          if (Pi < 0) mixk::ghost_viscous(-Pi, n3, fvp);
         }
         mixk::face_term<NS>(qm, qp, m1r.y, p1r.y, dpn, fvm, fvp, n3, gam, g);
       }
@@ -618,9 +621,19 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     for (int j = tid; j < nel * w; j += NT) {
       const int e = j / w, mm = m0 + (j - e * w);
       const size_t own = base + (size_t)e * Np + S.fm[mm];
-      const size_t P = (size_t)c.vmapP[(size_t)(e0 + e) * NF + mm];
-      const float4 o0 = c.node[2 * own], o1 = c.node[2 * own + 1], q0 = c.node[2 * P], q1 = c.node[2 * P + 1];
-      const float2 to = c.temp[own], tp = c.temp[P];
+      const int Pi = c.vmapP[(size_t)(e0 + e) * NF + mm];  // < 0: boundary face node, -DG_BC_* code
+      const size_t P = Pi >= 0 ? (size_t)Pi : own;          // a boundary node gathers its own record
+      const float4 o0 = c.node[2 * own], o1 = c.node[2 * own + 1];
+      float4 q0 = c.node[2 * P], q1 = c.node[2 * P + 1];
+      const float2 to = c.temp[own];
+      float2 tp = c.temp[P];
+      if (Pi < 0) {  // exterior values w(q+) of the face's ghost state
+        const int f = mm / C_::Nfp;
+        const float* G = S.geo + e * GS;
+        const float n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+        mixk::ghost_record(-Pi, n3, c, q0, q1);
+        if (-Pi == DG_BC_INFLOW) tp = c.in_temp;
+      }
       const float jv[5] = {(q0.x - o0.x) + (q1.w - o1.w), q0.y - o0.y, q0.z - o0.z, q0.w - o0.w,
                            (tp.x - to.x) + (tp.y - to.y)};
 #pragma unroll

@@ -35,6 +35,15 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
   c.Np = m.Np;
   c.dt = dt;
   c.gas = mixk::MixedGas{g.gamma, g.R, g.mu, g.kappa, 1.0 / g.R};
+  if (m.inflow_nvar == 5 && g.model == DG_GAS_PERFECT) {  // the inflow state as a node record
+    const double* qi = m.bc.q_in;
+    const double ke = 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];
+    const double p = (g.gamma - 1.0) * (qi[4] - ke), T = p / (qi[0] * g.R);
+    const float rho_hi = (float)qi[0], p_hi = (float)p, T_hi = (float)T;
+    c.in_node[0] = make_float4(rho_hi, (float)qi[1], (float)qi[2], (float)qi[3]);
+    c.in_node[1] = make_float4((float)qi[4], p_hi, (float)(p - (double)p_hi), (float)(qi[0] - (double)rho_hi));
+    c.in_temp = make_float2(T_hi, (float)(T - (double)T_hi));
+  }
   return c;
 }
 

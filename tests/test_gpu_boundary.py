@@ -8,7 +8,7 @@ import pytest
 import oracle.boundary as bd
 from oracle.lsrk import lsrk4_step
 from oracle.thermo import PerfectGas
-from tests._gpu import rel_err, torch_cuda
+from tests._gpu import field_err, rel_err, torch_cuda
 from tests._oracle_case import bc_disc
 from workloads import equispaced_tet_nodes, uniform_perturbation
 
@@ -86,13 +86,11 @@ def test_two_rk4_steps_with_boundaries(viscous):
     assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
 
 
-def test_boundary_meshes_reject_other_forms():
+def test_boundary_meshes_need_their_inflow_state():
     torch, dg, d, mesh, gas = _setup((2, 2, 2), 2, SIDES["in_out_x_walls_y"], True)
     from paper_2512_17101_gb300 import capi
     q = torch.tensor(_smooth(d.xyz), device="cuda")
     rhs = torch.empty_like(q)
-    with pytest.raises(capi.DGError):
-        dg.dg_rhs(mesh, gas, q, rhs, opts=dg._opts(precision=capi.DG_PREC_MIXED))
     bare = dg.Mesh(d.vertices, d.period, 2, equispaced_tet_nodes(2), face_bc=d.face_bc)
     with pytest.raises(capi.DGError):  # inflow faces without an inflow state
         dg.dg_rhs(bare, gas, q, rhs)
@@ -131,3 +129,42 @@ def test_channel_full_size_stage():
     want = bd.rhs_ns_bc(d.ref, d.geo, d.conn, q0, GAS, 1e-3, 0.71)
     assert rel_err(k.cpu().numpy(), cfg.dt * want) <= TOL
     assert mesh.status() == 0
+
+
+# --- the mixed-precision form with boundaries ------------------------------------------------------
+
+
+MIXED_RHS_TOL = 1e-4  # per field, as for the periodic mixed form (tests/test_gpu_mixed.py)
+
+
+def _mixed_opts(dg):
+    from paper_2512_17101_gb300 import capi
+    return dg._opts(precision=capi.DG_PREC_MIXED)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("name", list(SIDES))
+@pytest.mark.parametrize("N", [2, 3])
+def test_mixed_rhs_with_boundaries(N, name, viscous):
+    torch, dg, d, mesh, gas = _setup((3, 2, 2), N, SIDES[name], viscous)
+    q0 = _smooth(d.xyz)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs, opts=_mixed_opts(dg))
+    err = field_err(rhs.cpu().numpy(), _want(d, q0, viscous))
+    assert err <= MIXED_RHS_TOL, err
+    assert mesh.status() == 0
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_mixed_rk4_steps_with_boundaries(viscous):
+    """Two RK4 steps of the mixed form against the oracle: state error <= 1e-6 per field."""
+    torch, dg, d, mesh, gas = _setup((3, 3, 2), 3, SIDES["in_out_x_walls_y"], viscous)
+    q0 = _smooth(d.xyz, seed=3)
+    dt = 1e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.lsrk4_step(mesh, gas, q, dt, steps=2, opts=_mixed_opts(dg))
+    f = lambda u: _want(d, u, viscous)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    err = field_err(q.cpu().numpy(), want)
+    assert err <= 1e-6, err
