@@ -40,12 +40,12 @@ FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
-    ("46bd0c832d9bb35a", "rhs"): 289.528320e6 + 105.552384e6,
-    ("46bd0c832d9bb35a", "viscous"): 99.328000e6 + 74.704128e6,
+    ("ff6530f6721628b0", "rhs"): 289.511936e6 + 105.523456e6,
+    ("ff6530f6721628b0", "viscous"): 99.331328e6 + 74.569728e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("2ba9f488305c1d84", "mixed_rhs"): 256.088320e6 + 119.813376e6,
-    ("2ba9f488305c1d84", "mixed_viscous"): 90.063616e6 + 26.145024e6,
-    ("2ba9f488305c1d84", "mixed_prims"): 66.374912e6 + 14.992128e6,
+    ("583bb8011d7b7afd", "mixed_rhs"): 255.000576e6 + 117.647360e6,
+    ("583bb8011d7b7afd", "mixed_viscous"): 90.068992e6 + 26.120960e6,
+    ("583bb8011d7b7afd", "mixed_prims"): 66.372096e6 + 14.673920e6,
 }
 
 
