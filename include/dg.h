@@ -95,8 +95,9 @@ typedef struct {
  *   DG_BC_INFLOW      q+ = the state set by dg_mesh_set_inflow (supersonic inflow);
  *   DG_BC_OUTFLOW     q+ = q- (supersonic outflow).
  * BR1 exterior values are w(q+); away from walls the viscous exterior flux is the interior one.
- * Meshes with boundary faces run in the FP64 form with a perfect gas (Euler or Navier-Stokes);
- * the mixed-precision form, the mixture and the batched form reject them (DG_ERR_UNSUPPORTED).
+ * Meshes with boundary faces run with a perfect gas (Euler or Navier-Stokes) in the FP64 and
+ * the mixed-precision forms (there as ghost node records); the mixture and the batched form
+ * reject them (DG_ERR_UNSUPPORTED).
  * In the vmapP of dg_mesh_connectivity a boundary face node holds -code. */
 #define DG_BC_SLIP_WALL 1
 #define DG_BC_NOSLIP_WALL 2
