@@ -17,6 +17,8 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
   with the local Lax-Friedrichs flux n.F* = (n.F(q-) + n.F(q+))/2 + lambda (q- - q+)/2,
   lambda = max(|u-.n| + c-, |u+.n| + c+) at the face node; q+ is the neighbour's node at the
   same position on the shared face (periodic box).
+* boundary conditions on box faces (box["bc"][axis][end], the codes of oracle/boundary.py): q+
+  at a boundary face node is the ghost state of the condition, with n = -e_axis or +e_axis;
 * weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
   with the summation-by-parts identity W D + D^T W = diag(-1, 0, ..., 0, 1) it equals the
   strong form up to rounding.
@@ -105,7 +107,30 @@ def _face_slices(N, axis, end):
     return (Ellipsis,) + tuple(idx)
 
 
-def _surface_terms(ref, box, q5, gas):
+def _boundary_elements(box, axis, end):
+    """Elements whose face (axis, end) lies on the box boundary."""
+    nx, ny, nz = box["n"]
+    e = np.arange(nx * ny * nz)
+    c = [e % nx, (e // nx) % ny, e // (nx * ny)]
+    return c[axis] == (0 if end == 0 else box["n"][axis] - 1)
+
+
+def _exterior(box, axis, end, qm, qp, q_in):
+    """q+ of face (axis, end): the neighbour's trace, or on the box boundary the ghost state of
+    the face's condition box["bc"][axis][end] (oracle/boundary.py; n = -e_axis or +e_axis)."""
+    code = box.get("bc", ((0, 0), (0, 0), (0, 0)))[axis][end]
+    if not code:
+        return qp
+    from .boundary import exterior_state
+    shape = qm.shape[1:]  # [K][face nodes...]
+    n = np.zeros((3,) + shape)
+    n[axis] = -1.0 if end == 0 else 1.0
+    on = _boundary_elements(box, axis, end).reshape((-1,) + (1,) * (len(shape) - 1))
+    bc = np.broadcast_to(np.where(on, code, 0), shape)
+    return exterior_state(qm, qp, bc, n, q_in)
+
+
+def _surface_terms(ref, box, q5, gas, q_in=None):
     """Per face (axis, end): (selector, lifting factor, n.F(q-), n.F*) at the face nodes."""
     N = ref.N
     out = []
@@ -115,6 +140,7 @@ def _surface_terms(ref, box, q5, gas):
             nb = _neighbour(box, axis, -1 if end == 0 else 1)
             qm = q5[_face_slices(N, axis, end)]             # [V][K][face]
             qp = q5[:, nb][_face_slices(N, axis, 1 - end)]  # the neighbour's opposite face
+            qp = _exterior(box, axis, end, qm, qp, q_in)
             pm, cm = gas.pressure_sound_speed(qm)
             pp, cp = gas.pressure_sound_speed(qp)
             fm = sign * euler_flux(qm, pm)[axis]
@@ -130,20 +156,21 @@ def _volume_fluxes(q5, gas):
     return list(euler_flux(q5, gas.pressure(q5)))
 
 
-def hex_rhs_strong(ref, box, q, gas):
-    """Strong-form right-hand side, q[5][K][Np] -> rhs[5][K][Np]."""
+def hex_rhs_strong(ref, box, q, gas, q_in=None):
+    """Strong-form right-hand side, q[5][K][Np] -> rhs[5][K][Np]; box["bc"][axis][end] (optional)
+    puts a boundary condition on the box face instead of periodicity."""
     N = ref.N
     q5 = _shape(np.asarray(q, dtype=np.float64), N)
     F = _volume_fluxes(q5, gas)
     rhs = np.zeros_like(q5)
     for d in range(3):
         rhs -= (2.0 / box["h"][d]) * _along(ref.D, F[d], d)
-    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
         rhs[sel] += lift * (fm - fstar)
     return rhs.reshape(q.shape)
 
 
-def hex_rhs_weak(ref, box, q, gas):
+def hex_rhs_weak(ref, box, q, gas, q_in=None):
     """Weak-form right-hand side (the cross-check of the strong form)."""
     N = ref.N
     q5 = _shape(np.asarray(q, dtype=np.float64), N)
@@ -153,7 +180,7 @@ def hex_rhs_weak(ref, box, q, gas):
     rhs = np.zeros_like(q5)
     for d in range(3):
         rhs += (2.0 / box["h"][d]) * _along(Mt, F[d], d)
-    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
         rhs[sel] -= lift * fstar
     return rhs.reshape(q.shape)
 

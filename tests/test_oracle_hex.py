@@ -134,15 +134,15 @@ def test_translation_invariance():
 
 def _plant_wrong_lift(m):
     orig = m._surface_terms
-    return "_surface_terms", lambda ref, box, q5, gas: [(s, 0.5 * l, fm, fs) for s, l, fm, fs in
-                                                        orig(ref, box, q5, gas)]
+    return "_surface_terms", lambda ref, box, q5, gas, q_in=None: [(s, 0.5 * l, fm, fs) for s, l, fm, fs in
+                                                                   orig(ref, box, q5, gas, q_in)]
 
 
 def _plant_no_dissipation_sign(m):
     orig = m._surface_terms
 
-    def bad(ref, box, q5, gas):
-        return [(s, l, fm, 2 * fm - fs) for s, l, fm, fs in orig(ref, box, q5, gas)]
+    def bad(ref, box, q5, gas, q_in=None):
+        return [(s, l, fm, 2 * fm - fs) for s, l, fm, fs in orig(ref, box, q5, gas, q_in)]
     return "_surface_terms", bad
 
 
@@ -153,7 +153,7 @@ def _plant_transposed_d(m):
 
 def _plant_drop_a_face(m):
     orig = m._surface_terms
-    return "_surface_terms", lambda ref, box, q5, gas: orig(ref, box, q5, gas)[1:]
+    return "_surface_terms", lambda ref, box, q5, gas, q_in=None: orig(ref, box, q5, gas, q_in)[1:]
 
 
 @pytest.mark.parametrize("plant", [_plant_wrong_lift, _plant_no_dissipation_sign, _plant_transposed_d,
