@@ -420,6 +420,9 @@ typedef struct {
   int32_t N;               /* order, 1..DG_MAX_ORDER                                          */
   const double* nodes1d;   /* host [N+1]: the 1-D node set, ascending, first -1 and last 1
                               (copied; Gauss-Lobatto-Legendre points in the workloads)        */
+  int32_t bc[6];           /* DG_BC_* code of the box faces x-, x+, y-, y+, z-, z+; 0 on both
+                              faces of an axis: periodic along it (ghost states as for the
+                              tetrahedral path, with n = -e_axis or +e_axis)                  */
 } dg_hex_desc;
 /* Builds the 1-D operators on the host and uploads them.  Errors: DG_ERR_INVALID_ARG (sizes,
  * node set), DG_ERR_CUDA. */
@@ -445,6 +448,11 @@ int dg_hex_advection_rhs(dg_hex_mesh mesh, const double* velocity, const double*
 /* LSRK4 stage of the advection: k <- a_s k + dt rhs(u_in); u_out <- u_in + b_s k. */
 int dg_hex_advection_rk_stage(dg_hex_mesh mesh, const double* velocity, int32_t stage, double dt,
                               const double* u_in_dev, double* u_out_dev, double* k_dev, void* stream);
+/* Conserved state q_in[5] (host) imposed on DG_BC_INFLOW box faces; required before a
+ * right-hand side on a box with such faces.  Errors: DG_ERR_INVALID_ARG (NULL, nvar != 5,
+ * non-finite, rho <= 0).  The advection entry points take periodic boxes only
+ * (DG_ERR_UNSUPPORTED otherwise). */
+int dg_hex_set_inflow(dg_hex_mesh mesh, const double* q_in, int32_t nvar);
 /* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
 int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);
 

@@ -87,7 +87,7 @@ class dg_opts(ctypes.Structure):
 # name -> (restype, argtypes); every entry point declared in include/dg.h
 class dg_hex_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("L", ctypes.c_double * 3), ("N", ctypes.c_int32),
-                ("nodes1d", ctypes.c_void_p)]
+                ("nodes1d", ctypes.c_void_p), ("bc", ctypes.c_int32 * 6)]
 
 
 SIGNATURES = {
@@ -136,6 +136,7 @@ SIGNATURES = {
                                             ctypes.c_void_p]),
     "dg_hex_advection_rk_stage": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "dg_hex_set_inflow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "dg_hex_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
     "dg_round_to_float": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "dg_widen_to_double": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),

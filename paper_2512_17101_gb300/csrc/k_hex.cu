@@ -26,6 +26,9 @@
 
 struct dg_hex_mesh_s {
   int n[3] = {0, 0, 0};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double q_in[5] = {0, 0, 0, 0, 0};
+  bool has_inflow = false;
   double L[3] = {0, 0, 0};
   int N = 0, M = 0, Np = 0;
   int64_t K = 0;
@@ -48,6 +51,8 @@ struct HexCfg {
 // that the kernel accumulates dt * rhs directly: the volume term uses D_d = -(2/h_d) s D.
 struct HexGeo {
   int n[3];
+  int bc[6];        // DG_BC_* code of the box faces x-, x+, y-, y+, z-, z+ (0: periodic)
+  double q_in[5];   // DG_BC_INFLOW state
   double dsc[3];    // -(2/h_d) s
   double lf[3][2];  // (2/h_d) / w_end s / 2
 };
@@ -73,11 +78,11 @@ __device__ __forceinline__ void pc(double gamma, const double* q, double& ir, do
   c = sqrt_nr(gamma * p * ir);
 }
 
-// The six periodic neighbours of element e, slot 2d + end (end 0: the -x_d side), in 32-bit
+// The six neighbours of element e, slot 2d + end (end 0: the -x_d side), in 32-bit
 // arithmetic (K < 2^31 is checked on the host): the 64-bit integer division is a long sequence
 // whose conversions compete for the FP64 pipe that bounds these kernels.  Computed once per
 // element, not per face node.
-__device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* nb) {
+__device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* nb, const int* bc = nullptr) {
   const unsigned nx = n[0], ny = n[1], nz = n[2], nxy = nx * ny;
   const unsigned t = e / nx, ex = e - t * nx, ez = t / ny, ey = t - ez * ny;
   nb[0] = (int)(ex == 0 ? e + (nx - 1) : e - 1);
@@ -86,6 +91,14 @@ __device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* 
   nb[3] = (int)(ey == ny - 1 ? e - (ny - 1) * nx : e + nx);
   nb[4] = (int)(ez == 0 ? e + (nz - 1) * nxy : e - nxy);
   nb[5] = (int)(ez == nz - 1 ? e - (nz - 1) * nxy : e + nxy);
+  if (bc) {  // faces on a non-periodic box boundary: -code
+    if (ex == 0 && bc[0]) nb[0] = -bc[0];
+    if (ex == nx - 1 && bc[1]) nb[1] = -bc[1];
+    if (ey == 0 && bc[2]) nb[2] = -bc[2];
+    if (ey == ny - 1 && bc[3]) nb[3] = -bc[3];
+    if (ez == 0 && bc[4]) nb[4] = -bc[4];
+    if (ez == nz - 1 && bc[5]) nb[5] = -bc[5];
+  }
 }
 
 template <int N, bool RK>
@@ -112,7 +125,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
   double qv[5] = {0, 0, 0, 0, 0};
-  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid]);
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid], geo.bc);
   if (tid < nn) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
@@ -150,16 +163,30 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       const int node = (end ? N : 0) * stride[d] + ia * s1 + ib * s2;
       const int loc = el * Np + node;
       const int nnode = node + (end ? -N : N) * stride[d];  // mirrored index along d
-      const size_t gP = (size_t)sNb[el][2 * d + end] * Np + nnode, gM = base + loc;
+      const int enb = sNb[el][2 * d + end];                 // < 0: box boundary, -DG_BC_* code
+      const size_t gM = base + loc, gP = enb >= 0 ? (size_t)enb * Np + nnode : gM;
       double qm[5], qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         qm[v] = q[v * KNp + gM];
         qp[v] = q[v * KNp + gP];
       }
+      if (enb < 0) {  // ghost state (n = -e_d or +e_d): mirrored or reversed momentum, inflow, outflow
+        if (-enb == DG_BC_SLIP_WALL) {
+          qp[1 + d] = -qp[1 + d];
+        } else if (-enb == DG_BC_NOSLIP_WALL) {
+          qp[1] = -qp[1];
+          qp[2] = -qp[2];
+          qp[3] = -qp[3];
+        } else if (-enb == DG_BC_INFLOW) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qp[v] = geo.q_in[v];
+        }
+      }
       const double irm = sPC[0][loc], pm = sPC[1][loc], cm = sPC[2][loc];
       double irp, pp, cp;
       pc(gamma, qp, irp, pp, cp);
+      if (enb < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
       // n = +-e_d: n.F(q) = +-(F_d(q)); the sign folded into the lifted term
       const double um = qm[1 + d] * irm, up = qp[1 + d] * irp;
       const double lam = fmax(fabs(um) + cm, fabs(up) + cp);
@@ -343,6 +370,8 @@ cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, doub
   using C = HexCfg<N>;
   const double sc = RK ? dt : 1.0;
   HexGeo geo;
+  for (int f = 0; f < 6; ++f) geo.bc[f] = m.bc[f];
+  for (int v = 0; v < 5; ++v) geo.q_in[v] = m.q_in[v];
   for (int d = 0; d < 3; ++d) {
     geo.n[d] = m.n[d];
     const double two_h = 2.0 / (m.L[d] / m.n[d]);
@@ -456,11 +485,18 @@ int dg_hex_mesh_create(const dg_hex_desc* d, dg_hex_mesh* out) {
   if (x[0] != -1.0 || x[M - 1] != 1.0) return dg::fail(DG_ERR_INVALID_ARG, "the node set must start at -1 and end at 1");
   for (int i = 1; i < M; ++i)
     if (!(x[i] > x[i - 1])) return dg::fail(DG_ERR_INVALID_ARG, "the node set must be ascending");
+  for (int k = 0; k < 3; ++k) {
+    const int a = d->bc[2 * k], b = d->bc[2 * k + 1];
+    if ((a == 0) != (b == 0)) return dg::fail(DG_ERR_INVALID_ARG, "a box axis is periodic at both ends or at neither");
+    for (int c : {a, b})
+      if (c < 0 || c > DG_BC_OUTFLOW) return dg::fail(DG_ERR_INVALID_ARG, "unknown boundary-condition code");
+  }
   dg_hex_mesh_s* m = new dg_hex_mesh_s();
   for (int k = 0; k < 3; ++k) {
     m->n[k] = d->n[k];
     m->L[k] = d->L[k];
   }
+  for (int f = 0; f < 6; ++f) m->bc[f] = d->bc[f];
   m->N = d->N;
   m->M = M;
   m->Np = M * M * M;
@@ -515,6 +551,9 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
     return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path solves the Euler equations of a perfect gas");
   const size_t n = (size_t)5 * m->K * m->Np;
   if (q == out || (q < out + n && out < q + n)) return dg::fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
+  for (int f = 0; f < 6; ++f)
+    if (m->bc[f] == DG_BC_INFLOW && !m->has_inflow)
+      return dg::fail(DG_ERR_INVALID_ARG, "the box has an inflow face: set its state with dg_hex_set_inflow");
   const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
   const cudaError_t e = dg::hexk::launch(*m, gas->p.gamma, q, out, k, rk, a, b, dt, (cudaStream_t)stream);
   return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral right-hand-side kernel");
@@ -538,6 +577,8 @@ static int hex_adv_run(dg_hex_mesh m, const double* vel, const double* u, double
   if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
   for (int d = 0; d < 3; ++d)
     if (!std::isfinite(vel[d])) return dg::fail(DG_ERR_INVALID_ARG, "the velocity must be finite");
+  for (int f = 0; f < 6; ++f)
+    if (m->bc[f]) return dg::fail(DG_ERR_UNSUPPORTED, "the advection runs on periodic boxes");
   const size_t n = (size_t)m->K * m->Np;
   if (u == out || (u < out + n && out < u + n)) return dg::fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
   const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
@@ -552,6 +593,17 @@ int dg_hex_advection_rhs(dg_hex_mesh m, const double* velocity, const double* u,
 int dg_hex_advection_rk_stage(dg_hex_mesh m, const double* velocity, int32_t stage, double dt, const double* u_in,
                               double* u_out, double* k, void* stream) {
   return hex_adv_run(m, velocity, u_in, u_out, k, true, stage, dt, stream);
+}
+
+int dg_hex_set_inflow(dg_hex_mesh m, const double* q_in, int32_t nvar) {
+  if (!m || !q_in) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh or inflow state");
+  if (nvar != 5) return dg::fail(DG_ERR_INVALID_ARG, "the hexahedral path takes 5 conserved variables");
+  for (int v = 0; v < 5; ++v)
+    if (!std::isfinite(q_in[v])) return dg::fail(DG_ERR_INVALID_ARG, "the inflow state must be finite");
+  if (!(q_in[0] > 0)) return dg::fail(DG_ERR_INVALID_ARG, "the inflow density must be positive");
+  for (int v = 0; v < 5; ++v) m->q_in[v] = q_in[v];
+  m->has_inflow = true;
+  return DG_OK;
 }
 
 int dg_hex_status(dg_hex_mesh m, uint32_t* bits, int reset) {

@@ -316,7 +316,8 @@ def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, str
 class HexMesh:
     """A periodic box of axis-aligned hexahedra with tensor-product nodes (dg_hex_mesh handle)."""
 
-    def __init__(self, n, L, N, nodes1d):
+    def __init__(self, n, L, N, nodes1d, bc=None):
+        """bc: optional ((x-, x+), (y-, y+), (z-, z+)) DG_BC_* codes of the box faces (0: periodic)."""
         n3 = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
         L3 = (L, L, L) if np.isscalar(L) else tuple(float(v) for v in L)
         self.N = int(N)
@@ -326,6 +327,8 @@ class HexMesh:
         d.L = (ctypes.c_double * 3)(*L3)
         d.N = self.N
         d.nodes1d = self._nodes.ctypes.data_as(ctypes.c_void_p)
+        if bc is not None:
+            d.bc = (ctypes.c_int32 * 6)(*[int(c) for pair in bc for c in pair])
         h = ctypes.c_void_p()
         check(load().dg_hex_mesh_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -337,6 +340,11 @@ class HexMesh:
         D, w = np.zeros((M, M)), np.zeros(M)
         check(load().dg_hex_operators(self.handle, _hptr(D), _hptr(w)))
         return D, w
+
+    def set_inflow(self, q_in):
+        """Conserved state (5 values) imposed on DG_BC_INFLOW box faces."""
+        v = np.ascontiguousarray(q_in, dtype=np.float64).reshape(-1)
+        check(load().dg_hex_set_inflow(self.handle, _hptr(v), int(v.size)))
 
     def status(self, reset=True):
         bits = ctypes.c_uint32()

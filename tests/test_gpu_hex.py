@@ -188,3 +188,59 @@ def test_hex_advection_full_size_stage():
     want_u, want_k = lsrk4_stage(case["u"], np.zeros_like(case["u"]), 0, cfg.dt, f)
     assert _rel(k.cpu().numpy(), want_k) <= TOL
     assert _rel(u_out.cpu().numpy() - case["u"], want_u - case["u"]) <= TOL
+
+
+# --- box-face boundary conditions ------------------------------------------------------------------
+
+import oracle.boundary as bd  # noqa: E402
+
+HEX_BC = {
+    "channel": ((bd.INFLOW, bd.OUTFLOW), (bd.SLIP_WALL, bd.SLIP_WALL), (0, 0)),
+    "closed": ((bd.SLIP_WALL, bd.SLIP_WALL), (bd.NOSLIP_WALL, bd.NOSLIP_WALL), (bd.SLIP_WALL, bd.OUTFLOW)),
+}
+
+
+def _bc_setup(n, N, bc):
+    torch, dg, box, ref, q0, mesh, gas = _setup(n, N)
+    box["bc"] = bc
+    mesh = dg.HexMesh(box["n"], box["L"], N, gll_nodes(N), bc=bc)
+    q_in = q0[:, 0, 0].copy()
+    mesh.set_inflow(q_in)
+    return torch, dg, box, ref, q0, mesh, gas, q_in
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("name", list(HEX_BC))
+def test_hex_rhs_with_boundaries(name, N):
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((3, 2, 2), N, HEX_BC[name])
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, gas, q, rhs)
+    want = hx.hex_rhs_strong(ref, box, q0, GAS, q_in=q_in)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_two_rk4_steps_with_boundaries():
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((4, 3, 2), 3, HEX_BC["channel"])
+    dt = 2e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.hex_lsrk4_step(mesh, gas, q, dt, steps=2)
+    f = lambda u: hx.hex_rhs_strong(ref, box, u, GAS, q_in=q_in)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+
+
+def test_hex_boundary_arguments():
+    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
+    from paper_2512_17101_gb300 import capi
+    with pytest.raises(capi.DGError):  # periodic at one end only
+        dg.HexMesh(2, 1.0, 2, gll_nodes(2), bc=((bd.SLIP_WALL, 0), (0, 0), (0, 0)))
+    m = dg.HexMesh(2, 1.0, 2, gll_nodes(2), bc=HEX_BC["channel"])
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    with pytest.raises(capi.DGError):  # inflow face without its state
+        dg.dg_hex_rhs(m, gas, q, rhs)
+    u = torch.zeros(m.K * m.Np, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.DGError):  # the advection runs on periodic boxes
+        dg.dg_hex_advection_rhs(m, (1.0, 0.0, 0.0), u, torch.empty_like(u))
