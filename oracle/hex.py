@@ -17,6 +17,10 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
   with the local Lax-Friedrichs flux n.F* = (n.F(q-) + n.F(q+))/2 + lambda (q- - q+)/2,
   lambda = max(|u-.n| + c-, |u+.n| + c+) at the face node; q+ is the neighbour's node at the
   same position on the shared face (periodic box).
+* Navier-Stokes (periodic boxes): BR1 with central fluxes in both passes, as on tetrahedra
+  (oracle/ns.py): grad_d w = (2/h_d) D_d w plus, at the face nodes of the two d-faces,
+  (2/h_d)/w_end n_d (w+ - w-)/2, for w = (rho, rho u, rho v, rho w, T); the viscous flux
+  (tau, u.tau + kappa grad T) enters G = F - Fv, and the face term gains -n.(Fv- - Fv+)/2;
 * boundary conditions on box faces (box["bc"][axis][end], the codes of oracle/boundary.py): q+
   at a boundary face node is the ghost state of the condition, with n = -e_axis or +e_axis;
 * weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
@@ -234,6 +238,55 @@ def hex_advection_rhs_weak(ref, box, u, a):
     for sel, lift, fm, fstar in _advection_surface_terms(ref, box, u5, a):
         rhs[sel] -= lift * fstar
     return rhs.reshape(np.shape(u))
+
+
+def hex_gradient(ref, box, w):
+    """BR1 gradient grad[3][F][K][Np] of w[F][K][Np] on a periodic box (central flux)."""
+    N = ref.N
+    F = w.shape[0]
+    w5 = w.reshape(F, w.shape[1], N + 1, N + 1, N + 1)
+    out = np.zeros((3,) + w5.shape)
+    for d in range(3):
+        out[d] = (2.0 / box["h"][d]) * _along(ref.D, w5, d)
+        for end in (0, 1):
+            nd = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, d, -1 if end == 0 else 1)
+            sel = _face_slices(N, d, end)
+            wm = w5[sel]
+            wp = w5[:, nb][_face_slices(N, d, 1 - end)]
+            lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
+            out[d][sel] += lift * nd * 0.5 * (wp - wm)
+    return out.reshape((3,) + w.shape)
+
+
+def hex_rhs_ns(ref, box, q, gas, mu, Pr):
+    """Navier-Stokes right-hand side [5][K][Np] of a perfect gas on a periodic box."""
+    from .ns import viscous_flux
+    N = ref.N
+    q = np.asarray(q, dtype=np.float64)
+    T = gas.temperature(q)
+    w = np.stack([q[0], q[1], q[2], q[3], T])
+    grad = hex_gradient(ref, box, w)
+    Fv = viscous_flux(q, T, grad, mu, mu * gas.cp / Pr)  # [3][5][K][Np]
+    q5 = _shape(q, N)
+    Fv5 = Fv.reshape((3, 5) + q5.shape[1:])
+    Fe = _volume_fluxes(q5, gas)
+    rhs = np.zeros_like(q5)
+    for d in range(3):
+        rhs -= (2.0 / box["h"][d]) * _along(ref.D, Fe[d] - Fv5[d], d)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+        rhs[sel] += lift * (fm - fstar)
+    # central viscous flux: the face term gains -n.(Fv- - Fv+)/2
+    for d in range(3):
+        for end in (0, 1):
+            nd = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, d, -1 if end == 0 else 1)
+            sel = _face_slices(N, d, end)
+            fvm = Fv5[d][sel]
+            fvp = Fv5[d][:, nb][_face_slices(N, d, 1 - end)]
+            lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
+            rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
+    return rhs.reshape(q.shape)
 
 
 def hex_integrate(ref, box, u):
