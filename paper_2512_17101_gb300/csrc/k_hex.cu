@@ -1,6 +1,6 @@
 // Nodal DG on tensor-product hexahedra (the element type of the paper's timed runs, Sec. 5.2-5.4):
-// Euler equations of a perfect gas, and scalar advection, on a periodic box of axis-aligned
-// hexahedra, FP64, fused with the low-storage RK4 stage like the tetrahedral path.
+// Euler and Navier-Stokes (BR1) equations of a perfect gas, and scalar advection, on a box of
+// axis-aligned hexahedra, FP64, fused with the low-storage RK4 stage like the tetrahedral path.
 //
 // Discretisation (collocated nodal spectral-element DG): tensor-product nodes from a 1-D node
 // set x_0 = -1 < ... < x_N = 1 (Gauss-Lobatto-Legendre in the workloads), quadrature weights
@@ -34,6 +34,7 @@ struct dg_hex_mesh_s {
   int64_t K = 0;
   std::vector<double> nodes, w, D;  // host copies
   double* D_dev = nullptr;          // [M][M]
+  double* fv_dev = nullptr;         // Navier-Stokes viscous flux [9][K][Np] (on first use)
   unsigned* status = nullptr;
 };
 
@@ -101,13 +102,20 @@ __device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* 
   }
 }
 
-template <int N, bool RK>
+// Viscous flux storage of the Navier-Stokes form: [9][K][Np] = tau_xx, tau_yy, tau_zz, tau_xy,
+// tau_xz, tau_yz, E_x, E_y, E_z (E_d = sum_i u_i tau_id + kappa dT/dx_d).
+__host__ __device__ constexpr int hex_tau(int i, int d) { return i == d ? i : (i + d == 1 ? 3 : (i + d == 2 ? 4 : 5)); }
+
+// VISC: Navier-Stokes; fv holds the viscous flux of every node (hex_vis_kernel), subtracted from
+// the volume fluxes and from the face traces' normal fluxes (central viscous flux).
+template <int N, bool RK, bool VISC>
 __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                                  double* __restrict__ kreg,
                                                                  const double* __restrict__ D_g, const HexGeo geo,
                                                                  const int64_t K, const double gamma, const double a,
                                                                  const double b, const int accumulate,
-                                                                 unsigned* __restrict__ status) {
+                                                                 unsigned* __restrict__ status,
+                                                                 const double* __restrict__ fv) {
   using C = HexCfg<N>;
   constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
   __shared__ double sD[3][M * M];     // -(2/h_d) s D per axis
@@ -144,6 +152,11 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       sF[d][3][tid] = qv[3] * ud;
       sF[d][1 + d][tid] += p;
       sF[d][4][tid] = ud * (qv[4] + p);
+      if (VISC) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sF[d][1 + i][tid] -= fv[hex_tau(i, d) * KNp + base + tid];
+        sF[d][4][tid] -= fv[(6 + d) * KNp + base + tid];
+      }
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) sS[v][tid] = 0.0;
@@ -202,7 +215,16 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       fp[1 + d] += pp;
       fm[4] = um * (qm[4] + pm);
       fp[4] = up * (qp[4] + pp);
-      // n.F- - n.F* = (sgn (F_d- - F_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end (times s)
+      if (VISC) {  // G_d = F_d - Fv_d on both traces: the central viscous flux (periodic boxes)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          fm[1 + i] -= fv[hex_tau(i, d) * KNp + gM];
+          fp[1 + i] -= fv[hex_tau(i, d) * KNp + gP];
+        }
+        fm[4] -= fv[(6 + d) * KNp + gM];
+        fp[4] -= fv[(6 + d) * KNp + gP];
+      }
+      // n.G- - n.G* = (sgn (G_d- - G_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end (times s)
       const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
       const double sgnlf = end ? lf : -lf;
 #pragma unroll
@@ -242,6 +264,114 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       out[gi] = acc[v];
     }
   }
+}
+
+// BR1 gradient pass of the Navier-Stokes form (periodic boxes): w = (rho, rho u, rho v, rho w, T),
+//   grad_d w = (2/h_d) D_d w + (at a node of a d-face) (2/h_d)/w_end n_d (w+ - w-)/2,
+// then the viscous flux per node (Stokes hypothesis, kappa = mu cp / Pr) into fv [9][K][Np].
+// geo carries the unscaled coefficients: dsc[d] = -(2/h_d), lf[d][end] = (2/h_d)/w_end / 2.
+template <int N>
+__global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __restrict__ q, double* __restrict__ fv,
+                                                                 const double* __restrict__ D_g, const HexGeo geo,
+                                                                 const int64_t K, const double gamma, const double R,
+                                                                 const double mu, const double kappa) {
+  using C = HexCfg<N>;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
+  __shared__ double sD[3][M * M];     // (2/h_d) D per axis
+  __shared__ double sW[5][NODES];     // w of the block's nodes
+  __shared__ double sJ[3][5][NODES];  // lifted jump terms per axis
+  __shared__ int sNb[EPB][6];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int i = tid; i < M * M; i += NT) sD[d][i] = -geo.dsc[d] * D_g[i];
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+  const double gm1 = gamma - 1.0, iR = 1.0 / R;
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid]);
+  if (tid < nn) {
+    double qv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
+    const double ir = rcp_nr(qv[0]);
+    const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sW[v][tid] = qv[v];
+    sW[4][tid] = p * ir * iR;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sJ[d][v][tid] = 0.0;
+  }
+  __syncthreads();
+  constexpr int FPA = 2 * M * M;
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int s1 = stride[(d + 1) % 3], s2 = stride[(d + 2) % 3];
+    for (int w = tid; w < nel * FPA; w += NT) {
+      const int el = w / FPA, rem = w - el * FPA, end = rem / (M * M), ab = rem - end * M * M;
+      const int node = (end ? N : 0) * stride[d] + (ab % M) * s1 + (ab / M) * s2;
+      const int loc = el * Np + node;
+      const int nnode = node + (end ? -N : N) * stride[d];
+      const size_t gP = (size_t)sNb[el][2 * d + end] * Np + nnode;
+      double qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
+      const double irp = rcp_nr(qp[0]);
+      const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+      const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
+      const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
+      const double sgnlf = end ? lf : -lf;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sJ[d][v][loc] = sgnlf * (wp[v] - sW[v][loc]);
+    }
+  }
+  __syncthreads();
+  if (tid >= nn) return;
+  const int el = tid / Np, node = tid - el * Np;
+  const int idx[3] = {node % M, (node / M) % M, node / (M * M)};
+  double g[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int line0 = el * Np + node - idx[d] * stride[d];
+    const double* Drow = sD[d] + idx[d] * M;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = sJ[d][v][tid];
+#pragma unroll
+      for (int l = 0; l < M; ++l) acc = fma(Drow[l], sW[v][line0 + l * stride[d]], acc);
+      g[d][v] = acc;
+    }
+  }
+  const double rho = sW[0][tid], ir = rcp_nr(rho);
+  const double u[3] = {sW[1][tid] * ir, sW[2][tid] * ir, sW[3][tid] * ir};
+  double du[3][3];  // du[i][d] = d u_i / d x_d
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) du[i][d] = (g[d][1 + i] - u[i] * g[d][0]) * ir;
+  const double divu = du[0][0] + du[1][1] + du[2][2];
+  double tau[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tau[i][j] = mu * (du[i][j] + du[j][i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tau[i][i] -= (2.0 / 3.0) * mu * divu;
+  const size_t gi = base + tid;
+  fv[0 * KNp + gi] = tau[0][0];
+  fv[1 * KNp + gi] = tau[1][1];
+  fv[2 * KNp + gi] = tau[2][2];
+  fv[3 * KNp + gi] = tau[0][1];
+  fv[4 * KNp + gi] = tau[0][2];
+  fv[5 * KNp + gi] = tau[1][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    fv[(6 + d) * KNp + gi] = fma(u[0], tau[0][d], fma(u[1], tau[1][d], fma(u[2], tau[2][d], kappa * g[d][4])));
 }
 
 // Scalar advection du/dt + a . grad u = 0 (the paper's GPU comparison workload, Sec. 5.2): F_d = a_d u
@@ -364,11 +494,8 @@ cudaError_t launch_adv(const dg_hex_mesh_s& m, const double* vel, const double* 
   }
 }
 
-template <int N, bool RK>
-cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a, double b,
-                     double dt, cudaStream_t s) {
-  using C = HexCfg<N>;
-  const double sc = RK ? dt : 1.0;
+template <int N>
+HexGeo make_geo(const dg_hex_mesh_s& m, double sc) {
   HexGeo geo;
   for (int f = 0; f < 6; ++f) geo.bc[f] = m.bc[f];
   for (int v = 0; v < 5; ++v) geo.q_in[v] = m.q_in[v];
@@ -379,18 +506,48 @@ cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, doub
     geo.lf[d][0] = 0.5 * two_h / m.w[0] * sc;
     geo.lf[d][1] = 0.5 * two_h / m.w[N] * sc;
   }
+  return geo;
+}
+
+template <int N>
+cudaError_t launch_vis_t(const dg_hex_mesh_s& m, const GasParams& g, const double* q, cudaStream_t s) {
+  using C = HexCfg<N>;
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
-  hex_rhs_kernel<N, RK><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b, a != 0.0,
-                                                           m.status);
+  hex_vis_kernel<N><<<(unsigned)blocks, C::NT, 0, s>>>(q, m.fv_dev, m.D_dev, make_geo<N>(m, 1.0), m.K, g.gamma, g.R,
+                                                       g.mu, g.kappa);
   return cudaGetLastError();
 }
 
-cudaError_t launch(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, bool rk, double a,
-                   double b, double dt, cudaStream_t s) {
+template <int N, bool RK, bool VISC>
+cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a, double b,
+                     double dt, cudaStream_t s) {
+  using C = HexCfg<N>;
+  const HexGeo geo = make_geo<N>(m, RK ? dt : 1.0);
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_rhs_kernel<N, RK, VISC><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b,
+                                                                 a != 0.0, m.status, m.fv_dev);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_n(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                     double a, double b, double dt, cudaStream_t s) {
+  if (g.mu > 0) {
+    const cudaError_t e = launch_vis_t<N>(m, g, q, s);
+    if (e != cudaSuccess) return e;
+    return rk ? launch_t<N, true, true>(m, g.gamma, q, out, k, a, b, dt, s)
+              : launch_t<N, false, true>(m, g.gamma, q, out, k, a, b, dt, s);
+  }
+  return rk ? launch_t<N, true, false>(m, g.gamma, q, out, k, a, b, dt, s)
+            : launch_t<N, false, false>(m, g.gamma, q, out, k, a, b, dt, s);
+}
+
+cudaError_t launch(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                   double a, double b, double dt, cudaStream_t s) {
   switch (m.N) {
 #define DG_CASE(NN) \
   case NN:          \
-    return rk ? launch_t<NN, true>(m, gamma, q, out, k, a, b, dt, s) : launch_t<NN, false>(m, gamma, q, out, k, a, b, dt, s);
+    return launch_n<NN>(m, g, q, out, k, rk, a, b, dt, s);
     DG_CASE(1)
     DG_CASE(2)
     DG_CASE(3)
@@ -528,6 +685,7 @@ int dg_hex_mesh_create(const dg_hex_desc* d, dg_hex_mesh* out) {
 int dg_hex_mesh_free(dg_hex_mesh m) {
   if (!m) return DG_OK;
   cudaFree(m->D_dev);
+  cudaFree(m->fv_dev);
   cudaFree(m->status);
   delete m;
   return DG_OK;
@@ -547,15 +705,23 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
   if (rk && !k) return dg::fail(DG_ERR_INVALID_ARG, "NULL RK register k");
   if (rk && (stage < 0 || stage > 4)) return dg::fail(DG_ERR_INVALID_ARG, "stage must be in 0..4");
   if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
-  if (gas->p.model != DG_GAS_PERFECT || gas->p.mu > 0)
-    return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path solves the Euler equations of a perfect gas");
+  if (gas->p.model != DG_GAS_PERFECT)
+    return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path takes a perfect gas");
+  if (gas->p.mu > 0) {
+    for (int f = 0; f < 6; ++f)
+      if (m->bc[f]) return dg::fail(DG_ERR_UNSUPPORTED, "Navier-Stokes on hexahedra runs on periodic boxes");
+    if (!m->fv_dev) {
+      const cudaError_t e = cudaMalloc((void**)&m->fv_dev, sizeof(double) * 9 * (size_t)m->K * m->Np);
+      if (e != cudaSuccess) return dg::cuda_fail(e, "hexahedral viscous-flux buffer");
+    }
+  }
   const size_t n = (size_t)5 * m->K * m->Np;
   if (q == out || (q < out + n && out < q + n)) return dg::fail(DG_ERR_INVALID_ARG, "output overlaps the input state");
   for (int f = 0; f < 6; ++f)
     if (m->bc[f] == DG_BC_INFLOW && !m->has_inflow)
       return dg::fail(DG_ERR_INVALID_ARG, "the box has an inflow face: set its state with dg_hex_set_inflow");
   const double a = rk ? dg::kRK4A[stage] : 0.0, b = rk ? dg::kRK4B[stage] : 0.0;
-  const cudaError_t e = dg::hexk::launch(*m, gas->p.gamma, q, out, k, rk, a, b, dt, (cudaStream_t)stream);
+  const cudaError_t e = dg::hexk::launch(*m, gas->p, q, out, k, rk, a, b, dt, (cudaStream_t)stream);
   return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral right-hand-side kernel");
 }
 

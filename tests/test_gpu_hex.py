@@ -64,9 +64,9 @@ def test_hex_rejects_what_it_does_not_solve():
     from paper_2512_17101_gb300 import capi
     q = torch.tensor(q0, device="cuda")
     rhs = torch.empty_like(q)
-    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=1e-3, Pr=0.71)
-    with pytest.raises(capi.DGError):
-        dg.dg_hex_rhs(mesh, ns, q, rhs)
+    mix = dg.Gas(model="nasa7", W=np.array([28.0]), nasa7=np.array([[3.5, 0, 0, 0, 0, 0, 0]]))
+    with pytest.raises(capi.DGError):  # a perfect gas only
+        dg.dg_hex_rhs(mesh, mix, q, rhs)
     with pytest.raises(capi.DGError):
         dg.dg_hex_rhs(mesh, gas, q, q)
     with pytest.raises(capi.DGError):
@@ -244,3 +244,44 @@ def test_hex_boundary_arguments():
     u = torch.zeros(m.K * m.Np, dtype=torch.float64, device="cuda")
     with pytest.raises(capi.DGError):  # the advection runs on periodic boxes
         dg.dg_hex_advection_rhs(m, (1.0, 0.0, 0.0), u, torch.empty_like(u))
+
+
+# --- Navier-Stokes on periodic boxes ---------------------------------------------------------------
+
+NS_MU, NS_PR = 2e-2, 0.71
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, (3, 2, 2)])
+def test_hex_navier_stokes_rhs(n, N):
+    torch, dg, box, ref, q0, mesh, gas = _setup(n, N)
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, ns, q, rhs)
+    want = hx.hex_rhs_ns(ref, box, q0, GAS, NS_MU, NS_PR)
+    got = rhs.cpu().numpy()
+    assert rel_err(got, want) <= TOL
+    euler = hx.hex_rhs_strong(ref, box, q0, GAS)
+    assert rel_err(got - euler, want - euler) <= 1e-9  # the viscous part on its own
+    assert mesh.status() == 0
+
+
+def test_hex_navier_stokes_two_rk4_steps():
+    torch, dg, box, ref, q0, mesh, gas = _setup((4, 3, 2), 3)
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    dt = 1e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.hex_lsrk4_step(mesh, ns, q, dt, steps=2)
+    f = lambda u: hx.hex_rhs_ns(ref, box, u, GAS, NS_MU, NS_PR)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+
+
+def test_hex_navier_stokes_needs_a_periodic_box():
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((3, 2, 2), 2, HEX_BC["channel"])
+    from paper_2512_17101_gb300 import capi
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
