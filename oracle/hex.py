@@ -17,7 +17,7 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
   with the local Lax-Friedrichs flux n.F* = (n.F(q-) + n.F(q+))/2 + lambda (q- - q+)/2,
   lambda = max(|u-.n| + c-, |u+.n| + c+) at the face node; q+ is the neighbour's node at the
   same position on the shared face (periodic box).
-* Navier-Stokes (periodic boxes): BR1 with central fluxes in both passes, as on tetrahedra
+* Navier-Stokes: BR1 with central fluxes in both passes, as on tetrahedra
   (oracle/ns.py): grad_d w = (2/h_d) D_d w plus, at the face nodes of the two d-faces,
   (2/h_d)/w_end n_d (w+ - w-)/2, for w = (rho, rho u, rho v, rho w, T); the viscous flux
   (tau, u.tau + kappa grad T) enters G = F - Fv, and the face term gains -n.(Fv- - Fv+)/2;
@@ -240,11 +240,18 @@ def hex_advection_rhs_weak(ref, box, u, a):
     return rhs.reshape(np.shape(u))
 
 
-def hex_gradient(ref, box, w):
-    """BR1 gradient grad[3][F][K][Np] of w[F][K][Np] on a periodic box (central flux)."""
+def _w_of(q, gas):
+    return np.stack([q[0], q[1], q[2], q[3], gas.temperature(q)])
+
+
+def hex_gradient(ref, box, w, q=None, gas=None, q_in=None):
+    """BR1 gradient grad[3][F][K][Np] of w[F][K][Np] (central flux).  On a box with boundary faces
+    (box["bc"]) the exterior values at a boundary face are w(q+) of the ghost state, which needs
+    the state q and the gas."""
     N = ref.N
     F = w.shape[0]
     w5 = w.reshape(F, w.shape[1], N + 1, N + 1, N + 1)
+    q5 = None if q is None else _shape(np.asarray(q, dtype=np.float64), N)
     out = np.zeros((3,) + w5.shape)
     for d in range(3):
         out[d] = (2.0 / box["h"][d]) * _along(ref.D, w5, d)
@@ -254,19 +261,27 @@ def hex_gradient(ref, box, w):
             sel = _face_slices(N, d, end)
             wm = w5[sel]
             wp = w5[:, nb][_face_slices(N, d, 1 - end)]
+            if box.get("bc", ((0, 0), (0, 0), (0, 0)))[d][end]:
+                qm = q5[sel]
+                qp = _exterior(box, d, end, qm, q5[:, nb][_face_slices(N, d, 1 - end)], q_in)
+                wp = np.where(_boundary_elements(box, d, end).reshape((1, -1, 1, 1)), _w_of(qp, gas), wp)
             lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
             out[d][sel] += lift * nd * 0.5 * (wp - wm)
     return out.reshape((3,) + w.shape)
 
 
-def hex_rhs_ns(ref, box, q, gas, mu, Pr):
-    """Navier-Stokes right-hand side [5][K][Np] of a perfect gas on a periodic box."""
+def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
+    """Navier-Stokes right-hand side [5][K][Np] of a perfect gas.  At boundary faces the exterior
+    viscous flux follows the tetrahedral reading (oracle/boundary.py): walls adiabatic
+    (E_d+ = -E_d-), a slip wall shear-free (tau_id+ = -tau_id- for i != d, tau_dd+ = tau_dd-),
+    inflow and outflow the interior flux."""
+    from .boundary import NOSLIP_WALL, SLIP_WALL
     from .ns import viscous_flux
     N = ref.N
     q = np.asarray(q, dtype=np.float64)
     T = gas.temperature(q)
     w = np.stack([q[0], q[1], q[2], q[3], T])
-    grad = hex_gradient(ref, box, w)
+    grad = hex_gradient(ref, box, w, q, gas, q_in)
     Fv = viscous_flux(q, T, grad, mu, mu * gas.cp / Pr)  # [3][5][K][Np]
     q5 = _shape(q, N)
     Fv5 = Fv.reshape((3, 5) + q5.shape[1:])
@@ -274,7 +289,7 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr):
     rhs = np.zeros_like(q5)
     for d in range(3):
         rhs -= (2.0 / box["h"][d]) * _along(ref.D, Fe[d] - Fv5[d], d)
-    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas):
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
         rhs[sel] += lift * (fm - fstar)
     # central viscous flux: the face term gains -n.(Fv- - Fv+)/2
     for d in range(3):
@@ -284,6 +299,17 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr):
             sel = _face_slices(N, d, end)
             fvm = Fv5[d][sel]
             fvp = Fv5[d][:, nb][_face_slices(N, d, 1 - end)]
+            code = box.get("bc", ((0, 0), (0, 0), (0, 0)))[d][end]
+            if code:
+                ghost = fvm.copy()
+                if code in (SLIP_WALL, NOSLIP_WALL):
+                    ghost[4] = -fvm[4]
+                if code == SLIP_WALL:
+                    for i in range(3):
+                        if i != d:
+                            ghost[1 + i] = -fvm[1 + i]
+                on = _boundary_elements(box, d, end).reshape((1, -1, 1, 1))
+                fvp = np.where(on, ghost, fvp)
             lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
             rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
     return rhs.reshape(q.shape)

@@ -113,11 +113,85 @@ def test_conservation_other_orders(N):
     assert _conserves(N) and _rest_is_steady(N)
 
 
+# --- walls -----------------------------------------------------------------------------------------
+
+import oracle.boundary as bd  # noqa: E402
+
+
+def _ns_mirror_matches(code, N=3):
+    """Navier-Stokes walls at y = 0 and y = 1 against the doubled periodic box holding the folded
+    state: the slip wall (shear-free, adiabatic) is the even image, the no-slip wall's inviscid and
+    gradient ghosts are the odd image; for the no-slip wall the viscous ghost differs from the odd
+    image, so only the slip wall is compared in full."""
+    box = hex_box((2, 2, 2), 1.0)
+    box["bc"] = ((0, 0), (code, code), (0, 0))
+    x = gll_nodes(N)
+    ref = hx.hex_reference(x)
+    xyz = hex_nodes(box, x)
+    big = hex_box((2, 4, 2), (1.0, 2.0, 1.0))
+    xyz2 = hex_nodes(big, x)
+    e = np.arange(16)
+    lower = ((e // 2) % 4) < 2
+
+    def folded(pts, upper):
+        xx, y, z = pts[..., 0], pts[..., 1], pts[..., 2]
+        yf = np.where(upper[:, None], 2.0 - y, y)
+        s = np.where(upper[:, None], -1.0, 1.0)
+        rho = 1.0 + 0.1 * np.sin(2 * np.pi * xx) * np.cos(1.3 * yf + 0.2)
+        u = 0.2 * np.cos(2 * np.pi * z) + 0.1 * yf
+        v = 0.15 * np.sin(np.pi * yf) * np.cos(2 * np.pi * xx)
+        w = 0.1 * np.sin(2 * np.pi * xx + 0.3)
+        p = 0.7 + 0.05 * np.cos(2 * np.pi * z) * np.sin(0.9 * yf)
+        return _state(rho, u, s * v, w, p)
+
+    r_wall = hx.hex_rhs_ns(ref, box, folded(xyz, np.zeros(8, dtype=bool)), GAS, MU, PR)
+    r_big = hx.hex_rhs_ns(ref, big, folded(xyz2, ~lower), GAS, MU, PR)
+    return np.abs(r_wall - r_big[:, lower]).max() <= 1e-11 * np.abs(r_big).max()
+
+
+def _noslip_box_conserves(N=3):
+    box = hex_box((2, 2, 2), 1.0)
+    box["bc"] = ((bd.NOSLIP_WALL,) * 2, (bd.NOSLIP_WALL,) * 2, (bd.SLIP_WALL,) * 2)
+    x = gll_nodes(N)
+    ref = hx.hex_reference(x)
+    xyz = hex_nodes(box, x)
+    q = uniform_perturbation(isentropic_vortex(xyz, 0.0, center=(0.45, 0.55), radius=0.15), 1e-2)
+    r = hx.hex_rhs_ns(ref, box, q, GAS, MU, PR)
+    tot, scale = hx.hex_integrate(ref, box, r), hx.hex_integrate(ref, box, np.abs(r))
+    return abs(tot[0]) <= 1e-12 * scale[0] and abs(tot[4]) <= 1e-12 * scale[4]
+
+
+def test_slip_wall_is_the_mirror_image_with_viscosity():
+    assert _ns_mirror_matches(bd.SLIP_WALL)
+
+
+def test_walled_box_conserves_mass_and_energy():
+    """Adiabatic no-slip and slip walls: no mass and no energy (heat or work) cross them."""
+    assert _noslip_box_conserves()
+
+
+def test_planted_heat_leak_at_walls_fails(monkeypatch):
+    orig = hx.hex_rhs_ns
+
+    def leaky(ref, box, q, gas, mu, Pr, q_in=None):  # walls that pass the interior energy flux
+        bc = box["bc"]
+        box2 = dict(box)
+        box2["bc"] = tuple(tuple(bd.OUTFLOW if c in (bd.SLIP_WALL, bd.NOSLIP_WALL) else c for c in ax) for ax in bc)
+        # inviscid and gradient ghosts of the walls kept, viscous exterior flux = interior one:
+        # the difference of the two right-hand sides is the walls' viscous correction
+        r_out = orig(ref, box2, q, gas, mu, Pr, q_in)
+        r_out_inv = orig(ref, box2, q, gas, 0.0, Pr, q_in)
+        r_wall_inv = orig(ref, box, q, gas, 0.0, Pr, q_in)
+        return r_wall_inv + (r_out - r_out_inv)
+    monkeypatch.setattr(hx, "hex_rhs_ns", leaky)
+    assert not _noslip_box_conserves()
+
+
 def test_planted_full_jump_fails(monkeypatch):
     orig = hx.hex_gradient
 
-    def bad(ref, box, w):  # jump (w+ - w-) instead of half of it
-        g = orig(ref, box, w)
+    def bad(ref, box, w, *rest):  # jump (w+ - w-) instead of half of it
+        g = orig(ref, box, w, *rest)
         N = ref.N
         vol = np.stack([(2.0 / box["h"][d]) * hx._along(ref.D, w.reshape(w.shape[0], w.shape[1], N + 1, N + 1, N + 1),
                                                         d).reshape(w.shape) for d in range(3)])
