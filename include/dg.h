@@ -405,8 +405,8 @@ int dg_batch_free(dg_batch batch);
 
 /* ---- tensor-product hexahedra ---------------------------------------------------------------
  * Nodal DG on a periodic box of axis-aligned hexahedra with tensor-product nodes, the element
- * type of the paper's timed runs (Sec. 5.2-5.4, "tensor product elements"); Euler and (periodic
- * boxes) Navier-Stokes equations of a perfect gas in FP64, the same local Lax-Friedrichs flux,
+ * type of the paper's timed runs (Sec. 5.2-5.4, "tensor product elements"); Euler and
+ * Navier-Stokes equations of a perfect gas in FP64, the same local Lax-Friedrichs flux,
  * BR1 central fluxes and fused LSRK4 stage as the tetrahedral path.  Collocated nodal spectral-element DG: quadrature weights w_i = integral of the
  * 1-D Lagrange basis through the node set, D[i][j] = l_j'(x_i), diagonal mass,
  *   rhs = - sum_d (2/h_d) D_d F_d + sum over the faces of a node (2/h_d) / w_end (n.F- - n.F*),
@@ -432,9 +432,9 @@ int dg_hex_mesh_free(dg_hex_mesh mesh);
  * (either may be NULL). */
 int dg_hex_operators(dg_hex_mesh mesh, double* D_host, double* w_host);
 /* rhs = right-hand side of q (device arrays [5][K][Np], caller-owned, not overlapping); the gas
- * must be a perfect gas (else DG_ERR_UNSUPPORTED); with mu > 0 (Navier-Stokes) the box must be
- * periodic, and the first such call allocates 9 doubles per node for the viscous flux.
- * Asynchronous on stream. */
+ * must be a perfect gas (else DG_ERR_UNSUPPORTED); with mu > 0 (Navier-Stokes) the first such
+ * call allocates 9 doubles per node for the viscous flux; walls are adiabatic and a slip wall
+ * shear-free, as on tetrahedra.  Asynchronous on stream. */
 int dg_hex_rhs(dg_hex_mesh mesh, dg_gas gas, const double* q_dev, double* rhs_dev, void* stream);
 /* LSRK4 stage (as dg_rk_stage): k <- a_s k + dt rhs(q_in); q_out <- q_in + b_s k. */
 int dg_hex_rk_stage(dg_hex_mesh mesh, dg_gas gas, int32_t stage, double dt, const double* q_in_dev,

@@ -106,6 +106,22 @@ __device__ __forceinline__ void hex_neighbours(unsigned e, const int n[3], int* 
 // tau_xz, tau_yz, E_x, E_y, E_z (E_d = sum_i u_i tau_id + kappa dT/dx_d).
 __host__ __device__ constexpr int hex_tau(int i, int d) { return i == d ? i : (i + d == 1 ? 3 : (i + d == 2 ? 4 : 5)); }
 
+// Ghost state of a box-face node (n = -e_d or +e_d; q holds the node's own state on entry): slip
+// wall (normal momentum mirrored), no-slip wall (momentum reversed), inflow (the prescribed state),
+// outflow (the node's own).
+__device__ __forceinline__ void hex_ghost(int code, int d, const HexGeo& geo, double* q) {
+  if (code == DG_BC_SLIP_WALL) {
+    q[1 + d] = -q[1 + d];
+  } else if (code == DG_BC_NOSLIP_WALL) {
+    q[1] = -q[1];
+    q[2] = -q[2];
+    q[3] = -q[3];
+  } else if (code == DG_BC_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = geo.q_in[v];
+  }
+}
+
 // VISC: Navier-Stokes; fv holds the viscous flux of every node (hex_vis_kernel), subtracted from
 // the volume fluxes and from the face traces' normal fluxes (central viscous flux).
 template <int N, bool RK, bool VISC>
@@ -184,18 +200,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
         qm[v] = q[v * KNp + gM];
         qp[v] = q[v * KNp + gP];
       }
-      if (enb < 0) {  // ghost state (n = -e_d or +e_d): mirrored or reversed momentum, inflow, outflow
-        if (-enb == DG_BC_SLIP_WALL) {
-          qp[1 + d] = -qp[1 + d];
-        } else if (-enb == DG_BC_NOSLIP_WALL) {
-          qp[1] = -qp[1];
-          qp[2] = -qp[2];
-          qp[3] = -qp[3];
-        } else if (-enb == DG_BC_INFLOW) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) qp[v] = geo.q_in[v];
-        }
-      }
+      if (enb < 0) hex_ghost(-enb, d, geo, qp);
       const double irm = sPC[0][loc], pm = sPC[1][loc], cm = sPC[2][loc];
       double irp, pp, cp;
       pc(gamma, qp, irp, pp, cp);
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
       fp[1 + d] += pp;
       fm[4] = um * (qm[4] + pm);
       fp[4] = up * (qp[4] + pp);
-      if (VISC) {  // G_d = F_d - Fv_d on both traces: the central viscous flux (periodic boxes)
+      if (VISC) {  // G_d = F_d - Fv_d on both traces: the central viscous flux
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           fm[1 + i] -= fv[hex_tau(i, d) * KNp + gM];
@@ -223,6 +228,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
         }
         fm[4] -= fv[(6 + d) * KNp + gM];
         fp[4] -= fv[(6 + d) * KNp + gP];
+        // at a box boundary gP is the node itself: walls are adiabatic (E_d+ = -E_d-) and a slip
+        // wall is shear-free (tau_id+ = -tau_id- for i != d)
+        if (enb == -DG_BC_SLIP_WALL || enb == -DG_BC_NOSLIP_WALL) {
+          fp[4] += 2.0 * fv[(6 + d) * KNp + gM];
+          if (enb == -DG_BC_SLIP_WALL)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              if (i != d) fp[1 + i] += 2.0 * fv[hex_tau(i, d) * KNp + gM];
+        }
       }
       // n.G- - n.G* = (sgn (G_d- - G_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end (times s)
       const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
@@ -266,7 +280,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   }
 }
 
-// BR1 gradient pass of the Navier-Stokes form (periodic boxes): w = (rho, rho u, rho v, rho w, T),
+// BR1 gradient pass of the Navier-Stokes form: w = (rho, rho u, rho v, rho w, T), exterior values
+// w(q+) of the ghost state at box-boundary faces,
 //   grad_d w = (2/h_d) D_d w + (at a node of a d-face) (2/h_d)/w_end n_d (w+ - w-)/2,
 // then the viscous flux per node (Stokes hypothesis, kappa = mu cp / Pr) into fv [9][K][Np].
 // geo carries the unscaled coefficients: dsc[d] = -(2/h_d), lf[d][end] = (2/h_d)/w_end / 2.
@@ -291,7 +306,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
   const double gm1 = gamma - 1.0, iR = 1.0 / R;
-  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid]);
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid], geo.bc);
   if (tid < nn) {
     double qv[5];
 #pragma unroll
@@ -317,10 +332,12 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
       const int node = (end ? N : 0) * stride[d] + (ab % M) * s1 + (ab / M) * s2;
       const int loc = el * Np + node;
       const int nnode = node + (end ? -N : N) * stride[d];
-      const size_t gP = (size_t)sNb[el][2 * d + end] * Np + nnode;
+      const int enb = sNb[el][2 * d + end];  // < 0: box boundary, -DG_BC_* code
+      const size_t gP = enb >= 0 ? (size_t)enb * Np + nnode : base + loc;
       double qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
+      if (enb < 0) hex_ghost(-enb, d, geo, qp);  // exterior values w(q+) of the ghost state
       const double irp = rcp_nr(qp[0]);
       const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
       const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
@@ -708,8 +725,6 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
   if (gas->p.model != DG_GAS_PERFECT)
     return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path takes a perfect gas");
   if (gas->p.mu > 0) {
-    for (int f = 0; f < 6; ++f)
-      if (m->bc[f]) return dg::fail(DG_ERR_UNSUPPORTED, "Navier-Stokes on hexahedra runs on periodic boxes");
     if (!m->fv_dev) {
       const cudaError_t e = cudaMalloc((void**)&m->fv_dev, sizeof(double) * 9 * (size_t)m->K * m->Np);
       if (e != cudaSuccess) return dg::cuda_fail(e, "hexahedral viscous-flux buffer");

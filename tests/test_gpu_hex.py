@@ -278,10 +278,16 @@ def test_hex_navier_stokes_two_rk4_steps():
     assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
 
 
-def test_hex_navier_stokes_needs_a_periodic_box():
-    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((3, 2, 2), 2, HEX_BC["channel"])
-    from paper_2512_17101_gb300 import capi
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("name", list(HEX_BC))
+def test_hex_navier_stokes_with_walls(name, N):
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((3, 2, 2), N, HEX_BC[name])
     ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
     q = torch.tensor(q0, device="cuda")
-    with pytest.raises(capi.DGError):
-        dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, ns, q, rhs)
+    want = hx.hex_rhs_ns(ref, box, q0, GAS, NS_MU, NS_PR, q_in=q_in)
+    got = rhs.cpu().numpy()
+    assert rel_err(got, want) <= TOL
+    euler = hx.hex_rhs_strong(ref, box, q0, GAS, q_in=q_in)
+    assert rel_err(got - euler, want - euler) <= 1e-9
