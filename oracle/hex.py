@@ -21,6 +21,12 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
   (oracle/ns.py): grad_d w = (2/h_d) D_d w plus, at the face nodes of the two d-faces,
   (2/h_d)/w_end n_d (w+ - w-)/2, for w = (rho, rho u, rho v, rho w, T); the viscous flux
   (tau, u.tau + kappa grad T) enters G = F - Fv, and the face term gains -n.(Fv- - Fv+)/2;
+* artificial viscosity (the reading of oracle/av.py on tensor-product elements): the indicator
+  of the density is the energy outside Q_{N-1} (the tensor-product Legendre modes with an index
+  equal to N) over the total energy, both in the GLL-weighted inner product, under which the
+  Legendre polynomials up to degree N are orthogonal; d q/dt += div(eps grad q) for every
+  conserved variable with BR1 central fluxes (exterior q+ of the ghost state at boundary faces,
+  exterior flux = interior flux there);
 * boundary conditions on box faces (box["bc"][axis][end], the codes of oracle/boundary.py): q+
   at a boundary face node is the ghost state of the condition, with n = -e_axis or +e_axis;
 * weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
@@ -313,6 +319,61 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
             lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
             rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
     return rhs.reshape(q.shape)
+
+
+def hex_indicator(ref, u):
+    """Smoothness indicator S_e of nodal values u[K][Np]: GLL-weighted energy of the Legendre modes
+    outside Q_{N-1} over the total."""
+    N = ref.N
+    L = np.stack([np.polynomial.legendre.Legendre.basis(a)(ref.nodes) for a in range(N + 1)])  # [a][i]
+    norm = (L ** 2) @ ref.w  # discrete norms
+    T = (L * ref.w[None, :]) / norm[:, None]  # nodal values -> Legendre coefficients
+    u5 = np.asarray(u, dtype=np.float64).reshape(-1, N + 1, N + 1, N + 1)  # [K][k][j][i]
+    c = np.einsum("ai,bj,ck,ekji->ecba", T, T, T, u5)  # [K][c][b][a]
+    e = c ** 2 * (norm[:, None, None] * norm[None, :, None] * norm[None, None, :])[None]  # [K][c][b][a]
+    a, b, cc = np.meshgrid(np.arange(N + 1), np.arange(N + 1), np.arange(N + 1), indexing="ij")  # [c][b][a]
+    top = np.maximum(np.maximum(a, b), cc) == N
+    return e[:, top].sum(axis=1) / e.reshape(e.shape[0], -1).sum(axis=1)
+
+
+def hex_gradient_state(ref, box, q, q_in=None):
+    """BR1 gradient [3][5][K][Np] of the conserved variables themselves (exterior values: the
+    ghost state q+ at boundary faces)."""
+    N = ref.N
+    q5 = _shape(np.asarray(q, dtype=np.float64), N)
+    out = np.zeros((3,) + q5.shape)
+    for d in range(3):
+        out[d] = (2.0 / box["h"][d]) * _along(ref.D, q5, d)
+        for end in (0, 1):
+            nd = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, d, -1 if end == 0 else 1)
+            sel = _face_slices(N, d, end)
+            qm = q5[sel]
+            qp = _exterior(box, d, end, qm, q5[:, nb][_face_slices(N, d, 1 - end)], q_in)
+            lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
+            out[d][sel] += lift * nd * 0.5 * (qp - qm)
+    return out.reshape((3,) + np.shape(q))
+
+
+def hex_rhs_av(ref, box, q, eps, q_in=None):
+    """div_h(eps grad_h q) [5][K][Np] for the per-element viscosity eps[K] (central fluxes)."""
+    N = ref.N
+    grad = hex_gradient_state(ref, box, q, q_in)
+    sig = (eps[None, None, :, None] * grad).reshape((3, 5, -1, N + 1, N + 1, N + 1))
+    out = np.zeros(sig.shape[1:])
+    for d in range(3):
+        out += (2.0 / box["h"][d]) * _along(ref.D, sig[d], d)
+        for end in (0, 1):
+            nd = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, d, -1 if end == 0 else 1)
+            sel = _face_slices(N, d, end)
+            sm = sig[d][sel]
+            sp = sig[d][:, nb][_face_slices(N, d, 1 - end)]
+            if box.get("bc", ((0, 0), (0, 0), (0, 0)))[d][end]:
+                sp = np.where(_boundary_elements(box, d, end).reshape((1, -1, 1, 1)), sm, sp)
+            lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
+            out[sel] += lift * nd * 0.5 * (sp - sm)
+    return out.reshape(np.shape(q))
 
 
 def hex_integrate(ref, box, u):
