@@ -455,6 +455,14 @@ int dg_hex_advection_rk_stage(dg_hex_mesh mesh, const double* velocity, int32_t 
  * non-finite, rho <= 0).  The advection entry points take periodic boxes only
  * (DG_ERR_UNSUPPORTED otherwise). */
 int dg_hex_set_inflow(dg_hex_mesh mesh, const double* q_in, int32_t nvar);
+/* Artificial viscosity on hexahedra (the reading of dg_mesh_set_av on tensor-product elements):
+ * the indicator is the GLL-weighted energy of the density's Legendre modes with an index equal to
+ * N over its total energy; the term div(eps grad q) is added with BR1 central fluxes.  params NULL
+ * or eps0 = 0 turns it off; the first call that turns it on allocates 15 doubles per node and one
+ * per element.  Errors as dg_mesh_set_av. */
+int dg_hex_set_av(dg_hex_mesh mesh, const dg_av_params* params);
+/* eps_dev [K] <- the element viscosities of q_dev [5][K][Np] under the mesh's parameters. */
+int dg_hex_av_viscosity(dg_hex_mesh mesh, const double* q_dev, double* eps_dev, void* stream);
 /* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
 int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);
 

@@ -35,6 +35,12 @@ struct dg_hex_mesh_s {
   std::vector<double> nodes, w, D;  // host copies
   double* D_dev = nullptr;          // [M][M]
   double* fv_dev = nullptr;         // Navier-Stokes viscous flux [9][K][Np] (on first use)
+  // artificial viscosity (dg_hex_set_av): parameters, element viscosity [K], flux [15][K][Np]
+  double av_eps0 = 0.0, av_s0 = 0.0, av_kappa = 1.0;
+  double* av_eps = nullptr;
+  double* av_sig = nullptr;
+  std::vector<double> modal;        // [M][M]: nodal values -> Legendre coefficients (GLL-weighted)
+  std::vector<double> modal_norm;   // [M]: discrete norms of the Legendre polynomials
   unsigned* status = nullptr;
 };
 
@@ -124,14 +130,18 @@ __device__ __forceinline__ void hex_ghost(int code, int d, const HexGeo& geo, do
 
 // VISC: Navier-Stokes; fv holds the viscous flux of every node (hex_vis_kernel), subtracted from
 // the volume fluxes and from the face traces' normal fluxes (central viscous flux).
-template <int N, bool RK, bool VISC>
+// AV: the artificial-viscosity flux sig [(5 d + v)][K][Np] (eps grad q_v, stored only for elements
+// with eps > 0) is subtracted like the viscous flux.
+template <int N, bool RK, bool VISC, bool AV>
 __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                                  double* __restrict__ kreg,
                                                                  const double* __restrict__ D_g, const HexGeo geo,
                                                                  const int64_t K, const double gamma, const double a,
                                                                  const double b, const int accumulate,
                                                                  unsigned* __restrict__ status,
-                                                                 const double* __restrict__ fv) {
+                                                                 const double* __restrict__ fv,
+                                                                 const double* __restrict__ sig,
+                                                                 const double* __restrict__ eps) {
   using C = HexCfg<N>;
   constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
   __shared__ double sD[3][M * M];     // -(2/h_d) s D per axis
@@ -172,6 +182,10 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
 #pragma unroll
         for (int i = 0; i < 3; ++i) sF[d][1 + i][tid] -= fv[hex_tau(i, d) * KNp + base + tid];
         sF[d][4][tid] -= fv[(6 + d) * KNp + base + tid];
+      }
+      if (AV && eps[e0 + tid / Np] > 0.0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sF[d][v][tid] -= sig[(5 * d + v) * KNp + base + tid];
       }
     }
 #pragma unroll
@@ -236,6 +250,14 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
 #pragma unroll
             for (int i = 0; i < 3; ++i)
               if (i != d) fp[1 + i] += 2.0 * fv[hex_tau(i, d) * KNp + gM];
+        }
+      }
+      if (AV) {  // central artificial-viscosity flux; at a box boundary the exterior flux is the interior one
+        const bool onM = eps[e0 + el] > 0.0, onP = enb >= 0 ? eps[enb] > 0.0 : onM;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (onM) fm[v] -= sig[(5 * d + v) * KNp + gM];
+          if (onP) fp[v] -= sig[(5 * d + v) * KNp + gP];
         }
       }
       // n.G- - n.G* = (sgn (G_d- - G_d+) - lam (q- - q+)) / 2, lifted by (2/h_d) / w_end (times s)
@@ -391,6 +413,147 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
     fv[(6 + d) * KNp + gi] = fma(u[0], tau[0][d], fma(u[1], tau[1][d], fma(u[2], tau[2][d], kappa * g[d][4])));
 }
 
+// Artificial viscosity on hexahedra (the reading of the tetrahedral path on tensor-product
+// elements).  Indicator of the density per element: the GLL-weighted energy of its Legendre
+// modes with an index equal to N over its total energy; the transform to the coefficients is the
+// 1-D matrix T[a][i] = w_i L_a(x_i) / |L_a|^2 along each axis (sum factorisation).
+struct HexAv {
+  double T[25];    // [M][M], row a
+  double nrm[5];   // |L_a|^2 in the GLL-weighted inner product
+  double eps0, s0, kappa;
+};
+
+template <int N>
+__global__ void __launch_bounds__(HexCfg<N>::NT) hex_av_sensor_kernel(const double* __restrict__ q,
+                                                                       const HexAv av, const int64_t K,
+                                                                       double* __restrict__ eps) {
+  using C = HexCfg<N>;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES;
+  __shared__ double sA[NODES], sB[NODES];
+  const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t base = (size_t)e0 * Np;
+  if (tid < nn) sA[tid] = q[base + tid];  // density
+  __syncthreads();
+  // three passes: index i (x) -> a, j (y) -> b, k (z) -> c; node index i + M (j + M k)
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double* src = (d & 1) ? sB : sA;
+    double* dst = (d & 1) ? sA : sB;
+    if (tid < nn) {
+      const int el = tid / Np, node = tid - el * Np;
+      const int id = (node / stride[d]) % M;
+      const int line0 = el * Np + node - id * stride[d];
+      double c = 0.0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) c = fma(av.T[id * M + l], src[line0 + l * stride[d]], c);
+      dst[tid] = c;
+    }
+    __syncthreads();
+  }
+  // coefficients are in sB (three passes: A -> B -> A -> B)
+  if (tid < nel) {
+    double num = 0.0, den = 0.0;
+    for (int m = 0; m < Np; ++m) {
+      const int ia = m % M, ib = (m / M) % M, ic = m / (M * M);
+      const double c = sB[tid * Np + m];
+      const double en = c * c * av.nrm[ia] * av.nrm[ib] * av.nrm[ic];
+      den += en;
+      if (ia == N || ib == N || ic == N) num += en;
+    }
+    double e = 0.0;
+    if (num > 0.0 && den > 0.0) {
+      const double sv = log10(num / den);
+      if (sv > av.s0 + av.kappa)
+        e = av.eps0;
+      else if (sv >= av.s0 - av.kappa)
+        e = 0.5 * av.eps0 * (1.0 + sin(3.141592653589793 * (sv - av.s0) / (2.0 * av.kappa)));
+    }
+    eps[e0 + tid] = e;
+  }
+}
+
+// BR1 gradient of the conserved variables (exterior values: the ghost state at box-boundary
+// faces) times the element viscosity, into sig [(5 d + v)][K][Np]; blocks whose elements all have
+// eps = 0 return at once (the right-hand side reads sig only where eps > 0).
+template <int N>
+__global__ void __launch_bounds__(HexCfg<N>::NT) hex_av_flux_kernel(const double* __restrict__ q,
+                                                                     const double* __restrict__ eps,
+                                                                     double* __restrict__ sig,
+                                                                     const double* __restrict__ D_g,
+                                                                     const HexGeo geo, const int64_t K) {
+  using C = HexCfg<N>;
+  constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
+  __shared__ double sD[3][M * M];
+  __shared__ double sW[5][NODES];
+  __shared__ double sJ[3][5][NODES];
+  __shared__ int sNb[EPB][6];
+  const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  if (!__syncthreads_or(tid < nel && eps[e0 + tid] > 0.0)) return;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int i = tid; i < M * M; i += NT) sD[d][i] = -geo.dsc[d] * D_g[i];
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid], geo.bc);
+  if (tid < nn) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sW[v][tid] = q[v * KNp + base + tid];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sJ[d][v][tid] = 0.0;
+  }
+  __syncthreads();
+  constexpr int FPA = 2 * M * M;
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int s1 = stride[(d + 1) % 3], s2 = stride[(d + 2) % 3];
+    for (int w = tid; w < nel * FPA; w += NT) {
+      const int el = w / FPA, rem = w - el * FPA, end = rem / (M * M), ab = rem - end * M * M;
+      const int node = (end ? N : 0) * stride[d] + (ab % M) * s1 + (ab / M) * s2;
+      const int loc = el * Np + node;
+      const int nnode = node + (end ? -N : N) * stride[d];
+      const int enb = sNb[el][2 * d + end];
+      const size_t gP = enb >= 0 ? (size_t)enb * Np + nnode : base + loc;
+      double qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
+      if (enb < 0) hex_ghost(-enb, d, geo, qp);
+      const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
+      const double sgnlf = end ? lf : -lf;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sJ[d][v][loc] = sgnlf * (qp[v] - sW[v][loc]);
+    }
+  }
+  __syncthreads();
+  if (tid >= nn) return;
+  const int el = tid / Np, node = tid - el * Np;
+  const double ee = eps[e0 + el];
+  if (!(ee > 0.0)) return;
+  const int idx[3] = {node % M, (node / M) % M, node / (M * M)};
+  const size_t gi = base + tid;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int line0 = el * Np + node - idx[d] * stride[d];
+    const double* Drow = sD[d] + idx[d] * M;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = sJ[d][v][tid];
+#pragma unroll
+      for (int l = 0; l < M; ++l) acc = fma(Drow[l], sW[v][line0 + l * stride[d]], acc);
+      sig[(5 * d + v) * KNp + gi] = ee * acc;
+    }
+  }
+}
+
 // Scalar advection du/dt + a . grad u = 0 (the paper's GPU comparison workload, Sec. 5.2): F_d = a_d u
 // and the Lax-Friedrichs flux with lambda = |a . n|, i.e. the upwind flux, so that a face adds
 //   (2/h_d)/w_end (n.F- - n.F*) = (2/h_d)/w_end (s a_d - |a_d|)/2 (u- - u+),  s = -1 (end 0), +1 (end 1),
@@ -535,28 +698,77 @@ cudaError_t launch_vis_t(const dg_hex_mesh_s& m, const GasParams& g, const doubl
   return cudaGetLastError();
 }
 
-template <int N, bool RK, bool VISC>
+template <int N>
+HexAv make_av(const dg_hex_mesh_s& m) {
+  HexAv av{};
+  for (size_t i = 0; i < m.modal.size(); ++i) av.T[i] = m.modal[i];
+  for (size_t a = 0; a < m.modal_norm.size(); ++a) av.nrm[a] = m.modal_norm[a];
+  av.eps0 = m.av_eps0;
+  av.s0 = m.av_s0;
+  av.kappa = m.av_kappa;
+  return av;
+}
+
+template <int N>
+cudaError_t launch_av_sensor_t(const dg_hex_mesh_s& m, const double* q, double* eps, cudaStream_t s) {
+  using C = HexCfg<N>;
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_av_sensor_kernel<N><<<(unsigned)blocks, C::NT, 0, s>>>(q, make_av<N>(m), m.K, eps);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_av_flux_t(const dg_hex_mesh_s& m, const double* q, cudaStream_t s) {
+  using C = HexCfg<N>;
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_av_flux_kernel<N><<<(unsigned)blocks, C::NT, 0, s>>>(q, m.av_eps, m.av_sig, m.D_dev, make_geo<N>(m, 1.0), m.K);
+  return cudaGetLastError();
+}
+
+template <int N, bool RK, bool VISC, bool AV>
 cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a, double b,
                      double dt, cudaStream_t s) {
   using C = HexCfg<N>;
   const HexGeo geo = make_geo<N>(m, RK ? dt : 1.0);
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
-  hex_rhs_kernel<N, RK, VISC><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b,
-                                                                 a != 0.0, m.status, m.fv_dev);
+  hex_rhs_kernel<N, RK, VISC, AV><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b,
+                                                                     a != 0.0, m.status, m.fv_dev, m.av_sig,
+                                                                     m.av_eps);
   return cudaGetLastError();
+}
+
+template <int N, bool VISC, bool AV>
+cudaError_t launch_rk(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
+                      double a, double b, double dt, cudaStream_t s) {
+  return rk ? launch_t<N, true, VISC, AV>(m, g.gamma, q, out, k, a, b, dt, s)
+            : launch_t<N, false, VISC, AV>(m, g.gamma, q, out, k, a, b, dt, s);
 }
 
 template <int N>
 cudaError_t launch_n(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                      double a, double b, double dt, cudaStream_t s) {
-  if (g.mu > 0) {
-    const cudaError_t e = launch_vis_t<N>(m, g, q, s);
-    if (e != cudaSuccess) return e;
-    return rk ? launch_t<N, true, true>(m, g.gamma, q, out, k, a, b, dt, s)
-              : launch_t<N, false, true>(m, g.gamma, q, out, k, a, b, dt, s);
+  cudaError_t e;
+  if (g.mu > 0 && (e = launch_vis_t<N>(m, g, q, s)) != cudaSuccess) return e;
+  const bool av = m.av_eps0 > 0;
+  if (av) {
+    if ((e = launch_av_sensor_t<N>(m, q, m.av_eps, s)) != cudaSuccess) return e;
+    if ((e = launch_av_flux_t<N>(m, q, s)) != cudaSuccess) return e;
   }
-  return rk ? launch_t<N, true, false>(m, g.gamma, q, out, k, a, b, dt, s)
-            : launch_t<N, false, false>(m, g.gamma, q, out, k, a, b, dt, s);
+  if (g.mu > 0)
+    return av ? launch_rk<N, true, true>(m, g, q, out, k, rk, a, b, dt, s)
+              : launch_rk<N, true, false>(m, g, q, out, k, rk, a, b, dt, s);
+  return av ? launch_rk<N, false, true>(m, g, q, out, k, rk, a, b, dt, s)
+            : launch_rk<N, false, false>(m, g, q, out, k, rk, a, b, dt, s);
+}
+
+cudaError_t launch_av_sensor(const dg_hex_mesh_s& m, const double* q, double* eps, cudaStream_t s) {
+  switch (m.N) {
+    case 1: return launch_av_sensor_t<1>(m, q, eps, s);
+    case 2: return launch_av_sensor_t<2>(m, q, eps, s);
+    case 3: return launch_av_sensor_t<3>(m, q, eps, s);
+    case 4: return launch_av_sensor_t<4>(m, q, eps, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
@@ -685,6 +897,28 @@ int dg_hex_mesh_create(const dg_hex_desc* d, dg_hex_mesh* out) {
     delete m;
     return dg::fail(DG_ERR_INVALID_ARG, err);
   }
+  {  // Legendre modal analysis at the nodes (long double recurrence), for the AV indicator
+    std::vector<long double> L((size_t)M * M);  // L[a][j]
+    for (int j = 0; j < M; ++j) {
+      long double p0 = 1.0L, p1 = (long double)x[j];
+      L[j] = p0;
+      if (M > 1) L[M + j] = p1;
+      for (int a = 1; a + 1 < M; ++a) {
+        const long double p2 = ((2 * a + 1) * (long double)x[j] * p1 - a * p0) / (a + 1);
+        L[(size_t)(a + 1) * M + j] = p2;
+        p0 = p1;
+        p1 = p2;
+      }
+    }
+    m->modal.assign((size_t)M * M, 0.0);
+    m->modal_norm.assign(M, 0.0);
+    for (int a = 0; a < M; ++a) {
+      long double nrm = 0.0L;
+      for (int j = 0; j < M; ++j) nrm += (long double)m->w[j] * L[(size_t)a * M + j] * L[(size_t)a * M + j];
+      m->modal_norm[a] = (double)nrm;
+      for (int j = 0; j < M; ++j) m->modal[(size_t)a * M + j] = (double)((long double)m->w[j] * L[(size_t)a * M + j] / nrm);
+    }
+  }
   cudaError_t e = cudaMalloc((void**)&m->D_dev, sizeof(double) * M * M);
   if (e == cudaSuccess) e = cudaMemcpy(m->D_dev, m->D.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->status, sizeof(unsigned));
@@ -703,6 +937,8 @@ int dg_hex_mesh_free(dg_hex_mesh m) {
   if (!m) return DG_OK;
   cudaFree(m->D_dev);
   cudaFree(m->fv_dev);
+  cudaFree(m->av_eps);
+  cudaFree(m->av_sig);
   cudaFree(m->status);
   delete m;
   return DG_OK;
@@ -774,6 +1010,37 @@ int dg_hex_advection_rhs(dg_hex_mesh m, const double* velocity, const double* u,
 int dg_hex_advection_rk_stage(dg_hex_mesh m, const double* velocity, int32_t stage, double dt, const double* u_in,
                               double* u_out, double* k, void* stream) {
   return hex_adv_run(m, velocity, u_in, u_out, k, true, stage, dt, stream);
+}
+
+int dg_hex_set_av(dg_hex_mesh m, const dg_av_params* p) {
+  if (!m) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (!p || p->eps0 == 0.0) {
+    m->av_eps0 = 0.0;
+    return DG_OK;
+  }
+  if (!(p->eps0 > 0) || !std::isfinite(p->eps0) || !std::isfinite(p->s0) || !(p->kappa > 0) ||
+      !std::isfinite(p->kappa))
+    return dg::fail(DG_ERR_INVALID_ARG, "need eps0 >= 0, kappa > 0, all finite");
+  if (!m->av_eps) {
+    cudaError_t e = cudaMalloc((void**)&m->av_eps, sizeof(double) * (size_t)m->K);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->av_sig, sizeof(double) * 15 * (size_t)m->K * m->Np);
+    if (e != cudaSuccess) {
+      cudaFree(m->av_eps);
+      cudaFree(m->av_sig);
+      m->av_eps = m->av_sig = nullptr;
+      return dg::cuda_fail(e, "hexahedral artificial-viscosity scratch");
+    }
+  }
+  m->av_eps0 = p->eps0;
+  m->av_s0 = p->s0;
+  m->av_kappa = p->kappa;
+  return DG_OK;
+}
+
+int dg_hex_av_viscosity(dg_hex_mesh m, const double* q, double* eps, void* stream) {
+  if (!m || !q || !eps) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh, state or output");
+  const cudaError_t e = dg::hexk::launch_av_sensor(*m, q, eps, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral smoothness-indicator kernel");
 }
 
 int dg_hex_set_inflow(dg_hex_mesh m, const double* q_in, int32_t nvar) {

@@ -341,6 +341,24 @@ class HexMesh:
         check(load().dg_hex_operators(self.handle, _hptr(D), _hptr(w)))
         return D, w
 
+    def set_av(self, eps0, s0=None, kappa=0.5):
+        """Artificial viscosity for later right-hand sides (eps0 = 0 turns it off); s0 defaults to
+        -4 log10 N."""
+        p = capi.dg_av_params()
+        p.eps0 = float(eps0)
+        p.s0 = float(-4.0 * np.log10(self.N) if s0 is None else s0)
+        p.kappa = float(kappa)
+        check(load().dg_hex_set_av(self.handle, ctypes.byref(p)))
+
+    def av_viscosity(self, q, eps, stream=None):
+        """eps [K] (CUDA float64) <- the element viscosities of q under the mesh's parameters."""
+        import torch
+        if eps.numel() != self.K:
+            raise ValueError(f"eps must hold {self.K} values")
+        _hex_sized(self, 5, q=q)
+        check(load().dg_hex_av_viscosity(self.handle, _dptr(q, torch.float64, "q"), _dptr(eps, torch.float64, "eps"),
+                                         _stream_ptr(stream)))
+
     def set_inflow(self, q_in):
         """Conserved state (5 values) imposed on DG_BC_INFLOW box faces."""
         v = np.ascontiguousarray(q_in, dtype=np.float64).reshape(-1)

@@ -291,3 +291,80 @@ def test_hex_navier_stokes_with_walls(name, N):
     assert rel_err(got, want) <= TOL
     euler = hx.hex_rhs_strong(ref, box, q0, GAS, q_in=q_in)
     assert rel_err(got - euler, want - euler) <= 1e-9
+
+
+# --- artificial viscosity --------------------------------------------------------------------------
+
+AV_EPS0 = 1e-2
+
+
+def _front_state(xyz):
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    th = np.tanh((x - 0.5) / 0.04)
+    rho = 1.5 + 0.5 * th + 0.05 * np.sin(2 * np.pi * y)
+    u = 0.3 - 0.2 * th
+    v = 0.05 * np.cos(2 * np.pi * z)
+    w = 0.02 * np.sin(2 * np.pi * x)
+    p = 1.2 + 0.4 * th
+    return np.stack([rho, rho * u, rho * v, rho * w, p / 0.4 + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def _av_thresholds(ref, q):
+    """s0 at the second-largest indicator value of the state and kappa half its distance to the
+    nearest other value: elements fall on zero, on the ramp and on eps0."""
+    u = np.unique(np.round(np.log10(hx.hex_indicator(ref, q[0])), 9))
+    s0 = u[-2]
+    return s0, 0.5 * min(u[-1] - s0, s0 - u[-3])
+
+
+def _av_setup(N, bc=None):
+    torch, dg, box, ref, q0, mesh, gas = _setup((4, 2, 2), N)
+    q0 = _front_state(hex_nodes(box, gll_nodes(N)))
+    if bc is not None:
+        box["bc"] = bc
+        mesh = dg.HexMesh(box["n"], box["L"], N, gll_nodes(N), bc=bc)
+        mesh.set_inflow(q0[:, 0, 0])
+    s0, kappa = _av_thresholds(ref, q0)
+    mesh.set_av(AV_EPS0, s0, kappa)
+    return torch, dg, box, ref, q0, mesh, gas, (s0, kappa)
+
+
+def _av_eps(ref, q, th):
+    import oracle.av as oav
+    return oav.viscosity(hx.hex_indicator(ref, q[0]), AV_EPS0, th[0], th[1])
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_hex_element_viscosity(N):
+    torch, dg, box, ref, q0, mesh, gas, th = _av_setup(N)
+    eps = torch.empty(mesh.K, dtype=torch.float64, device="cuda")
+    mesh.av_viscosity(torch.tensor(q0, device="cuda"), eps)
+    want = _av_eps(ref, q0, th)
+    assert np.abs(eps.cpu().numpy() - want).max() <= 1e-11 * AV_EPS0
+    assert (want == 0).any() and (want == AV_EPS0).any() and ((want > 0) & (want < AV_EPS0)).any()
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_hex_rhs_with_artificial_viscosity(N, viscous):
+    torch, dg, box, ref, q0, mesh, gas, th = _av_setup(N)
+    g = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU if viscous else 0.0, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, g, q, rhs)
+    base = hx.hex_rhs_ns(ref, box, q0, GAS, NS_MU, NS_PR) if viscous else hx.hex_rhs_strong(ref, box, q0, GAS)
+    want = base + hx.hex_rhs_av(ref, box, q0, _av_eps(ref, q0, th))
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_artificial_viscosity_with_walls():
+    torch, dg, box, ref, q0, mesh, gas, th = _av_setup(3, bc=HEX_BC["channel"])
+    g = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, g, q, rhs)
+    q_in = q0[:, 0, 0]
+    want = (hx.hex_rhs_ns(ref, box, q0, GAS, NS_MU, NS_PR, q_in=q_in)
+            + hx.hex_rhs_av(ref, box, q0, _av_eps(ref, q0, th), q_in=q_in))
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
