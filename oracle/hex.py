@@ -27,6 +27,12 @@ DG on Gauss-Lobatto-Legendre points, written from its definitions:
   Legendre polynomials up to degree N are orthogonal; d q/dt += div(eps grad q) for every
   conserved variable with BR1 central fluxes (exterior q+ of the ghost state at boundary faces,
   exterior flux = interior flux there);
+* over-integration (weak form; the paper names it among its shock stabilisations, §5.3): the
+  volume integral of grad(phi_i) . F(q_h) with Q Gauss-Legendre points per axis instead of the
+  collocated nodes, rhs_vol = sum_d (2/h_d) (A_d (x) B (x) B) F_d(I q), with the interpolation
+  I [Q][N+1] from the nodes to the Gauss points, A = W^-1 (I D)^T W_Q along d and
+  B = W^-1 I^T W_Q along the other axes (W: nodal weights, W_Q: Gauss weights); the face terms
+  are the collocated ones of the weak form;
 * boundary conditions on box faces (box["bc"][axis][end], the codes of oracle/boundary.py): q+
   at a boundary face node is the ghost state of the condition, with n = -e_axis or +e_axis;
 * weak form (cross-check): dq/dt = sum_d (2/h_d) W^-1 D^T W F_d - sum_f (2/h_d)/w_end n.F*_f;
@@ -319,6 +325,54 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
             lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
             rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
     return rhs.reshape(q.shape)
+
+
+def _gauss_operators(ref, Q):
+    """(I, A, B) of the over-integration with Q Gauss-Legendre points (see the module notes)."""
+    xg, wg = np.polynomial.legendre.leggauss(Q)
+    x = ref.nodes
+    M = x.size
+    I = np.ones((Q, M))
+    for j in range(M):
+        for k in range(M):
+            if k != j:
+                I[:, j] *= (xg - x[k]) / (x[j] - x[k])
+    A = (np.diag(1.0 / ref.w) @ (I @ ref.D).T) * wg[None, :]
+    B = (np.diag(1.0 / ref.w) @ I.T) * wg[None, :]
+    return I, A, B
+
+
+def _along_rect(Mx, a, axis):
+    """Apply the rectangular matrix Mx [out][in] along tensor axis `axis` of a[..., k, j, i]."""
+    ax = {0: -1, 1: -2, 2: -3}[axis]
+    a = np.moveaxis(a, ax, -1)
+    return np.moveaxis(a @ Mx.T, -1, ax)
+
+
+def hex_overint_volume(ref, box, q5, gas, Q):
+    """Over-integrated volume term [5][K][M][M][M] of the weak form."""
+    I, A, B = _gauss_operators(ref, Q)
+    qg = q5
+    for d in range(3):
+        qg = _along_rect(I, qg, d)  # nodes -> Gauss points along every axis
+    Fg = _volume_fluxes(qg, gas)
+    out = np.zeros_like(q5)
+    for d in range(3):
+        t = Fg[d]
+        for e in range(3):
+            t = _along_rect(A if e == d else B, t, e)
+        out += (2.0 / box["h"][d]) * t
+    return out
+
+
+def hex_rhs_overint(ref, box, q, gas, Q, q_in=None):
+    """Weak-form Euler right-hand side with over-integrated volume fluxes (Q Gauss points per axis)."""
+    N = ref.N
+    q5 = _shape(np.asarray(q, dtype=np.float64), N)
+    rhs = hex_overint_volume(ref, box, q5, gas, Q)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
+        rhs[sel] -= lift * fstar
+    return rhs.reshape(np.shape(q))
 
 
 def hex_indicator(ref, u):
