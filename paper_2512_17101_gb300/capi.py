@@ -138,6 +138,7 @@ SIGNATURES = {
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_hex_set_inflow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "dg_hex_set_av": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "dg_hex_set_overintegration": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "dg_hex_av_viscosity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_hex_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
     "dg_round_to_float": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),

@@ -39,6 +39,8 @@ struct dg_hex_mesh_s {
   double av_eps0 = 0.0, av_s0 = 0.0, av_kappa = 1.0;
   double* av_eps = nullptr;
   double* av_sig = nullptr;
+  bool overint = false;             // dg_hex_set_overintegration
+  std::vector<double> oi_I, oi_A, oi_B;  // [Q][M], [M][Q], [M][Q]
   std::vector<double> modal;        // [M][M]: nodal values -> Legendre coefficients (GLL-weighted)
   std::vector<double> modal_norm;   // [M]: discrete norms of the Legendre polynomials
   unsigned* status = nullptr;
@@ -554,6 +556,211 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_av_flux_kernel(const double
   }
 }
 
+// Over-integration (weak form; the paper names it among the stabilisations of its shock cases,
+// Sec. 5.3): the volume integral of grad(phi_i) . F(q_h) with Q = ceil(3 (N+1) / 2) Gauss-Legendre
+// points per axis,
+//   rhs_vol = sum_d (2/h_d) (A_d (x) B (x) B) F_d(I q),
+// I [Q][M] the interpolation from the nodes to the Gauss points, A = W^-1 (I D)^T W_Q along d,
+// B = W^-1 I^T W_Q along the other axes; the face terms are the collocated weak-form ones,
+// -(2/h_d)/w_end n.F*.  Everything per element stays in shared memory: the interpolated state
+// (three passes), each direction's fluxes at the Gauss points and their three contractions.
+template <int N>
+struct OiCfg {
+  static constexpr int M = N + 1, Q = (3 * (N + 1) + 1) / 2, Np = M * M * M;
+  static constexpr int EPB = N == 1 ? 16 : (N == 2 ? 4 : (N == 3 ? 2 : 1));
+  static constexpr int NT = 256;
+  // doubles per element: nodal state, x-, y- and z-interpolated state, fluxes, volume and face terms
+  static constexpr int PER = 5 * (Np + M * M * Q + M * Q * Q + 2 * Q * Q * Q + 2 * Np);
+  static constexpr size_t SMEM = sizeof(double) * PER * EPB + sizeof(int) * 6 * EPB;
+};
+
+struct HexOI {
+  double I[40];  // [Q][M]
+  double A[40];  // [M][Q]
+  double B[40];  // [M][Q]
+};
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(OiCfg<N>::NT) hex_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
+                                                               double* __restrict__ kreg, const HexGeo geo,
+                                                               const HexOI op, const int64_t K, const double gamma,
+                                                               const double a, const double b, const int accumulate,
+                                                               unsigned* __restrict__ status) {
+  using C = OiCfg<N>;
+  constexpr int M = C::M, Q = C::Q, Np = C::Np, EPB = C::EPB, NT = C::NT;
+  constexpr int M2 = M * M, Q2 = Q * Q, Q3 = Q * Q * Q;
+  extern __shared__ double sm[];
+  double* sq = sm;                      // [5][EPB][Np]
+  double* sA = sq + 5 * EPB * Np;       // [5][EPB][M][M][Q]  (x interpolated)   / [5][EPB][Q][M][M] later
+  double* sB = sA + 5 * EPB * M2 * Q;   // [5][EPB][M][Q][Q]  (x, y interpolated)/ [5][EPB][Q][Q][M] later
+  double* sC = sB + 5 * EPB * M * Q2;   // [5][EPB][Q][Q][Q]  state at the Gauss points
+  double* sF = sC + 5 * EPB * Q3;       // [5][EPB][Q][Q][Q]  flux along d at the Gauss points
+  double* acc = sF + 5 * EPB * Q3;      // [5][EPB][Np]       volume term
+  double* sS = acc + 5 * EPB * Np;      // [5][EPB][Np]       face terms
+  int(*sNb)[6] = reinterpret_cast<int(*)[6]>(sS + 5 * EPB * Np);
+  const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)min((int64_t)EPB, K - e0);
+  const int nn = nel * Np;
+  const size_t KNp = (size_t)K * Np;
+  const size_t base = (size_t)e0 * Np;
+  if (tid < nel) hex_neighbours((unsigned)(e0 + tid), geo.n, sNb[tid], geo.bc);
+  for (int t = tid; t < 5 * nn; t += NT) {
+    const int v = t / nn, i = t - v * nn;
+    sq[v * EPB * Np + i] = q[v * KNp + base + i];
+    acc[v * EPB * Np + i] = 0.0;
+    sS[v * EPB * Np + i] = 0.0;
+  }
+  __syncthreads();
+  // interpolation to the Gauss points: along x, then y, then z
+  for (int t = tid; t < 5 * nel * M2 * Q; t += NT) {
+    const int v = t / (nel * M2 * Q), r = t - v * nel * M2 * Q, el = r / (M2 * Q), s2 = r - el * M2 * Q;
+    const int kj = s2 / Q, qa = s2 - kj * Q;  // kj = k M + j
+    const double* src = sq + v * EPB * Np + el * Np + kj * M;
+    double c = 0.0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) c = fma(op.I[qa * M + i], src[i], c);
+    sA[v * EPB * M2 * Q + el * M2 * Q + s2] = c;
+  }
+  __syncthreads();
+  for (int t = tid; t < 5 * nel * M * Q2; t += NT) {
+    const int v = t / (nel * M * Q2), r = t - v * nel * M * Q2, el = r / (M * Q2), s2 = r - el * M * Q2;
+    const int k = s2 / Q2, qb = (s2 / Q) % Q, qa = s2 % Q;
+    const double* src = sA + v * EPB * M2 * Q + el * M2 * Q + k * M * Q + qa;
+    double c = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) c = fma(op.I[qb * M + j], src[j * Q], c);
+    sB[v * EPB * M * Q2 + el * M * Q2 + s2] = c;
+  }
+  __syncthreads();
+  for (int t = tid; t < 5 * nel * Q3; t += NT) {
+    const int v = t / (nel * Q3), r = t - v * nel * Q3, el = r / Q3, s2 = r - el * Q3;
+    const int qc = s2 / Q2, qba = s2 - qc * Q2;
+    const double* src = sB + v * EPB * M * Q2 + el * M * Q2 + qba;
+    double c = 0.0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) c = fma(op.I[qc * M + k], src[k * Q2], c);
+    sC[v * EPB * Q3 + el * Q3 + s2] = c;
+  }
+  __syncthreads();
+  const double gm1 = gamma - 1.0;
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    // fluxes along d at the Gauss points
+    for (int t = tid; t < nel * Q3; t += NT) {
+      double qv[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qv[v] = sC[v * EPB * Q3 + t];
+      const double ir = rcp_nr(qv[0]);
+      const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
+      if (d == 0 && (!(qv[0] > 0.0) || !(p > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      const double ud = qv[1 + d] * ir;
+      sF[0 * EPB * Q3 + t] = qv[1 + d];
+      sF[1 * EPB * Q3 + t] = qv[1] * ud + (d == 0 ? p : 0.0);
+      sF[2 * EPB * Q3 + t] = qv[2] * ud + (d == 1 ? p : 0.0);
+      sF[3 * EPB * Q3 + t] = qv[3] * ud + (d == 2 ? p : 0.0);
+      sF[4 * EPB * Q3 + t] = ud * (qv[4] + p);
+    }
+    __syncthreads();
+    // contraction along x: [Q][Q][Q] -> [Q][Q][M] (into the sB region)
+    const double* Mx = d == 0 ? op.A : op.B;
+    const double* My = d == 1 ? op.A : op.B;
+    const double* Mz = d == 2 ? op.A : op.B;
+    for (int t = tid; t < 5 * nel * Q2 * M; t += NT) {
+      const int v = t / (nel * Q2 * M), r = t - v * nel * Q2 * M, el = r / (Q2 * M), s2 = r - el * Q2 * M;
+      const int cb = s2 / M, i = s2 - cb * M;  // cb = qc Q + qb
+      const double* src = sF + v * EPB * Q3 + el * Q3 + cb * Q;
+      double c = 0.0;
+#pragma unroll
+      for (int qa = 0; qa < Q; ++qa) c = fma(Mx[i * Q + qa], src[qa], c);
+      sB[v * EPB * M * Q2 + el * M * Q2 + s2] = c;
+    }
+    __syncthreads();
+    // along y: [Q][Q][M] -> [Q][M][M] (into the sA region)
+    for (int t = tid; t < 5 * nel * Q * M2; t += NT) {
+      const int v = t / (nel * Q * M2), r = t - v * nel * Q * M2, el = r / (Q * M2), s2 = r - el * Q * M2;
+      const int qc = s2 / M2, j = (s2 / M) % M, i = s2 % M;
+      const double* src = sB + v * EPB * M * Q2 + el * M * Q2 + qc * Q * M + i;
+      double c = 0.0;
+#pragma unroll
+      for (int qb = 0; qb < Q; ++qb) c = fma(My[j * Q + qb], src[qb * M], c);
+      sA[v * EPB * M2 * Q + el * M2 * Q + s2] = c;
+    }
+    __syncthreads();
+    // along z: [Q][M][M] -> [M][M][M], added to the volume term with the factor (2/h_d) s
+    const double fac = -geo.dsc[d];
+    for (int t = tid; t < 5 * nn; t += NT) {
+      const int v = t / nn, r = t - v * nn, el = r / Np, node = r - el * Np;
+      const int k = node / M2, ji = node - k * M2;
+      const double* src = sA + v * EPB * M2 * Q + el * M2 * Q + ji;
+      double c = 0.0;
+#pragma unroll
+      for (int qc = 0; qc < Q; ++qc) c = fma(Mz[k * Q + qc], src[qc * M2], c);
+      acc[v * EPB * Np + r] = fma(fac, c, acc[v * EPB * Np + r]);
+    }
+    __syncthreads();
+  }
+  // weak-form face terms -(2/h_d)/w_end n.F* (times s), one axis per pass
+  constexpr int FPA = 2 * M * M;
+  constexpr int stride[3] = {1, M, M * M};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int s1 = stride[(d + 1) % 3], s2 = stride[(d + 2) % 3];
+    for (int w = tid; w < nel * FPA; w += NT) {
+      const int el = w / FPA, rem = w - el * FPA, end = rem / (M * M), ab = rem - end * M * M;
+      const int node = (end ? N : 0) * stride[d] + (ab % M) * s1 + (ab / M) * s2;
+      const int loc = el * Np + node;
+      const int nnode = node + (end ? -N : N) * stride[d];
+      const int enb = sNb[el][2 * d + end];
+      const size_t gP = enb >= 0 ? (size_t)enb * Np + nnode : base + loc;
+      double qm[5], qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = sq[v * EPB * Np + loc];
+        qp[v] = q[v * KNp + gP];
+      }
+      if (enb < 0) hex_ghost(-enb, d, geo, qp);
+      double irm, pm, cm, irp, pp, cp;
+      pc(gamma, qm, irm, pm, cm);
+      pc(gamma, qp, irp, pp, cp);
+      if (enb < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      const double um = qm[1 + d] * irm, up = qp[1 + d] * irp;
+      const double lam = fmax(fabs(um) + cm, fabs(up) + cp);
+      double fm[5], fp[5];
+      fm[0] = qm[1 + d];
+      fp[0] = qp[1 + d];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        fm[1 + i] = qm[1 + i] * um;
+        fp[1 + i] = qp[1 + i] * up;
+      }
+      fm[1 + d] += pm;
+      fp[1 + d] += pp;
+      fm[4] = um * (qm[4] + pm);
+      fp[4] = up * (qp[4] + pp);
+      // -(2/h_d)/w_end n.F* = -(sgn (F_d- + F_d+) + lam (q- - q+)) (2/h_d)/w_end / 2 (times s)
+      const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
+      const double sgnlf = end ? lf : -lf;
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        sS[v * EPB * Np + loc] -= fma(sgnlf, fm[v] + fp[v], lf * lam * (qm[v] - qp[v]));
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < 5 * nn; t += NT) {
+    const int v = t / nn, r = t - v * nn;
+    const double rv = acc[v * EPB * Np + r] + sS[v * EPB * Np + r];  // s rhs
+    const size_t gi = v * KNp + base + r;
+    if (RK) {
+      const double kk = accumulate ? fma(a, kreg[gi], rv) : rv;
+      kreg[gi] = kk;
+      out[gi] = fma(b, kk, sq[v * EPB * Np + r]);
+    } else {
+      out[gi] = rv;
+    }
+  }
+}
+
 // Scalar advection du/dt + a . grad u = 0 (the paper's GPU comparison workload, Sec. 5.2): F_d = a_d u
 // and the Lax-Friedrichs flux with lambda = |a . n|, i.e. the upwind flux, so that a face adds
 //   (2/h_d)/w_end (n.F- - n.F*) = (2/h_d)/w_end (s a_d - |a_d|)/2 (u- - u+),  s = -1 (end 0), +1 (end 1),
@@ -744,9 +951,33 @@ cudaError_t launch_rk(const dg_hex_mesh_s& m, const GasParams& g, const double* 
             : launch_t<N, false, VISC, AV>(m, g.gamma, q, out, k, a, b, dt, s);
 }
 
+template <int N, bool RK>
+cudaError_t launch_oi_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a,
+                        double b, double dt, cudaStream_t s) {
+  using C = OiCfg<N>;
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(hex_oi_kernel<N, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  HexOI op{};
+  for (size_t i = 0; i < m.oi_I.size(); ++i) op.I[i] = m.oi_I[i];
+  for (size_t i = 0; i < m.oi_A.size(); ++i) op.A[i] = m.oi_A[i];
+  for (size_t i = 0; i < m.oi_B.size(); ++i) op.B[i] = m.oi_B[i];
+  const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
+  hex_oi_kernel<N, RK><<<(unsigned)blocks, C::NT, C::SMEM, s>>>(q, out, k, make_geo<N>(m, RK ? dt : 1.0), op, m.K,
+                                                                 gamma, a, b, a != 0.0, m.status);
+  return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t launch_n(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                      double a, double b, double dt, cudaStream_t s) {
+  if (m.overint)
+    return rk ? launch_oi_t<N, true>(m, g.gamma, q, out, k, a, b, dt, s)
+              : launch_oi_t<N, false>(m, g.gamma, q, out, k, a, b, dt, s);
   cudaError_t e;
   if (g.mu > 0 && (e = launch_vis_t<N>(m, g, q, s)) != cudaSuccess) return e;
   const bool av = m.av_eps0 > 0;
@@ -960,6 +1191,8 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
   if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
   if (gas->p.model != DG_GAS_PERFECT)
     return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path takes a perfect gas");
+  if (m->overint && (gas->p.mu > 0 || m->av_eps0 > 0))
+    return dg::fail(DG_ERR_UNSUPPORTED, "over-integration runs with the Euler equations, without artificial viscosity");
   if (gas->p.mu > 0) {
     if (!m->fv_dev) {
       const cudaError_t e = cudaMalloc((void**)&m->fv_dev, sizeof(double) * 9 * (size_t)m->K * m->Np);
@@ -1041,6 +1274,52 @@ int dg_hex_av_viscosity(dg_hex_mesh m, const double* q, double* eps, void* strea
   if (!m || !q || !eps) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh, state or output");
   const cudaError_t e = dg::hexk::launch_av_sensor(*m, q, eps, (cudaStream_t)stream);
   return e == cudaSuccess ? DG_OK : dg::cuda_fail(e, "hexahedral smoothness-indicator kernel");
+}
+
+int dg_hex_set_overintegration(dg_hex_mesh m, int32_t enable) {
+  if (!m) return dg::fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  m->overint = enable != 0;
+  if (!m->overint || !m->oi_I.empty()) return DG_OK;
+  // Q = ceil(3 (N+1) / 2) Gauss-Legendre points (Newton on P_Q, long double), the interpolation
+  // from the nodes and the two contraction matrices
+  const int M = m->M, Q = (3 * M + 1) / 2;
+  typedef long double ld;
+  std::vector<ld> xg(Q), wg(Q);
+  const ld pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < Q; ++i) {
+    ld z = cosl(pi * (i + 0.75L) / (Q + 0.5L)), dp = 1.0L;
+    for (int it = 0; it < 100; ++it) {
+      ld p0 = 1.0L, p1 = z;
+      for (int n = 2; n <= Q; ++n) {
+        const ld p2 = ((2 * n - 1) * z * p1 - (n - 1) * p0) / n;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = Q * (z * p1 - p0) / (z * z - 1.0L);
+      const ld dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-19L) break;
+    }
+    xg[i] = z;
+    wg[i] = 2.0L / ((1.0L - z * z) * dp * dp);
+  }
+  std::vector<ld> I((size_t)Q * M, 1.0L);
+  for (int g = 0; g < Q; ++g)
+    for (int j = 0; j < M; ++j)
+      for (int k = 0; k < M; ++k)
+        if (k != j) I[(size_t)g * M + j] *= (xg[g] - (ld)m->nodes[k]) / ((ld)m->nodes[j] - (ld)m->nodes[k]);
+  m->oi_I.assign((size_t)Q * M, 0.0);
+  m->oi_A.assign((size_t)M * Q, 0.0);
+  m->oi_B.assign((size_t)M * Q, 0.0);
+  for (int g = 0; g < Q; ++g)
+    for (int i = 0; i < M; ++i) {
+      m->oi_I[(size_t)g * M + i] = (double)I[(size_t)g * M + i];
+      ld id = 0.0L;  // (I D)[g][i]
+      for (int k = 0; k < M; ++k) id += I[(size_t)g * M + k] * (ld)m->D[(size_t)k * M + i];
+      m->oi_A[(size_t)i * Q + g] = (double)(id * wg[g] / (ld)m->w[i]);
+      m->oi_B[(size_t)i * Q + g] = (double)(I[(size_t)g * M + i] * wg[g] / (ld)m->w[i]);
+    }
+  return DG_OK;
 }
 
 int dg_hex_set_inflow(dg_hex_mesh m, const double* q_in, int32_t nvar) {

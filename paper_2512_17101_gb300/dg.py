@@ -359,6 +359,10 @@ class HexMesh:
         check(load().dg_hex_av_viscosity(self.handle, _dptr(q, torch.float64, "q"), _dptr(eps, torch.float64, "eps"),
                                          _stream_ptr(stream)))
 
+    def set_overintegration(self, enable=True):
+        """Weak-form Euler right-hand side with ceil(3 (N+1) / 2) Gauss points per axis."""
+        check(load().dg_hex_set_overintegration(self.handle, int(bool(enable))))
+
     def set_inflow(self, q_in):
         """Conserved state (5 values) imposed on DG_BC_INFLOW box faces."""
         v = np.ascontiguousarray(q_in, dtype=np.float64).reshape(-1)

@@ -368,3 +368,45 @@ def test_hex_artificial_viscosity_with_walls():
     want = (hx.hex_rhs_ns(ref, box, q0, GAS, NS_MU, NS_PR, q_in=q_in)
             + hx.hex_rhs_av(ref, box, q0, _av_eps(ref, q0, th), q_in=q_in))
     assert rel_err(rhs.cpu().numpy(), want) <= TOL
+
+
+# --- over-integration -------------------------------------------------------------------------------
+
+def _q32(N):
+    return int(np.ceil(3 * (N + 1) / 2))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, (3, 2, 2), (5, 1, 3)])
+def test_hex_overintegrated_rhs(n, N):
+    torch, dg, box, ref, q0, mesh, gas = _setup(n, N)
+    mesh.set_overintegration(True)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, gas, q, rhs)
+    want = hx.hex_rhs_overint(ref, box, q0, GAS, _q32(N))
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_overintegrated_with_boundaries_and_rk_steps():
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((4, 3, 2), 3, HEX_BC["channel"])
+    mesh.set_overintegration(True)
+    dt = 2e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.hex_lsrk4_step(mesh, gas, q, dt, steps=2)
+    f = lambda u: hx.hex_rhs_overint(ref, box, u, GAS, _q32(3), q_in=q_in)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+
+
+def test_hex_overintegration_is_euler_only():
+    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
+    from paper_2512_17101_gb300 import capi
+    mesh.set_overintegration(True)
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    with pytest.raises(capi.DGError):
+        dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
+    mesh.set_overintegration(False)
+    dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
