@@ -57,7 +57,7 @@ def kernel_source_hash(files=FP64_SOURCES):
     return h.hexdigest()[:16]
 
 
-# ---- algorithmic work per launch (documented in the design doc) --------------------------------------
+# ---- algorithmic work per launch ------------------------------------------------------------
 
 def rhs_flops_per_element(Np, NF, V, viscous):
     """FP64 flops the fused right-hand side + stage update needs per element."""
