@@ -57,6 +57,15 @@ def kernel_source_hash(files=FP64_SOURCES):
     return h.hexdigest()[:16]
 
 
+# The paper's own right-hand-side throughput figures (Sec. 5.3), with their hardware: context only
+# (other hardware, a 2-D p = 1 tensor-product shock/boundary-layer case, no stated precision).
+PAPER_CONTEXT = [
+    {"figure": "RHS throughput", "value": 1.6e6, "unit": "DOFs/s", "hardware": "Apple M2 (CPU)",
+     "case": "shock/boundary-layer Navier-Stokes, 2M p = 1 tensor-product elements (8M DOFs)"},
+    {"figure": "RHS throughput", "value": 100.4e6, "unit": "DOFs/s", "hardware": "AMD MI300A (1 device)",
+     "case": "same case"},
+]
+
 # ---- algorithmic work per launch ------------------------------------------------------------
 
 def rhs_flops_per_element(Np, NF, V, viscous):
@@ -469,6 +478,7 @@ def gpu_arm(args, cfg, world, rank, local):
             "roofline": roofline(head, per_head), "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
+            "paper_context": PAPER_CONTEXT,
             "hex_advection_form": hexadv, "hex_shock_form": hexshock, "boundary_form": bnd, "av_form": avf, "mixture_ns_form": mixns, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
