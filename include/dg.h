@@ -400,7 +400,11 @@ int dg_batch_step(dg_batch batch, int32_t steps, void* stream);
  * pointer may be NULL). */
 int dg_batch_tiles(dg_batch batch, int32_t* rhs_tiles_host, int32_t* viscous_tiles_host, double* rhs_tune_ms_host);
 
+/* DG_STATUS_* bits of the batch's cases (non-physical states, a tensor-core wait that timed out),
+ * after synchronising the device; reset != 0 clears them. */
 int dg_batch_status(dg_batch batch, uint32_t* bits, int reset);
+/* Frees the batch's device memory and CUDA graph (the cases' meshes, gases and states stay the
+ * caller's). NULL is a no-op. */
 int dg_batch_free(dg_batch batch);
 
 /* ---- tensor-product hexahedra ---------------------------------------------------------------
