@@ -152,6 +152,27 @@ int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* params);
  * [V][K][Np]; its density is read) under the mesh's parameters.  Asynchronous on stream. */
 int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* stream);
 
+/* ---- partitioned meshes: halo exchange support -------------------------------------------
+ * A partition of a mesh over several processes (the paper's multi-GPU runs exchange face data
+ * between ranks, Sec. 5.4) is uploaded as its owned elements followed by copies of their face
+ * neighbours owned elsewhere (halo elements, whose outer faces carry DG_BC_OUTFLOW); before each
+ * right-hand side the halo copies are refreshed from their owners, and for Navier-Stokes the
+ * viscous flux is computed, its halo refreshed, and then used (dg_opts.viscous_given).  These
+ * entry points move the data; the transport between processes is the caller's. */
+/* dst [V][n][Np] <- src [V][K][Np] at the elements elems_dev[n] (device int32, each in [0, K);
+ * an entry outside that range is skipped: its slot of dst is left as it was).  Asynchronous on
+ * stream; n = 0 does nothing.  Errors: DG_ERR_INVALID_ARG (NULL with n > 0, V < 1, Np < 1, K < 1). */
+int dg_gather_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np, const int32_t* elems_dev,
+                       int32_t n, double* dst_dev, void* stream);
+/* dst [V][K][Np] at the elements elems_dev[n] <- src [V][n][Np]; same rules as the gather. */
+int dg_scatter_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np, const int32_t* elems_dev,
+                        int32_t n, double* dst_dev, void* stream);
+/* The BR1 viscous flux of q (perfect gas, FP64 form) into the mesh's buffer, and that buffer's
+ * device address and layout ([9][K][Np]: tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, E_x,
+ * E_y, E_z), valid while the mesh lives. */
+int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q_dev, void* stream);
+int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv_dev);
+
 /* Sizes of an uploaded mesh. Any pointer may be NULL. */
 int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp);
 
@@ -237,11 +258,14 @@ int dg_gas_status(dg_gas gas, uint32_t* bits, int reset);
 #define DG_TSEED_MLP 2   /* Newton starts from the gas's trained MLP guess            */
 
 typedef struct {
-  int32_t precision;  /* DG_PREC_*                                                   */
-  int32_t t_seed;     /* DG_TSEED_*                                                  */
-  double t_const;     /* constant Newton seed for DG_TSEED_CONST                     */
-  int32_t reserved[8];
-} dg_opts;            /* NULL = defaults: DG_PREC_FP64, DG_TSEED_INPUT              */
+  int32_t precision;      /* DG_PREC_*                                               */
+  int32_t t_seed;         /* DG_TSEED_*                                              */
+  double t_const;         /* constant Newton seed for DG_TSEED_CONST                 */
+  int32_t viscous_given;  /* FP64 Navier-Stokes: != 0 uses the viscous flux already   */
+                          /* in the mesh's buffer (dg_viscous_flux, then a halo       */
+                          /* exchange) instead of computing it                        */
+  int32_t reserved[7];
+} dg_opts;                /* NULL = defaults: DG_PREC_FP64, DG_TSEED_INPUT          */
 
 /* ---- the hot path ------------------------------------------------------------ */
 

@@ -81,7 +81,8 @@ class dg_batch_case(ctypes.Structure):
 
 
 class dg_opts(ctypes.Structure):
-    _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("reserved", c_int32 * 8)]
+    _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("viscous_given", c_int32),
+                ("reserved", c_int32 * 7)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/dg.h
@@ -99,6 +100,12 @@ SIGNATURES = {
     "dg_mesh_connectivity": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "dg_mesh_set_inflow": (c_int32, [c_void_p, c_void_p, c_int32]),
     "dg_mesh_set_av": (c_int32, [c_void_p, c_void_p]),
+    "dg_gather_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,
+                                     c_void_p]),
+    "dg_scatter_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,
+                                      c_void_p]),
+    "dg_viscous_flux": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_viscous_buffer": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),
     "dg_av_viscosity": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),
     "dg_mesh_set_timing": (c_int32, [c_void_p, c_int32]),

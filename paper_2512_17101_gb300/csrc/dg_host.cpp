@@ -213,7 +213,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
-  if (g.mu > 0) {
+  if (g.mu > 0 && !(opts && opts->viscous_given)) {
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
   }
@@ -403,6 +403,22 @@ int dg_av_viscosity(dg_mesh mesh, const double* q, double* eps, void* stream) {
   if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
   const cudaError_t e = dg::launch_av_sensor(mesh->d, q, eps, (cudaStream_t)stream);
   return e == cudaSuccess ? DG_OK : cuda_fail(e, "smoothness-indicator kernel");
+}
+
+int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q, void* stream) {
+  if (!mesh || !gas || !q) return fail(DG_ERR_INVALID_ARG, "NULL mesh, gas or state");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  if (gas->p.model != DG_GAS_PERFECT || !(gas->p.mu > 0))
+    return fail(DG_ERR_INVALID_ARG, "the viscous pass needs a viscous perfect gas");
+  const cudaError_t e = dg::launch_viscous_flux(mesh->d, gas->p, q, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "viscous flux kernel");
+}
+
+int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv) {
+  if (!mesh || !fv) return fail(DG_ERR_INVALID_ARG, "NULL mesh or output");
+  if (!mesh->d.scratch) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  *fv = mesh->d.scratch;
+  return DG_OK;
 }
 
 int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP, double* geo) {

@@ -161,6 +161,7 @@ class Gas:
                  R_universal=8314.462618, newton_tol=1e-10, newton_max_it=50, Sc=0.0):
         """Sc: Schmidt number of the species diffusion of a viscous NASA-7 mixture."""
         lib = load()
+        self.mu = float(mu)
         d = capi.dg_gas_desc()
         d.mu = mu
         d.Pr = Pr

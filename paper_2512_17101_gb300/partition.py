@@ -1,0 +1,200 @@
+"""Element partitions of a tetrahedral mesh for the multi-process form, and their halo exchange.
+
+The paper runs its largest cases over many GPUs, exchanging face data between the ranks of a
+domain decomposition (§5.4).  Here a rank uploads its owned elements followed by copies of their
+face neighbours owned by other ranks (halo elements; their faces that lead out of the local set
+carry DG_BC_OUTFLOW, so the local mesh is closed; the halo's own right-hand side is never used).
+Before each right-hand side the halo copies are refreshed from their owners; for Navier-Stokes the
+viscous flux is computed, its halo refreshed the same way, and the stage then uses it
+(`dg_opts.viscous_given`).  The library moves the data (`dg_gather_elements`,
+`dg_scatter_elements`); the transport between ranks is a small object with one method,
+`exchange_all(sends, recv_shapes, like)`: `TorchTransport` uses torch.distributed point-to-point
+messages (NCCL on GPUs, gloo on CPUs) for the one partition a process holds, `LocalRouter` hands
+the buffers between partitions held by one process.
+
+Partitioning: contiguous ranges of the element index (for the box meshes of the workloads these
+are slabs across the z direction); the face adjacency comes from the library's own connectivity.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import capi
+from .capi import check, load
+
+OUTFLOW = capi.DG_BC_OUTFLOW
+
+
+@dataclass
+class Partition:
+    rank: int
+    owned: np.ndarray            # global element ids owned by this rank (ascending)
+    halo: np.ndarray             # global ids of the halo elements (ascending)
+    vertices: np.ndarray         # [len(owned) + len(halo)][4][3]
+    face_bc: np.ndarray          # [len(owned) + len(halo)][4]
+    send: dict = field(default_factory=dict)   # rank -> local indices of owned elements it holds as halo
+    recv: dict = field(default_factory=dict)   # rank -> local indices of the halo elements it owns
+
+    @property
+    def local(self) -> np.ndarray:
+        return np.concatenate([self.owned, self.halo])
+
+
+def partition_mesh(vertices, period, N, ref_nodes, nparts, face_bc=None):
+    """The nparts partitions of a mesh (contiguous element ranges), each with its halo and
+    exchange lists.  Send and receive lists between two ranks are in ascending global order, so
+    that they pair up element by element."""
+    from .dg import Mesh
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    K = v.shape[0]
+    if not 1 <= nparts <= K:
+        raise ValueError("need 1 <= nparts <= K")
+    glob = Mesh(v, period, N, ref_nodes, host_only=True, face_bc=face_bc)
+    vmapP, _ = glob.connectivity()
+    Np, Nfp = glob.Np, glob.Nfp
+    first = vmapP[:, ::Nfp]  # [K][4]: a face node's partner, or -code on a boundary face
+    partner = np.where(first >= 0, first // Np, -1)
+    gbc = np.zeros((K, 4), dtype=np.int32) if face_bc is None else np.asarray(face_bc, dtype=np.int32)
+    owner = (np.arange(K, dtype=np.int64) * nparts) // K
+    parts = []
+    for r in range(nparts):
+        owned = np.flatnonzero(owner == r)
+        nbs = partner[owned].ravel()
+        halo = np.setdiff1d(np.unique(nbs[nbs >= 0]), owned)
+        local = np.concatenate([owned, halo])
+        in_local = np.zeros(K, dtype=bool)
+        in_local[local] = True
+        fbc = gbc[local].copy()
+        hp = partner[halo]  # [H][4]
+        leaves = (hp >= 0) & ~in_local[np.maximum(hp, 0)]
+        fbc[len(owned):][leaves] = OUTFLOW  # halo faces leading out of the local set
+        parts.append(Partition(rank=r, owned=owned, halo=halo, vertices=np.ascontiguousarray(v[local]),
+                               face_bc=np.ascontiguousarray(fbc, dtype=np.int32)))
+    for p in parts:
+        pos = {int(g): i for i, g in enumerate(p.local)}
+        for s in range(nparts):
+            if s == p.rank:
+                continue
+            mine_there = np.intersect1d(p.owned, parts[s].halo)   # ascending
+            theirs_here = p.halo[owner[p.halo] == s]               # ascending
+            if len(mine_there):
+                p.send[s] = np.array([pos[int(g)] for g in mine_there], dtype=np.int32)
+            if len(theirs_here):
+                p.recv[s] = np.array([pos[int(g)] for g in theirs_here], dtype=np.int32)
+    return parts
+
+
+class TorchTransport:
+    """Point-to-point exchange through torch.distributed (one message each way per neighbour),
+    for the one partition this process holds."""
+
+    def __init__(self, group=None):
+        self.group = group
+
+    def exchange_all(self, sends: list, recv_shapes: list, like) -> list:
+        import torch
+        import torch.distributed as dist
+        assert len(sends) == 1, "a process holds one partition"
+        out = {s: torch.empty(shape, dtype=like.dtype, device=like.device) for s, shape in recv_shapes[0].items()}
+        reqs = [dist.isend(buf.contiguous(), dst=s, group=self.group) for s, buf in sends[0].items()]
+        reqs += [dist.irecv(out[s], src=s, group=self.group) for s in out]
+        for r in reqs:
+            r.wait()
+        return [out]
+
+
+class LocalRouter:
+    """Exchange among partitions held by one process (each message is the sender's buffer)."""
+
+    def exchange_all(self, sends: list, recv_shapes: list, like) -> list:
+        out = [dict() for _ in sends]
+        for r, sd in enumerate(sends):
+            for s, buf in sd.items():
+                out[s][r] = buf
+        for r, shapes in enumerate(recv_shapes):
+            for s, shape in shapes.items():
+                assert tuple(out[r][s].shape) == tuple(shape), "send and receive lists do not pair up"
+        return out
+
+
+class HaloExchange:
+    """Refreshes the halo of [V][K_local][Np] device arrays of one partition."""
+
+    def __init__(self, part: Partition, Np: int, device):
+        import torch
+        self.part, self.Np = part, Np
+        self.K = len(part.local)
+        self.send = {s: torch.tensor(ix, device=device) for s, ix in part.send.items()}
+        self.recv = {s: torch.tensor(ix, device=device) for s, ix in part.recv.items()}
+
+    def pack(self, ptr: int, V: int, like) -> dict:
+        import torch
+        out = {}
+        for s, ix in self.send.items():
+            buf = torch.empty((V, len(ix), self.Np), dtype=torch.float64, device=like.device)
+            check(load().dg_gather_elements(ctypes.c_void_p(ptr), V, self.K, self.Np, ctypes.c_void_p(ix.data_ptr()),
+                                            len(ix), ctypes.c_void_p(buf.data_ptr()), None))
+            out[s] = buf
+        return out
+
+    def unpack(self, ptr: int, V: int, received: dict):
+        for s, buf in received.items():
+            ix = self.recv[s]
+            check(load().dg_scatter_elements(ctypes.c_void_p(buf.data_ptr()), V, self.K, self.Np,
+                                             ctypes.c_void_p(ix.data_ptr()), len(ix), ctypes.c_void_p(ptr), None))
+
+    def recv_shapes(self, V: int) -> dict:
+        return {s: (V, len(ix), self.Np) for s, ix in self.recv.items()}
+
+
+def viscous_buffer(mesh) -> int:
+    p = ctypes.c_void_p()
+    check(load().dg_mesh_viscous_buffer(mesh.handle, ctypes.byref(p)))
+    return p.value
+
+
+@dataclass
+class RankState:
+    """One partition on this process: its mesh, halo exchange, state and RK work buffers."""
+    mesh: object
+    halo: HaloExchange
+    q: object
+    work: tuple
+
+
+def _refresh(ranks, transport, ptrs, V):
+    like = ranks[0].q
+    got = transport.exchange_all([r.halo.pack(p, V, like) for r, p in zip(ranks, ptrs)],
+                                 [r.halo.recv_shapes(V) for r in ranks], like)
+    for r, p, g in zip(ranks, ptrs, got):
+        r.halo.unpack(p, V, g)
+
+
+def partitioned_lsrk4_step(ranks: list, gas, transport, dt):
+    """One LSRK4 step of the partitions held by this process (FP64 form).  Before every stage
+    the halos of the states are refreshed; with viscosity each partition's viscous flux is
+    computed, its halo refreshed, and the stage uses it."""
+    from .dg import _opts, dg_rk_stage
+    V = ranks[0].q.shape[0]
+    viscous = gas.mu > 0
+    opts = _opts()
+    if viscous:
+        opts.viscous_given = 1
+    cur = [r.q for r in ranks]
+    nxt = [r.work[0] for r in ranks]
+    for s in range(5):
+        _refresh(ranks, transport, [c.data_ptr() for c in cur], V)
+        if viscous:
+            for r, c in zip(ranks, cur):
+                check(load().dg_viscous_flux(r.mesh.handle, gas.handle, ctypes.c_void_p(c.data_ptr()), None))
+            _refresh(ranks, transport, [viscous_buffer(r.mesh) for r in ranks], 9)
+        for r, c, n in zip(ranks, cur, nxt):
+            dg_rk_stage(r.mesh, gas, s, dt, c, n, r.work[1], opts=opts)
+        cur, nxt = nxt, cur
+    for r, c in zip(ranks, cur):
+        if c is not r.q:
+            r.q.copy_(c)

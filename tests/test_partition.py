@@ -1,0 +1,109 @@
+"""Host logic of the partitioned form (paper_2512_17101_gb300/partition.py), on CPU: every
+element is owned once, a partition holds every face neighbour of its owned elements, send and
+receive lists pair up element by element, the right-hand side of a partition (the oracle's, on
+the partition's mesh with its halo filled) equals the global one at its owned elements, and the
+torch.distributed transport delivers the halo between two gloo ranks."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from tests._oracle_case import Disc
+from workloads import box_mesh, equispaced_tet_nodes, isentropic_vortex, uniform_perturbation
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    from paper_2512_17101_gb300 import capi
+    if not os.path.exists(capi.LIB_PATH):
+        __graft_entry__.build()
+    return capi.load()
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 5])
+def test_partition_invariants(lib, nparts):
+    from paper_2512_17101_gb300.partition import partition_mesh
+    from paper_2512_17101_gb300 import dg
+    N = 2
+    v, per = box_mesh((3, 2, 2), 1.0)
+    parts = partition_mesh(v, per, N, equispaced_tet_nodes(N), nparts)
+    owned = np.concatenate([p.owned for p in parts])
+    assert np.array_equal(np.sort(owned), np.arange(v.shape[0]))
+    for p in parts:
+        # the local mesh is closed (the library accepts it) and holds every neighbour of an owned element
+        m = dg.Mesh(p.vertices, per, N, equispaced_tet_nodes(N), host_only=True, face_bc=p.face_bc)
+        vmapP, _ = m.connectivity()
+        own_faces = vmapP[:len(p.owned)]
+        assert np.all(own_faces >= 0)
+        for s, ix in p.send.items():
+            theirs = parts[s].local[parts[s].recv[p.rank]]
+            assert np.array_equal(p.local[ix], theirs)
+
+
+def test_partition_rhs_matches_global_at_owned_elements(lib):
+    """Euler, the oracle on each partition's own mesh with the halo filled from the global state."""
+    import oracle.boundary as bd
+    from oracle.euler import rhs_strong
+    from oracle.thermo import PerfectGas
+    from paper_2512_17101_gb300.partition import partition_mesh
+    N = 2
+    v, per = box_mesh((4, 2, 2), 1.0)
+    g = Disc(v, per, N)
+    q = uniform_perturbation(isentropic_vortex(g.xyz, 0.0, period=per), 1e-3)
+    gas = PerfectGas(1.4, 1.0)
+    want = rhs_strong(g.ref, g.geo, g.conn, q, gas)
+    for p in partition_mesh(v, per, N, equispaced_tet_nodes(N), 3):
+        d = Disc(p.vertices, per, N, face_bc=p.face_bc)
+        r = bd.rhs_euler_bc(d.ref, d.geo, d.conn, q[:, p.local], gas)
+        no = len(p.owned)
+        assert np.abs(r[:, :no] - want[:, p.owned]).max() <= 1e-13 * np.abs(want).max()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _exchange_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ok = False
+    try:
+        from paper_2512_17101_gb300.partition import TorchTransport, partition_mesh
+        N, Np = 1, 4
+        v, per = box_mesh((4, 2, 2), 1.0)
+        parts = partition_mesh(v, per, N, equispaced_tet_nodes(N), world)
+        p = parts[rank]
+        rng = np.random.default_rng(0)
+        glob = rng.standard_normal((5, v.shape[0], Np))  # every rank knows the global field here
+        local = glob[:, p.local].copy()
+        local[:, len(p.owned):] = np.nan  # the halo before the exchange
+        sends = {s: torch.from_numpy(local[:, ix]) for s, ix in p.send.items()}
+        shapes = {s: (5, len(ix), Np) for s, ix in p.recv.items()}
+        got = TorchTransport().exchange_all([sends], [shapes], torch.zeros(1, dtype=torch.float64))[0]
+        for s, buf in got.items():
+            local[:, p.recv[s]] = buf.numpy()
+        ok = bool(np.array_equal(local, glob[:, p.local]))
+    finally:
+        out.put((rank, ok))
+        dist.destroy_process_group()
+
+
+def test_gloo_halo_exchange_two_ranks(lib):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    assert res == {0: True, 1: True}
