@@ -468,6 +468,9 @@ def gpu_arm(args, cfg, world, rank, local):
         bnd = boundary_form(args, local, periodic)
         avf = av_form(args, local)
         mixns = mixture_ns_form(args, local)
+    partf = None
+    if rank == 0 and not args.no_partitioned:
+        partf = partitioned_form(args, local, runs["fp64"]["ms"] if cfg.name == "ns_viscous" else None)
     launches = sum(v["launches"] for v in per_head.values())
     if rank == 0:
         line = {
@@ -479,7 +482,8 @@ def gpu_arm(args, cfg, world, rank, local):
             "clocks": runs[head]["clocks"], "other_form": other_line, "mixed_error": mixed_err,
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
             "paper_context": PAPER_CONTEXT,
-            "hex_advection_form": hexadv, "hex_shock_form": hexshock, "boundary_form": bnd, "av_form": avf, "mixture_ns_form": mixns, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "hex_advection_form": hexadv, "hex_shock_form": hexshock, "boundary_form": bnd, "av_form": avf, "mixture_ns_form": mixns,
+            "partitioned_form": partf, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
 
@@ -1059,6 +1063,67 @@ def hex_advection_form(args, local):
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
+def partitioned_form(args, local, whole_ms=None):
+    """The Navier-Stokes workload (24^3 x 6 tets, N = 3) split into two element partitions (z
+    slabs, each with its halo) held on one device: before every stage the halos of the state and
+    of the BR1 viscous flux are refreshed through the library's gather / scatter kernels, handed
+    over by the in-process router (between GPUs the same buffers would travel as torch.distributed
+    point-to-point messages).  RK4 steps with CUDA events against the same steps on the whole
+    mesh; owned DOFs only count toward the value."""
+    import numpy as np
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from paper_2512_17101_gb300.partition import (HaloExchange, LocalRouter, RankState, partition_mesh,
+                                                  partitioned_lsrk4_step)
+    from workloads.configs import build_case, get_config
+
+    cfg = get_config("ns_viscous")
+    dev = torch.device("cuda", local)
+    case = build_case(cfg)
+    g = cfg.gas
+    gas = dg.Gas(model="perfect", gamma=g.gamma, R=g.R, mu=g.mu, Pr=g.Pr)
+    parts = partition_mesh(case["vertices"], case["period"], cfg.N, case["ref_nodes"], 2)
+    ranks = []
+    for p in parts:
+        m = dg.Mesh(p.vertices, case["period"], cfg.N, case["ref_nodes"], face_bc=p.face_bc)
+        q = torch.tensor(np.ascontiguousarray(case["q"][:, p.local]), device=dev)
+        ranks.append(RankState(m, HaloExchange(p, m.Np, dev), q, (torch.empty_like(q), torch.zeros_like(q))))
+    q0 = [r.q.clone() for r in ranks]
+    router = LocalRouter()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        partitioned_lsrk4_step(ranks, gas, router, cfg.dt)
+    for r, q in zip(ranks, q0):
+        r.q.copy_(q)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        partitioned_lsrk4_step(ranks, gas, router, cfg.dt)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    for r in ranks:
+        if r.mesh.status() != 0:
+            raise SystemExit("status flags set in the partitioned run")
+    ms = total / max(1, args.steps)
+    halo = sum(len(p.halo) for p in parts)
+    per_stage = sum(len(ix) for p in parts for ix in p.recv.values()) * cfg.Np * 8 * (5 + (9 if g.mu > 0 else 0))
+    out = {"workload": f"{cfg.name} in 2 partitions on one device: {cfg.description}", "K": cfg.K, "N": cfg.N,
+           "dtype": "f64", "steps": max(1, args.steps), "ms_per_step": ms,
+           "value": cfg.dofs * 5 / (ms * 1e-3), "unit": "DOF-updates/s (owned DOFs)",
+           "halo_elements": halo, "halo_fraction": halo / cfg.K,
+           "exchange_bytes_per_step": 5 * per_stage,
+           "transport": "in-process router (no copy); the bytes are what each stage moves between partitions",
+           "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
+    if whole_ms:
+        out["ms_per_step_whole_mesh"] = whole_ms
+        out["overhead"] = ms / whole_ms - 1.0
+    return out
+
+
 def batched_form(args, local):
     """The batched workload (64 uneven cases, orders 1..4, half Euler / half NS, mixed precision):
     one graph launch per RK4 step, against stepping the same cases one by one."""
@@ -1123,6 +1188,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
     ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel, artificial-viscosity and viscous-mixture sections")
+    ap.add_argument("--no-partitioned", action="store_true", help="skip the two-partition section")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="form timed for the headline value (the other form is reported beside it)")
     args = ap.parse_args()
