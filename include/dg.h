@@ -173,6 +173,28 @@ int dg_scatter_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np,
 int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q_dev, void* stream);
 int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv_dev);
 
+/* ---- global reductions: conservation integrals and the stability rate -------------------------
+ * The two reductions a distributed run needs beside the halo exchange: the integrals of the
+ * conserved variables (conservation diagnostics) and the largest stability rate, from which the
+ * caller takes the time step dt = CFL / rate.  Both reduce over the first K_count elements of the
+ * mesh (a partition's owned elements come first), run a fixed grid whose partials are combined in
+ * a fixed order (bitwise reproducible), write device memory and are asynchronous on stream; the
+ * caller combines the values of several ranks (sum, max).  The paper fixes neither: the
+ * definitions are stated with each call.  Errors: DG_ERR_INVALID_ARG (NULL pointers, a host-only
+ * mesh, K_count outside [0, K], nvar outside 1..5+DG_MAX_SPECIES). */
+/* out_dev[v] <- integral of q_v over the first K_count elements, v < nvar:
+ * sum_e J_e sum_i w_i q[v][e][i], w_i the integral of the i-th nodal basis function over the
+ * reference tetrahedron (exact for the element's polynomial).  q_dev [>= nvar][K][Np]. */
+int dg_integrals(dg_mesh mesh, const double* q_dev, int32_t nvar, int64_t K_count, double* out_dev, void* stream);
+/* out_dev[0] <- max over the first K_count elements and their nodes of
+ *   (N+1)^2/2 F_e (|u| + c) + (N+1)^4/4 F_e^2 nu,   F_e = max over the element's faces of Fscale,
+ *   nu = (mu / rho) max(4/3, gamma / Pr) (0 for an inviscid gas),
+ * the nodal-DG step estimate (advective (N+1)^2/h, diffusive (N+1)^4/h^2, 1/h read as F_e/2);
+ * 0 for K_count = 0.  A node with rho <= 0 or p <= 0 gives +infinity and sets
+ * DG_STATUS_NONPHYSICAL in the mesh status.  q_dev [5][K][Np]; perfect gas only
+ * (DG_ERR_UNSUPPORTED otherwise). */
+int dg_max_rate(dg_mesh mesh, dg_gas gas, const double* q_dev, int64_t K_count, double* out_dev, void* stream);
+
 /* Sizes of an uploaded mesh. Any pointer may be NULL. */
 int dg_mesh_info(dg_mesh mesh, int32_t* K, int32_t* N, int32_t* Np, int32_t* Nfp);
 

@@ -105,6 +105,8 @@ SIGNATURES = {
     "dg_scatter_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,
                                       c_void_p]),
     "dg_viscous_flux": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_integrals": (c_int32, [c_void_p, c_void_p, c_int32, ctypes.c_int64, c_void_p, c_void_p]),
+    "dg_max_rate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
     "dg_mesh_viscous_buffer": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),
     "dg_av_viscosity": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_status": (c_int32, [c_void_p, ctypes.POINTER(c_uint32), c_int32]),

@@ -49,6 +49,8 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.av_eps);
   cudaFree(d.av_sig);
   cudaFree(d.mix_fv);
+  cudaFree(d.wq);
+  cudaFree(d.diag);
   d = dg::MeshDev();
 }
 
@@ -302,6 +304,8 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);
   if (e == cudaSuccess) e = upload(&d.modal, m->ops.modal.data(), m->ops.modal.size());
+  if (e == cudaSuccess) e = upload(&d.wq, m->ops.wq.data(), m->ops.wq.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.diag, dg::kDiagPartialBytes);
   d.ntop = m->ops.ntop;
   if (e != cudaSuccess) {
     free_mesh_device(d);

@@ -24,6 +24,7 @@ struct RefOps {
   std::vector<double> modal;       // [Np][Np]: orthonormal (PKDO) coefficients from nodal values,
                                    // the ntop modes of total degree N in the last rows
   int ntop = 0;
+  std::vector<double> wq;          // [Np]: integral of each nodal basis function over the element
 };
 
 // Reference operators of order N on the given nodes (refops.cpp).
@@ -93,6 +94,8 @@ struct MeshDev {
                                // mixed form node records (dg_mixed.cuh NodeTables) or mixture tables
   float* geo32 = nullptr;      // [K][DG_GEO_STRIDE] float copy of geo (mixed form)
   unsigned* status = nullptr;  // device status word
+  double* wq = nullptr;        // [Np] reference quadrature weights (mass-matrix row sums)
+  double* diag = nullptr;      // per-block partials of the global reductions (k_diag.cu)
 };
 
 // LSRK4 coefficients (Carpenter & Kennedy 1994, five stages, 2N storage).
@@ -127,6 +130,10 @@ cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q,
 cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// Global reductions (k_diag.cu): a fixed grid of kDiagBlocks blocks writes per-block partials
+// into MeshDev::diag, one block combines them in a fixed order.
+constexpr int kDiagBlocks = 512, kDiagThreads = 256, kDiagMaxV = 5 + DG_MAX_SPECIES;
+constexpr size_t kDiagPartialBytes = sizeof(double) * kDiagBlocks * kDiagMaxV;
 // Outputs of the mixed-precision form that the temperature solve also writes (rec null: none):
 // the node records [n][4] float4 {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, c},
 // {rho Y_1..4}, {rho Y_5..8}; rho <= 0 or p <= 0 sets DG_STATUS_NONPHYSICAL in *status.

@@ -252,6 +252,18 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err) {
   for (int a = 0; a <= N; ++a)
     for (int b = 0; a + b <= N; ++b)
       for (int c = 0; a + b + c <= N; ++c) deg.push_back(a + b + c);
+  // quadrature weights w = M 1 with M = Vo^-T Vo^-1: the integral of each nodal basis function
+  out.wq.assign(Np, 0.0);
+  {
+    std::vector<ld> c(Np, 0);  // Vo^-1 1: orthonormal coefficients of the constant 1
+    for (int m = 0; m < Np; ++m)
+      for (int j = 0; j < Np; ++j) c[m] += Voi[m * Np + j];
+    for (int i = 0; i < Np; ++i) {
+      ld w = 0;
+      for (int m = 0; m < Np; ++m) w += Voi[m * Np + i] * c[m];
+      out.wq[i] = (double)w;
+    }
+  }
   out.modal.clear();
   out.ntop = 0;
   for (int pass = 0; pass < 2; ++pass)

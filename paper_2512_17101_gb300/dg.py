@@ -290,6 +290,38 @@ def dg_split_to_float_pair(x, hi, lo, stream=None):
                                         _dptr(lo, torch.float32, "lo"), x.numel(), _stream_ptr(stream)))
 
 
+def dg_integrals(mesh: Mesh, q, nvar=None, K_count=None, out=None, stream=None):
+    """[nvar] CUDA float64: the integrals of q's variables over the first K_count elements."""
+    import torch
+    nvar = q.shape[0] if nvar is None else int(nvar)
+    K_count = mesh.K if K_count is None else int(K_count)
+    if q.dim() != 3 or tuple(q.shape[1:]) != (mesh.K, mesh.Np) or q.shape[0] < nvar:
+        raise ValueError("q must be [>= nvar][K][Np]")
+    if out is None:
+        out = torch.empty(nvar, dtype=torch.float64, device=q.device)
+    check(load().dg_integrals(mesh.handle, _dptr(q, torch.float64, "q"), nvar, K_count,
+                              _dptr(out, torch.float64, "out"), _stream_ptr(stream)))
+    return out
+
+
+def dg_max_rate(mesh: Mesh, gas: Gas, q, K_count=None, out=None, stream=None):
+    """[1] CUDA float64: the largest stability rate over the first K_count elements."""
+    import torch
+    K_count = mesh.K if K_count is None else int(K_count)
+    if q.dim() != 3 or tuple(q.shape[1:]) != (mesh.K, mesh.Np) or q.shape[0] < 5:
+        raise ValueError("q must be [5][K][Np]")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=q.device)
+    check(load().dg_max_rate(mesh.handle, gas.handle, _dptr(q, torch.float64, "q"), K_count,
+                             _dptr(out, torch.float64, "out"), _stream_ptr(stream)))
+    return out
+
+
+def stable_dt(mesh: Mesh, gas: Gas, q, cfl, stream=None) -> float:
+    """CFL / (largest stability rate); reads the rate back to the host."""
+    return float(cfl) / float(dg_max_rate(mesh, gas, q, stream=stream).item())
+
+
 def dg_rk_stage_noalloc(tables, gas_desc, stage, dt, q_in, q_out, k, status, stream=None):
     """Allocation-free viscous stage on caller-owned tables.
 

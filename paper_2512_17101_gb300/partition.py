@@ -8,7 +8,8 @@ Before each right-hand side the halo copies are refreshed from their owners; for
 viscous flux is computed, its halo refreshed the same way, and the stage then uses it
 (`dg_opts.viscous_given`).  The library moves the data (`dg_gather_elements`,
 `dg_scatter_elements`); the transport between ranks is a small object with one method,
-`exchange_all(sends, recv_shapes, like)`: `TorchTransport` uses torch.distributed point-to-point
+`exchange_all(sends, recv_shapes, like)`, and one more for the global reductions,
+`reduce_all(values, op)` (op "sum" or "max"): `TorchTransport` uses torch.distributed point-to-point
 messages (NCCL on GPUs, gloo on CPUs) for the one partition a process holds, `LocalRouter` hands
 the buffers between partitions held by one process.
 
@@ -106,6 +107,13 @@ class TorchTransport:
             r.wait()
         return [out]
 
+    def reduce_all(self, values: list, op: str) -> list:
+        import torch.distributed as dist
+        assert len(values) == 1, "a process holds one partition"
+        t = values[0].clone()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM if op == "sum" else dist.ReduceOp.MAX, group=self.group)
+        return [t]
+
 
 class LocalRouter:
     """Exchange among partitions held by one process (each message is the sender's buffer)."""
@@ -119,6 +127,12 @@ class LocalRouter:
             for s, shape in shapes.items():
                 assert tuple(out[r][s].shape) == tuple(shape), "send and receive lists do not pair up"
         return out
+
+    def reduce_all(self, values: list, op: str) -> list:
+        import torch
+        st = torch.stack(values)
+        t = st.sum(dim=0) if op == "sum" else st.max(dim=0).values
+        return [t.clone() for _ in values]
 
 
 class HaloExchange:
@@ -198,3 +212,18 @@ def partitioned_lsrk4_step(ranks: list, gas, transport, dt):
     for r, c in zip(ranks, cur):
         if c is not r.q:
             r.q.copy_(c)
+
+
+def partitioned_integrals(ranks: list, transport):
+    """The integrals of the conserved variables over the whole mesh (each partition's owned
+    elements, then summed across partitions); one device tensor [V] per partition held here."""
+    from .dg import dg_integrals
+    vals = [dg_integrals(r.mesh, r.q, K_count=len(r.halo.part.owned)) for r in ranks]
+    return transport.reduce_all(vals, "sum")
+
+
+def partitioned_stable_dt(ranks: list, gas, transport, cfl) -> float:
+    """CFL / (largest stability rate over every partition's owned elements)."""
+    from .dg import dg_max_rate
+    vals = [dg_max_rate(r.mesh, gas, r.q, K_count=len(r.halo.part.owned)) for r in ranks]
+    return float(cfl) / float(transport.reduce_all(vals, "max")[0].item())

@@ -2,7 +2,7 @@
 element is owned once, a partition holds every face neighbour of its owned elements, send and
 receive lists pair up element by element, the right-hand side of a partition (the oracle's, on
 the partition's mesh with its halo filled) equals the global one at its owned elements, and the
-torch.distributed transport delivers the halo between two gloo ranks."""
+torch.distributed transport delivers the halo between two gloo ranks and reduces across them."""
 
 import os
 import socket
@@ -90,6 +90,10 @@ def _exchange_worker(rank, world, port, out):
         for s, buf in got.items():
             local[:, p.recv[s]] = buf.numpy()
         ok = bool(np.array_equal(local, glob[:, p.local]))
+        t = TorchTransport()
+        v = torch.tensor([1.0 + rank, 10.0 * rank], dtype=torch.float64)
+        ok = ok and t.reduce_all([v], "sum")[0].tolist() == [3.0, 10.0]
+        ok = ok and t.reduce_all([v], "max")[0].tolist() == [2.0, 10.0] and v.tolist() == [1.0 + rank, 10.0 * rank]
     finally:
         out.put((rank, ok))
         dist.destroy_process_group()
