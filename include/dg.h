@@ -217,7 +217,7 @@ int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset);
 #define DG_KERNEL_VISCOUS 0     /* BR1 gradient + viscous flux pass            */
 #define DG_KERNEL_RHS 1         /* fused right-hand side (+ RK stage)          */
 #define DG_KERNEL_TEMPERATURE 2 /* Newton temperature solve inside dg_rhs/stage */
-#define DG_KERNEL_PRIMS 3       /* per-node pressure / temperature pass (mixed form) */
+#define DG_KERNEL_PRIMS 3       /* per-node primitives pass (1/rho, p, c; mixed form: + T, records) */
 #define DG_KERNEL_AV 4          /* artificial viscosity: indicator + flux passes  */
 #define DG_NUM_KERNELS 5
 

@@ -49,6 +49,7 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.av_eps);
   cudaFree(d.av_sig);
   cudaFree(d.mix_fv);
+  cudaFree(d.prim);
   cudaFree(d.wq);
   cudaFree(d.diag);
   d = dg::MeshDev();
@@ -215,6 +216,10 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
+  if (g.model == DG_GAS_PERFECT) {  // (1/rho, p, c) once per node for the viscous and right-hand-side kernels
+    e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_fp64(m, g, q, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "primitives kernel");
+  }
   if (g.mu > 0 && !(opts && opts->viscous_given)) {
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
@@ -300,6 +305,7 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
     e = upload(&d.geo32, g32.data(), g32.size());
   }
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.scratch, sizeof(double) * 10 * (size_t)d.K * Np);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.prim, sizeof(double) * 3 * (size_t)d.K * Np);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d.status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dg::build_tc_ops(d, m->ops);
@@ -414,8 +420,9 @@ int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q, void* stream) {
   if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
   if (gas->p.model != DG_GAS_PERFECT || !(gas->p.mu > 0))
     return fail(DG_ERR_INVALID_ARG, "the viscous pass needs a viscous perfect gas");
-  const cudaError_t e = dg::launch_viscous_flux(mesh->d, gas->p, q, (cudaStream_t)stream);
-  return e == cudaSuccess ? DG_OK : cuda_fail(e, "viscous flux kernel");
+  cudaError_t e = dg::launch_prims_fp64(mesh->d, gas->p, q, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = dg::launch_viscous_flux(mesh->d, gas->p, q, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "viscous flux kernels");
 }
 
 int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv) {

@@ -96,6 +96,8 @@ struct MeshDev {
   unsigned* status = nullptr;  // device status word
   double* wq = nullptr;        // [Np] reference quadrature weights (mass-matrix row sums)
   double* diag = nullptr;      // per-block partials of the global reductions (k_diag.cu)
+  double* prim = nullptr;      // FP64 form, perfect gas: [3][K][Np] (1/rho, p, c) of the state being
+                               // differentiated, written by the primitives pass before each stage
 };
 
 // LSRK4 coefficients (Carpenter & Kennedy 1994, five stages, 2N storage).
@@ -130,6 +132,9 @@ cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q,
 cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// Per-node (1/rho, p, c) of a perfect-gas state into m.prim (k_ns.cu); the FP64 viscous and
+// right-hand-side kernels of the perfect gas read them.
+cudaError_t launch_prims_fp64(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Global reductions (k_diag.cu): a fixed grid of kDiagBlocks blocks writes per-block partials
 // into MeshDev::diag, one block combines them in a fixed order.
 constexpr int kDiagBlocks = 512, kDiagThreads = 256, kDiagMaxV = 5 + DG_MAX_SPECIES;

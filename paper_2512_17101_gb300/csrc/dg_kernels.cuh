@@ -122,11 +122,15 @@ __device__ __forceinline__ void ghost_state(int code, const double* qm, double n
 //   RK == false: out = rhs
 //   RK == true : k <- a k + dt rhs (k read only if a != 0), out = q + b k
 // V is the compile-time maximum of variables; nvar (runtime) <= V are used.
+// prim (perfect gas; may be null): [3][K][Np] = (1/rho, p, c) of q per node, evaluated once by
+// prims_fp64_kernel instead of at every node and at both traces of every face node here; null:
+// evaluated here.
 // ---------------------------------------------------------------------------------------------
 template <int N, int V, int PHYS, bool RK>
 __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* __restrict__ q, double* __restrict__ out, double* __restrict__ kreg,
-    const double* __restrict__ Tg, const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g,
+    const double* __restrict__ Tg, const double* __restrict__ prim, const double* __restrict__ ops_g,
+    const int32_t* __restrict__ fmask_g,
     const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
     const double* __restrict__ av_g, const double* __restrict__ av_eps, unsigned* __restrict__ status,
     const GasParams gp, const BcParams bc, const int K, const int nvar, const double a, const double b,
@@ -172,10 +176,16 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     double qv[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) qv[v] = v < nvar ? sQ[v * NODES + tid] : 0.0;
-    const double ir = 1.0 / qv[0];
-    double p, c;
-    thermo<PHYS, V>(gp, qv, ir, is_mix(PHYS) ? sT[tid] : 0.0, p, c);
-    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    double ir, p;
+    if (!is_mix(PHYS) && prim) {  // the primitives pass has checked rho and p
+      ir = prim[base + tid];
+      p = prim[KNp + base + tid];
+    } else {
+      double c;
+      ir = 1.0 / qv[0];
+      thermo<PHYS, V>(gp, qv, ir, is_mix(PHYS) ? sT[tid] : 0.0, p, c);
+      if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    }
     const double vel[3] = {qv[1] * ir, qv[2] * ir, qv[3] * ir};
     double F[3][V];
 #pragma unroll
@@ -236,10 +246,26 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
       qp[v] = v < nvar ? q[v * KNp + Pn] : 0.0;
     }
     if (P < 0) ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
-    const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
-    double pm, cm, pp, cp;
-    thermo<PHYS, V>(gp, qm, irm, is_mix(PHYS) ? sT[own] : 0.0, pm, cm);
-    thermo<PHYS, V>(gp, qp, irp, is_mix(PHYS) ? Tg[Pn] : 0.0, pp, cp);
+    double irm, irp, pm, cm, pp, cp;
+    if (!is_mix(PHYS) && prim) {
+      const size_t gM = base + own;
+      irm = prim[gM];
+      pm = prim[KNp + gM];
+      cm = prim[2 * KNp + gM];
+      if (P >= 0) {
+        irp = prim[Pn];
+        pp = prim[KNp + Pn];
+        cp = prim[2 * KNp + Pn];
+      } else {  // a ghost state
+        irp = 1.0 / qp[0];
+        thermo<PHYS, V>(gp, qp, irp, 0.0, pp, cp);
+      }
+    } else {
+      irm = 1.0 / qm[0];
+      irp = 1.0 / qp[0];
+      thermo<PHYS, V>(gp, qm, irm, is_mix(PHYS) ? sT[own] : 0.0, pm, cm);
+      thermo<PHYS, V>(gp, qp, irp, is_mix(PHYS) ? Tg[Pn] : 0.0, pp, cp);
+    }
     if (P < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
     const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
     const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
@@ -391,12 +417,14 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
 //   grad_d w = sum_a (dr_a/dx_d) D_a w + sum_f n_d,f LIFT_f (Fscale (w+ - w-)/2)
 //   out[9][K][Np] = (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, Q_x, Q_y, Q_z),
 //   Q_d = sum_i u_i tau_id + kappa dT/dx_d.
+// prim (may be null): the per-node (1/rho, p, c) of q, as for rhs_kernel.
 // ---------------------------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
-    const double* __restrict__ q, double* __restrict__ fv_out, const double* __restrict__ ops_g,
-    const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP,
-    unsigned* __restrict__ status, const GasParams gp, const BcParams bc, const int K) {
+    const double* __restrict__ q, double* __restrict__ fv_out, const double* __restrict__ prim,
+    const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g,
+    const int32_t* __restrict__ vmapP, unsigned* __restrict__ status, const GasParams gp, const BcParams bc,
+    const int K) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   constexpr int W = 5;
@@ -419,12 +447,19 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
   for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)e0 * GS + i];
   const double gm1 = gp.gamma - 1.0, iR = 1.0 / gp.R;
   if (tid < nn) {
-    double qv[5];
+    double qv[4];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
-    const double ir = 1.0 / qv[0];
-    const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
-    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    for (int v = 0; v < 4; ++v) qv[v] = q[v * KNp + base + tid];
+    double ir, p;
+    if (prim) {
+      ir = prim[base + tid];
+      p = prim[KNp + base + tid];
+    } else {
+      const double E = q[4 * KNp + base + tid];
+      ir = 1.0 / qv[0];
+      p = gm1 * (E - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
+      if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    }
 #pragma unroll
     for (int v = 0; v < 4; ++v) sW[v * NODES + tid] = qv[v];
     sW[4 * NODES + tid] = p * ir * iR;
@@ -447,8 +482,14 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
       for (int v = 0; v < 5; ++v) qm[v] = qp[v];
       ghost_state<5>(-P, qm, G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f], bc, 5, qp);
     }
-    const double irp = 1.0 / qp[0];
-    const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+    double irp, pp;
+    if (prim && P >= 0) {
+      irp = prim[Pn];
+      pp = prim[KNp + Pn];
+    } else {
+      irp = 1.0 / qp[0];
+      pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+    }
     const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
     const double hf = 0.5 * fs;
 #pragma unroll
@@ -501,7 +542,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
 #pragma unroll
         for (int v = 0; v < W; ++v) grad[d][v] = fma(nf[d], lf[v], grad[d][v]);
     }
-    const double rho = sW[tid], ir = 1.0 / rho;
+    const double ir = prim ? prim[base + tid] : 1.0 / sW[tid];  // reloaded: not held across the passes
     const double u[3] = {sW[NODES + tid] * ir, sW[2 * NODES + tid] * ir, sW[3 * NODES + tid] * ir};
     double du[3][3];  // du[i][d] = d u_i / d x_d
 #pragma unroll
@@ -559,7 +600,8 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.ops, m.fmask, m.geo, m.vmapP,
+  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, is_mix(PHYS) ? nullptr : m.prim, m.ops,
+                                                           m.fmask, m.geo, m.vmapP,
                                                            PHYS == MIXTURE_NS ? m.mix_fv : m.scratch,
                                                            m.av_sig, m.av_eps, m.status, g, m.bc, m.K, nvar, a, b,
                                                            dt);

@@ -10,6 +10,28 @@ cudaError_t launch_rhs_ns(const MeshDev& m, const GasParams& g, const double* q,
 }
 
 namespace {
+
+// Per-node primitives of a perfect gas for the FP64 kernels, once per node:
+// prim[0][n] = 1/rho, prim[1][n] = p = (gamma - 1)(rho E - |rho u|^2 / (2 rho)), prim[2][n] = c =
+// sqrt(gamma p / rho); a node with rho <= 0 or p <= 0 sets DG_STATUS_NONPHYSICAL.
+constexpr int kPrimThreads = 256;
+__global__ void __launch_bounds__(kPrimThreads) prims_fp64_kernel(const double* __restrict__ q,
+                                                                  double* __restrict__ prim, const int64_t n,
+                                                                  const double gamma,
+                                                                  unsigned* __restrict__ status) {
+  bool bad = false;
+  for (int64_t t = blockIdx.x * (int64_t)kPrimThreads + threadIdx.x; t < n; t += (int64_t)gridDim.x * kPrimThreads) {
+    const double rho = q[t], mx = q[n + t], my = q[2 * n + t], mz = q[3 * n + t], E = q[4 * n + t];
+    const double ir = 1.0 / rho;
+    const double p = (gamma - 1.0) * (E - 0.5 * ir * (mx * mx + my * my + mz * mz));
+    if (!(rho > 0.0) || !(p > 0.0)) bad = true;
+    prim[t] = ir;
+    prim[n + t] = p;
+    prim[2 * n + t] = sqrt(gamma * p * ir);
+  }
+  if (bad) atomicOr(status, (unsigned)DG_STATUS_NONPHYSICAL);
+}
+
 template <int N>
 cudaError_t launch_viscous_t(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
   using O = kern::Ord<N>;
@@ -22,11 +44,19 @@ cudaError_t launch_viscous_t(const MeshDev& m, const GasParams& g, const double*
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  kern::viscous_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.scratch, m.ops, m.fmask, m.geo, m.vmapP, m.status, g, m.bc,
-                                                      m.K);
+  kern::viscous_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.scratch, m.prim, m.ops, m.fmask, m.geo, m.vmapP, m.status,
+                                                      g, m.bc, m.K);
   return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t launch_prims_fp64(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
+  const int64_t n = (int64_t)m.K * m.Np;
+  const int64_t want = (n + kPrimThreads - 1) / kPrimThreads;
+  const int blocks = (int)(want < 65535 ? want : 65535);
+  prims_fp64_kernel<<<blocks, kPrimThreads, 0, s>>>(q, m.prim, n, g.gamma, m.status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
   switch (m.N) {
