@@ -40,8 +40,9 @@ FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
-    ("ff6530f6721628b0", "rhs"): 289.511936e6 + 105.523456e6,
-    ("ff6530f6721628b0", "viscous"): 99.331328e6 + 74.569728e6,
+    ("4d32ce7f64cf840d", "rhs"): 331.120384e6 + 107.956480e6,
+    ("4d32ce7f64cf840d", "viscous"): 126.835456e6 + 78.017792e6,
+    ("4d32ce7f64cf840d", "prims"): 66.384640e6 + 8.758016e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
     ("583bb8011d7b7afd", "mixed_rhs"): 255.000576e6 + 117.647360e6,
     ("583bb8011d7b7afd", "mixed_viscous"): 90.068992e6 + 26.120960e6,
@@ -92,13 +93,18 @@ def viscous_flops_per_element(Np, NF):
 
 def rhs_bytes_per_element(Np, NF, V, viscous):
     b = Np * 8 * 4 * V + 26 * 8 + 4 * NF  # q, k in; q_out, k out; geometry; neighbour map
+    b += Np * 8 * 3                        # the primitives pass's (1/rho, p, c)
     if viscous:
         b += Np * 8 * 9                    # viscous flux in
     return b
 
 
 def viscous_bytes_per_element(Np, NF):
-    return Np * 8 * (5 + 9) + 26 * 8 + 4 * NF
+    return Np * 8 * (5 + 9 + 2) + 26 * 8 + 4 * NF  # q in, flux out, (1/rho, p) in; geometry; map
+
+
+def prims_bytes_per_element(Np):
+    return Np * 8 * (5 + 3)  # q in, (1/rho, p, c) out
 
 
 # ---- clocks ------------------------------------------------------------------------------------
@@ -377,6 +383,12 @@ def gpu_arm(args, cfg, world, rank, local):
         dom = max(per, key=lambda k: per[k]["avg_ms"] * per[k]["launches"])
         avg_s = per[dom]["avg_ms"] * 1e-3
         if form == "fp64":
+            for name, fn in (("rhs", lambda: rhs_bytes_per_element(Np, NF, 5, viscous)),
+                             ("viscous", lambda: viscous_bytes_per_element(Np, NF)),
+                             ("prims", lambda: prims_bytes_per_element(Np))):
+                if name in per:
+                    per[name]["algorithmic_bytes"] = fn() * cfg.K
+                    per[name]["traffic"] = TRAFFIC.get((src, name))
             if dom == "rhs":
                 flops = rhs_flops_per_element(Np, NF, 5, viscous) * cfg.K
                 nbytes = rhs_bytes_per_element(Np, NF, 5, viscous) * cfg.K

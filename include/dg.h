@@ -167,9 +167,10 @@ int dg_gather_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np, 
 /* dst [V][K][Np] at the elements elems_dev[n] <- src [V][n][Np]; same rules as the gather. */
 int dg_scatter_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np, const int32_t* elems_dev,
                         int32_t n, double* dst_dev, void* stream);
-/* The BR1 viscous flux of q (perfect gas, FP64 form) into the mesh's buffer, and that buffer's
- * device address and layout ([9][K][Np]: tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, E_x,
- * E_y, E_z), valid while the mesh lives. */
+/* The BR1 viscous flux of q (perfect gas, FP64 form) into the mesh's buffer (after the per-node
+ * primitives 1/rho, p, c of q into the mesh's own primitives buffer), and that buffer's device
+ * address and layout ([9][K][Np]: tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, E_x, E_y, E_z),
+ * valid while the mesh lives. */
 int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q_dev, void* stream);
 int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv_dev);
 
