@@ -35,6 +35,7 @@ struct dg_hex_mesh_s {
   std::vector<double> nodes, w, D;  // host copies
   double* D_dev = nullptr;          // [M][M]
   double* fv_dev = nullptr;         // Navier-Stokes viscous flux [9][K][Np] (on first use)
+  double* prim = nullptr;           // [3][K][Np] 1/rho, p, c of the state (on first use)
   // artificial viscosity (dg_hex_set_av): parameters, element viscosity [K], flux [15][K][Np]
   double av_eps0 = 0.0, av_s0 = 0.0, av_kappa = 1.0;
   double* av_eps = nullptr;
@@ -85,6 +86,25 @@ __device__ __forceinline__ void pc(double gamma, const double* q, double& ir, do
   ir = rcp_nr(q[0]);
   p = (gamma - 1.0) * (q[4] - 0.5 * ir * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]));
   c = sqrt_nr(gamma * p * ir);
+}
+
+// 1/rho, p and c of every node into prim [3][K][Np], once per node: the right-hand-side and
+// viscous kernels read them at their own nodes and at the neighbour trace of every face node
+// instead of evaluating them there.  rho <= 0 or p <= 0 at a node sets DG_STATUS_NONPHYSICAL.
+__global__ void __launch_bounds__(256) hex_prims_kernel(const double* __restrict__ q, double* __restrict__ prim,
+                                                        const int64_t n, const double gamma,
+                                                        unsigned* __restrict__ status) {
+  bool bad = false;
+  for (int64_t t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    const double qv[5] = {q[t], q[n + t], q[2 * n + t], q[3 * n + t], q[4 * n + t]};
+    double ir, p, c;
+    pc(gamma, qv, ir, p, c);
+    if (!(qv[0] > 0.0) || !(p > 0.0)) bad = true;
+    prim[t] = ir;
+    prim[n + t] = p;
+    prim[2 * n + t] = c;
+  }
+  if (bad) atomicOr(status, (unsigned)DG_STATUS_NONPHYSICAL);
 }
 
 // The six neighbours of element e, slot 2d + end (end 0: the -x_d side), in 32-bit
@@ -143,7 +163,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
                                                                  unsigned* __restrict__ status,
                                                                  const double* __restrict__ fv,
                                                                  const double* __restrict__ sig,
-                                                                 const double* __restrict__ eps) {
+                                                                 const double* __restrict__ eps,
+                                                                 const double* __restrict__ prim) {
   using C = HexCfg<N>;
   constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
   __shared__ double sD[3][M * M];     // -(2/h_d) s D per axis
@@ -165,12 +186,10 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
   if (tid < nn) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
-    double ir, p, c;
-    pc(gamma, qv, ir, p, c);
-    if (!(qv[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    const double ir = prim[base + tid], p = prim[KNp + base + tid];  // checked by the primitives pass
     sPC[0][tid] = ir;
     sPC[1][tid] = p;
-    sPC[2][tid] = c;
+    sPC[2][tid] = prim[2 * KNp + base + tid];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double ud = qv[1 + d] * ir;
@@ -216,11 +235,17 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_rhs_kernel(const double* __
         qm[v] = q[v * KNp + gM];
         qp[v] = q[v * KNp + gP];
       }
-      if (enb < 0) hex_ghost(-enb, d, geo, qp);
       const double irm = sPC[0][loc], pm = sPC[1][loc], cm = sPC[2][loc];
       double irp, pp, cp;
-      pc(gamma, qp, irp, pp, cp);
-      if (enb < 0 && (!(qp[0] > 0.0) || !(pp > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      if (enb >= 0) {
+        irp = prim[gP];
+        pp = prim[KNp + gP];
+        cp = prim[2 * KNp + gP];
+      } else {  // the ghost state
+        hex_ghost(-enb, d, geo, qp);
+        pc(gamma, qp, irp, pp, cp);
+        if (!(qp[0] > 0.0) || !(pp > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      }
       // n = +-e_d: n.F(q) = +-(F_d(q)); the sign folded into the lifted term
       const double um = qm[1 + d] * irm, up = qp[1 + d] * irp;
       const double lam = fmax(fabs(um) + cm, fabs(up) + cp);
@@ -313,7 +338,8 @@ template <int N>
 __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __restrict__ q, double* __restrict__ fv,
                                                                  const double* __restrict__ D_g, const HexGeo geo,
                                                                  const int64_t K, const double gamma, const double R,
-                                                                 const double mu, const double kappa) {
+                                                                 const double mu, const double kappa,
+                                                                 const double* __restrict__ prim) {
   using C = HexCfg<N>;
   constexpr int M = C::M, Np = C::Np, EPB = C::EPB, NODES = C::NODES, NT = C::NT;
   __shared__ double sD[3][M * M];     // (2/h_d) D per axis
@@ -334,9 +360,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
   if (tid < nn) {
     double qv[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qv[v] = q[v * KNp + base + tid];
-    const double ir = rcp_nr(qv[0]);
-    const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
+    for (int v = 0; v < 4; ++v) qv[v] = q[v * KNp + base + tid];
+    const double ir = prim[base + tid], p = prim[KNp + base + tid];
 #pragma unroll
     for (int v = 0; v < 4; ++v) sW[v][tid] = qv[v];
     sW[4][tid] = p * ir * iR;
@@ -361,9 +386,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
       double qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qp[v] = q[v * KNp + gP];
-      if (enb < 0) hex_ghost(-enb, d, geo, qp);  // exterior values w(q+) of the ghost state
-      const double irp = rcp_nr(qp[0]);
-      const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+      double irp, pp;
+      if (enb >= 0) {
+        irp = prim[gP];
+        pp = prim[KNp + gP];
+      } else {  // exterior values w(q+) of the ghost state
+        hex_ghost(-enb, d, geo, qp);
+        irp = rcp_nr(qp[0]);
+        pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+      }
       const double wp[5] = {qp[0], qp[1], qp[2], qp[3], pp * irp * iR};
       const double lf = end ? geo.lf[d][1] : geo.lf[d][0];
       const double sgnlf = end ? lf : -lf;
@@ -388,7 +419,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_vis_kernel(const double* __
       g[d][v] = acc;
     }
   }
-  const double rho = sW[0][tid], ir = rcp_nr(rho);
+  const double ir = prim[base + tid];
   const double u[3] = {sW[1][tid] * ir, sW[2][tid] * ir, sW[3][tid] * ir};
   double du[3][3];  // du[i][d] = d u_i / d x_d
 #pragma unroll
@@ -901,7 +932,7 @@ cudaError_t launch_vis_t(const dg_hex_mesh_s& m, const GasParams& g, const doubl
   using C = HexCfg<N>;
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
   hex_vis_kernel<N><<<(unsigned)blocks, C::NT, 0, s>>>(q, m.fv_dev, m.D_dev, make_geo<N>(m, 1.0), m.K, g.gamma, g.R,
-                                                       g.mu, g.kappa);
+                                                       g.mu, g.kappa, m.prim);
   return cudaGetLastError();
 }
 
@@ -940,7 +971,7 @@ cudaError_t launch_t(const dg_hex_mesh_s& m, double gamma, const double* q, doub
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
   hex_rhs_kernel<N, RK, VISC, AV><<<(unsigned)blocks, C::NT, 0, s>>>(q, out, k, m.D_dev, geo, m.K, gamma, a, b,
                                                                      a != 0.0, m.status, m.fv_dev, m.av_sig,
-                                                                     m.av_eps);
+                                                                     m.av_eps, m.prim);
   return cudaGetLastError();
 }
 
@@ -979,6 +1010,11 @@ cudaError_t launch_n(const dg_hex_mesh_s& m, const GasParams& g, const double* q
     return rk ? launch_oi_t<N, true>(m, g.gamma, q, out, k, a, b, dt, s)
               : launch_oi_t<N, false>(m, g.gamma, q, out, k, a, b, dt, s);
   cudaError_t e;
+  {
+    const int64_t n = m.K * m.Np, want = (n + 255) / 256;
+    hex_prims_kernel<<<(unsigned)(want < 65535 ? want : 65535), 256, 0, s>>>(q, m.prim, n, g.gamma, m.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (g.mu > 0 && (e = launch_vis_t<N>(m, g, q, s)) != cudaSuccess) return e;
   const bool av = m.av_eps0 > 0;
   if (av) {
@@ -1168,6 +1204,7 @@ int dg_hex_mesh_free(dg_hex_mesh m) {
   if (!m) return DG_OK;
   cudaFree(m->D_dev);
   cudaFree(m->fv_dev);
+  cudaFree(m->prim);
   cudaFree(m->av_eps);
   cudaFree(m->av_sig);
   cudaFree(m->status);
@@ -1193,6 +1230,10 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
     return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path takes a perfect gas");
   if (m->overint && (gas->p.mu > 0 || m->av_eps0 > 0))
     return dg::fail(DG_ERR_UNSUPPORTED, "over-integration runs with the Euler equations, without artificial viscosity");
+  if (!m->overint && !m->prim) {  // the primitives buffer of the Euler / Navier-Stokes kernels
+    const cudaError_t e = cudaMalloc((void**)&m->prim, sizeof(double) * 3 * (size_t)m->K * m->Np);
+    if (e != cudaSuccess) return dg::cuda_fail(e, "hexahedral primitives buffer");
+  }
   if (gas->p.mu > 0) {
     if (!m->fv_dev) {
       const cudaError_t e = cudaMalloc((void**)&m->fv_dev, sizeof(double) * 9 * (size_t)m->K * m->Np);
