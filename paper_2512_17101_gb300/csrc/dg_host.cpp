@@ -196,9 +196,13 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     const int mode = opts ? opts->t_seed : DG_TSEED_INPUT;
     const double tc = opts ? opts->t_const : 0.0;
     if (mode == DG_TSEED_MLP && !gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "DG_TSEED_MLP needs a trained MLP");
+    dg::MixturePrims mp64;  // 1/rho, p, c at the converged temperature, for the right-hand side
+    mp64.prim = m.prim;
+    mp64.status = m.status;
     e = timed(mesh, DG_KERNEL_TEMPERATURE, s, [&] {
-      if (mode == DG_TSEED_MLP) return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s);
-      return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, tc, gas->status, s);
+      if (mode == DG_TSEED_MLP)
+        return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s, mp64);
+      return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, tc, gas->status, s, mp64);
     });
     if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
     T = T_io;

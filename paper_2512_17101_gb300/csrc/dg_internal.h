@@ -143,7 +143,8 @@ constexpr size_t kDiagPartialBytes = sizeof(double) * kDiagBlocks * kDiagMaxV;
 // the node records [n][4] float4 {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, c},
 // {rho Y_1..4}, {rho Y_5..8}; rho <= 0 or p <= 0 sets DG_STATUS_NONPHYSICAL in *status.
 struct MixturePrims {
-  float4* rec = nullptr;
+  float4* rec = nullptr;      // mixed form: the node records
+  double* prim = nullptr;     // FP64 form: [3][n] 1/rho, p, c at the converged temperature
   unsigned* status = nullptr;
 };
 // The mesh scratch's mixture tables (k_mixed.cu).

@@ -122,9 +122,9 @@ __device__ __forceinline__ void ghost_state(int code, const double* qm, double n
 //   RK == false: out = rhs
 //   RK == true : k <- a k + dt rhs (k read only if a != 0), out = q + b k
 // V is the compile-time maximum of variables; nvar (runtime) <= V are used.
-// prim (perfect gas; may be null): [3][K][Np] = (1/rho, p, c) of q per node, evaluated once by
-// prims_fp64_kernel instead of at every node and at both traces of every face node here; null:
-// evaluated here.
+// prim (may be null): [3][K][Np] = (1/rho, p, c) of q per node, evaluated once (a perfect gas by
+// prims_fp64_kernel, a mixture by the temperature solve at its converged T) instead of at every
+// node and at both traces of every face node here; null: evaluated here.
 // ---------------------------------------------------------------------------------------------
 template <int N, int V, int PHYS, bool RK>
 __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
 #pragma unroll
     for (int v = 0; v < V; ++v) qv[v] = v < nvar ? sQ[v * NODES + tid] : 0.0;
     double ir, p;
-    if (!is_mix(PHYS) && prim) {  // the primitives pass has checked rho and p
+    if (is_mix(PHYS) || prim) {  // the pass that wrote them has checked rho and p (a mixture always has them)
       ir = prim[base + tid];
       p = prim[KNp + base + tid];
     } else {
@@ -247,12 +247,12 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     }
     if (P < 0) ghost_state<V>(-P, qm, nx, ny, nz, bc, nvar, qp);
     double irm, irp, pm, cm, pp, cp;
-    if (!is_mix(PHYS) && prim) {
+    if (is_mix(PHYS) || prim) {
       const size_t gM = base + own;
       irm = prim[gM];
       pm = prim[KNp + gM];
       cm = prim[2 * KNp + gM];
-      if (P >= 0) {
+      if (is_mix(PHYS) || P >= 0) {  // mixtures have no boundary faces
         irp = prim[Pn];
         pp = prim[KNp + Pn];
         cp = prim[2 * KNp + Pn];
@@ -600,7 +600,7 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, is_mix(PHYS) ? nullptr : m.prim, m.ops,
+  rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.prim, m.ops,
                                                            m.fmask, m.geo, m.vmapP,
                                                            PHYS == MIXTURE_NS ? m.mix_fv : m.scratch,
                                                            m.av_sig, m.av_eps, m.status, g, m.bc, m.K, nvar, a, b,

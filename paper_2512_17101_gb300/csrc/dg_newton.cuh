@@ -87,5 +87,18 @@ __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasPar
   r[3] = make_float4(v[12], v[13], v[14], v[15]);
 }
 
+// The FP64 form's primitives at the converged temperature t: 1/rho, p = rho R_mix t and
+// c = sqrt(cp/cv p/rho), with cv = de/dT of the folded quintic at t and cp = cv + R_mix.
+__device__ __forceinline__ void store_prims64(const MixturePrims& mp, const double c[6], int64_t n, int64_t node,
+                                              double rho, double Rmix, double t) {
+  const double cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
+  const double ir = 1.0 / rho;
+  const double p = rho * Rmix * t;
+  if (!(rho > 0.0) || !(p > 0.0)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
+  mp.prim[node] = ir;
+  mp.prim[n + node] = p;
+  mp.prim[2 * n + node] = sqrt((cv + Rmix) / cv * p * ir);
+}
+
 }  // namespace newton
 }  // namespace dg

@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g,
     T[node] = t;
     if (iters) iters[node] = it;
     if (mp.rec) newton::store_prims(mp, g, q, n, node, rho, Rmix, t, cv);
+    if (mp.prim) newton::store_prims64(mp, c, n, node, rho, Rmix, t);
   }
 }
 

@@ -8,7 +8,7 @@
 // Newton update then costs two Horner evaluations and a reciprocal:
 //   T <- T - (e(T) - e) / cv(T),  cv = de/dT,  until |dT| < tol (capped)
 // (dg_newton.cuh).  In the mixed-precision form the same kernel also writes the
-// node's pressure, sound speed and float state copy.
+// node's pressure, sound speed and float state copy; in the FP64 form 1/rho, p and c.
 #include "dg_newton.cuh"
 
 namespace dg {
@@ -32,6 +32,7 @@ __global__ void temperature_kernel(const GasParams g, const int64_t n, const dou
     T[i] = t;
     if (iters) iters[i] = it;
     if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, Rmix, t, cv);
+    if (mp.prim) newton::store_prims64(mp, c, n, i, rho, Rmix, t);
   }
 }
 
