@@ -30,6 +30,27 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The oracle's CPU timings run on one thread, its numpy BLAS calls included, so that the core
+# count they report is the one they used (set before numpy is first imported).
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+
+def host_cpu():
+    """The host beside a CPU timing: architecture, logical CPUs, and the model where the kernel
+    names one."""
+    import platform
+    info = {"machine": platform.machine(), "nproc": os.cpu_count()}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    info["model"] = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return info
+
 METRIC = "RK4 stage DOF-updates/s on 1 GB300: mixed/learned vs plain FP64 at fixed error"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (the pool's recipe table); an FMA-loop probe measured 1.198
 L2_FLUSH_BYTES = 256 << 20
@@ -259,7 +280,7 @@ def reference_arm(args, cfg, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(cfg),
-        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "host": host_cpu(), "kind": "oracle",
                          "sample": f"each step: {desc} (half-size box of the workload); numpy, single thread"},
         "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -460,7 +481,7 @@ def gpu_arm(args, cfg, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, desc, secs = time_oracle(cfg, 1)
-        cpu = {"value": val, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": val, "unit": "DOF-updates/s", "cores": 1, "host": host_cpu(), "kind": "oracle",
                "sample": f"{desc}: the full workload's mesh; numpy, single thread; {secs:.1f} s"}
 
     learned = None
@@ -722,7 +743,7 @@ def hex_form(args, local):
         t0 = time.perf_counter()
         hx.hex_rhs_strong(ref, small["box"], small["q"], PerfectGas(1.4, 1.0))
         cpu_s = time.perf_counter() - t0
-        cpu = {"value": 16 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+        cpu = {"value": 16 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1, "host": host_cpu(),
                "sample": f"one right-hand side of the oracle on 16^3 hexahedra, N = {cfg.N} "
                          f"(numpy, single thread), {cpu_s:.2f} s"}
     return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
@@ -811,7 +832,7 @@ def boundary_form(args, local, periodic_fp64=None):
         t0 = time.perf_counter()
         bd.rhs_ns_bc(ref, geo, conn, small["q"], PerfectGas(g.gamma, g.R), g.mu, g.Pr)
         cpu_s = time.perf_counter() - t0
-        cpu = {"value": small["q"].shape[1] * small["q"].shape[2] / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+        cpu = {"value": small["q"].shape[1] * small["q"].shape[2] / cpu_s, "unit": "DOF-updates/s", "cores": 1, "host": host_cpu(),
                "sample": f"one right-hand side of the oracle on the channel at 6^3 x 6 tets, N = {cfg.N} "
                          f"(numpy, single thread), {cpu_s:.2f} s"}
     return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": cfg.Np, "dtype": "f64",
@@ -1062,7 +1083,7 @@ def hex_advection_form(args, local):
         t0 = time.perf_counter()
         hx.hex_advection_rhs_strong(ref, small["box"], small["u"], vel)
         cpu_s = time.perf_counter() - t0
-        cpu = {"value": 32 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1,
+        cpu = {"value": 32 ** 3 * M ** 3 / cpu_s, "unit": "DOF-updates/s", "cores": 1, "host": host_cpu(),
                "sample": f"one right-hand side of the oracle on 32^3 hexahedra, N = {cfg.N} "
                          f"(numpy, single thread), {cpu_s:.2f} s"}
     return {"workload": f"{cfg.name}: {cfg.description}", "K": cfg.K, "N": cfg.N, "Np": M ** 3, "dtype": "f64",
