@@ -61,9 +61,9 @@ FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
-    ("4d32ce7f64cf840d", "rhs"): 331.120384e6 + 107.956480e6,
-    ("4d32ce7f64cf840d", "viscous"): 126.835456e6 + 78.017792e6,
-    ("4d32ce7f64cf840d", "prims"): 66.384640e6 + 8.758016e6,
+    ("fd640972440b44d5", "rhs"): 330.799104e6 + 104.880640e6,
+    ("fd640972440b44d5", "viscous"): 126.838528e6 + 75.130112e6,
+    ("fd640972440b44d5", "prims"): 66.396160e6 + 7.919616e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
     ("583bb8011d7b7afd", "mixed_rhs"): 255.000576e6 + 117.647360e6,
     ("583bb8011d7b7afd", "mixed_viscous"): 90.068992e6 + 26.120960e6,
