@@ -52,22 +52,23 @@ def host_cpu():
     return info
 
 METRIC = "RK4 stage DOF-updates/s on 1 GB300: mixed/learned vs plain FP64 at fixed error"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (the pool's recipe table); an FMA-loop probe measured 1.198
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (2 FMA lanes x 152 SMs x 2.07 GHz x 2); an FMA-loop probe measured 1.198
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture, keyed by the
-# sha256 of the kernel sources they were taken on; a changed kernel reports null traffic.
+# sha256 of the kernel sources they were taken on, the workload and the kernel; a changed kernel or
+# another workload reports null traffic.
 FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
-    ("fd640972440b44d5", "rhs"): 330.799104e6 + 104.880640e6,
-    ("fd640972440b44d5", "viscous"): 126.838528e6 + 75.130112e6,
-    ("fd640972440b44d5", "prims"): 66.396160e6 + 7.919616e6,
+    ("fd640972440b44d5", "ns_viscous", "rhs"): 330.799104e6 + 104.880640e6,
+    ("fd640972440b44d5", "ns_viscous", "viscous"): 126.838528e6 + 75.130112e6,
+    ("fd640972440b44d5", "ns_viscous", "prims"): 66.396160e6 + 7.919616e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("583bb8011d7b7afd", "mixed_rhs"): 255.000576e6 + 117.647360e6,
-    ("583bb8011d7b7afd", "mixed_viscous"): 90.068992e6 + 26.120960e6,
-    ("583bb8011d7b7afd", "mixed_prims"): 66.372096e6 + 14.673920e6,
+    ("583bb8011d7b7afd", "ns_viscous", "mixed_rhs"): 255.000576e6 + 117.647360e6,
+    ("583bb8011d7b7afd", "ns_viscous", "mixed_viscous"): 90.068992e6 + 26.120960e6,
+    ("583bb8011d7b7afd", "ns_viscous", "mixed_prims"): 66.372096e6 + 14.673920e6,
 }
 
 
@@ -409,7 +410,7 @@ def gpu_arm(args, cfg, world, rank, local):
                              ("prims", lambda: prims_bytes_per_element(Np))):
                 if name in per:
                     per[name]["algorithmic_bytes"] = fn() * cfg.K
-                    per[name]["traffic"] = TRAFFIC.get((src, name))
+                    per[name]["traffic"] = TRAFFIC.get((src, cfg.name, name))
             if dom == "rhs":
                 flops = rhs_flops_per_element(Np, NF, 5, viscous) * cfg.K
                 nbytes = rhs_bytes_per_element(Np, NF, 5, viscous) * cfg.K
@@ -418,11 +419,11 @@ def gpu_arm(args, cfg, world, rank, local):
                 nbytes = viscous_bytes_per_element(Np, NF) * cfg.K
             ach = flops / avg_s / 1e12
             return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((src, dom)), "kernel": dom,
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((src, cfg.name, dom)), "kernel": dom,
                     "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                     "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
                     "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak, "kernels": per,
-                    "peak_note": "FP64 nominal 1.25 TFLOP/s (pool recipe table); HBM: measured copy"}
+                    "peak_note": "FP64 nominal 1.25 TFLOP/s (2 FMA lanes x 152 SMs x 2.07 GHz); HBM: measured copy"}
         per_el = {"rhs": mixed_rhs_bytes_per_element(Np, NF, viscous),
                   "viscous": mixed_viscous_bytes_per_element(Np, NF),
                   "prims": mixed_prims_bytes_per_element(Np, viscous)}
@@ -433,7 +434,7 @@ def gpu_arm(args, cfg, world, rank, local):
         nbytes = per_el[dom] * cfg.K
         ach = nbytes / avg_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": TRAFFIC.get((src_mixed, "mixed_" + dom)), "kernel": dom,
+                "traffic": TRAFFIC.get((src_mixed, cfg.name, "mixed_" + dom)), "kernel": dom,
                 "algorithmic_bytes_per_launch": nbytes,
                 "tensor_flops_per_step": mixed_tensor_flops_per_element(Np, NF, viscous) * cfg.K * 5,
                 "kernels": per, "peak_note": "HBM: measured copy (MEASURED_PEAKS.json)"}

@@ -7,7 +7,7 @@
 //     then an Adam update; samples come from the Newton solver;
 //   * inference, FP16 operands with FP32 accumulation on the tensor cores
 //     (mma.sync m16n8k16), fused with the FP64 Newton iteration that it seeds:
-//     Newton stays the judge and the fallback, to the same |dT| < tol.
+//     Newton stays the arbiter and the fallback, to the same |dT| < tol.
 //
 // Flat parameter layout (float): W1 [64][8] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64] | b3.
 #include <cuda_fp16.h>
@@ -175,7 +175,7 @@ __device__ __forceinline__ void mma16816h(float* c, const uint32_t* a, uint32_t 
 }
 
 // Hardware tanh (tanh.approx.f32, about 11 correct bits): the inference only seeds Newton,
-// which stays the judge of T; training uses the precise tanhf.
+// which stays the arbiter of T; training uses the precise tanhf.
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
