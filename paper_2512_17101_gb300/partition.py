@@ -91,7 +91,8 @@ def partition_mesh(vertices, period, N, ref_nodes, nparts, face_bc=None):
 
 class TorchTransport:
     """Point-to-point exchange through torch.distributed (one message each way per neighbour),
-    for the one partition this process holds."""
+    for the one partition this process holds.  As in the paper's execution engine (§5.4), every
+    receive is posted before the sends."""
 
     def __init__(self, group=None):
         self.group = group
@@ -101,8 +102,8 @@ class TorchTransport:
         import torch.distributed as dist
         assert len(sends) == 1, "a process holds one partition"
         out = {s: torch.empty(shape, dtype=like.dtype, device=like.device) for s, shape in recv_shapes[0].items()}
-        reqs = [dist.isend(buf.contiguous(), dst=s, group=self.group) for s, buf in sends[0].items()]
-        reqs += [dist.irecv(out[s], src=s, group=self.group) for s in out]
+        reqs = [dist.irecv(out[s], src=s, group=self.group) for s in out]
+        reqs += [dist.isend(buf.contiguous(), dst=s, group=self.group) for s, buf in sends[0].items()]
         for r in reqs:
             r.wait()
         return [out]
