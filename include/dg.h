@@ -114,11 +114,14 @@ typedef struct {
  * normals, Fscale = face area / (2 J)) and the face connectivity (faces paired
  * by centroid modulo the period, face nodes by coordinates under the face
  * pair's periodic shift), then copies them to the current device together with
- * a scratch buffer for the viscous flux (9 doubles per node).  Sec. 1 Fig. 1
- * (element-local arrays), Sec. 4.1.2 / Sec. 4.3 (connectivity, indirect gather).
+ * per-node scratch: the viscous flux (9 doubles per node), the FP64 form's primitives
+ * (1/rho, p, c: 3 doubles per node) and the partials of the global reductions.  Sec. 1
+ * Fig. 1 (element-local arrays), Sec. 4.1.2 / Sec. 4.3 (connectivity, indirect gather).
  * Every face must find exactly one partner, or carry a DG_BC_* code in face_bc;
  * a paired face must carry 0; otherwise DG_ERR_INVALID_ARG.  Allocates device
- * memory (cudaMalloc); *out owns it. */
+ * memory (cudaMalloc); *out owns it.  The scratch is the mesh's: calls on one mesh from
+ * several streams or host threads at once race on it and must be serialised (a state
+ * per stream needs a mesh per stream). */
 int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out);
 int dg_mesh_free(dg_mesh mesh);
 
