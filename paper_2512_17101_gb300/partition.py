@@ -190,10 +190,12 @@ def _refresh(ranks, transport, ptrs, V):
 
 
 def partitioned_lsrk4_step(ranks: list, gas, transport, dt):
-    """One LSRK4 step of the partitions held by this process (FP64 form).  Before every stage
-    the halos of the states are refreshed; with viscosity each partition's viscous flux is
-    computed, its halo refreshed, and the stage uses it."""
+    """One LSRK4 step of the partitions held by this process (FP64 form, perfect gas).  Before
+    every stage the halos of the states are refreshed; with viscosity each partition's viscous
+    flux is computed, its halo refreshed, and the stage uses it."""
     from .dg import _opts, dg_rk_stage
+    if getattr(gas, "model", "perfect") != "perfect":
+        raise ValueError("the partitioned step takes a perfect gas")
     V = ranks[0].q.shape[0]
     viscous = gas.mu > 0
     opts = _opts()
