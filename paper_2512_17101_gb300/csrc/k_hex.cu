@@ -675,18 +675,35 @@ __global__ void __launch_bounds__(OiCfg<N>::NT) hex_oi_kernel(const double* __re
   }
   __syncthreads();
   const double gm1 = gamma - 1.0;
+  // 1/rho and p at this thread's Gauss points, once for the three flux directions (a thread
+  // handles the same Gauss points in every direction's pass)
+  constexpr int GPT = (EPB * Q3 + NT - 1) / NT;
+  double g_ir[GPT], g_p[GPT];
+#pragma unroll
+  for (int s = 0; s < GPT; ++s) {
+    const int t = tid + s * NT;
+    g_ir[s] = g_p[s] = 0.0;
+    if (t < nel * Q3) {
+      const double r = sC[t], mx = sC[EPB * Q3 + t], my = sC[2 * EPB * Q3 + t], mz = sC[3 * EPB * Q3 + t];
+      g_ir[s] = rcp_nr(r);
+      g_p[s] = gm1 * (sC[4 * EPB * Q3 + t] - 0.5 * g_ir[s] * (mx * mx + my * my + mz * mz));
+      if (!(r > 0.0) || !(g_p[s] > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+    }
+  }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     // fluxes along d at the Gauss points
-    for (int t = tid; t < nel * Q3; t += NT) {
+#pragma unroll
+    for (int s = 0; s < GPT; ++s) {
+      const int t = tid + s * NT;
+      if (t >= nel * Q3) break;
       double qv[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qv[v] = sC[v * EPB * Q3 + t];
-      const double ir = rcp_nr(qv[0]);
-      const double p = gm1 * (qv[4] - 0.5 * ir * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]));
-      if (d == 0 && (!(qv[0] > 0.0) || !(p > 0.0))) atomicOr(status, DG_STATUS_NONPHYSICAL);
-      const double ud = qv[1 + d] * ir;
-      sF[0 * EPB * Q3 + t] = qv[1 + d];
+      const double ir = g_ir[s], p = g_p[s];
+      const double md = d == 0 ? qv[1] : (d == 1 ? qv[2] : qv[3]);  // a select: qv stays in registers
+      const double ud = md * ir;
+      sF[0 * EPB * Q3 + t] = md;
       sF[1 * EPB * Q3 + t] = qv[1] * ud + (d == 0 ? p : 0.0);
       sF[2 * EPB * Q3 + t] = qv[2] * ud + (d == 1 ? p : 0.0);
       sF[3 * EPB * Q3 + t] = qv[3] * ud + (d == 2 ? p : 0.0);
