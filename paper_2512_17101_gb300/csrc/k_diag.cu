@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kDiagThreads) integrals_partial(const double* 
     for (int v = 0; v < kDiagMaxV; ++v)
       if (v < nvar) acc[v] = fma(wJ, q[v * KNp + t], acc[v]);
   }
-  for (int v = 0; v < nvar; ++v) {
+#pragma unroll
+  for (int v = 0; v < kDiagMaxV; ++v) {  // unrolled: acc stays in registers (nvar is block-uniform)
+    if (v >= nvar) break;
     const double r = block_reduce<false>(acc[v], red);
     if (threadIdx.x == 0) part[blockIdx.x * kDiagMaxV + v] = r;
   }
