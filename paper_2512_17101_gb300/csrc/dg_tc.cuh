@@ -5,14 +5,14 @@
 //
 // Tile: 25 elements, rows r = 5 e + v (125 of the MMA's M = 128 rows; rows 125..127 are never
 // read), columns = output nodes i (N = NPAD = Np rounded up to 16).  The reduction runs over
-// chunks of KV = NPAD columns: three volume chunks (reference directions r, s, t: the
-// contravariant fluxes against -D_r, -D_s, -D_t) and one or two surface chunks (Fscale g
-// against LIFT).  Each chunk is produced by all threads into one shared-memory slot, then
-// contracted by KV/16 k-steps of the six split-BF16 products while nothing else may touch
-// the slot; two or three blocks per SM overlap one block's production with another's MMAs.
-// Operand columns past Np (volume) or past the face-node count (last surface chunk) hold
-// zeros or stale finite values from an earlier chunk; the operator table is zero there, so
-// they contribute nothing.
+// chunks: three volume chunks of KV = NPAD columns (reference directions r, s, t: the
+// contravariant fluxes against -D_r, -D_s, -D_t) and one or two surface chunks of KS columns
+// (Fscale g against LIFT; one chunk of 48 at N = 3).  Each chunk is produced by all threads
+// into one shared-memory slot, then contracted by width/16 k-steps of the six split-BF16
+// products while nothing else may touch the slot; two or three blocks per SM overlap one
+// block's production with another's MMAs.  Operand columns past Np (volume) or past the
+// face-node count (last surface chunk) hold zeros or stale finite values from an earlier chunk;
+// the operator table is zero there, so they contribute nothing.
 #pragma once
 
 #include "dg_mixed.cuh"
@@ -141,6 +141,14 @@ __host__ __device__ constexpr int aim_blocks(int smem, int nt, int min_regs = 64
   return r < 1 ? 1 : r;
 }
 
+// Columns of a surface chunk.  At N = 3 the 40 face nodes of an element go into one chunk of
+// 48 columns instead of chunks of 32 and 8: one MMA round trip and one gather pass less per
+// tile, for a wider operand slot that still leaves the resident blocks per SM unchanged.  Other
+// orders keep the volume width: at N = 2 the wider slot would cost the 128-thread tiles resident
+// blocks, at N = 4 half of them.  A function of the order alone, so that every tile variant of
+// an order shares one operator table.
+__host__ __device__ constexpr int surface_cols(int N, int KV, int NF) { return N == 3 ? round16(NF) : KV; }
+
 // Threads per tile of a mixture (13 rows per element, 9 elements per tile): about one node per thread.
 __host__ __device__ constexpr int mixture_nt(int N) { return N <= 2 ? 128 : (N == 3 ? 192 : 320); }
 
@@ -151,10 +159,12 @@ struct Cfg {
   static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
   static constexpr int E = 128 / V, ROWS = 128;  // rows (element, variable) of one MMA tile
   static constexpr int KV = round16(Np), NPAD = KV;
-  static constexpr int NSURF = (NF + KV - 1) / KV, NCHUNK = 3 + NSURF, KB = NCHUNK * KV;
-  // operand slot: 3 terms x 128 rows x KV columns; core matrices adjacent in K are 144 B apart
+  // surface columns per chunk (surface_cols: all face nodes in one chunk at N = 3)
+  static constexpr int NVOL = 3, KS = surface_cols(N, KV, NF), KA = KS > KV ? KS : KV;
+  static constexpr int NSURF = (NF + KS - 1) / KS, NCHUNK = NVOL + NSURF, KB = NVOL * KV + NSURF * KS;
+  // operand slot: 3 terms x 128 rows x KA columns; core matrices adjacent in K are 144 B apart
   // (not 128) so that the 16 B rows written by consecutive node threads fall in distinct banks
-  static constexpr int A_LBO = 144, A_SBO = (KV / 8) * A_LBO, A_TERM = 16 * A_SBO;
+  static constexpr int A_LBO = 144, A_SBO = (KA / 8) * A_LBO, A_TERM = 16 * A_SBO;
   // operator table: 3 terms x NPAD rows x KB columns
   static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NPAD / 8) * B_SBO;
   static constexpr int CS = NPAD + 1;  // row stride (floats) of the accumulator copy
@@ -246,21 +256,26 @@ __device__ __forceinline__ void block_teardown(const Smem<C_>& S, uint32_t phase
   if (threadIdx.x < 32) tmem_dealloc(*S.tmem, C_::TMEM_COLS);
 }
 
-// Issue the MMAs of chunk c (KV/16 k-steps x 6 split products) and commit them to the mbarrier.
+// Issue the MMAs of chunk c (width/16 k-steps x 6 split products) and commit them to the
+// mbarrier.  Chunks 0 .. NVOL-1 are KV columns wide, the surface chunks after them KS.
 template <class C_>
 __device__ __forceinline__ void issue_chunk(const Smem<C_>& S, int c) {
   const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B), tmem = *S.tmem;
   // products (A term, B term) whose term orders add up to at most 2
   constexpr int PA[6] = {0, 0, 1, 0, 1, 2}, PB[6] = {0, 1, 0, 2, 1, 0};
+  const bool vol = c < C_::NVOL;
+  const int nks = (vol ? C_::KV : C_::KS) / 16;
+  const int col8 = (vol ? c * C_::KV : C_::NVOL * C_::KV + (c - C_::NVOL) * C_::KS) / 8;  // first column / 8
 #pragma unroll
-  for (int ks = 0; ks < C_::KV / 16; ++ks)
+  for (int ks = 0; ks < C_::KA / 16; ++ks) {
+    if (ks >= nks) break;
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
       const uint64_t ad = umma_desc(a0 + PA[p] * C_::A_TERM + ks * 2 * C_::A_LBO, C_::A_LBO, C_::A_SBO);
-      const uint64_t bd =
-          umma_desc(b0 + PB[p] * C_::B_TERM + (c * (C_::KV / 8) + 2 * ks) * C_::B_LBO, C_::B_LBO, C_::B_SBO);
+      const uint64_t bd = umma_desc(b0 + PB[p] * C_::B_TERM + (col8 + 2 * ks) * C_::B_LBO, C_::B_LBO, C_::B_SBO);
       mma_bf16(tmem, ad, bd, C_::IDESC, (c > 0 || ks > 0 || p > 0) ? 1u : 0u);
     }
+  }
   mma_commit(smem_u32(S.bar));
 }
 
@@ -375,11 +390,11 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
     if (!run_chunk<C_>(S, ra, phase, status)) return false;
   }
 
-  // surface chunks: face nodes [sc KV, sc KV + KV) of every element
+  // surface chunks: face nodes [sc KS, sc KS + KS) of every element
   const float gam = (float)c.gas.gamma;
 #pragma unroll 1
   for (int sc = 0; sc < C_::NSURF; ++sc) {
-    const int m0 = sc * KV, w = min(KV, NF - m0);
+    const int m0 = sc * C_::KS, w = min(C_::KS, NF - m0);
     for (int j = tid; j < nel * w; j += NT) {
       const int e = j / w, mm = m0 + (j - e * w), f = mm / Nfp;
       const float* G = S.geo + e * GS;
@@ -537,8 +552,9 @@ struct VCfg {
   static constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF;
   static constexpr int E = 25, ROWS = 128;
   static constexpr int KV = round16(Np), NPAD = KV, NOUT = 3 * NPAD;
-  static constexpr int NSURF = (NF + KV - 1) / KV, NCHUNK = 1 + NSURF, KB = NCHUNK * KV;
-  static constexpr int A_LBO = 144, A_SBO = (KV / 8) * A_LBO, A_TERM = 16 * A_SBO;
+  static constexpr int NVOL = 1, KS = surface_cols(N, KV, NF), KA = KS > KV ? KS : KV;
+  static constexpr int NSURF = (NF + KS - 1) / KS, NCHUNK = NVOL + NSURF, KB = NVOL * KV + NSURF * KS;
+  static constexpr int A_LBO = 144, A_SBO = (KA / 8) * A_LBO, A_TERM = 16 * A_SBO;
   static constexpr int B_LBO = 128, B_SBO = (KB / 8) * B_LBO, B_TERM = (NOUT / 8) * B_SBO;
   static constexpr int CS = NPAD + 1;  // one reference direction's columns are copied at a time
   static constexpr int TMEM_COLS = NOUT <= 64 ? 64 : (NOUT <= 128 ? 128 : 256);
@@ -614,10 +630,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
   }
   if (!run_chunk<C_>(S, 0, phase, status)) return false;
 
-  // surface chunks: jumps w+ - w- at face nodes [sc KV, sc KV + KV)
+  // surface chunks: jumps w+ - w- at face nodes [sc KS, sc KS + KS)
 #pragma unroll 1
   for (int sc = 0; sc < C_::NSURF; ++sc) {
-    const int m0 = sc * KV, w = min(KV, NF - m0);
+    const int m0 = sc * C_::KS, w = min(C_::KS, NF - m0);
     for (int j = tid; j < nel * w; j += NT) {
       const int e = j / w, mm = m0 + (j - e * w);
       const size_t own = base + (size_t)e * Np + S.fm[mm];
