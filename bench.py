@@ -66,9 +66,9 @@ TRAFFIC = {
     ("fd640972440b44d5", "ns_viscous", "viscous"): 126.838528e6 + 75.130112e6,
     ("fd640972440b44d5", "ns_viscous", "prims"): 66.396160e6 + 7.919616e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("583bb8011d7b7afd", "ns_viscous", "mixed_rhs"): 255.000576e6 + 117.647360e6,
-    ("583bb8011d7b7afd", "ns_viscous", "mixed_viscous"): 90.068992e6 + 26.120960e6,
-    ("583bb8011d7b7afd", "ns_viscous", "mixed_prims"): 66.372096e6 + 14.673920e6,
+    ("87e643df5d6591a7", "ns_viscous", "mixed_rhs"): 253.629184e6 + 112.609792e6,
+    ("87e643df5d6591a7", "ns_viscous", "mixed_viscous"): 90.059264e6 + 22.807040e6,
+    ("87e643df5d6591a7", "ns_viscous", "mixed_prims"): 66.376448e6 + 14.456064e6,
 }
 
 
