@@ -143,11 +143,14 @@ __host__ __device__ constexpr int aim_blocks(int smem, int nt, int min_regs = 64
 
 // Columns of a surface chunk.  At N = 3 the 40 face nodes of an element go into one chunk of
 // 48 columns instead of chunks of 32 and 8: one MMA round trip and one gather pass less per
-// tile, for a wider operand slot that still leaves the resident blocks per SM unchanged.  Other
-// orders keep the volume width: at N = 2 the wider slot would cost the 128-thread tiles resident
-// blocks, at N = 4 half of them.  A function of the order alone, so that every tile variant of
-// an order shares one operator table.
-__host__ __device__ constexpr int surface_cols(int N, int KV, int NF) { return N == 3 ? round16(NF) : KV; }
+// tile, for a wider operand slot that still leaves the resident blocks per SM unchanged.  In the
+// right-hand-side tile (merge_n2) the same holds at N = 2, 24 face nodes in one chunk of 32
+// instead of 16 and 8.  N = 4 keeps the volume width: the wider slot would cost half the
+// resident blocks.  A function of the order (and tile kind) alone, so that every tile variant
+// of an order shares one operator table.
+__host__ __device__ constexpr int surface_cols(int N, int KV, int NF, bool merge_n2 = false) {
+  return (N == 3 || (merge_n2 && N == 2)) ? round16(NF) : KV;
+}
 
 // Threads per tile of a mixture (13 rows per element, 9 elements per tile): about one node per thread.
 __host__ __device__ constexpr int mixture_nt(int N) { return N <= 2 ? 128 : (N == 3 ? 192 : 320); }
@@ -160,7 +163,7 @@ struct Cfg {
   static constexpr int E = 128 / V, ROWS = 128;  // rows (element, variable) of one MMA tile
   static constexpr int KV = round16(Np), NPAD = KV;
   // surface columns per chunk (surface_cols: all face nodes in one chunk at N = 3)
-  static constexpr int NVOL = 3, KS = surface_cols(N, KV, NF), KA = KS > KV ? KS : KV;
+  static constexpr int NVOL = 3, KS = surface_cols(N, KV, NF, true), KA = KS > KV ? KS : KV;
   static constexpr int NSURF = (NF + KS - 1) / KS, NCHUNK = NVOL + NSURF, KB = NVOL * KV + NSURF * KS;
   // operand slot: 3 terms x 128 rows x KA columns; core matrices adjacent in K are 144 B apart
   // (not 128) so that the 16 B rows written by consecutive node threads fall in distinct banks
