@@ -66,9 +66,9 @@ TRAFFIC = {
     ("fd640972440b44d5", "ns_viscous", "viscous"): 126.838528e6 + 75.130112e6,
     ("fd640972440b44d5", "ns_viscous", "prims"): 66.396160e6 + 7.919616e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("87e643df5d6591a7", "ns_viscous", "mixed_rhs"): 253.629184e6 + 112.609792e6,
-    ("87e643df5d6591a7", "ns_viscous", "mixed_viscous"): 90.059264e6 + 22.807040e6,
-    ("87e643df5d6591a7", "ns_viscous", "mixed_prims"): 66.376448e6 + 14.456064e6,
+    ("17750afbff787730", "ns_viscous", "mixed_rhs"): 251.656192e6 + 111.862016e6,
+    ("17750afbff787730", "ns_viscous", "mixed_viscous"): 90.061568e6 + 23.028480e6,
+    ("17750afbff787730", "ns_viscous", "mixed_prims"): 66.375424e6 + 14.374656e6,
 }
 
 
