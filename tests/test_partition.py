@@ -62,6 +62,38 @@ def test_partition_rhs_matches_global_at_owned_elements(lib):
         assert np.abs(r[:, :no] - want[:, p.owned]).max() <= 1e-13 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("viscous", [False, True])
+def test_partition_rhs_with_boundary_faces(lib, viscous):
+    """Walls and inflow / outflow faces stay with their elements: the oracle right-hand side of
+    each partition (halo filled from the global state) equals the global one at owned elements.
+    Navier-Stokes needs a second halo layer (the viscous flux of a halo element depends on its
+    own neighbours), so there the comparison covers the owned elements whose neighbours are all
+    owned."""
+    import oracle.boundary as bd
+    from oracle.thermo import PerfectGas
+    from paper_2512_17101_gb300.partition import partition_mesh
+    from tests._oracle_case import bc_disc
+    N = 2
+    sides = {(0, 0): bd.INFLOW, (0, 1): bd.OUTFLOW, (1, 0): bd.NOSLIP_WALL, (1, 1): bd.SLIP_WALL}
+    g = bc_disc((4, 2, 2), N, sides)
+    q = uniform_perturbation(isentropic_vortex(g.xyz, 0.0, period=np.where(g.period > 0, g.period, 1.0)), 1e-3)
+    q_in = q[:, 0, 0].copy()
+    gas = PerfectGas(1.4, 1.0)
+    f = (lambda d, u: bd.rhs_ns_bc(d.ref, d.geo, d.conn, u, gas, 0.02, 0.71, q_in=q_in)) if viscous else \
+        (lambda d, u: bd.rhs_euler_bc(d.ref, d.geo, d.conn, u, gas, q_in=q_in))
+    want = f(g, q)
+    for p in partition_mesh(g.vertices, g.period, N, equispaced_tet_nodes(N), 3, face_bc=g.face_bc):
+        d = Disc(p.vertices, g.period, N, face_bc=p.face_bc)
+        r = f(d, q[:, p.local])
+        no = len(p.owned)
+        keep = np.arange(no)
+        if viscous:  # owned elements without a halo neighbour
+            nb = d.conn.vmapP.reshape(d.K, -1) // d.ref.Np  # boundary nodes give negative values
+            keep = np.array([e for e in range(no) if np.all(nb[e][nb[e] >= 0] < no)], dtype=int)
+            assert len(keep) > 0
+        assert np.abs(r[:, keep] - want[:, p.owned[keep]]).max() <= 1e-13 * np.abs(want).max()
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
