@@ -94,6 +94,22 @@ def test_partition_rhs_with_boundary_faces(lib, viscous):
         assert np.abs(r[:, keep] - want[:, p.owned[keep]]).max() <= 1e-13 * np.abs(want).max()
 
 
+def test_partition_arguments_and_local_reductions(lib):
+    import torch
+    from paper_2512_17101_gb300.partition import LocalRouter, partition_mesh
+    v, per = box_mesh((2, 1, 1), 1.0)
+    with pytest.raises(ValueError):
+        partition_mesh(v, per, 1, equispaced_tet_nodes(1), 0)
+    with pytest.raises(ValueError):
+        partition_mesh(v, per, 1, equispaced_tet_nodes(1), v.shape[0] + 1)
+    parts = partition_mesh(v, per, 1, equispaced_tet_nodes(1), v.shape[0])  # one element each
+    assert all(len(p.owned) == 1 for p in parts)
+    vals = [torch.tensor([1.0, -2.0]), torch.tensor([3.0, 5.0]), torch.tensor([-4.0, 0.5])]
+    r = LocalRouter()
+    assert all(t.tolist() == [0.0, 3.5] for t in r.reduce_all(vals, "sum"))
+    assert all(t.tolist() == [3.0, 5.0] for t in r.reduce_all(vals, "max"))
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
