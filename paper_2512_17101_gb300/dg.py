@@ -318,7 +318,9 @@ def dg_max_rate(mesh: Mesh, gas: Gas, q, K_count=None, out=None, stream=None):
 
 
 def stable_dt(mesh: Mesh, gas: Gas, q, cfl, stream=None) -> float:
-    """CFL / (largest stability rate); reads the rate back to the host."""
+    """CFL / (largest stability rate); reads the rate back to the host.  A node with rho <= 0 or
+    p <= 0 makes the rate infinite (and sets DG_STATUS_NONPHYSICAL in the mesh status), so the
+    step returned is 0."""
     return float(cfl) / float(dg_max_rate(mesh, gas, q, stream=stream).item())
 
 
