@@ -365,6 +365,17 @@ int dg_mlp_get(dg_gas gas, float* params_host, dg_mlp_norm* norm);
 int dg_mlp_loss_grad(int64_t n, const float* params_dev, const float* x_dev, const float* t_dev, float* grad_dev,
                      float* loss_dev, void* stream);
 
+/* One Adam update of the training loop (Kingma & Ba 2015, Algorithm 1, with beta1 = 0.9,
+ * beta2 = 0.999, eps = 1e-8), exposed for checks: elementwise over the DG_MLP_PARAMS float device
+ * arrays, with g = grad,
+ *   m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+ *   params <- params - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ * then grad <- 0 (the next batch accumulates into it).  t >= 1 is the step number (the bias
+ * corrections are formed in FP64, the update in FP32).  Asynchronous on stream.  Errors:
+ * DG_ERR_INVALID_ARG (NULL, t < 1, non-finite lr). */
+int dg_mlp_adam_step(int32_t t, float lr, float* params_dev, float* grad_dev, float* m_dev, float* v_dev,
+                     void* stream);
+
 /* Train the gas's MLP on n samples (e_dev [n], Y_dev [nspecies][n], T_dev [n],
  * float64 device arrays; T typically from dg_temperature), starting from
  * init_params_host, with the normalisation taken from the samples' means and
@@ -385,8 +396,11 @@ int dg_mlp_guess(dg_gas gas, int64_t n, const double* q_dev, double* T_dev, void
  * (dg_mesh_operators, dg_mesh_connectivity; no CUDA call is made to build it),
  * and calls dg_rk_stage_noalloc, which allocates nothing: the viscous-flux
  * scratch of the BR1 pass lives in a static device array of
- * DG_STATIC_SCRATCH_NODES * 9 doubles (36 MiB) that every GPU which loads the
- * library holds until the process exits. */
+ * DG_STATIC_SCRATCH_NODES * 9 doubles (36 MiB).  With CUDA's default lazy module
+ * loading that array is committed on a device when the first call there loads
+ * the code module that holds it, and it stays until the process exits (or the
+ * context is reset); make that first call before the caller's allocator reserves
+ * the device's memory, or it can fail with DG_ERR_CUDA (out of memory). */
 #define DG_STATIC_SCRATCH_NODES (1 << 19) /* largest K * Np accepted */
 
 typedef struct {
@@ -395,20 +409,25 @@ typedef struct {
   const double* ops_dev;     /* [3 Np Np + Np 4 Nfp]: Dr | Ds | Dt | LIFT, row-major  */
   const int32_t* fmask_dev;  /* [4][Nfp]                                               */
   const double* geo_dev;     /* [K][DG_GEO_STRIDE]                                     */
-  const int32_t* vmapP_dev;  /* [K][4 Nfp]                                             */
+  const int32_t* vmapP_dev;  /* [K][4 Nfp]; boundary face nodes hold -code for          */
+                             /* DG_BC_SLIP_WALL, DG_BC_NOSLIP_WALL or DG_BC_OUTFLOW     */
 } dg_mesh_tables;
 
 /* Same stage as dg_rk_stage for a viscous perfect gas (gas->model ==
  * DG_GAS_PERFECT, gas->mu > 0): k <- a_s k + dt rhs(q_in), q_out <- q_in + b_s k,
  * with the same kernels, on caller-owned tables and buffers.  status_dev: one
  * uint32 in device memory that receives DG_STATUS_* bits (atomic OR; the
- * caller clears it).  Rejects K * Np > DG_STATIC_SCRATCH_NODES with
- * DG_ERR_INVALID_ARG.  The first call on a device looks up the device address
- * of the static array (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call shares the one array
- * and leaves its content behind; the stage writes all of it that it reads, so
- * nothing needs clearing, but calls that overlap in time on the GPU (other
- * streams, other host threads) race on it and must be serialised. */
+ * caller clears it).  Periodic faces and wall and outflow boundary faces are
+ * supported; there is no inflow state here, so a face coded DG_BC_INFLOW gets a
+ * zero ghost density, which sets DG_STATUS_NONPHYSICAL (the tables are device
+ * memory and are not read on the host).  Rejects K * Np > DG_STATIC_SCRATCH_NODES
+ * with DG_ERR_INVALID_ARG.  Each call looks up the static array's device address
+ * in the current context (cudaGetSymbolAddress); the first call on a device
+ * loads the code module (see above) and must come before any stream capture.  Every
+ * call shares the one array and leaves its content behind; the stage writes all
+ * of it that it reads, so nothing needs clearing, but calls that overlap in time
+ * on the GPU (other streams, other host threads) race on it and must be
+ * serialised. */
 int dg_rk_stage_noalloc(const dg_mesh_tables* tables, const dg_gas_desc* gas, int32_t stage, double dt,
                         const double* q_in_dev, double* q_out_dev, double* k_dev, uint32_t* status_dev,
                         void* stream);

@@ -1,4 +1,4 @@
-"""Small MLP for the temperature initial guess: FP64 forward pass and backpropagation.
+"""Small MLP for the temperature initial guess: FP64 forward pass, backpropagation and Adam step.
 
 Not in the paper (it appears only as a requirement of this build's learned form):
 an 8 -> 64 -> 64 -> 1 perceptron with tanh hidden layers maps normalised
@@ -10,6 +10,10 @@ Parameter vector (the library's flat layout, float):
     W1 [64][8], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1]   (4801 values)
 Model:  h1 = tanh(W1 x + b1),  h2 = tanh(W2 h1 + b2),  y = W3 . h2 + b3
 Loss:   L = mean over the batch of (y - t)^2
+Update: Adam (Kingma & Ba, "Adam: A Method for Stochastic Optimization", ICLR 2015, Algorithm 1).
+
+Test infrastructure only: the tests, the smoke check and the benchmark's CPU baseline use it; the
+library never does.
 """
 
 from __future__ import annotations
@@ -77,3 +81,19 @@ def init_params(seed=0):
         else:
             parts[name] = np.zeros(shape)
     return pack(parts)
+
+
+def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step number t >= 1, in FP64.
+
+    First and second raw moment estimates m, v are exponential averages of the gradient and its
+    square; dividing them by 1 - beta^t removes the bias of their zero initialisation; the step is
+    lr * m_hat / (sqrt(v_hat) + eps).  Returns (theta', m', v').
+    """
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    theta = np.asarray(theta, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return theta, m, v

@@ -7,6 +7,7 @@ Translation units are compiled in parallel into ``_build/`` and linked into
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -27,17 +28,27 @@ def _sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
-def _headers_mtime():
-    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+def _headers():
+    hs = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
     hs.append(os.path.join(INCLUDE, "dg.h"))
-    return max(os.path.getmtime(h) for h in hs)
+    return hs
+
+
+def _digest(cmd, path):
+    """Hash of the compile command, the source and every header: an object is reused only when all
+    of them are byte-identical to the ones it was built from (timestamps are not trusted: a copied
+    tree keeps stale objects newer than their sources)."""
+    h = hashlib.sha256(" ".join(cmd).encode())
+    for f in [path] + _headers():
+        with open(f, "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def _compile(src, verbose=False, ptxas_info=False):
     path = os.path.join(CSRC, src)
     obj = os.path.join(BUILD, src + ".o")
-    if os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(path), _headers_mtime()):
-        return obj, ""
     if src.endswith(".cu"):
         cmd = [NVCC, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                "-c", path, "-o", obj]
@@ -46,9 +57,17 @@ def _compile(src, verbose=False, ptxas_info=False):
     else:
         cmd = ["g++", "-O2", "-fPIC", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-I",
                os.path.join(CUDA_HOME, "include"), "-c", path, "-o", obj]
+    stamp = obj + ".sha256"
+    key = _digest(cmd, path) + " " + os.uname().machine
+    if not ptxas_info and os.path.exists(obj) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == key:
+                return obj, ""
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compiling {src} failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    with open(stamp, "w") as fh:
+        fh.write(key + "\n")
     return obj, (r.stdout + r.stderr) if (verbose or ptxas_info) else ""
 
 

@@ -479,6 +479,9 @@ int dg_gas_create(const dg_gas_desc* desc, dg_gas* out) {
       if (!(desc->W[k] > 0)) return fail(DG_ERR_INVALID_ARG, "molar masses must be > 0");
       p.Rk[k] = desc->R_universal / desc->W[k];
       for (int i = 0; i < 7; ++i) p.a[k][i] = desc->nasa7[7 * k + i];
+      const double* a = p.a[k];
+      const double fc[6] = {a[5], a[0] - 1.0, a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0};
+      for (int j = 0; j < 6; ++j) p.fc[k][j] = p.Rk[k] * fc[j];
     }
     p.newton_tol = desc->newton_tol;
     p.newton_max_it = desc->newton_max_it;
@@ -582,6 +585,15 @@ int dg_mlp_loss_grad(int64_t n, const float* params, const float* x, const float
   if (!params || !x || !t || !grad || !loss) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
   cudaError_t e = dg::mlp_loss_grad(n, params, x, t, grad, loss, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "MLP gradient kernel");
+  return DG_OK;
+}
+
+int dg_mlp_adam_step(int32_t t, float lr, float* params, float* grad, float* m, float* v, void* stream) {
+  if (!params || !grad || !m || !v) return fail(DG_ERR_INVALID_ARG, "NULL pointer");
+  if (t < 1) return fail(DG_ERR_INVALID_ARG, "the step number t must be >= 1");
+  if (!std::isfinite(lr)) return fail(DG_ERR_INVALID_ARG, "lr must be finite");
+  cudaError_t e = dg::mlp_adam_step(t, lr, params, grad, m, v, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "Adam kernel");
   return DG_OK;
 }
 

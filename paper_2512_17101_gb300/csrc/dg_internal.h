@@ -47,6 +47,9 @@ struct GasParams {  // passed to kernels by value
   double gamma, R, mu, Pr, kappa, cp;
   double Rk[DG_MAX_SPECIES];
   double a[DG_MAX_SPECIES][7];
+  // NASA-7: species k's share of the internal-energy quintic per unit mass fraction,
+  // e_k(T) = sum_j fc[k][j] T^j = R_k (a6 + (a1 - 1) T + a2/2 T^2 + a3/3 T^3 + a4/4 T^4 + a5/5 T^5)
+  double fc[DG_MAX_SPECIES][6];
   double newton_tol;
   int newton_max_it;
   double Sc;        // NASA-7 with viscosity: Schmidt number, rho D = mu / Sc
@@ -200,11 +203,14 @@ struct dg_gas_s {
 
 namespace dg {
 // k_mlp.cu
+// wait_polls: polls per mbarrier wait of the inference MMAs (0 = the default bound).
 cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, double* T, int32_t* iters, int guess_only,
-                                   cudaStream_t s, const MixturePrims& mp = MixturePrims());
+                                   cudaStream_t s, const MixturePrims& mp = MixturePrims(), int wait_polls = 0);
 cudaError_t mlp_set_params(dg_gas gas, const float* theta_host, const dg_mlp_norm& nrm);
 cudaError_t mlp_loss_grad(int64_t n, const float* theta, const float* X, const float* t, float* grad, float* loss,
                           cudaStream_t s);
+// One Adam step (step number t >= 1) on the DG_MLP_PARAMS parameters; zeroes grad.
+cudaError_t mlp_adam_step(int t, float lr, float* theta, float* grad, float* m, float* v, cudaStream_t s);
 cudaError_t mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* Y_dev, const double* T_dev,
                       const dg_mlp_train_opts& o, const float* init_host, float* history);
 }  // namespace dg

@@ -1,12 +1,21 @@
 // Per-node temperature Newton solve of a NASA-7 mixture, shared by the seeded kernel
-// (k_thermo.cu) and the MLP-seeded kernel (k_mlp.cu), and the mixed-precision form's
-// per-node outputs that the converged solve yields almost for free.
+// (k_thermo.cu) and the MLP-seeded kernel (k_mlp.cu), and the per-node outputs that the
+// converged solve yields almost for free.
 //
-// For fixed Y the mixture internal energy is a quintic in T whose coefficients c[0..5]
-// fold the species sums (sum_k Y_k R_k a_kj / (j+1), the -R_mix T of e = h - R T included);
-// each Newton update evaluates e(T) and cv(T) = de/dT by Horner and takes
-// T <- T - (e(T) - e) / cv(T) until |dT| < tol (capped).
-// At the converged T: cp = cv + R_mix, p = rho R_mix T, c^2 = cp/cv p/rho = R_mix T (cv + R_mix)/cv.
+// For fixed mass fractions the internal energy per unit volume is a quintic in T,
+//   rho e(T) = sum_j C_j T^j,   C_j = sum_k (rho Y_k) fc[k][j]
+// (fc folds R_k, the 1/(j+1) of the enthalpy integral and the -R_k T of e = h - R T; the gas
+// precomputes it), so a node folds its species once and every Newton update evaluates the quintic
+// and its derivative rho cv(T) by Horner:
+//   T <- T - (rho e(T) - rho e) / (rho cv(T))   until |dT| < tol (capped).
+// Working per unit volume leaves the iterates unchanged (numerator and denominator both carry rho)
+// and saves the seven divisions of rho Y_k by rho.  At the converged T: p = rho R_mix T with
+// rho R_mix = sum_k (rho Y_k) R_k, and c^2 = R_mix T (cv + R_mix) / cv.
+//
+// The block solve runs the updates in rounds: in each round every still-active node takes one
+// update, and the nodes that have not converged are packed onto the first threads of the block for
+// the next round.  A round costs ceil(active / 32) warp-updates, so the solve costs the mean number
+// of updates per node rather than the maximum over each warp's 32 nodes.
 #pragma once
 
 #include "dg_cvt.cuh"
@@ -22,54 +31,122 @@ __device__ __forceinline__ double rcp64(double x) {
   return r * fma(-x, r, 2.0);
 }
 
-// Fold the species polynomials into the quintic e(T) = c0 + c1 T + ... + c5 T^5 (J/kg).
-__device__ __forceinline__ void fold(const GasParams& g, const double* Y, double c[6], double& Rmix) {
+// FP64 square root of x > 0 from an FP32 reciprocal-square-root seed y0: one Newton step for
+// 1/sqrt(x) (y1 = y0 (3 - x y0^2) / 2), then s = x y1 corrected once by s + y1 (x - s^2) / 2
+// (relative error ~1e-15); zero and negative inputs give the hardware result.
+__device__ __forceinline__ double sqrt64(double x) {
+  if (!(x > 0.0)) return sqrt(x);
+  const double y0 = cvt::widen(rsqrtf(cvt::narrow(x)));
+  const double y1 = y0 * fma(-0.5 * x * y0, y0, 1.5);
+  const double s = x * y1;
+  return fma(0.5 * y1, fma(-s, s, x), s);
+}
+
+// Fold the species of one node: C[0..5] of rho e(T) and rho R_mix, from the partial densities
+// rhoY[0..ns).
+__device__ __forceinline__ void fold(const GasParams& g, const double* rhoY, double C[6], double& rhoR) {
 #pragma unroll
-  for (int j = 0; j < 6; ++j) c[j] = 0.0;
-  Rmix = 0.0;
+  for (int j = 0; j < 6; ++j) C[j] = 0.0;
+  rhoR = 0.0;
 #pragma unroll
   for (int k = 0; k < DG_MAX_SPECIES; ++k) {
     if (k >= g.ns) break;
-    const double yr = Y[k] * g.Rk[k];
-    const double* a = g.a[k];
-    Rmix += yr;
-    c[0] = fma(yr, a[5], c[0]);
-    c[1] = fma(yr, a[0] - 1.0, c[1]);
-    c[2] = fma(yr, a[1] * 0.5, c[2]);
-    c[3] = fma(yr, a[2] * (1.0 / 3.0), c[3]);
-    c[4] = fma(yr, a[3] * 0.25, c[4]);
-    c[5] = fma(yr, a[4] * 0.2, c[5]);
+    const double r = rhoY[k];
+    rhoR = fma(r, g.Rk[k], rhoR);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) C[j] = fma(r, g.fc[k][j], C[j]);
   }
 }
 
-// Newton from seed t; returns true when |dT| < tol was met within max_it updates.  On return
-// t is the solution, it the updates taken and cv the heat capacity at the last iterate.
-__device__ __forceinline__ bool solve(const double c[6], double e, double& t, int max_it, double tol, int& it,
-                                      double& cv) {
-  it = 0;
-  cv = 1.0;
-  while (it < max_it) {
-    const double eT = c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * (c[4] + t * c[5]))));
-    cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
-    const double dT = (eT - e) * rcp64(cv);
-    t -= dT;
-    ++it;
-    if (fabs(dT) < tol) return true;
-  }
-  return false;
+// rho cv(T) = d(rho e)/dT.
+__device__ __forceinline__ double heat_capacity(const double C[6], double t) {
+  return fma(t, fma(t, fma(t, fma(t, 5.0 * C[5], 4.0 * C[4]), 3.0 * C[3]), 2.0 * C[2]), C[1]);
 }
 
-// The mixed-precision form's node record from the converged temperature t (cv at the last
-// iterate): the float state, p = rho R_mix t as a float pair, and the sound speed from c^2 formed
-// in FP64 and rounded once.
+// Block-level solve state for NB nodes (slot = thread index).  D holds the derivative
+// coefficients 2 C2, 3 C3, 4 C4, 5 C5 so that an update reloads them instead of recomputing.
+template <int NB>
+struct Rounds {
+  double C[6][NB];
+  double D[4][NB];
+  double e[NB];  // rho e of the node
+  double t[NB];  // current iterate
+  int it[NB];    // updates taken
+  int list[2][NB];
+  int count[3];
+};
+
+// All 32 lanes of the warp call this: lanes with flag append value to list (length *cnt).
+__device__ __forceinline__ void append(int* list, int* cnt, bool flag, int value) {
+  const unsigned mask = __ballot_sync(0xffffffffu, flag);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(cnt, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (flag) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
+}
+
+// Every thread of the block (blockDim.x == NB) stages its node (valid or not): coefficients, rho e
+// and the seed; the valid slots form the first active list.  Begins with a barrier so that the
+// previous use of R is over.
+template <int NB>
+__device__ __forceinline__ void stage(Rounds<NB>& R, bool valid, const double C[6], double rho_e, double seed) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  if (tid == 0) R.count[0] = R.count[1] = R.count[2] = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) R.C[j][tid] = C[j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) R.D[j][tid] = (double)(j + 2) * C[j + 2];
+  R.e[tid] = rho_e;
+  R.t[tid] = seed;
+  R.it[tid] = 0;
+  __syncthreads();
+  append(R.list[0], &R.count[0], valid, tid);
+  __syncthreads();
+}
+
+// Newton rounds over the staged nodes; returns true when some node had not converged after
+// max_it updates (block-uniform).  On return R.t and R.it hold every slot's result.
+template <int NB>
+__device__ __forceinline__ bool rounds(Rounds<NB>& R, int max_it, double tol) {
+  const int tid = threadIdx.x;
+  int m = R.count[0];
+  for (int r = 0; m > 0 && r < max_it; ++r) {
+    bool again = false;
+    int slot = 0;
+    if (tid < m) {
+      slot = R.list[r & 1][tid];
+      const double t = R.t[slot];
+      const double eT = fma(t, fma(t, fma(t, fma(t, fma(t, R.C[5][slot], R.C[4][slot]), R.C[3][slot]),
+                                             R.C[2][slot]), R.C[1][slot]), R.C[0][slot]);
+      const double cv = fma(t, fma(t, fma(t, fma(t, R.D[3][slot], R.D[2][slot]), R.D[1][slot]), R.D[0][slot]),
+                            R.C[1][slot]);
+      const double dT = (eT - R.e[slot]) * rcp64(cv);
+      R.t[slot] = t - dT;
+      R.it[slot] = r + 1;
+      again = !(fabs(dT) < tol);
+    }
+    if (tid == 0) R.count[(r + 2) % 3] = 0;  // the list before last: nobody reads its count again
+    append(R.list[(r + 1) & 1], &R.count[(r + 1) % 3], again, slot);
+    __syncthreads();
+    m = R.count[(r + 1) % 3];
+  }
+  return m > 0;
+}
+
+// The mixed-precision form's node record from the converged temperature t: the float state,
+// p = rho R_mix t as a float pair, and the sound speed from c^2 = R_mix t (cv + R_mix) / cv formed
+// in FP64 and rounded once (rhoR = rho R_mix, rhocv = rho cv: their ratio is R_mix / cv).
 __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasParams& g, const double* __restrict__ q,
-                                            int64_t n, int64_t node, double rho, double Rmix, double t, double cv) {
+                                            int64_t n, int64_t node, double rho, double ir, double rhoR, double t,
+                                            double rhocv) {
   const int nvar = 5 + g.ns;
   float v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = 0.0f;
   const float2 rho2 = cvt::split(rho);
-  const double p = rho * Rmix * t;
+  const double p = rhoR * t;
   const float2 p2 = cvt::split(p);
   if (!(rho2.x > 0.0f) || !(p2.x > 0.0f)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
   v[0] = rho2.x;
@@ -77,7 +154,7 @@ __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasPar
   v[4] = cvt::narrow(q[4 * n + node]);
   v[5] = p2.x;
   v[6] = p2.y;
-  const double c2 = Rmix * t * fma(Rmix, rcp64(cv), 1.0);
+  const double c2 = p * ir * fma(rhoR, rcp64(rhocv), 1.0);
   v[7] = sqrtf(cvt::narrow(c2));
   for (int k = 0; k < nvar - 5; ++k) v[8 + k] = cvt::narrow(q[(5 + k) * n + node]);
   float4* r = mp.rec + 4 * node;
@@ -88,16 +165,28 @@ __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasPar
 }
 
 // The FP64 form's primitives at the converged temperature t: 1/rho, p = rho R_mix t and
-// c = sqrt(cp/cv p/rho), with cv = de/dT of the folded quintic at t and cp = cv + R_mix.
-__device__ __forceinline__ void store_prims64(const MixturePrims& mp, const double c[6], int64_t n, int64_t node,
-                                              double rho, double Rmix, double t) {
-  const double cv = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * (4.0 * c[4] + t * 5.0 * c[5])));
-  const double ir = 1.0 / rho;
-  const double p = rho * Rmix * t;
+// c = sqrt(c^2), c^2 = (p / rho) (1 + R_mix / cv).
+__device__ __forceinline__ void store_prims64(const MixturePrims& mp, int64_t n, int64_t node, double rho, double ir,
+                                              double rhoR, double t, double rhocv) {
+  const double p = rhoR * t;
   if (!(rho > 0.0) || !(p > 0.0)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
   mp.prim[node] = ir;
   mp.prim[n + node] = p;
-  mp.prim[2 * n + node] = sqrt((cv + Rmix) / cv * p * ir);
+  mp.prim[2 * n + node] = sqrt64(p * ir * fma(rhoR, rcp64(rhocv), 1.0));
+}
+
+// Loads node i of q [5 + ns][n]: rho, its reciprocal, rho e = rho E - |rho u|^2 / (2 rho) and the
+// fold of the partial densities.
+__device__ __forceinline__ void load_node(const GasParams& g, const double* __restrict__ q, int64_t n, int64_t i,
+                                          double& rho, double& ir, double& rho_e, double C[6], double& rhoR,
+                                          double* rhoY) {
+  rho = q[i];
+  ir = rcp64(rho);
+  const double mx = q[n + i], my = q[2 * n + i], mz = q[3 * n + i];
+  rho_e = fma(-0.5 * ir, fma(mx, mx, fma(my, my, mz * mz)), q[4 * n + i]);
+#pragma unroll
+  for (int k = 0; k < DG_MAX_SPECIES; ++k) rhoY[k] = k < g.ns ? q[(5 + k) * n + i] : 0.0;
+  fold(g, rhoY, C, rhoR);
 }
 
 }  // namespace newton

@@ -5,9 +5,12 @@
 //   * training, FP32: per-sample forward and backward passes, gradients summed
 //     over each block's samples in shared memory and added to the batch gradient,
 //     then an Adam update; samples come from the Newton solver;
-//   * inference, FP16 operands with FP32 accumulation on the tensor cores
-//     (mma.sync m16n8k16), fused with the FP64 Newton iteration that it seeds:
-//     Newton stays the arbiter and the fallback, to the same |dT| < tol.
+//   * inference, FP16 operands with FP32 accumulation on the fifth-generation tensor
+//     cores: a block takes 128 nodes as the M = 128 rows of two tcgen05 MMAs (features
+//     x W1^T, then tanh(.) x W2^T, accumulators in tensor memory), the activations
+//     through the hardware tanh on FP16 pairs; the guess seeds the FP64 Newton solve
+//     of the same nodes (dg_newton.cuh), which stays the arbiter and the fallback, to
+//     the same |dT| < tol.
 //
 // Flat parameter layout (float): W1 [64][8] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64] | b3.
 #include <cuda_fp16.h>
@@ -18,6 +21,7 @@
 #include <vector>
 
 #include "dg_newton.cuh"
+#include "dg_umma.cuh"
 
 namespace dg {
 namespace {
@@ -130,11 +134,13 @@ constexpr size_t kGradSmem = sizeof(float) * (DG_MLP_PARAMS + TS * NI + 4 * TS *
 
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ grad, float* __restrict__ m,
                             float* __restrict__ v, float lr, float bc1, float bc2) {
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  // beta1 = 0.9, beta2 = 0.999 and 1 - beta each rounded to FP32 once (1.0f - 0.999f would be
+  // 1.3e-5 away from 0.001, and the bias corrections bc1, bc2 are formed from the exact decimals)
+  const float b1 = 0.9f, b2 = 0.999f, c1 = 0.1f, c2 = 0.001f, eps = 1e-8f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < DG_MLP_PARAMS; i += gridDim.x * blockDim.x) {
     const float g = grad[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * g;
-    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    const float mi = fmaf(b1, m[i], c1 * g);
+    const float vi = fmaf(b2, v[i], c2 * g * g);
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
@@ -153,32 +159,43 @@ __global__ void features_kernel(int64_t n, int ns, const double* __restrict__ e,
   }
 }
 
-// FP16 inference weights: W1 [64][16] (k padded with zeros), W2 [64][64]
-__global__ void to_half_kernel(const float* __restrict__ theta, __half* __restrict__ w1h, __half* __restrict__ w2h) {
+// ---- inference on the tensor cores, fused with Newton ------------------------------------------
+// Operands in shared memory in the UMMA K-major layout without swizzle: 8-row x 16-byte core
+// matrices, LBO = 128 B between core matrices adjacent in K, SBO between 8-row groups.
+//   A1 [128 nodes][16]: the 8 features (columns 8..15 zero)          SBO 256
+//   B1 [64 units][16]:  W1 (input columns 8..15 zero)                  SBO 256
+//   A2 [128 nodes][64]: tanh(h1) in FP16                               SBO 1024
+//   B2 [64 units][64]:  W2                                             SBO 1024
+// MMA 1: D[128][64] = A1 . B1^T (K = 16); MMA 2: D = A2 . B2^T (four K = 16 steps), both into
+// the same 64 TMEM columns (the first accumulator is read out before the second MMA is issued).
+constexpr int kMlpRows = 128;
+constexpr int A1_SBO = 256, A2_SBO = 1024, LBO = 128;
+constexpr int W1_IMG = NH / 8 * A1_SBO, W2_IMG = NH / 8 * A2_SBO;  // bytes: 2 KB, 8 KB
+
+__host__ __device__ constexpr int umma_off(int row, int k, int sbo) {
+  return (row >> 3) * sbo + (k >> 3) * LBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// The FP16 weight images (W1 padded to 16 inputs), exactly as the inference block holds them.
+__global__ void mlp_image_kernel(const float* __restrict__ theta, __half* __restrict__ w1img,
+                                 __half* __restrict__ w2img) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NH * 16 + NH * NH; i += gridDim.x * blockDim.x) {
     if (i < NH * 16) {
       const int j = i / 16, k = i - j * 16;
-      w1h[i] = __float2half_rn(k < NI ? theta[P_W1 + j * NI + k] : 0.0f);
+      w1img[umma_off(j, k, A1_SBO) / 2] = __float2half_rn(k < NI ? theta[P_W1 + j * NI + k] : 0.0f);
     } else {
-      w2h[i - NH * 16] = __float2half_rn(theta[P_W2 + i - NH * 16]);
+      const int i2 = i - NH * 16, r = i2 / NH, k = i2 - r * NH;
+      w2img[umma_off(r, k, A2_SBO) / 2] = __float2half_rn(theta[P_W2 + r * NH + k]);
     }
   }
 }
 
-// ---- inference fused with Newton ----------------------------------------------------------------
-__device__ __forceinline__ void mma16816h(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Hardware tanh (tanh.approx.f32, about 11 correct bits): the inference only seeds Newton,
-// which stays the arbiter of T; training uses the precise tanhf.
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+// tanh of two floats through the hardware approximation on an FP16 pair (about 11 correct bits:
+// the guess only seeds Newton); the result's low half is tanh(lo).
+__device__ __forceinline__ uint32_t tanh_pair(float lo, float hi) {
+  uint32_t x, y;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(x) : "f"(hi), "f"(lo));
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x));
   return y;
 }
 
@@ -186,122 +203,169 @@ __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
   return (uint32_t)__half_as_ushort(__float2half_rn(lo)) | ((uint32_t)__half_as_ushort(__float2half_rn(hi)) << 16);
 }
 
-constexpr int W1S = 12;  // words per row of W1 (16 halves + 8 pad)
-constexpr int W2S = 36;  // words per row of W2 (64 halves + 8 pad)
-constexpr int XS = 12;   // words per row of the input tile
-
 struct MlpDev {
-  const uint32_t* w1h;  // [64][8] words
-  const uint32_t* w2h;  // [64][32] words
-  const float* theta;   // fp32 master (biases, W3)
+  const uint4* w1img;  // [W1_IMG / 16]
+  const uint4* w2img;  // [W2_IMG / 16]
+  const float* theta;  // fp32 master (biases, W3)
   dg_mlp_norm nrm;
 };
 
-// Per node: the MLP guess (mode DG_TSEED_MLP) or the given seed, then Newton.
-// 4 warps per block; each warp handles groups of 32 nodes (two 16-row tiles).
-__global__ void __launch_bounds__(128) temperature_mlp_kernel(const GasParams g, const int64_t n,
-                                                              const double* __restrict__ q, double* __restrict__ T,
-                                                              int32_t* __restrict__ iters, const MlpDev mlp,
-                                                              const int guess_only, unsigned* __restrict__ status,
-                                                              const MixturePrims mp) {
-  __shared__ uint32_t sW1[NH * W1S];
-  __shared__ uint32_t sW2[NH * W2S];
-  __shared__ float sb1[NH], sb2[NH], sW3[NH];
-  __shared__ uint32_t sX[4][32 * XS];
-  __shared__ float sY[4][32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  for (int i = tid; i < NH * 8; i += blockDim.x) sW1[(i / 8) * W1S + (i % 8)] = mlp.w1h[i];
-  for (int i = tid; i < NH * 32; i += blockDim.x) sW2[(i / 32) * W2S + (i % 32)] = mlp.w2h[i];
-  for (int i = tid; i < NH; i += blockDim.x) {
-    sb1[i] = mlp.theta[P_B1 + i];
-    sb2[i] = mlp.theta[P_B2 + i];
-    sW3[i] = mlp.theta[P_W3 + i];
+struct __align__(128) MlpSmem {
+  unsigned char B1[W1_IMG];
+  unsigned char B2[W2_IMG];
+  unsigned char A1[kMlpRows / 8 * A1_SBO];
+  unsigned char A2[kMlpRows / 8 * A2_SBO];
+  float b1[NH], b2[NH], w3[NH];
+  newton::Rounds<kMlpRows> R;
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
+};
+static_assert(sizeof(MlpSmem) <= 48 * 1024, "static shared memory");
+
+// 128 nodes per tile, one per thread (thread i = MMA row i = TMEM lane i): features, the two MMAs,
+// the guess, then (unless guess_only) the block's Newton rounds from it.
+__global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasParams g, const int64_t n,
+                                                                   const double* __restrict__ q,
+                                                                   double* __restrict__ T, int32_t* __restrict__ iters,
+                                                                   const MlpDev mlp, const int guess_only,
+                                                                   unsigned* __restrict__ status,
+                                                                   const MixturePrims mp, const int wait_polls) {
+  __shared__ MlpSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < W1_IMG / 16; i += kMlpRows) reinterpret_cast<uint4*>(S.B1)[i] = mlp.w1img[i];
+  for (int i = tid; i < W2_IMG / 16; i += kMlpRows) reinterpret_cast<uint4*>(S.B2)[i] = mlp.w2img[i];
+  for (int i = tid; i < (int)sizeof(S.A1) / 16; i += kMlpRows)
+    reinterpret_cast<uint4*>(S.A1)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < NH; i += kMlpRows) {
+    S.b1[i] = mlp.theta[P_B1 + i];
+    S.b2[i] = mlp.theta[P_B2 + i];
+    S.w3[i] = mlp.theta[P_W3 + i];
   }
   const float b3 = mlp.theta[P_B3];
+  const float e_mean = (float)mlp.nrm.e_mean, inv_e_scale = (float)(1.0 / mlp.nrm.e_scale);
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(&S.bar), 1);
+    S.abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&S.tmem), NH);
+  tc::fence_async_smem();
+  tc::tc_fence_before();
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * 4 * 32;
-  for (int64_t g0 = ((int64_t)blockIdx.x * 4 + warp) * 32; g0 < n; g0 += stride) {
-    const int64_t node = g0 + lane;
-    const bool valid = node < n;
-    double e = 0.0, rho = 1.0, Rmix = 0.0, c[6] = {0, 0, 0, 0, 0, 0};
+  tc::tc_fence_after();
+  const uint32_t tm_lane = S.tmem + ((uint32_t)(warp * 32) << 16);  // this warp's quarter of the lanes
+  const uint32_t bar = tc::smem_u32(&S.bar);
+  constexpr uint32_t IDESC = tc::idesc_f16(kMlpRows, NH);
+  uint32_t phase = 0;
+  const int64_t ntiles = (n + kMlpRows - 1) / kMlpRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t i = tile * kMlpRows + tid;
+    const bool valid = i < n;
+    double rho = 1.0, ir = 1.0, rho_e = 0.0, C[6] = {0, 0, 0, 0, 0, 0}, rhoR = 0.0;
     float feat[NI] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid) {
-      rho = q[node];
-      const double ir = newton::rcp64(rho);
-      const double mx = q[n + node], my = q[2 * n + node], mz = q[3 * n + node];
-      e = q[4 * n + node] * ir - 0.5 * ir * ir * (mx * mx + my * my + mz * mz);
-      feat[0] = (float)((e - mlp.nrm.e_mean) / mlp.nrm.e_scale);
-      double Y[DG_MAX_SPECIES];
+      double rhoY[DG_MAX_SPECIES];
+      newton::load_node(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
+      feat[0] = (cvt::narrow(rho_e * ir) - e_mean) * inv_e_scale;
+      const float irf = cvt::narrow(ir);
 #pragma unroll
-      for (int k = 0; k < DG_MAX_SPECIES; ++k) {
-        Y[k] = k < g.ns ? q[(5 + k) * n + node] * ir : 0.0;
-        if (k < NI - 1) feat[1 + k] = (float)Y[k];
-      }
-      newton::fold(g, Y, c, Rmix);
+      for (int k = 0; k < NI - 1; ++k) feat[1 + k] = k < g.ns ? cvt::narrow(rhoY[k]) * irf : 0.0f;
     }
-    uint32_t* xr = sX[warp] + lane * XS;
+    *reinterpret_cast<uint4*>(S.A1 + umma_off(tid, 0, A1_SBO)) =
+        make_uint4(pack_half2(feat[0], feat[1]), pack_half2(feat[2], feat[3]), pack_half2(feat[4], feat[5]),
+                   pack_half2(feat[6], feat[7]));
+    // layer 1
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (S.abort) break;
+    if (tid == 0) {
+      tc::tc_fence_after();
+      tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(S.A1), LBO, A1_SBO), tc::umma_desc(tc::smem_u32(S.B1), LBO,
+                                                                                         A1_SBO),
+                   IDESC, 0u);
+      tc::mma_commit(bar);
+    }
+    if (!tc::mbar_wait(bar, phase, wait_polls)) {
+      S.abort = 1;
+      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+    }
+    phase ^= 1u;
+    tc::tc_fence_after();
+    {
+      float acc[32];
 #pragma unroll
-    for (int k = 0; k < NI / 2; ++k) xr[k] = pack_half2(feat[2 * k], feat[2 * k + 1]);
+      for (int half = 0; half < 2; ++half) {
+        tc::tmem_ld32(tm_lane + (uint32_t)(32 * half), acc);
+        uint32_t w[16];
 #pragma unroll
-    for (int k = NI / 2; k < 8; ++k) xr[k] = 0u;
-    __syncwarp();
+        for (int j = 0; j < 16; ++j)
+          w[j] = tanh_pair(acc[2 * j] + S.b1[32 * half + 2 * j], acc[2 * j + 1] + S.b1[32 * half + 2 * j + 1]);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const uint32_t* x0 = sX[warp] + (mt * 16 + gq) * XS;
-      const uint32_t* x1 = sX[warp] + (mt * 16 + gq + 8) * XS;
-      const uint32_t a1[4] = {x0[tq], x1[tq], x0[4 + tq], x1[4 + tq]};
-      uint32_t a2[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        float cc[4] = {0, 0, 0, 0};
-        const uint32_t* w = sW1 + (nt * 8 + gq) * W1S;
-        mma16816h(cc, a1, w[tq], w[4 + tq]);
-        const int col = nt * 8 + 2 * tq;
-        const float h0 = tanh_fast(cc[0] + sb1[col]), h1 = tanh_fast(cc[1] + sb1[col + 1]);
-        const float h2 = tanh_fast(cc[2] + sb1[col]), h3 = tanh_fast(cc[3] + sb1[col + 1]);
-        // accumulator tile nt becomes half of the A fragment of layer-2 k-tile nt/2
-        const int kt = nt >> 1, hi = nt & 1;
-        a2[kt][hi ? 2 : 0] = pack_half2(h0, h1);
-        a2[kt][hi ? 3 : 1] = pack_half2(h2, h3);
-      }
-      float y0 = 0.0f, y1 = 0.0f;
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        float cc[4] = {0, 0, 0, 0};
-        const uint32_t* w = sW2 + (nt * 8 + gq) * W2S;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) mma16816h(cc, a2[kt], w[kt * 8 + tq], w[kt * 8 + 4 + tq]);
-        const int col = nt * 8 + 2 * tq;
-        y0 = fmaf(sW3[col], tanh_fast(cc[0] + sb2[col]), fmaf(sW3[col + 1], tanh_fast(cc[1] + sb2[col + 1]), y0));
-        y1 = fmaf(sW3[col], tanh_fast(cc[2] + sb2[col]), fmaf(sW3[col + 1], tanh_fast(cc[3] + sb2[col + 1]), y1));
-      }
-      y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-      y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-      y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-      y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-      if (tq == 0) {
-        sY[warp][mt * 16 + gq] = y0 + b3;
-        sY[warp][mt * 16 + gq + 8] = y1 + b3;
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4*>(S.A2 + umma_off(tid, 32 * half + 8 * c, A2_SBO)) =
+              make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
       }
     }
-    __syncwarp();
-    double t = mlp.nrm.T_mean + mlp.nrm.T_scale * (double)sY[warp][lane];
+    // layer 2
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (S.abort) break;
+    if (tid == 0) {
+      tc::tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < NH / 16; ++ks)
+        tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(S.A2) + ks * 2 * LBO, LBO, A2_SBO),
+                     tc::umma_desc(tc::smem_u32(S.B2) + ks * 2 * LBO, LBO, A2_SBO), IDESC, ks > 0 ? 1u : 0u);
+      tc::mma_commit(bar);
+    }
+    if (!tc::mbar_wait(bar, phase, wait_polls)) {
+      S.abort = 1;
+      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+    }
+    phase ^= 1u;
+    tc::tc_fence_after();
+    float y = b3;
+    {
+      float acc[32];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        tc::tmem_ld32(tm_lane + (uint32_t)(32 * half), acc);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int u = 32 * half + 2 * j;
+          const uint32_t h = tanh_pair(acc[2 * j] + S.b2[u], acc[2 * j + 1] + S.b2[u + 1]);
+          const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&h));
+          y = fmaf(S.w3[u], hf.x, fmaf(S.w3[u + 1], hf.y, y));
+        }
+      }
+    }
+    double t = fma(mlp.nrm.T_scale, (double)y, mlp.nrm.T_mean);
     t = fmin(fmax(t, mlp.nrm.T_min), mlp.nrm.T_max);
-    __syncwarp();
-    if (!valid) continue;
     if (guess_only) {
-      T[node] = t;
+      if (valid) T[i] = t;
       continue;
     }
-    int it;
-    double cv;
-    if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
-    T[node] = t;
-    if (iters) iters[node] = it;
-    if (mp.rec) newton::store_prims(mp, g, q, n, node, rho, Rmix, t, cv);
-    if (mp.prim) newton::store_prims64(mp, c, n, node, rho, Rmix, t);
+    newton::stage(S.R, valid, C, rho_e, t);
+    if (newton::rounds(S.R, g.newton_max_it, g.newton_tol) && tid == 0) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+    if (!valid) continue;
+    t = S.R.t[tid];
+    T[i] = t;
+    if (iters) iters[i] = S.R.it[tid];
+    if (mp.rec || mp.prim) {
+      const double rhocv = newton::heat_capacity(C, t);
+      if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, ir, rhoR, t, rhocv);
+      if (mp.prim) newton::store_prims64(mp, n, i, rho, ir, rhoR, t, rhocv);
+    }
   }
+  // after an abort the MMA whose wait timed out (parity phase ^ 1) may still be in flight: one more
+  // wait, with the full bound, before its accumulator is released
+  if (S.abort && tid == 0) tc::mbar_wait(bar, phase ^ 1u);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(S.tmem, NH);
 }
 
 int sm_count() {
@@ -313,11 +377,11 @@ int sm_count() {
 
 cudaError_t ensure_half_weights(dg_gas gas) {
   if (!gas->mlp_w1h) {
-    cudaError_t e = cudaMalloc((void**)&gas->mlp_w1h, sizeof(__half) * NH * 16);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&gas->mlp_w2h, sizeof(__half) * NH * NH);
+    cudaError_t e = cudaMalloc((void**)&gas->mlp_w1h, W1_IMG);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&gas->mlp_w2h, W2_IMG);
     if (e != cudaSuccess) return e;
   }
-  to_half_kernel<<<16, 256>>>(gas->mlp_theta, (__half*)gas->mlp_w1h, (__half*)gas->mlp_w2h);
+  mlp_image_kernel<<<16, 256>>>(gas->mlp_theta, (__half*)gas->mlp_w1h, (__half*)gas->mlp_w2h);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e;
@@ -326,12 +390,15 @@ cudaError_t ensure_half_weights(dg_gas gas) {
 }  // namespace
 
 cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, double* T, int32_t* iters, int guess_only,
-                                   cudaStream_t s, const MixturePrims& mp) {
+                                   cudaStream_t s, const MixturePrims& mp, int wait_polls) {
   if (n <= 0) return cudaSuccess;
-  MlpDev m{(const uint32_t*)gas->mlp_w1h, (const uint32_t*)gas->mlp_w2h, gas->mlp_theta, gas->mlp_norm};
-  const int64_t groups = (n + 31) / 32;
-  int blocks = (int)std::min<int64_t>((groups + 3) / 4, (int64_t)sm_count() * 16);
-  temperature_mlp_kernel<<<blocks, 128, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status, mp);
+  MlpDev m{(const uint4*)gas->mlp_w1h, (const uint4*)gas->mlp_w2h, gas->mlp_theta, gas->mlp_norm};
+  static int per_sm = 0;
+  if (!per_sm) per_sm = std::max(1, resident_blocks((const void*)temperature_mlp_kernel, kMlpRows, 0, NH));
+  const int64_t tiles = (n + kMlpRows - 1) / kMlpRows;
+  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm * device_sms());
+  temperature_mlp_kernel<<<blocks, kMlpRows, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status, mp,
+                                                     wait_polls > 0 ? wait_polls : tc::kWaitPolls);
   return cudaGetLastError();
 }
 
@@ -359,6 +426,13 @@ cudaError_t mlp_loss_grad(int64_t n, const float* theta, const float* X, const f
   }
   const int64_t blocks = (n + TS - 1) / TS;
   mlp_grad_kernel<<<(unsigned)blocks, TS, kGradSmem, s>>>(theta, X, t, n, 1.0f / (float)n, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam_step(int t, float lr, float* theta, float* grad, float* m, float* v, cudaStream_t s) {
+  // bias corrections 1 - beta^t formed in FP64 and rounded once
+  const float bc1 = (float)(1.0 - std::pow(0.9, (double)t)), bc2 = (float)(1.0 - std::pow(0.999, (double)t));
+  adam_kernel<<<(DG_MLP_PARAMS + 255) / 256, 256, 0, s>>>(theta, grad, m, v, lr, bc1, bc2);
   return cudaGetLastError();
 }
 
@@ -406,7 +480,7 @@ cudaError_t mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* 
                                                  (int)kGradSmem);
   const int64_t batch = o.batch;
   const int64_t nb = n / batch;  // full batches only
-  double b1t = 1.0, b2t = 1.0;
+  int64_t step = 0;
   float lr = o.lr;
   for (int ep = 0; ep < o.epochs && e == cudaSuccess; ++ep) {
     e = cudaMemset(loss, 0, sizeof(float));
@@ -414,11 +488,8 @@ cudaError_t mlp_train(dg_gas gas, int64_t n, const double* e_dev, const double* 
       const int64_t off = ((b + (int64_t)ep * 7919) % nb) * batch;  // batch order rotates per epoch
       mlp_grad_kernel<<<(unsigned)((batch + TS - 1) / TS), TS, kGradSmem>>>(theta, X + off * NI, t + off, batch,
                                                                              1.0f / (float)batch, grad, loss);
-      b1t *= 0.9;
-      b2t *= 0.999;
-      adam_kernel<<<(DG_MLP_PARAMS + 255) / 256, 256>>>(theta, grad, m, v, lr, (float)(1.0 - b1t),
-                                                        (float)(1.0 - b2t));
       e = cudaGetLastError();
+      if (e == cudaSuccess) e = mlp_adam_step((int)std::min<int64_t>(++step, 1 << 30), lr, theta, grad, m, v, 0);
     }
     float l = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpy(&l, loss, sizeof(float), cudaMemcpyDeviceToHost);

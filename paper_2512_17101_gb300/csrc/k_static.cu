@@ -3,7 +3,6 @@
 // callers that cannot allocate device memory.  No counterpart in the paper.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "dg_kernels.cuh"
@@ -13,24 +12,15 @@ namespace {
 // 9 doubles per node: the viscous flux handed from the BR1 pass to the RHS kernel.
 static __device__ __align__(256) double g_static_scratch[9 * (size_t)DG_STATIC_SCRATCH_NODES];
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
-
-// Device address of g_static_scratch on the current device (looked up once per device).
+// Device address of g_static_scratch in the current context.  Looked up on every call rather
+// than cached: cudaGetSymbolAddress is a host-side table lookup once the module is loaded, and a
+// cached address would go stale after cudaDeviceReset or a reset of the primary context.  The
+// first lookup in a context loads this file's module (lazy module loading) and commits the array.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

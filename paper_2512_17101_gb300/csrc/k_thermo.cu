@@ -7,32 +7,47 @@
 // so each node first folds the species sums into six coefficients; every
 // Newton update then costs two Horner evaluations and a reciprocal:
 //   T <- T - (e(T) - e) / cv(T),  cv = de/dT,  until |dT| < tol (capped)
-// (dg_newton.cuh).  In the mixed-precision form the same kernel also writes the
-// node's pressure, sound speed and float state copy; in the FP64 form 1/rho, p and c.
+// (dg_newton.cuh; a block's nodes iterate in rounds, the unconverged ones packed
+// onto the first threads after each round).  In the mixed-precision form the same
+// kernel also writes the node's pressure, sound speed and float state copy; in the
+// FP64 form 1/rho, p and c.
+#include <algorithm>
+
 #include "dg_newton.cuh"
 
 namespace dg {
 namespace {
 
-__global__ void temperature_kernel(const GasParams g, const int64_t n, const double* __restrict__ q,
-                                   double* __restrict__ T, int32_t* __restrict__ iters, const int mode,
-                                   const double t_const, unsigned* __restrict__ status, const MixturePrims mp) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double rho = q[i], ir = newton::rcp64(rho);
-    const double mx = q[n + i], my = q[2 * n + i], mz = q[3 * n + i];
-    const double e = q[4 * n + i] * ir - 0.5 * ir * ir * (mx * mx + my * my + mz * mz);
-    double Y[DG_MAX_SPECIES];
-#pragma unroll
-    for (int k = 0; k < DG_MAX_SPECIES; ++k) Y[k] = k < g.ns ? q[(5 + k) * n + i] * ir : 0.0;
-    double c[6], Rmix, cv;
-    newton::fold(g, Y, c, Rmix);
-    double t = mode == DG_TSEED_CONST ? t_const : T[i];
-    int it;
-    if (!newton::solve(c, e, t, g.newton_max_it, g.newton_tol, it, cv)) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+constexpr int kNB = 128;  // nodes (threads) per block
+
+__global__ void __launch_bounds__(kNB) temperature_kernel(const GasParams g, const int64_t n,
+                                                          const double* __restrict__ q, double* __restrict__ T,
+                                                          int32_t* __restrict__ iters, const int mode,
+                                                          const double t_const, unsigned* __restrict__ status,
+                                                          const MixturePrims mp) {
+  __shared__ newton::Rounds<kNB> R;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (n + kNB - 1) / kNB;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t i = tile * kNB + tid;
+    const bool valid = i < n;
+    double rho = 1.0, ir = 1.0, rho_e = 0.0, C[6] = {0, 0, 0, 0, 0, 0}, rhoR = 0.0, seed = 0.0;
+    if (valid) {
+      double rhoY[DG_MAX_SPECIES];
+      newton::load_node(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
+      seed = mode == DG_TSEED_CONST ? t_const : T[i];
+    }
+    newton::stage(R, valid, C, rho_e, seed);
+    if (newton::rounds(R, g.newton_max_it, g.newton_tol) && tid == 0) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+    if (!valid) continue;
+    const double t = R.t[tid];
     T[i] = t;
-    if (iters) iters[i] = it;
-    if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, Rmix, t, cv);
-    if (mp.prim) newton::store_prims64(mp, c, n, i, rho, Rmix, t);
+    if (iters) iters[i] = R.it[tid];
+    if (mp.rec || mp.prim) {
+      const double rhocv = newton::heat_capacity(C, t);
+      if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, ir, rhoR, t, rhocv);
+      if (mp.prim) newton::store_prims64(mp, n, i, rho, ir, rhoR, t, rhocv);
+    }
   }
 }
 
@@ -66,7 +81,11 @@ cudaError_t launch_temperature(const GasParams& g, int64_t n, const double* q, d
                                int seed_mode, double t_const, unsigned* status, cudaStream_t s,
                                const MixturePrims& mp) {
   if (n <= 0) return cudaSuccess;
-  temperature_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
+  static int per_sm = 0;
+  if (!per_sm) per_sm = std::max(1, resident_blocks((const void*)temperature_kernel, kNB, 0));
+  const int64_t tiles = (n + kNB - 1) / kNB;
+  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm * device_sms());
+  temperature_kernel<<<blocks, kNB, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
   return cudaGetLastError();
 }
 

@@ -520,6 +520,14 @@ def dg_mlp_loss_grad(params, x, t, grad, loss, stream=None):
                                   _dptr(loss, torch.float32, "loss"), _stream_ptr(stream)))
 
 
+def dg_mlp_adam_step(t, lr, params, grad, m, v, stream=None):
+    """One Adam update in place on float32 CUDA tensors of DG_MLP_PARAMS values (zeroes grad)."""
+    import torch
+    check(load().dg_mlp_adam_step(int(t), float(lr), _dptr(params, torch.float32, "params"),
+                                  _dptr(grad, torch.float32, "grad"), _dptr(m, torch.float32, "m"),
+                                  _dptr(v, torch.float32, "v"), _stream_ptr(stream)))
+
+
 def dg_mlp_train(gas: Gas, e, Y, T, init_params, epochs=20, batch=4096, lr=3e-3, lr_decay=0.9):
     """Train the gas's MLP on device samples (float64 tensors); returns the per-epoch loss history."""
     import torch
