@@ -82,6 +82,26 @@ typedef struct {
   const int32_t* face_bc;    /* host [K][4] or NULL: DG_BC_* code of each face that */
                              /* has no partner, 0 on paired faces (face f has the   */
                              /* vertex triple 012, 013, 123, 023 for f = 0..3)      */
+  /* Optional tables of the caller (Sec. 1 Fig. 1 and Sec. 4.1.2: element-local arrays plus
+   * connectivity data).  NULL: the library builds the table, as described at dg_mesh_upload.
+   * Every table given is checked on the host and copied; a malformed one is DG_ERR_INVALID_ARG. */
+  const int32_t* EToV;       /* host [K][4]: global vertex numbers (periodic images     */
+                             /* share a number); checked against the face pairing:     */
+                             /* paired faces have the same three vertex numbers         */
+  const int32_t* EToE;       /* host [K][4] with EToF: the element and face (0..3)       */
+  const int32_t* EToF;       /* paired with each face, -1 in EToE for a face without a  */
+                             /* partner (which needs a face_bc code); must be symmetric */
+  const int32_t* vmapP;      /* host [K][4 Nfp]: flat node index k2 Np + n2 of the      */
+                             /* partner of each face node, -code at boundary faces;     */
+                             /* checked for range, symmetry and coincident positions    */
+                             /* (modulo the period), and against EToE / EToF if given   */
+  const double* Dr;          /* host [Np][Np] row-major, with Ds, Dt, LIFT and Fmask:    */
+  const double* Ds;          /* all five or none; D must annihilate constants and the   */
+  const double* Dt;          /* Fmask nodes must lie on their faces of the reference    */
+  const double* LIFT;        /* tetrahedron (ref_nodes); LIFT [Np][4 Nfp]                */
+  const int32_t* Fmask;      /* [4][Nfp]                                                  */
+  const double* geo;         /* host [K][DG_GEO_STRIDE]: geometric factors (finite,       */
+                             /* J > 0, unit normals, Fscale > 0)                          */
 } dg_mesh_desc;
 
 /* Boundary conditions of faces without a partner (Sec. 5.3-5.4 run wall-bounded and inflow /
@@ -109,11 +129,15 @@ typedef struct {
  * rejected by the compute calls.  Lets the host logic be checked without a GPU. */
 #define DG_MESH_HOST_ONLY 1
 
-/* Builds the reference operators (Dr, Ds, Dt, LIFT = M^-1 E, Fmask) from the
- * reference nodes, the affine geometric factors (inverse Jacobian, unit outward
- * normals, Fscale = face area / (2 J)) and the face connectivity (faces paired
- * by centroid modulo the period, face nodes by coordinates under the face
- * pair's periodic shift), then copies them to the current device together with
+/* Uploads the mesh: the element-local arrays and connectivity data of the paper's problem
+ * statement (Sec. 1 Fig. 1; Sec. 4.1.2 / Sec. 4.3 connectivity and indirect gather).  Tables the
+ * caller does not give are built: the reference operators (Dr, Ds, Dt, LIFT = M^-1 E, Fmask) from
+ * the reference nodes, the affine geometric factors (inverse Jacobian, unit outward normals,
+ * Fscale = face area / (2 J)) from the vertices, and vmapP from the caller's EToE / EToF (face
+ * nodes matched by coordinates under each pair's periodic shift) or, without them, with the faces
+ * paired by centroid modulo the period.  The quadrature weights, the modal matrix of the shock
+ * sensor and the tensor-core operator tables always come from the reference nodes and the
+ * (given or built) operators.  Then copies them to the current device together with
  * per-node scratch: the viscous flux (9 doubles per node), the FP64 form's primitives
  * (1/rho, p, c: 3 doubles per node) and the partials of the global reductions.  Sec. 1
  * Fig. 1 (element-local arrays), Sec. 4.1.2 / Sec. 4.3 (connectivity, indirect gather).
@@ -213,6 +237,10 @@ int dg_mesh_operators(dg_mesh mesh, double* Dr_host, double* Ds_host, double* Dt
 #define DG_GEO_STRIDE 26 /* rx ry rz sx sy sz tx ty tz | (nx ny nz Fscale) x 4 faces | J */
 int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP_host, double* geo_host);
 
+/* Copies the face pairing EToE, EToF [K][4] (element and face of each face's partner, -1 in both
+ * for a face without one) to host buffers (either may be NULL). */
+int dg_mesh_face_pairs(dg_mesh mesh, int32_t* EToE_host, int32_t* EToF_host);
+
 /* Reads (and with reset != 0 clears) the device status word of the mesh, after
  * synchronising the device.  *bits receives DG_STATUS_* bits. */
 int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset);
@@ -290,7 +318,12 @@ typedef struct {
   int32_t viscous_given;  /* FP64 Navier-Stokes: != 0 uses the viscous flux already   */
                           /* in the mesh's buffer (dg_viscous_flux, then a halo       */
                           /* exchange) instead of computing it                        */
-  int32_t reserved[7];
+  int32_t wait_polls;     /* tensor-core kernels (mixed form, MLP guess): polls of    */
+                          /* each bounded wait for an MMA completion; 0 = the default  */
+                          /* bound.  A test aid: a small value makes the waits run    */
+                          /* out, which the kernels report as DG_STATUS_TIMEOUT (the  */
+                          /* output is then incomplete) and return without hanging    */
+  int32_t reserved[6];
 } dg_opts;                /* NULL = defaults: DG_PREC_FP64, DG_TSEED_INPUT          */
 
 /* ---- the hot path ------------------------------------------------------------ */

@@ -49,7 +49,10 @@ c_int32, c_int64, c_uint32, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64,
 
 class dg_mesh_desc(ctypes.Structure):
     _fields_ = [("K", c_int32), ("N", c_int32), ("ref_nodes", c_void_p), ("vertices", c_void_p),
-                ("period", c_double * 3), ("flags", c_int32), ("face_bc", c_void_p)]
+                ("period", c_double * 3), ("flags", c_int32), ("face_bc", c_void_p),
+                ("EToV", c_void_p), ("EToE", c_void_p), ("EToF", c_void_p), ("vmapP", c_void_p),
+                ("Dr", c_void_p), ("Ds", c_void_p), ("Dt", c_void_p), ("LIFT", c_void_p), ("Fmask", c_void_p),
+                ("geo", c_void_p)]
 
 
 class dg_av_params(ctypes.Structure):
@@ -82,7 +85,7 @@ class dg_batch_case(ctypes.Structure):
 
 class dg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("viscous_given", c_int32),
-                ("reserved", c_int32 * 7)]
+                ("wait_polls", c_int32), ("reserved", c_int32 * 6)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/dg.h
@@ -98,6 +101,7 @@ SIGNATURES = {
                                ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "dg_mesh_operators": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mesh_connectivity": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_face_pairs": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "dg_mesh_set_inflow": (c_int32, [c_void_p, c_void_p, c_int32]),
     "dg_mesh_set_av": (c_int32, [c_void_p, c_void_p]),
     "dg_gather_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,

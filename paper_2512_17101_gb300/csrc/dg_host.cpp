@@ -69,6 +69,7 @@ int check_opts(const dg_opts* o) {
   if (o->t_seed != DG_TSEED_INPUT && o->t_seed != DG_TSEED_CONST && o->t_seed != DG_TSEED_MLP)
     return fail(DG_ERR_INVALID_ARG, "unknown temperature seed mode");
   if (o->t_seed == DG_TSEED_CONST && !(o->t_const > 0)) return fail(DG_ERR_INVALID_ARG, "t_const must be > 0");
+  if (o->wait_polls < 0) return fail(DG_ERR_INVALID_ARG, "wait_polls must be >= 0");
   return DG_OK;
 }
 
@@ -173,7 +174,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       const dg::MixturePrims mp = dg::mixture_prims_out(m);
       e = timed(mesh, DG_KERNEL_TEMPERATURE, s, [&] {
         if (mode == DG_TSEED_MLP)
-          return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s, mp);
+          return dg::launch_temperature_mlp(gas, (int64_t)m.K * m.Np, q, T_io, nullptr, 0, s, mp, opts->wait_polls);
         return dg::launch_temperature(g, (int64_t)m.K * m.Np, q, T_io, nullptr, mode, opts->t_const, gas->status, s,
                                       mp);
       });
@@ -182,11 +183,13 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_mixed(m, g, q, s); });
       if (e != cudaSuccess) return cuda_fail(e, "mixed primitives kernel");
       if (g.mu > 0) {
-        e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_tc(m, g, q, s); });
+        e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_tc(m, g, q, s, opts->wait_polls); });
         if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
       }
     }
-    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_tc(m, g, q, out, k, rk, a, b, dt, s); });
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] {
+      return dg::launch_rhs_tc(m, g, q, out, k, rk, a, b, dt, s, opts->wait_polls);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "mixed right-hand-side kernel");
     return DG_OK;
   }
@@ -267,13 +270,59 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   for (int x = 0; x < 3; ++x)
     if (!(desc->period[x] >= 0) || !std::isfinite(desc->period[x]))
       return fail(DG_ERR_INVALID_ARG, "period must be finite and >= 0");
+  const int n_ops = !!desc->Dr + !!desc->Ds + !!desc->Dt + !!desc->LIFT + !!desc->Fmask;
+  if (n_ops != 0 && n_ops != 5) return fail(DG_ERR_INVALID_ARG, "give all of Dr, Ds, Dt, LIFT and Fmask, or none");
+  if (!desc->EToE != !desc->EToF) return fail(DG_ERR_INVALID_ARG, "give EToE and EToF together");
   dg_mesh m = new (std::nothrow) dg_mesh_s();
   if (!m) return fail(DG_ERR_OOM, "host allocation failed");
   std::string err;
-  if (!dg::build_ref_ops(desc->N, desc->ref_nodes, m->ops, err) ||
-      !dg::build_geometry(desc->K, desc->vertices, m->geo, err) ||
-      !dg::build_connectivity(desc->K, desc->vertices, desc->period, m->ops, desc->ref_nodes, desc->face_bc,
-                              m->vmapP, err)) {
+  const int K = desc->K;
+  bool ok = dg::build_ref_ops(desc->N, desc->ref_nodes, m->ops, err);
+  if (ok && n_ops == 5) {  // the caller's operators replace the built ones
+    const int Np = m->ops.Np, Nfp = m->ops.Nfp;
+    ok = dg::check_ref_ops(desc->N, desc->ref_nodes, desc->Dr, desc->Ds, desc->Dt, desc->LIFT, desc->Fmask, err);
+    if (ok) {
+      m->ops.Dr.assign(desc->Dr, desc->Dr + Np * Np);
+      m->ops.Ds.assign(desc->Ds, desc->Ds + Np * Np);
+      m->ops.Dt.assign(desc->Dt, desc->Dt + Np * Np);
+      m->ops.LIFT.assign(desc->LIFT, desc->LIFT + (size_t)Np * 4 * Nfp);
+      m->ops.Fmask.assign(desc->Fmask, desc->Fmask + 4 * Nfp);
+    }
+  }
+  if (ok) {
+    if (desc->geo) {
+      ok = dg::check_geometry(K, desc->geo, err);
+      if (ok) m->geo.assign(desc->geo, desc->geo + (size_t)K * DG_GEO_STRIDE);
+    } else {
+      ok = dg::build_geometry(K, desc->vertices, m->geo, err);
+    }
+  }
+  if (ok) {
+    if (desc->vmapP) {
+      ok = dg::check_connectivity(K, desc->vertices, desc->period, m->ops, desc->ref_nodes, desc->face_bc,
+                                  desc->vmapP, m->partner, err);
+      if (ok) m->vmapP.assign(desc->vmapP, desc->vmapP + (size_t)K * 4 * m->ops.Nfp);
+    } else if (desc->EToE) {
+      ok = dg::build_connectivity_from_faces(K, desc->vertices, desc->period, m->ops, desc->ref_nodes, desc->face_bc,
+                                             desc->EToE, desc->EToF, m->vmapP, err, m->partner);
+    } else {
+      ok = dg::build_connectivity(K, desc->vertices, desc->period, m->ops, desc->ref_nodes, desc->face_bc,
+                                  m->vmapP, err, &m->partner);
+    }
+  }
+  if (ok && desc->EToE && desc->vmapP) {  // both given: they must describe the same pairing
+    for (int kf = 0; kf < 4 * K && ok; ++kf) {
+      const int pf = m->partner[kf];
+      const int e2 = pf < 0 ? -1 : pf / 4, f2 = pf < 0 ? -1 : pf % 4;
+      if (desc->EToE[kf] != e2 || (e2 >= 0 && desc->EToF[kf] != f2)) {
+        err = "EToE / EToF disagree with vmapP at face " + std::to_string(kf % 4) + " of element " +
+              std::to_string(kf / 4);
+        ok = false;
+      }
+    }
+  }
+  if (ok && desc->EToV) ok = dg::check_vertex_numbers(K, desc->EToV, m->partner, err);
+  if (!ok) {
     delete m;
     return fail(DG_ERR_INVALID_ARG, err);
   }
@@ -443,6 +492,16 @@ int dg_mesh_connectivity(dg_mesh mesh, int32_t* vmapP, double* geo) {
   return DG_OK;
 }
 
+int dg_mesh_face_pairs(dg_mesh mesh, int32_t* EToE, int32_t* EToF) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  for (size_t kf = 0; kf < mesh->partner.size(); ++kf) {
+    const int pf = mesh->partner[kf];
+    if (EToE) EToE[kf] = pf < 0 ? -1 : pf / 4;
+    if (EToF) EToF[kf] = pf < 0 ? -1 : pf % 4;
+  }
+  return DG_OK;
+}
+
 int dg_mesh_status(dg_mesh mesh, uint32_t* bits, int reset) {
   if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
   if (!mesh->d.status) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
@@ -482,6 +541,11 @@ int dg_gas_create(const dg_gas_desc* desc, dg_gas* out) {
       const double* a = p.a[k];
       const double fc[6] = {a[5], a[0] - 1.0, a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0};
       for (int j = 0; j < 6; ++j) p.fc[k][j] = p.Rk[k] * fc[j];
+      for (int j = 0; j < 7; ++j) {
+        const double x = j < 6 ? p.fc[k][j] : p.Rk[k];
+        const float hi = (float)x;
+        p.fc2[k][j] = make_float2(hi, (float)(x - (double)hi));
+      }
     }
     p.newton_tol = desc->newton_tol;
     p.newton_max_it = desc->newton_max_it;
@@ -540,7 +604,8 @@ int dg_temperature(dg_gas gas, int64_t n, const double* q, double* T_io, int32_t
   const double tc = opts ? opts->t_const : 0.0;
   if (mode == DG_TSEED_MLP && !gas->has_mlp) return fail(DG_ERR_INVALID_ARG, "DG_TSEED_MLP needs a trained MLP");
   cudaError_t e = mode == DG_TSEED_MLP
-                      ? dg::launch_temperature_mlp(gas, n, q, T_io, iters, 0, (cudaStream_t)stream)
+                      ? dg::launch_temperature_mlp(gas, n, q, T_io, iters, 0, (cudaStream_t)stream,
+                                                   dg::MixturePrims(), opts ? opts->wait_polls : 0)
                       : dg::launch_temperature(gas->p, n, q, T_io, iters, mode, tc, gas->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "temperature kernel");
   return DG_OK;

@@ -36,9 +36,29 @@ bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::s
 // Periodic face-node connectivity vmapP[K][4 Nfp] (mesh.cpp).
 // face_bc [K][4] (may be null): DG_BC_* code of the faces without a partner; their face nodes
 // get vmapP = -code.
+// partner_out (optional) receives the face pairing [4K]: 4 k2 + f2, -1 at boundary faces.
 bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
                         const double* ref_nodes, const int32_t* face_bc, std::vector<int32_t>& vmapP,
-                        std::string& err);
+                        std::string& err, std::vector<int>* partner_out = nullptr);
+
+// The same from a face pairing given by the caller (EToE / EToF [K][4], -1 for a face without a
+// partner; the pairing must be symmetric).
+bool build_connectivity_from_faces(int K, const double* verts, const double period[3], const RefOps& ops,
+                                   const double* ref_nodes, const int32_t* face_bc, const int32_t* EToE,
+                                   const int32_t* EToF, std::vector<int32_t>& vmapP, std::string& err,
+                                   std::vector<int>& partner);
+// Checks of caller-supplied tables (mesh.cpp): a vmapP (range, one partner face per face, coincident
+// partner nodes modulo the period, symmetry, boundary codes as in face_bc; partner [4K] receives the
+// face pairing), global vertex numbers against the pairing, reference operators (finite, D
+// annihilates constants, Fmask nodes on their faces), geometric factors (finite, J > 0, unit
+// normals, Fscale > 0).
+bool check_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
+                        const double* ref_nodes, const int32_t* face_bc, const int32_t* vmapP,
+                        std::vector<int>& partner, std::string& err);
+bool check_vertex_numbers(int K, const int32_t* EToV, const std::vector<int>& partner, std::string& err);
+bool check_ref_ops(int N, const double* ref_nodes, const double* Dr, const double* Ds, const double* Dt,
+                   const double* LIFT, const int32_t* Fmask, std::string& err);
+bool check_geometry(int K, const double* geo, std::string& err);
 
 // ---- device-side parameter blocks -------------------------------------------
 struct GasParams {  // passed to kernels by value
@@ -50,6 +70,10 @@ struct GasParams {  // passed to kernels by value
   // NASA-7: species k's share of the internal-energy quintic per unit mass fraction,
   // e_k(T) = sum_j fc[k][j] T^j = R_k (a6 + (a1 - 1) T + a2/2 T^2 + a3/3 T^3 + a4/4 T^4 + a5/5 T^5)
   double fc[DG_MAX_SPECIES][6];
+  // the same coefficients and R_k as float pairs (hi = the value rounded to FP32, lo = the rest
+  // rounded to FP32), for the mixed-precision form's fold on the FP32 pipe: [k][0..5] = fc[k][j],
+  // [k][6] = R_k
+  float2 fc2[DG_MAX_SPECIES][7];
   double newton_tol;
   int newton_max_it;
   double Sc;        // NASA-7 with viscosity: Schmidt number, rho D = mu / Sc
@@ -130,9 +154,12 @@ cudaError_t launch_rhs_av(const MeshDev& m, const GasParams& g, const double* q,
 void free_mixed_ops(MeshDev& m);
 cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops);
+// wait_polls: polls per bounded mbarrier wait (0 = the default bound; a small value is a test aid
+// that makes the waits run out).
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
-                          double a, double b, double dt, cudaStream_t s);
-cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+                          double a, double b, double dt, cudaStream_t s, int wait_polls = 0);
+cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s,
+                              int wait_polls = 0);
 // BR1 pass 1: viscous flux of a perfect gas into m.scratch.
 cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Per-node (1/rho, p, c) of a perfect-gas state into m.prim (k_ns.cu); the FP64 viscous and
@@ -147,6 +174,7 @@ constexpr size_t kDiagPartialBytes = sizeof(double) * kDiagBlocks * kDiagMaxV;
 // {rho Y_1..4}, {rho Y_5..8}; rho <= 0 or p <= 0 sets DG_STATUS_NONPHYSICAL in *status.
 struct MixturePrims {
   float4* rec = nullptr;      // mixed form: the node records
+  float4* lo = nullptr;       // mixed form: [n] low halves of momentum and energy
   double* prim = nullptr;     // FP64 form: [3][n] 1/rho, p, c at the converged temperature
   unsigned* status = nullptr;
 };
@@ -186,6 +214,7 @@ struct dg_mesh_s {
   dg::RefOps ops;
   std::vector<int32_t> vmapP;
   std::vector<double> geo;
+  std::vector<int> partner;  // [4 K]: 4 k2 + f2 of each face's partner, -1 at boundary faces
   int device = 0;
 };
 

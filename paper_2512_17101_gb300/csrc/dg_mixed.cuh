@@ -78,8 +78,9 @@ struct MixedCase {
   float4* fv4;
   float* fvz;
   float2* temp;
-  // mixture: node records (see mixture_records)
+  // mixture: node records and the low halves of momentum and energy (see mixture_records)
   float4* mrec;
+  float4* mlo;
   const float* geo;
   const int32_t* vmapP;
   int K;
@@ -90,6 +91,7 @@ struct MixedCase {
   // DG_BC_INFLOW state as a node record and a temperature pair (perfect gas)
   float4 in_node[2];
   float2 in_temp;
+  int wait_polls;  // polls per bounded mbarrier wait of the tensor-core kernels; 0 = the default
 };
 
 // Exterior record of a boundary face node (code = -vmapP; r0, r1 hold the node's own record on
@@ -141,9 +143,17 @@ __device__ __forceinline__ void ghost_viscous(int code, const float n[3], float 
 // by the temperature Newton kernels at the converged temperature (dg_newton.cuh):
 //   [KNp][4] float4: {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, c},
 //                    {rho Y_1 .. rho Y_4}, {rho Y_5 .. rho Y_8}   (absent species 0)
+// and, in the remaining 16 bytes, the low halves of the float pairs of momentum and energy:
+//   [KNp] float4: {(rho u)_lo, (rho v)_lo, (rho w)_lo, (rho E)_lo}
+// read only where a difference would cancel: the Lax-Friedrichs jumps q- - q+, multiplied by the
+// wave speed (a sound speed of ~1e3 m/s against velocities of ~10 m/s here), whose FP32 rounding
+// would otherwise dominate the momentum error.
 constexpr int MIX_V = 5 + DG_MAX_SPECIES;
 static_assert(MIX_V <= 13, "the mixture record holds up to 8 species");
 __host__ __device__ inline float4* mixture_records(double* base) { return reinterpret_cast<float4*>(base); }
+__host__ __device__ inline float4* mixture_lo(double* base, size_t KNp) {
+  return reinterpret_cast<float4*>(base) + 4 * KNp;
+}
 
 // ---- pass 0: per node, FP64 pressure (and temperature) and the node record, so that the later
 // kernels read traces without recomputing or converting them.
@@ -270,10 +280,12 @@ __device__ __forceinline__ void node_flux_mix(const float q[V], int nvar, float 
 }
 
 // Mixture surface term of one face node before Fscale: local Lax-Friedrichs with the sound
-// speeds of both traces (from the primitives pass).
+// speeds of both traces (from the temperature solve).  dlo: the differences of the low halves of
+// momentum and energy, added to the jumps q- - q+ of the dissipation term.
 template <int V>
 __device__ __forceinline__ void face_term_mix(const float qm[V], const float qp[V], int nvar, float pm, float pp,
-                                              float dpn, float cm, float cp, const float n[3], float g[V]) {
+                                              float dpn, float cm, float cp, const float n[3], const float dlo[4],
+                                              float g[V]) {
   const float irm = 1.0f / qm[0], irp = 1.0f / qp[0];
   const float unm = (qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2]) * irm;
   const float unp = (qp[1] * n[0] + qp[2] * n[1] + qp[3] * n[2]) * irp;
@@ -281,6 +293,8 @@ __device__ __forceinline__ void face_term_mix(const float qm[V], const float qp[
   float dq[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) dq[v] = qm[v] - qp[v];
+#pragma unroll
+  for (int v = 1; v < 5; ++v) dq[v] += dlo[v - 1];
   float dF[V];
   dF[0] = dq[1] * n[0] + dq[2] * n[1] + dq[3] * n[2];
 #pragma unroll

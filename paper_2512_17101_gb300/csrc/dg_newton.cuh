@@ -58,6 +58,48 @@ __device__ __forceinline__ void fold(const GasParams& g, const double* rhoY, dou
   }
 }
 
+// Float-pair arithmetic on the FP32 pipe (a value is hi + lo, about 48 significant bits): the
+// error-free sum of two floats (Knuth's TwoSum) and the product-accumulate acc += x y, whose
+// partial products are formed exactly with FMA and then renormalised (Dekker / Knuth).  The
+// _rn intrinsics keep the compiler from contracting a product into a later sum, which would break
+// the error-free transformations.
+struct FP2 {
+  float hi, lo;
+};
+__device__ __forceinline__ FP2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return FP2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ void fp2_fma(FP2& acc, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));  // the product's rounding + cross terms
+  const FP2 s = two_sum(acc.hi, p);
+  const float lo = __fadd_rn(s.lo, __fadd_rn(e, acc.lo));
+  const float hi = __fadd_rn(s.hi, lo);  // renormalise (|s.hi| >= |lo|)
+  acc = FP2{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+
+// The fold of the mixed-precision form: the same sums as fold() in float-pair arithmetic on the
+// FP32 pipe (the FP64 pipe, 1/64 of the FP32 rate here, then only adds the two halves), from the
+// partial densities split into float pairs.  The coefficients carry ~48 bits (relative error a few
+// 1e-15 of the summed magnitudes), which moves the converged temperature by ~1e-11 K, well below
+// the Newton tolerance; the Newton iteration itself stays FP64.
+__device__ __forceinline__ void fold_fp2(const GasParams& g, const double* rhoY, double C[6], double& rhoR) {
+  FP2 a[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) a[j] = FP2{0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < DG_MAX_SPECIES; ++k) {
+    if (k >= g.ns) break;
+    const float2 r = cvt::split(rhoY[k]);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) fp2_fma(a[j], r, g.fc2[k][j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) C[j] = cvt::widen(a[j].hi) + cvt::widen(a[j].lo);
+  rhoR = cvt::widen(a[6].hi) + cvt::widen(a[6].lo);
+}
+
 // rho cv(T) = d(rho e)/dT.
 __device__ __forceinline__ double heat_capacity(const double C[6], double t) {
   return fma(t, fma(t, fma(t, fma(t, 5.0 * C[5], 4.0 * C[4]), 3.0 * C[3]), 2.0 * C[2]), C[1]);
@@ -150,8 +192,14 @@ __device__ __forceinline__ void store_prims(const MixturePrims& mp, const GasPar
   const float2 p2 = cvt::split(p);
   if (!(rho2.x > 0.0f) || !(p2.x > 0.0f)) atomicOr(mp.status, DG_STATUS_NONPHYSICAL);
   v[0] = rho2.x;
-  for (int j = 1; j < 4; ++j) v[j] = cvt::narrow(q[j * n + node]);
-  v[4] = cvt::narrow(q[4 * n + node]);
+  float lo[4];
+#pragma unroll
+  for (int j = 1; j < 5; ++j) {
+    const float2 s = cvt::split(q[j * n + node]);
+    v[j] = s.x;
+    lo[j - 1] = s.y;
+  }
+  mp.lo[node] = make_float4(lo[0], lo[1], lo[2], lo[3]);
   v[5] = p2.x;
   v[6] = p2.y;
   const double c2 = p * ir * fma(rhoR, rcp64(rhocv), 1.0);
@@ -177,6 +225,7 @@ __device__ __forceinline__ void store_prims64(const MixturePrims& mp, int64_t n,
 
 // Loads node i of q [5 + ns][n]: rho, its reciprocal, rho e = rho E - |rho u|^2 / (2 rho) and the
 // fold of the partial densities.
+template <bool FP2FOLD = false>
 __device__ __forceinline__ void load_node(const GasParams& g, const double* __restrict__ q, int64_t n, int64_t i,
                                           double& rho, double& ir, double& rho_e, double C[6], double& rhoR,
                                           double* rhoY) {
@@ -186,7 +235,10 @@ __device__ __forceinline__ void load_node(const GasParams& g, const double* __re
   rho_e = fma(-0.5 * ir, fma(mx, mx, fma(my, my, mz * mz)), q[4 * n + i]);
 #pragma unroll
   for (int k = 0; k < DG_MAX_SPECIES; ++k) rhoY[k] = k < g.ns ? q[(5 + k) * n + i] : 0.0;
-  fold(g, rhoY, C, rhoR);
+  if (FP2FOLD)
+    fold_fp2(g, rhoY, C, rhoR);
+  else
+    fold(g, rhoY, C, rhoR);
 }
 
 }  // namespace newton

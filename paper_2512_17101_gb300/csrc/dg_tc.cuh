@@ -170,8 +170,9 @@ __device__ __forceinline__ void block_setup(const Smem<C_>& S, const uint4* __re
 template <class C_>
 __device__ __forceinline__ void block_teardown(const Smem<C_>& S, uint32_t phase) {
   // after an abort the MMA group whose wait timed out (parity phase ^ 1) may still be in
-  // flight: give it one more bounded wait before the accumulator is released
-  if (*S.abort && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), phase ^ 1u);
+  // flight: give it one more wait, with the full bound, before the accumulator is released.
+  // The decision is a block-wide OR: a thread whose last wait ran out has set the flag itself.
+  if (__syncthreads_or(*S.abort) && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), phase ^ 1u);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -204,17 +205,20 @@ __device__ __forceinline__ void issue_chunk(const Smem<C_>& S, int c) {
 // After a chunk's operand is in the slot: make it visible to the tensor core, issue its MMAs
 // and wait for them (the slot is rewritten next).  Returns false once any wait has timed out
 // (uniform across the block).
+// The stop decision is a block-wide OR of the flag as each thread sees it on arrival: a thread whose
+// wait ran out wrote the flag before arriving, so every thread gets the same answer even when
+// another thread reads the flag before that write.  `polls` bounds each wait (0: the default).
 template <class C_>
-__device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& phase, unsigned* status) {
+__device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& phase, unsigned* status,
+                                          int polls = 0) {
   fence_async_smem();
   tc_fence_before();
-  __syncthreads();
-  if (*S.abort) return false;
+  if (__syncthreads_or(*S.abort)) return false;
   if (threadIdx.x == 0) {
     tc_fence_after();
     issue_chunk<C_>(S, c);
   }
-  if (!mbar_wait(smem_u32(S.bar), phase)) {
+  if (!mbar_wait(smem_u32(S.bar), phase, polls > 0 ? polls : kWaitPolls)) {
     *S.abort = 1;
     atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
   }
@@ -309,7 +313,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
                     fmaf(gx, F[s][0][v], fmaf(gy, F[s][1][v], gz * F[s][2][v])));
       }
     }
-    if (!run_chunk<C_>(S, ra, phase, status)) return false;
+    if (!run_chunk<C_>(S, ra, phase, status, c.wait_polls)) return false;
   }
 
   // surface chunks: face nodes [sc KS, sc KS + KS) of every element
@@ -331,7 +335,9 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         const float4 am = c.mrec[4 * own + 1], ap = c.mrec[4 * P + 1];  // {rho E, p_hi, p_lo, c}
         load_mix_record(c.mrec + 4 * own, qm);
         load_mix_record(c.mrec + 4 * P, qp);
-        mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, g);
+        const float4 lm = c.mlo[own], lp = c.mlo[P];
+        const float dlo[4] = {lm.x - lp.x, lm.y - lp.y, lm.z - lp.z, lm.w - lp.w};
+        mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, dlo, g);
       } else {
         const float4 m0r = c.node[2 * own], m1r = c.node[2 * own + 1];
         float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];
@@ -353,7 +359,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       for (int v = 0; v < V; ++v)
         put3_umma(S.A, C_::A_TERM, umma_off(e * V + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
     }
-    if (!run_chunk<C_>(S, 3 + sc, phase, status)) return false;
+    if (!run_chunk<C_>(S, 3 + sc, phase, status, c.wait_polls)) return false;
   }
 
   // accumulator -> shared memory (warps 0..3 own TMEM lanes 0..127), then the node-parallel update
@@ -550,7 +556,7 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, i, C_::A_LBO, C_::A_SBO), w_n[s][f]);
     }
   }
-  if (!run_chunk<C_>(S, 0, phase, status)) return false;
+  if (!run_chunk<C_>(S, 0, phase, status, c.wait_polls)) return false;
 
   // surface chunks: jumps w+ - w- at face nodes [sc KS, sc KS + KS)
 #pragma unroll 1
@@ -578,7 +584,7 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       for (int f = 0; f < 5; ++f)
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, mm - m0, C_::A_LBO, C_::A_SBO), jv[f]);
     }
-    if (!run_chunk<C_>(S, 1 + sc, phase, status)) return false;
+    if (!run_chunk<C_>(S, 1 + sc, phase, status, c.wait_polls)) return false;
   }
 
   // reference derivatives -> gradients, one reference direction at a time through shared memory

@@ -56,9 +56,23 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 constexpr int kWaitPolls = 1 << 22;
 
 // Bounded wait for the phase with the given parity to complete; false when `polls` polls did not
-// see it.
+// see it.  The default bound polls with mbarrier.try_wait (which may suspend the thread for a short
+// system-dependent time per poll); any other bound is a test aid and polls with the non-blocking
+// mbarrier.test_wait, so that a bound of a few polls runs out before an MMA group can complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int polls = kWaitPolls) {
-  for (int it = 0; it < polls; ++it) {
+  if (polls != kWaitPolls) {
+    for (int it = 0; it < polls; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred q;\n mbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
+      if (done) return true;
+    }
+    return false;
+  }
+  for (int it = 0; it < kWaitPolls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"

@@ -21,6 +21,7 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
   c.k = k;
   if (g.model == DG_GAS_NASA7) {
     c.mrec = mixk::mixture_records(m.scratch);
+    c.mlo = mixk::mixture_lo(m.scratch, (size_t)m.K * m.Np);
   } else {
     const mixk::NodeTables t = mixk::node_tables(m.scratch, (size_t)m.K * m.Np);
     c.node = t.node;
@@ -62,6 +63,7 @@ cudaError_t launch_prims_mixed(const MeshDev& m, const GasParams& g, const doubl
 MixturePrims mixture_prims_out(const MeshDev& m) {
   MixturePrims mp;
   mp.rec = mixk::mixture_records(m.scratch);
+  mp.lo = mixk::mixture_lo(m.scratch, (size_t)m.K * m.Np);
   mp.status = m.status;
   return mp;
 }

@@ -9,8 +9,8 @@
 //     cores: a block takes 128 nodes as the M = 128 rows of two tcgen05 MMAs (features
 //     x W1^T, then tanh(.) x W2^T, accumulators in tensor memory), the activations
 //     through the hardware tanh on FP16 pairs; the guess seeds the FP64 Newton solve
-//     of the same nodes (dg_newton.cuh), which stays the arbiter and the fallback, to
-//     the same |dT| < tol.
+//     of the same nodes in the same kernel (dg_newton.cuh), which stays the arbiter and
+//     the fallback, to the same |dT| < tol.
 //
 // Flat parameter layout (float): W1 [64][8] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64] | b3.
 #include <cuda_fp16.h>
@@ -210,33 +210,44 @@ struct MlpDev {
   dg_mlp_norm nrm;
 };
 
+// The activations' operands and the Newton state are live at different times of a tile (the MMAs
+// have completed before the Newton rounds begin, and the rounds' results are read before the next
+// tile's features are written), so they share storage: 31 KB per block, seven blocks per SM.
 struct __align__(128) MlpSmem {
   unsigned char B1[W1_IMG];
   unsigned char B2[W2_IMG];
-  unsigned char A1[kMlpRows / 8 * A1_SBO];
-  unsigned char A2[kMlpRows / 8 * A2_SBO];
+  union {
+    struct {
+      unsigned char A1[kMlpRows / 8 * A1_SBO];
+      unsigned char A2[kMlpRows / 8 * A2_SBO];
+    } op;
+    newton::Rounds<kMlpRows> R;
+  } u;
   float b1[NH], b2[NH], w3[NH];
-  newton::Rounds<kMlpRows> R;
   uint64_t bar;
   uint32_t tmem;
-  int abort;
 };
-static_assert(sizeof(MlpSmem) <= 48 * 1024, "static shared memory");
+static_assert(sizeof(MlpSmem) <= 32 * 1024, "seven blocks per SM");
+constexpr int kMlpBlocksPerSm = 7;
 
-// 128 nodes per tile, one per thread (thread i = MMA row i = TMEM lane i): features, the two MMAs,
-// the guess, then (unless guess_only) the block's Newton rounds from it.
-__global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasParams g, const int64_t n,
-                                                                   const double* __restrict__ q,
-                                                                   double* __restrict__ T, int32_t* __restrict__ iters,
-                                                                   const MlpDev mlp, const int guess_only,
-                                                                   unsigned* __restrict__ status,
-                                                                   const MixturePrims mp, const int wait_polls) {
+// 128 nodes per tile, one per thread (thread i = MMA row i = TMEM lane i): the node's state and
+// species fold (FP2FOLD: the mixed form's float-pair fold), the features, the two MMAs, tanh on
+// FP16 pairs, W3 . h2 + b3, the clamped guess, then (unless guess_only) the block's Newton rounds
+// from the guesses and the node's outputs.  Fusing the inference with the solve reads the state
+// once, and while one block waits for its MMAs the other blocks on the SM keep the FP64 pipe
+// busy.  A wait that runs out of polls sets DG_STATUS_TIMEOUT; the block stops at its next issue
+// point (decided by a block-wide OR, so every thread stops at the same one), waits once more with
+// the full bound for the MMA group that thread 0 issued last, and frees its tensor memory; the
+// tiles not reached are not written.
+template <bool FP2FOLD>
+__global__ void __launch_bounds__(kMlpRows, kMlpBlocksPerSm) temperature_mlp_kernel(
+    const GasParams g, const int64_t n, const double* __restrict__ q, double* __restrict__ T,
+    int32_t* __restrict__ iters, const MlpDev mlp, const int guess_only, unsigned* __restrict__ status,
+    const MixturePrims mp, const int wait_polls) {
   __shared__ MlpSmem S;
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < W1_IMG / 16; i += kMlpRows) reinterpret_cast<uint4*>(S.B1)[i] = mlp.w1img[i];
   for (int i = tid; i < W2_IMG / 16; i += kMlpRows) reinterpret_cast<uint4*>(S.B2)[i] = mlp.w2img[i];
-  for (int i = tid; i < (int)sizeof(S.A1) / 16; i += kMlpRows)
-    reinterpret_cast<uint4*>(S.A1)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < NH; i += kMlpRows) {
     S.b1[i] = mlp.theta[P_B1 + i];
     S.b2[i] = mlp.theta[P_B2 + i];
@@ -244,10 +255,7 @@ __global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasPara
   }
   const float b3 = mlp.theta[P_B3];
   const float e_mean = (float)mlp.nrm.e_mean, inv_e_scale = (float)(1.0 / mlp.nrm.e_scale);
-  if (tid == 0) {
-    tc::mbar_init(tc::smem_u32(&S.bar), 1);
-    S.abort = 0;
-  }
+  if (tid == 0) tc::mbar_init(tc::smem_u32(&S.bar), 1);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&S.tmem), NH);
   tc::fence_async_smem();
   tc::tc_fence_before();
@@ -257,6 +265,18 @@ __global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasPara
   const uint32_t bar = tc::smem_u32(&S.bar);
   constexpr uint32_t IDESC = tc::idesc_f16(kMlpRows, NH);
   uint32_t phase = 0;
+  bool timed_out = false;  // this thread saw a wait run out
+  bool pending = false;    // thread 0: an issued MMA group it has not yet seen complete
+  auto wait = [&]() {
+    if (tc::mbar_wait(bar, phase, wait_polls)) {
+      if (tid == 0) pending = false;
+    } else if (!timed_out) {
+      timed_out = true;
+      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+    }
+    phase ^= 1u;
+    tc::tc_fence_after();
+  };
   const int64_t ntiles = (n + kMlpRows - 1) / kMlpRows;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t i = tile * kMlpRows + tid;
@@ -265,33 +285,31 @@ __global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasPara
     float feat[NI] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid) {
       double rhoY[DG_MAX_SPECIES];
-      newton::load_node(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
+      newton::load_node<FP2FOLD>(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
       feat[0] = (cvt::narrow(rho_e * ir) - e_mean) * inv_e_scale;
       const float irf = cvt::narrow(ir);
 #pragma unroll
       for (int k = 0; k < NI - 1; ++k) feat[1 + k] = k < g.ns ? cvt::narrow(rhoY[k]) * irf : 0.0f;
     }
-    *reinterpret_cast<uint4*>(S.A1 + umma_off(tid, 0, A1_SBO)) =
+    __syncthreads();  // the previous tile's Newton state (same storage as the operands) has been read
+    unsigned char* A1 = S.u.op.A1;
+    *reinterpret_cast<uint4*>(A1 + umma_off(tid, 0, A1_SBO)) =
         make_uint4(pack_half2(feat[0], feat[1]), pack_half2(feat[2], feat[3]), pack_half2(feat[4], feat[5]),
                    pack_half2(feat[6], feat[7]));
+    *reinterpret_cast<uint4*>(A1 + umma_off(tid, 8, A1_SBO)) = make_uint4(0u, 0u, 0u, 0u);  // K padding
     // layer 1
     tc::fence_async_smem();
     tc::tc_fence_before();
-    __syncthreads();
-    if (S.abort) break;
+    if (__syncthreads_or(timed_out)) break;
     if (tid == 0) {
       tc::tc_fence_after();
-      tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(S.A1), LBO, A1_SBO), tc::umma_desc(tc::smem_u32(S.B1), LBO,
-                                                                                         A1_SBO),
-                   IDESC, 0u);
+      tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(A1), LBO, A1_SBO), tc::umma_desc(tc::smem_u32(S.B1), LBO,
+                                                                                      A1_SBO),
+                  IDESC, 0u);
       tc::mma_commit(bar);
+      pending = true;
     }
-    if (!tc::mbar_wait(bar, phase, wait_polls)) {
-      S.abort = 1;
-      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
-    }
-    phase ^= 1u;
-    tc::tc_fence_after();
+    wait();
     {
       float acc[32];
 #pragma unroll
@@ -303,29 +321,24 @@ __global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasPara
           w[j] = tanh_pair(acc[2 * j] + S.b1[32 * half + 2 * j], acc[2 * j + 1] + S.b1[32 * half + 2 * j + 1]);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          *reinterpret_cast<uint4*>(S.A2 + umma_off(tid, 32 * half + 8 * c, A2_SBO)) =
+          *reinterpret_cast<uint4*>(S.u.op.A2 + umma_off(tid, 32 * half + 8 * c, A2_SBO)) =
               make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
       }
     }
     // layer 2
     tc::fence_async_smem();
     tc::tc_fence_before();
-    __syncthreads();
-    if (S.abort) break;
+    if (__syncthreads_or(timed_out)) break;
     if (tid == 0) {
       tc::tc_fence_after();
 #pragma unroll
       for (int ks = 0; ks < NH / 16; ++ks)
-        tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(S.A2) + ks * 2 * LBO, LBO, A2_SBO),
-                     tc::umma_desc(tc::smem_u32(S.B2) + ks * 2 * LBO, LBO, A2_SBO), IDESC, ks > 0 ? 1u : 0u);
+        tc::mma_f16(S.tmem, tc::umma_desc(tc::smem_u32(S.u.op.A2) + ks * 2 * LBO, LBO, A2_SBO),
+                    tc::umma_desc(tc::smem_u32(S.B2) + ks * 2 * LBO, LBO, A2_SBO), IDESC, ks > 0 ? 1u : 0u);
       tc::mma_commit(bar);
+      pending = true;
     }
-    if (!tc::mbar_wait(bar, phase, wait_polls)) {
-      S.abort = 1;
-      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
-    }
-    phase ^= 1u;
-    tc::tc_fence_after();
+    wait();
     float y = b3;
     {
       float acc[32];
@@ -347,21 +360,22 @@ __global__ void __launch_bounds__(kMlpRows) temperature_mlp_kernel(const GasPara
       if (valid) T[i] = t;
       continue;
     }
-    newton::stage(S.R, valid, C, rho_e, t);
-    if (newton::rounds(S.R, g.newton_max_it, g.newton_tol) && tid == 0) atomicOr(status, DG_STATUS_NO_CONVERGENCE);
+    newton::stage(S.u.R, valid, C, rho_e, t);
+    if (newton::rounds(S.u.R, g.newton_max_it, g.newton_tol) && tid == 0)
+      atomicOr(status, DG_STATUS_NO_CONVERGENCE);
     if (!valid) continue;
-    t = S.R.t[tid];
+    t = S.u.R.t[tid];
     T[i] = t;
-    if (iters) iters[i] = S.R.it[tid];
+    if (iters) iters[i] = S.u.R.it[tid];
     if (mp.rec || mp.prim) {
       const double rhocv = newton::heat_capacity(C, t);
       if (mp.rec) newton::store_prims(mp, g, q, n, i, rho, ir, rhoR, t, rhocv);
       if (mp.prim) newton::store_prims64(mp, n, i, rho, ir, rhoR, t, rhocv);
     }
   }
-  // after an abort the MMA whose wait timed out (parity phase ^ 1) may still be in flight: one more
-  // wait, with the full bound, before its accumulator is released
-  if (S.abort && tid == 0) tc::mbar_wait(bar, phase ^ 1u);
+  // an MMA group whose wait ran out for thread 0 (parity phase ^ 1: phase flipped after the wait)
+  // may still be in flight: one more wait, with the full bound, before the accumulator is released
+  if (tid == 0 && pending) tc::mbar_wait(bar, phase ^ 1u);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -393,12 +407,21 @@ cudaError_t launch_temperature_mlp(dg_gas gas, int64_t n, const double* q, doubl
                                    cudaStream_t s, const MixturePrims& mp, int wait_polls) {
   if (n <= 0) return cudaSuccess;
   MlpDev m{(const uint4*)gas->mlp_w1h, (const uint4*)gas->mlp_w2h, gas->mlp_theta, gas->mlp_norm};
-  static int per_sm = 0;
-  if (!per_sm) per_sm = std::max(1, resident_blocks((const void*)temperature_mlp_kernel, kMlpRows, 0, NH));
+  // the mixed-precision form (node records out) folds the species in float pairs
+  const bool fp2 = mp.rec != nullptr;
+  static int per_sm[2] = {0, 0};
+  if (!per_sm[fp2])
+    per_sm[fp2] = std::max(1, resident_blocks(fp2 ? (const void*)temperature_mlp_kernel<true>
+                                                  : (const void*)temperature_mlp_kernel<false>, kMlpRows, 0, NH));
   const int64_t tiles = (n + kMlpRows - 1) / kMlpRows;
-  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm * device_sms());
-  temperature_mlp_kernel<<<blocks, kMlpRows, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status, mp,
-                                                     wait_polls > 0 ? wait_polls : tc::kWaitPolls);
+  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm[fp2] * device_sms());
+  const int polls = wait_polls > 0 ? wait_polls : tc::kWaitPolls;
+  if (fp2)
+    temperature_mlp_kernel<true><<<blocks, kMlpRows, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status, mp,
+                                                             polls);
+  else
+    temperature_mlp_kernel<false><<<blocks, kMlpRows, 0, s>>>(gas->p, n, q, T, iters, m, guess_only, gas->status,
+                                                              mp, polls);
   return cudaGetLastError();
 }
 

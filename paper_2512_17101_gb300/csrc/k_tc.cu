@@ -119,8 +119,10 @@ cudaError_t launch_vis_t(const MeshDev& m, const mixk::MixedCase& c, cudaStream_
 
 }  // namespace
 
-cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s) {
-  const mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
+cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s,
+                              int wait_polls) {
+  mixk::MixedCase c = make_mixed_case(m, g, q, nullptr, nullptr, 0.0);
+  c.wait_polls = wait_polls;
   switch (m.N) {
     case 1: return launch_vis_t<1>(m, c, s);
     case 2: return launch_vis_t<2>(m, c, s);
@@ -141,8 +143,9 @@ cudaError_t build_tc_ops(MeshDev& m, const RefOps& ops) {
 }
 
 cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
-                          double a, double b, double dt, cudaStream_t s) {
-  const mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
+                          double a, double b, double dt, cudaStream_t s, int wait_polls) {
+  mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
+  c.wait_polls = wait_polls;
   if (g.model == DG_GAS_NASA7) return dispatch<kern::MIXTURE>(m, c, rk, a, b, s);
   if (g.mu > 0) return dispatch<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
   return dispatch<kern::EULER>(m, c, rk, a, b, s);

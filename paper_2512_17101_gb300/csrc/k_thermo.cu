@@ -20,6 +20,8 @@ namespace {
 
 constexpr int kNB = 128;  // nodes (threads) per block
 
+// FP2FOLD: the mixed-precision form's float-pair species fold (dg_newton.cuh).
+template <bool FP2FOLD>
 __global__ void __launch_bounds__(kNB) temperature_kernel(const GasParams g, const int64_t n,
                                                           const double* __restrict__ q, double* __restrict__ T,
                                                           int32_t* __restrict__ iters, const int mode,
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(kNB) temperature_kernel(const GasParams g, con
     double rho = 1.0, ir = 1.0, rho_e = 0.0, C[6] = {0, 0, 0, 0, 0, 0}, rhoR = 0.0, seed = 0.0;
     if (valid) {
       double rhoY[DG_MAX_SPECIES];
-      newton::load_node(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
+      newton::load_node<FP2FOLD>(g, q, n, i, rho, ir, rho_e, C, rhoR, rhoY);
       seed = mode == DG_TSEED_CONST ? t_const : T[i];
     }
     newton::stage(R, valid, C, rho_e, seed);
@@ -81,11 +83,18 @@ cudaError_t launch_temperature(const GasParams& g, int64_t n, const double* q, d
                                int seed_mode, double t_const, unsigned* status, cudaStream_t s,
                                const MixturePrims& mp) {
   if (n <= 0) return cudaSuccess;
-  static int per_sm = 0;
-  if (!per_sm) per_sm = std::max(1, resident_blocks((const void*)temperature_kernel, kNB, 0));
+  // the mixed-precision form (node records out) folds the species in float pairs
+  const bool fp2 = mp.rec != nullptr;
+  static int per_sm[2] = {0, 0};
+  if (!per_sm[fp2])
+    per_sm[fp2] = std::max(1, resident_blocks(fp2 ? (const void*)temperature_kernel<true>
+                                                  : (const void*)temperature_kernel<false>, kNB, 0));
   const int64_t tiles = (n + kNB - 1) / kNB;
-  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm * device_sms());
-  temperature_kernel<<<blocks, kNB, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
+  const int blocks = (int)std::min<int64_t>(tiles, (int64_t)per_sm[fp2] * device_sms());
+  if (fp2)
+    temperature_kernel<true><<<blocks, kNB, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
+  else
+    temperature_kernel<false><<<blocks, kNB, 0, s>>>(g, n, q, T, iters, seed_mode, t_const, status, mp);
   return cudaGetLastError();
 }
 

@@ -107,25 +107,44 @@ bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::s
   return true;
 }
 
-bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
-                        const double* ref_nodes, const int32_t* face_bc, std::vector<int32_t>& vmapP,
-                        std::string& err) {
-  const int Np = ops.Np, Nfp = ops.Nfp, NF = 4 * Nfp;
-  if ((int64_t)K * Np >= (int64_t)INT32_MAX) {
-    err = "K * Np exceeds the int32 node index range";
-    return false;
+namespace {
+
+// Physical coordinates of reference node n of element k (affine map of the vertices).
+inline void node_xyz(const double* verts, const double* ref_nodes, int k, int n, double* x) {
+  const double r = ref_nodes[3 * n], s = ref_nodes[3 * n + 1], t = ref_nodes[3 * n + 2];
+  const double w[4] = {-0.5 * (1 + r + s + t), 0.5 * (1 + r), 0.5 * (1 + s), 0.5 * (1 + t)};
+  for (int d = 0; d < 3; ++d) {
+    x[d] = 0;
+    for (int m = 0; m < 4; ++m) x[d] += w[m] * verts[12 * k + 3 * m + d];
   }
+}
+
+inline void face_centroid(const double* verts, int k, int f, double* c) {
+  for (int x = 0; x < 3; ++x) {
+    c[x] = 0.0;
+    for (int j = 0; j < 3; ++j) c[x] += verts[12 * k + 3 * kFaceVerts[f][j] + x] / 3.0;
+  }
+}
+
+// Wraps a coordinate difference by the whole periods it spans (periodic axes only).
+inline void unwrap(const double period[3], double* d) {
+  for (int x = 0; x < 3; ++x)
+    if (period[x] > 0) d[x] -= period[x] * std::nearbyint(d[x] / period[x]);
+}
+
+std::string face_name(int kf) { return "face " + std::to_string(kf % 4) + " of element " + std::to_string(kf / 4); }
+
+// Faces paired by centroid modulo the period: partner[4 k + f] = 4 k2 + f2, or -1 for a face
+// without a partner, which must carry a face_bc code.
+bool pair_faces_by_centroid(int K, const double* verts, const double period[3], const int32_t* face_bc,
+                            std::vector<int>& partner, std::string& err) {
   const double h = min_edge(K, verts);
   const double quantum = 1e-6 * h;
-  // face centroids (unwrapped) and their wrapped, quantised keys
-  std::vector<std::array<double, 3>> cent((size_t)K * 4);
   std::vector<std::array<long long, 3>> key((size_t)K * 4);
   for (int k = 0; k < K; ++k)
     for (int f = 0; f < 4; ++f) {
-      std::array<double, 3> c{};
-      for (int j = 0; j < 3; ++j)
-        for (int x = 0; x < 3; ++x) c[x] += verts[12 * k + 3 * kFaceVerts[f][j] + x] / 3.0;
-      cent[4 * k + f] = c;
+      double c[3];
+      face_centroid(verts, k, f, c);
       for (int x = 0; x < 3; ++x) {
         double w = c[x];
         if (period[x] > 0) w -= period[x] * std::floor(w / period[x] + 1e-7);
@@ -135,44 +154,38 @@ bool build_connectivity(int K, const double* verts, const double period[3], cons
   std::vector<int> order((size_t)K * 4);
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
-  std::vector<int> partner((size_t)K * 4, -1);
+  partner.assign((size_t)K * 4, -1);
   for (size_t i = 0; i < order.size();) {
     size_t j = i + 1;
     while (j < order.size() && key[order[j]] == key[order[i]]) ++j;
     if (j - i == 1 && face_bc && face_bc[order[i]] != 0) {  // boundary face
-      const int code = face_bc[order[i]];
-      if (code < DG_BC_SLIP_WALL || code > DG_BC_OUTFLOW) {
-        err = "face_bc holds an unknown boundary-condition code " + std::to_string(code);
-        return false;
-      }
       i = j;
       continue;
     }
     if (j - i == 2 && face_bc && (face_bc[order[i]] != 0 || face_bc[order[i + 1]] != 0)) {
-      const int kf = face_bc[order[i]] != 0 ? order[i] : order[i + 1];
-      err = "face " + std::to_string(kf % 4) + " of element " + std::to_string(kf / 4) +
+      err = face_name(face_bc[order[i]] != 0 ? order[i] : order[i + 1]) +
             " has a partner but carries a boundary condition";
       return false;
     }
     if (j - i != 2) {
-      int kf = order[i];
-      err = "face " + std::to_string(kf % 4) + " of element " + std::to_string(kf / 4) + " has " +
-            std::to_string(j - i - 1) + " partners (expected exactly 1; is the mesh closed under the period?)";
+      err = face_name(order[i]) + " has " + std::to_string(j - i - 1) +
+            " partners (expected exactly 1; is the mesh closed under the period?)";
       return false;
     }
     partner[order[i]] = order[i + 1];
     partner[order[i + 1]] = order[i];
     i = j;
   }
-  // physical node coordinates on demand
-  auto node_xyz = [&](int k, int n, double* x) {
-    const double r = ref_nodes[3 * n], s = ref_nodes[3 * n + 1], t = ref_nodes[3 * n + 2];
-    const double w[4] = {-0.5 * (1 + r + s + t), 0.5 * (1 + r), 0.5 * (1 + s), 0.5 * (1 + t)};
-    for (int d = 0; d < 3; ++d) {
-      x[d] = 0;
-      for (int m = 0; m < 4; ++m) x[d] += w[m] * verts[12 * k + 3 * m + d];
-    }
-  };
+  return true;
+}
+
+// vmapP from a face pairing: the face nodes of a pair matched by coordinates under the pair's
+// periodic shift (the centroid difference rounded to whole periods); boundary faces get -code.
+bool match_face_nodes(int K, const double* verts, const double period[3], const RefOps& ops,
+                      const double* ref_nodes, const int32_t* face_bc, const std::vector<int>& partner,
+                      std::vector<int32_t>& vmapP, std::string& err) {
+  const int Np = ops.Np, Nfp = ops.Nfp, NF = 4 * Nfp;
+  const double h = min_edge(K, verts);
   vmapP.assign((size_t)K * NF, -1);
   std::vector<double> own(3 * Nfp), nb(3 * Nfp);
   std::vector<char> used(Nfp);
@@ -184,14 +197,16 @@ bool build_connectivity(int K, const double* verts, const double period[3], cons
         continue;
       }
       const int k2 = pf / 4, f2 = pf % 4;
-      double shift[3];
+      double ca[3], cb[3], shift[3];
+      face_centroid(verts, k, f, ca);
+      face_centroid(verts, k2, f2, cb);
       for (int x = 0; x < 3; ++x) {
-        double d = cent[4 * k + f][x] - cent[pf][x];
+        const double d = ca[x] - cb[x];
         shift[x] = period[x] > 0 ? period[x] * std::nearbyint(d / period[x]) : 0.0;
       }
       for (int i = 0; i < Nfp; ++i) {
-        node_xyz(k, ops.Fmask[f * Nfp + i], &own[3 * i]);
-        node_xyz(k2, ops.Fmask[f2 * Nfp + i], &nb[3 * i]);
+        node_xyz(verts, ref_nodes, k, ops.Fmask[f * Nfp + i], &own[3 * i]);
+        node_xyz(verts, ref_nodes, k2, ops.Fmask[f2 * Nfp + i], &nb[3 * i]);
       }
       std::fill(used.begin(), used.end(), 0);
       for (int i = 0; i < Nfp; ++i) {
@@ -207,14 +222,240 @@ bool build_connectivity(int K, const double* verts, const double period[3], cons
           }
         }
         if (bd > 1e-6 * h || used[best]) {
-          err = "face node " + std::to_string(i) + " of face " + std::to_string(f) + " of element " +
-                std::to_string(k) + " has no unique coincident partner";
+          err = "face node " + std::to_string(i) + " of " + face_name(4 * k + f) +
+                " has no unique coincident partner";
           return false;
         }
         used[best] = 1;
         vmapP[(size_t)k * NF + f * Nfp + i] = k2 * Np + ops.Fmask[f2 * Nfp + best];
       }
     }
+  return true;
+}
+
+bool check_face_bc(int K, const int32_t* face_bc, const std::vector<int>& partner, std::string& err) {
+  for (int kf = 0; kf < 4 * K; ++kf) {
+    const int code = face_bc ? face_bc[kf] : 0;
+    if (partner[kf] < 0 && (code < DG_BC_SLIP_WALL || code > DG_BC_OUTFLOW)) {
+      err = face_name(kf) + (code == 0 ? " has no partner and no boundary-condition code"
+                                       : " holds an unknown boundary-condition code " + std::to_string(code));
+      return false;
+    }
+    if (partner[kf] >= 0 && code != 0) {
+      err = face_name(kf) + " has a partner but carries a boundary condition";
+      return false;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+bool build_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
+                        const double* ref_nodes, const int32_t* face_bc, std::vector<int32_t>& vmapP,
+                        std::string& err, std::vector<int>* partner_out) {
+  if ((int64_t)K * ops.Np >= (int64_t)INT32_MAX) {
+    err = "K * Np exceeds the int32 node index range";
+    return false;
+  }
+  std::vector<int> local;
+  std::vector<int>& partner = partner_out ? *partner_out : local;
+  return pair_faces_by_centroid(K, verts, period, face_bc, partner, err) &&
+         check_face_bc(K, face_bc, partner, err) &&
+         match_face_nodes(K, verts, period, ops, ref_nodes, face_bc, partner, vmapP, err);
+}
+
+bool build_connectivity_from_faces(int K, const double* verts, const double period[3], const RefOps& ops,
+                                   const double* ref_nodes, const int32_t* face_bc, const int32_t* EToE,
+                                   const int32_t* EToF, std::vector<int32_t>& vmapP, std::string& err,
+                                   std::vector<int>& partner) {
+  if ((int64_t)K * ops.Np >= (int64_t)INT32_MAX) {
+    err = "K * Np exceeds the int32 node index range";
+    return false;
+  }
+  partner.assign((size_t)4 * K, -1);
+  for (int kf = 0; kf < 4 * K; ++kf) {
+    const int e2 = EToE[kf], f2 = EToF[kf];
+    if (e2 == -1) continue;  // no partner: a boundary face
+    if (e2 < 0 || e2 >= K || f2 < 0 || f2 > 3) {
+      err = "EToE / EToF of " + face_name(kf) + " is out of range";
+      return false;
+    }
+    const int pf = 4 * e2 + f2;
+    if (pf == kf || EToE[pf] != kf / 4 || EToF[pf] != kf % 4) {
+      err = "EToE / EToF are not symmetric at " + face_name(kf);
+      return false;
+    }
+    partner[kf] = pf;
+  }
+  return check_face_bc(K, face_bc, partner, err) &&
+         match_face_nodes(K, verts, period, ops, ref_nodes, face_bc, partner, vmapP, err);
+}
+
+bool check_connectivity(int K, const double* verts, const double period[3], const RefOps& ops,
+                        const double* ref_nodes, const int32_t* face_bc, const int32_t* vmapP,
+                        std::vector<int>& partner, std::string& err) {
+  const int Np = ops.Np, Nfp = ops.Nfp, NF = 4 * Nfp;
+  if ((int64_t)K * Np >= (int64_t)INT32_MAX) {
+    err = "K * Np exceeds the int32 node index range";
+    return false;
+  }
+  const double h = min_edge(K, verts);
+  partner.assign((size_t)4 * K, -1);
+  for (int k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      const int32_t* v = vmapP + (size_t)k * NF + f * Nfp;
+      if (v[0] < 0) {  // a boundary face: every node holds the same -code, as face_bc says
+        for (int i = 0; i < Nfp; ++i)
+          if (v[i] != v[0] || -v[0] < DG_BC_SLIP_WALL || -v[0] > DG_BC_OUTFLOW ||
+              !face_bc || face_bc[4 * k + f] != -v[0]) {
+            err = "vmapP of " + face_name(4 * k + f) + " mixes boundary codes or disagrees with face_bc";
+            return false;
+          }
+        continue;
+      }
+      // an interior face: all partners on one face f2 of one element k2
+      int k2 = -1, f2 = -1;
+      for (int i = 0; i < Nfp; ++i)
+        if (v[i] < 0 || (int64_t)v[i] >= (int64_t)K * Np || (i > 0 && v[i] / Np != v[0] / Np)) {
+          err = "vmapP of " + face_name(4 * k + f) + " is out of range or spans several elements";
+          return false;
+        }
+      k2 = v[0] / Np;
+      for (int g = 0; g < 4 && f2 < 0; ++g) {
+        bool all = true;
+        for (int i = 0; i < Nfp && all; ++i) {
+          bool found = false;
+          for (int j = 0; j < Nfp && !found; ++j) found = ops.Fmask[g * Nfp + j] == v[i] % Np;
+          all = found;
+        }
+        if (all) f2 = g;
+      }
+      if (f2 < 0 || (k2 == k && f2 == f)) {
+        err = "vmapP of " + face_name(4 * k + f) + " does not map onto another face";
+        return false;
+      }
+      partner[4 * k + f] = 4 * k2 + f2;
+      for (int i = 0; i < Nfp; ++i) {
+        // the partner node coincides with the own node (modulo the period) ...
+        double a[3], b[3];
+        node_xyz(verts, ref_nodes, k, ops.Fmask[f * Nfp + i], a);
+        node_xyz(verts, ref_nodes, k2, v[i] % Np, b);
+        double d[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+        unwrap(period, d);
+        if (std::sqrt(dot3(d, d)) > 1e-6 * h) {
+          err = "vmapP of face node " + std::to_string(i) + " of " + face_name(4 * k + f) +
+                " names a node at another position";
+          return false;
+        }
+        // ... and maps back
+        const int32_t* w = vmapP + (size_t)k2 * NF + f2 * Nfp;
+        bool back = false;
+        for (int j = 0; j < Nfp && !back; ++j)
+          back = ops.Fmask[f2 * Nfp + j] == v[i] % Np && w[j] == k * Np + ops.Fmask[f * Nfp + i];
+        if (!back) {
+          err = "vmapP is not symmetric at face node " + std::to_string(i) + " of " + face_name(4 * k + f);
+          return false;
+        }
+      }
+    }
+  return check_face_bc(K, face_bc, partner, err);
+}
+
+bool check_vertex_numbers(int K, const int32_t* EToV, const std::vector<int>& partner, std::string& err) {
+  for (int kf = 0; kf < 4 * K; ++kf) {
+    if (EToV[kf] < 0) {
+      err = "EToV of element " + std::to_string(kf / 4) + " holds a negative vertex number";
+      return false;
+    }
+    const int pf = partner[kf];
+    if (pf < 0) continue;
+    std::array<int32_t, 3> a, b;
+    for (int j = 0; j < 3; ++j) {
+      a[j] = EToV[4 * (kf / 4) + kFaceVerts[kf % 4][j]];
+      b[j] = EToV[4 * (pf / 4) + kFaceVerts[pf % 4][j]];
+    }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a != b) {
+      err = "EToV disagrees with the face pairing at " + face_name(kf) + " (paired faces share their vertices)";
+      return false;
+    }
+  }
+  return true;
+}
+
+bool check_ref_ops(int N, const double* ref_nodes, const double* Dr, const double* Ds, const double* Dt,
+                   const double* LIFT, const int32_t* Fmask, std::string& err) {
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2;
+  const double* D[3] = {Dr, Ds, Dt};
+  for (int a = 0; a < 3; ++a) {
+    double big = 0.0;
+    for (int i = 0; i < Np * Np; ++i) {
+      if (!std::isfinite(D[a][i])) {
+        err = "a differentiation matrix has a non-finite entry";
+        return false;
+      }
+      big = std::max(big, std::fabs(D[a][i]));
+    }
+    for (int i = 0; i < Np; ++i) {  // the derivative of a constant is zero
+      double row = 0.0;
+      for (int j = 0; j < Np; ++j) row += D[a][i * Np + j];
+      if (std::fabs(row) > 1e-9 * Np * big) {
+        err = "row " + std::to_string(i) + " of D" + "rst"[a] + " does not annihilate constants";
+        return false;
+      }
+    }
+  }
+  for (int i = 0; i < Np * 4 * Nfp; ++i)
+    if (!std::isfinite(LIFT[i])) {
+      err = "LIFT has a non-finite entry";
+      return false;
+    }
+  for (int f = 0; f < 4; ++f)
+    for (int i = 0; i < Nfp; ++i) {
+      const int n = Fmask[f * Nfp + i];
+      if (n < 0 || n >= Np) {
+        err = "Fmask holds a node index outside 0..Np-1";
+        return false;
+      }
+      for (int j = 0; j < i; ++j)
+        if (Fmask[f * Nfp + j] == n) {
+          err = "Fmask lists a node twice on face " + std::to_string(f);
+          return false;
+        }
+      // face f of the reference tetrahedron: t = -1, s = -1, r + s + t = -1, r = -1
+      const double r = ref_nodes[3 * n], s2 = ref_nodes[3 * n + 1], t = ref_nodes[3 * n + 2];
+      const double on[4] = {t + 1.0, s2 + 1.0, r + s2 + t + 1.0, r + 1.0};
+      if (std::fabs(on[f]) > 1e-10) {
+        err = "Fmask lists node " + std::to_string(n) + " on face " + std::to_string(f) + ", which it is not on";
+        return false;
+      }
+    }
+  return true;
+}
+
+bool check_geometry(int K, const double* geo, std::string& err) {
+  for (int k = 0; k < K; ++k) {
+    const double* g = geo + (size_t)k * DG_GEO_STRIDE;
+    for (int j = 0; j < DG_GEO_STRIDE; ++j)
+      if (!std::isfinite(g[j])) {
+        err = "geometric factors of element " + std::to_string(k) + " are not finite";
+        return false;
+      }
+    if (!(g[25] > 0)) {
+      err = "element " + std::to_string(k) + " has a non-positive Jacobian in the given geometric factors";
+      return false;
+    }
+    for (int f = 0; f < 4; ++f) {
+      const double* n = g + 9 + 4 * f;
+      if (std::fabs(dot3(n, n) - 1.0) > 1e-10 || !(n[3] > 0)) {
+        err = "face " + std::to_string(f) + " of element " + std::to_string(k) +
+              " has a normal that is not a unit vector or a non-positive Fscale";
+        return false;
+      }
+    }
+  }
   return true;
 }
 

@@ -40,11 +40,12 @@ def _hptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0):
+def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0, wait_polls=0):
     o = capi.dg_opts()
     o.precision = precision
     o.t_seed = t_seed
     o.t_const = t_const
+    o.wait_polls = wait_polls
     return o
 
 
@@ -53,8 +54,18 @@ def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0):
 class Mesh:
     """An uploaded mesh (dg_mesh handle)."""
 
-    def __init__(self, vertices, period, N, ref_nodes, host_only=False, face_bc=None):
-        """face_bc: optional [K][4] DG_BC_* codes of the faces without a partner (0 elsewhere)."""
+    # caller tables of dg_mesh_desc: name -> (dtype, shape as a function of K, Np, Nfp)
+    _TABLES = {"EToV": (np.int32, lambda K, Np, Nfp: (K, 4)), "EToE": (np.int32, lambda K, Np, Nfp: (K, 4)),
+               "EToF": (np.int32, lambda K, Np, Nfp: (K, 4)), "vmapP": (np.int32, lambda K, Np, Nfp: (K, 4 * Nfp)),
+               "Dr": (np.float64, lambda K, Np, Nfp: (Np, Np)), "Ds": (np.float64, lambda K, Np, Nfp: (Np, Np)),
+               "Dt": (np.float64, lambda K, Np, Nfp: (Np, Np)), "LIFT": (np.float64, lambda K, Np, Nfp: (Np, 4 * Nfp)),
+               "Fmask": (np.int32, lambda K, Np, Nfp: (4, Nfp)),
+               "geo": (np.float64, lambda K, Np, Nfp: (K, capi.DG_GEO_STRIDE))}
+
+    def __init__(self, vertices, period, N, ref_nodes, host_only=False, face_bc=None, tables=None):
+        """face_bc: optional [K][4] DG_BC_* codes of the faces without a partner (0 elsewhere).
+        tables: optional dict of caller tables (EToV, EToE, EToF, vmapP, Dr, Ds, Dt, LIFT, Fmask, geo),
+        which the library checks and uses instead of building them."""
         lib = load()
         self._v = np.ascontiguousarray(vertices, dtype=np.float64)
         self._r = np.ascontiguousarray(ref_nodes, dtype=np.float64)
@@ -74,6 +85,17 @@ class Mesh:
             d.period[i] = float(period[i])
         d.flags = capi.DG_MESH_HOST_ONLY if host_only else 0
         d.face_bc = None if self._bc is None else _hptr(self._bc)
+        self._tables = {}
+        Np_, Nfp_ = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+        for name, arr in (tables or {}).items():
+            if name not in self._TABLES:
+                raise ValueError(f"unknown mesh table {name!r}")
+            dtype, shape = self._TABLES[name]
+            a = np.ascontiguousarray(arr, dtype=dtype)
+            if a.shape != shape(d.K, Np_, Nfp_):
+                raise ValueError(f"{name} must have the shape {shape(d.K, Np_, Nfp_)}")
+            self._tables[name] = a
+            setattr(d, name, _hptr(a))
         h = ctypes.c_void_p()
         check(lib.dg_mesh_upload(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -94,6 +116,13 @@ class Mesh:
         geo = np.zeros((self.K, capi.DG_GEO_STRIDE))
         check(load().dg_mesh_connectivity(self.handle, _hptr(vmapP), _hptr(geo)))
         return vmapP, geo
+
+    def face_pairs(self):
+        """(EToE, EToF) [K][4]: the element and face paired with each face (-1 at boundary faces)."""
+        EToE = np.zeros((self.K, 4), dtype=np.int32)
+        EToF = np.zeros((self.K, 4), dtype=np.int32)
+        check(load().dg_mesh_face_pairs(self.handle, _hptr(EToE), _hptr(EToF)))
+        return EToE, EToF
 
     def set_inflow(self, q_in):
         """Conserved state imposed on DG_BC_INFLOW faces (5 values for a perfect gas)."""

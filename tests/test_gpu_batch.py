@@ -9,7 +9,7 @@ from oracle.euler import rhs_strong
 from oracle.lsrk import lsrk4_step
 from oracle.ns import rhs_ns
 from oracle.thermo import PerfectGas
-from tests._gpu import field_err, torch_cuda
+from tests._gpu import component_err, field_err, torch_cuda
 from tests._oracle_case import Disc
 from workloads.configs import batched_cases
 
@@ -78,6 +78,7 @@ def test_batch_against_oracle():
             f = lambda u: rhs_strong(d.ref, d.geo, d.conn, u, PerfectGas(g.gamma, g.R))
         want = lsrk4_step(c["q"], dt, f)
         assert field_err(q.cpu().numpy(), want) <= 1e-6
+        assert component_err(q.cpu().numpy(), want) <= 1e-4
 
 
 @pytest.mark.slow

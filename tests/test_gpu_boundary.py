@@ -8,7 +8,7 @@ import pytest
 import oracle.boundary as bd
 from oracle.lsrk import lsrk4_step
 from oracle.thermo import PerfectGas
-from tests._gpu import field_err, rel_err, torch_cuda
+from tests._gpu import component_err, field_err, rel_err, torch_cuda
 from tests._oracle_case import bc_disc
 from workloads import equispaced_tet_nodes, uniform_perturbation
 
@@ -168,3 +168,4 @@ def test_mixed_rk4_steps_with_boundaries(viscous):
     want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
     err = field_err(q.cpu().numpy(), want)
     assert err <= 1e-6, err
+    assert component_err(q.cpu().numpy(), want) <= 1e-4

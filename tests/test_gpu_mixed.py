@@ -17,7 +17,7 @@ from oracle.euler import rhs_strong
 from oracle.lsrk import lsrk4_step
 from oracle.ns import rhs_ns
 from oracle.thermo import Nasa7Gas, PerfectGas
-from tests._gpu import field_err, torch_cuda
+from tests._gpu import component_err, field_err, torch_cuda
 from tests._oracle_case import Disc
 from workloads import box_mesh, equispaced_tet_nodes, isentropic_vortex, taylor_green, uniform_perturbation
 from workloads.gas import mixture_primitive_state, seeded_nasa7_mixture
@@ -25,7 +25,15 @@ from workloads.mlp import glorot_params, temperature_samples
 
 pytestmark = pytest.mark.gpu
 RHS_TOL = 1e-4     # right-hand side, relative per variable
-STATE_TOL = 1e-6   # state after the RK4 steps (the precision form's bar)
+STATE_TOL = 1e-6   # state after the RK4 steps (the precision form's bar, per field: tests._gpu.field_err)
+COMPONENT_TOL = 1e-4  # the same states per component (tests._gpu.component_err)
+
+
+def _assert_state(got, want):
+    err = field_err(got, want)
+    assert err <= STATE_TOL, err
+    cerr = component_err(got, want)
+    assert cerr <= COMPONENT_TOL, cerr
 
 
 def _mixed_opts():
@@ -99,8 +107,7 @@ def test_mixed_precision_config_state_error_reduced_mesh():
     want = q0
     for _ in range(10):
         want = lsrk4_step(want, dt, f)
-    err = field_err(q.cpu().numpy(), want)
-    assert err <= STATE_TOL, err
+    _assert_state(q.cpu().numpy(), want)
     assert mesh.status() == 0
 
 
@@ -121,7 +128,7 @@ def test_mixed_many_tiles_per_block_against_fp64_path(N):
     dt = _tgv_dt(14, N)
     dg.lsrk4_step(mesh, gas, q64, dt, steps=2)
     dg.lsrk4_step(mesh, gas, qmx, dt, steps=2, opts=_mixed_opts())
-    assert field_err(qmx.cpu().numpy(), q64.cpu().numpy()) <= STATE_TOL
+    _assert_state(qmx.cpu().numpy(), q64.cpu().numpy())
     assert mesh.status() == 0
 
 
@@ -140,8 +147,7 @@ def test_mixed_precision_config_full_size_against_fp64_path():
     qmx = q64.clone()
     dg.lsrk4_step(mesh, gas, q64, cfg.dt, steps=cfg.steps)
     dg.lsrk4_step(mesh, gas, qmx, cfg.dt, steps=cfg.steps, opts=_mixed_opts())
-    err = field_err(qmx.cpu().numpy(), q64.cpu().numpy())
-    assert err <= STATE_TOL, err
+    _assert_state(qmx.cpu().numpy(), q64.cpu().numpy())
     assert mesh.status() == 0
 
 
@@ -208,7 +214,7 @@ def test_mixed_precision_plus_learned_guess_step():
     want = q0
     for _ in range(2):
         want = lsrk4_step(want, dt, f)
-    assert field_err(q.cpu().numpy(), want) <= STATE_TOL
+    _assert_state(q.cpu().numpy(), want)
     assert mesh.status() == 0 and gas.status() == 0
 
 
@@ -243,5 +249,5 @@ def test_mixed_plus_learned_full_size_against_fp64_path():
                   opts=dg._opts(t_seed=capi.DG_TSEED_CONST, t_const=1650.0))
     dg.lsrk4_step(mesh, gas, qmx, cfg.dt, steps=cfg.steps, T_io=Tmx,
                   opts=dg._opts(precision=capi.DG_PREC_MIXED, t_seed=capi.DG_TSEED_MLP))
-    assert field_err(qmx.cpu().numpy(), q64.cpu().numpy()) <= STATE_TOL
+    _assert_state(qmx.cpu().numpy(), q64.cpu().numpy())
     assert mesh.status() == 0 and gas.status() == 0
