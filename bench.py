@@ -66,9 +66,9 @@ TRAFFIC = {
     ("fd640972440b44d5", "ns_viscous", "viscous"): 126.838528e6 + 75.130112e6,
     ("fd640972440b44d5", "ns_viscous", "prims"): 66.396160e6 + 7.919616e6,
     # profiles/mixed_tc_ns_N3_K82944.md (first stage: the RK register is not read)
-    ("17750afbff787730", "ns_viscous", "mixed_rhs"): 251.656192e6 + 111.862016e6,
-    ("17750afbff787730", "ns_viscous", "mixed_viscous"): 90.061568e6 + 23.028480e6,
-    ("17750afbff787730", "ns_viscous", "mixed_prims"): 66.375424e6 + 14.374656e6,
+    ("60bbd0ca050e05bd", "ns_viscous", "mixed_rhs"): 252.058624e6 + 112.077312e6,
+    ("60bbd0ca050e05bd", "ns_viscous", "mixed_viscous"): 90.059264e6 + 22.826240e6,
+    ("60bbd0ca050e05bd", "ns_viscous", "mixed_prims"): 66.368512e6 + 14.308608e6,
 }
 
 
