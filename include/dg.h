@@ -328,7 +328,10 @@ typedef struct {
 
 /* ---- the hot path ------------------------------------------------------------ */
 
-/* Semi-discrete right-hand side rhs = dq/dt (strong form):
+/* Semi-discrete right-hand side rhs = dq/dt (strong form) of the nodal DG discretisation that
+ * MIRGE-Com evaluates (Sec. 1 and Fig. 1: element-local DOF arrays; Sec. 4.2.2 / Sec. 5.2: the
+ * reference-operator contractions of the full assembly; Sec. 4.3: the indirect face gather;
+ * Sec. 5.2 Euler, Sec. 5.3 Navier-Stokes):
  *   rhs = -sum_d dG_d/dx_d + LIFT( Fscale * (n.G(q-) - G*) ),  G = F_euler - F_viscous,
  * with the pointwise Lax-Friedrichs flux for F_euler and, when mu > 0, BR1
  * central fluxes for the gradients of (rho, rho u, T) and for F_viscous.
@@ -339,7 +342,9 @@ typedef struct {
 int dg_rhs(dg_mesh mesh, dg_gas gas, const double* q_dev, double* rhs_dev, double* T_io_dev,
            const dg_opts* opts, void* stream);
 
-/* Stage s (0..4) of the five-stage 2N-storage RK4 (Carpenter & Kennedy 1994):
+/* Stage s (0..4) of the explicit fourth-order Runge-Kutta time stepping of the paper's runs
+ * (Sec. 5.2, the MFEM comparison advances the DG discretisation with explicit fourth-order
+ * Runge-Kutta), here the five-stage 2N-storage RK4 of Carpenter & Kennedy (1994):
  *   k <- a_s k + dt rhs(q_in),   q_out <- q_in + b_s k.
  * The right-hand side and the update are fused; k_dev is updated in place
  * (a_0 = 0, so its content is ignored at s = 0).  q_out_dev must not overlap
@@ -350,7 +355,9 @@ int dg_rk_stage(dg_mesh mesh, dg_gas gas, int32_t stage, double dt, const double
 /* The coefficients a_s, b_s (s = 0..4) used by dg_rk_stage (host arrays of 5). */
 int dg_lsrk4_coefficients(double* a_host, double* b_host);
 
-/* Per-node temperature of a NASA-7 mixture from the conserved state:
+/* Per-node temperature of a NASA-7 mixture from the conserved state, the pointwise solve of the
+ * paper's multi-species model (Sec. 4: the compressible multispecies flow example; Sec. 5:
+ * MIRGE-Com's reactive mixture viscous flows):
  * e = rho E / rho - |u|^2/2, Y_k = rho Y_k / rho, Newton T <- T - (e(T) - e)/cv(T)
  * from the seed (T_io or opts.t_const) until |dT| < newton_tol.  n nodes;
  * q_dev: [V][n] (V = 5 + nspecies); T_io_dev: [n]; iters_dev (nullable):

@@ -98,12 +98,11 @@ def _w_of(q, gas):
     return np.stack([q[0], q[1], q[2], q[3], p / (q[0] * gas.R)])
 
 
-def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong"):
-    """Navier-Stokes right-hand side [5][K][Np] (BR1, central fluxes) with boundary faces."""
+def viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None):
+    """The first BR1 pass: the viscous flux Fv[3][5][K][Np] of q from the BR1 gradients of
+    w = (rho, rho u, rho v, rho w, T) with central fluxes, exterior values w(q+) at boundary faces."""
     kappa = mu * gas.cp / Pr
-    p, c = gas.pressure_sound_speed(q)
     n, qM, qP = _traces(conn, geo, ref, q, q_in)
-    # BR1 gradient of w = (rho, rho u, rho v, rho w, T), exterior values w(q+)
     w = _w_of(q, gas)
     wM, wP = gather(w, conn.vmapM), _w_of(qP, gas)
     drdx = geo.drdx()
@@ -113,7 +112,17 @@ def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong"):
         for a in range(3):
             grad[d] += drdx[a, d][None, :, None] * dref[a]
         grad[d] += lift(ref, geo, n[d][None] * 0.5 * (wP - wM))
-    Fv = viscous_flux(q, w[4], grad, mu, kappa)
+    return viscous_flux(q, w[4], grad, mu, kappa)
+
+
+def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong", Fv=None):
+    """Navier-Stokes right-hand side [5][K][Np] (BR1, central fluxes) with boundary faces.  Fv: the
+    viscous flux of the first BR1 pass (viscous_flux_bc), computed here when not given (a
+    partitioned run passes it with its halo filled from the owners)."""
+    p, c = gas.pressure_sound_speed(q)
+    n, qM, qP = _traces(conn, geo, ref, q, q_in)
+    if Fv is None:
+        Fv = viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in)
     FvM = np.stack([gather(Fv[d], conn.vmapM) for d in range(3)])
     nvM = normal_flux(FvM, n)  # [5][K][4 Nfp]: 0, traction t, energy flux e
     nvP = normal_flux(np.stack([gather(Fv[d], conn.vmapP) for d in range(3)]), n)

@@ -189,28 +189,48 @@ def _refresh(ranks, transport, ptrs, V):
         r.halo.unpack(p, V, g)
 
 
-def partitioned_lsrk4_step(ranks: list, gas, transport, dt):
-    """One LSRK4 step of the partitions held by this process (FP64 form, perfect gas).  Before
-    every stage the halos of the states are refreshed; with viscosity each partition's viscous
-    flux is computed, its halo refreshed, and the stage uses it."""
-    from .dg import _opts, dg_rk_stage
+class LibdgBackend:
+    """The partitioned step on the library's kernels (FP64 form, perfect gas): the halo packed and
+    unpacked on the device (dg_gather_elements / dg_scatter_elements), the BR1 viscous flux into
+    the mesh's buffer (dg_viscous_flux, 9 fields per node), the stage by dg_rk_stage with
+    viscous_given when the gas is viscous."""
+
+    flux_vars = 9
+
+    def refresh(self, ranks, transport, arrays, V):
+        _refresh(ranks, transport, [a if isinstance(a, int) else a.data_ptr() for a in arrays], V)
+
+    def viscous_flux(self, rank, gas, q):
+        check(load().dg_viscous_flux(rank.mesh.handle, gas.handle, ctypes.c_void_p(q.data_ptr()), None))
+        return viscous_buffer(rank.mesh)
+
+    def stage(self, rank, gas, s, dt, q_in, q_out, viscous):
+        from .dg import _opts, dg_rk_stage
+        opts = _opts()
+        opts.viscous_given = 1 if viscous else 0
+        dg_rk_stage(rank.mesh, gas, s, dt, q_in, q_out, rank.work[1], opts=opts)
+
+
+def partitioned_lsrk4_step(ranks: list, gas, transport, dt, backend=None):
+    """One LSRK4 step of the partitions held by this process (perfect gas).  Before every stage the
+    halos of the states are refreshed; with viscosity each partition's viscous flux is computed,
+    its halo refreshed, and the stage uses it (the two exchanges of a BR1 right-hand side).
+    backend: the compute of one partition (LibdgBackend, the default, runs the library's kernels;
+    any object with the same three methods and flux_vars works, e.g. a CPU one in the tests)."""
+    backend = backend or LibdgBackend()
     if getattr(gas, "model", "perfect") != "perfect":
         raise ValueError("the partitioned step takes a perfect gas")
     V = ranks[0].q.shape[0]
     viscous = gas.mu > 0
-    opts = _opts()
-    if viscous:
-        opts.viscous_given = 1
     cur = [r.q for r in ranks]
     nxt = [r.work[0] for r in ranks]
     for s in range(5):
-        _refresh(ranks, transport, [c.data_ptr() for c in cur], V)
+        backend.refresh(ranks, transport, cur, V)
         if viscous:
-            for r, c in zip(ranks, cur):
-                check(load().dg_viscous_flux(r.mesh.handle, gas.handle, ctypes.c_void_p(c.data_ptr()), None))
-            _refresh(ranks, transport, [viscous_buffer(r.mesh) for r in ranks], 9)
+            fv = [backend.viscous_flux(r, gas, c) for r, c in zip(ranks, cur)]
+            backend.refresh(ranks, transport, fv, backend.flux_vars)
         for r, c, n in zip(ranks, cur, nxt):
-            dg_rk_stage(r.mesh, gas, s, dt, c, n, r.work[1], opts=opts)
+            backend.stage(r, gas, s, dt, c, n, viscous)
         cur, nxt = nxt, cur
     for r, c in zip(ranks, cur):
         if c is not r.q:

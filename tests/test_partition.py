@@ -159,3 +159,119 @@ def test_gloo_halo_exchange_two_ranks(lib):
     for p in procs:
         p.join(timeout=60)
     assert res == {0: True, 1: True}
+
+
+class OracleBackend:
+    """The compute of one partition on the CPU with the oracle (the test's stand-in for the
+    library's kernels): halo rows copied by index, the BR1 viscous flux of the oracle's first pass
+    (3 x 5 fields per node), the stage from the oracle's right-hand side with that flux."""
+
+    flux_vars = 15
+
+    def __init__(self, gas, mu, Pr):
+        self.gas, self.mu, self.Pr = gas, mu, Pr
+
+    def refresh(self, ranks, transport, arrays, V):
+        import torch
+        like = torch.zeros(1, dtype=torch.float64)
+        sends = [{s: a[:, torch.from_numpy(ix).long()].contiguous() for s, ix in r.part.send.items()}
+                 for r, a in zip(ranks, arrays)]
+        shapes = [{s: (V, len(ix), a.shape[2]) for s, ix in r.part.recv.items()} for r, a in zip(ranks, arrays)]
+        for r, a, got in zip(ranks, arrays, transport.exchange_all(sends, shapes, like)):
+            for s, buf in got.items():
+                a[:, torch.from_numpy(r.part.recv[s]).long()] = buf
+
+    def viscous_flux(self, rank, gas, q):
+        import torch
+        import oracle.boundary as bd
+        d = rank.disc
+        fv = bd.viscous_flux_bc(d.ref, d.geo, d.conn, q.numpy(), self.gas, self.mu, self.Pr)
+        rank.fv = torch.from_numpy(np.ascontiguousarray(fv.reshape(15, d.K, d.ref.Np)))
+        return rank.fv
+
+    def stage(self, rank, gas, s, dt, q_in, q_out, viscous):
+        import torch
+        import oracle.boundary as bd
+        from oracle.lsrk import RK4A, RK4B
+        d, q = rank.disc, q_in.numpy()
+        if viscous:
+            rhs = bd.rhs_ns_bc(d.ref, d.geo, d.conn, q, self.gas, self.mu, self.Pr,
+                               Fv=rank.fv.numpy().reshape(3, 5, d.K, d.ref.Np))
+        else:
+            rhs = bd.rhs_euler_bc(d.ref, d.geo, d.conn, q, self.gas)
+        k = RK4A[s] * rank.work[1].numpy() + dt * rhs
+        rank.work[1].copy_(torch.from_numpy(k))
+        q_out.copy_(torch.from_numpy(q + RK4B[s] * k))
+
+
+def _two_step_case(viscous):
+    from workloads import physical_nodes, taylor_green
+    N = 2
+    v, per = box_mesh((4, 2, 2), 1.0)
+    nodes = equispaced_tet_nodes(N)
+    xyz = physical_nodes(v, nodes)
+    if viscous:
+        q0 = uniform_perturbation(taylor_green(xyz, mach=0.3, noise=0.01, seed=1), 1e-3, seed=2)
+    else:
+        q0 = uniform_perturbation(isentropic_vortex(xyz, 0.0, period=per), 1e-3, seed=2)
+    return N, v, per, nodes, q0, 2e-3, (2e-2 if viscous else 0.0)
+
+
+def _partitioned_step_worker(rank, world, port, viscous, out):
+    import types
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle.thermo import PerfectGas
+        from paper_2512_17101_gb300.partition import TorchTransport, partition_mesh, partitioned_lsrk4_step
+        N, v, per, nodes, q0, dt, mu = _two_step_case(viscous)
+        p = partition_mesh(v, per, N, nodes, world)[rank]
+        q = torch.from_numpy(np.ascontiguousarray(q0[:, p.local]))
+        q[:, len(p.owned):] = float("nan")  # the halo before the first exchange
+        st = types.SimpleNamespace(part=p, disc=Disc(p.vertices, per, N, face_bc=p.face_bc), q=q,
+                                   work=(torch.empty_like(q), torch.zeros_like(q)), fv=None)
+        gas = types.SimpleNamespace(model="perfect", mu=mu)
+        backend = OracleBackend(PerfectGas(1.4, 1.0), mu, 0.71)
+        for _ in range(2):
+            partitioned_lsrk4_step([st], gas, TorchTransport(), dt, backend=backend)
+        out.put((rank, p.owned, st.q[:, :len(p.owned)].numpy().copy()))
+    except Exception as e:  # reported to the parent, which fails the test
+        out.put((rank, None, repr(e)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_gloo_partitioned_lsrk4_steps_two_ranks(lib, viscous):
+    """Two full LSRK4 steps of a mesh split over two gloo ranks (halo of the state, and for
+    Navier-Stokes of the BR1 viscous flux, exchanged before every stage by TorchTransport), each
+    rank's compute by the oracle, equal the single-mesh oracle steps at 1e-12."""
+    import multiprocessing as mp
+    import oracle.boundary as bd
+    from oracle.lsrk import lsrk4_step
+    from oracle.thermo import PerfectGas
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_partitioned_step_worker, args=(r, 2, port, viscous, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [out.get(timeout=300) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    for _, owned, q in res:
+        assert owned is not None, q
+    N, v, per, nodes, q0, dt, mu = _two_step_case(viscous)
+    g = Disc(v, per, N)
+    gas = PerfectGas(1.4, 1.0)
+    f = (lambda u: bd.rhs_ns_bc(g.ref, g.geo, g.conn, u, gas, mu, 0.71)) if viscous else \
+        (lambda u: bd.rhs_euler_bc(g.ref, g.geo, g.conn, u, gas))
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    got = np.full_like(want, np.nan)
+    for _, owned, q in res:
+        got[:, owned] = q
+    assert not np.isnan(got).any()
+    scale = np.abs(want).max(axis=(1, 2))
+    assert (np.abs(got - want).max(axis=(1, 2)) / scale).max() <= 1e-12
