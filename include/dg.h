@@ -603,6 +603,14 @@ int dg_widen_to_double(const float* x_dev, double* y_dev, int64_t n, void* strea
  * temperature); hi, lo: device arrays of n floats. */
 int dg_split_to_float_pair(const double* x_dev, float* hi_dev, float* lo_dev, int64_t n, void* stream);
 
+/* ---- device characterisation ----------------------------------------------------------------
+ * *tflops_host <- the FP64 FMA throughput of the current device in TFLOP/s (an FMA counted as two
+ * flops), measured with a kernel of independent FMA chains on every SM (best of three timed
+ * launches after a warm-up; CUDA events).  The measured denominator beside the nominal FP64 peak
+ * for kernels that the FP64 pipe bounds.  The paper has no counterpart.  Synchronous; allocates
+ * 8 bytes of device memory.  Errors: DG_ERR_INVALID_ARG (NULL), DG_ERR_CUDA. */
+int dg_fp64_fma_rate(double* tflops_host);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dg_last_error(void);
 

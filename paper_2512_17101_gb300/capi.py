@@ -129,6 +129,7 @@ SIGNATURES = {
     "dg_mlp_set": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(dg_mlp_norm)]),
     "dg_mlp_get": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(dg_mlp_norm)]),
     "dg_mlp_loss_grad": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_fp64_fma_rate": (c_int32, [c_void_p]),
     "dg_mlp_adam_step": (c_int32, [c_int32, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mlp_train": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                ctypes.POINTER(dg_mlp_train_opts), c_void_p]),

@@ -549,6 +549,13 @@ def dg_mlp_loss_grad(params, x, t, grad, loss, stream=None):
                                   _dptr(loss, torch.float32, "loss"), _stream_ptr(stream)))
 
 
+def dg_fp64_fma_rate() -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s (synchronous)."""
+    r = ctypes.c_double()
+    check(load().dg_fp64_fma_rate(ctypes.byref(r)))
+    return r.value
+
+
 def dg_mlp_adam_step(t, lr, params, grad, m, v, stream=None):
     """One Adam update in place on float32 CUDA tensors of DG_MLP_PARAMS values (zeroes grad)."""
     import torch
