@@ -128,13 +128,25 @@ __device__ __forceinline__ void append(int* list, int* cnt, bool flag, int value
   if (flag) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
 }
 
-// Every thread of the block (blockDim.x == NB) stages its node (valid or not): coefficients, rho e
-// and the seed; the valid slots form the first active list.  Begins with a barrier so that the
-// previous use of R is over.
-template <int NB>
-__device__ __forceinline__ void stage(Rounds<NB>& R, bool valid, const double C[6], double rho_e, double seed) {
-  const int tid = threadIdx.x;
-  __syncthreads();
+// Barriers of the block solve: the whole block (__syncthreads), or a named barrier among the
+// `count` threads of a group of warps (a warp-specialised kernel whose other warps run other work).
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int ID, int COUNT>  // barrier 1..15, threads (a multiple of 32)
+struct GroupSync {
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "n"(COUNT) : "memory");
+  }
+};
+
+// Every thread of the group (NB threads, index tid in 0..NB-1) stages its node (valid or not):
+// coefficients, rho e and the seed; the valid slots form the first active list.  Begins with a
+// barrier so that the previous use of R is over.
+template <int NB, class Sync>
+__device__ __forceinline__ void stage(Rounds<NB>& R, bool valid, const double C[6], double rho_e, double seed,
+                                      int tid, Sync sync) {
+  sync();
   if (tid == 0) R.count[0] = R.count[1] = R.count[2] = 0;
 #pragma unroll
   for (int j = 0; j < 6; ++j) R.C[j][tid] = C[j];
@@ -143,16 +155,19 @@ __device__ __forceinline__ void stage(Rounds<NB>& R, bool valid, const double C[
   R.e[tid] = rho_e;
   R.t[tid] = seed;
   R.it[tid] = 0;
-  __syncthreads();
+  sync();
   append(R.list[0], &R.count[0], valid, tid);
-  __syncthreads();
+  sync();
+}
+template <int NB>
+__device__ __forceinline__ void stage(Rounds<NB>& R, bool valid, const double C[6], double rho_e, double seed) {
+  stage<NB>(R, valid, C, rho_e, seed, (int)threadIdx.x, BlockSync());
 }
 
 // Newton rounds over the staged nodes; returns true when some node had not converged after
-// max_it updates (block-uniform).  On return R.t and R.it hold every slot's result.
-template <int NB>
-__device__ __forceinline__ bool rounds(Rounds<NB>& R, int max_it, double tol) {
-  const int tid = threadIdx.x;
+// max_it updates (uniform over the group).  On return R.t and R.it hold every slot's result.
+template <int NB, class Sync>
+__device__ __forceinline__ bool rounds(Rounds<NB>& R, int max_it, double tol, int tid, Sync sync) {
   int m = R.count[0];
   for (int r = 0; m > 0 && r < max_it; ++r) {
     bool again = false;
@@ -171,10 +186,14 @@ __device__ __forceinline__ bool rounds(Rounds<NB>& R, int max_it, double tol) {
     }
     if (tid == 0) R.count[(r + 2) % 3] = 0;  // the list before last: nobody reads its count again
     append(R.list[(r + 1) & 1], &R.count[(r + 1) % 3], again, slot);
-    __syncthreads();
+    sync();
     m = R.count[(r + 1) % 3];
   }
   return m > 0;
+}
+template <int NB>
+__device__ __forceinline__ bool rounds(Rounds<NB>& R, int max_it, double tol) {
+  return rounds<NB>(R, max_it, tol, (int)threadIdx.x, BlockSync());
 }
 
 // The mixed-precision form's node record from the converged temperature t: the float state,
