@@ -115,9 +115,9 @@ typedef struct {
  *   DG_BC_INFLOW      q+ = the state set by dg_mesh_set_inflow (supersonic inflow);
  *   DG_BC_OUTFLOW     q+ = q- (supersonic outflow).
  * BR1 exterior values are w(q+); away from walls the viscous exterior flux is the interior one.
- * Meshes with boundary faces run with a perfect gas (Euler or Navier-Stokes) in the FP64 and
- * the mixed-precision forms (there as ghost node records); the mixture and the batched form
- * reject them (DG_ERR_UNSUPPORTED).
+ * Meshes with boundary faces run with a perfect gas (Euler or Navier-Stokes) in the FP64, the
+ * mixed-precision and the batched forms (the last two with ghost node records); the mixture
+ * rejects them (DG_ERR_UNSUPPORTED).
  * In the vmapP of dg_mesh_connectivity a boundary face node holds -code. */
 #define DG_BC_SLIP_WALL 1
 #define DG_BC_NOSLIP_WALL 2
@@ -473,8 +473,9 @@ int dg_rk_stage_noalloc(const dg_mesh_tables* tables, const dg_gas_desc* gas, in
                         void* stream);
 
 /* ---- batched form: many uneven cases, one graph launch per RK4 step --------------------
- * Cases of orders 1..4, Euler or Navier-Stokes (perfect gas), any sizes, advanced
- * together in the mixed-precision form (DG_PREC_MIXED).  Cases are grouped by
+ * Cases of orders 1..4, Euler or Navier-Stokes (perfect gas), any sizes, periodic or with
+ * boundary faces (the inflow state set where a mesh has inflow faces), advanced together in the
+ * mixed-precision form (DG_PREC_MIXED).  Cases are grouped by
  * (order, physics); each group's kernels are persistent over a device work list of
  * (case, element tile) items, so a stage costs one launch per group and pass, and
  * a whole RK4 step (5 stages, then each case's result copied back into its state)

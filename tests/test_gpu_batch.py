@@ -101,3 +101,59 @@ def test_full_batched_workload_equals_single_case_stages():
     assert batch.status() == 0
     for (mesh, gas, dt, q), qr in zip(hs, refs):
         assert float((q - qr).abs().max()) <= 1e-12 * float(qr.abs().max())
+
+
+def test_batch_with_boundary_faces_equals_single_case_stages():
+    """Cases with slip and no-slip walls and inflow / outflow faces (ghost node records) in one
+    batch with a periodic case: each equals its single-case mixed stages."""
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import capi, dg
+    from tests.test_gpu_boundary import Q_IN, SIDES, _smooth
+    from tests._oracle_case import bc_disc
+    from workloads import equispaced_tet_nodes
+    specs = [((3, 3, 2), 2, "noslip_y_slip_z", 2e-2), ((3, 3, 2), 3, "in_out_x_walls_y", 0.0),
+             ((3, 3, 2), 3, "slip_y", 2e-2), ((3, 3, 2), 2, None, 0.0)]
+    hs, q0s = [], []
+    for n, N, sides, mu in specs:
+        if sides is None:
+            from workloads import box_mesh
+            v, per = box_mesh(n, 1.0)
+            mesh = dg.Mesh(v, per, N, equispaced_tet_nodes(N))
+            xyz = Disc(v, per, N).xyz
+        else:
+            d = bc_disc(n, N, SIDES[sides])
+            mesh = dg.Mesh(d.vertices, d.period, N, equispaced_tet_nodes(N), face_bc=d.face_bc)
+            if "in_out" in sides:
+                mesh.set_inflow(Q_IN)
+            xyz = d.xyz
+        gas = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=mu, Pr=0.71)
+        q0 = _smooth(xyz, seed=len(hs))
+        q0s.append(q0)
+        hs.append((mesh, gas, 1e-3, torch.tensor(q0, device="cuda")))
+    batch = dg.Batch(hs, autotune=False)
+    opts = dg._opts(precision=capi.DG_PREC_MIXED)
+    refs = []
+    for (mesh, gas, dt, _), q0 in zip(hs, q0s):
+        qr = torch.tensor(q0, device="cuda")
+        dg.lsrk4_step(mesh, gas, qr, dt, steps=2, opts=opts)
+        refs.append(qr)
+    batch.step(2)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for (mesh, gas, dt, q), qr in zip(hs, refs):
+        assert mesh.status() == 0
+        assert float((q - qr).abs().max()) <= 1e-12 * float(qr.abs().max())
+
+
+def test_batch_needs_the_inflow_state():
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import capi, dg
+    from tests.test_gpu_boundary import SIDES, _smooth
+    from tests._oracle_case import bc_disc
+    from workloads import equispaced_tet_nodes
+    d = bc_disc((3, 3, 2), 2, SIDES["in_out_x_walls_y"])
+    mesh = dg.Mesh(d.vertices, d.period, 2, equispaced_tet_nodes(2), face_bc=d.face_bc)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    with pytest.raises(capi.DGError) as e:
+        dg.Batch([(mesh, gas, 1e-3, torch.tensor(_smooth(d.xyz), device="cuda"))], autotune=False)
+    assert e.value.code == capi.DG_ERR_INVALID_ARG
