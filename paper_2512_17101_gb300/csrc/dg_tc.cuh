@@ -60,6 +60,12 @@ __host__ __device__ constexpr int aim_blocks(int smem, int nt, int min_regs = 64
   return r < 1 ? 1 : r;
 }
 
+// Whether a tile layout ending at `end_vm` bytes (with the staged neighbour map) keeps as many
+// resident blocks per SM as the one ending at `end` (without it).
+__host__ __device__ constexpr bool vm_fits(int end, int end_vm, int nt, int min_regs) {
+  return aim_blocks(end_vm + 24, nt, min_regs) >= aim_blocks(end + 24, nt, min_regs);
+}
+
 // Columns of a surface chunk.  At N = 3 the 40 face nodes of an element go into one chunk of
 // 48 columns instead of chunks of 32 and 8: one MMA round trip and one gather pass less per
 // tile, for a wider operand slot that still leaves the resident blocks per SM unchanged.  In the
@@ -96,9 +102,23 @@ struct Cfg {
   static constexpr uint32_t IDESC = idesc_bf16(ROWS, NPAD);
   // shared-memory layout (bytes)
   static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
-  static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
-  static constexpr int SMEM = OFF_BAR + 16;
-  static constexpr int MINB = aim_blocks(SMEM, NT, V > 5 ? 96 : 64);  // a mixture node holds 3 x 13 fluxes
+  static constexpr int OFF_FM = OFF_GEO + E * GS * 4;
+  // registers a thread gets at least: a node's three 5-variable fluxes stay live over three MMA
+  // rounds (about 110 registers without spilling, which would go to L2: the L1 left beside this
+  // much shared memory is small); a mixture node holds 3 x 13 fluxes.  Tiles of more than 256
+  // threads (N = 4) keep two blocks per SM instead.
+  static constexpr int MIN_REGS = V > 5 ? 96 : (NT <= 256 ? 96 : 64);
+  // the tile's neighbour map, staged in shared memory where that costs no resident block
+  static constexpr int OFF_VM = (OFF_FM + NF * 4 + 15) / 16 * 16, VM_BYTES = E * NF * 4;
+  static constexpr bool VM = vm_fits(OFF_FM + NF * 4, OFF_VM + VM_BYTES, NT, MIN_REGS);
+  static constexpr int END_VM = VM ? OFF_VM + VM_BYTES : OFF_FM + NF * 4;
+  // perfect gas: the tile's own node records, viscous-flux records and Q_z values, staged one
+  // tile ahead (where that costs no resident block): [E Np] x 2 float4, [E Np] x 2 float4, [E Np]
+  static constexpr int OFF_ST = (END_VM + 15) / 16 * 16, ST_BYTES = E * Np * 64 + (E * Np * 4 + 15) / 16 * 16;
+  static constexpr bool STAGE = V == 5 && VM && vm_fits(END_VM, OFF_ST + ST_BYTES, NT, MIN_REGS);
+  static constexpr int OFF_BAR = ((STAGE ? OFF_ST + ST_BYTES : END_VM) + 7) / 8 * 8;
+  static constexpr int SMEM = OFF_BAR + 24;
+  static constexpr int MINB = aim_blocks(SMEM, NT, MIN_REGS);
   static_assert(ROWS * CS * 4 <= 3 * A_TERM, "the accumulator copy must fit in the operand slot");
   static_assert(ROWS * CS % 4 == 0, "the accumulator copy is cleared in 16 B words");
   static_assert(NPAD <= TMEM_COLS, "TMEM columns");
@@ -130,7 +150,13 @@ struct Smem {
   float* C;  // accumulator copy, aliases the operand slot once the tile's MMAs are done
   float* geo;
   int* fm;
-  uint64_t* bar;
+  int* vm;  // the tile's neighbour map [E][NF] (only when C_::VM)
+  // staged node records of the tile (only when C_::STAGE)
+  float4* st_node;
+  float4* st_fv4;
+  float* st_fvz;
+  uint64_t* bar;     // MMA completion
+  uint64_t* st_bar;  // staging copies
   uint32_t* tmem;
   int* abort;
   __device__ explicit Smem(unsigned char* raw) {
@@ -139,9 +165,14 @@ struct Smem {
     C = reinterpret_cast<float*>(A);
     geo = reinterpret_cast<float*>(raw + C_::OFF_GEO);
     fm = reinterpret_cast<int*>(raw + C_::OFF_FM);
+    vm = reinterpret_cast<int*>(raw + C_::OFF_VM);
+    st_node = reinterpret_cast<float4*>(raw + C_::OFF_ST);
+    st_fv4 = st_node + 2 * C_::E * C_::Np;
+    st_fvz = reinterpret_cast<float*>(st_fv4 + 2 * C_::E * C_::Np);
     bar = reinterpret_cast<uint64_t*>(raw + C_::OFF_BAR);
     tmem = reinterpret_cast<uint32_t*>(raw + C_::OFF_BAR + 8);
     abort = reinterpret_cast<int*>(raw + C_::OFF_BAR + 12);
+    st_bar = reinterpret_cast<uint64_t*>(raw + C_::OFF_BAR + 16);
   }
 };
 
@@ -158,6 +189,7 @@ __device__ __forceinline__ void block_setup(const Smem<C_>& S, const uint4* __re
   for (int i = tid; i < C_::NF; i += blockDim.x) S.fm[i] = fmask_g[i];
   if (tid == 0) {
     mbar_init(smem_u32(S.bar), 1);
+    if (C_::STAGE) mbar_init(smem_u32(S.st_bar), 1);
     *S.abort = 0;
   }
   if (tid < 32) tmem_alloc(smem_u32(S.tmem), C_::TMEM_COLS);
@@ -167,12 +199,22 @@ __device__ __forceinline__ void block_setup(const Smem<C_>& S, const uint4* __re
   tc_fence_after();
 }
 
+// Per-block pipeline state: MMA and staging mbarrier parities, and whether a staging copy has
+// been issued and not yet waited for.
+struct Pipe {
+  uint32_t phase = 0, sphase = 0;
+  bool staged = false;
+};
+
 template <class C_>
-__device__ __forceinline__ void block_teardown(const Smem<C_>& S, uint32_t phase) {
+__device__ __forceinline__ void block_teardown(const Smem<C_>& S, const Pipe& p) {
   // after an abort the MMA group whose wait timed out (parity phase ^ 1) may still be in
   // flight: give it one more wait, with the full bound, before the accumulator is released.
   // The decision is a block-wide OR: a thread whose last wait ran out has set the flag itself.
-  if (__syncthreads_or(*S.abort) && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), phase ^ 1u);
+  // Staging copies still in flight are waited for before the block's shared memory is released.
+  if (C_::STAGE) cp_async_wait_all();
+  if (__syncthreads_or(*S.abort) && threadIdx.x == 0) mbar_wait(smem_u32(S.bar), p.phase ^ 1u);
+  if (C_::STAGE && p.staged && threadIdx.x == 0) mbar_wait(smem_u32(S.st_bar), p.sphase);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -208,9 +250,14 @@ __device__ __forceinline__ void issue_chunk(const Smem<C_>& S, int c) {
 // The stop decision is a block-wide OR of the flag as each thread sees it on arrival: a thread whose
 // wait ran out wrote the flag before arriving, so every thread gets the same answer even when
 // another thread reads the flag before that write.  `polls` bounds each wait (0: the default).
-template <class C_>
+// `during()` runs between the issue and the wait (loads that overlap the MMAs).
+struct Nothing {
+  __device__ void operator()() const {}
+};
+
+template <class C_, class During = Nothing>
 __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& phase, unsigned* status,
-                                          int polls = 0) {
+                                          int polls = 0, const During& during = During()) {
   fence_async_smem();
   tc_fence_before();
   if (__syncthreads_or(*S.abort)) return false;
@@ -218,6 +265,7 @@ __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& ph
     tc_fence_after();
     issue_chunk<C_>(S, c);
   }
+  during();
   if (!mbar_wait(smem_u32(S.bar), phase, polls > 0 ? polls : kWaitPolls)) {
     *S.abort = 1;
     atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
@@ -225,6 +273,47 @@ __device__ __forceinline__ bool run_chunk(const Smem<C_>& S, int c, uint32_t& ph
   phase ^= 1u;
   tc_fence_after();
   return true;
+}
+
+// A tile's geometric factors and (C_::VM) neighbour map into shared memory by asynchronous
+// copies, whose latency overlaps the node loads issued after them; the caller completes them
+// (cp_async_wait_all) before the barrier that publishes them.
+template <class C_>
+__device__ __forceinline__ void stage_tile_tables(const Smem<C_>& S, const MixedCase& c, int e0, int nel) {
+  static_assert(C_::NF % 4 == 0, "whole 16 B rows of the neighbour map (NF = 4 Nfp, row starts 16 B aligned)");
+  const float* gs = c.geo + (size_t)e0 * GS;
+  for (int i = threadIdx.x; i < nel * GS; i += C_::NT) cp_async4(S.geo + i, gs + i);
+  if constexpr (C_::VM) {
+    const int4* vs = reinterpret_cast<const int4*>(c.vmapP + (size_t)e0 * C_::NF);
+    int4* vd = reinterpret_cast<int4*>(S.vm);
+    for (int i = threadIdx.x; i < nel * (C_::NF / 4); i += C_::NT) cp_async16(vd + i, vs + i);
+  }
+}
+
+// Issue the staging copies of tile [e0, e0 + 25) of case c (C_::STAGE): node records and, for
+// Navier-Stokes, viscous-flux records by the TMA engine (thread 0; completion on st_bar), the Q_z
+// values, geometric factors and neighbour map by per-thread asynchronous copies (each thread's
+// cp_async_wait_all; thread t copies the Q_z values of the nodes it reads in the flux phase).
+template <class C_, bool NS>
+__device__ __forceinline__ void stage_issue(const Smem<C_>& S, const MixedCase& c, int e0) {
+  const int nel = min(C_::E, c.K - e0), nn = nel * C_::Np;
+  const size_t base = (size_t)e0 * C_::Np;
+  if (threadIdx.x == 0) {
+    const uint32_t bar = smem_u32(S.st_bar);
+    mbar_expect_tx(bar, (uint32_t)nn * (NS ? 64u : 32u));
+    bulk_g2s(S.st_node, c.node + 2 * base, (uint32_t)nn * 32u, bar);
+    if (NS) bulk_g2s(S.st_fv4, c.fv4 + 2 * base, (uint32_t)nn * 32u, bar);
+  }
+  if (NS)
+    for (int i = threadIdx.x; i < nn; i += C_::NT) cp_async4(S.st_fvz + i, c.fvz + base + i);
+  stage_tile_tables<C_>(S, c, e0, nel);
+}
+
+// Neighbour-map entry of face node mm of tile element e: from the staged copy where there is one.
+template <class C_>
+__device__ __forceinline__ int tile_vmap(const Smem<C_>& S, const MixedCase& c, int e0, int e, int mm) {
+  if constexpr (C_::VM) return S.vm[e * C_::NF + mm];
+  return c.vmapP[(size_t)(e0 + e) * C_::NF + mm];
 }
 
 // Elements [e0, e0 + 25) of case c: right-hand side (RK = false: out = rhs) or the LSRK stage
@@ -241,9 +330,10 @@ __device__ __forceinline__ float load_mix_record(const float4* r, float* q) {
 template <class C_, int PHYS, bool RK>
 __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, const double* __restrict__ qin,
                                          double* __restrict__ out, const int e0, const double a, const double b,
-                                         uint32_t& phase, unsigned* status, const MixedCase* next, int next_e0) {
+                                         Pipe& p, unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT, V = C_::V;
   constexpr bool NS = PHYS == kern::NAVIER_STOKES, MIX = PHYS == kern::MIXTURE;
+  constexpr bool ST = C_::STAGE && !MIX;  // own records staged in shared memory
   static_assert(MIX ? V == mixk::MIX_V : V == 5, "5 conserved variables, or the 13 of a mixture record");
   const int tid = threadIdx.x;
   const int nvar = MIX ? c.nvar : 5;
@@ -264,7 +354,23 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       prefetch_tile_inputs(*next, next_e0, nnel, Np, NF, MIX, NS);
     }
   }
-  for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
+  if constexpr (ST) {
+    // this tile's staged records, copied during the previous tile (or the block set-up)
+    cp_async_wait_all();
+    if (mbar_wait(smem_u32(S.st_bar), p.sphase, c.wait_polls > 0 ? c.wait_polls : kWaitPolls)) {
+      p.sphase ^= 1u;
+      p.staged = false;
+    } else {  // the tile is abandoned at the first MMA round (block-wide OR of the flag)
+      *S.abort = 1;
+      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+    }
+  } else {
+    stage_tile_tables<C_>(S, c, e0, nel);
+  }
+  // the tile's own node records (tile-local node index), staged or in global memory
+  const float4* ND = ST ? S.st_node : c.node + 2 * base;
+  const float4* FV4 = ST ? S.st_fv4 : c.fv4 + 2 * base;
+  const float* FVZ = ST ? S.st_fvz : c.fvz + base;
 
   // volume fluxes of this thread's nodes (FP32; pressure relative to the element's first node in FP64)
   float F[NPT][3][V];
@@ -281,20 +387,22 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         const float p_lo = c.mrec[4 * gn + 1].z;
         mixk::node_flux_mix<V>(qv, nvar, (p1 - ref.y) + (p_lo - ref.z), p1, F[s]);
       } else {
-        const float4 a0 = c.node[2 * gn], a1 = c.node[2 * gn + 1], r1 = c.node[2 * g1 + 1];
+        const int l1 = e * Np;
+        const float4 a0 = ND[2 * n], a1 = ND[2 * n + 1], r1 = ND[2 * l1 + 1];
         const float qv[5] = {a0.x, a0.y, a0.z, a0.w, a1.x};
         float fv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         if constexpr (NS) {
-          const float4 f0 = c.fv4[2 * gn], f1 = c.fv4[2 * gn + 1];
+          const float4 f0 = FV4[2 * n], f1 = FV4[2 * n + 1];
           fv[0] = f0.x; fv[1] = f0.y; fv[2] = f0.z; fv[3] = f0.w;
           fv[4] = f1.x; fv[5] = f1.y; fv[6] = f1.z; fv[7] = f1.w;
-          fv[8] = c.fvz[gn];
+          fv[8] = FVZ[n];
         }
         // p - p_1 from the hi/lo pairs; p itself (energy flux) as its FP32 rounding
         mixk::node_flux<NS>(qv, (a1.y - r1.y) + (a1.z - r1.z), a1.y, fv, F[s]);
       }
     }
   }
+  cp_async_wait_all();
   __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
 
   // three volume chunks: contravariant flux sum_d (dr_a/dx_d) F_d at column i
@@ -313,7 +421,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
                     fmaf(gx, F[s][0][v], fmaf(gy, F[s][1][v], gz * F[s][2][v])));
       }
     }
-    if (!run_chunk<C_>(S, ra, phase, status, c.wait_polls)) return false;
+    if (!run_chunk<C_>(S, ra, p.phase, status, c.wait_polls)) return false;
   }
 
   // surface chunks: face nodes [sc KS, sc KS + KS) of every element
@@ -326,9 +434,12 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       const float* G = S.geo + e * GS;
       const float n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
       const float fs = G[12 + 4 * f];
-      const size_t own = base + (size_t)e * Np + S.fm[mm];
-      const int Pi = c.vmapP[(size_t)(e0 + e) * NF + mm];  // < 0: boundary face node, -DG_BC_* code
-      const size_t P = Pi >= 0 ? (size_t)Pi : own;          // a boundary node gathers its own record
+      const int ownl = e * Np + S.fm[mm];
+      const size_t own = base + ownl;
+      const int Pi = tile_vmap<C_>(S, c, e0, e, mm);  // < 0: boundary face node, -DG_BC_* code
+      const size_t P = Pi >= 0 ? (size_t)Pi : own;     // a boundary node gathers its own record
+      const size_t Pl = P - base;                      // tile-local index (wraps when P < base)
+      const bool Pin = ST && Pl < (size_t)nn;          // the neighbour's records are staged too
       float g[V];
       if constexpr (MIX) {
         float qm[V], qp[V];
@@ -339,18 +450,19 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         const float dlo[4] = {lm.x - lp.x, lm.y - lp.y, lm.z - lp.z, lm.w - lp.w};
         mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, dlo, g);
       } else {
-        const float4 m0r = c.node[2 * own], m1r = c.node[2 * own + 1];
-        float4 p0r = c.node[2 * P], p1r = c.node[2 * P + 1];
+        const float4 m0r = ND[2 * ownl], m1r = ND[2 * ownl + 1];
+        float4 p0r = Pin ? S.st_node[2 * Pl] : c.node[2 * P], p1r = Pin ? S.st_node[2 * Pl + 1] : c.node[2 * P + 1];
         if (Pi < 0) mixk::ghost_record(-Pi, n3, c, p0r, p1r);
         const float qm[5] = {m0r.x, m0r.y, m0r.z, m0r.w, m1r.x}, qp[5] = {p0r.x, p0r.y, p0r.z, p0r.w, p1r.x};
         const float dpn = (m1r.y - p1r.y) + (m1r.z - p1r.z);  // p- - p+ from the hi/lo pairs
         float fvm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, fvp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         if constexpr (NS) {
-          const float4 a = c.fv4[2 * own], b2 = c.fv4[2 * own + 1], cc4 = c.fv4[2 * P], d4 = c.fv4[2 * P + 1];
+          const float4 a = FV4[2 * ownl], b2 = FV4[2 * ownl + 1];
+          const float4 cc4 = Pin ? S.st_fv4[2 * Pl] : c.fv4[2 * P], d4 = Pin ? S.st_fv4[2 * Pl + 1] : c.fv4[2 * P + 1];
           fvm[0] = a.x; fvm[1] = a.y; fvm[2] = a.z; fvm[3] = a.w;
-          fvm[4] = b2.x; fvm[5] = b2.y; fvm[6] = b2.z; fvm[7] = b2.w; fvm[8] = c.fvz[own];
+          fvm[4] = b2.x; fvm[5] = b2.y; fvm[6] = b2.z; fvm[7] = b2.w; fvm[8] = FVZ[ownl];
           fvp[0] = cc4.x; fvp[1] = cc4.y; fvp[2] = cc4.z; fvp[3] = cc4.w;
-          fvp[4] = d4.x; fvp[5] = d4.y; fvp[6] = d4.z; fvp[7] = d4.w; fvp[8] = c.fvz[P];
+          fvp[4] = d4.x; fvp[5] = d4.y; fvp[6] = d4.z; fvp[7] = d4.w; fvp[8] = Pin ? S.st_fvz[Pl] : c.fvz[P];
           if (Pi < 0) mixk::ghost_viscous(-Pi, n3, fvp);
         }
         mixk::face_term<NS>(qm, qp, m1r.y, p1r.y, dpn, fvm, fvp, n3, gam, g);
@@ -359,8 +471,35 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       for (int v = 0; v < V; ++v)
         put3_umma(S.A, C_::A_TERM, umma_off(e * V + v, mm - m0, C_::A_LBO, C_::A_SBO), fs * g[v]);
     }
-    if (!run_chunk<C_>(S, 3 + sc, phase, status, c.wait_polls)) return false;
+    if (sc < C_::NSURF - 1) {
+      if (!run_chunk<C_>(S, 3 + sc, p.phase, status, c.wait_polls)) return false;
+    }
   }
+  // the last surface chunk; this thread's RK inputs are loaded while its MMAs run
+  double k_old[NPT][V], q_old[NPT][V];
+  const auto load_rk = [&] {
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int n = tid + s * NT;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const size_t gi = v * KNp + base + n;
+        k_old[s][v] = (RK && n < nn && v < nvar && a != 0.0) ? c.k[gi] : 0.0;
+        q_old[s][v] = (RK && n < nn && v < nvar) ? qin[gi] : 0.0;
+      }
+    }
+  };
+  // every thread is past its reads of the staged records: the next tile's copies start now
+  const auto during = [&] {
+    if constexpr (ST) {
+      if (next) {
+        stage_issue<C_, NS>(S, *next, next_e0);
+        p.staged = true;
+      }
+    }
+    load_rk();
+  };
+  if (!run_chunk<C_>(S, 3 + C_::NSURF - 1, p.phase, status, c.wait_polls, during)) return false;
 
   // accumulator -> shared memory (warps 0..3 own TMEM lanes 0..127), then the node-parallel update
   if (tid < 128) {
@@ -382,14 +521,6 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
     const int n = tid + s * NT;
     if (n < nn) {
       const int e = n / Np, i = n - e * Np;
-      // all of this node's RK inputs first, so that their loads overlap
-      double k_old[V], q_old[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const size_t gi = v * KNp + base + n;
-        k_old[v] = (RK && v < nvar && a != 0.0) ? c.k[gi] : 0.0;
-        q_old[v] = (RK && v < nvar) ? qin[gi] : 0.0;
-      }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         if (v < nvar) {
@@ -398,9 +529,9 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
           if (RK) {
             // dt rhs formed in FP32 (the right-hand side carries FP32-level error already) and
             // widened on the integer pipe; the accumulation is FP64
-            const double kk = fma(a, k_old[v], cvt::widen(dtf * r));
+            const double kk = fma(a, k_old[s][v], cvt::widen(dtf * r));
             c.k[gi] = kk;
-            out[gi] = fma(b, kk, q_old[v]);
+            out[gi] = fma(b, kk, q_old[s][v]);
           } else {
             out[gi] = cvt::widen(r);
           }
@@ -429,13 +560,19 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT, tile_v(PHYS)>::MINB)) rhs_tc_k
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
-  uint32_t phase = 0;
+  Pipe p;
+  if constexpr (C_::STAGE && PHYS != kern::MIXTURE) {
+    if (blockIdx.x * C_::E < c.K) {
+      stage_issue<C_, PHYS == kern::NAVIER_STOKES>(S, c, blockIdx.x * C_::E);
+      p.staged = true;
+    }
+  }
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
     const int ne0 = e0 + gridDim.x * C_::E;
-    if (!rhs_tile<C_, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, phase, status, ne0 < c.K ? &c : nullptr, ne0))
+    if (!rhs_tile<C_, PHYS, RK>(S, c, c.q[0], c.q[1], e0, a, b, p, status, ne0 < c.K ? &c : nullptr, ne0))
       break;
   }
-  block_teardown<C_>(S, phase);
+  block_teardown<C_>(S, p);
 }
 
 // A batch of cases: persistent over a work list of (case, first element) tiles; the stage's
@@ -451,17 +588,24 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const M
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
-  uint32_t phase = 0;
+  Pipe p;
+  if constexpr (C_::STAGE && PHYS != kern::MIXTURE) {
+    if (blockIdx.x < nwork) {
+      const int2 it = work[blockIdx.x];
+      stage_issue<C_, PHYS == kern::NAVIER_STOKES>(S, cases[it.x], it.y);
+      p.staged = true;
+    }
+  }
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
     const int wn = w + gridDim.x;
     const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
-    if (!rhs_tile<C_, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, phase, status,
+    if (!rhs_tile<C_, PHYS, true>(S, c, c.q[stage & 1], c.q[(stage & 1) ^ 1], it.y, a, b, p, status,
                                   wn < nwork ? &cases[nx.x] : nullptr, nx.y))
       break;
   }
-  block_teardown<C_>(S, phase);
+  block_teardown<C_>(S, p);
 }
 
 // ==== BR1 pass on the tensor cores ===============================================================
@@ -490,8 +634,13 @@ struct VCfg {
   static constexpr int NODES = E * Np, NPT = (NODES + NT - 1) / NT;
   static constexpr uint32_t IDESC = idesc_bf16(ROWS, NOUT);
   static constexpr int OFF_B = 0, OFF_A = 3 * B_TERM, OFF_GEO = OFF_A + 3 * A_TERM;
-  static constexpr int OFF_FM = OFF_GEO + E * GS * 4, OFF_BAR = (OFF_FM + NF * 4 + 7) / 8 * 8;
-  static constexpr int SMEM = OFF_BAR + 16;
+  static constexpr int OFF_FM = OFF_GEO + E * GS * 4;
+  static constexpr int OFF_VM = (OFF_FM + NF * 4 + 15) / 16 * 16, VM_BYTES = E * NF * 4;
+  static constexpr bool VM = vm_fits(OFF_FM + NF * 4, OFF_VM + VM_BYTES, NT, 64);
+  static constexpr int OFF_BAR = ((VM ? OFF_VM + VM_BYTES : OFF_FM + NF * 4) + 7) / 8 * 8;
+  static constexpr int OFF_ST = 0;
+  static constexpr bool STAGE = false;
+  static constexpr int SMEM = OFF_BAR + 24;
   static constexpr int MINB = aim_blocks(SMEM, NT);
   static_assert(NT % 32 == 0 && NT >= 128 && NT <= 1024, "whole warps, at least the four TMEM lane quarters");
   static_assert(NOUT <= 256 && NOUT % 16 == 0, "MMA N");
@@ -520,7 +669,7 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     prefetch_l2(next->geo + (size_t)next_e0 * GS, (size_t)nnel * GS * 4);
     prefetch_l2(next->vmapP + (size_t)next_e0 * NF, (size_t)nnel * NF * 4);
   }
-  for (int i = tid; i < nel * GS; i += NT) S.geo[i] = c.geo[(size_t)e0 * GS + i];
+  stage_tile_tables<C_>(S, c, e0, nel);
 
   // volume chunk: (rho - rho_1, m, T - T_1) per node; the differences to the element's first node
   // from the hi/lo pairs
@@ -545,6 +694,7 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       w_n[s][4] = (t.x - t1.x) + (t.y - t1.y);
     }
   }
+  cp_async_wait_all();
   __syncthreads();  // geometry in place; the previous tile's accumulator copy has been cleared
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
@@ -565,8 +715,8 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     for (int j = tid; j < nel * w; j += NT) {
       const int e = j / w, mm = m0 + (j - e * w);
       const size_t own = base + (size_t)e * Np + S.fm[mm];
-      const int Pi = c.vmapP[(size_t)(e0 + e) * NF + mm];  // < 0: boundary face node, -DG_BC_* code
-      const size_t P = Pi >= 0 ? (size_t)Pi : own;          // a boundary node gathers its own record
+      const int Pi = tile_vmap<C_>(S, c, e0, e, mm);  // < 0: boundary face node, -DG_BC_* code
+      const size_t P = Pi >= 0 ? (size_t)Pi : own;     // a boundary node gathers its own record
       const float4 o0 = c.node[2 * own], o1 = c.node[2 * own + 1];
       float4 q0 = c.node[2 * P], q1 = c.node[2 * P + 1];
       const float2 to = c.temp[own];
@@ -654,12 +804,12 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_kernel(const M
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
-  uint32_t phase = 0;
+  Pipe p;
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
     const int ne0 = e0 + gridDim.x * C_::E;
-    if (!vis_tile<C_>(S, c, e0, phase, status, ne0 < c.K ? &c : nullptr, ne0)) break;
+    if (!vis_tile<C_>(S, c, e0, p.phase, status, ne0 < c.K ? &c : nullptr, ne0)) break;
   }
-  block_teardown<C_>(S, phase);
+  block_teardown<C_>(S, p);
 }
 
 template <int N, int NT>
@@ -674,15 +824,15 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_batched(const 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
-  uint32_t phase = 0;
+  Pipe p;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
     const int wn = w + gridDim.x;
     const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
-    if (!vis_tile<C_>(S, c, it.y, phase, status, wn < nwork ? &cases[nx.x] : nullptr, nx.y)) break;
+    if (!vis_tile<C_>(S, c, it.y, p.phase, status, wn < nwork ? &cases[nx.x] : nullptr, nx.y)) break;
   }
-  block_teardown<C_>(S, phase);
+  block_teardown<C_>(S, p);
 }
 
 }  // namespace tc

@@ -126,6 +126,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* out) {
   for (int j = 0; j < 32; ++j) out[j] = __uint_as_float(r[j]);
 }
 
+// Expect `bytes` more of the transaction count on the mbarrier's current phase, with this thread's
+// arrival.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk copy of `bytes` from global to this block's shared memory by the TMA engine, counted on
+// the mbarrier's transaction count.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(smem)),
+               "l"(gmem), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Asynchronous global -> shared copies (no registers hold the data; cp_async_wait_all completes
+// this thread's copies).  Sizes 4 and 16 bytes; both addresses aligned to the size.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Bulk prefetch of [ptr, ptr + bytes) into L2 by the TMA engine, clamped inward to 16-byte
 // boundaries (cp.async.bulk.prefetch needs a 16-byte aligned start and size), so that it never
 // touches memory outside the range.
