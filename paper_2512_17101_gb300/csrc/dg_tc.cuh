@@ -155,6 +155,7 @@ struct Smem {
   float4* st_node;
   float4* st_fv4;
   float* st_fvz;
+  float2* st_temp;  // BR1 tile: the staged temperature pairs (after the node records)
   uint64_t* bar;     // MMA completion
   uint64_t* st_bar;  // staging copies
   uint32_t* tmem;
@@ -169,6 +170,7 @@ struct Smem {
     st_node = reinterpret_cast<float4*>(raw + C_::OFF_ST);
     st_fv4 = st_node + 2 * C_::E * C_::Np;
     st_fvz = reinterpret_cast<float*>(st_fv4 + 2 * C_::E * C_::Np);
+    st_temp = reinterpret_cast<float2*>(st_fv4);
     bar = reinterpret_cast<uint64_t*>(raw + C_::OFF_BAR);
     tmem = reinterpret_cast<uint32_t*>(raw + C_::OFF_BAR + 8);
     abort = reinterpret_cast<int*>(raw + C_::OFF_BAR + 12);
@@ -608,6 +610,20 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const M
   block_teardown<C_>(S, p);
 }
 
+// Issue the staging copies of BR1 tile [e0, e0 + 25) of case c (C_::STAGE): node records and
+// temperature pairs by the TMA engine (thread 0; completion on st_bar).
+template <class C_>
+__device__ __forceinline__ void stage_issue_vis(const Smem<C_>& S, const MixedCase& c, int e0) {
+  static_assert(C_::Np % 2 == 0, "16-byte aligned temperature runs");
+  if (threadIdx.x != 0) return;
+  const int nel = min(C_::E, c.K - e0), nn = nel * C_::Np;
+  const size_t base = (size_t)e0 * C_::Np;
+  const uint32_t bar = smem_u32(S.st_bar);
+  mbar_expect_tx(bar, (uint32_t)nn * 40u);
+  bulk_g2s(S.st_node, c.node + 2 * base, (uint32_t)nn * 32u, bar);
+  bulk_g2s(S.st_temp, c.temp + base, (uint32_t)nn * 8u, bar);
+}
+
 // ==== BR1 pass on the tensor cores ===============================================================
 // For affine tetrahedra the outward normal times Fscale of face f is a fixed combination of the
 // rows of dr/dx (Nanson's relation): n_f Fscale_f = sum_a c_{f,a} grad r_a with c = (0,0,-1),
@@ -637,9 +653,13 @@ struct VCfg {
   static constexpr int OFF_FM = OFF_GEO + E * GS * 4;
   static constexpr int OFF_VM = (OFF_FM + NF * 4 + 15) / 16 * 16, VM_BYTES = E * NF * 4;
   static constexpr bool VM = vm_fits(OFF_FM + NF * 4, OFF_VM + VM_BYTES, NT, 64);
-  static constexpr int OFF_BAR = ((VM ? OFF_VM + VM_BYTES : OFF_FM + NF * 4) + 7) / 8 * 8;
-  static constexpr int OFF_ST = 0;
-  static constexpr bool STAGE = false;
+  static constexpr int END_VM = VM ? OFF_VM + VM_BYTES : OFF_FM + NF * 4;
+  // the tile's own node records and temperature pairs, staged one tile ahead by bulk copies
+  // ([E Np] x 2 float4, [E Np] float2; tile starts and sizes are 16-byte multiples for even Np)
+  // where that costs no resident block
+  static constexpr int OFF_ST = (END_VM + 15) / 16 * 16, ST_BYTES = E * Np * 40;
+  static constexpr bool STAGE = VM && NSURF == 1 && Np % 2 == 0 && vm_fits(END_VM, OFF_ST + ST_BYTES, NT, 64);
+  static constexpr int OFF_BAR = ((STAGE ? OFF_ST + ST_BYTES : END_VM) + 7) / 8 * 8;
   static constexpr int SMEM = OFF_BAR + 24;
   static constexpr int MINB = aim_blocks(SMEM, NT);
   static_assert(NT % 32 == 0 && NT >= 128 && NT <= 1024, "whole warps, at least the four TMEM lane quarters");
@@ -651,9 +671,10 @@ struct VCfg {
 // Elements [e0, e0 + 25) of case c: the viscous-flux records from the node records (rho and T as
 // hi/lo pairs, momentum) and the temperature pairs.
 template <class C_>
-__device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const int e0, uint32_t& phase,
+__device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, const int e0, Pipe& p,
                                          unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT;
+  constexpr bool ST = C_::STAGE;
   const int tid = threadIdx.x;
   const int nel = min(C_::E, c.K - e0);
   const int nn = nel * Np;
@@ -669,7 +690,20 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     prefetch_l2(next->geo + (size_t)next_e0 * GS, (size_t)nnel * GS * 4);
     prefetch_l2(next->vmapP + (size_t)next_e0 * NF, (size_t)nnel * NF * 4);
   }
+  if constexpr (ST) {
+    // this tile's staged records, copied during the previous tile (or the block set-up)
+    if (mbar_wait(smem_u32(S.st_bar), p.sphase, c.wait_polls > 0 ? c.wait_polls : kWaitPolls)) {
+      p.sphase ^= 1u;
+      p.staged = false;
+    } else {  // the tile is abandoned at the first MMA round (block-wide OR of the flag)
+      *S.abort = 1;
+      atomicOr(status, (unsigned)DG_STATUS_TIMEOUT);
+    }
+  }
   stage_tile_tables<C_>(S, c, e0, nel);
+  // the tile's own node records and temperature pairs (tile-local node index)
+  const float4* ND = ST ? S.st_node : c.node + 2 * base;
+  const float2* TD = ST ? S.st_temp : c.temp + base;
 
   // volume chunk: (rho - rho_1, m, T - T_1) per node; the differences to the element's first node
   // from the hi/lo pairs
@@ -678,11 +712,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
   for (int s = 0; s < NPT; ++s) {
     const int n = tid + s * NT;
     if (n < nn) {
-      const int e = n / Np;
-      const size_t gn = base + n, g1 = base + (size_t)e * Np;
-      const float4 a0 = c.node[2 * gn], a1 = c.node[2 * gn + 1];
-      const float4 r0 = c.node[2 * g1], r1 = c.node[2 * g1 + 1];
-      const float2 t = c.temp[gn], t1 = c.temp[g1];
+      const int l1 = (n / Np) * Np;
+      const float4 a0 = ND[2 * n], a1 = ND[2 * n + 1];
+      const float4 r0 = ND[2 * l1], r1 = ND[2 * l1 + 1];
+      const float2 t = TD[n], t1 = TD[l1];
       rho_n[s] = a0.x;
       m_n[s][0] = a0.y;
       m_n[s][1] = a0.z;
@@ -706,7 +739,7 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, i, C_::A_LBO, C_::A_SBO), w_n[s][f]);
     }
   }
-  if (!run_chunk<C_>(S, 0, phase, status, c.wait_polls)) return false;
+  if (!run_chunk<C_>(S, 0, p.phase, status, c.wait_polls)) return false;
 
   // surface chunks: jumps w+ - w- at face nodes [sc KS, sc KS + KS)
 #pragma unroll 1
@@ -714,13 +747,16 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     const int m0 = sc * C_::KS, w = min(C_::KS, NF - m0);
     for (int j = tid; j < nel * w; j += NT) {
       const int e = j / w, mm = m0 + (j - e * w);
-      const size_t own = base + (size_t)e * Np + S.fm[mm];
-      const int Pi = tile_vmap<C_>(S, c, e0, e, mm);  // < 0: boundary face node, -DG_BC_* code
-      const size_t P = Pi >= 0 ? (size_t)Pi : own;     // a boundary node gathers its own record
-      const float4 o0 = c.node[2 * own], o1 = c.node[2 * own + 1];
-      float4 q0 = c.node[2 * P], q1 = c.node[2 * P + 1];
-      const float2 to = c.temp[own];
-      float2 tp = c.temp[P];
+      const int ownl = e * Np + S.fm[mm];
+      const int Pi = tile_vmap<C_>(S, c, e0, e, mm);    // < 0: boundary face node, -DG_BC_* code
+      const size_t P = Pi >= 0 ? (size_t)Pi : base + ownl;  // a boundary node gathers its own record
+      const size_t Pl = P - base;                           // tile-local index (wraps when P < base)
+      const bool Pin = ST && Pl < (size_t)nn;               // the neighbour's records are staged too
+      const float4 o0 = ND[2 * ownl], o1 = ND[2 * ownl + 1];
+      const float4* pn = Pin ? S.st_node + 2 * Pl : c.node + 2 * P;
+      float4 q0 = pn[0], q1 = pn[1];
+      const float2 to = TD[ownl];
+      float2 tp = Pin ? S.st_temp[Pl] : c.temp[P];
       if (Pi < 0) {  // exterior values w(q+) of the face's ghost state
         const int f = mm / C_::Nfp;
         const float* G = S.geo + e * GS;
@@ -734,7 +770,17 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       for (int f = 0; f < 5; ++f)
         put3_umma(S.A, C_::A_TERM, umma_off(e * 5 + f, mm - m0, C_::A_LBO, C_::A_SBO), jv[f]);
     }
-    if (!run_chunk<C_>(S, 1 + sc, phase, status, c.wait_polls)) return false;
+    // after the last gathers every thread is past its reads of the staged records: the next
+    // tile's copies start with the MMAs (the staged node records are not read again here)
+    const auto during = [&] {
+      if constexpr (ST) {
+        if (sc == C_::NSURF - 1 && next) {
+          stage_issue_vis<C_>(S, *next, next_e0);
+          p.staged = true;
+        }
+      }
+    };
+    if (!run_chunk<C_>(S, 1 + sc, p.phase, status, c.wait_polls, during)) return false;
   }
 
   // reference derivatives -> gradients, one reference direction at a time through shared memory
@@ -805,9 +851,15 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_kernel(const M
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   Pipe p;
+  if constexpr (C_::STAGE) {
+    if (blockIdx.x * C_::E < c.K) {
+      stage_issue_vis<C_>(S, c, blockIdx.x * C_::E);
+      p.staged = true;
+    }
+  }
   for (int e0 = blockIdx.x * C_::E; e0 < c.K; e0 += gridDim.x * C_::E) {
     const int ne0 = e0 + gridDim.x * C_::E;
-    if (!vis_tile<C_>(S, c, e0, p.phase, status, ne0 < c.K ? &c : nullptr, ne0)) break;
+    if (!vis_tile<C_>(S, c, e0, p, status, ne0 < c.K ? &c : nullptr, ne0)) break;
   }
   block_teardown<C_>(S, p);
 }
@@ -825,12 +877,19 @@ __global__ void __launch_bounds__(NT, (VCfg<N, NT>::MINB)) vis_tc_batched(const 
   const Smem<C_> S(smem_raw);
   block_setup<C_>(S, b_g, fmask_g);
   Pipe p;
+  if constexpr (C_::STAGE) {
+    if (blockIdx.x < nwork) {
+      const int2 it = work[blockIdx.x];
+      stage_issue_vis<C_>(S, cases[it.x], it.y);
+      p.staged = true;
+    }
+  }
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const MixedCase& c = cases[it.x];
     const int wn = w + gridDim.x;
     const int2 nx = wn < nwork ? work[wn] : make_int2(0, 0);
-    if (!vis_tile<C_>(S, c, it.y, p.phase, status, wn < nwork ? &cases[nx.x] : nullptr, nx.y)) break;
+    if (!vis_tile<C_>(S, c, it.y, p, status, wn < nwork ? &cases[nx.x] : nullptr, nx.y)) break;
   }
   block_teardown<C_>(S, p);
 }
