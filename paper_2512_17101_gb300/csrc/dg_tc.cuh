@@ -107,8 +107,8 @@ struct Cfg {
   // rounds (about 110 registers without spilling, which would go to L2: the L1 left beside this
   // much shared memory is small); a mixture node holds 3 x 13 fluxes (128: four blocks of 128
   // threads per SM at N = 2, measured faster than five spilling ones and three of 160 registers).
-  // Tiles of more than 256 threads (N = 4) keep two blocks per SM instead.
-  static constexpr int MIN_REGS = V > 5 ? 128 : (NT <= 256 ? 96 : 64);
+  // Larger tiles (N = 4) keep two blocks per SM instead.
+  static constexpr int MIN_REGS = V > 5 ? (NT <= 192 ? 128 : 96) : (NT <= 256 ? 96 : 64);
   // the tile's neighbour map, staged in shared memory where that costs no resident block
   static constexpr int OFF_VM = (OFF_FM + NF * 4 + 15) / 16 * 16, VM_BYTES = E * NF * 4;
   static constexpr bool VM = vm_fits(OFF_FM + NF * 4, OFF_VM + VM_BYTES, NT, MIN_REGS);
