@@ -199,6 +199,21 @@ int dg_scatter_elements(const double* src_dev, int32_t V, int64_t K, int32_t Np,
  * address and layout ([9][K][Np]: tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, E_x, E_y, E_z),
  * valid while the mesh lives. */
 int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q_dev, void* stream);
+/* The pieces of a stage that a partition schedules around its halo exchanges (its interior
+ * elements first, while the exchange is in flight; the rest after it; Sec. 4.6.1), FP64 form,
+ * perfect gas, asynchronous on stream:
+ * dg_primitives: (1/rho, p, c) of q at the nodes of elements [elem_begin, elem_end) into the
+ * mesh's primitives buffer (DG_STATUS_NONPHYSICAL where rho <= 0 or p <= 0 there);
+ * dg_viscous_flux_range: the BR1 viscous flux of the elements [elem_begin, elem_end) into the
+ * mesh's buffer (the other elements' entries are left as they were), from the primitives already
+ * in the primitives buffer, which must hold those of q at these elements' nodes and at their face
+ * neighbours' nodes.  A stage then follows with dg_opts.viscous_given, prims_given and the element
+ * range.  Errors: as dg_viscous_flux (dg_primitives: a perfect gas), and DG_ERR_INVALID_ARG
+ * unless 0 <= elem_begin <= elem_end <= K. */
+int dg_primitives(dg_mesh mesh, dg_gas gas, const double* q_dev, int32_t elem_begin, int32_t elem_end,
+                  void* stream);
+int dg_viscous_flux_range(dg_mesh mesh, dg_gas gas, const double* q_dev, int32_t elem_begin, int32_t elem_end,
+                          void* stream);
 int dg_mesh_viscous_buffer(dg_mesh mesh, double** fv_dev);
 
 /* ---- global reductions: conservation integrals and the stability rate -------------------------
@@ -323,7 +338,23 @@ typedef struct {
                           /* bound.  A test aid: a small value makes the waits run    */
                           /* out, which the kernels report as DG_STATUS_TIMEOUT (the  */
                           /* output is then incomplete) and return without hanging    */
-  int32_t reserved[6];
+  int32_t elem_range;     /* FP64 form, perfect gas, no artificial viscosity: != 0    */
+  int32_t elem_begin;     /* evaluates the right-hand side / stage of the elements    */
+  int32_t elem_end;       /* [elem_begin, elem_end) only (0 <= elem_begin <= elem_end */
+                          /* <= K; an empty range does nothing); the other elements'  */
+                          /* outputs (and RK register) are left as they were.  The    */
+                          /* primitives of every node (and,                           */
+                          /* without viscous_given, the viscous flux of every         */
+                          /* element) are still computed, unless prims_given.  A      */
+                          /* partition evaluates its interior elements while a halo   */
+                          /* exchange is in flight and the rest after it (parts run   */
+                          /* as soon as their inputs are there, Sec. 4.6.1).  Other   */
+                          /* forms: DG_ERR_UNSUPPORTED                                */
+  int32_t prims_given;    /* FP64 form, perfect gas: != 0 skips the primitives pass:  */
+                          /* the mesh's primitives buffer already holds those of q    */
+                          /* at every node the call reads (dg_primitives).  Other     */
+                          /* forms: DG_ERR_UNSUPPORTED                                */
+  int32_t reserved[2];
 } dg_opts;                /* NULL = defaults: DG_PREC_FP64, DG_TSEED_INPUT          */
 
 /* ---- the hot path ------------------------------------------------------------ */

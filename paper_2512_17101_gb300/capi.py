@@ -85,7 +85,8 @@ class dg_batch_case(ctypes.Structure):
 
 class dg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("t_seed", c_int32), ("t_const", c_double), ("viscous_given", c_int32),
-                ("wait_polls", c_int32), ("reserved", c_int32 * 6)]
+                ("wait_polls", c_int32), ("elem_range", c_int32), ("elem_begin", c_int32),
+                ("elem_end", c_int32), ("prims_given", c_int32), ("reserved", c_int32 * 2)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/dg.h
@@ -109,6 +110,8 @@ SIGNATURES = {
     "dg_scatter_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,
                                       c_void_p]),
     "dg_viscous_flux": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_viscous_flux_range": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+    "dg_primitives": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
     "dg_integrals": (c_int32, [c_void_p, c_void_p, c_int32, ctypes.c_int64, c_void_p, c_void_p]),
     "dg_max_rate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
     "dg_mesh_viscous_buffer": (c_int32, [c_void_p, ctypes.POINTER(c_void_p)]),

@@ -145,6 +145,19 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const dg::GasParams& g = gas->p;
   const int V = 5 + g.ns;
   const bool av = m.av.eps0 > 0;
+  // an element range: the FP64 form of a perfect gas without artificial viscosity only
+  dg::ElemRange range;
+  if (opts && opts->elem_range) {
+    if (opts->elem_begin < 0 || opts->elem_end < opts->elem_begin || opts->elem_end > m.K)
+      return fail(DG_ERR_INVALID_ARG, "need 0 <= elem_begin <= elem_end <= K");
+    if (opts->precision != DG_PREC_FP64 || g.model != DG_GAS_PERFECT || av)
+      return fail(DG_ERR_UNSUPPORTED, "element ranges are for the FP64 form of a perfect gas without AV");
+    range.begin = opts->elem_begin;
+    range.end = opts->elem_end;
+  }
+  const bool prims_given = opts && opts->prims_given;
+  if (prims_given && (opts->precision != DG_PREC_FP64 || g.model != DG_GAS_PERFECT))
+    return fail(DG_ERR_UNSUPPORTED, "prims_given is for the FP64 form of a perfect gas");
   if (av) {
     if (opts && opts->precision == DG_PREC_MIXED)
       return fail(DG_ERR_UNSUPPORTED, "artificial viscosity runs in the FP64 form only");
@@ -223,11 +236,12 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
-  if (g.model == DG_GAS_PERFECT) {  // (1/rho, p, c) once per node for the viscous and right-hand-side kernels
+  if (g.model == DG_GAS_PERFECT && !prims_given) {  // (1/rho, p, c) once per node for the next kernels
     e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_fp64(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "primitives kernel");
   }
   if (g.mu > 0 && !(opts && opts->viscous_given)) {
+    // the whole mesh: the range's right-hand side reads its neighbours' viscous flux
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
   }
@@ -241,7 +255,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
-  e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs(m, g, q, out, k, T, rk, a, b, dt, s); });
+  e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs(m, g, q, out, k, T, rk, a, b, dt, s, range); });
   if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
   return DG_OK;
 }
@@ -468,11 +482,40 @@ int dg_av_viscosity(dg_mesh mesh, const double* q, double* eps, void* stream) {
   return e == cudaSuccess ? DG_OK : cuda_fail(e, "smoothness-indicator kernel");
 }
 
-int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q, void* stream) {
+namespace {
+// Arguments shared by the ranged FP64 perfect-gas entry points.
+int check_range_call(dg_mesh mesh, dg_gas gas, const double* q, int32_t b, int32_t e, bool viscous) {
   if (!mesh || !gas || !q) return fail(DG_ERR_INVALID_ARG, "NULL mesh, gas or state");
   if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
-  if (gas->p.model != DG_GAS_PERFECT || !(gas->p.mu > 0))
-    return fail(DG_ERR_INVALID_ARG, "the viscous pass needs a viscous perfect gas");
+  if (gas->p.model != DG_GAS_PERFECT || (viscous && !(gas->p.mu > 0)))
+    return fail(DG_ERR_INVALID_ARG, viscous ? "the viscous pass needs a viscous perfect gas"
+                                            : "the primitives pass needs a perfect gas");
+  if (b < 0 || e < b || e > mesh->d.K) return fail(DG_ERR_INVALID_ARG, "need 0 <= elem_begin <= elem_end <= K");
+  return DG_OK;
+}
+}  // namespace
+
+int dg_primitives(dg_mesh mesh, dg_gas gas, const double* q, int32_t elem_begin, int32_t elem_end, void* stream) {
+  if (int rc = check_range_call(mesh, gas, q, elem_begin, elem_end, false)) return rc;
+  dg::ElemRange r;
+  r.begin = elem_begin;
+  r.end = elem_end;
+  const cudaError_t e = dg::launch_prims_fp64(mesh->d, gas->p, q, (cudaStream_t)stream, r);
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "primitives kernel");
+}
+
+int dg_viscous_flux_range(dg_mesh mesh, dg_gas gas, const double* q, int32_t elem_begin, int32_t elem_end,
+                          void* stream) {
+  if (int rc = check_range_call(mesh, gas, q, elem_begin, elem_end, true)) return rc;
+  dg::ElemRange r;
+  r.begin = elem_begin;
+  r.end = elem_end;
+  const cudaError_t e = dg::launch_viscous_flux(mesh->d, gas->p, q, (cudaStream_t)stream, r);
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "viscous flux kernel");
+}
+
+int dg_viscous_flux(dg_mesh mesh, dg_gas gas, const double* q, void* stream) {
+  if (int rc = check_range_call(mesh, gas, q, 0, mesh ? mesh->d.K : 0, true)) return rc;
   cudaError_t e = dg::launch_prims_fp64(mesh->d, gas->p, q, (cudaStream_t)stream);
   if (e == cudaSuccess) e = dg::launch_viscous_flux(mesh->d, gas->p, q, (cudaStream_t)stream);
   return e == cudaSuccess ? DG_OK : cuda_fail(e, "viscous flux kernels");

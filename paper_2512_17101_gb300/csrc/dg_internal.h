@@ -132,11 +132,17 @@ extern const double kRK4A[5];
 extern const double kRK4B[5];
 
 // ---- kernel launchers (kernels_dg.cu, kernels_thermo.cu) ------------------------
+// Elements [begin, end) of a launch; end < 0: to the mesh's last element.
+struct ElemRange {
+  int begin = 0, end = -1;
+};
 // Right-hand side (rk == false: out = rhs) or fused RK stage (rk == true:
 // k <- a k + dt rhs, out = q + b k).  T (may be null for a perfect gas) holds
-// the node temperatures of a mixture.
+// the node temperatures of a mixture.  r: the elements evaluated (perfect gas; a mixture
+// is always evaluated whole).
 cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
-                       const double* T, bool rk, double a, double b, double dt, cudaStream_t s);
+                       const double* T, bool rk, double a, double b, double dt, cudaStream_t s,
+                       ElemRange r = ElemRange());
 // Artificial viscosity (k_av.cu): element viscosities of q into eps [K]; the flux eps grad q into
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
 cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
@@ -160,11 +166,13 @@ cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q,
                           double a, double b, double dt, cudaStream_t s, int wait_polls = 0);
 cudaError_t launch_viscous_tc(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s,
                               int wait_polls = 0);
-// BR1 pass 1: viscous flux of a perfect gas into m.scratch.
-cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+// BR1 pass 1: viscous flux of a perfect gas into m.scratch, for the elements r.
+cudaError_t launch_viscous_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s,
+                                ElemRange r = ElemRange());
 // Per-node (1/rho, p, c) of a perfect-gas state into m.prim (k_ns.cu); the FP64 viscous and
 // right-hand-side kernels of the perfect gas read them.
-cudaError_t launch_prims_fp64(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t launch_prims_fp64(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s,
+                              ElemRange r = ElemRange());
 // Global reductions (k_diag.cu): a fixed grid of kDiagBlocks blocks writes per-block partials
 // into MeshDev::diag, one block combines them in a fixed order.
 constexpr int kDiagBlocks = 512, kDiagThreads = 256, kDiagMaxV = 5 + DG_MAX_SPECIES;

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
     const double* __restrict__ geo_g, const int32_t* __restrict__ vmapP, const double* __restrict__ fv_g,
     const double* __restrict__ av_g, const double* __restrict__ av_eps, unsigned* __restrict__ status,
     const GasParams gp, const BcParams bc, const int K, const int nvar, const double a, const double b,
-    const double dt) {
+    const double dt, const int kb, const int ke) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   extern __shared__ double smem[];
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
   int* sFm = reinterpret_cast<int*>(sT + (is_mix(PHYS) ? NODES : 0));
 
   const int tid = threadIdx.x;
-  const int e0 = blockIdx.x * EPB;
-  const int nel = min(EPB, K - e0);
+  const int e0 = kb + blockIdx.x * EPB;  // the launch covers elements [kb, ke) of the K
+  const int nel = min(EPB, ke - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
     const double* __restrict__ q, double* __restrict__ fv_out, const double* __restrict__ prim,
     const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g,
     const int32_t* __restrict__ vmapP, unsigned* __restrict__ status, const GasParams gp, const BcParams bc,
-    const int K) {
+    const int K, const int kb, const int ke) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   constexpr int W = 5;
@@ -436,8 +436,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_kernel(
   int* sFm = reinterpret_cast<int*>(sJ + W * EPB * NF);
 
   const int tid = threadIdx.x;
-  const int e0 = blockIdx.x * EPB;
-  const int nel = min(EPB, K - e0);
+  const int e0 = kb + blockIdx.x * EPB;  // the launch covers elements [kb, ke) of the K
+  const int nel = min(EPB, ke - e0);
   const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
   const size_t base = (size_t)e0 * Np;
@@ -589,7 +589,8 @@ constexpr size_t viscous_smem() {
 
 template <int N, int V, int PHYS, bool RK>
 cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
-                         const double* T, int nvar, double a, double b, double dt, cudaStream_t s) {
+                         const double* T, int nvar, double a, double b, double dt, cudaStream_t s,
+                         ElemRange r = ElemRange()) {
   using O = Ord<N>;
   constexpr size_t smem = rhs_smem<N, V, PHYS>();
   static bool configured = false;
@@ -599,24 +600,27 @@ cudaError_t launch_rhs_t(const MeshDev& m, const GasParams& g, const double* q, 
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int blocks = (m.K + O::EPB - 1) / O::EPB;
+  const int kb = r.begin, ke = r.end < 0 ? m.K : r.end;
+  if (ke <= kb) return cudaSuccess;
+  const int blocks = (ke - kb + O::EPB - 1) / O::EPB;
   rhs_kernel<N, V, PHYS, RK><<<blocks, O::NT, smem, s>>>(q, out, k, T, m.prim, m.ops,
                                                            m.fmask, m.geo, m.vmapP,
                                                            PHYS == MIXTURE_NS ? m.mix_fv : m.scratch,
                                                            m.av_sig, m.av_eps, m.status, g, m.bc, m.K, nvar, a, b,
-                                                           dt);
+                                                           dt, kb, ke);
   return cudaGetLastError();
 }
 
 template <int V, int PHYS>
 cudaError_t dispatch_rhs(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
-                         const double* T, bool rk, double a, double b, double dt, cudaStream_t s) {
+                         const double* T, bool rk, double a, double b, double dt, cudaStream_t s,
+                         ElemRange r = ElemRange()) {
   const int nvar = 5 + g.ns;
   switch (m.N) {
 #define DG_CASE(NN)                                                                         \
   case NN:                                                                                  \
-    return rk ? launch_rhs_t<NN, V, PHYS, true>(m, g, q, out, k, T, nvar, a, b, dt, s)      \
-              : launch_rhs_t<NN, V, PHYS, false>(m, g, q, out, k, T, nvar, a, b, dt, s);
+    return rk ? launch_rhs_t<NN, V, PHYS, true>(m, g, q, out, k, T, nvar, a, b, dt, s, r)   \
+              : launch_rhs_t<NN, V, PHYS, false>(m, g, q, out, k, T, nvar, a, b, dt, s, r);
     DG_CASE(1)
     DG_CASE(2)
     DG_CASE(3)

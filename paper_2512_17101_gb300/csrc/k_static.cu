@@ -38,12 +38,12 @@ cudaError_t stage_t(const dg::MeshDev& m, const dg::GasParams& g, const double* 
   if (e != cudaSuccess) return e;
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
   dg::kern::viscous_kernel<N><<<blocks, O::NT, vs, s>>>(q, m.scratch, nullptr, m.ops, m.fmask, m.geo, m.vmapP,
-                                                        m.status, g, m.bc, m.K);
+                                                        m.status, g, m.bc, m.K, 0, m.K);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dg::kern::rhs_kernel<N, 5, dg::kern::NAVIER_STOKES, true><<<blocks, O::NT, rs, s>>>(
       q, out, k, nullptr, nullptr, m.ops, m.fmask, m.geo, m.vmapP, m.scratch, nullptr, nullptr, m.status, g, m.bc, m.K,
-      5, a, b, dt);
+      5, a, b, dt, 0, m.K);
   return cudaGetLastError();
 }
 

@@ -40,12 +40,18 @@ def _hptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0, wait_polls=0):
+def _opts(precision=capi.DG_PREC_FP64, t_seed=capi.DG_TSEED_INPUT, t_const=0.0, wait_polls=0, elems=None,
+          viscous_given=False, prims_given=False):
+    """dg_opts; elems = (begin, end): the element range of a FP64 perfect-gas right-hand side."""
     o = capi.dg_opts()
     o.precision = precision
     o.t_seed = t_seed
     o.t_const = t_const
     o.wait_polls = wait_polls
+    o.viscous_given = int(bool(viscous_given))
+    o.prims_given = int(bool(prims_given))
+    if elems is not None:
+        o.elem_range, o.elem_begin, o.elem_end = 1, int(elems[0]), int(elems[1])
     return o
 
 

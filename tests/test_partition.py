@@ -43,6 +43,89 @@ def test_partition_invariants(lib, nparts):
             assert np.array_equal(p.local[ix], theirs)
 
 
+@pytest.mark.parametrize("nparts", [1, 2, 3])
+def test_owned_elements_interior_first(lib, nparts):
+    """owned[:n_interior] have every face neighbour owned here; each of the others has one owned
+    elsewhere (a halo element), and the groups keep ascending global order."""
+    from paper_2512_17101_gb300 import dg
+    from paper_2512_17101_gb300.partition import partition_mesh
+    N = 2
+    v, per = box_mesh((4, 3, 4), 1.0)
+    glob = dg.Mesh(v, per, N, equispaced_tet_nodes(N), host_only=True)
+    EToE, _ = glob.face_pairs()
+    parts = partition_mesh(v, per, N, equispaced_tet_nodes(N), nparts)
+    for p in parts:
+        mine = set(p.owned.tolist())
+        ni = p.n_interior
+        inside = [all(int(n) in mine for n in EToE[e] if n >= 0) for e in p.owned]
+        assert all(inside[:ni]) and not any(inside[ni:])
+        assert np.all(np.diff(p.owned[:ni]) > 0) and np.all(np.diff(p.owned[ni:]) > 0)
+        if nparts == 1:
+            assert ni == len(p.owned) and len(p.halo) == 0
+        else:
+            assert 0 < ni < len(p.owned)
+
+
+class _RecordingBackend:
+    """Records the order of a partitioned step's operations (no arithmetic)."""
+
+    flux_vars = 9
+
+    def __init__(self):
+        self.log = []
+
+    def post(self, ranks, transport, arrays, V):
+        self.log.append(("post", V))
+        return None
+
+    def finish(self, ranks, transport, handle, arrays, V):
+        self.log.append(("finish", V))
+
+    def primitives(self, rank, gas, q, elems):
+        self.log.append(("prims", rank.i, tuple(elems)))
+
+    def viscous_flux(self, rank, gas, q, elems):
+        self.log.append(("viscous", rank.i, tuple(elems)))
+        return q
+
+    def stage(self, rank, gas, s, dt, q_in, q_out, viscous, elems):
+        self.log.append(("stage", rank.i, tuple(elems)))
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_partitioned_step_overlaps_each_exchange_with_interior_work(lib, viscous):
+    """Per stage: the state's exchange is posted before any compute and finished only after every
+    rank's owned-node primitives and interior viscous flux; the halo primitives and border flux
+    follow; the viscous flux's exchange is in flight over the interior stages; the border stages
+    come last.  Every element range is covered once per pass."""
+    import types
+    import torch
+    from paper_2512_17101_gb300.partition import LocalRouter, partition_mesh, partitioned_lsrk4_step
+    N = 1
+    v, per = box_mesh((3, 2, 4), 1.0)
+    parts = partition_mesh(v, per, N, equispaced_tet_nodes(N), 2)
+    ranks = []
+    for i, p in enumerate(parts):
+        q = torch.zeros(5, len(p.local), 4, dtype=torch.float64)
+        ranks.append(types.SimpleNamespace(i=i, halo=types.SimpleNamespace(part=p), q=q,
+                                           work=(torch.zeros_like(q), torch.zeros_like(q))))
+    be = _RecordingBackend()
+    partitioned_lsrk4_step(ranks, types.SimpleNamespace(model="perfect", mu=1e-2 if viscous else 0.0),
+                           LocalRouter(), 1e-3, backend=be)
+    groups = [((0, p.n_interior), (p.n_interior, len(p.owned)), (len(p.owned), len(p.local))) for p in parts]
+    stage = [("post", 5)]
+    stage += [op for i, (ig, bg, hg) in enumerate(groups)
+              for op in [("prims", i, (0, bg[1]))] + ([("viscous", i, ig)] if viscous else [])]
+    stage += [("finish", 5)]
+    stage += [op for i, (ig, bg, hg) in enumerate(groups)
+              for op in [("prims", i, hg)] + ([("viscous", i, bg)] if viscous else [])]
+    stage += [("post", 9)] if viscous else []
+    stage += [("stage", i, g[0]) for i, g in enumerate(groups)]
+    stage += [("finish", 9)] if viscous else []
+    stage += [("stage", i, g[1]) for i, g in enumerate(groups)]
+    assert be.log == stage * 5
+
+
 def test_partition_rhs_matches_global_at_owned_elements(lib):
     """Euler, the oracle on each partition's own mesh with the halo filled from the global state."""
     import oracle.boundary as bd
@@ -164,44 +247,60 @@ def test_gloo_halo_exchange_two_ranks(lib):
 class OracleBackend:
     """The compute of one partition on the CPU with the oracle (the test's stand-in for the
     library's kernels): halo rows copied by index, the BR1 viscous flux of the oracle's first pass
-    (3 x 5 fields per node), the stage from the oracle's right-hand side with that flux."""
+    (3 x 5 fields per node), the stage from the oracle's right-hand side with that flux.  The
+    element ranges are honoured the way the library does: each call computes from the whole local
+    state and stores the range's elements only, so a range that read a halo not yet refreshed
+    (NaN before the first exchange) would carry NaN into the result."""
 
     flux_vars = 15
 
     def __init__(self, gas, mu, Pr):
         self.gas, self.mu, self.Pr = gas, mu, Pr
 
-    def refresh(self, ranks, transport, arrays, V):
+    def post(self, ranks, transport, arrays, V):
         import torch
         like = torch.zeros(1, dtype=torch.float64)
         sends = [{s: a[:, torch.from_numpy(ix).long()].contiguous() for s, ix in r.part.send.items()}
                  for r, a in zip(ranks, arrays)]
         shapes = [{s: (V, len(ix), a.shape[2]) for s, ix in r.part.recv.items()} for r, a in zip(ranks, arrays)]
-        for r, a, got in zip(ranks, arrays, transport.exchange_all(sends, shapes, like)):
+        return transport.start(sends, shapes, like)
+
+    def finish(self, ranks, transport, handle, arrays, V):
+        import torch
+        for r, a, got in zip(ranks, arrays, transport.finish(handle)):
             for s, buf in got.items():
                 a[:, torch.from_numpy(r.part.recv[s]).long()] = buf
 
-    def viscous_flux(self, rank, gas, q):
+    def primitives(self, rank, gas, q, elems):
+        pass  # the oracle forms its primitives itself
+
+    def viscous_flux(self, rank, gas, q, elems):
         import torch
         import oracle.boundary as bd
         d = rank.disc
-        fv = bd.viscous_flux_bc(d.ref, d.geo, d.conn, q.numpy(), self.gas, self.mu, self.Pr)
-        rank.fv = torch.from_numpy(np.ascontiguousarray(fv.reshape(15, d.K, d.ref.Np)))
+        with np.errstate(all="ignore"):
+            fv = bd.viscous_flux_bc(d.ref, d.geo, d.conn, q.numpy(), self.gas, self.mu, self.Pr)
+        fv = torch.from_numpy(np.ascontiguousarray(fv.reshape(15, d.K, d.ref.Np)))
+        if rank.fv is None:
+            rank.fv = torch.full_like(fv, float("nan"))
+        rank.fv[:, elems[0]:elems[1]] = fv[:, elems[0]:elems[1]]
         return rank.fv
 
-    def stage(self, rank, gas, s, dt, q_in, q_out, viscous):
+    def stage(self, rank, gas, s, dt, q_in, q_out, viscous, elems):
         import torch
         import oracle.boundary as bd
         from oracle.lsrk import RK4A, RK4B
         d, q = rank.disc, q_in.numpy()
-        if viscous:
-            rhs = bd.rhs_ns_bc(d.ref, d.geo, d.conn, q, self.gas, self.mu, self.Pr,
-                               Fv=rank.fv.numpy().reshape(3, 5, d.K, d.ref.Np))
-        else:
-            rhs = bd.rhs_euler_bc(d.ref, d.geo, d.conn, q, self.gas)
-        k = RK4A[s] * rank.work[1].numpy() + dt * rhs
-        rank.work[1].copy_(torch.from_numpy(k))
-        q_out.copy_(torch.from_numpy(q + RK4B[s] * k))
+        with np.errstate(all="ignore"):
+            if viscous:
+                rhs = bd.rhs_ns_bc(d.ref, d.geo, d.conn, q, self.gas, self.mu, self.Pr,
+                                   Fv=rank.fv.numpy().reshape(3, 5, d.K, d.ref.Np))
+            else:
+                rhs = bd.rhs_euler_bc(d.ref, d.geo, d.conn, q, self.gas)
+        e = slice(elems[0], elems[1])
+        k = RK4A[s] * rank.work[1].numpy()[:, e] + dt * rhs[:, e]
+        rank.work[1][:, e] = torch.from_numpy(k)
+        q_out[:, e] = torch.from_numpy(q[:, e] + RK4B[s] * k)
 
 
 def _two_step_case(viscous):
@@ -230,8 +329,9 @@ def _partitioned_step_worker(rank, world, port, viscous, out):
         p = partition_mesh(v, per, N, nodes, world)[rank]
         q = torch.from_numpy(np.ascontiguousarray(q0[:, p.local]))
         q[:, len(p.owned):] = float("nan")  # the halo before the first exchange
-        st = types.SimpleNamespace(part=p, disc=Disc(p.vertices, per, N, face_bc=p.face_bc), q=q,
-                                   work=(torch.empty_like(q), torch.zeros_like(q)), fv=None)
+        st = types.SimpleNamespace(part=p, halo=types.SimpleNamespace(part=p),
+                                   disc=Disc(p.vertices, per, N, face_bc=p.face_bc), q=q,
+                                   work=(torch.full_like(q, float("nan")), torch.zeros_like(q)), fv=None)
         gas = types.SimpleNamespace(model="perfect", mu=mu)
         backend = OracleBackend(PerfectGas(1.4, 1.0), mu, 0.71)
         for _ in range(2):
