@@ -225,6 +225,14 @@ __device__ __forceinline__ void block_teardown(const Smem<C_>& S, const Pipe& p)
   if (threadIdx.x < 32) tmem_dealloc(*S.tmem, C_::TMEM_COLS);
 }
 
+// Column groups of 8 that npad accumulator columns split into among the block's warps: the most
+// groups, at most max_groups, that divide npad into multiples of 8.
+__host__ __device__ constexpr int copy_groups(int npad, int max_groups) {
+  for (int g = max_groups; g > 1; --g)
+    if (npad % (8 * g) == 0) return g;
+  return 1;
+}
+
 // Issue the MMAs of chunk c (width/16 k-steps x 6 split products) and commit them to the
 // mbarrier.  Chunks 0 .. NVOL-1 are KV columns wide, the surface chunks after them KS.
 template <class C_>
@@ -668,6 +676,13 @@ struct VCfg {
   static_assert(NOUT <= 256 && NOUT % 16 == 0, "MMA N");
   static_assert(ROWS * CS * 4 <= 3 * A_TERM && ROWS * CS % 4 == 0, "accumulator copy in the operand slot");
   static_assert(NOUT <= TMEM_COLS, "TMEM columns");
+  // Row-parallel gradients (where they fit in the operand slot): the threads of an accumulator row
+  // (element, field) read the row from TMEM for the three reference directions at once and write
+  // the node gradients [E Np][3][5] (stride GSTR floats per node) to shared memory; the warps
+  // split the columns into CG groups of 8 (warp w: TMEM lane quarter w % 4, group w / 4).
+  static constexpr int GSTR = 15, CG = copy_groups(NPAD, NT / 128), CPG = NPAD / CG;
+  static constexpr bool ROWGRAD = E * Np * GSTR * 4 <= 3 * A_TERM && CPG % 8 == 0;
+  static constexpr int CLEAR_BYTES = ROWGRAD ? (E * Np * GSTR * 4 + 15) / 16 * 16 : ROWS * CS * 4;
 };
 
 // Elements [e0, e0 + 25) of case c: the viscous-flux records from the node records (rho and T as
@@ -785,6 +800,65 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     if (!run_chunk<C_>(S, 1 + sc, p.phase, status, c.wait_polls, during)) return false;
   }
 
+  const float mu = (float)c.gas.mu, kap = (float)c.gas.kappa;
+  if constexpr (C_::ROWGRAD) {
+    // reference derivatives -> gradients, row-parallel: accumulator row r = 5 e + f holds
+    // D_a w_f + Lhat_a [w_f] of tile element e at columns a NPAD + i; the threads of the row (TMEM
+    // lane quarter r / 32, one column group each) form grad_d w_f = sum_a (dr_a/dx_d)(...) at their
+    // nodes and write them to the buffer [E Np][3][5], which aliases the operand slot
+    float* GR = S.C;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < 4 * C_::CG) {
+      const int q = warp & 3, g = warp >> 2, r = 32 * q + lane;
+      const int e = r / 5, f = r - 5 * e;
+      const bool row_ok = e < nel;  // rows past the tile's elements (and 125..127) hold nothing
+      float Gm[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Gm[a][d] = row_ok ? S.geo[e * GS + 3 * a + d] : 0.0f;
+      const uint32_t tl = *S.tmem + ((uint32_t)(32 * q) << 16);
+#pragma unroll
+      for (int c0 = 0; c0 < C_::CPG; c0 += 8) {
+        const int col = g * C_::CPG + c0;
+        float da[3][8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) tmem_ld8(tl + (uint32_t)(a * C_::NPAD + col), da[a]);  // the whole warp
+        if (row_ok) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int i = col + jj;
+            if (i < Np) {
+              float* out = GR + (e * Np + i) * C_::GSTR + f;
+#pragma unroll
+              for (int d = 0; d < 3; ++d)  // the direction order of the per-direction form below
+                out[5 * d] = fmaf(Gm[2][d], da[2][jj], fmaf(Gm[1][d], da[1][jj], fmaf(Gm[0][d], da[0][jj], 0.0f)));
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int n = tid + s * NT;
+      if (n < nn) {
+        float grad[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int fi = 0; fi < 5; ++fi) grad[d][fi] = GR[n * C_::GSTR + 5 * d + fi];
+        float f9[9];
+        mixk::viscous_flux_node(rho_n[s], m_n[s], grad, mu, kap, f9);
+        const size_t gn = base + n;
+        c.fv4[2 * gn] = make_float4(f9[0], f9[1], f9[2], f9[3]);
+        c.fv4[2 * gn + 1] = make_float4(f9[4], f9[5], f9[6], f9[7]);
+        c.fvz[gn] = f9[8];
+      }
+    }
+    __syncthreads();  // every read of the gradient buffer is done before it is cleared
+  } else {
   // reference derivatives -> gradients, one reference direction at a time through shared memory
   float grad[NPT][3][5];
 #pragma unroll
@@ -824,7 +898,6 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     }
     __syncthreads();
   }
-  const float mu = (float)c.gas.mu, kap = (float)c.gas.kappa;
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int n = tid + s * NT;
@@ -837,9 +910,10 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       c.fvz[gn] = f9[8];
     }
   }
-  // clear the accumulator copy (see rhs_tile); the last barrier above ordered its reads
+  }
+  // clear what aliased the operand slot (see rhs_tile); a barrier above ordered its reads
   uint4* Cz = reinterpret_cast<uint4*>(S.C);
-  for (int i = tid; i < C_::ROWS * C_::CS / 4; i += NT) Cz[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < C_::CLEAR_BYTES / 16; i += NT) Cz[i] = make_uint4(0u, 0u, 0u, 0u);
   return true;
 }
 
