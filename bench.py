@@ -61,14 +61,14 @@ L2_FLUSH_BYTES = 256 << 20
 FP64_SOURCES = ("dg_kernels.cuh", "k_ns.cu", "k_euler.cu")
 MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "dg_umma.cuh", "dg_cvt.cuh", "dg_kernels.cuh", "k_mixed.cu", "k_tc.cu")
 TRAFFIC = {
-    # profiles/ns_N3_K82944_fp64.md (RK stage 2: the register k is read)
-    ("fd640972440b44d5", "ns_viscous", "rhs"): 330.799104e6 + 104.880640e6,
-    ("fd640972440b44d5", "ns_viscous", "viscous"): 126.838528e6 + 75.130112e6,
-    ("fd640972440b44d5", "ns_viscous", "prims"): 66.396160e6 + 7.919616e6,
-    # profiles/mixed_tc_ns_N3_K82944.md (mean over the five stages of one RK4 step)
-    ("bb7f03807599f346", "ns_viscous", "mixed_rhs"): 258.283213e6 + 94.725069e6,
-    ("bb7f03807599f346", "ns_viscous", "mixed_viscous"): 90.059469e6 + 22.344806e6,
-    ("bb7f03807599f346", "ns_viscous", "mixed_prims"): 66.369280e6 + 12.339763e6,
+    # profiles/ns_N3_K82944_fp64.md and profiles/mixed_tc_ns_N3_K82944.md: DRAM read + write per
+    # launch, mean over the five stages of one RK4 step
+    ("c0a04080e1d1fa62", "ns_viscous", "rhs"): 317.780941e6 + 105.379021e6,
+    ("c0a04080e1d1fa62", "ns_viscous", "viscous"): 127.153510e6 + 74.815693e6,
+    ("c0a04080e1d1fa62", "ns_viscous", "prims"): 66.382694e6 + 6.039859e6,
+    ("e647c86fec354ee8", "ns_viscous", "mixed_rhs"): 258.197965e6 + 94.610022e6,
+    ("e647c86fec354ee8", "ns_viscous", "mixed_viscous"): 90.074368e6 + 22.365850e6,
+    ("e647c86fec354ee8", "ns_viscous", "mixed_prims"): 66.368870e6 + 15.947315e6,
 }
 
 
