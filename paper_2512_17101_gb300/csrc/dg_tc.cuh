@@ -622,16 +622,21 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const M
 
 // Issue the staging copies of BR1 tile [e0, e0 + 25) of case c (C_::STAGE): node records and
 // temperature pairs by the TMA engine (thread 0; completion on st_bar).
+// With odd Np the temperature pairs go by per-thread 8-byte asynchronous copies instead, thread t
+// copying those of the nodes t + j NT that it reads itself (each thread completes its copies with
+// cp_async_wait_all before it reads them).
 template <class C_>
 __device__ __forceinline__ void stage_issue_vis(const Smem<C_>& S, const MixedCase& c, int e0) {
-  static_assert(C_::Np % 2 == 0, "16-byte aligned temperature runs");
-  if (threadIdx.x != 0) return;
   const int nel = min(C_::E, c.K - e0), nn = nel * C_::Np;
   const size_t base = (size_t)e0 * C_::Np;
-  const uint32_t bar = smem_u32(S.st_bar);
-  mbar_expect_tx(bar, (uint32_t)nn * 40u);
-  bulk_g2s(S.st_node, c.node + 2 * base, (uint32_t)nn * 32u, bar);
-  bulk_g2s(S.st_temp, c.temp + base, (uint32_t)nn * 8u, bar);
+  if (threadIdx.x == 0) {
+    const uint32_t bar = smem_u32(S.st_bar);
+    mbar_expect_tx(bar, (uint32_t)nn * (C_::TEMP_BULK ? 40u : 32u));
+    bulk_g2s(S.st_node, c.node + 2 * base, (uint32_t)nn * 32u, bar);
+    if (C_::TEMP_BULK) bulk_g2s(S.st_temp, c.temp + base, (uint32_t)nn * 8u, bar);
+  }
+  if (!C_::TEMP_BULK)
+    for (int i = threadIdx.x; i < nn; i += C_::NT) cp_async8(S.st_temp + i, c.temp + base + i);
 }
 
 // ==== BR1 pass on the tensor cores ===============================================================
@@ -664,11 +669,12 @@ struct VCfg {
   static constexpr int OFF_VM = (OFF_FM + NF * 4 + 15) / 16 * 16, VM_BYTES = E * NF * 4;
   static constexpr bool VM = vm_fits(OFF_FM + NF * 4, OFF_VM + VM_BYTES, NT, 64);
   static constexpr int END_VM = VM ? OFF_VM + VM_BYTES : OFF_FM + NF * 4;
-  // the tile's own node records and temperature pairs, staged one tile ahead by bulk copies
-  // ([E Np] x 2 float4, [E Np] float2; tile starts and sizes are 16-byte multiples for even Np)
-  // where that costs no resident block
+  // the tile's own node records and temperature pairs, staged one tile ahead where that costs no
+  // resident block: [E Np] x 2 float4 by a bulk copy, [E Np] float2 by one too for even Np (tile
+  // starts and sizes are then 16-byte multiples), else by per-thread asynchronous copies
   static constexpr int OFF_ST = (END_VM + 15) / 16 * 16, ST_BYTES = E * Np * 40;
-  static constexpr bool STAGE = VM && NSURF == 1 && Np % 2 == 0 && vm_fits(END_VM, OFF_ST + ST_BYTES, NT, 64);
+  static constexpr bool STAGE = VM && vm_fits(END_VM, OFF_ST + ST_BYTES, NT, 64);
+  static constexpr bool TEMP_BULK = Np % 2 == 0;
   static constexpr int OFF_BAR = ((STAGE ? OFF_ST + ST_BYTES : END_VM) + 7) / 8 * 8;
   static constexpr int SMEM = OFF_BAR + 24;
   static constexpr int MINB = aim_blocks(SMEM, NT);
@@ -708,7 +714,9 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
     prefetch_l2(next->vmapP + (size_t)next_e0 * NF, (size_t)nnel * NF * 4);
   }
   if constexpr (ST) {
-    // this tile's staged records, copied during the previous tile (or the block set-up)
+    // this tile's staged records, copied during the previous tile (or the block set-up); the
+    // only asynchronous copies of this thread in flight here are its temperature pairs (odd Np)
+    if (!C_::TEMP_BULK) cp_async_wait_all();
     if (mbar_wait(smem_u32(S.st_bar), p.sphase, c.wait_polls > 0 ? c.wait_polls : kWaitPolls)) {
       p.sphase ^= 1u;
       p.staged = false;
@@ -732,7 +740,8 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       const int l1 = (n / Np) * Np;
       const float4 a0 = ND[2 * n], a1 = ND[2 * n + 1];
       const float4 r0 = ND[2 * l1], r1 = ND[2 * l1 + 1];
-      const float2 t = TD[n], t1 = TD[l1];
+      // (with per-thread temperature copies the reference node's pair is another thread's: global)
+      const float2 t = TD[n], t1 = (ST && !C_::TEMP_BULK) ? c.temp[base + l1] : TD[l1];
       rho_n[s] = a0.x;
       m_n[s][0] = a0.y;
       m_n[s][1] = a0.z;
@@ -869,15 +878,17 @@ __device__ __forceinline__ bool vis_tile(const Smem<C_>& S, const MixedCase& c, 
       for (int f = 0; f < 5; ++f) grad[s][d][f] = 0.0f;
 #pragma unroll 1
   for (int a = 0; a < 3; ++a) {
-    if (tid < 128) {
-      const int warp = tid >> 5;
-      float* Crow = S.C + tid * C_::CS;
+    // direction a's columns -> S.C, by the warps of CG column groups (warp w: TMEM lane quarter
+    // w % 4, the lanes a warp may access; column group w / 4)
+    if (tid < 128 * C_::CG) {
+      const int warp = tid >> 5, q = warp & 3, g = warp >> 2;
+      float* Crow = S.C + (32 * q + (tid & 31)) * C_::CS + g * C_::CPG;
 #pragma unroll
-      for (int c0 = 0; c0 < C_::NPAD; c0 += 16) {
-        float r[16];
-        tmem_ld16(*S.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * C_::NPAD + c0), r);
+      for (int c0 = 0; c0 < C_::CPG; c0 += 8) {
+        float r[8];
+        tmem_ld8(*S.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * C_::NPAD + g * C_::CPG + c0), r);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) Crow[c0 + jj] = r[jj];
+        for (int jj = 0; jj < 8; ++jj) Crow[c0 + jj] = r[jj];
       }
     }
     tc_fence_before();

@@ -152,9 +152,12 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t 
 }
 
 // Asynchronous global -> shared copies (no registers hold the data; cp_async_wait_all completes
-// this thread's copies).  Sizes 4 and 16 bytes; both addresses aligned to the size.
+// this thread's copies).  Sizes 4, 8 and 16 bytes; both addresses aligned to the size.
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
