@@ -9,8 +9,10 @@
 // contravariant fluxes against -D_r, -D_s, -D_t) and one or two surface chunks of KS columns
 // (Fscale g against LIFT; one chunk of 48 at N = 3).  Each chunk is produced by all threads
 // into one shared-memory slot, then contracted by width/16 k-steps of the six split-BF16
-// products while nothing else may touch the slot; two or three blocks per SM overlap one
-// block's production with another's MMAs.  Operand columns past Np (volume) or past the
+// products while nothing else may touch the slot; the blocks resident on an SM (two at N = 3)
+// overlap one block's production with another's MMAs.  A tile's own node records are staged in
+// shared memory one tile ahead (TMA bulk copies issued under the previous tile's last MMA
+// round), where that costs no resident block.  Operand columns past Np (volume) or past the
 // face-node count (last surface chunk) hold zeros or stale finite values from an earlier chunk;
 // the operator table is zero there, so they contribute nothing.
 #pragma once
