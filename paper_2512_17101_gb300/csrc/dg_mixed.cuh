@@ -26,6 +26,14 @@ namespace mixk {
 
 using kern::GS;
 
+// FP64 reciprocal from an FP32 seed plus one Newton step (relative error ~1e-14); the seed's
+// conversions run on the integer pipe.
+__device__ __forceinline__ double recip64(double x, float& r32) {
+  r32 = 1.0f / cvt::narrow(x);
+  const double r = cvt::widen(r32);
+  return r * fma(-x, r, 2.0);
+}
+
 // Per-node tables of the mixed form for a perfect gas, in the mesh's scratch (76 of its 80 bytes
 // per node), as records so that a node's values come in a few wide loads:
 //   node [KNp][2] float4: {rho_hi, rho u, rho v, rho w}, {rho E, p_hi, p_lo, rho_lo}
@@ -60,7 +68,6 @@ __device__ __forceinline__ float2 split2(double x) { return cvt::split(x); }
 // per-node tables, geometry, neighbour map, size, time step and gas.
 struct MixedGas {
   double gamma, R, mu, kappa, inv_R;
-  float2 gm1, inv_R2;  // gamma - 1 and 1 / R as float pairs (hi + lo)
 };
 
 struct MixedCase {
@@ -148,69 +155,21 @@ __host__ __device__ inline float4* mixture_lo(double* base, size_t KNp) {
   return reinterpret_cast<float4*>(base) + 4 * KNp;
 }
 
-// ---- float pairs for pass 0 -----------------------------------------------------------------------
-// A value is hi + lo with |lo| <= ulp(hi) / 2.  Knuth's TwoSum, Dekker's FastTwoSum (|a| >= |b|)
-// and the FMA TwoProduct are error-free transformations; the _rn intrinsics keep the compiler from
-// contracting or reordering their steps.  Products and quotients drop the lo x lo terms (about
-// 2^-48 relative), so the chains below carry about 46 significant bits.
-struct Pair {
-  float hi, lo;
-};
-__device__ __forceinline__ Pair pair_sum(float a, float b) {
-  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-  return Pair{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ Pair pair_norm(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return Pair{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ Pair pair_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return Pair{p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ Pair pair_mul(Pair x, float2 y) {
-  const Pair p = pair_prod(x.hi, y.x);
-  return pair_norm(p.hi, fmaf(x.hi, y.y, fmaf(x.lo, y.x, p.lo)));
-}
-// x / y: the FP32 quotient corrected once by the exact remainder x - q y (q y.hi by TwoProduct,
-// x.hi - q y.hi exact as the two are within a few ulps)
-__device__ __forceinline__ Pair pair_div(Pair x, float2 y) {
-  const float q = __fdividef(x.hi, y.x);
-  const Pair p = pair_prod(q, y.x);
-  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), fmaf(-q, y.y, x.lo));
-  return pair_norm(q, __fdividef(r, y.x));
-}
-
-// ---- pass 0: per node, pressure (and temperature) as float pairs and the node record, so that
-// the later kernels read traces without recomputing or converting them.  The state arrives in
-// FP64 and is split into float pairs on the integer pipe; p = (gamma - 1)(rho E - |rho u|^2 /
-// (2 rho)) and T = p / (rho R) are then formed in float-pair arithmetic on the FP32 pipe (the FP64
-// pipe runs at 1/64 of its rate here), to about 46 bits: the differences of p and T that the
-// later kernels form (against a reference node, across a face) need about 30.
+// ---- pass 0: per node, FP64 pressure (and temperature) and the node record, so that the later
+// kernels read traces without recomputing or converting them.
 __device__ __forceinline__ void prims_node(const MixedCase& c, const double* __restrict__ qin, size_t KNp, size_t i,
                                            unsigned* status) {
   double qv[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) qv[v] = qin[v * KNp + i];
-  const float2 r2 = split2(qv[0]), mx = split2(qv[1]), my = split2(qv[2]), mz = split2(qv[3]), E2 = split2(qv[4]);
-  // |rho u|^2: the hi x hi squares exactly, their sum and the cross terms 2 hi lo
-  const Pair sx = pair_prod(mx.x, mx.x), sy = pair_prod(my.x, my.x), sz = pair_prod(mz.x, mz.x);
-  const Pair a = pair_sum(sx.hi, sy.hi), b = pair_sum(a.hi, sz.hi);
-  const float cross = 2.0f * fmaf(mx.x, mx.y, fmaf(my.x, my.y, __fmul_rn(mz.x, mz.y)));
-  const float m2lo = __fadd_rn(__fadd_rn(__fadd_rn(sx.lo, sy.lo), __fadd_rn(sz.lo, a.lo)), __fadd_rn(b.lo, cross));
-  const Pair m2 = pair_norm(b.hi, m2lo);
-  // rho E - |rho u|^2 / (2 rho), then times gamma - 1
-  const Pair k2 = pair_div(m2, r2);
-  const Pair d = pair_sum(E2.x, -0.5f * k2.hi);
-  const Pair e = pair_norm(d.hi, __fadd_rn(d.lo, __fsub_rn(E2.y, 0.5f * k2.lo)));
-  const Pair p = pair_mul(e, c.gas.gm1);
-  if (!(r2.x > 0.0f) || !(p.hi > 0.0f)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-  c.node[2 * i] = make_float4(r2.x, mx.x, my.x, mz.x);
-  c.node[2 * i + 1] = make_float4(E2.x, p.hi, p.lo, r2.y);
-  if (c.gas.mu > 0.0) {  // T = p / (rho R)
-    const Pair T = pair_mul(pair_div(p, r2), c.gas.inv_R2);
-    c.temp[i] = make_float2(T.hi, T.lo);
-  }
+  float ir32;
+  const double ir = recip64(qv[0], ir32);
+  const double p = (c.gas.gamma - 1.0) * (qv[4] - 0.5 * ir * fma(qv[1], qv[1], fma(qv[2], qv[2], qv[3] * qv[3])));
+  const float2 rho2 = split2(qv[0]), p2 = split2(p);
+  if (!(rho2.x > 0.0f) || !(p2.x > 0.0f)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+  c.node[2 * i] = make_float4(rho2.x, cvt::narrow(qv[1]), cvt::narrow(qv[2]), cvt::narrow(qv[3]));
+  c.node[2 * i + 1] = make_float4(cvt::narrow(qv[4]), p2.x, p2.y, rho2.y);
+  if (c.gas.mu > 0.0) c.temp[i] = split2(p * ir * c.gas.inv_R);  // T = p / (rho R), no FP64 division
 }
 
 static __global__ void prims_kernel(const MixedCase c, const double* __restrict__ qin, const size_t KNp,

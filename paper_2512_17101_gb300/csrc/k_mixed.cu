@@ -35,11 +35,7 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
   c.K = m.K;
   c.Np = m.Np;
   c.dt = dt;
-  const double gm1 = g.gamma - 1.0, inv_R = 1.0 / g.R;
-  const float gm1_hi = (float)gm1, inv_R_hi = (float)inv_R;
-  c.gas = mixk::MixedGas{g.gamma, g.R, g.mu, g.kappa, inv_R,
-                         make_float2(gm1_hi, (float)(gm1 - (double)gm1_hi)),
-                         make_float2(inv_R_hi, (float)(inv_R - (double)inv_R_hi))};
+  c.gas = mixk::MixedGas{g.gamma, g.R, g.mu, g.kappa, 1.0 / g.R};
   if (m.inflow_nvar == 5 && g.model == DG_GAS_PERFECT) {  // the inflow state as a node record
     const double* qi = m.bc.q_in;
     const double ke = 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];

@@ -1,7 +1,7 @@
 """The node records of the mixed form's primitives pass (the float pairs that the tensor-core
 kernels read): rho, momentum and energy rounded to FP32 exactly as the hardware rounds, and
-rho, p and T as float pairs hi + lo within 1e-12 of their FP64 values (p = (gamma - 1)(rho E -
-|rho u|^2 / (2 rho)), T = p / (rho R)), normalised (|lo| <= ulp(hi) / 2)."""
+rho, p and T (evaluated in FP64: p = (gamma - 1)(rho E - |rho u|^2 / (2 rho)), T = p / (rho R))
+as float pairs hi + lo within 1e-12 of the FP64 values, normalised (|lo| <= ulp(hi) / 2)."""
 
 import ctypes
 
