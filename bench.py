@@ -66,9 +66,9 @@ TRAFFIC = {
     ("c0a04080e1d1fa62", "ns_viscous", "rhs"): 317.780941e6 + 105.379021e6,
     ("c0a04080e1d1fa62", "ns_viscous", "viscous"): 127.153510e6 + 74.815693e6,
     ("c0a04080e1d1fa62", "ns_viscous", "prims"): 66.382694e6 + 6.039859e6,
-    ("e647c86fec354ee8", "ns_viscous", "mixed_rhs"): 258.197965e6 + 94.610022e6,
-    ("e647c86fec354ee8", "ns_viscous", "mixed_viscous"): 90.074368e6 + 22.365850e6,
-    ("e647c86fec354ee8", "ns_viscous", "mixed_prims"): 66.368870e6 + 15.947315e6,
+    ("fa768e640d7cf4d9", "ns_viscous", "mixed_rhs"): 258.144870e6 + 94.679450e6,
+    ("fa768e640d7cf4d9", "ns_viscous", "mixed_viscous"): 90.065766e6 + 22.333286e6,
+    ("fa768e640d7cf4d9", "ns_viscous", "mixed_prims"): 66.374400e6 + 12.383130e6,
 }
 
 
