@@ -405,7 +405,7 @@ int dg_mixture_energy(dg_gas gas, int64_t n, const double* T_dev, const double* 
 /* ---- learned temperature guess (no counterpart in the paper) ------------------------
  * An 8 -> 64 -> 64 -> 1 tanh MLP maps x = ((e - e_mean)/e_scale, Y_1..Y_7) to
  * (T - T_mean)/T_scale; its guess (clamped to [T_min, T_max]) seeds the FP64
- * Newton solve, which stays the judge of the result (same |dT| < tol) and its
+ * Newton solve, which still decides the result (same |dT| < tol) and its
  * fallback.  Inference uses FP16 operands with FP32 accumulation on the tensor
  * cores; training runs the library's own FP32 forward/backward and Adam kernels.
  * Parameters, float, flat: W1 [64][8] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64] | b3. */

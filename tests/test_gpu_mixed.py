@@ -187,7 +187,7 @@ def test_mixed_precision_plus_learned_guess_step():
     from workloads.configs import _mixture_dt
     torch, dg, d, mesh, gas, gas_o, mix, q0 = _mixture(4, 2, seed=0)
     from paper_2512_17101_gb300 import capi
-    # a small training run: the network only seeds Newton, which stays the judge of T
+    # a small training run: the network only seeds Newton, which still decides T
     T, Y = temperature_samples(50_000, 7, seed=11)
     Td, Yd = torch.tensor(T, device="cuda"), torch.tensor(Y, device="cuda")
     e = torch.empty_like(Td)

@@ -1,6 +1,6 @@
 """Learned temperature guess: GPU gradients, Adam step and FP16 inference vs the FP64 oracle,
 training on Newton samples, and what the trained network gains over the Newton solve without it
-(Newton stays the judge)."""
+(Newton still decides the result)."""
 
 import numpy as np
 import pytest
@@ -194,7 +194,7 @@ def _iterations(torch, dg, capi, gas, qh, seed_value=1650.0):
 def test_mlp_training_reduces_loss_and_newton_iterations():
     """Trained on Newton-generated samples; on held-out samples with T spread over 300..3000 K the MLP
     seed needs fewer Newton updates than the constant seed; on the learned-form workload's field
-    (which clusters near the constant seed) it does not lose.  Newton judges both: same T."""
+    (which clusters near the constant seed) it does not lose.  Newton decides both: same T."""
     torch = torch_cuda()
     from paper_2512_17101_gb300 import capi, dg
     mix, gas, hist = _train(torch, dg)
