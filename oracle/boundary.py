@@ -23,6 +23,12 @@ the exterior normal viscous fluxes, with traction t = tau n and energy flux e = 
   the normal part of the interior one;
 * inflow and outflow: t+ = t-, e+ = e- (the central viscous flux is the interior one).
 
+Mixtures (the multi-species Euler right-hand side, §5.4's reacting runs in walled geometry
+without the reactions): the same ghost states, species densities carried like the density.  A
+wall or outflow ghost keeps the node's rho, |m|, rho E and rho Y, hence its internal energy, so
+its temperature is the node's own (T+ = T-); an inflow ghost has the temperature of q_in, the
+root of e(T) = e_in that a Newton solve gives (rhs_mixture_bc takes it as T_in).
+
 Codes (the library's DG_BC_* values): 1 slip wall, 2 no-slip wall, 3 inflow, 4 outflow.
 """
 
@@ -76,6 +82,30 @@ def rhs_euler_bc(ref, geo, conn, q, gas, q_in=None, form="strong"):
     n, qM, qP = _traces(conn, geo, ref, q, q_in)
     pM, cM = gas.pressure_sound_speed(qM)
     pP, cP = gas.pressure_sound_speed(qP)
+    fstar = lax_friedrichs(qM, qP, pM, pP, cM, cP, n)
+    if form == "strong":
+        return -divergence(ref, geo, F) + lift(ref, geo, normal_flux(euler_flux(qM, pM), n) - fstar)
+    return _weak_volume(ref, geo, F) - lift(ref, geo, fstar)
+
+
+def rhs_mixture_bc(ref, geo, conn, q, gas, T, q_in=None, T_in=None, form="strong"):
+    """Euler right-hand side [5 + ns][K][Np] of a NASA-7 mixture with boundary faces (strong or weak
+    form).  T [K][Np]: the node temperatures of q (the temperature solve's); T_in: the temperature
+    of the inflow state q_in.  The exterior temperature is the neighbour's on interior faces, the
+    node's own at wall and outflow ghosts (their internal energy is the node's) and T_in at inflow
+    ghosts; p and c of both traces follow from (q, T) as at the nodes."""
+    p, c = gas.pressure_sound_speed(q, T)
+    F = euler_flux(q, p)
+    n, qM, qP = _traces(conn, geo, ref, q, q_in)
+    TM = gather(T[None], conn.vmapM)[0]
+    TP = gather(T[None], conn.vmapP)[0]  # a boundary face node points at itself
+    inflow = conn.bc == INFLOW
+    if np.any(inflow):
+        if T_in is None:
+            raise ValueError("inflow faces need the inflow temperature T_in")
+        TP = np.where(inflow, T_in, TP)
+    pM, cM = gas.pressure_sound_speed(qM, TM)
+    pP, cP = gas.pressure_sound_speed(qP, TP)
     fstar = lax_friedrichs(qM, qP, pM, pP, cM, cP, n)
     if form == "strong":
         return -divergence(ref, geo, F) + lift(ref, geo, normal_flux(euler_flux(qM, pM), n) - fstar)
