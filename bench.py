@@ -63,12 +63,12 @@ MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "dg_umma.cuh", "dg_cvt.cuh", "dg_k
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md and profiles/mixed_tc_ns_N3_K82944.md: DRAM read + write per
     # launch, mean over the five stages of one RK4 step
-    ("c0a04080e1d1fa62", "ns_viscous", "rhs"): 317.780941e6 + 105.379021e6,
-    ("c0a04080e1d1fa62", "ns_viscous", "viscous"): 127.153510e6 + 74.815693e6,
-    ("c0a04080e1d1fa62", "ns_viscous", "prims"): 66.382694e6 + 6.039859e6,
-    ("fa768e640d7cf4d9", "ns_viscous", "mixed_rhs"): 258.144870e6 + 94.679450e6,
-    ("fa768e640d7cf4d9", "ns_viscous", "mixed_viscous"): 90.065766e6 + 22.333286e6,
-    ("fa768e640d7cf4d9", "ns_viscous", "mixed_prims"): 66.374400e6 + 12.383130e6,
+    ("d344a5980bd8972a", "ns_viscous", "rhs"): 317.775114e6 + 105.664227e6,
+    ("d344a5980bd8972a", "ns_viscous", "viscous"): 126.966533e6 + 75.377306e6,
+    ("d344a5980bd8972a", "ns_viscous", "prims"): 66.388736e6 + 6.113434e6,
+    ("fa7482e711b8b053", "ns_viscous", "mixed_rhs"): 258.201306e6 + 94.688461e6,
+    ("fa7482e711b8b053", "ns_viscous", "mixed_viscous"): 90.075962e6 + 22.346803e6,
+    ("fa7482e711b8b053", "ns_viscous", "mixed_prims"): 66.369690e6 + 12.294205e6,
 }
 
 

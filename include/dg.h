@@ -116,8 +116,11 @@ typedef struct {
  *   DG_BC_OUTFLOW     q+ = q- (supersonic outflow).
  * BR1 exterior values are w(q+); away from walls the viscous exterior flux is the interior one.
  * Meshes with boundary faces run with a perfect gas (Euler or Navier-Stokes) in the FP64, the
- * mixed-precision and the batched forms (the last two with ghost node records); the mixture
- * rejects them (DG_ERR_UNSUPPORTED).
+ * mixed-precision and the batched forms (the last two with ghost node records), and with an
+ * inviscid NASA-7 mixture in the FP64 and mixed-precision forms: species densities are carried
+ * like the density; a wall or outflow ghost keeps the node's internal energy and so its
+ * temperature, p and c; an inflow ghost takes p and c of q_in at its own temperature.  A viscous
+ * mixture on such a mesh is DG_ERR_UNSUPPORTED.
  * In the vmapP of dg_mesh_connectivity a boundary face node holds -code. */
 #define DG_BC_SLIP_WALL 1
 #define DG_BC_NOSLIP_WALL 2
@@ -149,10 +152,13 @@ typedef struct {
 int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out);
 int dg_mesh_free(dg_mesh mesh);
 
-/* Sets the conserved state q_in[nvar] (host; nvar = 5 for a perfect gas) that DG_BC_INFLOW
- * faces impose.  Required before a right-hand side on a mesh with inflow faces
- * (DG_ERR_INVALID_ARG otherwise, or when nvar differs from the gas's).  Errors:
- * DG_ERR_INVALID_ARG (NULL, nvar outside 5..5+DG_MAX_SPECIES, rho <= 0 or non-finite). */
+/* Sets the conserved state q_in[nvar] (host; nvar = 5 for a perfect gas, 5 + species for a
+ * NASA-7 mixture) that DG_BC_INFLOW faces impose.  Required before a right-hand side on a mesh
+ * with inflow faces (DG_ERR_INVALID_ARG otherwise, or when nvar differs from the gas's).  With a
+ * mixture, each right-hand side first solves the state's temperature on the host (Newton on
+ * e(T) = E/rho - |u|^2/2 from 1000 K to the gas's tolerance); a solve that does not reach a
+ * positive T with a positive cv makes that call fail with DG_ERR_INVALID_ARG before any launch.
+ * Errors: DG_ERR_INVALID_ARG (NULL, nvar outside 5..5+DG_MAX_SPECIES, rho <= 0 or non-finite). */
 int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar);
 
 /* ---- shock capturing: artificial viscosity ------------------------------------------------

@@ -62,6 +62,40 @@ cudaError_t upload(T** dst, const T* src, size_t count) {
   return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// The primitives of a mixture's inflow state q[5 + ns] (host): its temperature T by Newton on
+// e(T) = e, e(T) = sum_k Y_k sum_j fc[k][j] T^j with e = E/rho - |u|^2/2, from 1000 K until
+// |dT| < the gas's tolerance (at least 100 steps allowed); then 1/rho, p = rho R_mix T and
+// c = sqrt((p/rho)(1 + R_mix/cv)).  false when the solve does not reach a positive T.
+bool mixture_inflow_prims(const dg::GasParams& g, const double* q, dg::BcParams& bc) {
+  const double ir = 1.0 / q[0];
+  const double e = q[4] * ir - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir * ir;
+  double C[6] = {0, 0, 0, 0, 0, 0}, Rm = 0.0;
+  for (int k = 0; k < g.ns; ++k) {
+    const double Y = q[5 + k] * ir;
+    for (int j = 0; j < 6; ++j) C[j] += Y * g.fc[k][j];
+    Rm += Y * g.Rk[k];
+  }
+  auto cv_at = [&](double t) { return (((5.0 * C[5] * t + 4.0 * C[4]) * t + 3.0 * C[3]) * t + 2.0 * C[2]) * t + C[1]; };
+  double T = 1000.0;
+  bool done = false;
+  const int it_max = std::max(g.newton_max_it, 100);
+  for (int it = 0; it < it_max && !done; ++it) {
+    const double ev = ((((C[5] * T + C[4]) * T + C[3]) * T + C[2]) * T + C[1]) * T + C[0];
+    const double dT = (ev - e) / cv_at(T);
+    if (!std::isfinite(dT)) return false;
+    T -= dT;
+    done = std::fabs(dT) < g.newton_tol;
+  }
+  const double cv = cv_at(T);
+  if (!done || !(T > 0.0) || !(cv > 0.0) || !(Rm > 0.0)) return false;
+  const double p = q[0] * Rm * T;
+  bc.T_in = T;
+  bc.prim_in[0] = ir;
+  bc.prim_in[1] = p;
+  bc.prim_in[2] = std::sqrt(p * ir * (1.0 + Rm / cv));
+  return true;
+}
+
 int check_opts(const dg_opts* o) {
   if (!o) return DG_OK;
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED)
@@ -164,10 +198,12 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
   }
   if (m.boundary_faces > 0) {
-    if (g.model != DG_GAS_PERFECT)
-      return fail(DG_ERR_UNSUPPORTED, "meshes with boundary faces need a perfect gas");
+    if (g.model != DG_GAS_PERFECT && g.mu > 0)
+      return fail(DG_ERR_UNSUPPORTED, "viscous mixtures run on periodic meshes only");
     if (m.inflow_faces > 0 && m.inflow_nvar != V)
       return fail(DG_ERR_INVALID_ARG, "the mesh has inflow faces: set the inflow state with dg_mesh_set_inflow");
+    if (m.inflow_faces > 0 && g.model == DG_GAS_NASA7 && !mixture_inflow_prims(g, m.bc.q_in, mesh->d.bc))
+      return fail(DG_ERR_INVALID_ARG, "the inflow state has no temperature: its Newton solve did not converge");
   }
   const size_t bytes = sizeof(double) * (size_t)V * m.K * m.Np;
   if (q == out || (q < out + bytes / sizeof(double) && out < q + bytes / sizeof(double)))

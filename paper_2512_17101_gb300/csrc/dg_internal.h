@@ -93,9 +93,13 @@ struct AvParams {
   double eps0, s0, kappa;
 };
 
-// Boundary data passed to the FP64 kernels by value: the conserved state of DG_BC_INFLOW faces.
+// Boundary data passed to the FP64 kernels by value: the conserved state of DG_BC_INFLOW faces
+// and, for a mixture, (1/rho, p, c) of that state at its temperature T_in (the root of
+// e(T) = e_in, solved on the host before each right-hand side of a NASA-7 gas).
 struct BcParams {
   double q_in[5 + DG_MAX_SPECIES];
+  double prim_in[3];
+  double T_in;
 };
 
 struct MeshDev {

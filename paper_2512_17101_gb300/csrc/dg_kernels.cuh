@@ -252,11 +252,17 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
       irm = prim[gM];
       pm = prim[KNp + gM];
       cm = prim[2 * KNp + gM];
-      if (is_mix(PHYS) || P >= 0) {  // mixtures have no boundary faces
+      if (P >= 0 || (is_mix(PHYS) && P != -DG_BC_INFLOW)) {
+        // a neighbour node, or a mixture's wall or outflow ghost: that keeps the node's rho, |m|,
+        // rho E and rho Y, hence its temperature, p and c (Pn is then the node itself)
         irp = prim[Pn];
         pp = prim[KNp + Pn];
         cp = prim[2 * KNp + Pn];
-      } else {  // a ghost state
+      } else if (is_mix(PHYS)) {  // a mixture's inflow ghost: q_in at its own temperature
+        irp = bc.prim_in[0];
+        pp = bc.prim_in[1];
+        cp = bc.prim_in[2];
+      } else {  // a ghost state of the perfect gas
         irp = 1.0 / qp[0];
         thermo<PHYS, V>(gp, qp, irp, 0.0, pp, cp);
       }

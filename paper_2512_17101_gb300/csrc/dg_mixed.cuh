@@ -88,9 +88,12 @@ struct MixedCase {
   int nvar;   // conserved variables: 5, or 5 + species for a mixture
   double dt;
   MixedGas gas;
-  // DG_BC_INFLOW state as a node record and a temperature pair (perfect gas)
+  // DG_BC_INFLOW state as a node record and a temperature pair (perfect gas), or as a mixture
+  // record and its low halves (p and c at the inflow temperature)
   float4 in_node[2];
   float2 in_temp;
+  float4 in_mrec[4];
+  float4 in_mlo;
   int wait_polls;  // polls per bounded mbarrier wait of the tensor-core kernels; 0 = the default
 };
 
@@ -110,6 +113,38 @@ __device__ __forceinline__ void ghost_record(int code, const float n[3], const M
   } else if (code == DG_BC_INFLOW) {
     r0 = c.in_node[0];
     r1 = c.in_node[1];
+  }
+}
+
+// The same ghost states for a mixture node: q[13] its float state, a = {rho E, p_hi, p_lo, c} and
+// lo = the low halves of momentum and energy (the node's own on entry).  A wall ghost keeps rho,
+// |m|, rho E and rho Y, hence the node's temperature, p and c: only the momentum (both halves)
+// changes.  An inflow ghost is the inflow record.
+__device__ __forceinline__ void ghost_mix_record(int code, const float n[3], const MixedCase& c, float* q, float4& a,
+                                                 float4& lo) {
+  if (code == DG_BC_SLIP_WALL) {
+    const float mn2 = 2.0f * (q[1] * n[0] + q[2] * n[1] + q[3] * n[2]);
+    const float ln2 = 2.0f * (lo.x * n[0] + lo.y * n[1] + lo.z * n[2]);
+    q[1] -= mn2 * n[0];
+    q[2] -= mn2 * n[1];
+    q[3] -= mn2 * n[2];
+    lo.x -= ln2 * n[0];
+    lo.y -= ln2 * n[1];
+    lo.z -= ln2 * n[2];
+  } else if (code == DG_BC_NOSLIP_WALL) {
+    q[1] = -q[1];
+    q[2] = -q[2];
+    q[3] = -q[3];
+    lo.x = -lo.x;
+    lo.y = -lo.y;
+    lo.z = -lo.z;
+  } else if (code == DG_BC_INFLOW) {
+    const float4 r0 = c.in_mrec[0], r2 = c.in_mrec[2], r3 = c.in_mrec[3];
+    a = c.in_mrec[1];
+    lo = c.in_mlo;
+    q[0] = r0.x; q[1] = r0.y; q[2] = r0.z; q[3] = r0.w; q[4] = a.x;
+    q[5] = r2.x; q[6] = r2.y; q[7] = r2.z; q[8] = r2.w;
+    q[9] = r3.x; q[10] = r3.y; q[11] = r3.z; q[12] = r3.w;
   }
 }
 

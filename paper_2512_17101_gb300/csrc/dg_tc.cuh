@@ -457,10 +457,13 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
       float g[V];
       if constexpr (MIX) {
         float qm[V], qp[V];
-        const float4 am = c.mrec[4 * own + 1], ap = c.mrec[4 * P + 1];  // {rho E, p_hi, p_lo, c}
+        const float4 am = c.mrec[4 * own + 1];  // {rho E, p_hi, p_lo, c}
+        float4 ap = c.mrec[4 * P + 1];
         load_mix_record(c.mrec + 4 * own, qm);
         load_mix_record(c.mrec + 4 * P, qp);
-        const float4 lm = c.mlo[own], lp = c.mlo[P];
+        const float4 lm = c.mlo[own];
+        float4 lp = c.mlo[P];
+        if (Pi < 0) mixk::ghost_mix_record(-Pi, n3, c, qp, ap, lp);
         const float dlo[4] = {lm.x - lp.x, lm.y - lp.y, lm.z - lp.z, lm.w - lp.w};
         mixk::face_term_mix<V>(qm, qp, nvar, am.y, ap.y, (am.y - ap.y) + (am.z - ap.z), am.w, ap.w, n3, dlo, g);
       } else {

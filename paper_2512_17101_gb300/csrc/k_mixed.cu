@@ -45,6 +45,23 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
     c.in_node[1] = make_float4((float)qi[4], p_hi, (float)(p - (double)p_hi), (float)(qi[0] - (double)rho_hi));
     c.in_temp = make_float2(T_hi, (float)(T - (double)T_hi));
   }
+  if (m.inflow_nvar == 5 + g.ns && g.model == DG_GAS_NASA7) {
+    // the inflow state as a mixture record: p and c of its temperature, which the host solved for
+    // before the call (BcParams::prim_in)
+    const double* qi = m.bc.q_in;
+    auto hi = [](double x) { return (float)x; };
+    auto lo = [](double x) { return (float)(x - (double)(float)x); };
+    const double p = m.bc.prim_in[1];
+    float v[16] = {};
+    v[0] = hi(qi[0]);
+    for (int j = 1; j < 5; ++j) v[j] = hi(qi[j]);
+    v[5] = hi(p);
+    v[6] = lo(p);
+    v[7] = (float)m.bc.prim_in[2];
+    for (int k = 0; k < g.ns; ++k) v[8 + k] = hi(qi[5 + k]);
+    for (int r = 0; r < 4; ++r) c.in_mrec[r] = make_float4(v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
+    c.in_mlo = make_float4(lo(qi[1]), lo(qi[2]), lo(qi[3]), lo(qi[4]));
+  }
   return c;
 }
 
