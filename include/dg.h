@@ -64,6 +64,8 @@ extern "C" {
 /* ---- limits -------------------------------------------------------------- */
 #define DG_MAX_ORDER 4
 #define DG_MAX_SPECIES 8
+#define DG_MAX_OVERINT_POINTS 12   /* Gauss-Jacobi points per collapsed direction          */
+#define DG_OVERINT_DEFAULT (-1)    /* dg_mesh_set_overint: ceil(3N/2) points per direction */
 
 typedef struct dg_mesh_s* dg_mesh;
 typedef struct dg_gas_s* dg_gas;
@@ -184,6 +186,36 @@ int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* params);
 /* eps_dev [K] (device, caller-owned) <- the element viscosities of the state q_dev (device
  * [V][K][Np]; its density is read) under the mesh's parameters.  Asynchronous on stream. */
 int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* stream);
+
+/* ---- shock capturing: over-integration ------------------------------------------------------
+ * Sec. 5.3 also names over-integration among the stabilisations of its shock cases, without
+ * writing it out.  Reading: the Euler right-hand side in weak form, with the volume integral of
+ * each test function's gradient against the flux taken by a quadrature rule finer than the
+ * nodes, so that the flux of the interpolated state is integrated, not its nodal interpolant:
+ *   rhs = sum_a M^-1 (I D_a)^T W F_a(I q) - LIFT(Fscale f*),  F_a = sum_d (dr_a/dx_d) F_d,
+ * I the nodal basis at the rule's points, W its weights, f* the pointwise Lax-Friedrichs flux of
+ * the face-node traces (the ghost states at boundary faces).  The rule is the Stroud conical
+ * product on the collapsed cube: q Gauss-Jacobi points per direction for the weights 1, (1 - b),
+ * (1 - c)^2, so q^3 points with positive weights, exact for total degree 2q - 1; ceil(3N/2)
+ * points integrate degree 3N - 1, a degree-N field's quadratic fluxes against the test
+ * functions' gradients. */
+
+/* Host only (no CUDA call): the rule with q points per direction (1..DG_MAX_OVERINT_POINTS) on the
+ * reference tetrahedron, rst_host[q^3][3] and w_host[q^3] (caller-owned); point (k q + j) q + i
+ * is the image of (a_i, b_j, c_k) under r = (1+a)(1-b)(1-c)/4 - 1, s = (1+b)(1-c)/2 - 1, t = c.
+ * Errors: DG_ERR_INVALID_ARG (NULL, q out of range). */
+int dg_tet_quadrature(int32_t q, double* rst_host, double* w_host);
+
+/* Over-integration for later dg_rhs / dg_rk_stage calls on the mesh: q points per direction,
+ * DG_OVERINT_DEFAULT for ceil(3N/2), 0 for the collocated strong form again.  Builds the tables
+ * (the nodal basis at the points, the weights, M^-1 D_a^T) from the mesh's reference nodes and
+ * copies them to the device (cudaMalloc; the mesh owns them).  Right-hand sides with it on run
+ * in the FP64 form with an inviscid perfect gas, periodic or with boundary faces, over the whole
+ * mesh; the mixed-precision and batched forms, viscosity, a mixture, artificial viscosity and
+ * element ranges are DG_ERR_UNSUPPORTED then.  Errors: DG_ERR_INVALID_ARG (host-only mesh, q
+ * below -1 or above DG_MAX_OVERINT_POINTS), DG_ERR_UNSUPPORTED (the tables and one element's
+ * work do not fit in a block's shared memory), DG_ERR_CUDA, DG_ERR_OOM. */
+int dg_mesh_set_overint(dg_mesh mesh, int32_t q);
 
 /* ---- partitioned meshes: halo exchange support -------------------------------------------
  * A partition of a mesh over several processes (the paper's multi-GPU runs exchange face data

@@ -24,6 +24,8 @@ DG_STATUS_TIMEOUT = 4
 DG_BC_SLIP_WALL, DG_BC_NOSLIP_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW = 1, 2, 3, 4
 DG_MAX_ORDER = 4
 DG_MAX_SPECIES = 8
+DG_MAX_OVERINT_POINTS = 12
+DG_OVERINT_DEFAULT = -1
 DG_GEO_STRIDE = 26
 DG_GAS_PERFECT = 0
 DG_GAS_NASA7 = 1
@@ -105,6 +107,8 @@ SIGNATURES = {
     "dg_mesh_face_pairs": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "dg_mesh_set_inflow": (c_int32, [c_void_p, c_void_p, c_int32]),
     "dg_mesh_set_av": (c_int32, [c_void_p, c_void_p]),
+    "dg_mesh_set_overint": (c_int32, [c_void_p, c_int32]),
+    "dg_tet_quadrature": (c_int32, [c_int32, c_void_p, c_void_p]),
     "dg_gather_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,
                                      c_void_p]),
     "dg_scatter_elements": (c_int32, [c_void_p, c_int32, ctypes.c_int64, c_int32, c_void_p, c_int32, c_void_p,

@@ -52,6 +52,7 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.prim);
   cudaFree(d.wq);
   cudaFree(d.diag);
+  cudaFree(d.oi_tab);
   d = dg::MeshDev();
 }
 
@@ -192,6 +193,10 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const bool prims_given = opts && opts->prims_given;
   if (prims_given && (opts->precision != DG_PREC_FP64 || g.model != DG_GAS_PERFECT))
     return fail(DG_ERR_UNSUPPORTED, "prims_given is for the FP64 form of a perfect gas");
+  if (m.oi_q > 0 && ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || g.mu > 0 || av ||
+                     (opts && opts->elem_range) || prims_given))
+    return fail(DG_ERR_UNSUPPORTED,
+                "over-integration runs in the FP64 form with an inviscid perfect gas, without AV, over the whole mesh");
   if (av) {
     if (opts && opts->precision == DG_PREC_MIXED)
       return fail(DG_ERR_UNSUPPORTED, "artificial viscosity runs in the FP64 form only");
@@ -272,6 +277,11 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
+  if (m.oi_q > 0) {
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_overint(m, g, q, out, k, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "over-integrated right-hand-side kernel");
+    return DG_OK;
+  }
   if (g.model == DG_GAS_PERFECT && !prims_given) {  // (1/rho, p, c) once per node for the next kernels
     e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_fp64(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "primitives kernel");
@@ -328,6 +338,7 @@ int dg_mesh_upload(const dg_mesh_desc* desc, dg_mesh* out) {
   std::string err;
   const int K = desc->K;
   bool ok = dg::build_ref_ops(desc->N, desc->ref_nodes, m->ops, err);
+  if (ok) m->ref_nodes.assign(desc->ref_nodes, desc->ref_nodes + 3 * m->ops.Np);
   if (ok && n_ops == 5) {  // the caller's operators replace the built ones
     const int Np = m->ops.Np, Nfp = m->ops.Nfp;
     ok = dg::check_ref_ops(desc->N, desc->ref_nodes, desc->Dr, desc->Ds, desc->Dt, desc->LIFT, desc->Fmask, err);
@@ -508,6 +519,51 @@ int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* p) {
     }
   }
   d.av = dg::AvParams{p->eps0, p->s0, p->kappa};
+  return DG_OK;
+}
+
+int dg_tet_quadrature(int32_t q, double* rst, double* w) {
+  if (!rst || !w) return fail(DG_ERR_INVALID_ARG, "NULL output");
+  std::vector<double> r, ww;
+  std::string err;
+  if (!dg::tet_quadrature(q, r, ww, err)) return fail(DG_ERR_INVALID_ARG, err);
+  std::memcpy(rst, r.data(), sizeof(double) * r.size());
+  std::memcpy(w, ww.data(), sizeof(double) * ww.size());
+  return DG_OK;
+}
+
+int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
+  if (!mesh) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  if (!mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "the mesh was built with DG_MESH_HOST_ONLY");
+  if (q < DG_OVERINT_DEFAULT || q > DG_MAX_OVERINT_POINTS)
+    return fail(DG_ERR_INVALID_ARG, "points per direction must be DG_OVERINT_DEFAULT, 0 or 1..DG_MAX_OVERINT_POINTS");
+  dg::MeshDev& d = mesh->d;
+  if (q == 0) {
+    cudaFree(d.oi_tab);
+    d.oi_tab = nullptr;
+    d.oi_q = d.oi_ng = 0;
+    return DG_OK;
+  }
+  if (q == DG_OVERINT_DEFAULT) q = (3 * d.N + 1) / 2;
+  if (!dg::overint_fits(d.N, q * q * q))
+    return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
+  dg::OverintOps o;
+  std::string err;
+  if (!dg::build_overint_ops(d.N, mesh->ref_nodes.data(), q, o, err)) return fail(DG_ERR_INVALID_ARG, err);
+  std::vector<double> tab(o.IT);
+  tab.insert(tab.end(), o.w.begin(), o.w.end());
+  tab.insert(tab.end(), o.WtT.begin(), o.WtT.end());
+  double* dev = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dev, sizeof(double) * tab.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(e, "over-integration tables");
+  }
+  cudaFree(d.oi_tab);
+  d.oi_tab = dev;
+  d.oi_q = q;
+  d.oi_ng = o.Ng;
   return DG_OK;
 }
 

@@ -30,6 +30,18 @@ struct RefOps {
 // Reference operators of order N on the given nodes (refops.cpp).
 bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err);
 
+// Over-integration of the volume term (refops.cpp): the Stroud conical-product rule with q
+// Gauss-Jacobi points per collapsed direction on the reference tetrahedron, the nodal basis at its
+// points and the weak-form operators M^-1 D_a^T.
+struct OverintOps {
+  int q = 0, Ng = 0;                // points per direction, q^3 points
+  std::vector<double> rst, w;       // [Ng][3] points, [Ng] weights (point (k q + j) q + i of (a_i, b_j, c_k))
+  std::vector<double> IT;           // [Np][Ng]: the nodal basis l_j at point g, transposed
+  std::vector<double> WtT;          // [3][Np][Np]: WtT[a][j][i] = (M^-1 D_a^T)[i][j]
+};
+bool tet_quadrature(int q, std::vector<double>& rst, std::vector<double>& w, std::string& err);
+bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::string& err);
+
 // Affine geometric factors, geo[K][DG_GEO_STRIDE] (mesh.cpp).
 bool build_geometry(int K, const double* verts, std::vector<double>& geo, std::string& err);
 
@@ -129,6 +141,10 @@ struct MeshDev {
   double* diag = nullptr;      // per-block partials of the global reductions (k_diag.cu)
   double* prim = nullptr;      // FP64 form, perfect gas: [3][K][Np] (1/rho, p, c) of the state being
                                // differentiated, written by the primitives pass before each stage
+  // over-integration (dg_mesh_set_overint; oi_q = 0: off): [Np][Ng] nodal basis at the points,
+  // [Ng] weights, [3][Np][Np] (M^-1 D_a^T)^T (OverintOps)
+  double* oi_tab = nullptr;
+  int oi_q = 0, oi_ng = 0;
 };
 
 // LSRK4 coefficients (Carpenter & Kennedy 1994, five stages, 2N storage).
@@ -150,6 +166,11 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // Artificial viscosity (k_av.cu): element viscosities of q into eps [K]; the flux eps grad q into
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
 cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
+// Over-integrated weak-form Euler right-hand side / RK stage of a perfect gas (k_oi.cu), and whether
+// its tables and one element's work for Ng points fit in a block's shared memory at order N.
+cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                               bool rk, double a, double b, double dt, cudaStream_t s);
+bool overint_fits(int N, int Ng);
 cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
 // flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.
@@ -227,6 +248,7 @@ struct dg_mesh_s {
   std::vector<int32_t> vmapP;
   std::vector<double> geo;
   std::vector<int> partner;  // [4 K]: 4 k2 + f2 of each face's partner, -1 at boundary faces
+  std::vector<double> ref_nodes;  // [Np][3] reference nodes given at upload
   int device = 0;
 };
 

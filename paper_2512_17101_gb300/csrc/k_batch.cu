@@ -216,6 +216,8 @@ int dg_batch_create(const dg_batch_case* in, int32_t ncases, int32_t flags, dg_b
     if (!c.mesh->d.ops) return fail(DG_ERR_INVALID_ARG, "case " + std::to_string(i) + ": host-only mesh");
     if (c.mesh->d.av.eps0 > 0)
       return fail(DG_ERR_UNSUPPORTED, "case " + std::to_string(i) + ": artificial viscosity runs in the FP64 form");
+    if (c.mesh->d.oi_q > 0)
+      return fail(DG_ERR_UNSUPPORTED, "case " + std::to_string(i) + ": over-integration runs in the FP64 form");
     if (c.mesh->d.inflow_faces > 0 && c.mesh->d.inflow_nvar != 5)
       return fail(DG_ERR_INVALID_ARG, "case " + std::to_string(i) +
                                           ": the mesh has inflow faces: set the inflow state with dg_mesh_set_inflow");

@@ -1,0 +1,279 @@
+// Over-integrated Euler right-hand side on tetrahedra (Sec. 5.3 names over-integration among the
+// stabilisations of its shock runs): the weak form
+//   rhs = sum_a M^-1 (I D_a)^T W F_a(I q) - LIFT(Fscale f*),  F_a = sum_d (dr_a/dx_d) F_d,
+// with I the nodal basis at the q^3 points of a Stroud conical-product rule and W its weights
+// (tables from build_overint_ops), f* the pointwise Lax-Friedrichs flux of the face-node traces.
+//
+// One persistent block per group of E elements keeps every intermediate in shared memory:
+//   1. point-parallel : the state at the points (I q), the flux there, its contravariant components
+//                       times the weight -> sF[a][v][e][g]
+//   2. face-node-par. : the Lax-Friedrichs flux of the traces (ghost states at boundary faces) -> sG
+//   3. (a, v, e, i)   : y_a = I^T (W F_a), one sum over the points per output
+//   4. (v, e, i)      : rhs = sum_a (M^-1 D_a^T) y_a - LIFT (Fscale f*), then the RK update -> HBM
+// The tables (I^T with an odd row stride, the weights, (M^-1 D_a^T)^T, LIFT^T) are loaded once per
+// block, laid out so that consecutive threads read consecutive words.  All arithmetic is FP64.
+#include <algorithm>
+
+#include "dg_kernels.cuh"
+
+namespace dg {
+namespace {
+
+using kern::GS;
+using kern::Ord;
+
+// Row stride of I^T in shared memory: the point count, made odd so that threads reading one
+// point of consecutive rows hit distinct banks.
+__host__ __device__ inline int oi_ldq(int Ng) { return Ng | 1; }
+
+struct OiLayout {
+  int ldq, tables, per_elem;  // doubles: tables, and the per-element work
+};
+
+template <int N>
+__host__ __device__ inline OiLayout oi_layout(int Ng) {
+  using O = Ord<N>;
+  OiLayout L;
+  L.ldq = oi_ldq(Ng);
+  L.tables = O::Np * L.ldq + Ng + 3 * O::Np * O::Np + O::NF * O::Np;
+  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF;
+  return L;
+}
+
+template <int N>
+inline size_t oi_smem(int Ng, int E) {
+  const OiLayout L = oi_layout<N>(Ng);
+  return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * Ord<N>::NF;
+}
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
+                                                      double* __restrict__ kreg, const double* __restrict__ tab,
+                                                      const double* __restrict__ ops_g,
+                                                      const int32_t* __restrict__ fmask_g,
+                                                      const double* __restrict__ geo_g,
+                                                      const int32_t* __restrict__ vmapP, unsigned* __restrict__ status,
+                                                      const GasParams gp, const BcParams bc, const int K,
+                                                      const int Ng, const int E, const double a, const double b,
+                                                      const double dt) {
+  using O = Ord<N>;
+  constexpr int Np = O::Np, NF = O::NF;
+  const OiLayout L = oi_layout<N>(Ng);
+  const int ldq = L.ldq;
+  extern __shared__ double smem[];
+  double* sIT = smem;                  // [Np][ldq]: l_j at point g
+  double* sW = sIT + Np * ldq;         // [Ng]
+  double* sWt = sW + Ng;               // [3][Np(j)][Np(i)]: (M^-1 D_a^T)[i][j]
+  double* sLT = sWt + 3 * Np * Np;     // [NF][Np]: LIFT[i][m] at [m][i]
+  double* sGeo = sLT + NF * Np;        // [E][GS]
+  double* sQ = sGeo + E * GS;          // [5][E][Np]
+  double* sF = sQ + 5 * E * Np;        // [3][5][E][Ng]: w_g F_a at the points
+  double* sY = sF + 15 * E * Ng;       // [3][5][E][Np]
+  double* sG = sY + 15 * E * Np;       // [5][E][NF]: Fscale f*
+  int* sFm = reinterpret_cast<int*>(sG + 5 * E * NF);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const size_t KNp = (size_t)K * Np;
+
+  for (int i = tid; i < Np * Ng; i += NT) {
+    const int j = i / Ng, g = i - j * Ng;
+    sIT[j * ldq + g] = tab[i];
+  }
+  for (int i = tid; i < Ng; i += NT) sW[i] = tab[Np * Ng + i];
+  for (int i = tid; i < 3 * Np * Np; i += NT) sWt[i] = tab[Np * Ng + Ng + i];
+  for (int i = tid; i < Np * NF; i += NT) {
+    const int r = i / NF, m = i - r * NF;
+    sLT[m * Np + r] = ops_g[3 * Np * Np + i];
+  }
+  for (int i = tid; i < NF; i += NT) sFm[i] = fmask_g[i];
+
+  const double gm1 = gp.gamma - 1.0;
+  const int groups = (K + E - 1) / E;
+  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const int e0 = grp * E, nel = min(E, K - e0), nn = nel * Np;
+    const size_t base = (size_t)e0 * Np;
+    __syncthreads();  // the tables are in, and the previous group's reads of sQ/sGeo are done
+    for (int i = tid; i < nel * GS; i += NT) sGeo[i] = geo_g[(size_t)e0 * GS + i];
+    for (int v = 0; v < 5; ++v)
+      for (int i = tid; i < nn; i += NT) sQ[(v * E + i / Np) * Np + i % Np] = q[v * KNp + base + i];
+    __syncthreads();
+
+    // ---- 1: state, flux and weighted contravariant flux at every point ----
+    for (int it = tid; it < nel * Ng; it += NT) {
+      const int e = it / Ng, g = it - e * Ng;
+      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = 0; j < Np; ++j) {
+        const double l = sIT[j * ldq + g];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qg[v] = fma(l, sQ[(v * E + e) * Np + j], qg[v]);
+      }
+      const double ir = 1.0 / qg[0];
+      const double u[3] = {qg[1] * ir, qg[2] * ir, qg[3] * ir};
+      const double p = gm1 * (qg[4] - 0.5 * (qg[1] * u[0] + qg[2] * u[1] + qg[3] * u[2]));
+      if (!(qg[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      double F[3][5];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        F[d][0] = qg[1 + d];
+        F[d][1] = qg[1] * u[d];
+        F[d][2] = qg[2] * u[d];
+        F[d][3] = qg[3] * u[d];
+        F[d][1 + d] += p;
+        F[d][4] = u[d] * (qg[4] + p);
+      }
+      const double* G = sGeo + e * GS;
+      const double w = sW[g];
+#pragma unroll
+      for (int ra = 0; ra < 3; ++ra) {
+        const double gx = w * G[3 * ra], gy = w * G[3 * ra + 1], gz = w * G[3 * ra + 2];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          sF[((ra * 5 + v) * E + e) * Ng + g] = fma(gx, F[0][v], fma(gy, F[1][v], gz * F[2][v]));
+      }
+    }
+
+    // ---- 2: Fscale f* at the face nodes (weak form), ghost states at boundary faces ----
+    for (int j = tid; j < nel * NF; j += NT) {
+      const int e = j / NF, m = j - e * NF, f = m / O::Nfp;
+      const double* G = sGeo + e * GS;
+      const double nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
+      const int own = e * Np + sFm[m];
+      const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+      const size_t Pn = P >= 0 ? (size_t)P : base + own;
+      double qm[5], qp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = sQ[(v * E + e) * Np + sFm[m]];
+        qp[v] = q[v * KNp + Pn];
+      }
+      if (P < 0) kern::ghost_state<5>(-P, qm, nx, ny, nz, bc, 5, qp);
+      const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
+      const double pm = gm1 * (qm[4] - 0.5 * irm * (qm[1] * qm[1] + qm[2] * qm[2] + qm[3] * qm[3]));
+      const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
+      if (!(qp[0] > 0.0) || !(pp > 0.0) || !(qm[0] > 0.0) || !(pm > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      const double cm = sqrt(gp.gamma * pm * irm), cp = sqrt(gp.gamma * pp * irp);
+      const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
+      const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
+      const double lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
+      double fm[5], fp[5];
+      kern::normal_flux<5>(qm, unm, pm, nx, ny, nz, 5, fm);
+      kern::normal_flux<5>(qp, unp, pp, nx, ny, nz, 5, fp);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sG[(v * E + e) * NF + m] = fs * (0.5 * ((fm[v] + fp[v]) + lam * (qm[v] - qp[v])));
+    }
+    __syncthreads();
+
+    // ---- 3: y_a = I^T (W F_a), one output per thread ----
+    for (int it = tid; it < 15 * nel * Np; it += NT) {
+      const int i = it % Np, rest = it / Np, e = rest % nel, av = rest / nel;
+      const double* F = sF + (av * E + e) * Ng;
+      const double* l = sIT + i * ldq;
+      double y0 = 0.0, y1 = 0.0;
+      int g = 0;
+      for (; g + 1 < Ng; g += 2) {
+        y0 = fma(l[g], F[g], y0);
+        y1 = fma(l[g + 1], F[g + 1], y1);
+      }
+      if (g < Ng) y0 = fma(l[g], F[g], y0);
+      sY[(av * E + e) * Np + i] = y0 + y1;
+    }
+    __syncthreads();
+
+    // ---- 4: rhs = sum_a (M^-1 D_a^T) y_a - LIFT (Fscale f*), then the output or RK update ----
+    for (int it = tid; it < 5 * nel * Np; it += NT) {
+      const int i = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      double acc = 0.0;
+#pragma unroll
+      for (int ra = 0; ra < 3; ++ra) {
+        const double* y = sY + ((ra * 5 + v) * E + e) * Np;
+        const double* W = sWt + ra * Np * Np + i;
+#pragma unroll 4
+        for (int j = 0; j < Np; ++j) acc = fma(W[j * Np], y[j], acc);
+      }
+      const double* gq = sG + (v * E + e) * NF;
+#pragma unroll 4
+      for (int m = 0; m < NF; ++m) acc = fma(-sLT[m * Np + i], gq[m], acc);
+      const size_t gi = v * KNp + base + e * Np + i;
+      if (RK) {
+        const double kk = (a != 0.0 ? a * kreg[gi] : 0.0) + dt * acc;
+        kreg[gi] = kk;
+        out[gi] = fma(b, kk, sQ[(v * E + e) * Np + i]);
+      } else {
+        out[gi] = acc;
+      }
+    }
+  }
+}
+
+// Elements per block and blocks per SM: two blocks of at least two elements each if they fit in
+// an SM's shared memory, else one block with as many elements as fit; 0 when one element does not.
+template <int N>
+bool oi_config(int Ng, int& E, int& bps, size_t& smem) {
+  int dev = 0, per_sm = 0, per_block = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const OiLayout L = oi_layout<N>(Ng);
+  for (bps = 2; bps >= 1; --bps) {
+    const size_t budget = std::min((size_t)per_block, (size_t)per_sm / bps - 1024);
+    const size_t fixed = sizeof(double) * L.tables + sizeof(int) * Ord<N>::NF;
+    if (budget <= fixed) continue;
+    E = (int)((budget - fixed) / (sizeof(double) * L.per_elem));
+    E = std::min(E, 64);
+    if (E >= (bps == 2 ? 2 : 1)) {
+      smem = oi_smem<N>(Ng, E);
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int N, bool RK>
+cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, double a,
+                        double b, double dt, cudaStream_t s) {
+  int E = 0, bps = 0;
+  size_t smem = 0;
+  if (!oi_config<N>(m.oi_ng, E, bps, smem)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(rhs_oi_kernel<N, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int NT = bps == 2 ? 256 : 512;
+  const int groups = (m.K + E - 1) / E;
+  const int blocks = std::min(groups, sms * bps);
+  rhs_oi_kernel<N, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.ops, m.fmask, m.geo, m.vmapP, m.status, g,
+                                                 m.bc, m.K, m.oi_ng, E, a, b, dt);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool overint_fits(int N, int Ng) {
+  int E = 0, bps = 0;
+  size_t smem = 0;
+  switch (N) {
+    case 1: return oi_config<1>(Ng, E, bps, smem);
+    case 2: return oi_config<2>(Ng, E, bps, smem);
+    case 3: return oi_config<3>(Ng, E, bps, smem);
+    case 4: return oi_config<4>(Ng, E, bps, smem);
+    default: return false;
+  }
+}
+
+cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
+                               bool rk, double a, double b, double dt, cudaStream_t s) {
+  switch (m.N) {
+#define DG_CASE(NN) \
+  case NN:          \
+    return rk ? launch_oi_t<NN, true>(m, g, q, out, k, a, b, dt, s) : launch_oi_t<NN, false>(m, g, q, out, k, a, b, dt, s);
+    DG_CASE(1)
+    DG_CASE(2)
+    DG_CASE(3)
+    DG_CASE(4)
+#undef DG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dg

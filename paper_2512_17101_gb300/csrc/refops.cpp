@@ -25,6 +25,7 @@
 // into the constants); a and b are set to -1 where the collapse is singular.
 // Faces: 0: t = -1 (params r,s), 1: s = -1 (r,t), 2: r+s+t = -1 (s,t),
 // 3: r = -1 (s,t); face nodes are listed in increasing volume-node order.
+#include <cfloat>
 #include <cmath>
 
 #include "dg_internal.h"
@@ -117,7 +118,8 @@ void face_params(int f, ld r, ld s, ld t, ld& x, ld& y) {
 // Normalised Jacobi polynomial P~_n^(al,be)(x): the three-term recurrence of
 // the classical P_n^(al,be), divided by sqrt of
 // gamma_n = 2^(al+be+1) / (2n+al+be+1) * (n+al)! (n+be)! / ((n+al+be)! n!).
-ld jacobi(ld x, int al, int be, int n) {
+// The classical P_n^(al,be)(x) by its three-term recurrence.
+ld jacobi_classical(ld x, int al, int be, int n) {
   ld p0 = 1, p1 = 0.5L * ((al + be + 2) * x + (al - be));
   ld pn = n == 0 ? p0 : p1;
   for (int k = 2; k <= n; ++k) {
@@ -130,9 +132,58 @@ ld jacobi(ld x, int al, int be, int n) {
     p0 = p1;
     p1 = pn;
   }
+  return pn;
+}
+
+ld jacobi(ld x, int al, int be, int n) {
   const ld gam = ipow(2, al + be + 1) / (2 * n + al + be + 1) * factorial(n + al) * factorial(n + be) /
                  (factorial(n + al + be) * factorial(n));
-  return pn / sqrtl(gam);
+  return jacobi_classical(x, al, be, n) / sqrtl(gam);
+}
+
+// q-point Gauss-Jacobi rule on [-1, 1] for the weight (1 - x)^al: the roots of P_q^(al,0), found in
+// increasing order by Newton from Chebyshev guesses with the roots found so far deflated
+// (P'_q^(al,0) = (q + al + 1)/2 P_(q-1)^(al+1,1)), and the weights 2^(al+1) / ((1 - x^2) P'_q(x)^2)
+// (the Gauss-Jacobi weights, whose Gamma-function factor is 1 when the second exponent is 0).
+bool gauss_jacobi(int q, int al, std::vector<ld>& x, std::vector<ld>& w) {
+  x.assign(q, 0);
+  w.assign(q, 0);
+  for (int k = 0; k < q; ++k) {
+    ld r = -cosl((2 * k + 1) * 3.14159265358979323846264338327950288L / (2 * q));
+    if (k > 0) r = 0.5L * (r + x[k - 1]);
+    for (int it = 0; it < 100; ++it) {
+      const ld p = jacobi_classical(r, al, 0, q);
+      const ld dp = 0.5L * (q + al + 1) * jacobi_classical(r, al + 1, 1, q - 1);
+      ld defl = 0;
+      for (int j = 0; j < k; ++j) defl += 1 / (r - x[j]);
+      const ld delta = p / (dp - p * defl);
+      r -= delta;
+      if (fabsl(delta) <= 1e-30L + 4 * LDBL_EPSILON * fabsl(r)) break;
+    }
+    x[k] = r;
+  }
+  ld total = 0;
+  for (int k = 0; k < q; ++k) {
+    const ld dp = 0.5L * (q + al + 1) * jacobi_classical(x[k], al + 1, 1, q - 1);
+    w[k] = ipow(2, al + 1) / ((1 - x[k] * x[k]) * dp * dp);
+    total += w[k];
+    if (!(x[k] > -1 && x[k] < 1) || (k > 0 && !(x[k] > x[k - 1]))) return false;
+  }
+  return fabsl(total - ipow(2, al + 1) / (al + 1)) <= 1e-14L;  // the integral of the weight
+}
+
+// Exponents (a, b, c), a + b + c <= N, of the monomial basis r^a s^b t^c in the library's order.
+void monomial_exponents(int N, std::vector<int>& ea, std::vector<int>& eb, std::vector<int>& ec) {
+  ea.clear();
+  eb.clear();
+  ec.clear();
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; a + b <= N; ++b)
+      for (int c = 0; a + b + c <= N; ++c) {
+        ea.push_back(a);
+        eb.push_back(b);
+        ec.push_back(c);
+      }
 }
 
 ld ortho_tri(int i, int j, ld x, ld y) {
@@ -159,13 +210,7 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err) {
   const int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   const int Nfp = (N + 1) * (N + 2) / 2;
   std::vector<int> ea, eb, ec;
-  for (int a = 0; a <= N; ++a)
-    for (int b = 0; a + b <= N; ++b)
-      for (int c = 0; a + b + c <= N; ++c) {
-        ea.push_back(a);
-        eb.push_back(b);
-        ec.push_back(c);
-      }
+  monomial_exponents(N, ea, eb, ec);
   std::vector<ld> V(Np * Np), Vr(Np * Np, 0), Vs(Np * Np, 0), Vt(Np * Np, 0);
   for (int i = 0; i < Np; ++i) {
     ld r = nodes[3 * i], s = nodes[3 * i + 1], t = nodes[3 * i + 2];
@@ -272,6 +317,91 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err) {
         for (int j = 0; j < Np; ++j) out.modal.push_back((double)Voi[m * Np + j]);
         out.ntop += pass;
       }
+  return true;
+}
+
+bool tet_quadrature(int q, std::vector<double>& rst, std::vector<double>& w, std::string& err) {
+  if (q < 1 || q > DG_MAX_OVERINT_POINTS) {
+    err = "points per direction must be in 1.." + std::to_string(DG_MAX_OVERINT_POINTS);
+    return false;
+  }
+  std::vector<ld> a, wa, b, wb, c, wc;
+  if (!gauss_jacobi(q, 0, a, wa) || !gauss_jacobi(q, 1, b, wb) || !gauss_jacobi(q, 2, c, wc)) {
+    err = "Gauss-Jacobi roots did not converge";
+    return false;
+  }
+  const int Ng = q * q * q;
+  rst.assign(3 * Ng, 0.0);
+  w.assign(Ng, 0.0);
+  for (int k = 0; k < q; ++k)
+    for (int j = 0; j < q; ++j)
+      for (int i = 0; i < q; ++i) {
+        const int g = (k * q + j) * q + i;
+        rst[3 * g] = (double)(0.25L * (1 + a[i]) * (1 - b[j]) * (1 - c[k]) - 1);
+        rst[3 * g + 1] = (double)(0.5L * (1 + b[j]) * (1 - c[k]) - 1);
+        rst[3 * g + 2] = (double)c[k];
+        w[g] = (double)(wa[i] * wb[j] * wc[k] / 8);
+      }
+  return true;
+}
+
+bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::string& err) {
+  if (N < 1 || N > DG_MAX_ORDER) {
+    err = "order must be in 1.." + std::to_string(DG_MAX_ORDER);
+    return false;
+  }
+  std::vector<double> rst, w;
+  if (!tet_quadrature(q, rst, w, err)) return false;
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Ng = q * q * q;
+  std::vector<int> ea, eb, ec;
+  monomial_exponents(N, ea, eb, ec);
+  // monomial Vandermonde at the nodes (and its derivatives) and at the points
+  std::vector<ld> V(Np * Np), Vd[3], Vq((size_t)Ng * Np);
+  for (int d = 0; d < 3; ++d) Vd[d].assign(Np * Np, 0);
+  for (int i = 0; i < Np; ++i) {
+    const ld r = nodes[3 * i], s = nodes[3 * i + 1], t = nodes[3 * i + 2];
+    for (int m = 0; m < Np; ++m) {
+      const int a = ea[m], b = eb[m], c = ec[m];
+      V[i * Np + m] = ipow(r, a) * ipow(s, b) * ipow(t, c);
+      if (a) Vd[0][i * Np + m] = a * ipow(r, a - 1) * ipow(s, b) * ipow(t, c);
+      if (b) Vd[1][i * Np + m] = b * ipow(r, a) * ipow(s, b - 1) * ipow(t, c);
+      if (c) Vd[2][i * Np + m] = c * ipow(r, a) * ipow(s, b) * ipow(t, c - 1);
+    }
+  }
+  for (int g = 0; g < Ng; ++g)
+    for (int m = 0; m < Np; ++m)
+      Vq[(size_t)g * Np + m] = ipow(rst[3 * g], ea[m]) * ipow(rst[3 * g + 1], eb[m]) * ipow(rst[3 * g + 2], ec[m]);
+  std::vector<ld> Vinv = V;
+  if (!invert(Vinv, Np)) {
+    err = "reference nodes are not unisolvent for this order";
+    return false;
+  }
+  // M^-1 = Vo Vo^T from the orthonormal basis, as for LIFT
+  std::vector<ld> Vo(Np * Np);
+  for (int n = 0; n < Np; ++n) {
+    const ld r = nodes[3 * n], s = nodes[3 * n + 1], t = nodes[3 * n + 2];
+    for (int m = 0; m < Np; ++m) Vo[n * Np + m] = ortho_tet(ea[m], eb[m], ec[m], r, s, t);
+  }
+  const std::vector<ld> Minv = matmul(Vo, transpose(Vo, Np, Np), Np, Np, Np);
+  const std::vector<ld> I = matmul(Vq, Vinv, Ng, Np, Np);  // [Ng][Np]: the nodal basis at the points
+  out.q = q;
+  out.Ng = Ng;
+  out.rst = rst;
+  out.w = w;
+  out.IT.assign((size_t)Np * Ng, 0.0);
+  for (int g = 0; g < Ng; ++g)
+    for (int j = 0; j < Np; ++j) out.IT[(size_t)j * Ng + g] = (double)I[(size_t)g * Np + j];
+  // WtT[a][j][i] = (M^-1 D_a^T)[i][j] = sum_k Minv[i][k] D_a[j][k]
+  out.WtT.assign(3 * Np * Np, 0.0);
+  for (int a = 0; a < 3; ++a) {
+    const std::vector<ld> D = matmul(Vd[a], Vinv, Np, Np, Np);
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < Np; ++i) {
+        ld acc = 0;
+        for (int k = 0; k < Np; ++k) acc += Minv[i * Np + k] * D[j * Np + k];
+        out.WtT[(a * Np + j) * Np + i] = (double)acc;
+      }
+  }
   return true;
 }
 

@@ -152,6 +152,11 @@ class Mesh:
         check(load().dg_av_viscosity(self.handle, _dptr(q, torch.float64, "q"), _dptr(eps, torch.float64, "eps"),
                                      _stream_ptr(stream)))
 
+    def set_overint(self, q=capi.DG_OVERINT_DEFAULT):
+        """Over-integrated volume term for later right-hand sides: q Gauss-Jacobi points per
+        collapsed direction (the library's default for DG_OVERINT_DEFAULT, 0 turns it off)."""
+        check(load().dg_mesh_set_overint(self.handle, int(q)))
+
     def set_timing(self, enable=True):
         check(load().dg_mesh_set_timing(self.handle, int(enable)))
 
@@ -263,6 +268,15 @@ def dg_rk_stage(mesh: Mesh, gas: Gas, stage, dt, q_in, q_out, k, T_io=None, opts
     check(load().dg_rk_stage(mesh.handle, gas.handle, int(stage), float(dt), _dptr(q_in, torch.float64, "q_in"),
                              _dptr(q_out, torch.float64, "q_out"), _dptr(k, torch.float64, "k"),
                              _dptr(T_io, torch.float64, "T_io"), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def dg_tet_quadrature(q):
+    """(points [q^3][3], weights [q^3]) of the library's Stroud rule on the reference tetrahedron
+    (host only, no GPU)."""
+    pts = np.zeros((q ** 3, 3))
+    w = np.zeros(q ** 3)
+    check(load().dg_tet_quadrature(int(q), _hptr(pts), _hptr(w)))
+    return pts, w
 
 
 def dg_lsrk4_coefficients():

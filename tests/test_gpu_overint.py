@@ -1,0 +1,157 @@
+"""GPU parity of over-integration on tetrahedra: the weak-form Euler right-hand side with the volume
+term on the Stroud rule (dg_mesh_set_overint), through the C ABI, against oracle/overint.py at
+1e-11 per conserved variable.  Orders 1-4, periodic and walled / inflow / outflow boxes, the
+default and other point counts, ragged last element groups and blocks that loop over several
+groups, two RK4 steps, switching it off, and the combinations the library refuses."""
+
+import numpy as np
+import pytest
+
+import oracle.boundary as bd
+import oracle.overint as oi
+from oracle.euler import rhs_strong
+from oracle.lsrk import lsrk4_step
+from oracle.thermo import PerfectGas
+from tests._gpu import rel_err, torch_cuda
+from tests._oracle_case import bc_disc, box_disc
+from workloads import equispaced_tet_nodes, isentropic_vortex, uniform_perturbation
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+GAS = PerfectGas(1.4, 1.0)
+SLIP, NOSLIP, INFLOW, OUTFLOW = bd.SLIP_WALL, bd.NOSLIP_WALL, bd.INFLOW, bd.OUTFLOW
+SIDES = {
+    "periodic": None,
+    "in_out_x_walls_y": {(0, 0): INFLOW, (0, 1): OUTFLOW, (1, 0): SLIP, (1, 1): NOSLIP},
+}
+
+
+def _state(rho, u, v, w, p):
+    E = p / (GAS.gamma - 1) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E])
+
+
+Q_IN = _state(np.array(1.1), np.array(1.8), np.array(0.05), np.array(-0.02), np.array(0.75))
+
+
+def _smooth(xyz, seed=0):
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    rho = 1.0 + 0.2 * np.sin(2.1 * x + 0.7 * y) * np.cos(1.3 * z)
+    u = 1.5 + 0.3 * np.cos(1.7 * y + 0.4 * z)
+    v = 0.2 * np.sin(2.3 * x) * np.sin(0.9 * z + 0.2)
+    w = 0.1 + 0.2 * np.cos(1.1 * x + 1.9 * y)
+    p = 1.0 / 1.4 + 0.2 * np.sin(0.8 * x - 1.4 * z)
+    return uniform_perturbation(_state(rho, u, v, w, p), 1e-3, seed=seed)
+
+
+def _setup(n, N, sides, q=None):
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    d = box_disc(n, N) if sides is None else bc_disc(n, N, sides)
+    mesh = dg.Mesh(d.vertices, d.period, N, equispaced_tet_nodes(N), face_bc=d.face_bc)
+    if sides and any(c == INFLOW for c in sides.values()):
+        mesh.set_inflow(Q_IN)
+    mesh.set_overint(-1 if q is None else q)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    return torch, dg, d, mesh, gas
+
+
+def _want(d, q0, Q=None):
+    return oi.rhs_overint(d.ref, d.geo, d.conn, q0, GAS, Q=Q, q_in=Q_IN)
+
+
+@pytest.mark.parametrize("name", list(SIDES))
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_overint_rhs(N, name):
+    n = 3 if SIDES[name] is None else (3, 2, 2)
+    torch, dg, d, mesh, gas = _setup(n, N, SIDES[name])
+    q0 = _smooth(d.xyz)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL
+    assert mesh.status() == 0
+
+
+@pytest.mark.parametrize("N,Q", [(1, 1), (2, 2), (2, 4), (3, 6), (4, 7)])
+def test_overint_other_point_counts(N, Q):
+    torch, dg, d, mesh, gas = _setup((3, 2, 2), N, SIDES["in_out_x_walls_y"], q=Q)
+    q0 = _smooth(d.xyz, seed=2)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0, Q=Q)) <= TOL
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_overint_many_groups_per_block(N):
+    """Enough elements that every persistent block loops over several element groups."""
+    torch, dg, d, mesh, gas = _setup(6, N, None)
+    q0 = uniform_perturbation(isentropic_vortex(d.xyz, 0.0), 1e-3, seed=5)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL
+
+
+def test_overint_rk4_steps():
+    torch, dg, d, mesh, gas = _setup((3, 3, 2), 3, SIDES["in_out_x_walls_y"])
+    q0 = _smooth(d.xyz, seed=3)
+    dt = 1e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.lsrk4_step(mesh, gas, q, dt, steps=2)
+    f = lambda u: _want(d, u)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+    assert mesh.status() == 0
+
+
+def test_overint_off_is_the_collocated_form():
+    torch, dg, d, mesh, gas = _setup(3, 2, None)
+    q0 = _smooth(d.xyz, seed=4)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    mesh.set_overint(0)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), rhs_strong(d.ref, d.geo, d.conn, q0, GAS)) <= TOL
+    mesh.set_overint(-1)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL
+
+
+def test_overint_flags_a_nonphysical_state():
+    torch, dg, d, mesh, gas = _setup(2, 2, None)
+    q0 = _smooth(d.xyz)
+    q0[4, 3, :] = 0.01  # energy below the kinetic energy in one element: p < 0 at its points
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    from paper_2512_17101_gb300 import capi
+    assert mesh.status() & capi.DG_STATUS_NONPHYSICAL
+
+
+def test_overint_refusals():
+    """Viscosity, the mixed form, artificial viscosity, element ranges and point counts whose tables
+    do not fit are refused; the mesh keeps working."""
+    from paper_2512_17101_gb300 import capi
+    torch, dg, d, mesh, gas = _setup(2, 4, None)
+    q0 = _smooth(d.xyz)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    visc = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=1e-3, Pr=0.71)
+    with pytest.raises(capi.DGError):
+        dg.dg_rhs(mesh, visc, q, rhs)
+    with pytest.raises(capi.DGError):
+        dg.dg_rhs(mesh, gas, q, rhs, opts=dg._opts(precision=capi.DG_PREC_MIXED))
+    with pytest.raises(capi.DGError):
+        dg.dg_rhs(mesh, gas, q, rhs, opts=dg._opts(elems=(0, 6)))
+    with pytest.raises(capi.DGError):
+        mesh.set_overint(capi.DG_MAX_OVERINT_POINTS)  # N = 4: 1728 points do not fit
+    with pytest.raises(capi.DGError):
+        mesh.set_overint(-2)
+    mesh.set_av(0.1)
+    with pytest.raises(capi.DGError):
+        dg.dg_rhs(mesh, gas, q, rhs)
+    mesh.set_av(0.0)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL
