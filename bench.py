@@ -601,6 +601,9 @@ def gpu_arm(args, cfg, world, rank, local):
         bnd = boundary_form(args, local, periodic)
         avf = av_form(args, local)
         mixns = mixture_ns_form(args, local)
+    oif = None
+    if rank == 0 and not args.no_overint:
+        oif = overint_form(args, local)
     partf = None
     if rank == 0 and not args.no_partitioned:
         partf = partitioned_form(args, local, runs["fp64"]["ms"] if cfg.name == "ns_viscous" else None)
@@ -616,9 +619,80 @@ def gpu_arm(args, cfg, world, rank, local):
             "learned_form": learned, "batched_form": batched, "hex_form": hexf,
             "paper_context": PAPER_CONTEXT,
             "hex_advection_form": hexadv, "hex_shock_form": hexshock, "boundary_form": bnd, "av_form": avf, "mixture_ns_form": mixns,
-            "partitioned_form": partf, "kernel_src": {"fp64": src, "mixed": src_mixed}, "impl": "gpu",
+            "partitioned_form": partf, "overint_form": oif, "kernel_src": {"fp64": src, "mixed": src_mixed},
+            "impl": "gpu",
         }
         print(json.dumps(line), flush=True)
+
+
+def overint_flops_per_element(N, Q):
+    """FP64 flops of one element in the over-integrated right-hand side (Ng = Q^3 points): per
+    point, the 5 fields interpolated (10 Np), the flux (30) and its weighted contravariant
+    components (93); the contraction back to the nodes (30 Np Ng); the weak-form operators and
+    LIFT (10 Np (3 Np + 4 Nfp)); about 100 per face node for the Lax-Friedrichs flux."""
+    Np, Nfp, Ng = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2, Q ** 3
+    return Ng * (10 * Np + 123) + 30 * Np * Ng + 10 * Np * (3 * Np + 4 * Nfp) + 100 * 4 * Nfp
+
+
+def overint_form(args, local):
+    """Over-integration (weak form, Stroud rule with ceil(3N/2) points per collapsed direction) on the
+    periodic Euler vortex with the main workload's mesh and order (24^3 x 6 tets, N = 3): FP64 RK4
+    steps with CUDA events, against the collocated strong form on the same mesh, and the kernel's
+    FP64 rate from its flop count."""
+    import torch
+    from paper_2512_17101_gb300 import dg
+    from workloads import box_mesh, equispaced_tet_nodes, isentropic_vortex, physical_nodes, uniform_perturbation
+
+    n, N = 24, 3
+    dev = torch.device("cuda", local)
+    v, per = box_mesh(n, 1.0)
+    nodes = equispaced_tet_nodes(N)
+    mesh = dg.Mesh(v, per, N, nodes)
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
+    q0 = torch.tensor(uniform_perturbation(isentropic_vortex(physical_nodes(v, nodes), 0.0), 1e-3, seed=0),
+                      device=dev)
+    K, Np = v.shape[0], nodes.shape[0]
+    dt = 1e-4
+    work = (torch.empty_like(q0), torch.zeros_like(q0))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(1, min(args.steps, 10))
+    out = {}
+    for label, oq in (("collocated", 0), ("overint", -1)):
+        mesh.set_overint(oq)
+        q = q0.clone()
+        for _ in range(max(3, args.warmup)):
+            dg.lsrk4_step(mesh, gas, q, dt, steps=1, work=work)
+        q.copy_(q0)
+        total = 0.0
+        mesh.kernel_times(reset=True)
+        mesh.set_timing(True)
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dg.lsrk4_step(mesh, gas, q, dt, steps=1, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        mesh.set_timing(False)
+        kt = mesh.kernel_times(reset=True)
+        if mesh.status() != 0:
+            raise SystemExit("status flags set in the over-integration run")
+        ms = total / steps
+        out[label] = {"ms_per_step": ms, "value": K * Np * 5 / (ms * 1e-3),
+                      "rhs_avg_ms": kt["rhs"][0] / kt["rhs"][1] if kt["rhs"][1] else None}
+    Q = (3 * N + 1) // 2
+    flops = overint_flops_per_element(N, Q) * K
+    ach = flops / (out["overint"]["rhs_avg_ms"] * 1e-3) / 1e12
+    return {
+        "workload": f"periodic Euler isentropic vortex + U(+-1e-3), {n}^3 x 6 = {K} tets, N = {N}, FP64",
+        "points_per_direction": Q, "points_per_element": Q ** 3, "unit": "DOF-updates/s",
+        "collocated": out["collocated"], "overint": out["overint"],
+        "slowdown": out["overint"]["ms_per_step"] / out["collocated"]["ms_per_step"],
+        "roofline": {"bound": "alu", "kernel": "rhs_oi_kernel", "flops_per_launch": flops, "achieved": ach,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                     "peak_kind": "nominal FP64"},
+    }
 
 
 def learned_form(args, local):
@@ -1350,6 +1424,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--no-hex", action="store_true", help="skip the tensor-product hexahedron section")
+    ap.add_argument("--no-overint", action="store_true", help="skip the over-integration section")
     ap.add_argument("--no-boundary", action="store_true", help="skip the wall-bounded channel, artificial-viscosity and viscous-mixture sections")
     ap.add_argument("--no-partitioned", action="store_true", help="skip the two-partition section")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
