@@ -145,14 +145,11 @@ def viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None):
     return viscous_flux(q, w[4], grad, mu, kappa)
 
 
-def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong", Fv=None):
-    """Navier-Stokes right-hand side [5][K][Np] (BR1, central fluxes) with boundary faces.  Fv: the
-    viscous flux of the first BR1 pass (viscous_flux_bc), computed here when not given (a
-    partitioned run passes it with its halo filled from the owners)."""
-    p, c = gas.pressure_sound_speed(q)
+def ns_face_flux(ref, geo, conn, q, gas, Fv, q_in=None):
+    """Normal numerical flux n.G* [5][K][4 Nfp] of G = F - Fv at the face nodes: Lax-Friedrichs for
+    the Euler part and the central viscous flux, with the exterior viscous fluxes of the boundary
+    conditions; also n, q-, p- and the interior viscous flux FvM [3][5][K][4 Nfp]."""
     n, qM, qP = _traces(conn, geo, ref, q, q_in)
-    if Fv is None:
-        Fv = viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in)
     FvM = np.stack([gather(Fv[d], conn.vmapM) for d in range(3)])
     nvM = normal_flux(FvM, n)  # [5][K][4 Nfp]: 0, traction t, energy flux e
     nvP = normal_flux(np.stack([gather(Fv[d], conn.vmapP) for d in range(3)]), n)
@@ -165,6 +162,17 @@ def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong", Fv=None)
     pM, cM = gas.pressure_sound_speed(qM)
     pP, cP = gas.pressure_sound_speed(qP)
     fstar = lax_friedrichs(qM, qP, pM, pP, cM, cP, n) - 0.5 * (nvM + nvP)
+    return fstar, n, qM, pM, FvM
+
+
+def rhs_ns_bc(ref, geo, conn, q, gas, mu, Pr, q_in=None, form="strong", Fv=None):
+    """Navier-Stokes right-hand side [5][K][Np] (BR1, central fluxes) with boundary faces.  Fv: the
+    viscous flux of the first BR1 pass (viscous_flux_bc), computed here when not given (a
+    partitioned run passes it with its halo filled from the owners)."""
+    p, c = gas.pressure_sound_speed(q)
+    if Fv is None:
+        Fv = viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in)
+    fstar, n, qM, pM, FvM = ns_face_flux(ref, geo, conn, q, gas, Fv, q_in)
     G = euler_flux(q, p) - Fv
     if form == "strong":
         GM = euler_flux(qM, pM) - FvM

@@ -16,6 +16,13 @@ interpolant:
 The faces keep the collocated weak-form term -LIFT(Fscale f*) with the pointwise Lax-Friedrichs
 flux f* of the face-node traces, and boundary faces take the ghost states of oracle/boundary.py.
 
+Navier-Stokes: the whole flux G = F - Fv is integrated on the rule, with the nodal BR1 viscous flux
+Fv (oracle/boundary.py viscous_flux_bc) interpolated to the points.  Fv is a degree-N field, so its
+part of the integral is exact and equals the collocated weak-form term; the convective part is the
+over-integrated one.  The faces take the weak-form normal flux n.G* of the collocated
+Navier-Stokes right-hand side (Lax-Friedrichs minus the central viscous flux, with the walls'
+exterior viscous fluxes).
+
 Rule: the Stroud conical product on the collapsed cube (a, b, c) in [-1, 1]^3,
     r = (1+a)(1-b)(1-c)/4 - 1,  s = (1+b)(1-c)/2 - 1,  t = c,   dr ds dt = (1-b)(1-c)^2/8 da db dc,
 with q Gauss-Jacobi points per direction for the weights 1, (1-b) and (1-c)^2 (scipy's roots),
@@ -32,7 +39,7 @@ import mpmath
 import numpy as np
 from scipy.special import roots_jacobi
 
-from .boundary import _traces
+from .boundary import _traces, ns_face_flux, viscous_flux_bc
 from .euler import euler_flux, lax_friedrichs, lift
 from .refelem import _DPS, _monomials3, _to_np
 
@@ -72,13 +79,16 @@ def interpolation(ref, q):
     return _interp_cached(tuple(np.asarray(ref.nodes, dtype=np.float64).ravel()), ref.N, q)
 
 
-def overint_volume(ref, geo, q, gas, Q):
-    """sum_a M^-1 (I D_a)^T W F_a(I q) [V][K][Np] with Q points per collapsed direction."""
+def overint_volume(ref, geo, q, gas, Q, Fv=None):
+    """sum_a M^-1 (I D_a)^T W G_a [V][K][Np] with Q points per collapsed direction, G = F(I q), or
+    F(I q) - I Fv with a nodal viscous flux Fv [3][5][K][Np]."""
     Iq = interpolation(ref, Q)
     _, w = tet_rule(Q)
     qg = np.einsum("gj,vkj->vkg", Iq, q)  # the state at the points
     p, _ = gas.pressure_sound_speed(qg)
     F = euler_flux(qg, p)  # [3][V][K][Ng]
+    if Fv is not None:
+        F = F - np.einsum("gj,dvkj->dvkg", Iq, Fv)
     drdx = geo.drdx()  # [a][d][K]
     Minv = np.linalg.inv(ref.M)
     out = np.zeros(q.shape)
@@ -99,3 +109,14 @@ def rhs_overint(ref, geo, conn, q, gas, Q=None, q_in=None):
     fstar = lax_friedrichs(qM, qP, pM, pP, cM, cP, n)
     return overint_volume(ref, geo, q, gas, Q) - lift(ref, geo, fstar)
 
+
+def rhs_overint_ns(ref, geo, conn, q, gas, mu, Pr, Q=None, q_in=None, Fv=None):
+    """Weak-form Navier-Stokes right-hand side [5][K][Np] of a perfect gas (BR1, central viscous
+    fluxes) with the volume integral of G = F - Fv on the rule (default ceil(3N/2) points per
+    collapsed direction); periodic or boundary faces.  Fv: the nodal viscous flux of the first BR1
+    pass, computed here when not given."""
+    Q = default_points(ref.N) if Q is None else Q
+    if Fv is None:
+        Fv = viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in)
+    fstar = ns_face_flux(ref, geo, conn, q, gas, Fv, q_in)[0]
+    return overint_volume(ref, geo, q, gas, Q, Fv) - lift(ref, geo, fstar)

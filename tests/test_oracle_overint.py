@@ -11,7 +11,10 @@ fixes:
 * periodic meshes conserve mass, momentum and energy; a uniform flow tangent to slip walls with a
   matching inflow stays steady;
 * the right-hand side of the translating isentropic vortex converges to its exact time derivative
-  at order >= N - 0.9 (the same consistency bar as the collocated form).
+  at order >= N - 0.9 (the same consistency bar as the collocated form);
+* Navier-Stokes: with a degree-N convective flux it is the collocated Navier-Stokes right-hand side
+  (walls included); periodic boxes conserve mass, momentum and energy and boxes closed by no-slip
+  walls mass and energy; the rest state between no-slip walls is steady.
 Planted mistakes in the oracle must break at least one pin."""
 
 import dataclasses
@@ -28,7 +31,7 @@ from tests._oracle_case import Disc, bc_disc, box_disc
 from workloads import box_mesh, isentropic_vortex, uniform_perturbation
 
 GAS = PerfectGas(1.4, 1.0)
-SLIP, INFLOW, OUTFLOW = bd.SLIP_WALL, bd.INFLOW, bd.OUTFLOW
+SLIP, NOSLIP, INFLOW, OUTFLOW = bd.SLIP_WALL, bd.NOSLIP_WALL, bd.INFLOW, bd.OUTFLOW
 
 
 def _rel(a, b):
@@ -139,6 +142,62 @@ def test_uniform_flow_between_walls_is_steady():
     assert _freestream_holds(3)
 
 
+# --- Navier-Stokes ---------------------------------------------------------------------------------------
+
+MU, PR = 2e-2, 0.71
+WALLS = {(1, 0): NOSLIP, (1, 1): SLIP}
+
+
+def _ns_poly_flux_is_collocated(N=3):
+    """Uniform rho and u with a degree-N pressure between a no-slip and a slip wall: the convective
+    flux is a degree-N polynomial and the viscous one a nodal field, so over-integration gives the
+    collocated Navier-Stokes right-hand side."""
+    d = bc_disc((2, 2, 2), N, WALLS)
+    x, y, z = d.xyz[..., 0], d.xyz[..., 1], d.xyz[..., 2]
+    one = np.ones_like(x)
+    p = 1.0 + 0.1 * (x - 0.5) ** N + 0.05 * y * z
+    q = _state(one, 0.3 * one, -0.2 * one, 0.1 * one, p)
+    a = oi.rhs_overint_ns(d.ref, d.geo, d.conn, q, GAS, MU, PR)
+    b = bd.rhs_ns_bc(d.ref, d.geo, d.conn, q, GAS, MU, PR)
+    return _rel(a, b) <= 1e-12
+
+
+def test_ns_polynomial_flux_reduces_to_the_collocated_rhs():
+    assert _ns_poly_flux_is_collocated(2)
+    assert _ns_poly_flux_is_collocated(3)
+
+
+def _ns_conserves(N=2):
+    d = box_disc(2, N)
+    q = uniform_perturbation(isentropic_vortex(d.xyz, 0.0), 1e-2, seed=6)
+    r = oi.rhs_overint_ns(d.ref, d.geo, d.conn, q, GAS, MU, PR)
+    periodic = all(abs(d.integrate(r[v])) <= 1e-12 * d.abs_integral(r[v]) for v in range(5))
+    b = bc_disc((2, 2, 2), N, {(a, e): NOSLIP for a in range(3) for e in (0, 1)})
+    x, y, z = b.xyz[..., 0], b.xyz[..., 1], b.xyz[..., 2]
+    qb = uniform_perturbation(_state(np.ones_like(x), 0.1 * np.sin(3 * y), 0.05 * np.cos(2 * x), 0 * x,
+                                     0.8 + 0.05 * z), 1e-3, seed=7)
+    rb = oi.rhs_overint_ns(b.ref, b.geo, b.conn, qb, GAS, MU, PR)
+    closed = all(abs(b.integrate(rb[v])) <= 1e-12 * b.abs_integral(rb[v]) for v in (0, 4))
+    return periodic and closed
+
+
+def test_ns_conserves_in_periodic_and_closed_boxes():
+    assert _ns_conserves(2)
+
+
+def _ns_rest_holds(N=2):
+    d = bc_disc((2, 2, 2), N, {(a, e): NOSLIP for a in range(3) for e in (0, 1)})
+    one = np.ones(d.xyz.shape[:-1])
+    q = _state(one, 0 * one, 0 * one, 0 * one, 0.8 * one)
+    r = oi.rhs_overint_ns(d.ref, d.geo, d.conn, q, GAS, MU, PR)
+    return np.abs(r).max() <= 1e-12
+
+
+def test_ns_rest_state_between_walls_is_steady():
+    assert _ns_rest_holds(2)
+    assert _ns_rest_holds(3)
+
+
 # --- consistency with the vortex ------------------------------------------------------------------
 
 _L, _R = 10.0, 1.0
@@ -166,7 +225,8 @@ def test_vortex_consistency_converges():
 
 def _all_pins_hold():
     return (_poly_flux_is_collocated(2) and _exact_integration(2) and _exact_integration(3)
-            and _conserves(2) and _freestream_holds(2))
+            and _conserves(2) and _freestream_holds(2) and _ns_poly_flux_is_collocated(2)
+            and _ns_conserves(2) and _ns_rest_holds(2))
 
 
 def test_pins_hold_unplanted():
@@ -181,29 +241,36 @@ def _uniform_weights(q):
 _RULE = oi.tet_rule
 
 
-def _planted_volume_transposed(ref, geo, q, gas, Q):
+def _planted_volume_transposed(ref, geo, q, gas, Q, Fv=None):
     """The r and s derivative operators exchanged in the volume term."""
-    return _VOLUME(dataclasses.replace(ref, Dr=ref.Ds, Ds=ref.Dr), geo, q, gas, Q)
+    return _VOLUME(dataclasses.replace(ref, Dr=ref.Ds, Ds=ref.Dr), geo, q, gas, Q, Fv)
 
 
-def _planted_no_metric(ref, geo, q, gas, Q):
+def _planted_no_metric(ref, geo, q, gas, Q, Fv=None):
     """The contravariant flux taken as the Cartesian one (dr_a/dx_d dropped)."""
     class Unit:
         def drdx(self):
             K = geo.drdx().shape[2]
             return np.broadcast_to(np.eye(3)[:, :, None], (3, 3, K))
-    return _VOLUME(ref, Unit(), q, gas, Q)
+    return _VOLUME(ref, Unit(), q, gas, Q, Fv)
 
 
 _VOLUME = oi.overint_volume
 
 
-@pytest.mark.parametrize("plant", ["uniform_weights", "transposed", "no_metric"])
+def _planted_no_viscous_volume(ref, geo, q, gas, Q, Fv=None):
+    """The viscous flux left out of the integrand at the points."""
+    return _VOLUME(ref, geo, q, gas, Q)
+
+
+@pytest.mark.parametrize("plant", ["uniform_weights", "transposed", "no_metric", "no_viscous_volume"])
 def test_planted_mistake_fails_a_pin(plant, monkeypatch):
     if plant == "uniform_weights":
         monkeypatch.setattr(oi, "tet_rule", _uniform_weights)
     elif plant == "transposed":
         monkeypatch.setattr(oi, "overint_volume", _planted_volume_transposed)
-    else:
+    elif plant == "no_metric":
         monkeypatch.setattr(oi, "overint_volume", _planted_no_metric)
+    else:
+        monkeypatch.setattr(oi, "overint_volume", _planted_no_viscous_volume)
     assert not _all_pins_hold()
