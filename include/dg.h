@@ -198,7 +198,10 @@ int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* st
  * product on the collapsed cube: q Gauss-Jacobi points per direction for the weights 1, (1 - b),
  * (1 - c)^2, so q^3 points with positive weights, exact for total degree 2q - 1; ceil(3N/2)
  * points integrate degree 3N - 1, a degree-N field's quadratic fluxes against the test
- * functions' gradients. */
+ * functions' gradients.  Navier-Stokes: the whole flux G = F - Fv is integrated on the rule, with
+ * the nodal BR1 viscous flux Fv of the first pass interpolated to the points (a degree-N field,
+ * so that part equals the collocated weak-form term), and the face flux gains minus the central
+ * viscous flux with the walls' exterior viscous fluxes, as in the collocated form. */
 
 /* Host only (no CUDA call): the rule with q points per direction (1..DG_MAX_OVERINT_POINTS) on the
  * reference tetrahedron, rst_host[q^3][3] and w_host[q^3] (caller-owned); point (k q + j) q + i
@@ -210,11 +213,13 @@ int dg_tet_quadrature(int32_t q, double* rst_host, double* w_host);
  * DG_OVERINT_DEFAULT for ceil(3N/2), 0 for the collocated strong form again.  Builds the tables
  * (the nodal basis at the points, the weights, M^-1 D_a^T) from the mesh's reference nodes and
  * copies them to the device (cudaMalloc; the mesh owns them).  Right-hand sides with it on run
- * in the FP64 form with an inviscid perfect gas, periodic or with boundary faces, over the whole
- * mesh; the mixed-precision and batched forms, viscosity, a mixture, artificial viscosity and
- * element ranges are DG_ERR_UNSUPPORTED then.  Errors: DG_ERR_INVALID_ARG (host-only mesh, q
- * below -1 or above DG_MAX_OVERINT_POINTS), DG_ERR_UNSUPPORTED (the tables and one element's
- * work do not fit in a block's shared memory), DG_ERR_CUDA, DG_ERR_OOM. */
+ * in the FP64 form with a perfect gas (Euler or Navier-Stokes), periodic or with boundary faces,
+ * over the whole mesh; the mixed-precision and batched forms, a mixture, artificial viscosity,
+ * element ranges and prims_given are DG_ERR_UNSUPPORTED then, and so is a viscous right-hand
+ * side whose larger per-element work does not fit at this point count.  Errors:
+ * DG_ERR_INVALID_ARG (host-only mesh, q below -1 or above DG_MAX_OVERINT_POINTS),
+ * DG_ERR_UNSUPPORTED (the tables and one element's Euler work do not fit in a block's shared
+ * memory), DG_ERR_CUDA, DG_ERR_OOM. */
 int dg_mesh_set_overint(dg_mesh mesh, int32_t q);
 
 /* ---- partitioned meshes: halo exchange support -------------------------------------------

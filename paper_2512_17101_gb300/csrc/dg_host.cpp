@@ -193,10 +193,15 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   const bool prims_given = opts && opts->prims_given;
   if (prims_given && (opts->precision != DG_PREC_FP64 || g.model != DG_GAS_PERFECT))
     return fail(DG_ERR_UNSUPPORTED, "prims_given is for the FP64 form of a perfect gas");
-  if (m.oi_q > 0 && ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || g.mu > 0 || av ||
-                     (opts && opts->elem_range) || prims_given))
-    return fail(DG_ERR_UNSUPPORTED,
-                "over-integration runs in the FP64 form with an inviscid perfect gas, without AV, over the whole mesh");
+  if (m.oi_q > 0) {
+    if ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || av || (opts && opts->elem_range) ||
+        prims_given)
+      return fail(DG_ERR_UNSUPPORTED,
+                  "over-integration runs in the FP64 form with a perfect gas, without AV, over the whole mesh");
+    if (!dg::overint_fits(m.N, m.oi_ng, g.mu > 0))
+      return fail(DG_ERR_UNSUPPORTED, "the viscous over-integration tables and one element's work exceed a block's "
+                                      "shared memory at this point count");
+  }
   if (av) {
     if (opts && opts->precision == DG_PREC_MIXED)
       return fail(DG_ERR_UNSUPPORTED, "artificial viscosity runs in the FP64 form only");
@@ -277,12 +282,8 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
   }
-  if (m.oi_q > 0) {
-    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_overint(m, g, q, out, k, rk, a, b, dt, s); });
-    if (e != cudaSuccess) return cuda_fail(e, "over-integrated right-hand-side kernel");
-    return DG_OK;
-  }
-  if (g.model == DG_GAS_PERFECT && !prims_given) {  // (1/rho, p, c) once per node for the next kernels
+  // (1/rho, p, c) once per node for the next kernels (the over-integrated Euler kernel reads none)
+  if (g.model == DG_GAS_PERFECT && !prims_given && !(m.oi_q > 0 && g.mu == 0)) {
     e = timed(mesh, DG_KERNEL_PRIMS, s, [&] { return dg::launch_prims_fp64(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "primitives kernel");
   }
@@ -290,6 +291,11 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     // the whole mesh: the range's right-hand side reads its neighbours' viscous flux
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
+  }
+  if (m.oi_q > 0) {
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_overint(m, g, q, out, k, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "over-integrated right-hand-side kernel");
+    return DG_OK;
   }
   if (av) {
     e = timed(mesh, DG_KERNEL_AV, s, [&] {
@@ -545,7 +551,7 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
     return DG_OK;
   }
   if (q == DG_OVERINT_DEFAULT) q = (3 * d.N + 1) / 2;
-  if (!dg::overint_fits(d.N, q * q * q))
+  if (!dg::overint_fits(d.N, q * q * q, false))
     return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
   dg::OverintOps o;
   std::string err;

@@ -1,12 +1,15 @@
-// Over-integrated Euler right-hand side on tetrahedra (Sec. 5.3 names over-integration among the
-// stabilisations of its shock runs): the weak form
-//   rhs = sum_a M^-1 (I D_a)^T W F_a(I q) - LIFT(Fscale f*),  F_a = sum_d (dr_a/dx_d) F_d,
+// Over-integrated Euler and Navier-Stokes right-hand sides on tetrahedra (Sec. 5.3 names
+// over-integration among the stabilisations of its shock runs): the weak form
+//   rhs = sum_a M^-1 (I D_a)^T W G_a - LIFT(Fscale n.G*),  G_a = sum_d (dr_a/dx_d) G_d,
 // with I the nodal basis at the q^3 points of a Stroud conical-product rule and W its weights
-// (tables from build_overint_ops), f* the pointwise Lax-Friedrichs flux of the face-node traces.
+// (tables from build_overint_ops).  Euler: G = F(I q), n.G* the pointwise Lax-Friedrichs flux of
+// the face-node traces.  Navier-Stokes (VISC): G = F(I q) - I Fv with the nodal BR1 viscous flux Fv
+// of the first pass, and n.G* gains minus the central viscous flux, with the walls' exterior
+// viscous fluxes (adiabatic; shear-free at a slip wall).
 //
 // One persistent block per group of E elements keeps every intermediate in shared memory:
-//   1. point-parallel : the state at the points (I q), the flux there, its contravariant components
-//                       times the weight -> sF[a][v][e][g]
+//   1. point-parallel : the state (and viscous flux) at the points, the flux there, its
+//                       contravariant components times the weight -> sF[a][v][e][g]
 //   2. face-node-par. : the Lax-Friedrichs flux of the traces (ghost states at boundary faces) -> sG
 //   3. (a, v, e, i)   : y_a = I^T (W F_a), one sum over the points per output
 //   4. (v, e, i)      : rhs = sum_a (M^-1 D_a^T) y_a - LIFT (Fscale f*), then the RK update -> HBM
@@ -31,24 +34,25 @@ struct OiLayout {
 };
 
 template <int N>
-__host__ __device__ inline OiLayout oi_layout(int Ng) {
+__host__ __device__ inline OiLayout oi_layout(int Ng, bool visc) {
   using O = Ord<N>;
   OiLayout L;
   L.ldq = oi_ldq(Ng);
   L.tables = O::Np * L.ldq + Ng + 3 * O::Np * O::Np + O::NF * O::Np;
-  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF;
+  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF + (visc ? 9 * O::Np : 0);
   return L;
 }
 
 template <int N>
-inline size_t oi_smem(int Ng, int E) {
-  const OiLayout L = oi_layout<N>(Ng);
+inline size_t oi_smem(int Ng, int E, bool visc) {
+  const OiLayout L = oi_layout<N>(Ng, visc);
   return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * Ord<N>::NF;
 }
 
-template <int N, bool RK>
-__global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
+template <int N, bool VISC, bool RK>
+__global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                       double* __restrict__ kreg, const double* __restrict__ tab,
+                                                      const double* __restrict__ fv_g,
                                                       const double* __restrict__ ops_g,
                                                       const int32_t* __restrict__ fmask_g,
                                                       const double* __restrict__ geo_g,
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
                                                       const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, NF = O::NF;
-  const OiLayout L = oi_layout<N>(Ng);
+  const OiLayout L = oi_layout<N>(Ng, VISC);
   const int ldq = L.ldq;
   extern __shared__ double smem[];
   double* sIT = smem;                  // [Np][ldq]: l_j at point g
@@ -69,8 +73,9 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
   double* sQ = sGeo + E * GS;          // [5][E][Np]
   double* sF = sQ + 5 * E * Np;        // [3][5][E][Ng]: w_g F_a at the points
   double* sY = sF + 15 * E * Ng;       // [3][5][E][Np]
-  double* sG = sY + 15 * E * Np;       // [5][E][NF]: Fscale f*
-  int* sFm = reinterpret_cast<int*>(sG + 5 * E * NF);
+  double* sG = sY + 15 * E * Np;       // [5][E][NF]: Fscale n.G*
+  double* sFv = sG + 5 * E * NF;       // VISC: [9][E][Np] nodal viscous flux (tau xx yy zz xy xz yz, Q)
+  int* sFm = reinterpret_cast<int*>(sFv + (VISC ? 9 * E * Np : 0));
   const int tid = threadIdx.x, NT = blockDim.x;
   const size_t KNp = (size_t)K * Np;
 
@@ -95,16 +100,25 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
     for (int i = tid; i < nel * GS; i += NT) sGeo[i] = geo_g[(size_t)e0 * GS + i];
     for (int v = 0; v < 5; ++v)
       for (int i = tid; i < nn; i += NT) sQ[(v * E + i / Np) * Np + i % Np] = q[v * KNp + base + i];
+    if (VISC)
+      for (int c = 0; c < 9; ++c)
+        for (int i = tid; i < nn; i += NT) sFv[(c * E + i / Np) * Np + i % Np] = fv_g[c * KNp + base + i];
     __syncthreads();
 
     // ---- 1: state, flux and weighted contravariant flux at every point ----
     for (int it = tid; it < nel * Ng; it += NT) {
       const int e = it / Ng, g = it - e * Ng;
-      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, fvg[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) fvg[c] = 0.0;
       for (int j = 0; j < Np; ++j) {
         const double l = sIT[j * ldq + g];
 #pragma unroll
         for (int v = 0; v < 5; ++v) qg[v] = fma(l, sQ[(v * E + e) * Np + j], qg[v]);
+        if (VISC) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) fvg[c] = fma(l, sFv[(c * E + e) * Np + j], fvg[c]);
+        }
       }
       const double ir = 1.0 / qg[0];
       const double u[3] = {qg[1] * ir, qg[2] * ir, qg[3] * ir};
@@ -119,6 +133,11 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
         F[d][3] = qg[3] * u[d];
         F[d][1 + d] += p;
         F[d][4] = u[d] * (qg[4] + p);
+        if (VISC) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) F[d][1 + i] -= fvg[kern::tau_index(i, d)];
+          F[d][4] -= fvg[6 + d];
+        }
       }
       const double* G = sGeo + e * GS;
       const double w = sW[g];
@@ -157,8 +176,45 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
       double fm[5], fp[5];
       kern::normal_flux<5>(qm, unm, pm, nx, ny, nz, 5, fm);
       kern::normal_flux<5>(qp, unp, pp, nx, ny, nz, 5, fp);
+      double gs[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sG[(v * E + e) * NF + m] = fs * (0.5 * ((fm[v] + fp[v]) + lam * (qm[v] - qp[v])));
+      for (int v = 0; v < 5; ++v) gs[v] = 0.5 * ((fm[v] + fp[v]) + lam * (qm[v] - qp[v]));
+      if (VISC) {
+        // minus the central viscous flux (n.Fv- + n.Fv+)/2: traction t = tau n and energy flux e;
+        // at a boundary node the exterior flux is the interior one (Pn is the node itself), except
+        // that walls are adiabatic (e+ = -e-) and a slip wall is shear-free (t+ = 2 (n.t-) n - t-)
+        const double nn3[3] = {nx, ny, nz};
+        double tm[3], tp[3], em = 0.0, ep = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          tm[i] = 0.0;
+          tp[i] = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int c = kern::tau_index(i, d);
+            tm[i] = fma(nn3[d], sFv[(c * E + e) * Np + sFm[m]], tm[i]);
+            tp[i] = fma(nn3[d], fv_g[c * KNp + Pn], tp[i]);
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          em = fma(nn3[d], sFv[((6 + d) * E + e) * Np + sFm[m]], em);
+          ep = fma(nn3[d], fv_g[(6 + d) * KNp + Pn], ep);
+        }
+        if (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) {
+          ep = -em;
+          if (P == -DG_BC_SLIP_WALL) {
+            const double tn = tm[0] * nx + tm[1] * ny + tm[2] * nz;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) tp[i] = 2.0 * tn * nn3[i] - tm[i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gs[1 + i] -= 0.5 * (tm[i] + tp[i]);
+        gs[4] -= 0.5 * (em + ep);
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sG[(v * E + e) * NF + m] = fs * gs[v];
     }
     __syncthreads();
 
@@ -207,12 +263,12 @@ __global__ void __launch_bounds__(512) rhs_oi_kernel(const double* __restrict__ 
 // Elements per block and blocks per SM: two blocks of at least two elements each if they fit in
 // an SM's shared memory, else one block with as many elements as fit; 0 when one element does not.
 template <int N>
-bool oi_config(int Ng, int& E, int& bps, size_t& smem) {
+bool oi_config(int Ng, bool visc, int& E, int& bps, size_t& smem) {
   int dev = 0, per_sm = 0, per_block = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const OiLayout L = oi_layout<N>(Ng);
+  const OiLayout L = oi_layout<N>(Ng, visc);
   for (bps = 2; bps >= 1; --bps) {
     const size_t budget = std::min((size_t)per_block, (size_t)per_sm / bps - 1024);
     const size_t fixed = sizeof(double) * L.tables + sizeof(int) * Ord<N>::NF;
@@ -220,20 +276,21 @@ bool oi_config(int Ng, int& E, int& bps, size_t& smem) {
     E = (int)((budget - fixed) / (sizeof(double) * L.per_elem));
     E = std::min(E, 64);
     if (E >= (bps == 2 ? 2 : 1)) {
-      smem = oi_smem<N>(Ng, E);
+      smem = oi_smem<N>(Ng, E, visc);
       return true;
     }
   }
   return false;
 }
 
-template <int N, bool RK>
+template <int N, bool VISC, bool RK>
 cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, double a,
                         double b, double dt, cudaStream_t s) {
   int E = 0, bps = 0;
   size_t smem = 0;
-  if (!oi_config<N>(m.oi_ng, E, bps, smem)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(rhs_oi_kernel<N, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!oi_config<N>(m.oi_ng, VISC, E, bps, smem)) return cudaErrorInvalidConfiguration;
+  cudaError_t e =
+      cudaFuncSetAttribute(rhs_oi_kernel<N, VISC, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -241,21 +298,21 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
   const int NT = bps == 2 ? 256 : 512;
   const int groups = (m.K + E - 1) / E;
   const int blocks = std::min(groups, sms * bps);
-  rhs_oi_kernel<N, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.ops, m.fmask, m.geo, m.vmapP, m.status, g,
-                                                 m.bc, m.K, m.oi_ng, E, a, b, dt);
+  rhs_oi_kernel<N, VISC, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.scratch, m.ops, m.fmask, m.geo,
+                                                        m.vmapP, m.status, g, m.bc, m.K, m.oi_ng, E, a, b, dt);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool overint_fits(int N, int Ng) {
+bool overint_fits(int N, int Ng, bool visc) {
   int E = 0, bps = 0;
   size_t smem = 0;
   switch (N) {
-    case 1: return oi_config<1>(Ng, E, bps, smem);
-    case 2: return oi_config<2>(Ng, E, bps, smem);
-    case 3: return oi_config<3>(Ng, E, bps, smem);
-    case 4: return oi_config<4>(Ng, E, bps, smem);
+    case 1: return oi_config<1>(Ng, visc, E, bps, smem);
+    case 2: return oi_config<2>(Ng, visc, E, bps, smem);
+    case 3: return oi_config<3>(Ng, visc, E, bps, smem);
+    case 4: return oi_config<4>(Ng, visc, E, bps, smem);
     default: return false;
   }
 }
@@ -263,9 +320,13 @@ bool overint_fits(int N, int Ng) {
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s) {
   switch (m.N) {
-#define DG_CASE(NN) \
-  case NN:          \
-    return rk ? launch_oi_t<NN, true>(m, g, q, out, k, a, b, dt, s) : launch_oi_t<NN, false>(m, g, q, out, k, a, b, dt, s);
+#define DG_CASE(NN)                                                                            \
+  case NN:                                                                                     \
+    if (g.mu > 0)                                                                              \
+      return rk ? launch_oi_t<NN, true, true>(m, g, q, out, k, a, b, dt, s)                    \
+                : launch_oi_t<NN, true, false>(m, g, q, out, k, a, b, dt, s);                  \
+    return rk ? launch_oi_t<NN, false, true>(m, g, q, out, k, a, b, dt, s)                     \
+              : launch_oi_t<NN, false, false>(m, g, q, out, k, a, b, dt, s);
     DG_CASE(1)
     DG_CASE(2)
     DG_CASE(3)
