@@ -625,20 +625,25 @@ def gpu_arm(args, cfg, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def overint_flops_per_element(N, Q):
+def overint_flops_per_element(N, Q, viscous=False):
     """FP64 flops of one element in the over-integrated right-hand side (Ng = Q^3 points): per
     point, the 5 fields interpolated (10 Np), the flux (30) and its weighted contravariant
     components (93); the contraction back to the nodes (30 Np Ng); the weak-form operators and
-    LIFT (10 Np (3 Np + 4 Nfp)); about 100 per face node for the Lax-Friedrichs flux."""
+    LIFT (10 Np (3 Np + 4 Nfp)); about 100 per face node for the Lax-Friedrichs flux.  Viscous:
+    per point the 9 viscous-flux components interpolated (18 Np) and subtracted (12), and about
+    40 more per face node for the central viscous flux."""
     Np, Nfp, Ng = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2, Q ** 3
-    return Ng * (10 * Np + 123) + 30 * Np * Ng + 10 * Np * (3 * Np + 4 * Nfp) + 100 * 4 * Nfp
+    f = Ng * (10 * Np + 123) + 30 * Np * Ng + 10 * Np * (3 * Np + 4 * Nfp) + 100 * 4 * Nfp
+    if viscous:
+        f += Ng * (18 * Np + 12) + 40 * 4 * Nfp
+    return f
 
 
 def overint_form(args, local):
     """Over-integration (weak form, Stroud rule with ceil(3N/2) points per collapsed direction) on the
-    periodic Euler vortex with the main workload's mesh and order (24^3 x 6 tets, N = 3): FP64 RK4
-    steps with CUDA events, against the collocated strong form on the same mesh, and the kernel's
-    FP64 rate from its flop count."""
+    periodic vortex with the main workload's mesh and order (24^3 x 6 tets, N = 3), Euler and
+    Navier-Stokes (mu = 1e-3, Pr = 0.71): FP64 RK4 steps with CUDA events, against the collocated
+    strong form on the same mesh, and the over-integrated kernel's FP64 rate from its flop count."""
     import torch
     from paper_2512_17101_gb300 import dg
     from workloads import box_mesh, equispaced_tet_nodes, isentropic_vortex, physical_nodes, uniform_perturbation
@@ -648,7 +653,6 @@ def overint_form(args, local):
     v, per = box_mesh(n, 1.0)
     nodes = equispaced_tet_nodes(N)
     mesh = dg.Mesh(v, per, N, nodes)
-    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0)
     q0 = torch.tensor(uniform_perturbation(isentropic_vortex(physical_nodes(v, nodes), 0.0), 1e-3, seed=0),
                       device=dev)
     K, Np = v.shape[0], nodes.shape[0]
@@ -657,7 +661,9 @@ def overint_form(args, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     steps = max(1, min(args.steps, 10))
     out = {}
-    for label, oq in (("collocated", 0), ("overint", -1)):
+    for label, oq, mu in (("collocated", 0, 0.0), ("overint", -1, 0.0), ("ns_collocated", 0, 1e-3),
+                          ("ns_overint", -1, 1e-3)):
+        gas = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=mu, Pr=0.71)
         mesh.set_overint(oq)
         q = q0.clone()
         for _ in range(max(3, args.warmup)):
@@ -682,16 +688,21 @@ def overint_form(args, local):
         out[label] = {"ms_per_step": ms, "value": K * Np * 5 / (ms * 1e-3),
                       "rhs_avg_ms": kt["rhs"][0] / kt["rhs"][1] if kt["rhs"][1] else None}
     Q = (3 * N + 1) // 2
-    flops = overint_flops_per_element(N, Q) * K
-    ach = flops / (out["overint"]["rhs_avg_ms"] * 1e-3) / 1e12
+
+    def roof(viscous):
+        flops = overint_flops_per_element(N, Q, viscous) * K
+        ach = flops / (out["ns_overint" if viscous else "overint"]["rhs_avg_ms"] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "rhs_oi_kernel", "flops_per_launch": flops, "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "peak_kind": "nominal FP64"}
+
     return {
-        "workload": f"periodic Euler isentropic vortex + U(+-1e-3), {n}^3 x 6 = {K} tets, N = {N}, FP64",
-        "points_per_direction": Q, "points_per_element": Q ** 3, "unit": "DOF-updates/s",
-        "collocated": out["collocated"], "overint": out["overint"],
+        "workload": f"periodic isentropic vortex + U(+-1e-3), {n}^3 x 6 = {K} tets, N = {N}, FP64; "
+                    "Euler and Navier-Stokes (mu = 1e-3, Pr = 0.71)",
+        "points_per_direction": Q, "points_per_element": Q ** 3, "unit": "DOF-updates/s", **out,
         "slowdown": out["overint"]["ms_per_step"] / out["collocated"]["ms_per_step"],
-        "roofline": {"bound": "alu", "kernel": "rhs_oi_kernel", "flops_per_launch": flops, "achieved": ach,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                     "peak_kind": "nominal FP64"},
+        "ns_slowdown": out["ns_overint"]["ms_per_step"] / out["ns_collocated"]["ms_per_step"],
+        "roofline": roof(False), "ns_roofline": roof(True),
     }
 
 
