@@ -63,12 +63,12 @@ MIXED_SOURCES = ("dg_mixed.cuh", "dg_tc.cuh", "dg_umma.cuh", "dg_cvt.cuh", "dg_k
 TRAFFIC = {
     # profiles/ns_N3_K82944_fp64.md and profiles/mixed_tc_ns_N3_K82944.md: DRAM read + write per
     # launch, mean over the five stages of one RK4 step
-    ("d344a5980bd8972a", "ns_viscous", "rhs"): 317.775114e6 + 105.664227e6,
-    ("d344a5980bd8972a", "ns_viscous", "viscous"): 126.966533e6 + 75.377306e6,
-    ("d344a5980bd8972a", "ns_viscous", "prims"): 66.388736e6 + 6.113434e6,
-    ("fa7482e711b8b053", "ns_viscous", "mixed_rhs"): 258.201306e6 + 94.688461e6,
-    ("fa7482e711b8b053", "ns_viscous", "mixed_viscous"): 90.075962e6 + 22.346803e6,
-    ("fa7482e711b8b053", "ns_viscous", "mixed_prims"): 66.369690e6 + 12.294205e6,
+    ("276e74aec8aa44ec", "ns_viscous", "rhs"): 317.652700e6 + 105.683300e6,
+    ("276e74aec8aa44ec", "ns_viscous", "viscous"): 126.923400e6 + 75.355550e6,
+    ("276e74aec8aa44ec", "ns_viscous", "prims"): 66.387510e6 + 6.057626e6,
+    ("f0a6c77b28aa1245", "ns_viscous", "mixed_rhs"): 258.704700e6 + 95.412990e6,
+    ("f0a6c77b28aa1245", "ns_viscous", "mixed_viscous"): 90.074830e6 + 23.521790e6,
+    ("f0a6c77b28aa1245", "ns_viscous", "mixed_prims"): 66.371430e6 + 12.297160e6,
 }
 
 

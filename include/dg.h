@@ -119,10 +119,10 @@ typedef struct {
  * BR1 exterior values are w(q+); away from walls the viscous exterior flux is the interior one.
  * Meshes with boundary faces run with a perfect gas (Euler or Navier-Stokes) in the FP64, the
  * mixed-precision and the batched forms (the last two with ghost node records), and with an
- * inviscid NASA-7 mixture in the FP64 and mixed-precision forms: species densities are carried
- * like the density; a wall or outflow ghost keeps the node's internal energy and so its
- * temperature, p and c; an inflow ghost takes p and c of q_in at its own temperature.  A viscous
- * mixture on such a mesh is DG_ERR_UNSUPPORTED.
+ * NASA-7 mixture in the FP64 form (inviscid or viscous) and the mixed-precision form (inviscid):
+ * species densities are carried like the density; a wall or outflow ghost keeps the node's
+ * internal energy and so its temperature, p and c; an inflow ghost takes p and c of q_in at its
+ * own temperature.
  * In the vmapP of dg_mesh_connectivity a boundary face node holds -code. */
 #define DG_BC_SLIP_WALL 1
 #define DG_BC_NOSLIP_WALL 2
@@ -324,13 +324,16 @@ int dg_mesh_set_timing(dg_mesh mesh, int enable);
 int dg_mesh_kernel_times(dg_mesh mesh, double* ms_host, int64_t* launches_host, int reset);
 
 /* ---- gas ----------------------------------------------------------------- */
-/* A NASA-7 mixture with mu > 0 (FP64 form, periodic meshes) carries viscosity, heat conduction
+/* A NASA-7 mixture with mu > 0 (FP64 form) carries viscosity, heat conduction
  * and species diffusion (the paper's viscous multi-species flows, Sec. 4-5, name no transport
  * model; reading): constant mu, Stokes hypothesis; kappa = mu cp_mix(T, Y) / Pr; Fickian
  * diffusion at the Schmidt number Sc with the zero-sum correction,
  * J_k = -(mu / Sc) (grad Y_k - Y_k sum_j grad Y_j); heat flux q = -kappa grad T + sum_k h_k J_k;
- * BR1 central fluxes on (rho, rho u, T, Y_k).  The mesh allocates 33 doubles per node for its
- * viscous flux on the first such call. */
+ * BR1 central fluxes on (rho, rho u, T, Y_k).  At boundary faces the gradient pass takes the
+ * ghost state's values (the node's own T and Y at walls and outflow, the inflow state's at
+ * inflow); walls are adiabatic (the energy flux holds the enthalpy diffusion too) and impermeable
+ * (the species rows' exterior normal flux is minus the interior one), a slip wall shear-free.  The
+ * mesh allocates 33 doubles per node for its viscous flux on the first such call. */
 #define DG_GAS_PERFECT 0
 #define DG_GAS_NASA7 1
 

@@ -208,8 +208,6 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
   }
   if (m.boundary_faces > 0) {
-    if (g.model != DG_GAS_PERFECT && g.mu > 0)
-      return fail(DG_ERR_UNSUPPORTED, "viscous mixtures run on periodic meshes only");
     if (m.inflow_faces > 0 && m.inflow_nvar != V)
       return fail(DG_ERR_INVALID_ARG, "the mesh has inflow faces: set the inflow state with dg_mesh_set_inflow");
     if (m.inflow_faces > 0 && g.model == DG_GAS_NASA7 && !mixture_inflow_prims(g, m.bc.q_in, mesh->d.bc))

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
         }
       }
     }
-    if (PHYS == MIXTURE_NS) {  // central viscous flux of the mixture (periodic meshes only)
+    if (PHYS == MIXTURE_NS) {  // central viscous flux of the mixture
       const size_t gM = base + own;
       const double nn3[3] = {nx, ny, nz};
 #pragma unroll
@@ -324,6 +324,33 @@ __global__ void __launch_bounds__(Ord<N>::NT) rhs_kernel(
           dp = fma(nn3[d], fv_g[(c0 + d) * KNp + Pn], dp);
         }
         g[v] -= 0.5 * (dm - dp);
+      }
+      // at a boundary node the terms above cancel (exterior = interior flux); walls are adiabatic
+      // and impermeable (the energy and species rows' exterior normal fluxes are minus the interior
+      // ones: g gains minus the interior flux) and a slip wall is shear-free (t+ = 2 (n.t-) n - t-:
+      // g gains -(t- - (n.t-) n))
+      if (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) {
+#pragma unroll
+        for (int v = 4; v < V; ++v) {
+          if (v >= nvar) break;
+          const int c0 = v == 4 ? 6 : 9 + 3 * (v - 5);
+          double dm = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) dm = fma(nn3[d], fv_g[(c0 + d) * KNp + gM], dm);
+          g[v] -= dm;
+        }
+        if (P == -DG_BC_SLIP_WALL) {
+          double tm[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            tm[i] = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) tm[i] = fma(nn3[d], fv_g[tau_index(i, d) * KNp + gM], tm[i]);
+          }
+          const double tn = tm[0] * nx + tm[1] * ny + tm[2] * nz;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) g[1 + i] -= tm[i] - tn * nn3[i];
+        }
       }
     }
     if (VISC) {

@@ -1,4 +1,4 @@
-// Navier-Stokes right-hand side of a NASA-7 mixture with species diffusion, FP64, periodic meshes.
+// Navier-Stokes right-hand side of a NASA-7 mixture with species diffusion, FP64.
 // The paper's solver targets viscous multi-species flows (Sec. 4-5) and names no transport
 // model; the reading here: constant viscosity mu (Stokes hypothesis), heat conduction
 // kappa = mu cp_mix(T, Y) / Pr, Fickian diffusion at a constant Schmidt number with the
@@ -8,6 +8,9 @@
 // flux (subtracted from the Euler flux): momentum tau, energy u.tau - q, species -J_k, stored as
 // [9 + 3 k + d] (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, E_x, E_y, E_z, then species k
 // along x_d).  BR1 gradients with the central flux of w = (rho, rho u, rho v, rho w, T, Y_k).
+// At a boundary face node the exterior values are those of the ghost state: the momentum
+// mirrored (slip wall) or reversed (no-slip wall) with the node's own rho, T and Y; the inflow
+// state with its temperature; the node's own at outflow.
 #include "dg_kernels.cuh"
 
 namespace dg {
@@ -25,7 +28,7 @@ template <int N>
 __global__ void __launch_bounds__(Ord<N>::NT) viscous_mix_kernel(
     const double* __restrict__ q, const double* __restrict__ Tg, double* __restrict__ fv_out,
     const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g,
-    const int32_t* __restrict__ vmapP, const GasParams gp, const int K) {
+    const int32_t* __restrict__ vmapP, const GasParams gp, const BcParams bc, const int K) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   extern __shared__ double smem[];
@@ -61,14 +64,37 @@ __global__ void __launch_bounds__(Ord<N>::NT) viscous_mix_kernel(
     const int e = j / NF, m = j - e * NF, f = m / Nfp;
     const double hf = 0.5 * sGeo[e * GS + 12 + 4 * f];
     const int own = e * Np + sFm[m];
-    const size_t P = (size_t)vmapP[(size_t)(e0 + e) * NF + m];
-    const double rp = q[P], irp = 1.0 / rp;
-    sJ[j] = hf * (rp - sW[own]);
+    const int Pi = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    if (Pi >= 0) {
+      const size_t P = (size_t)Pi;
+      const double rp = q[P], irp = 1.0 / rp;
+      sJ[j] = hf * (rp - sW[own]);
 #pragma unroll
-    for (int v = 1; v < 4; ++v) sJ[v * EPB * NF + j] = hf * (q[v * KNp + P] - sW[v * NODES + own]);
-    sJ[4 * EPB * NF + j] = hf * (Tg[P] - sW[4 * NODES + own]);
-    for (int k = 0; k < ns; ++k)
-      sJ[(5 + k) * EPB * NF + j] = hf * (q[(5 + k) * KNp + P] * irp - sW[(5 + k) * NODES + own]);
+      for (int v = 1; v < 4; ++v) sJ[v * EPB * NF + j] = hf * (q[v * KNp + P] - sW[v * NODES + own]);
+      sJ[4 * EPB * NF + j] = hf * (Tg[P] - sW[4 * NODES + own]);
+      for (int k = 0; k < ns; ++k)
+        sJ[(5 + k) * EPB * NF + j] = hf * (q[(5 + k) * KNp + P] * irp - sW[(5 + k) * NODES + own]);
+    } else if (-Pi == DG_BC_INFLOW) {  // the inflow state at its temperature
+      const double irp = 1.0 / bc.q_in[0];
+      sJ[j] = hf * (bc.q_in[0] - sW[own]);
+#pragma unroll
+      for (int v = 1; v < 4; ++v) sJ[v * EPB * NF + j] = hf * (bc.q_in[v] - sW[v * NODES + own]);
+      sJ[4 * EPB * NF + j] = hf * (bc.T_in - sW[4 * NODES + own]);
+      for (int k = 0; k < ns; ++k) sJ[(5 + k) * EPB * NF + j] = hf * (bc.q_in[5 + k] * irp - sW[(5 + k) * NODES + own]);
+    } else {  // walls and outflow: rho, T and Y jump by nothing; the momentum by its ghost's
+      const double* G = sGeo + e * GS;
+      const double n3[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
+      const double m3[3] = {sW[NODES + own], sW[2 * NODES + own], sW[3 * NODES + own]};
+      const double mn = m3[0] * n3[0] + m3[1] * n3[1] + m3[2] * n3[2];
+      sJ[j] = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double mp = -Pi == DG_BC_SLIP_WALL ? m3[i] - 2.0 * mn * n3[i] : (-Pi == DG_BC_NOSLIP_WALL ? -m3[i] : m3[i]);
+        sJ[(1 + i) * EPB * NF + j] = hf * (mp - m3[i]);
+      }
+      sJ[4 * EPB * NF + j] = 0.0;
+      for (int k = 0; k < ns; ++k) sJ[(5 + k) * EPB * NF + j] = 0.0;
+    }
   }
   __syncthreads();
 
@@ -164,7 +190,7 @@ cudaError_t launch_visc_mix_t(const MeshDev& m, const GasParams& g, const double
     configured = true;
   }
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  viscous_mix_kernel<N><<<blocks, O::NT, smem, s>>>(q, T, m.mix_fv, m.ops, m.fmask, m.geo, m.vmapP, g, m.K);
+  viscous_mix_kernel<N><<<blocks, O::NT, smem, s>>>(q, T, m.mix_fv, m.ops, m.fmask, m.geo, m.vmapP, g, m.bc, m.K);
   return cudaGetLastError();
 }
 
