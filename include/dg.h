@@ -214,9 +214,11 @@ int dg_tet_quadrature(int32_t q, double* rst_host, double* w_host);
  * (the nodal basis at the points, the weights, M^-1 D_a^T) from the mesh's reference nodes and
  * copies them to the device (cudaMalloc; the mesh owns them).  Right-hand sides with it on run
  * in the FP64 form with a perfect gas (Euler or Navier-Stokes), periodic or with boundary faces,
- * over the whole mesh; the mixed-precision and batched forms, a mixture, artificial viscosity,
- * element ranges and prims_given are DG_ERR_UNSUPPORTED then, and so is a viscous right-hand
- * side whose larger per-element work does not fit at this point count.  Errors:
+ * over the whole mesh, with or without artificial viscosity (whose flux sigma = eps grad_h q, a
+ * degree-N field, is integrated on the rule with G, and whose central face flux joins n.G*); the
+ * mixed-precision and batched forms, a mixture, element ranges and prims_given are
+ * DG_ERR_UNSUPPORTED then, and so is a viscous or AV right-hand side whose larger per-element work
+ * does not fit at this point count.  Errors:
  * DG_ERR_INVALID_ARG (host-only mesh, q below -1 or above DG_MAX_OVERINT_POINTS),
  * DG_ERR_UNSUPPORTED (the tables and one element's Euler work do not fit in a block's shared
  * memory), DG_ERR_CUDA, DG_ERR_OOM. */

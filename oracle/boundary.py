@@ -114,7 +114,7 @@ def rhs_mixture_bc(ref, geo, conn, q, gas, T, q_in=None, T_in=None, form="strong
 
 def _weak_volume(ref, geo, F):
     drdx = geo.drdx()
-    Minv = np.linalg.inv(ref.M)
+    Minv = ref.Minv
     out = np.zeros(F.shape[1:])
     for a, D in enumerate((ref.Dr, ref.Ds, ref.Dt)):
         W = Minv @ D.T @ ref.M

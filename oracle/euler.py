@@ -116,7 +116,7 @@ def rhs_weak(ref, geo, conn, q, gas, T=None):
     p, c = gas.pressure_sound_speed(q, T)
     F = euler_flux(q, p)
     drdx = geo.drdx()
-    Minv = np.linalg.inv(ref.M)
+    Minv = ref.Minv
     out = np.zeros(q.shape)
     for a, D in enumerate((ref.Dr, ref.Ds, ref.Dt)):
         W = Minv @ D.T @ ref.M

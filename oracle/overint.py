@@ -90,7 +90,7 @@ def overint_volume(ref, geo, q, gas, Q, Fv=None):
     if Fv is not None:
         F = F - np.einsum("gj,dvkj->dvkg", Iq, Fv)
     drdx = geo.drdx()  # [a][d][K]
-    Minv = np.linalg.inv(ref.M)
+    Minv = ref.Minv
     out = np.zeros(q.shape)
     for a, D in enumerate((ref.Dr, ref.Ds, ref.Dt)):
         Fa = sum(drdx[a, d][None, :, None] * F[d] for d in range(3))
@@ -120,3 +120,14 @@ def rhs_overint_ns(ref, geo, conn, q, gas, mu, Pr, Q=None, q_in=None, Fv=None):
         Fv = viscous_flux_bc(ref, geo, conn, q, gas, mu, Pr, q_in)
     fstar = ns_face_flux(ref, geo, conn, q, gas, Fv, q_in)[0]
     return overint_volume(ref, geo, q, gas, Q, Fv) - lift(ref, geo, fstar)
+
+
+def rhs_overint_av(ref, geo, conn, q, gas, eps, mu=0.0, Pr=0.71, Q=None, q_in=None):
+    """The over-integrated Euler (mu = 0) or Navier-Stokes right-hand side plus the artificial-
+    viscosity term div(eps grad_h q) of oracle/av.py for the element viscosities eps [K].  The AV
+    flux sigma = eps grad_h q is a degree-N field in each element (eps is constant there), so its
+    weak form on the rule is exact and equals that collocated strong term."""
+    from .av import rhs_av
+    base = (rhs_overint_ns(ref, geo, conn, q, gas, mu, Pr, Q=Q, q_in=q_in) if mu > 0
+            else rhs_overint(ref, geo, conn, q, gas, Q=Q, q_in=q_in))
+    return base + rhs_av(ref, geo, conn, q, eps, q_in)

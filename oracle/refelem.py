@@ -158,6 +158,7 @@ class RefElement:
     Fmask: np.ndarray  # [4][Nfp] volume-node index of each face node
     E: np.ndarray  # [Np][4 Nfp]
     LIFT: np.ndarray  # [Np][4 Nfp]
+    Minv: np.ndarray = None  # [Np][Np] the inverse mass matrix, formed in extended precision and rounded once
 
 
 def build_reference(N: int, nodes: np.ndarray, tol: float = 1e-10) -> RefElement:
@@ -188,6 +189,8 @@ def build_reference(N: int, nodes: np.ndarray, tol: float = 1e-10) -> RefElement
             for a, i in enumerate(Fmask[f]):
                 for b in range(Nfp):
                     E[int(i), f * Nfp + b] = Mf[a, b]
-        LIFT = mpmath.inverse(M) * E
+        Minv = mpmath.inverse(M)
+        LIFT = Minv * E
         return RefElement(N=N, Np=Np, Nfp=Nfp, nodes=nodes, V=_to_np(V), Dr=_to_np(Dr), Ds=_to_np(Ds),
-                          Dt=_to_np(Dt), M=_to_np(M), Fmask=Fmask, E=_to_np(E), LIFT=_to_np(LIFT))
+                          Dt=_to_np(Dt), M=_to_np(M), Fmask=Fmask, E=_to_np(E), LIFT=_to_np(LIFT),
+                          Minv=_to_np(Minv))

@@ -194,13 +194,12 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   if (prims_given && (opts->precision != DG_PREC_FP64 || g.model != DG_GAS_PERFECT))
     return fail(DG_ERR_UNSUPPORTED, "prims_given is for the FP64 form of a perfect gas");
   if (m.oi_q > 0) {
-    if ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || av || (opts && opts->elem_range) ||
+    if ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || (opts && opts->elem_range) ||
         prims_given)
-      return fail(DG_ERR_UNSUPPORTED,
-                  "over-integration runs in the FP64 form with a perfect gas, without AV, over the whole mesh");
-    if (!dg::overint_fits(m.N, m.oi_ng, g.mu > 0))
-      return fail(DG_ERR_UNSUPPORTED, "the viscous over-integration tables and one element's work exceed a block's "
-                                      "shared memory at this point count");
+      return fail(DG_ERR_UNSUPPORTED, "over-integration runs in the FP64 form with a perfect gas over the whole mesh");
+    if (!dg::overint_fits(m.N, m.oi_ng, g.mu > 0, av))
+      return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's viscous or AV work exceed a "
+                                      "block's shared memory at this point count");
   }
   if (av) {
     if (opts && opts->precision == DG_PREC_MIXED)
@@ -290,17 +289,19 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_flux(m, g, q, s); });
     if (e != cudaSuccess) return cuda_fail(e, "viscous flux kernel");
   }
-  if (m.oi_q > 0) {
-    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_overint(m, g, q, out, k, rk, a, b, dt, s); });
-    if (e != cudaSuccess) return cuda_fail(e, "over-integrated right-hand-side kernel");
-    return DG_OK;
-  }
   if (av) {
     e = timed(mesh, DG_KERNEL_AV, s, [&] {
       cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s);
       return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
     });
     if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
+  }
+  if (m.oi_q > 0) {
+    e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_overint(m, g, q, out, k, rk, a, b, dt, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "over-integrated right-hand-side kernel");
+    return DG_OK;
+  }
+  if (av) {
     e = timed(mesh, DG_KERNEL_RHS, s, [&] { return dg::launch_rhs_av(m, g, q, out, k, rk, a, b, dt, s); });
     if (e != cudaSuccess) return cuda_fail(e, "right-hand-side kernel");
     return DG_OK;
@@ -549,7 +550,7 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
     return DG_OK;
   }
   if (q == DG_OVERINT_DEFAULT) q = (3 * d.N + 1) / 2;
-  if (!dg::overint_fits(d.N, q * q * q, false))
+  if (!dg::overint_fits(d.N, q * q * q, false, false))
     return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
   dg::OverintOps o;
   std::string err;

@@ -167,11 +167,12 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
 cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
 // Over-integrated weak-form Euler or Navier-Stokes right-hand side / RK stage of a perfect gas
-// (k_oi.cu; Navier-Stokes reads the BR1 viscous flux in m.scratch), and whether its tables and one
-// element's work for Ng points fit in a block's shared memory at order N.
+// (k_oi.cu; Navier-Stokes reads the BR1 viscous flux in m.scratch, artificial viscosity the flux of
+// the AV pass in m.av_sig), and whether its tables and one element's work for Ng points fit in a
+// block's shared memory at order N.
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s);
-bool overint_fits(int N, int Ng, bool visc);
+bool overint_fits(int N, int Ng, bool visc, bool av);
 cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
 // flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.

@@ -5,7 +5,10 @@
 // (tables from build_overint_ops).  Euler: G = F(I q), n.G* the pointwise Lax-Friedrichs flux of
 // the face-node traces.  Navier-Stokes (VISC): G = F(I q) - I Fv with the nodal BR1 viscous flux Fv
 // of the first pass, and n.G* gains minus the central viscous flux, with the walls' exterior
-// viscous fluxes (adiabatic; shear-free at a slip wall).
+// viscous fluxes (adiabatic; shear-free at a slip wall).  Artificial viscosity (AV): G also loses the
+// interpolant of the nodal flux sigma = eps grad_h q of the AV pass (nonzero only in elements with
+// eps > 0), and n.G* the central flux n.(sigma- + sigma+)/2 (sigma+ = sigma- at boundary faces).
+// Both fluxes are degree-N fields, so their parts of the integral are exact.
 //
 // One persistent block per group of E elements keeps every intermediate in shared memory:
 //   1. point-parallel : the state (and viscous flux) at the points, the flux there, its
@@ -34,25 +37,27 @@ struct OiLayout {
 };
 
 template <int N>
-__host__ __device__ inline OiLayout oi_layout(int Ng, bool visc) {
+__host__ __device__ inline OiLayout oi_layout(int Ng, bool visc, bool av) {
   using O = Ord<N>;
   OiLayout L;
   L.ldq = oi_ldq(Ng);
   L.tables = O::Np * L.ldq + Ng + 3 * O::Np * O::Np + O::NF * O::Np;
-  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF + (visc ? 9 * O::Np : 0);
+  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF + (visc ? 9 * O::Np : 0) + (av ? 15 * O::Np : 0);
   return L;
 }
 
 template <int N>
-inline size_t oi_smem(int Ng, int E, bool visc) {
-  const OiLayout L = oi_layout<N>(Ng, visc);
+inline size_t oi_smem(int Ng, int E, bool visc, bool av) {
+  const OiLayout L = oi_layout<N>(Ng, visc, av);
   return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * Ord<N>::NF;
 }
 
-template <int N, bool VISC, bool RK>
+template <int N, bool VISC, bool AV, bool RK>
 __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                       double* __restrict__ kreg, const double* __restrict__ tab,
                                                       const double* __restrict__ fv_g,
+                                                      const double* __restrict__ av_g,
+                                                      const double* __restrict__ av_eps,
                                                       const double* __restrict__ ops_g,
                                                       const int32_t* __restrict__ fmask_g,
                                                       const double* __restrict__ geo_g,
@@ -62,7 +67,7 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
                                                       const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, NF = O::NF;
-  const OiLayout L = oi_layout<N>(Ng, VISC);
+  const OiLayout L = oi_layout<N>(Ng, VISC, AV);
   const int ldq = L.ldq;
   extern __shared__ double smem[];
   double* sIT = smem;                  // [Np][ldq]: l_j at point g
@@ -75,7 +80,8 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   double* sY = sF + 15 * E * Ng;       // [3][5][E][Np]
   double* sG = sY + 15 * E * Np;       // [5][E][NF]: Fscale n.G*
   double* sFv = sG + 5 * E * NF;       // VISC: [9][E][Np] nodal viscous flux (tau xx yy zz xy xz yz, Q)
-  int* sFm = reinterpret_cast<int*>(sFv + (VISC ? 9 * E * Np : 0));
+  double* sS = sFv + (VISC ? 9 * E * Np : 0);  // AV: [15][E][Np] sigma[(5 d + v)], 0 where eps = 0
+  int* sFm = reinterpret_cast<int*>(sS + (AV ? 15 * E * Np : 0));
   const int tid = threadIdx.x, NT = blockDim.x;
   const size_t KNp = (size_t)K * Np;
 
@@ -103,14 +109,21 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
     if (VISC)
       for (int c = 0; c < 9; ++c)
         for (int i = tid; i < nn; i += NT) sFv[(c * E + i / Np) * Np + i % Np] = fv_g[c * KNp + base + i];
+    if (AV)  // the AV flux is stored only in elements with eps > 0
+      for (int c = 0; c < 15; ++c)
+        for (int i = tid; i < nn; i += NT)
+          sS[(c * E + i / Np) * Np + i % Np] = av_eps[e0 + i / Np] > 0.0 ? av_g[c * KNp + base + i] : 0.0;
     __syncthreads();
 
     // ---- 1: state, flux and weighted contravariant flux at every point ----
     for (int it = tid; it < nel * Ng; it += NT) {
       const int e = it / Ng, g = it - e * Ng;
-      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, fvg[9];
+      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, fvg[9], sg[15];
 #pragma unroll
       for (int c = 0; c < 9; ++c) fvg[c] = 0.0;
+#pragma unroll
+      for (int c = 0; c < 15; ++c) sg[c] = 0.0;
+      const bool on = AV && av_eps[e0 + e] > 0.0;
       for (int j = 0; j < Np; ++j) {
         const double l = sIT[j * ldq + g];
 #pragma unroll
@@ -118,6 +131,10 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
         if (VISC) {
 #pragma unroll
           for (int c = 0; c < 9; ++c) fvg[c] = fma(l, sFv[(c * E + e) * Np + j], fvg[c]);
+        }
+        if (AV && on) {
+#pragma unroll
+          for (int c = 0; c < 15; ++c) sg[c] = fma(l, sS[(c * E + e) * Np + j], sg[c]);
         }
       }
       const double ir = 1.0 / qg[0];
@@ -137,6 +154,10 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 #pragma unroll
           for (int i = 0; i < 3; ++i) F[d][1 + i] -= fvg[kern::tau_index(i, d)];
           F[d][4] -= fvg[6 + d];
+        }
+        if (AV) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) F[d][v] -= sg[5 * d + v];
         }
       }
       const double* G = sGeo + e * GS;
@@ -213,6 +234,24 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
         for (int i = 0; i < 3; ++i) gs[1 + i] -= 0.5 * (tm[i] + tp[i]);
         gs[4] -= 0.5 * (em + ep);
       }
+      if (AV) {
+        // minus the central AV flux n.(sigma- + sigma+)/2; at a boundary node Pn is the node itself,
+        // so sigma+ = sigma-
+        const bool onM = av_eps[e0 + e] > 0.0, onP = av_eps[Pn / Np] > 0.0;
+        if (onM || onP) {
+          const int own_n = sFm[m];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            double sm = 0.0, sp = 0.0;
+            if (onM)
+              sm = fma(nx, sS[(v * E + e) * Np + own_n],
+                       fma(ny, sS[((5 + v) * E + e) * Np + own_n], nz * sS[((10 + v) * E + e) * Np + own_n]));
+            if (onP)
+              sp = fma(nx, av_g[v * KNp + Pn], fma(ny, av_g[(5 + v) * KNp + Pn], nz * av_g[(10 + v) * KNp + Pn]));
+            gs[v] -= 0.5 * (sm + sp);
+          }
+        }
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) sG[(v * E + e) * NF + m] = fs * gs[v];
     }
@@ -263,12 +302,12 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 // Elements per block and blocks per SM: two blocks of at least two elements each if they fit in
 // an SM's shared memory, else one block with as many elements as fit; 0 when one element does not.
 template <int N>
-bool oi_config(int Ng, bool visc, int& E, int& bps, size_t& smem) {
+bool oi_config(int Ng, bool visc, bool av, int& E, int& bps, size_t& smem) {
   int dev = 0, per_sm = 0, per_block = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const OiLayout L = oi_layout<N>(Ng, visc);
+  const OiLayout L = oi_layout<N>(Ng, visc, av);
   for (bps = 2; bps >= 1; --bps) {
     const size_t budget = std::min((size_t)per_block, (size_t)per_sm / bps - 1024);
     const size_t fixed = sizeof(double) * L.tables + sizeof(int) * Ord<N>::NF;
@@ -276,21 +315,21 @@ bool oi_config(int Ng, bool visc, int& E, int& bps, size_t& smem) {
     E = (int)((budget - fixed) / (sizeof(double) * L.per_elem));
     E = std::min(E, 64);
     if (E >= (bps == 2 ? 2 : 1)) {
-      smem = oi_smem<N>(Ng, E, visc);
+      smem = oi_smem<N>(Ng, E, visc, av);
       return true;
     }
   }
   return false;
 }
 
-template <int N, bool VISC, bool RK>
+template <int N, bool VISC, bool AV, bool RK>
 cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k, double a,
                         double b, double dt, cudaStream_t s) {
   int E = 0, bps = 0;
   size_t smem = 0;
-  if (!oi_config<N>(m.oi_ng, VISC, E, bps, smem)) return cudaErrorInvalidConfiguration;
+  if (!oi_config<N>(m.oi_ng, VISC, AV, E, bps, smem)) return cudaErrorInvalidConfiguration;
   cudaError_t e =
-      cudaFuncSetAttribute(rhs_oi_kernel<N, VISC, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(rhs_oi_kernel<N, VISC, AV, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -298,40 +337,47 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
   const int NT = bps == 2 ? 256 : 512;
   const int groups = (m.K + E - 1) / E;
   const int blocks = std::min(groups, sms * bps);
-  rhs_oi_kernel<N, VISC, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.scratch, m.ops, m.fmask, m.geo,
-                                                        m.vmapP, m.status, g, m.bc, m.K, m.oi_ng, E, a, b, dt);
+  rhs_oi_kernel<N, VISC, AV, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.scratch, m.av_sig, m.av_eps, m.ops,
+                                                            m.fmask, m.geo, m.vmapP, m.status, g, m.bc, m.K, m.oi_ng,
+                                                            E, a, b, dt);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool overint_fits(int N, int Ng, bool visc) {
+bool overint_fits(int N, int Ng, bool visc, bool av) {
   int E = 0, bps = 0;
   size_t smem = 0;
   switch (N) {
-    case 1: return oi_config<1>(Ng, visc, E, bps, smem);
-    case 2: return oi_config<2>(Ng, visc, E, bps, smem);
-    case 3: return oi_config<3>(Ng, visc, E, bps, smem);
-    case 4: return oi_config<4>(Ng, visc, E, bps, smem);
+    case 1: return oi_config<1>(Ng, visc, av, E, bps, smem);
+    case 2: return oi_config<2>(Ng, visc, av, E, bps, smem);
+    case 3: return oi_config<3>(Ng, visc, av, E, bps, smem);
+    case 4: return oi_config<4>(Ng, visc, av, E, bps, smem);
     default: return false;
   }
 }
 
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s) {
+  const bool av = m.av.eps0 > 0;
   switch (m.N) {
-#define DG_CASE(NN)                                                                            \
-  case NN:                                                                                     \
-    if (g.mu > 0)                                                                              \
-      return rk ? launch_oi_t<NN, true, true>(m, g, q, out, k, a, b, dt, s)                    \
-                : launch_oi_t<NN, true, false>(m, g, q, out, k, a, b, dt, s);                  \
-    return rk ? launch_oi_t<NN, false, true>(m, g, q, out, k, a, b, dt, s)                     \
-              : launch_oi_t<NN, false, false>(m, g, q, out, k, a, b, dt, s);
+#define DG_PICK(NN, VI, AVV)                                                          \
+  return rk ? launch_oi_t<NN, VI, AVV, true>(m, g, q, out, k, a, b, dt, s)            \
+            : launch_oi_t<NN, VI, AVV, false>(m, g, q, out, k, a, b, dt, s);
+#define DG_CASE(NN)                    \
+  case NN:                             \
+    if (g.mu > 0) {                    \
+      if (av) { DG_PICK(NN, true, true) } \
+      DG_PICK(NN, true, false)         \
+    }                                  \
+    if (av) { DG_PICK(NN, false, true) } \
+    DG_PICK(NN, false, false)
     DG_CASE(1)
     DG_CASE(2)
     DG_CASE(3)
     DG_CASE(4)
 #undef DG_CASE
+#undef DG_PICK
     default:
       return cudaErrorInvalidValue;
   }

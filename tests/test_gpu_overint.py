@@ -2,8 +2,8 @@
 sides with the volume term on the Stroud rule (dg_mesh_set_overint), through the C ABI, against
 oracle/overint.py at 1e-11 per conserved variable.  Orders 1-4, periodic and walled / inflow /
 outflow boxes, the default and other point counts, ragged last element groups and blocks that
-loop over several groups, two RK4 steps, switching it off, and the combinations the library
-refuses."""
+loop over several groups, two RK4 steps, artificial viscosity on top, switching it off, and the
+combinations the library refuses."""
 
 import numpy as np
 import pytest
@@ -147,9 +147,39 @@ def test_overint_flags_a_nonphysical_state():
     assert mesh.status() & capi.DG_STATUS_NONPHYSICAL
 
 
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("name", list(SIDES))
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_overint_with_artificial_viscosity(N, name, viscous):
+    """Over-integration plus the AV term on a steep front whose elements span all three regimes of
+    the viscosity ramp (the front and thresholds of tests/test_gpu_av.py), with a z velocity of
+    the size of the x velocity.  (On that test's own front rho w is 1/700 of rho u; the weak form
+    cancels terms several hundred times that row's result across the reference directions, and
+    at N = 4 the row keeps 3e-11 of its own maximum in rounding, against an extended-precision
+    evaluation, while the FP64 oracle keeps 1e-12.)"""
+    import oracle.av as av
+    from tests.test_gpu_av import EPS0, _front, _thresholds
+    sides = SIDES[name]
+    torch, dg, d, mesh, gas = _setup((4, 2, 2), N, sides, viscous=viscous)
+    q0 = _front(d.xyz)
+    w = 0.2 + 0.1 * np.cos(2 * np.pi * d.xyz[..., 1])  # rho w of the size of rho u, E to match
+    q0[4] += 0.5 * ((q0[0] * w) ** 2 - q0[3] ** 2) / q0[0]
+    q0[3] = q0[0] * w
+    s0, kappa = _thresholds(d, q0)
+    mesh.set_av(EPS0, s0, kappa)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    eps = av.element_viscosity(d.ref, q0, EPS0, s0, kappa)
+    assert (eps == 0).any() and (eps > 0).any()
+    want = oi.rhs_overint_av(d.ref, d.geo, d.conn, q0, GAS, eps, mu=MU if viscous else 0.0, Pr=PR, q_in=Q_IN)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
 def test_overint_refusals():
-    """A mixture, the mixed form, artificial viscosity, element ranges and point counts whose tables
-    do not fit are refused; the mesh keeps working."""
+    """A mixture, the mixed form, element ranges and point counts whose tables do not fit are
+    refused; the mesh keeps working, with and without artificial viscosity."""
     from paper_2512_17101_gb300 import capi
     from workloads.gas import seeded_nasa7_mixture
     torch, dg, d, mesh, gas = _setup(2, 4, None)
@@ -170,9 +200,5 @@ def test_overint_refusals():
         mesh.set_overint(capi.DG_MAX_OVERINT_POINTS)  # N = 4: 1728 points do not fit
     with pytest.raises(capi.DGError):
         mesh.set_overint(-2)
-    mesh.set_av(0.1)
-    with pytest.raises(capi.DGError):
-        dg.dg_rhs(mesh, gas, q, rhs)
-    mesh.set_av(0.0)
     dg.dg_rhs(mesh, gas, q, rhs)
     assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL

@@ -14,7 +14,9 @@ fixes:
   at order >= N - 0.9 (the same consistency bar as the collocated form);
 * Navier-Stokes: with a degree-N convective flux it is the collocated Navier-Stokes right-hand side
   (walls included); periodic boxes conserve mass, momentum and energy and boxes closed by no-slip
-  walls mass and energy; the rest state between no-slip walls is steady.
+  walls mass and energy; the rest state between no-slip walls is steady;
+* the artificial-viscosity flux, a degree-N field, integrated on the rule in weak form with its
+  central face flux is the collocated strong AV term.
 Planted mistakes in the oracle must break at least one pin."""
 
 import dataclasses
@@ -196,6 +198,35 @@ def _ns_rest_holds(N=2):
 def test_ns_rest_state_between_walls_is_steady():
     assert _ns_rest_holds(2)
     assert _ns_rest_holds(3)
+
+
+# --- the artificial-viscosity flux on the rule ----------------------------------------------------------
+
+def _av_weak_is_strong(N=3):
+    """The AV flux sigma = eps grad_h q integrated on the rule in weak form, with the central face
+    flux n.(sigma- + sigma+)/2, equals the collocated strong AV term of oracle/av.py (integration by
+    parts is exact for the degree-N field sigma)."""
+    import oracle.av as av
+    from oracle.euler import face_normals, gather, lift, normal_flux
+    d = bc_disc((3, 2, 2), N, {(0, 0): INFLOW, (0, 1): OUTFLOW, (1, 0): SLIP, (1, 1): NOSLIP})
+    x, y, z = d.xyz[..., 0], d.xyz[..., 1], d.xyz[..., 2]
+    q = uniform_perturbation(_state(1.0 + 0.2 * np.sin(3 * x), 0.3 + 0 * x, 0.1 * np.cos(2 * y), 0 * x,
+                                    0.9 + 0.1 * z), 1e-2, seed=9)
+    q_in = q[:, 0, 0]
+    eps = np.linspace(0.0, 0.03, d.K)
+    sigma = eps[None, None, :, None] * av.br1_gradient(d.ref, d.geo, d.conn, q, q_in)  # [3][5][K][Np]
+    vol = (oi.overint_volume(d.ref, d.geo, q, GAS, 4, Fv=sigma) - oi.overint_volume(d.ref, d.geo, q, GAS, 4))
+    n = face_normals(d.geo, d.ref.Nfp)
+    sM = np.stack([gather(sigma[k], d.conn.vmapM) for k in range(3)])
+    sP = np.stack([gather(sigma[k], d.conn.vmapP) for k in range(3)])
+    sP = np.where((d.conn.bc != 0)[None, None], sM, sP)
+    weak = vol + lift(d.ref, d.geo, 0.5 * (normal_flux(sM, n) + normal_flux(sP, n)))
+    return _rel(weak, av.rhs_av(d.ref, d.geo, d.conn, q, eps, q_in)) <= 1e-11
+
+
+def test_av_flux_weak_on_the_rule_is_the_strong_term():
+    assert _av_weak_is_strong(2)
+    assert _av_weak_is_strong(3)
 
 
 # --- consistency with the vortex ------------------------------------------------------------------
