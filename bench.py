@@ -66,9 +66,9 @@ TRAFFIC = {
     ("276e74aec8aa44ec", "ns_viscous", "rhs"): 317.652700e6 + 105.683300e6,
     ("276e74aec8aa44ec", "ns_viscous", "viscous"): 126.923400e6 + 75.355550e6,
     ("276e74aec8aa44ec", "ns_viscous", "prims"): 66.387510e6 + 6.057626e6,
-    ("f0a6c77b28aa1245", "ns_viscous", "mixed_rhs"): 258.704700e6 + 95.412990e6,
-    ("f0a6c77b28aa1245", "ns_viscous", "mixed_viscous"): 90.074830e6 + 23.521790e6,
-    ("f0a6c77b28aa1245", "ns_viscous", "mixed_prims"): 66.371430e6 + 12.297160e6,
+    ("9cd242f4cd10185f", "ns_viscous", "mixed_rhs"): 258.499700e6 + 95.220530e6,
+    ("9cd242f4cd10185f", "ns_viscous", "mixed_viscous"): 90.070680e6 + 23.047480e6,
+    ("9cd242f4cd10185f", "ns_viscous", "mixed_prims"): 66.372200e6 + 12.271460e6,
 }
 
 
@@ -1064,7 +1064,8 @@ def boundary_form(args, local, periodic_fp64=None):
 def av_form(args, local):
     """Shock capturing: Euler with artificial viscosity on two smoothed Sod fronts (24^3 x 6 tets,
     N = 3), FP64 RK4 steps with CUDA events and the kernel split, against the same steps with
-    the artificial viscosity off."""
+    the artificial viscosity off; and the same steps in the mixed-precision form, with their state
+    error against the FP64 form."""
     import numpy as np
     import torch
     from paper_2512_17101_gb300 import dg
@@ -1080,11 +1081,14 @@ def av_form(args, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     params = dict(eps0=5e-3, s0=-4.0 * np.log10(cfg.N), kappa=1.0)
 
-    def run(on):
+    from paper_2512_17101_gb300 import capi
+    mixed = dg._opts(precision=capi.DG_PREC_MIXED)
+
+    def run(on, opts=None):
         mesh.set_av(params["eps0"] if on else 0.0, params["s0"], params["kappa"])
         q = q0.clone()
         for _ in range(max(3, args.warmup)):
-            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work, opts=opts)
         q.copy_(q0)
         mesh.kernel_times(reset=True)
         mesh.set_timing(True)
@@ -1093,7 +1097,7 @@ def av_form(args, local):
             flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work)
+            dg.lsrk4_step(mesh, gas, q, cfg.dt, steps=1, work=work, opts=opts)
             b.record()
             torch.cuda.synchronize()
             total += a.elapsed_time(b)
@@ -1101,10 +1105,15 @@ def av_form(args, local):
         kt = {n: {"avg_ms": ms / c, "launches": c} for n, (ms, c) in mesh.kernel_times(reset=True).items() if c}
         if mesh.status() != 0:
             raise SystemExit("status flags set in the artificial-viscosity run")
-        return total / max(1, args.steps), kt
+        return total / max(1, args.steps), kt, q
 
-    ms_on, kt_on = run(True)
-    ms_off, _ = run(False)
+    ms_on, kt_on, q64 = run(True)
+    ms_off, _, _ = run(False)
+    ms_mx, kt_mx, qmx = run(True, mixed)
+    a64, amx = q64.cpu().numpy(), qmx.cpu().numpy()
+    groups = [[0], [1, 2, 3], [4]]
+    mixed_err = max(max(np.abs(amx[v] - a64[v]).max() for v in g) / max(np.abs(a64[v]).max() for v in g)
+                    for g in groups)
     mesh.set_av(params["eps0"], params["s0"], params["kappa"])
     eps = torch.empty(cfg.K, dtype=torch.float64, device=dev)
     mesh.av_viscosity(q0, eps)
@@ -1114,6 +1123,10 @@ def av_form(args, local):
             "unit": "DOF-updates/s", "ms_per_step_without_av": ms_off, "av_overhead": ms_on / ms_off - 1.0,
             "kernels": kt_on, "elements_with_eps": {"zero": int((e == 0).sum()), "ramp": int(((e > 0) & (e < 5e-3)).sum()),
                                                       "eps0": int((e == 5e-3).sum())},
+            "mixed": {"ms_per_step": ms_mx, "value": cfg.dofs * 5 / (ms_mx * 1e-3), "kernels": kt_mx,
+                      "speedup_vs_fp64": ms_on / ms_mx,
+                      "state_error_vs_fp64": {"per_field_max": mixed_err, "steps": max(1, args.steps),
+                                              "fields": "rho, momentum as one vector, rho E"}},
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 

@@ -171,8 +171,11 @@ int dg_mesh_set_inflow(dg_mesh mesh, const double* q_in, int32_t nvar);
  * eps0 (s > s0 + kappa), eps0/2 (1 + sin(pi (s - s0) / (2 kappa))) in between; the right-hand
  * side gains div(eps grad q) on every conserved variable with BR1 central fluxes in both passes
  * (at boundary faces the gradient pass takes the ghost state and the exterior flux is the
- * interior one).  FP64 form with a perfect gas (Euler or Navier-Stokes); the mixed-precision and
- * batched forms and the mixture reject a mesh with it on (DG_ERR_UNSUPPORTED). */
+ * interior one).  A perfect gas (Euler or Navier-Stokes) in the FP64 form, and in the
+ * mixed-precision form: there the indicator and the flux sigma are formed in FP64 as above and the
+ * tensor-core right-hand side subtracts sigma (in FP32, only in elements with eps > 0) and adds its
+ * central face flux.  The batched form and the mixture reject a mesh with it on
+ * (DG_ERR_UNSUPPORTED). */
 typedef struct {
   double eps0;   /* maximum viscosity, >= 0; 0 turns the term off                            */
   double s0;     /* indicator threshold, log10 scale (e.g. -4 log10 N)                       */

@@ -201,11 +201,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's viscous or AV work exceed a "
                                       "block's shared memory at this point count");
   }
-  if (av) {
-    if (opts && opts->precision == DG_PREC_MIXED)
-      return fail(DG_ERR_UNSUPPORTED, "artificial viscosity runs in the FP64 form only");
-    if (g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
-  }
+  if (av && g.model != DG_GAS_PERFECT) return fail(DG_ERR_UNSUPPORTED, "artificial viscosity needs a perfect gas");
   if (m.boundary_faces > 0) {
     if (m.inflow_faces > 0 && m.inflow_nvar != V)
       return fail(DG_ERR_INVALID_ARG, "the mesh has inflow faces: set the inflow state with dg_mesh_set_inflow");
@@ -241,6 +237,13 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       if (g.mu > 0) {
         e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_tc(m, g, q, s, opts->wait_polls); });
         if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
+      }
+      if (av) {  // the element viscosities and the AV flux in FP64, for the tensor-core right-hand side
+        e = timed(mesh, DG_KERNEL_AV, s, [&] {
+          cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s);
+          return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
       }
     }
     e = timed(mesh, DG_KERNEL_RHS, s, [&] {

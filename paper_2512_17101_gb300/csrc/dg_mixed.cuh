@@ -94,6 +94,10 @@ struct MixedCase {
   float2 in_temp;
   float4 in_mrec[4];
   float4 in_mlo;
+  // artificial viscosity (perfect gas, FP64 passes): element viscosities [K] and the flux
+  // sigma = eps grad_h q, [(5 d + v)][K][Np], stored only in elements with eps > 0
+  const double* av_eps;
+  const double* av_sig;
   int wait_polls;  // polls per bounded mbarrier wait of the tensor-core kernels; 0 = the default
 };
 

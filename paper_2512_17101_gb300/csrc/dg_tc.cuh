@@ -26,6 +26,12 @@ namespace tc {
 using mixk::MixedCase;
 using kern::GS;
 
+// Tiles of the Navier-Stokes right-hand side, with or without artificial viscosity: they read the
+// BR1 viscous-flux records.
+__host__ __device__ constexpr bool tile_ns(int PHYS) {
+  return PHYS == kern::NAVIER_STOKES || PHYS == kern::NS_AV;
+}
+
 // One thread's L2 prefetch of a tile's contiguous inputs (the node records or, for a mixture,
 // the float state copy, pressure and sound speed; the viscous-flux records for Navier-Stokes),
 // geometry and neighbour map of elements [e0, e0 + nel).
@@ -346,7 +352,7 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
                                          double* __restrict__ out, const int e0, const double a, const double b,
                                          Pipe& p, unsigned* status, const MixedCase* next, int next_e0) {
   constexpr int Np = C_::Np, Nfp = C_::Nfp, NF = C_::NF, KV = C_::KV, NT = C_::NT, NPT = C_::NPT, V = C_::V;
-  constexpr bool NS = PHYS == kern::NAVIER_STOKES, MIX = PHYS == kern::MIXTURE;
+  constexpr bool NS = tile_ns(PHYS), MIX = PHYS == kern::MIXTURE, AVP = kern::has_av(PHYS);
   constexpr bool ST = C_::STAGE && !MIX;  // own records staged in shared memory
   static_assert(MIX ? V == mixk::MIX_V : V == 5, "5 conserved variables, or the 13 of a mixture record");
   const int tid = threadIdx.x;
@@ -413,6 +419,14 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
         }
         // p - p_1 from the hi/lo pairs; p itself (energy flux) as its FP32 rounding
         mixk::node_flux<NS>(qv, (a1.y - r1.y) + (a1.z - r1.z), a1.y, fv, F[s]);
+        if constexpr (AVP) {  // minus the artificial-viscosity flux, where the element has eps > 0
+          if (c.av_eps[e0 + e] > 0.0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+              for (int v = 0; v < 5; ++v) F[s][d][v] -= cvt::narrow(c.av_sig[(5 * d + v) * KNp + gn]);
+          }
+        }
       }
     }
   }
@@ -483,6 +497,24 @@ __device__ __forceinline__ bool rhs_tile(const Smem<C_>& S, const MixedCase& c, 
           if (Pi < 0) mixk::ghost_viscous(-Pi, n3, fvp);
         }
         mixk::face_term<NS>(qm, qp, m1r.y, p1r.y, dpn, fvm, fvp, n3, gam, g);
+        if constexpr (AVP) {
+          // central artificial-viscosity flux: g gains -(n.sigma- - n.sigma+)/2; at a boundary node
+          // P is the node itself, so the term vanishes (sigma+ = sigma-)
+          const bool onM = c.av_eps[e0 + e] > 0.0, onP = c.av_eps[P / Np] > 0.0;
+          if (onM || onP) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              double sm = 0.0, sp = 0.0;
+              if (onM)
+                sm = fma((double)n3[0], c.av_sig[v * KNp + own],
+                         fma((double)n3[1], c.av_sig[(5 + v) * KNp + own], (double)n3[2] * c.av_sig[(10 + v) * KNp + own]));
+              if (onP)
+                sp = fma((double)n3[0], c.av_sig[v * KNp + P],
+                         fma((double)n3[1], c.av_sig[(5 + v) * KNp + P], (double)n3[2] * c.av_sig[(10 + v) * KNp + P]));
+              g[v] -= 0.5f * cvt::narrow(sm - sp);
+            }
+          }
+        }
       }
 #pragma unroll
       for (int v = 0; v < V; ++v)
@@ -580,7 +612,7 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT, tile_v(PHYS)>::MINB)) rhs_tc_k
   Pipe p;
   if constexpr (C_::STAGE && PHYS != kern::MIXTURE) {
     if (blockIdx.x * C_::E < c.K) {
-      stage_issue<C_, PHYS == kern::NAVIER_STOKES>(S, c, blockIdx.x * C_::E);
+      stage_issue<C_, tile_ns(PHYS)>(S, c, blockIdx.x * C_::E);
       p.staged = true;
     }
   }
@@ -609,7 +641,7 @@ __global__ void __launch_bounds__(NT, (Cfg<N, NT>::MINB)) rhs_tc_batched(const M
   if constexpr (C_::STAGE && PHYS != kern::MIXTURE) {
     if (blockIdx.x < nwork) {
       const int2 it = work[blockIdx.x];
-      stage_issue<C_, PHYS == kern::NAVIER_STOKES>(S, cases[it.x], it.y);
+      stage_issue<C_, tile_ns(PHYS)>(S, cases[it.x], it.y);
       p.staged = true;
     }
   }

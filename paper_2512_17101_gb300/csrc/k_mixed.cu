@@ -36,6 +36,8 @@ mixk::MixedCase make_mixed_case(const MeshDev& m, const GasParams& g, const doub
   c.Np = m.Np;
   c.dt = dt;
   c.gas = mixk::MixedGas{g.gamma, g.R, g.mu, g.kappa, 1.0 / g.R};
+  c.av_eps = m.av.eps0 > 0 ? m.av_eps : nullptr;
+  c.av_sig = m.av.eps0 > 0 ? m.av_sig : nullptr;
   if (m.inflow_nvar == 5 && g.model == DG_GAS_PERFECT) {  // the inflow state as a node record
     const double* qi = m.bc.q_in;
     const double ke = 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];

@@ -147,8 +147,9 @@ cudaError_t launch_rhs_tc(const MeshDev& m, const GasParams& g, const double* q,
   mixk::MixedCase c = make_mixed_case(m, g, q, out, k, dt);
   c.wait_polls = wait_polls;
   if (g.model == DG_GAS_NASA7) return dispatch<kern::MIXTURE>(m, c, rk, a, b, s);
-  if (g.mu > 0) return dispatch<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
-  return dispatch<kern::EULER>(m, c, rk, a, b, s);
+  const bool av = m.av.eps0 > 0;  // the AV passes have filled m.av_eps and m.av_sig
+  if (g.mu > 0) return av ? dispatch<kern::NS_AV>(m, c, rk, a, b, s) : dispatch<kern::NAVIER_STOKES>(m, c, rk, a, b, s);
+  return av ? dispatch<kern::EULER_AV>(m, c, rk, a, b, s) : dispatch<kern::EULER>(m, c, rk, a, b, s);
 }
 
 }  // namespace dg

@@ -1,6 +1,7 @@
 """GPU parity of the artificial viscosity: element viscosities (smoothness indicator + ramp) and
 the FP64 right-hand sides with the artificial-viscosity flux, through the C ABI, against the
-oracle (oracle/av.py with oracle/boundary.py) at 1e-11."""
+oracle (oracle/av.py with oracle/boundary.py) at 1e-11; the mixed-precision form with AV at its
+bars (right-hand side 1e-4 per field, state after RK4 steps 1e-6 per field)."""
 
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ import oracle.av as av
 import oracle.boundary as bd
 from oracle.lsrk import lsrk4_step
 from oracle.thermo import PerfectGas
-from tests._gpu import rel_err, torch_cuda
+from tests._gpu import field_err, rel_err, torch_cuda
 from tests._oracle_case import bc_disc, box_disc
 from workloads import equispaced_tet_nodes
 
@@ -114,16 +115,76 @@ def test_two_rk4_steps_with_artificial_viscosity():
 
 
 def test_artificial_viscosity_off_and_rejections():
+    """A mixture with AV is refused before any launch; AV off gives the plain right-hand side."""
+    from workloads.gas import seeded_nasa7_mixture
     d = box_disc(2, 2)
     torch, dg, mesh, gas, s0 = _setup(d, 2, False)
     from paper_2512_17101_gb300 import capi
     q0 = _front(d.xyz)
     q = torch.tensor(q0, device="cuda")
     rhs = torch.empty_like(q)
+    mix = seeded_nasa7_mixture(2, seed=0)
+    mgas = dg.Gas(model="nasa7", W=mix.W, nasa7=mix.coeffs)
+    qm = torch.zeros((7,) + tuple(q.shape[1:]), device="cuda", dtype=torch.float64)
+    T = torch.full(tuple(q.shape[1:]), 1000.0, device="cuda", dtype=torch.float64)
     with pytest.raises(capi.DGError):
-        dg.dg_rhs(mesh, gas, q, rhs, opts=dg._opts(precision=capi.DG_PREC_MIXED))
+        dg.dg_rhs(mesh, mgas, qm, torch.empty_like(qm), T_io=T)
     mesh.set_av(0.0)
     dg.dg_rhs(mesh, gas, q, rhs)
     assert rel_err(rhs.cpu().numpy(), bd.rhs_euler_bc(d.ref, d.geo, d.conn, q0, GAS)) <= TOL
     with pytest.raises(capi.DGError):
         mesh.set_av(1e-2, 0.0, -1.0)
+
+
+# --- the mixed-precision form with artificial viscosity ------------------------------------------
+
+MIXED_RHS_TOL = 1e-4  # per field, as for the mixed form without AV (tests/test_gpu_mixed.py)
+
+
+def _mixed(dg):
+    from paper_2512_17101_gb300 import capi
+    return dg._opts(precision=capi.DG_PREC_MIXED)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_mixed_rhs_with_artificial_viscosity(N, viscous):
+    d = box_disc((4, 2, 2), N)
+    torch, dg, mesh, gas, s0 = _setup(d, N, viscous)
+    q0 = _front(d.xyz)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs, opts=_mixed(dg))
+    err = field_err(rhs.cpu().numpy(), _want(d, q0, viscous, s0))
+    assert err <= MIXED_RHS_TOL, err
+    assert mesh.status() == 0
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_mixed_rhs_with_artificial_viscosity_and_boundaries(viscous):
+    sides = {(0, 0): bd.INFLOW, (0, 1): bd.OUTFLOW, (1, 0): bd.SLIP_WALL, (1, 1): bd.NOSLIP_WALL}
+    d = bc_disc((4, 2, 2), 3, sides)
+    q0 = _front(d.xyz)
+    q_in = q0[:, 0, 0].copy()
+    torch, dg, mesh, gas, s0 = _setup(d, 3, viscous, q_in=q_in)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs, opts=_mixed(dg))
+    err = field_err(rhs.cpu().numpy(), _want(d, q0, viscous, s0, q_in=q_in))
+    assert err <= MIXED_RHS_TOL, err
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_mixed_rk4_steps_with_artificial_viscosity(N):
+    """Two RK4 steps of the mixed form with AV against the oracle: state error <= 1e-6 per field."""
+    d = box_disc((4, 2, 2), N)
+    torch, dg, mesh, gas, s0 = _setup(d, N, True)
+    q0 = _front(d.xyz, seed=4)
+    dt = 2e-4
+    q = torch.tensor(q0, device="cuda")
+    dg.lsrk4_step(mesh, gas, q, dt, steps=2, opts=_mixed(dg))
+    f = lambda u: _want(d, u, True, s0)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    err = field_err(q.cpu().numpy(), want)
+    assert err <= 1e-6, err
+    assert mesh.status() == 0
