@@ -48,6 +48,7 @@ void free_mesh_device(dg::MeshDev& d) {
   cudaFree(d.modal);
   cudaFree(d.av_eps);
   cudaFree(d.av_sig);
+  cudaFree(d.av_list);
   cudaFree(d.mix_fv);
   cudaFree(d.prim);
   cudaFree(d.wq);
@@ -240,7 +241,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       }
       if (av) {  // the element viscosities and the AV flux in FP64, for the tensor-core right-hand side
         e = timed(mesh, DG_KERNEL_AV, s, [&] {
-          cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s);
+          cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s, m.av_list);
           return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
         });
         if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
@@ -294,7 +295,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
   }
   if (av) {
     e = timed(mesh, DG_KERNEL_AV, s, [&] {
-      cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s);
+      cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s, m.av_list);
       return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
     });
     if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
@@ -519,10 +520,13 @@ int dg_mesh_set_av(dg_mesh mesh, const dg_av_params* p) {
   if (!d.av_eps) {
     cudaError_t e = cudaMalloc((void**)&d.av_eps, sizeof(double) * (size_t)d.K);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d.av_sig, sizeof(double) * 15 * (size_t)d.K * d.Np);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.av_list, sizeof(int) * (1 + (size_t)d.K));
     if (e != cudaSuccess) {
       cudaFree(d.av_eps);
       cudaFree(d.av_sig);
+      cudaFree(d.av_list);
       d.av_eps = d.av_sig = nullptr;
+      d.av_list = nullptr;
       return cuda_fail(e, "artificial-viscosity scratch");
     }
   }

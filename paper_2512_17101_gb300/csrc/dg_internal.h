@@ -126,6 +126,7 @@ struct MeshDev {
   int ntop = 0;
   double* modal = nullptr;
   double* av_eps = nullptr;
+  int* av_list = nullptr;      // [1 + K]: the count, then the elements with eps > 0 (the last indicator pass's)
   double* av_sig = nullptr;
   double* mix_fv = nullptr;  // viscous flux of a mixture, [9 + 3 DG_MAX_SPECIES][K][Np] (on first use)
   MixedOps mx;
@@ -165,7 +166,8 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
                        ElemRange r = ElemRange());
 // Artificial viscosity (k_av.cu): element viscosities of q into eps [K]; the flux eps grad q into
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
-cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s);
+// list (may be null): m.av_list, refilled with the elements whose eps > 0 for launch_av_flux.
+cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s, int* list = nullptr);
 // Over-integrated weak-form Euler or Navier-Stokes right-hand side / RK stage of a perfect gas
 // (k_oi.cu; Navier-Stokes reads the BR1 viscous flux in m.scratch, artificial viscosity the flux of
 // the AV pass in m.av_sig), and whether its tables and one element's work for Ng points fit in a

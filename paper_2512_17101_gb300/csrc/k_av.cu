@@ -7,6 +7,7 @@
 //   * flux sigma_v = eps grad q_v for every conserved variable, BR1 gradient with the central
 //     flux (exterior values from the ghost states at boundary faces), added to the right-hand
 //     side through the central flux (rhs_kernel<EULER_AV / NS_AV>).
+#include <algorithm>
 #include <cmath>
 
 #include "dg_kernels.cuh"
@@ -16,11 +17,12 @@ namespace kern {
 
 // One thread per (element, mode): the mode's coefficient from the element's nodal densities;
 // then one thread per element sums the energies.
+// list (may be null): [0] a count the caller has zeroed, then the elements with eps > 0 in any order.
 template <int N>
 __global__ void __launch_bounds__(Ord<N>::NT) av_sensor_kernel(const double* __restrict__ q,
                                                                const double* __restrict__ modal_g, const int ntop,
                                                                const AvParams av, const int K,
-                                                               double* __restrict__ eps) {
+                                                               double* __restrict__ eps, int* __restrict__ list) {
   using O = Ord<N>;
   constexpr int Np = O::Np, EPB = O::EPB, NODES = O::NODES;
   __shared__ double sH[Np * Np];
@@ -58,17 +60,20 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_sensor_kernel(const double* __r
         e = 0.5 * av.eps0 * (1.0 + sin(3.141592653589793 * (sv - av.s0) / (2.0 * av.kappa)));
     }
     eps[e0 + tid] = e;
+    if (list && e > 0.0) list[1 + atomicAdd(list, 1)] = e0 + tid;
   }
 }
 
 // BR1 gradient of the five conserved variables, times the element viscosity:
 //   grad_d q = sum_a (dr_a/dx_d) D_a q + sum_f n_d,f LIFT_f (Fscale (q+ - q-)/2),
-//   sig[(5 d + v)][K][Np] = eps_e grad_d q_v.
+//   sig[(5 d + v)][K][Np] = eps_e grad_d q_v,
+// for the elements of the sensor's list only (sigma = 0 wherever eps = 0, and the right-hand sides
+// read sigma only where eps > 0).  Persistent: each block takes groups of EPB listed elements.
 template <int N>
 __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
     const double* __restrict__ q, const double* __restrict__ eps, double* __restrict__ sig,
     const double* __restrict__ ops_g, const int32_t* __restrict__ fmask_g, const double* __restrict__ geo_g,
-    const int32_t* __restrict__ vmapP, const BcParams bc, const int K) {
+    const int32_t* __restrict__ vmapP, const BcParams bc, const int K, const int* __restrict__ list) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, EPB = O::EPB, NODES = O::NODES;
   constexpr int W = 5;
@@ -78,23 +83,23 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
   double* sW = sGeo + EPB * GS;
   double* sJ = sW + W * NODES;
   int* sFm = reinterpret_cast<int*>(sJ + W * EPB * NF);
+  int* sE = sFm + NF;  // [EPB]: the group's element indices
 
   const int tid = threadIdx.x;
-  const int e0 = blockIdx.x * EPB;
-  const int nel = min(EPB, K - e0);
-  const int nn = nel * Np;
   const size_t KNp = (size_t)K * Np;
-  const size_t base = (size_t)e0 * Np;
-  // sigma = 0 wherever eps = 0, and the right-hand side reads sigma only where eps > 0: a block
-  // whose elements all have eps = 0 has nothing to do
-  if (!__syncthreads_or(tid < nel && eps[e0 + tid] > 0.0)) return;
-
+  const int count = list[0];
   for (int i = tid; i < O::OPS; i += blockDim.x) sOps[i] = ops_g[i];
   for (int i = tid; i < NF; i += blockDim.x) sFm[i] = fmask_g[i];
-  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)e0 * GS + i];
+  for (int g0 = blockIdx.x * EPB; g0 < count; g0 += gridDim.x * EPB) {
+  const int nel = min(EPB, count - g0);
+  const int nn = nel * Np;
+  __syncthreads();  // the previous group's reads of sE, sGeo, sW and sJ are done
+  if (tid < nel) sE[tid] = list[1 + g0 + tid];
+  __syncthreads();
+  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)sE[i / GS] * GS + i % GS];
 #pragma unroll
   for (int v = 0; v < W; ++v)
-    for (int i = tid; i < nn; i += blockDim.x) sW[v * NODES + i] = q[v * KNp + base + i];
+    for (int i = tid; i < nn; i += blockDim.x) sW[v * NODES + i] = q[v * KNp + (size_t)sE[i / Np] * Np + i % Np];
   __syncthreads();
 
   for (int j = tid; j < nel * NF; j += blockDim.x) {
@@ -102,8 +107,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
     const double* G = sGeo + e * GS;
     const double hf = 0.5 * G[12 + 4 * f];
     const int own = e * Np + sFm[m];
-    const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
-    const size_t Pn = P >= 0 ? (size_t)P : base + own;  // a boundary node gathers its own trace
+    const int P = vmapP[(size_t)sE[e] * NF + m];  // < 0: boundary face node, -DG_BC_* code
+    const size_t Pn = P >= 0 ? (size_t)P : (size_t)sE[e] * Np + sFm[m];  // a boundary node gathers its own trace
     double qm[W], qp[W];
 #pragma unroll
     for (int v = 0; v < W; ++v) {
@@ -161,47 +166,57 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
 #pragma unroll
         for (int v = 0; v < W; ++v) grad[d][v] = fma(nf[d], lf[v], grad[d][v]);
     }
-    const double ee = eps[e0 + e];
-    const size_t gi = base + tid;
-    if (ee > 0.0)
+    const double ee = eps[sE[e]];
+    const size_t gi = (size_t)sE[e] * Np + i;
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * grad[d][v];
+      for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * grad[d][v];
+  }
   }
 }
 
 template <int N>
-cudaError_t launch_sensor_t(const MeshDev& m, const double* q, double* eps, cudaStream_t s) {
+cudaError_t launch_sensor_t(const MeshDev& m, const double* q, double* eps, int* list, cudaStream_t s) {
   using O = Ord<N>;
   const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  av_sensor_kernel<N><<<blocks, O::NT, 0, s>>>(q, m.modal, m.ntop, m.av, m.K, eps);
+  if (list) {
+    cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
+  av_sensor_kernel<N><<<blocks, O::NT, 0, s>>>(q, m.modal, m.ntop, m.av, m.K, eps, list);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_flux_t(const MeshDev& m, const double* q, cudaStream_t s) {
   using O = Ord<N>;
-  constexpr size_t smem = viscous_smem<N>();
-  static bool configured = false;
-  if (!configured) {
+  constexpr size_t smem = viscous_smem<N>() + sizeof(int) * O::EPB;
+  static int grid_cap = 0;
+  if (!grid_cap) {  // a persistent grid: the blocks that fit on the device at once
     cudaError_t e = cudaFuncSetAttribute(av_flux_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, av_flux_kernel<N>, O::NT, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid_cap = std::max(1, per_sm) * sms;
   }
-  const int blocks = (m.K + O::EPB - 1) / O::EPB;
-  av_flux_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.av_eps, m.av_sig, m.ops, m.fmask, m.geo, m.vmapP, m.bc, m.K);
+  const int blocks = std::min((m.K + O::EPB - 1) / O::EPB, grid_cap);
+  av_flux_kernel<N><<<blocks, O::NT, smem, s>>>(q, m.av_eps, m.av_sig, m.ops, m.fmask, m.geo, m.vmapP, m.bc, m.K,
+                                                 m.av_list);
   return cudaGetLastError();
 }
 
 }  // namespace kern
 
-cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s) {
+cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s, int* list) {
   switch (m.N) {
-    case 1: return kern::launch_sensor_t<1>(m, q, eps, s);
-    case 2: return kern::launch_sensor_t<2>(m, q, eps, s);
-    case 3: return kern::launch_sensor_t<3>(m, q, eps, s);
-    case 4: return kern::launch_sensor_t<4>(m, q, eps, s);
+    case 1: return kern::launch_sensor_t<1>(m, q, eps, list, s);
+    case 2: return kern::launch_sensor_t<2>(m, q, eps, list, s);
+    case 3: return kern::launch_sensor_t<3>(m, q, eps, list, s);
+    case 4: return kern::launch_sensor_t<4>(m, q, eps, list, s);
     default: return cudaErrorInvalidValue;
   }
 }
