@@ -287,7 +287,6 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
     viscous flux follows the tetrahedral reading (oracle/boundary.py): walls adiabatic
     (E_d+ = -E_d-), a slip wall shear-free (tau_id+ = -tau_id- for i != d, tau_dd+ = tau_dd-),
     inflow and outflow the interior flux."""
-    from .boundary import NOSLIP_WALL, SLIP_WALL
     from .ns import viscous_flux
     N = ref.N
     q = np.asarray(q, dtype=np.float64)
@@ -304,6 +303,18 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
     for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
         rhs[sel] += lift * (fm - fstar)
     # central viscous flux: the face term gains -n.(Fv- - Fv+)/2
+    for d, end, sel, lift, nd, fvm, fvp in _viscous_face_traces(ref, box, Fv5):
+        rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
+    return rhs.reshape(q.shape)
+
+
+def _viscous_face_traces(ref, box, Fv5):
+    """Per axis d and end: the face's node slice, lift factor (2/h_d)/w_end, normal sign, and the
+    interior and exterior viscous fluxes along d [5][...]; at a box boundary the exterior flux is
+    the interior one, except that walls are adiabatic (E_d+ = -E_d-) and a slip wall is shear-free
+    (tau_id+ = -tau_id- for i != d)."""
+    from .boundary import NOSLIP_WALL, SLIP_WALL
+    N = ref.N
     for d in range(3):
         for end in (0, 1):
             nd = -1.0 if end == 0 else 1.0
@@ -323,8 +334,7 @@ def hex_rhs_ns(ref, box, q, gas, mu, Pr, q_in=None):
                 on = _boundary_elements(box, d, end).reshape((1, -1, 1, 1))
                 fvp = np.where(on, ghost, fvp)
             lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
-            rhs[sel] -= lift * nd * 0.5 * (fvm - fvp)
-    return rhs.reshape(q.shape)
+            yield d, end, sel, lift, nd, fvm, fvp
 
 
 def _gauss_operators(ref, Q):
@@ -349,8 +359,9 @@ def _along_rect(Mx, a, axis):
     return np.moveaxis(a @ Mx.T, -1, ax)
 
 
-def hex_overint_volume(ref, box, q5, gas, Q):
-    """Over-integrated volume term [5][K][M][M][M] of the weak form."""
+def hex_overint_volume(ref, box, q5, gas, Q, Fv5=None):
+    """Over-integrated volume term [5][K][M][M][M] of the weak form; with a nodal viscous flux
+    Fv5 [3][5][K][M][M][M], of G = F(I q) - I Fv."""
     I, A, B = _gauss_operators(ref, Q)
     qg = q5
     for d in range(3):
@@ -359,6 +370,11 @@ def hex_overint_volume(ref, box, q5, gas, Q):
     out = np.zeros_like(q5)
     for d in range(3):
         t = Fg[d]
+        if Fv5 is not None:
+            fvg = Fv5[d]
+            for e in range(3):
+                fvg = _along_rect(I, fvg, e)
+            t = t - fvg
         for e in range(3):
             t = _along_rect(A if e == d else B, t, e)
         out += (2.0 / box["h"][d]) * t
@@ -436,3 +452,25 @@ def hex_integrate(ref, box, u):
     w3 = (ref.w[None, None, :] * ref.w[None, :, None] * ref.w[:, None, None]).ravel()  # [Np] with k, j, i
     J = np.prod(box["h"]) / 8.0
     return J * np.tensordot(u, w3, axes=([-1], [0])).sum(axis=-1)
+
+
+def hex_rhs_overint_ns(ref, box, q, gas, mu, Pr, Q, q_in=None):
+    """Weak-form Navier-Stokes right-hand side with over-integrated volume fluxes (Q Gauss points per
+    axis): the whole flux G = F - Fv on the points, with the nodal BR1 viscous flux Fv interpolated
+    to them (a degree-N field per axis, so its part is exact), and the weak-form face term with the
+    central viscous flux and the walls' exterior viscous fluxes of hex_rhs_ns."""
+    from .ns import viscous_flux
+    N = ref.N
+    q = np.asarray(q, dtype=np.float64)
+    T = gas.temperature(q)
+    w = np.stack([q[0], q[1], q[2], q[3], T])
+    grad = hex_gradient(ref, box, w, q, gas, q_in)
+    Fv = viscous_flux(q, T, grad, mu, mu * gas.cp / Pr)  # [3][5][K][Np]
+    q5 = _shape(q, N)
+    Fv5 = Fv.reshape((3, 5) + q5.shape[1:])
+    rhs = hex_overint_volume(ref, box, q5, gas, Q, Fv5)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
+        rhs[sel] -= lift * fstar
+    for d, end, sel, lift, nd, fvm, fvp in _viscous_face_traces(ref, box, Fv5):
+        rhs[sel] += lift * nd * 0.5 * (fvm + fvp)
+    return rhs.reshape(q.shape)

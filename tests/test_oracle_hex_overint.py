@@ -1,7 +1,10 @@
 """Pins of the over-integrated hexahedral right-hand side (oracle/hex.py: hex_rhs_overint):
 freestream preservation, conservation, exact integration of polynomial fluxes (Q >= 2N Gauss points
 reproduce a 24-point rule for fluxes of degree 3N, while N + 1 points alias them), convergence to
-the translating vortex; planted mistakes must break a pin."""
+the translating vortex; and of its Navier-Stokes form (hex_rhs_overint_ns): for a gas at rest with a
+temperature of x alone its viscous part is the collocated one (adiabatic walls included),
+conservation in periodic and no-slip boxes, a steady rest state between walls; planted mistakes
+must break a pin."""
 
 import numpy as np
 import pytest
@@ -106,3 +109,89 @@ def test_planted_swapped_operators_fail(monkeypatch):
     orig = hx._gauss_operators
     monkeypatch.setattr(hx, "_gauss_operators", lambda ref, Q: (lambda I, A, B: (I, B, A))(*orig(ref, Q)))
     assert not _all_pins_hold()
+
+
+# --- Navier-Stokes ---------------------------------------------------------------------------------
+
+import oracle.boundary as bd  # noqa: E402
+
+MU, PR = 2e-2, 0.71
+
+
+def _ns_case(N, bc, n=(2, 2, 2)):
+    box = hex_box(n, 1.0)
+    box["bc"] = bc
+    ref = hx.hex_reference(gll_nodes(N))
+    return box, ref, hex_nodes(box, ref.nodes)
+
+
+def _ns_state(rho, u, v, w, p):
+    E = p / 0.4 + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E])
+
+
+def _ns_viscous_part_is_collocated(N=3):
+    """A gas at rest with a temperature of x alone between a no-slip wall at x = 0 and a slip wall
+    at x = 1: the viscous flux is the heat flux kappa T'(x) along x only, a field of x alone, on
+    which the rule and the collocation agree; so the viscous part (Navier-Stokes minus Euler) of
+    the over-integrated right-hand side is that of the collocated one.  (The whole right-hand sides
+    differ: the pressure enters the transverse momentum fluxes, across which the collocation lumps
+    the mass and the rule does not.)"""
+    box, ref, xyz = _ns_case(N, ((bd.NOSLIP_WALL, bd.SLIP_WALL), (0, 0), (0, 0)))
+    x = xyz[..., 0]
+    one = np.ones_like(x)
+    p = 1.0 + 0.1 * (x - 0.5) ** N + 0.05 * np.sin(3 * x)
+    q = _ns_state(one, 0 * one, 0 * one, 0 * one, p)
+    Q = _q32(N)
+    vo = hx.hex_rhs_overint_ns(ref, box, q, GAS, MU, PR, Q) - hx.hex_rhs_overint(ref, box, q, GAS, Q)
+    vc = hx.hex_rhs_ns(ref, box, q, GAS, MU, PR) - hx.hex_rhs_ns(ref, box, q, GAS, 0.0, PR)
+    return np.abs(vo - vc).max() <= 1e-11 * np.abs(vc).max() and np.abs(vc).max() > 1e-3
+
+
+def _ns_conserves(N=3):
+    box, ref, xyz = _ns_case(N, ((0, 0), (0, 0), (0, 0)), n=(3, 2, 2))
+    q = isentropic_vortex(xyz, 0.0, center=(0.45, 0.55), radius=0.15, period=box["L"])
+    r = hx.hex_rhs_overint_ns(ref, box, q, GAS, MU, PR, _q32(N))
+    periodic = bool(np.all(np.abs(hx.hex_integrate(ref, box, r)) <= 1e-12 * hx.hex_integrate(ref, box, np.abs(r))))
+    box, ref, xyz = _ns_case(N, ((bd.NOSLIP_WALL,) * 2, (bd.NOSLIP_WALL,) * 2, (bd.NOSLIP_WALL,) * 2))
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    qb = _ns_state(1.0 + 0.1 * np.sin(2 * x), 0.1 * np.sin(3 * y), 0.05 * np.cos(2 * x), 0 * x, 0.8 + 0.05 * z)
+    rb = hx.hex_rhs_overint_ns(ref, box, qb, GAS, MU, PR, _q32(N))
+    ib, ab = hx.hex_integrate(ref, box, rb), hx.hex_integrate(ref, box, np.abs(rb))
+    closed = abs(ib[0]) <= 1e-12 * ab[0] and abs(ib[4]) <= 1e-12 * ab[4]
+    return periodic and closed
+
+
+def _ns_rest(N=3):
+    box, ref, xyz = _ns_case(N, ((bd.NOSLIP_WALL,) * 2, (bd.NOSLIP_WALL,) * 2, (bd.SLIP_WALL,) * 2))
+    one = np.ones(xyz.shape[:-1])
+    q = _ns_state(one, 0 * one, 0 * one, 0 * one, 0.8 * one)
+    return np.abs(hx.hex_rhs_overint_ns(ref, box, q, GAS, MU, PR, _q32(N))).max() <= 1e-11
+
+
+def test_ns_viscous_part_is_the_collocated_one():
+    assert _ns_viscous_part_is_collocated(2)
+    assert _ns_viscous_part_is_collocated(3)
+
+
+def test_ns_conservation_and_rest_state():
+    assert _ns_conserves(2)
+    assert _ns_rest(2)
+    assert _ns_rest(3)
+
+
+def _ns_pins_hold():
+    return _ns_viscous_part_is_collocated(2) and _ns_conserves(2) and _ns_rest(2)
+
+
+_VOL = hx.hex_overint_volume
+
+
+@pytest.mark.parametrize("plant", ["no_viscous_volume", "viscous_faces_dropped"])
+def test_planted_ns_mistake_fails(plant, monkeypatch):
+    assert _ns_pins_hold()
+    if plant == "no_viscous_volume":
+        monkeypatch.setattr(hx, "hex_overint_volume", lambda ref, box, q5, gas, Q, Fv5=None: _VOL(ref, box, q5, gas, Q))
+    else:
+        monkeypatch.setattr(hx, "_viscous_face_traces", lambda ref, box, Fv5: iter(()))
+    assert not _ns_pins_hold()
