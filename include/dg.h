@@ -663,8 +663,10 @@ int dg_hex_av_viscosity(dg_hex_mesh mesh, const double* q_dev, double* eps_dev, 
  * enable != 0 the Euler right-hand side uses the weak form with its volume integral evaluated on
  * Q = ceil(3 (N+1) / 2) Gauss-Legendre points per axis (the state interpolated there, the fluxes
  * evaluated there, contracted back with W^-1 (I D)^T W_Q and W^-1 I^T W_Q); the face terms are
- * the collocated weak-form ones.  Euler only: a viscous gas or artificial viscosity with it is
- * DG_ERR_UNSUPPORTED at the right-hand side. */
+ * the collocated weak-form ones.  Navier-Stokes: the whole flux G = F - Fv is integrated on the
+ * points, the nodal BR1 viscous flux interpolated to them, and the face terms take the central
+ * viscous flux with the walls' exterior viscous fluxes of the collocated form.  Artificial
+ * viscosity with it is DG_ERR_UNSUPPORTED at the right-hand side. */
 int dg_hex_set_overintegration(dg_hex_mesh mesh, int32_t enable);
 /* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
 int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);

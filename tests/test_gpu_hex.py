@@ -400,13 +400,44 @@ def test_hex_overintegrated_with_boundaries_and_rk_steps():
     assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
 
 
-def test_hex_overintegration_is_euler_only():
-    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
-    from paper_2512_17101_gb300 import capi
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc", [None, "closed"])
+def test_hex_overintegrated_ns_rhs(N, bc):
+    """Navier-Stokes with over-integration: periodic, and closed by no-slip and slip walls."""
+    if bc is None:
+        torch, dg, box, ref, q0, mesh, gas = _setup((3, 2, 2), N)
+        q_in = None
+    else:
+        torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((3, 2, 2), N, HEX_BC[bc])
     mesh.set_overintegration(True)
     ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
     q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, ns, q, rhs)
+    want = hx.hex_rhs_overint_ns(ref, box, q0, GAS, NS_MU, NS_PR, _q32(N), q_in=q_in)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_overintegrated_ns_channel_rk_steps():
+    torch, dg, box, ref, q0, mesh, gas, q_in = _bc_setup((4, 3, 2), 3, HEX_BC["channel"])
+    mesh.set_overintegration(True)
+    ns = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    dt = 1e-3
+    q = torch.tensor(q0, device="cuda")
+    dg.hex_lsrk4_step(mesh, ns, q, dt, steps=2)
+    f = lambda u: hx.hex_rhs_overint_ns(ref, box, u, GAS, NS_MU, NS_PR, _q32(3), q_in=q_in)
+    want = lsrk4_step(lsrk4_step(q0, dt, f), dt, f)
+    assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
+
+
+def test_hex_overintegration_refuses_artificial_viscosity():
+    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
+    from paper_2512_17101_gb300 import capi
+    mesh.set_overintegration(True)
+    mesh.set_av(1e-2)
+    q = torch.tensor(q0, device="cuda")
     with pytest.raises(capi.DGError):
-        dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
-    mesh.set_overintegration(False)
-    dg.dg_hex_rhs(mesh, ns, q, torch.empty_like(q))
+        dg.dg_hex_rhs(mesh, gas, q, torch.empty_like(q))
+    mesh.set_av(0.0)
+    dg.dg_hex_rhs(mesh, gas, q, torch.empty_like(q))
