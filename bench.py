@@ -936,10 +936,27 @@ def hex_form(args, local):
         b.record()
         torch.cuda.synchronize()
         total_oi += a.elapsed_time(b)
-    mesh.set_overintegration(False)
     if mesh.status() != 0:
         raise SystemExit("status flags set in the over-integrated hexahedral run")
     ms_oi = total_oi / steps
+    # and the Navier-Stokes steps with over-integration
+    qon = q0.clone()
+    for _ in range(max(3, args.warmup)):
+        dg.hex_lsrk4_step(mesh, ns, qon, cfg.dt, steps=1, work=work)
+    qon.copy_(q0)
+    total_oin = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.hex_lsrk4_step(mesh, ns, qon, cfg.dt, steps=1, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        total_oin += a.elapsed_time(b)
+    mesh.set_overintegration(False)
+    if mesh.status() != 0:
+        raise SystemExit("status flags set in the over-integrated hexahedral Navier-Stokes run")
+    ms_oin = total_oin / steps
     M = cfg.N + 1
     stage_s = ms * 1e-3 / 5
     flops, nbytes = hex_flops_per_element(M) * cfg.K, hex_bytes_per_element(M) * cfg.K
@@ -972,7 +989,8 @@ def hex_form(args, local):
             "navier_stokes": {"mu": 1e-3, "Pr": 0.71, "ms_per_step": ms_ns,
                               "value": cfg.dofs * 5 / (ms_ns * 1e-3), "unit": "DOF-updates/s"},
             "overintegrated": {"gauss_points_per_axis": (3 * M + 1) // 2, "ms_per_step": ms_oi,
-                               "value": cfg.dofs * 5 / (ms_oi * 1e-3), "unit": "DOF-updates/s"},
+                               "value": cfg.dofs * 5 / (ms_oi * 1e-3), "unit": "DOF-updates/s",
+                               "navier_stokes_ms_per_step": ms_oin},
             "l2": "256 MiB buffer written before every timed step (outside the step's events)"}
 
 
