@@ -474,3 +474,38 @@ def hex_rhs_overint_ns(ref, box, q, gas, mu, Pr, Q, q_in=None):
     for d, end, sel, lift, nd, fvm, fvp in _viscous_face_traces(ref, box, Fv5):
         rhs[sel] += lift * nd * 0.5 * (fvm + fvp)
     return rhs.reshape(q.shape)
+
+
+def hex_rhs_overint_av(ref, box, q, gas, eps, Q, mu=0.0, Pr=0.71, q_in=None):
+    """The over-integrated Euler (mu = 0) or Navier-Stokes right-hand side with the artificial-
+    viscosity term of hex_rhs_av: its flux sigma = eps grad_h q (a degree-N field per axis in each
+    element) is interpolated to the Gauss points and integrated with the other fluxes, and the
+    face terms gain its central flux n.(sigma- + sigma+)/2, sigma+ = sigma- at box boundaries."""
+    from .ns import viscous_flux
+    N = ref.N
+    q = np.asarray(q, dtype=np.float64)
+    q5 = _shape(q, N)
+    sig5 = (eps[None, None, :, None] * hex_gradient_state(ref, box, q, q_in)).reshape((3, 5) + q5.shape[1:])
+    Fv5 = None
+    if mu > 0:
+        T = gas.temperature(q)
+        grad = hex_gradient(ref, box, np.stack([q[0], q[1], q[2], q[3], T]), q, gas, q_in)
+        Fv5 = viscous_flux(q, T, grad, mu, mu * gas.cp / Pr).reshape((3, 5) + q5.shape[1:])
+    rhs = hex_overint_volume(ref, box, q5, gas, Q, sig5 if Fv5 is None else Fv5 + sig5)
+    for sel, lift, fm, fstar in _surface_terms(ref, box, q5, gas, q_in):
+        rhs[sel] -= lift * fstar
+    if Fv5 is not None:
+        for d, end, sel, lift, nd, fvm, fvp in _viscous_face_traces(ref, box, Fv5):
+            rhs[sel] += lift * nd * 0.5 * (fvm + fvp)
+    for d in range(3):
+        for end in (0, 1):
+            nd = -1.0 if end == 0 else 1.0
+            nb = _neighbour(box, d, -1 if end == 0 else 1)
+            sel = _face_slices(N, d, end)
+            sm = sig5[d][sel]
+            sp = sig5[d][:, nb][_face_slices(N, d, 1 - end)]
+            if box.get("bc", ((0, 0), (0, 0), (0, 0)))[d][end]:
+                sp = np.where(_boundary_elements(box, d, end).reshape((1, -1, 1, 1)), sm, sp)
+            lift = (2.0 / box["h"][d]) / ref.w[0 if end == 0 else N]
+            rhs[sel] += lift * nd * 0.5 * (sm + sp)
+    return rhs.reshape(q.shape)

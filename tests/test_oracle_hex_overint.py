@@ -3,8 +3,9 @@ freestream preservation, conservation, exact integration of polynomial fluxes (Q
 reproduce a 24-point rule for fluxes of degree 3N, while N + 1 points alias them), convergence to
 the translating vortex; and of its Navier-Stokes form (hex_rhs_overint_ns): for a gas at rest with a
 temperature of x alone its viscous part is the collocated one (adiabatic walls included),
-conservation in periodic and no-slip boxes, a steady rest state between walls; planted mistakes
-must break a pin."""
+conservation in periodic and no-slip boxes, a steady rest state between walls; with artificial
+viscosity (hex_rhs_overint_av), for a state of x alone its AV part is the collocated AV term, and
+periodic boxes conserve; planted mistakes must break a pin."""
 
 import numpy as np
 import pytest
@@ -180,8 +181,40 @@ def test_ns_conservation_and_rest_state():
     assert _ns_rest(3)
 
 
+def _av_part_is_collocated(N=3, mu=0.0):
+    """A state of x alone with the element viscosities varying along x, between walls at x = 0 and
+    x = 1: the AV flux is along x only and a field of x alone, so the AV part of the
+    over-integrated right-hand side (with minus without AV) equals the collocated AV term."""
+    box, ref, xyz = _ns_case(N, ((bd.SLIP_WALL, bd.NOSLIP_WALL), (0, 0), (0, 0)), n=(3, 1, 1))
+    x = xyz[..., 0]
+    rho = 1.0 + 0.2 * np.sin(3 * x)
+    q = _ns_state(rho, 0.3 + 0.1 * np.cos(2 * x), 0 * x, 0 * x, 1.0 + 0.1 * x ** 2)
+    eps = np.array([0.0, 0.02, 0.05])
+    Q = _q32(N)
+    with_av = hx.hex_rhs_overint_av(ref, box, q, GAS, eps, Q, mu=mu, Pr=PR)
+    without = hx.hex_rhs_overint_av(ref, box, q, GAS, 0 * eps, Q, mu=mu, Pr=PR)
+    want = hx.hex_rhs_av(ref, box, q, eps)
+    return np.abs((with_av - without) - want).max() <= 1e-11 * np.abs(want).max() and np.abs(want).max() > 1e-3
+
+
+def _av_conserves(N=2):
+    box, ref, xyz = _ns_case(N, ((0, 0), (0, 0), (0, 0)), n=(3, 2, 2))
+    q = isentropic_vortex(xyz, 0.0, center=(0.45, 0.55), radius=0.15, period=box["L"])
+    eps = np.linspace(0.0, 0.03, q.shape[1])
+    r = hx.hex_rhs_overint_av(ref, box, q, GAS, eps, _q32(N), mu=MU, Pr=PR)
+    return bool(np.all(np.abs(hx.hex_integrate(ref, box, r)) <= 1e-12 * hx.hex_integrate(ref, box, np.abs(r))))
+
+
+def test_av_part_is_the_collocated_one():
+    assert _av_part_is_collocated(2)
+    assert _av_part_is_collocated(3)
+    assert _av_part_is_collocated(3, mu=MU)
+    assert _av_conserves(2)
+
+
 def _ns_pins_hold():
-    return _ns_viscous_part_is_collocated(2) and _ns_conserves(2) and _ns_rest(2)
+    return (_ns_viscous_part_is_collocated(2) and _ns_conserves(2) and _ns_rest(2)
+            and _av_part_is_collocated(2))
 
 
 _VOL = hx.hex_overint_volume
