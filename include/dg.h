@@ -666,7 +666,8 @@ int dg_hex_av_viscosity(dg_hex_mesh mesh, const double* q_dev, double* eps_dev, 
  * the collocated weak-form ones.  Navier-Stokes: the whole flux G = F - Fv is integrated on the
  * points, the nodal BR1 viscous flux interpolated to them, and the face terms take the central
  * viscous flux with the walls' exterior viscous fluxes of the collocated form.  Artificial
- * viscosity with it is DG_ERR_UNSUPPORTED at the right-hand side. */
+ * viscosity: its flux sigma = eps grad_h q joins the fluxes on the points and its central flux the
+ * face terms. */
 int dg_hex_set_overintegration(dg_hex_mesh mesh, int32_t enable);
 /* DG_STATUS_* bits of the mesh (rho <= 0 or p <= 0 met); synchronises the device. */
 int dg_hex_status(dg_hex_mesh mesh, uint32_t* bits, int reset);

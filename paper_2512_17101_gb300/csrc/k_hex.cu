@@ -595,14 +595,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_av_flux_kernel(const double
 // B = W^-1 I^T W_Q along the other axes; the face terms are the collocated weak-form ones,
 // -(2/h_d)/w_end n.F*.  Everything per element stays in shared memory: the interpolated state
 // (three passes), each direction's fluxes at the Gauss points and their three contractions.
-template <int N, bool VISC = false>
+template <int N, bool VISC = false, bool AV = false>
 struct OiCfg {
   static constexpr int M = N + 1, Q = (3 * (N + 1) + 1) / 2, Np = M * M * M;
   static constexpr int EPB = N == 1 ? 16 : (N == 2 ? 4 : (N == 3 ? 2 : 1));
   static constexpr int NT = 256;
   // doubles per element: nodal state, x-, y- and z-interpolated state, fluxes, volume and face terms;
-  // VISC: the four nodal viscous-flux components of one direction and their Gauss-point values
-  static constexpr int PER = 5 * (Np + M * M * Q + M * Q * Q + 2 * Q * Q * Q + 2 * Np) + (VISC ? 4 * (Np + Q * Q * Q) : 0);
+  // VISC or AV: the nodal diffusive flux (viscous and artificial) of one direction, five rows, and
+  // its Gauss-point values
+  static constexpr int PER = 5 * (Np + M * M * Q + M * Q * Q + 2 * Q * Q * Q + 2 * Np) + (VISC || AV ? 5 * (Np + Q * Q * Q) : 0);
   static constexpr size_t SMEM = sizeof(double) * PER * EPB + sizeof(int) * 6 * EPB;
 };
 
@@ -612,13 +613,15 @@ struct HexOI {
   double B[40];  // [M][Q]
 };
 
-template <int N, bool RK, bool VISC>
-__global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
+template <int N, bool RK, bool VISC, bool AV>
+__global__ void __launch_bounds__(OiCfg<N, VISC, AV>::NT) hex_oi_kernel(const double* __restrict__ q, double* __restrict__ out,
                                                                double* __restrict__ kreg, const HexGeo geo,
                                                                const HexOI op, const int64_t K, const double gamma,
                                                                const double a, const double b, const int accumulate,
-                                                               unsigned* __restrict__ status, const double* __restrict__ fv) {
-  using C = OiCfg<N, VISC>;
+                                                               unsigned* __restrict__ status, const double* __restrict__ fv,
+                                                               const double* __restrict__ sig, const double* __restrict__ eps) {
+  using C = OiCfg<N, VISC, AV>;
+  constexpr bool DIF = VISC || AV;  // a diffusive flux (viscous, artificial or both) joins F
   constexpr int M = C::M, Q = C::Q, Np = C::Np, EPB = C::EPB, NT = C::NT;
   constexpr int M2 = M * M, Q2 = Q * Q, Q3 = Q * Q * Q;
   extern __shared__ double sm[];
@@ -629,9 +632,9 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
   double* sF = sC + 5 * EPB * Q3;       // [5][EPB][Q][Q][Q]  flux along d at the Gauss points
   double* acc = sF + 5 * EPB * Q3;      // [5][EPB][Np]       volume term
   double* sS = acc + 5 * EPB * Np;      // [5][EPB][Np]       face terms
-  double* sFvN = sS + 5 * EPB * Np;     // VISC: [4][EPB][Np] nodal tau_1d, tau_2d, tau_3d, Q_d
-  double* sV = sFvN + (VISC ? 4 * EPB * Np : 0);  // VISC: [4][EPB][Q][Q][Q] the same at the Gauss points
-  int(*sNb)[6] = reinterpret_cast<int(*)[6]>(sV + (VISC ? 4 * EPB * Q3 : 0));
+  double* sFvN = sS + 5 * EPB * Np;     // DIF: [5][EPB][Np] the nodal diffusive flux along d, row by row
+  double* sV = sFvN + (DIF ? 5 * EPB * Np : 0);  // DIF: [5][EPB][Q][Q][Q] the same at the Gauss points
+  int(*sNb)[6] = reinterpret_cast<int(*)[6]>(sV + (DIF ? 5 * EPB * Q3 : 0));
   const int tid = threadIdx.x;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int nel = (int)min((int64_t)EPB, K - e0);
@@ -695,16 +698,19 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
   }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    if constexpr (VISC) {
-      // the viscous flux along d (tau_id, Q_d) at the Gauss points: three interpolation passes
-      // through the sA and sB scratch, as for the state
-      for (int t = tid; t < 4 * nn; t += NT) {
-        const int c = t / nn, r = t - c * nn;
-        const int comp = c < 3 ? hex_tau(c, d) : 6 + d;
-        sFvN[c * EPB * Np + r] = fv[comp * KNp + base + r];
+    if constexpr (DIF) {
+      // the diffusive flux along d at the Gauss points, row v: the viscous tau_(v-1)d or Q_d
+      // (VISC) plus the artificial sigma_dv where the element has eps > 0 (AV); three interpolation
+      // passes through the sA and sB scratch, as for the state
+      for (int t = tid; t < 5 * nn; t += NT) {
+        const int v = t / nn, r = t - v * nn;
+        double f = 0.0;
+        if (VISC && v > 0) f = fv[(v < 4 ? hex_tau(v - 1, d) : 6 + d) * KNp + base + r];
+        if (AV && eps[e0 + r / Np] > 0.0) f += sig[(5 * d + v) * KNp + base + r];
+        sFvN[v * EPB * Np + r] = f;
       }
       __syncthreads();
-      for (int t = tid; t < 4 * nel * M2 * Q; t += NT) {
+      for (int t = tid; t < 5 * nel * M2 * Q; t += NT) {
         const int v = t / (nel * M2 * Q), r = t - v * nel * M2 * Q, el = r / (M2 * Q), s2 = r - el * M2 * Q;
         const int kj = s2 / Q, qa = s2 - kj * Q;
         const double* src = sFvN + v * EPB * Np + el * Np + kj * M;
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
         sA[v * EPB * M2 * Q + el * M2 * Q + s2] = c;
       }
       __syncthreads();
-      for (int t = tid; t < 4 * nel * M * Q2; t += NT) {
+      for (int t = tid; t < 5 * nel * M * Q2; t += NT) {
         const int v = t / (nel * M * Q2), r = t - v * nel * M * Q2, el = r / (M * Q2), s2 = r - el * M * Q2;
         const int k = s2 / Q2, qb = (s2 / Q) % Q, qa = s2 % Q;
         const double* src = sA + v * EPB * M2 * Q + el * M2 * Q + k * M * Q + qa;
@@ -724,7 +730,7 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
         sB[v * EPB * M * Q2 + el * M * Q2 + s2] = c;
       }
       __syncthreads();
-      for (int t = tid; t < 4 * nel * Q3; t += NT) {
+      for (int t = tid; t < 5 * nel * Q3; t += NT) {
         const int v = t / (nel * Q3), r = t - v * nel * Q3, el = r / Q3, s2 = r - el * Q3;
         const int qc = s2 / Q2, qba = s2 - qc * Q2;
         const double* src = sB + v * EPB * M * Q2 + el * M * Q2 + qba;
@@ -751,9 +757,9 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
       sF[2 * EPB * Q3 + t] = qv[2] * ud + (d == 1 ? p : 0.0);
       sF[3 * EPB * Q3 + t] = qv[3] * ud + (d == 2 ? p : 0.0);
       sF[4 * EPB * Q3 + t] = ud * (qv[4] + p);
-      if constexpr (VISC) {  // G_d = F_d - Fv_d
+      if constexpr (DIF) {  // G_d = F_d minus the diffusive flux
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sF[(1 + c) * EPB * Q3 + t] -= sV[c * EPB * Q3 + t];
+        for (int v = 0; v < 5; ++v) sF[v * EPB * Q3 + t] -= sV[v * EPB * Q3 + t];
       }
     }
     __syncthreads();
@@ -850,6 +856,15 @@ __global__ void __launch_bounds__(OiCfg<N, VISC>::NT) hex_oi_kernel(const double
 #pragma unroll
             for (int i = 0; i < 3; ++i)
               if (i != d) fp[1 + i] += 2.0 * fv[hex_tau(i, d) * KNp + gM];
+        }
+      }
+      if constexpr (AV) {  // the central AV flux; at a box boundary the exterior flux is the interior one
+        const size_t gM = base + loc;
+        const bool onM = eps[e0 + el] > 0.0, onP = enb >= 0 ? eps[enb] > 0.0 : onM;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (onM) fm[v] -= sig[(5 * d + v) * KNp + gM];
+          if (onP) fp[v] -= sig[(5 * d + v) * KNp + gP];
         }
       }
       // -(2/h_d)/w_end n.G* = -(sgn (G_d- + G_d+) + lam (q- - q+)) (2/h_d)/w_end / 2 (times s)
@@ -1065,14 +1080,14 @@ cudaError_t launch_rk(const dg_hex_mesh_s& m, const GasParams& g, const double* 
             : launch_t<N, false, VISC, AV>(m, g.gamma, q, out, k, a, b, dt, s);
 }
 
-template <int N, bool RK, bool VISC>
+template <int N, bool RK, bool VISC, bool AV>
 cudaError_t launch_oi_t(const dg_hex_mesh_s& m, double gamma, const double* q, double* out, double* k, double a,
                         double b, double dt, cudaStream_t s) {
-  using C = OiCfg<N, VISC>;
+  using C = OiCfg<N, VISC, AV>;
   static bool configured = false;
   if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(hex_oi_kernel<N, RK, VISC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)C::SMEM);
+    const cudaError_t e = cudaFuncSetAttribute(hex_oi_kernel<N, RK, VISC, AV>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -1081,31 +1096,37 @@ cudaError_t launch_oi_t(const dg_hex_mesh_s& m, double gamma, const double* q, d
   for (size_t i = 0; i < m.oi_A.size(); ++i) op.A[i] = m.oi_A[i];
   for (size_t i = 0; i < m.oi_B.size(); ++i) op.B[i] = m.oi_B[i];
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
-  hex_oi_kernel<N, RK, VISC><<<(unsigned)blocks, C::NT, C::SMEM, s>>>(q, out, k, make_geo<N>(m, RK ? dt : 1.0), op,
-                                                                        m.K, gamma, a, b, a != 0.0, m.status, m.fv_dev);
+  hex_oi_kernel<N, RK, VISC, AV><<<(unsigned)blocks, C::NT, C::SMEM, s>>>(
+      q, out, k, make_geo<N>(m, RK ? dt : 1.0), op, m.K, gamma, a, b, a != 0.0, m.status, m.fv_dev, m.av_sig, m.av_eps);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_n(const dg_hex_mesh_s& m, const GasParams& g, const double* q, double* out, double* k, bool rk,
                      double a, double b, double dt, cudaStream_t s) {
-  if (m.overint && !(g.mu > 0))
-    return rk ? launch_oi_t<N, true, false>(m, g.gamma, q, out, k, a, b, dt, s)
-              : launch_oi_t<N, false, false>(m, g.gamma, q, out, k, a, b, dt, s);
+  const bool av = m.av_eps0 > 0;
+  if (m.overint && !(g.mu > 0) && !av)
+    return rk ? launch_oi_t<N, true, false, false>(m, g.gamma, q, out, k, a, b, dt, s)
+              : launch_oi_t<N, false, false, false>(m, g.gamma, q, out, k, a, b, dt, s);
   cudaError_t e;
-  {
+  if (!m.overint || g.mu > 0) {  // the primitives of the collocated kernels and of the BR1 pass
     const int64_t n = m.K * m.Np, want = (n + 255) / 256;
     hex_prims_kernel<<<(unsigned)(want < 65535 ? want : 65535), 256, 0, s>>>(q, m.prim, n, g.gamma, m.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (g.mu > 0 && (e = launch_vis_t<N>(m, g, q, s)) != cudaSuccess) return e;
-  if (m.overint)  // Navier-Stokes: the BR1 pass above, then the over-integrated right-hand side
-    return rk ? launch_oi_t<N, true, true>(m, g.gamma, q, out, k, a, b, dt, s)
-              : launch_oi_t<N, false, true>(m, g.gamma, q, out, k, a, b, dt, s);
-  const bool av = m.av_eps0 > 0;
   if (av) {
     if ((e = launch_av_sensor_t<N>(m, q, m.av_eps, s)) != cudaSuccess) return e;
     if ((e = launch_av_flux_t<N>(m, q, s)) != cudaSuccess) return e;
+  }
+  if (m.overint) {  // the BR1 and AV passes above, then the over-integrated right-hand side
+    if (g.mu > 0)
+      return av ? (rk ? launch_oi_t<N, true, true, true>(m, g.gamma, q, out, k, a, b, dt, s)
+                      : launch_oi_t<N, false, true, true>(m, g.gamma, q, out, k, a, b, dt, s))
+                : (rk ? launch_oi_t<N, true, true, false>(m, g.gamma, q, out, k, a, b, dt, s)
+                      : launch_oi_t<N, false, true, false>(m, g.gamma, q, out, k, a, b, dt, s));
+    return rk ? launch_oi_t<N, true, false, true>(m, g.gamma, q, out, k, a, b, dt, s)
+              : launch_oi_t<N, false, false, true>(m, g.gamma, q, out, k, a, b, dt, s);
   }
   if (g.mu > 0)
     return av ? launch_rk<N, true, true>(m, g, q, out, k, rk, a, b, dt, s)
@@ -1314,9 +1335,9 @@ static int hex_run(dg_hex_mesh m, dg_gas gas, const double* q, double* out, doub
   if (rk && !std::isfinite(dt)) return dg::fail(DG_ERR_INVALID_ARG, "dt must be finite");
   if (gas->p.model != DG_GAS_PERFECT)
     return dg::fail(DG_ERR_UNSUPPORTED, "the hexahedral path takes a perfect gas");
-  if (m->overint && m->av_eps0 > 0)
-    return dg::fail(DG_ERR_UNSUPPORTED, "over-integration runs without artificial viscosity on hexahedra");
-  if ((!m->overint || gas->p.mu > 0) && !m->prim) {  // the primitives buffer of the collocated and BR1 kernels
+  // the primitives buffer, which the collocated kernels and the BR1 pass read (launch_n runs the
+  // primitives pass under the same condition)
+  if ((!m->overint || gas->p.mu > 0) && !m->prim) {
     const cudaError_t e = cudaMalloc((void**)&m->prim, sizeof(double) * 3 * (size_t)m->K * m->Np);
     if (e != cudaSuccess) return dg::cuda_fail(e, "hexahedral primitives buffer");
   }

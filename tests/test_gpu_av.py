@@ -188,3 +188,32 @@ def test_mixed_rk4_steps_with_artificial_viscosity(N):
     err = field_err(q.cpu().numpy(), want)
     assert err <= 1e-6, err
     assert mesh.status() == 0
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("regime", ["none", "all"])
+def test_av_element_list_extremes(regime, mixed):
+    """Thresholds under which no element and every element has eps > 0: the flux pass's element
+    list is empty or holds all K elements; the right-hand sides match the oracle."""
+    from paper_2512_17101_gb300 import capi
+    d = box_disc((4, 2, 2), 3)
+    torch = torch_cuda()
+    from paper_2512_17101_gb300 import dg
+    mesh = dg.Mesh(d.vertices, d.period, 3, equispaced_tet_nodes(3))
+    gas = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=MU, Pr=PR)
+    q0 = _front(d.xyz)
+    th = (50.0, 1.0) if regime == "none" else (-50.0, 1.0)
+    mesh.set_av(EPS0, th[0], th[1])
+    eps = av.element_viscosity(d.ref, q0, EPS0, th[0], th[1])
+    assert (eps == 0).all() if regime == "none" else (eps == EPS0).all()
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    opts = dg._opts(precision=capi.DG_PREC_MIXED) if mixed else None
+    for _ in range(2):  # twice: the list is rebuilt, not appended to
+        dg.dg_rhs(mesh, gas, q, rhs, opts=opts)
+    want = _want(d, q0, True, th)
+    if mixed:
+        assert field_err(rhs.cpu().numpy(), want) <= MIXED_RHS_TOL
+    else:
+        assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0

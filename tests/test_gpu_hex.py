@@ -431,13 +431,30 @@ def test_hex_overintegrated_ns_channel_rk_steps():
     assert rel_err(q.cpu().numpy() - q0, want - q0) <= TOL
 
 
-def test_hex_overintegration_refuses_artificial_viscosity():
-    torch, dg, box, ref, q0, mesh, gas = _setup(2, 2)
-    from paper_2512_17101_gb300 import capi
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_hex_overintegrated_with_artificial_viscosity(N, viscous):
+    """Over-integration with the AV term on the steep front (all three regimes of the ramp), and
+    with walls at N = 3."""
+    torch, dg, box, ref, q0, mesh, gas, th = _av_setup(N)
     mesh.set_overintegration(True)
-    mesh.set_av(1e-2)
+    g = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU if viscous else 0.0, Pr=NS_PR)
     q = torch.tensor(q0, device="cuda")
-    with pytest.raises(capi.DGError):
-        dg.dg_hex_rhs(mesh, gas, q, torch.empty_like(q))
-    mesh.set_av(0.0)
-    dg.dg_hex_rhs(mesh, gas, q, torch.empty_like(q))
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, g, q, rhs)
+    want = hx.hex_rhs_overint_av(ref, box, q0, GAS, _av_eps(ref, q0, th), _q32(N),
+                                 mu=NS_MU if viscous else 0.0, Pr=NS_PR)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
+
+
+def test_hex_overintegrated_with_artificial_viscosity_and_walls():
+    torch, dg, box, ref, q0, mesh, gas, th = _av_setup(3, bc=HEX_BC["channel"])
+    mesh.set_overintegration(True)
+    g = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=NS_MU, Pr=NS_PR)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_hex_rhs(mesh, g, q, rhs)
+    want = hx.hex_rhs_overint_av(ref, box, q0, GAS, _av_eps(ref, q0, th), _q32(3), mu=NS_MU, Pr=NS_PR,
+                                 q_in=q0[:, 0, 0])
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
