@@ -198,7 +198,9 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
     if ((opts && opts->precision == DG_PREC_MIXED) || g.model != DG_GAS_PERFECT || (opts && opts->elem_range) ||
         prims_given)
       return fail(DG_ERR_UNSUPPORTED, "over-integration runs in the FP64 form with a perfect gas over the whole mesh");
-    if (!dg::overint_fits(m.N, m.oi_ng, g.mu > 0, av))
+    if ((g.mu > 0 || av) && m.oi_q <= m.N)
+      return fail(DG_ERR_UNSUPPORTED, "viscous and AV fluxes need at least N + 1 points per direction over-integrated");
+    if (!dg::overint_fits(m.N, m.oi_q, g.mu > 0, av))
       return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's viscous or AV work exceed a "
                                       "block's shared memory at this point count");
   }
@@ -557,14 +559,15 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
     return DG_OK;
   }
   if (q == DG_OVERINT_DEFAULT) q = (3 * d.N + 1) / 2;
-  if (!dg::overint_fits(d.N, q * q * q, false, false))
+  if (!dg::overint_fits(d.N, q, false, false))
     return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
   dg::OverintOps o;
   std::string err;
   if (!dg::build_overint_ops(d.N, mesh->ref_nodes.data(), q, o, err)) return fail(DG_ERR_INVALID_ARG, err);
-  std::vector<double> tab(o.IT);
-  tab.insert(tab.end(), o.w.begin(), o.w.end());
-  tab.insert(tab.end(), o.WtT.begin(), o.WtT.end());
+  // device layout: A | Aw | B | Bw | C | Cw | V_o^-T | Z^T | Dw^T (the kernel's order)
+  std::vector<double> tab;
+  for (const std::vector<double>* t : {&o.A, &o.Aw, &o.B, &o.Bw, &o.C, &o.Cw, &o.VinvT, &o.ZT, &o.DwT})
+    tab.insert(tab.end(), t->begin(), t->end());
   double* dev = nullptr;
   cudaError_t e = cudaMalloc((void**)&dev, sizeof(double) * tab.size());
   if (e == cudaSuccess) e = cudaMemcpy(dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);

@@ -36,8 +36,15 @@ bool build_ref_ops(int N, const double* nodes, RefOps& out, std::string& err);
 struct OverintOps {
   int q = 0, Ng = 0;                // points per direction, q^3 points
   std::vector<double> rst, w;       // [Ng][3] points, [Ng] weights (point (k q + j) q + i of (a_i, b_j, c_k))
-  std::vector<double> IT;           // [Np][Ng]: the nodal basis l_j at point g, transposed
-  std::vector<double> WtT;          // [3][Np][Np]: WtT[a][j][i] = (M^-1 D_a^T)[i][j]
+  // sum-factorised form: the orthonormal modes psi_pqr = A_p(a) B_pq(b) C_pqr(c) at the rule's
+  // collapsed coordinates (modes in (p, q, r) order, p outermost; pq pairs in (p, q) order); the
+  // weighted copies carry half the 1-D Gauss-Jacobi weight each, so that their product is w_g
+  std::vector<double> A, Aw;        // [N+1][q]: A_p(a_i)
+  std::vector<double> B, Bw;        // [(N+1)(N+2)/2][q]: B_pq(b_j)
+  std::vector<double> C, Cw;        // [Np][q]: C_pqr(c_k)
+  std::vector<double> VinvT;        // [Np(j)][Np(n)]: (V_o^-1)[n][j], nodal values -> mode n
+  std::vector<double> ZT;           // [3][Np(n)][Np(i)]: (M^-1 D_a^T V_o^-T)[i][n], modal moments -> nodes
+  std::vector<double> DwT;          // [3][Np(j)][Np(i)]: (M^-1 D_a^T M)[i][j], weak form of a nodal flux
 };
 bool tet_quadrature(int q, std::vector<double>& rst, std::vector<double>& w, std::string& err);
 bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::string& err);
@@ -142,8 +149,8 @@ struct MeshDev {
   double* diag = nullptr;      // per-block partials of the global reductions (k_diag.cu)
   double* prim = nullptr;      // FP64 form, perfect gas: [3][K][Np] (1/rho, p, c) of the state being
                                // differentiated, written by the primitives pass before each stage
-  // over-integration (dg_mesh_set_overint; oi_q = 0: off): [Np][Ng] nodal basis at the points,
-  // [Ng] weights, [3][Np][Np] (M^-1 D_a^T)^T (OverintOps)
+  // over-integration (dg_mesh_set_overint; oi_q = 0: off): the sum-factorised tables of
+  // OverintOps, A | Aw | B | Bw | C | Cw | V_o^-T | Z^T | Dw^T
   double* oi_tab = nullptr;
   int oi_q = 0, oi_ng = 0;
 };
@@ -174,7 +181,7 @@ cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cud
 // block's shared memory at order N.
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s);
-bool overint_fits(int N, int Ng, bool visc, bool av);
+bool overint_fits(int N, int q, bool visc, bool av);
 cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
 // flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.

@@ -8,16 +8,30 @@
 // viscous fluxes (adiabatic; shear-free at a slip wall).  Artificial viscosity (AV): G also loses the
 // interpolant of the nodal flux sigma = eps grad_h q of the AV pass (nonzero only in elements with
 // eps > 0), and n.G* the central flux n.(sigma- + sigma+)/2 (sigma+ = sigma- at boundary faces).
-// Both fluxes are degree-N fields, so their parts of the integral are exact.
+//
+// Sum factorisation.  The rule is a tensor product in the collapsed coordinates (a_i, b_j, c_k)
+// and the orthonormal modes factor there, psi_pqr = A_p(a) B_pq(b) C_pqr(c), so the state at the
+// points is u = sum_p A_p sum_q B_pq sum_r C_pqr m_pqr with the modes m = V_o^-1 q, and the
+// moments y_n = sum_g w_g psi_n(g) F(g) run the same sums backwards (the weights split over the
+// three directions).  The weak-form operator on the moments is Z_a = M^-1 D_a^T V_o^-T, because
+// I = Psi V_o^-1.  The geometric factors are constant per element (affine tetrahedra), so the
+// moments are taken of the physical flux components and turned contravariant on the Np modes, not
+// on the q^3 points.  The diffusive fluxes (VISC, AV) are degree-N nodal fields, whose products
+// with the degree-N test functions the rule integrates exactly when q >= N + 1: their part is the
+// exact M^-1 D_a^T M applied to their nodal contravariant components (the host refuses fewer
+// points for them).
 //
 // One persistent block per group of E elements keeps every intermediate in shared memory:
-//   1. point-parallel : the state (and viscous flux) at the points, the flux there, its
-//                       contravariant components times the weight -> sF[a][v][e][g]
-//   2. face-node-par. : the Lax-Friedrichs flux of the traces (ghost states at boundary faces) -> sG
-//   3. (a, v, e, i)   : y_a = I^T (W F_a), one sum over the points per output
-//   4. (v, e, i)      : rhs = sum_a (M^-1 D_a^T) y_a - LIFT (Fscale f*), then the RK update -> HBM
-// The tables (I^T with an odd row stride, the weights, (M^-1 D_a^T)^T, LIFT^T) are loaded once per
-// block, laid out so that consecutive threads read consecutive words.  All arithmetic is FP64.
+//   A. the modes X = V_o^-1 q; the Lax-Friedrichs flux of the face traces (ghost states at
+//      boundary faces), minus the central diffusive fluxes -> sG; the nodal contravariant
+//      diffusive flux -> sD
+//   B. T1[pq][k] = sum_r C_pqr(c_k) X_pqr                      C. T2[p][j][k] = sum_q B_pq(b_j) T1
+//   D. per point: the state sum_p A_p(a_i) T2, its Euler flux F_d -> F (no weight, physical axes)
+//   E. S1[p][j][k] = sum_i Aw_p(a_i) F[i][j][k]                 F. S2[pq][k] = sum_j Bw_pq(b_j) S1
+//   G. y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], then Y_a = sum_d (dr_a/dx_d) y_d
+//   H. rhs = sum_a Z_a Y_a - sum_a Dw_a D_a - LIFT (Fscale f*), then the RK update -> HBM
+// Buffers that are dead by then are reused: T2 and S1 share R2, X|T1 and S2 share R3, F and Y R1.
+// All arithmetic is FP64.
 #include <algorithm>
 
 #include "dg_kernels.cuh"
@@ -28,28 +42,34 @@ namespace {
 using kern::GS;
 using kern::Ord;
 
-// Row stride of I^T in shared memory: the point count, made odd so that threads reading one
-// point of consecutive rows hit distinct banks.
-__host__ __device__ inline int oi_ldq(int Ng) { return Ng | 1; }
-
+// Shared-memory plan in doubles: the tables once per block, then per element.
 struct OiLayout {
-  int ldq, tables, per_elem;  // doubles: tables, and the per-element work
+  int tA, tB, tC, tables;             // table lengths: A, B, C (each doubled with its weighted copy)
+  int r1, r2, r3, per_elem, ints;
 };
 
 template <int N>
-__host__ __device__ inline OiLayout oi_layout(int Ng, bool visc, bool av) {
+__host__ __device__ inline OiLayout oi_layout(int q, bool diff) {
   using O = Ord<N>;
+  constexpr int Np = O::Np, Nt2 = (N + 1) * (N + 2) / 2;
   OiLayout L;
-  L.ldq = oi_ldq(Ng);
-  L.tables = O::Np * L.ldq + Ng + 3 * O::Np * O::Np + O::NF * O::Np;
-  L.per_elem = GS + 5 * O::Np + 15 * Ng + 15 * O::Np + 5 * O::NF + (visc ? 9 * O::Np : 0) + (av ? 15 * O::Np : 0);
+  L.tA = (N + 1) * q;
+  L.tB = Nt2 * q;
+  L.tC = Np * q;
+  L.tables = 2 * (L.tA + L.tB + L.tC) + Np * Np + 3 * Np * Np + (diff ? 3 * Np * Np : 0) + O::NF * Np;
+  const int q2 = q * q, q3 = q2 * q;
+  L.r1 = 15 * (q3 > Np ? q3 : Np);
+  L.r2 = 15 * (N + 1) * q2;
+  L.r3 = 5 * Np + 5 * Nt2 * q > 15 * Nt2 * q ? 5 * Np + 5 * Nt2 * q : 15 * Nt2 * q;
+  L.per_elem = GS + 5 * Np + 5 * O::NF + L.r1 + L.r2 + L.r3 + (diff ? 15 * Np : 0);
+  L.ints = O::NF + 3 * Nt2 + (N + 1) + Np;  // fmask, pq -> (p, first mode, count), p -> first pq, mode -> pq
   return L;
 }
 
 template <int N>
-inline size_t oi_smem(int Ng, int E, bool visc, bool av) {
-  const OiLayout L = oi_layout<N>(Ng, visc, av);
-  return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * Ord<N>::NF;
+inline size_t oi_smem(int q, int E, bool diff) {
+  const OiLayout L = oi_layout<N>(q, diff);
+  return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * (size_t)L.ints;
 }
 
 template <int N, bool VISC, bool AV, bool RK>
@@ -63,122 +83,91 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
                                                       const double* __restrict__ geo_g,
                                                       const int32_t* __restrict__ vmapP, unsigned* __restrict__ status,
                                                       const GasParams gp, const BcParams bc, const int K,
-                                                      const int Ng, const int E, const double a, const double b,
+                                                      const int nq, const int E, const double a, const double b,
                                                       const double dt) {
   using O = Ord<N>;
-  constexpr int Np = O::Np, NF = O::NF;
-  const OiLayout L = oi_layout<N>(Ng, VISC, AV);
-  const int ldq = L.ldq;
+  constexpr int Np = O::Np, NF = O::NF, Nt2 = (N + 1) * (N + 2) / 2;
+  constexpr bool DIFF = VISC || AV;
+  const OiLayout L = oi_layout<N>(nq, DIFF);
+  const int q2 = nq * nq, q3 = q2 * nq;
+  const int lT1 = Nt2 * nq, lT2 = (N + 1) * q2;  // per-slab lengths of T1|S2 and T2|S1
   extern __shared__ double smem[];
-  double* sIT = smem;                  // [Np][ldq]: l_j at point g
-  double* sW = sIT + Np * ldq;         // [Ng]
-  double* sWt = sW + Ng;               // [3][Np(j)][Np(i)]: (M^-1 D_a^T)[i][j]
-  double* sLT = sWt + 3 * Np * Np;     // [NF][Np]: LIFT[i][m] at [m][i]
+  double* sA = smem;                   // [N+1][q], then Aw
+  double* sAw = sA + L.tA;
+  double* sB = sAw + L.tA;             // [Nt2][q], then Bw
+  double* sBw = sB + L.tB;
+  double* sC = sBw + L.tB;             // [Np][q], then Cw
+  double* sCw = sC + L.tC;
+  double* sVi = sCw + L.tC;            // [Np(j)][Np(n)]: (V_o^-1)[n][j]
+  double* sZ = sVi + Np * Np;          // [3][Np(n)][Np(i)]: Z_a[i][n]
+  double* sDw = sZ + 3 * Np * Np;      // DIFF: [3][Np(j)][Np(i)]: Dw_a[i][j]
+  double* sLT = sDw + (DIFF ? 3 * Np * Np : 0);  // [NF][Np]: LIFT[i][m] at [m][i]
   double* sGeo = sLT + NF * Np;        // [E][GS]
   double* sQ = sGeo + E * GS;          // [5][E][Np]
-  double* sF = sQ + 5 * E * Np;        // [3][5][E][Ng]: w_g F_a at the points
-  double* sY = sF + 15 * E * Ng;       // [3][5][E][Np]
-  double* sG = sY + 15 * E * Np;       // [5][E][NF]: Fscale n.G*
-  double* sFv = sG + 5 * E * NF;       // VISC: [9][E][Np] nodal viscous flux (tau xx yy zz xy xz yz, Q)
-  double* sS = sFv + (VISC ? 9 * E * Np : 0);  // AV: [15][E][Np] sigma[(5 d + v)], 0 where eps = 0
-  int* sFm = reinterpret_cast<int*>(sS + (AV ? 15 * E * Np : 0));
+  double* sG = sQ + 5 * E * Np;        // [5][E][NF]: Fscale n.G*
+  double* R1 = sG + 5 * E * NF;        // F [15][E][q3] (slab 5 d + v), then Y [15][E][Np] (slab 5 a + v)
+  double* R2 = R1 + E * L.r1;          // T2 [5][E][lT2], then S1 [15][E][lT2]
+  double* R3 = R2 + E * L.r2;          // X [5][E][Np] | T1 [5][E][lT1], then S2 [15][E][lT1]
+  double* sD = R3 + E * L.r3;          // DIFF: [15][E][Np] contravariant diffusive flux (slab 5 a + v)
+  int* sFm = reinterpret_cast<int*>(sD + (DIFF ? 15 * E * Np : 0));
+  int* sPQp = sFm + NF;                // pq -> p
+  int* sPQn = sPQp + Nt2;              // pq -> first mode
+  int* sPQc = sPQn + Nt2;              // pq -> modes with this (p, q)
+  int* sP0 = sPQc + Nt2;               // p -> first pq
+  int* sNpq = sP0 + (N + 1);           // mode -> pq
+  double* sX = R3;
+  double* sT1 = R3 + 5 * E * Np;
   const int tid = threadIdx.x, NT = blockDim.x;
   const size_t KNp = (size_t)K * Np;
 
-  for (int i = tid; i < Np * Ng; i += NT) {
-    const int j = i / Ng, g = i - j * Ng;
-    sIT[j * ldq + g] = tab[i];
+  {
+    const int ntab = 2 * (L.tA + L.tB + L.tC) + 4 * Np * Np + (DIFF ? 3 * Np * Np : 0);
+    for (int i = tid; i < ntab; i += NT) smem[i] = tab[i];
   }
-  for (int i = tid; i < Ng; i += NT) sW[i] = tab[Np * Ng + i];
-  for (int i = tid; i < 3 * Np * Np; i += NT) sWt[i] = tab[Np * Ng + Ng + i];
   for (int i = tid; i < Np * NF; i += NT) {
     const int r = i / NF, m = i - r * NF;
     sLT[m * Np + r] = ops_g[3 * Np * Np + i];
   }
   for (int i = tid; i < NF; i += NT) sFm[i] = fmask_g[i];
+  if (tid == 0) {
+    for (int p = 0, pq = 0, n = 0; p <= N; ++p) {
+      sP0[p] = pq;
+      for (int qq = 0; p + qq <= N; ++qq, ++pq) {
+        sPQp[pq] = p;
+        sPQn[pq] = n;
+        sPQc[pq] = N + 1 - p - qq;
+        for (int r = 0; p + qq + r <= N; ++r) sNpq[n++] = pq;
+      }
+    }
+  }
 
   const double gm1 = gp.gamma - 1.0;
   const int groups = (K + E - 1) / E;
   for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
     const int e0 = grp * E, nel = min(E, K - e0), nn = nel * Np;
     const size_t base = (size_t)e0 * Np;
-    __syncthreads();  // the tables are in, and the previous group's reads of sQ/sGeo are done
+    __syncthreads();  // the tables are in, and the previous group's reads of sQ, sGeo and R1 are done
     for (int i = tid; i < nel * GS; i += NT) sGeo[i] = geo_g[(size_t)e0 * GS + i];
     for (int v = 0; v < 5; ++v)
       for (int i = tid; i < nn; i += NT) sQ[(v * E + i / Np) * Np + i % Np] = q[v * KNp + base + i];
-    if (VISC)
-      for (int c = 0; c < 9; ++c)
-        for (int i = tid; i < nn; i += NT) sFv[(c * E + i / Np) * Np + i % Np] = fv_g[c * KNp + base + i];
-    if (AV)  // the AV flux is stored only in elements with eps > 0
-      for (int c = 0; c < 15; ++c)
-        for (int i = tid; i < nn; i += NT)
-          sS[(c * E + i / Np) * Np + i % Np] = av_eps[e0 + i / Np] > 0.0 ? av_g[c * KNp + base + i] : 0.0;
     __syncthreads();
 
-    // ---- 1: state, flux and weighted contravariant flux at every point ----
-    for (int it = tid; it < nel * Ng; it += NT) {
-      const int e = it / Ng, g = it - e * Ng;
-      double qg[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, fvg[9], sg[15];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) fvg[c] = 0.0;
-#pragma unroll
-      for (int c = 0; c < 15; ++c) sg[c] = 0.0;
-      const bool on = AV && av_eps[e0 + e] > 0.0;
-      for (int j = 0; j < Np; ++j) {
-        const double l = sIT[j * ldq + g];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) qg[v] = fma(l, sQ[(v * E + e) * Np + j], qg[v]);
-        if (VISC) {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) fvg[c] = fma(l, sFv[(c * E + e) * Np + j], fvg[c]);
-        }
-        if (AV && on) {
-#pragma unroll
-          for (int c = 0; c < 15; ++c) sg[c] = fma(l, sS[(c * E + e) * Np + j], sg[c]);
-        }
-      }
-      const double ir = 1.0 / qg[0];
-      const double u[3] = {qg[1] * ir, qg[2] * ir, qg[3] * ir};
-      const double p = gm1 * (qg[4] - 0.5 * (qg[1] * u[0] + qg[2] * u[1] + qg[3] * u[2]));
-      if (!(qg[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
-      double F[3][5];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        F[d][0] = qg[1 + d];
-        F[d][1] = qg[1] * u[d];
-        F[d][2] = qg[2] * u[d];
-        F[d][3] = qg[3] * u[d];
-        F[d][1 + d] += p;
-        F[d][4] = u[d] * (qg[4] + p);
-        if (VISC) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) F[d][1 + i] -= fvg[kern::tau_index(i, d)];
-          F[d][4] -= fvg[6 + d];
-        }
-        if (AV) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F[d][v] -= sg[5 * d + v];
-        }
-      }
-      const double* G = sGeo + e * GS;
-      const double w = sW[g];
-#pragma unroll
-      for (int ra = 0; ra < 3; ++ra) {
-        const double gx = w * G[3 * ra], gy = w * G[3 * ra + 1], gz = w * G[3 * ra + 2];
-#pragma unroll
-        for (int v = 0; v < 5; ++v)
-          sF[((ra * 5 + v) * E + e) * Ng + g] = fma(gx, F[0][v], fma(gy, F[1][v], gz * F[2][v]));
-      }
+    // ---- A: modes; face fluxes; nodal contravariant diffusive fluxes ----
+    for (int it = tid; it < 5 * nn; it += NT) {
+      const int n = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      const double* x = sQ + (v * E + e) * Np;
+      double acc = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < Np; ++j) acc = fma(sVi[j * Np + n], x[j], acc);
+      sX[(v * E + e) * Np + n] = acc;
     }
-
-    // ---- 2: Fscale f* at the face nodes (weak form), ghost states at boundary faces ----
     for (int j = tid; j < nel * NF; j += NT) {
       const int e = j / NF, m = j - e * NF, f = m / O::Nfp;
       const double* G = sGeo + e * GS;
       const double nx = G[9 + 4 * f], ny = G[10 + 4 * f], nz = G[11 + 4 * f], fs = G[12 + 4 * f];
-      const int own = e * Np + sFm[m];
+      const size_t Mn = base + (size_t)(e * Np + sFm[m]);
       const int P = vmapP[(size_t)(e0 + e) * NF + m];  // < 0: boundary face node, -DG_BC_* code
-      const size_t Pn = P >= 0 ? (size_t)P : base + own;
+      const size_t Pn = P >= 0 ? (size_t)P : Mn;
       double qm[5], qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -213,13 +202,13 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
             const int c = kern::tau_index(i, d);
-            tm[i] = fma(nn3[d], sFv[(c * E + e) * Np + sFm[m]], tm[i]);
+            tm[i] = fma(nn3[d], fv_g[c * KNp + Mn], tm[i]);
             tp[i] = fma(nn3[d], fv_g[c * KNp + Pn], tp[i]);
           }
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          em = fma(nn3[d], sFv[((6 + d) * E + e) * Np + sFm[m]], em);
+          em = fma(nn3[d], fv_g[(6 + d) * KNp + Mn], em);
           ep = fma(nn3[d], fv_g[(6 + d) * KNp + Pn], ep);
         }
         if (P == -DG_BC_SLIP_WALL || P == -DG_BC_NOSLIP_WALL) {
@@ -239,15 +228,11 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
         // so sigma+ = sigma-
         const bool onM = av_eps[e0 + e] > 0.0, onP = av_eps[Pn / Np] > 0.0;
         if (onM || onP) {
-          const int own_n = sFm[m];
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             double sm = 0.0, sp = 0.0;
-            if (onM)
-              sm = fma(nx, sS[(v * E + e) * Np + own_n],
-                       fma(ny, sS[((5 + v) * E + e) * Np + own_n], nz * sS[((10 + v) * E + e) * Np + own_n]));
-            if (onP)
-              sp = fma(nx, av_g[v * KNp + Pn], fma(ny, av_g[(5 + v) * KNp + Pn], nz * av_g[(10 + v) * KNp + Pn]));
+            if (onM) sm = fma(nx, av_g[v * KNp + Mn], fma(ny, av_g[(5 + v) * KNp + Mn], nz * av_g[(10 + v) * KNp + Mn]));
+            if (onP) sp = fma(nx, av_g[v * KNp + Pn], fma(ny, av_g[(5 + v) * KNp + Pn], nz * av_g[(10 + v) * KNp + Pn]));
             gs[v] -= 0.5 * (sm + sp);
           }
         }
@@ -255,38 +240,160 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 #pragma unroll
       for (int v = 0; v < 5; ++v) sG[(v * E + e) * NF + m] = fs * gs[v];
     }
-    __syncthreads();
-
-    // ---- 3: y_a = I^T (W F_a), one output per thread ----
-    for (int it = tid; it < 15 * nel * Np; it += NT) {
-      const int i = it % Np, rest = it / Np, e = rest % nel, av = rest / nel;
-      const double* F = sF + (av * E + e) * Ng;
-      const double* l = sIT + i * ldq;
-      double y0 = 0.0, y1 = 0.0;
-      int g = 0;
-      for (; g + 1 < Ng; g += 2) {
-        y0 = fma(l[g], F[g], y0);
-        y1 = fma(l[g + 1], F[g + 1], y1);
+    if (DIFF) {
+      // sD[5 a + v] = sum_d (dr_a/dx_d) Fd_d[v], Fd = Fv + sigma (Fv: rows 1-4, sigma only where
+      // eps > 0); a row with nothing in it is left out of H and not written
+      for (int it = tid; it < nn; it += NT) {
+        const int e = it / Np, j = it - e * Np;
+        const double* G = sGeo + e * GS;
+        const size_t gn = base + it;
+        const bool on = AV && av_eps[e0 + e] > 0.0;
+        double fd[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fd[d][v] = on ? av_g[(5 * d + v) * KNp + gn] : 0.0;
+          if (VISC) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) fd[d][1 + i] += fv_g[kern::tau_index(i, d) * KNp + gn];
+            fd[d][4] += fv_g[(6 + d) * KNp + gn];
+          }
+        }
+#pragma unroll
+        for (int ra = 0; ra < 3; ++ra)
+#pragma unroll
+          for (int v = 0; v < 5; ++v)
+            sD[((5 * ra + v) * E + e) * Np + j] =
+                fma(G[3 * ra], fd[0][v], fma(G[3 * ra + 1], fd[1][v], G[3 * ra + 2] * fd[2][v]));
       }
-      if (g < Ng) y0 = fma(l[g], F[g], y0);
-      sY[(av * E + e) * Np + i] = y0 + y1;
     }
     __syncthreads();
 
-    // ---- 4: rhs = sum_a (M^-1 D_a^T) y_a - LIFT (Fscale f*), then the output or RK update ----
-    for (int it = tid; it < 5 * nel * Np; it += NT) {
-      const int i = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+    // ---- B: T1[pq][k] = sum_r C_pqr(c_k) X_pqr ----
+    for (int it = tid; it < 5 * nel * lT1; it += NT) {
+      const int idx = it % lT1, rest = it / lT1, e = rest % nel, v = rest / nel;
+      const int pq = idx / nq, k = idx - pq * nq;
+      const int n0 = sPQn[pq], cnt = sPQc[pq];
+      const double* x = sX + (v * E + e) * Np + n0;
       double acc = 0.0;
+      for (int r = 0; r < cnt; ++r) acc = fma(sC[(n0 + r) * nq + k], x[r], acc);
+      sT1[(v * E + e) * lT1 + idx] = acc;
+    }
+    __syncthreads();
+
+    // ---- C: T2[p][j][k] = sum_q B_pq(b_j) T1[pq][k] (into R2) ----
+    for (int it = tid; it < 5 * nel * lT2; it += NT) {
+      const int idx = it % lT2, rest = it / lT2, e = rest % nel, v = rest / nel;
+      const int p = idx / q2, jk = idx - p * q2, j = jk / nq, k = jk - j * nq;
+      const int pq0 = sP0[p];
+      const double* t1 = sT1 + (v * E + e) * lT1 + k;
+      double acc = 0.0;
+      for (int qq = 0; qq <= N - p; ++qq) acc = fma(sB[(pq0 + qq) * nq + j], t1[(pq0 + qq) * nq], acc);
+      R2[(v * E + e) * lT2 + idx] = acc;
+    }
+    __syncthreads();
+
+    // ---- D: state and Euler flux at every point (g = (k q + j) q + i) -> F (R1) ----
+    for (int it = tid; it < nel * q3; it += NT) {
+      const int e = it / q3, g = it - e * q3;
+      const int i = g % nq, jk = g / nq;  // jk = k q + j
+      const int j = jk % nq, k = jk / nq;
+      double qg[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double* t2 = R2 + (v * E + e) * lT2 + j * nq + k;
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p <= N; ++p) acc = fma(sA[p * nq + i], t2[p * q2], acc);
+        qg[v] = acc;
+      }
+      const double ir = 1.0 / qg[0];
+      const double u[3] = {qg[1] * ir, qg[2] * ir, qg[3] * ir};
+      const double p = gm1 * (qg[4] - 0.5 * (qg[1] * u[0] + qg[2] * u[1] + qg[3] * u[2]));
+      if (!(qg[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      double* F = R1 + e * q3 + g;
+      const int sl = E * q3;  // slab stride
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        F[(5 * d + 0) * sl] = qg[1 + d];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[(5 * d + 1 + c) * sl] = c == d ? fma(qg[1 + c], u[d], p) : qg[1 + c] * u[d];
+        F[(5 * d + 4) * sl] = u[d] * (qg[4] + p);
+      }
+    }
+    __syncthreads();
+
+    // ---- E: S1[p][j][k] = sum_i Aw_p(a_i) F[(k q + j) q + i] (into R2) ----
+    for (int it = tid; it < 15 * nel * lT2; it += NT) {
+      const int idx = it % lT2, rest = it / lT2, e = rest % nel, s = rest / nel;
+      const int p = idx / q2, jk = idx - p * q2, j = jk / nq, k = jk - j * nq;
+      const double* f = R1 + (s * E + e) * q3 + (k * nq + j) * nq;
+      const double* w = sAw + p * nq;
+      double acc = 0.0;
+      for (int i = 0; i < nq; ++i) acc = fma(w[i], f[i], acc);
+      R2[(s * E + e) * lT2 + idx] = acc;
+    }
+    __syncthreads();
+
+    // ---- F: S2[pq][k] = sum_j Bw_pq(b_j) S1[p][j][k] (into R3) ----
+    for (int it = tid; it < 15 * nel * lT1; it += NT) {
+      const int idx = it % lT1, rest = it / lT1, e = rest % nel, s = rest / nel;
+      const int pq = idx / nq, k = idx - pq * nq;
+      const double* s1 = R2 + (s * E + e) * lT2 + sPQp[pq] * q2 + k;
+      const double* w = sBw + pq * nq;
+      double acc = 0.0;
+      for (int j = 0; j < nq; ++j) acc = fma(w[j], s1[j * nq], acc);
+      R3[(s * E + e) * lT1 + idx] = acc;
+    }
+    __syncthreads();
+
+    // ---- G: moments y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], contravariant Y_a (into R1) ----
+    for (int it = tid; it < 5 * nn; it += NT) {
+      const int n = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      const double* w = sCw + n * nq;
+      const int off = sNpq[n] * nq;
+      double y[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double* s2 = R3 + ((5 * d + v) * E + e) * lT1 + off;
+        double acc = 0.0;
+        for (int k = 0; k < nq; ++k) acc = fma(w[k], s2[k], acc);
+        y[d] = acc;
+      }
+      const double* G = sGeo + e * GS;
+#pragma unroll
+      for (int ra = 0; ra < 3; ++ra)
+        R1[((5 * ra + v) * E + e) * Np + n] = fma(G[3 * ra], y[0], fma(G[3 * ra + 1], y[1], G[3 * ra + 2] * y[2]));
+    }
+    __syncthreads();
+
+    // ---- H: rhs = sum_a Z_a Y_a - sum_a Dw_a D_a - LIFT (Fscale f*), then the output or RK update ----
+    for (int it = tid; it < 5 * nn; it += NT) {
+      const int i = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      double acc = 0.0, acd = 0.0;
 #pragma unroll
       for (int ra = 0; ra < 3; ++ra) {
-        const double* y = sY + ((ra * 5 + v) * E + e) * Np;
-        const double* W = sWt + ra * Np * Np + i;
+        const double* y = R1 + ((5 * ra + v) * E + e) * Np;
+        const double* Z = sZ + ra * Np * Np + i;
 #pragma unroll 4
-        for (int j = 0; j < Np; ++j) acc = fma(W[j * Np], y[j], acc);
+        for (int n = 0; n < Np; ++n) acc = fma(Z[n * Np], y[n], acc);
+      }
+      if (DIFF) {
+        const bool on = AV && av_eps[e0 + e] > 0.0;
+        if (on || (VISC && v > 0)) {
+#pragma unroll
+          for (int ra = 0; ra < 3; ++ra) {
+            const double* dd = sD + ((5 * ra + v) * E + e) * Np;
+            const double* W = sDw + ra * Np * Np + i;
+#pragma unroll 4
+            for (int j = 0; j < Np; ++j) acd = fma(W[j * Np], dd[j], acd);
+          }
+        }
       }
       const double* gq = sG + (v * E + e) * NF;
 #pragma unroll 4
-      for (int m = 0; m < NF; ++m) acc = fma(-sLT[m * Np + i], gq[m], acc);
+      for (int m = 0; m < NF; ++m) acd = fma(sLT[m * Np + i], gq[m], acd);
+      acc -= acd;
       const size_t gi = v * KNp + base + e * Np + i;
       if (RK) {
         const double kk = (a != 0.0 ? a * kreg[gi] : 0.0) + dt * acc;
@@ -300,22 +407,23 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 }
 
 // Elements per block and blocks per SM: two blocks of at least two elements each if they fit in
-// an SM's shared memory, else one block with as many elements as fit; 0 when one element does not.
+// an SM's shared memory, else one block with as many elements as fit; false when one element does
+// not.
 template <int N>
-bool oi_config(int Ng, bool visc, bool av, int& E, int& bps, size_t& smem) {
+bool oi_config(int nq, bool diff, int& E, int& bps, size_t& smem) {
   int dev = 0, per_sm = 0, per_block = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const OiLayout L = oi_layout<N>(Ng, visc, av);
+  const OiLayout L = oi_layout<N>(nq, diff);
   for (bps = 2; bps >= 1; --bps) {
     const size_t budget = std::min((size_t)per_block, (size_t)per_sm / bps - 1024);
-    const size_t fixed = sizeof(double) * L.tables + sizeof(int) * Ord<N>::NF;
+    const size_t fixed = sizeof(double) * L.tables + sizeof(int) * L.ints;
     if (budget <= fixed) continue;
     E = (int)((budget - fixed) / (sizeof(double) * L.per_elem));
     E = std::min(E, 64);
     if (E >= (bps == 2 ? 2 : 1)) {
-      smem = oi_smem<N>(Ng, E, visc, av);
+      smem = oi_smem<N>(nq, E, diff);
       return true;
     }
   }
@@ -327,7 +435,7 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
                         double b, double dt, cudaStream_t s) {
   int E = 0, bps = 0;
   size_t smem = 0;
-  if (!oi_config<N>(m.oi_ng, VISC, AV, E, bps, smem)) return cudaErrorInvalidConfiguration;
+  if (!oi_config<N>(m.oi_q, VISC || AV, E, bps, smem)) return cudaErrorInvalidConfiguration;
   cudaError_t e =
       cudaFuncSetAttribute(rhs_oi_kernel<N, VISC, AV, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -338,21 +446,22 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
   const int groups = (m.K + E - 1) / E;
   const int blocks = std::min(groups, sms * bps);
   rhs_oi_kernel<N, VISC, AV, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.scratch, m.av_sig, m.av_eps, m.ops,
-                                                            m.fmask, m.geo, m.vmapP, m.status, g, m.bc, m.K, m.oi_ng,
+                                                            m.fmask, m.geo, m.vmapP, m.status, g, m.bc, m.K, m.oi_q,
                                                             E, a, b, dt);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool overint_fits(int N, int Ng, bool visc, bool av) {
+bool overint_fits(int N, int q, bool visc, bool av) {
   int E = 0, bps = 0;
   size_t smem = 0;
+  const bool diff = visc || av;
   switch (N) {
-    case 1: return oi_config<1>(Ng, visc, av, E, bps, smem);
-    case 2: return oi_config<2>(Ng, visc, av, E, bps, smem);
-    case 3: return oi_config<3>(Ng, visc, av, E, bps, smem);
-    case 4: return oi_config<4>(Ng, visc, av, E, bps, smem);
+    case 1: return oi_config<1>(q, diff, E, bps, smem);
+    case 2: return oi_config<2>(q, diff, E, bps, smem);
+    case 3: return oi_config<3>(q, diff, E, bps, smem);
+    case 4: return oi_config<4>(q, diff, E, bps, smem);
     default: return false;
   }
 }

@@ -25,6 +25,7 @@
 // into the constants); a and b are set to -1 where the collapse is singular.
 // Faces: 0: t = -1 (params r,s), 1: s = -1 (r,t), 2: r+s+t = -1 (s,t),
 // 3: r = -1 (s,t); face nodes are listed in increasing volume-node order.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -388,20 +389,100 @@ bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::
   out.Ng = Ng;
   out.rst = rst;
   out.w = w;
-  out.IT.assign((size_t)Np * Ng, 0.0);
-  for (int g = 0; g < Ng; ++g)
-    for (int j = 0; j < Np; ++j) out.IT[(size_t)j * Ng + g] = (double)I[(size_t)g * Np + j];
-  // WtT[a][j][i] = (M^-1 D_a^T)[i][j] = sum_k Minv[i][k] D_a[j][k]
-  out.WtT.assign(3 * Np * Np, 0.0);
+  // Wt_a = M^-1 D_a^T: Wt_a[i][j] = sum_k Minv[i][k] D_a[j][k]
+  std::vector<ld> Dl[3], WtL[3];
   for (int a = 0; a < 3; ++a) {
-    const std::vector<ld> D = matmul(Vd[a], Vinv, Np, Np, Np);
+    Dl[a] = matmul(Vd[a], Vinv, Np, Np, Np);
+    WtL[a].assign(Np * Np, 0);
     for (int j = 0; j < Np; ++j)
       for (int i = 0; i < Np; ++i) {
         ld acc = 0;
-        for (int k = 0; k < Np; ++k) acc += Minv[i * Np + k] * D[j * Np + k];
-        out.WtT[(a * Np + j) * Np + i] = (double)acc;
+        for (int k = 0; k < Np; ++k) acc += Minv[i * Np + k] * Dl[a][j * Np + k];
+        WtL[a][i * Np + j] = acc;
       }
   }
+  // sum-factorised tables: psi_pqr(a, b, c) = A_p(a) B_pq(b) C_pqr(c) with A_p = P~_p^(0,0),
+  // B_pq = P~_q^(2p+1,0) (1-b)^p, C_pqr = 2 sqrt 2 P~_r^(2p+2q+2,0) (1-c)^(p+q) (ortho_tet's factors)
+  std::vector<ld> ga, gwa, gb, gwb, gc, gwc;
+  if (!gauss_jacobi(q, 0, ga, gwa) || !gauss_jacobi(q, 1, gb, gwb) || !gauss_jacobi(q, 2, gc, gwc)) {
+    err = "Gauss-Jacobi roots did not converge";
+    return false;
+  }
+  const int Nt2 = (N + 1) * (N + 2) / 2;
+  std::vector<ld> Al((N + 1) * q), Bl(Nt2 * q), Cl(Np * q);
+  for (int p = 0; p <= N; ++p)
+    for (int i = 0; i < q; ++i) Al[p * q + i] = jacobi(ga[i], 0, 0, p);
+  for (int p = 0, pq = 0; p <= N; ++p)
+    for (int qq = 0; p + qq <= N; ++qq, ++pq)
+      for (int j = 0; j < q; ++j) Bl[pq * q + j] = jacobi(gb[j], 2 * p + 1, 0, qq) * ipow(1 - gb[j], p);
+  for (int p = 0, n = 0; p <= N; ++p)
+    for (int qq = 0; p + qq <= N; ++qq)
+      for (int r = 0; p + qq + r <= N; ++r, ++n)
+        for (int k = 0; k < q; ++k)
+          Cl[n * q + k] = 2 * sqrtl(2.0L) * jacobi(gc[k], 2 * p + 2 * qq + 2, 0, r) * ipow(1 - gc[k], p + qq);
+  std::vector<ld> Voi = Vo;
+  if (!invert(Voi, Np)) {
+    err = "orthonormal Vandermonde matrix is singular";
+    return false;
+  }
+  // self-check: the factored modes through V_o^-1 reproduce the nodal basis at every point
+  {
+    ld worst = 0, scale = 0;
+    for (int k = 0; k < q; ++k)
+      for (int j = 0; j < q; ++j)
+        for (int i = 0; i < q; ++i) {
+          const int g = (k * q + j) * q + i;
+          std::vector<ld> psi(Np);
+          for (int p = 0, n = 0, pq = 0; p <= N; ++p)
+            for (int qq = 0; p + qq <= N; ++qq, ++pq)
+              for (int r = 0; p + qq + r <= N; ++r, ++n) psi[n] = Al[p * q + i] * Bl[pq * q + j] * Cl[n * q + k];
+          for (int jn = 0; jn < Np; ++jn) {
+            ld v = 0;
+            for (int n = 0; n < Np; ++n) v += psi[n] * Voi[n * Np + jn];
+            worst = std::max(worst, fabsl(v - I[(size_t)g * Np + jn]));
+            scale = std::max(scale, fabsl(I[(size_t)g * Np + jn]));
+          }
+        }
+    if (!(worst <= 1e-12L * scale)) {
+      err = "the factored modes do not reproduce the interpolation";
+      return false;
+    }
+  }
+  out.A.assign(Al.begin(), Al.end());
+  out.B.assign(Bl.begin(), Bl.end());
+  out.C.assign(Cl.begin(), Cl.end());
+  out.Aw.resize(Al.size());
+  out.Bw.resize(Bl.size());
+  out.Cw.resize(Cl.size());
+  for (size_t x = 0; x < Al.size(); ++x) out.Aw[x] = (double)(Al[x] * gwa[x % q] / 2);
+  for (size_t x = 0; x < Bl.size(); ++x) out.Bw[x] = (double)(Bl[x] * gwb[x % q] / 2);
+  for (size_t x = 0; x < Cl.size(); ++x) out.Cw[x] = (double)(Cl[x] * gwc[x % q] / 2);
+  out.VinvT.assign(Np * Np, 0.0);
+  for (int n = 0; n < Np; ++n)
+    for (int j = 0; j < Np; ++j) out.VinvT[j * Np + n] = (double)Voi[n * Np + j];
+  // ZT[a][n][i] = (Wt_a V_o^-T)[i][n] = sum_j Wt_a[i][j] Voi[n][j];  DwT[a][j][i] = (Wt_a M)[i][j]
+  std::vector<ld> Mm = Voi;  // M = V_o^-T V_o^-1
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      ld acc = 0;
+      for (int n = 0; n < Np; ++n) acc += Voi[n * Np + i] * Voi[n * Np + j];
+      Mm[i * Np + j] = acc;
+    }
+  out.ZT.assign(3 * Np * Np, 0.0);
+  out.DwT.assign(3 * Np * Np, 0.0);
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < Np; ++i) {
+      for (int n = 0; n < Np; ++n) {
+        ld acc = 0;
+        for (int j = 0; j < Np; ++j) acc += WtL[a][i * Np + j] * Voi[n * Np + j];
+        out.ZT[(a * Np + n) * Np + i] = (double)acc;
+      }
+      for (int j = 0; j < Np; ++j) {
+        ld acc = 0;
+        for (int k = 0; k < Np; ++k) acc += WtL[a][i * Np + k] * Mm[k * Np + j];
+        out.DwT[(a * Np + j) * Np + i] = (double)acc;
+      }
+    }
   return true;
 }
 
