@@ -652,17 +652,28 @@ def gpu_arm(args, cfg, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# nonzeros of the three modal derivative matrices V_o^-1 D_a V_o of the orthonormal tetrahedral
+# basis, by order (their zero pattern is structural: a mode's derivative has lower degree)
+MODAL_DERIVATIVE_NNZ = {1: 6, 2: 46, 3: 202, 4: 647}
+
+
 def overint_flops_per_element(N, Q, viscous=False):
-    """FP64 flops of one element in the over-integrated right-hand side (Ng = Q^3 points): per
-    point, the 5 fields interpolated (10 Np), the flux (30) and its weighted contravariant
-    components (93); the contraction back to the nodes (30 Np Ng); the weak-form operators and
-    LIFT (10 Np (3 Np + 4 Nfp)); about 100 per face node for the Lax-Friedrichs flux.  Viscous:
-    per point the 9 viscous-flux components interpolated (18 Np) and subtracted (12), and about
-    40 more per face node for the central viscous flux."""
-    Np, Nfp, Ng = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2, Q ** 3
-    f = Ng * (10 * Np + 123) + 30 * Np * Ng + 10 * Np * (3 * Np + 4 * Nfp) + 100 * 4 * Nfp
+    """FP64 flops of one element in the sum-factorised over-integrated right-hand side (Q points
+    per collapsed direction, Q^3 in all; an FMA counts two): the modes (V_o^-1 on 5 fields), the
+    three 1-D sums to the points, per point the state's last sum and the Euler flux (about 30), the
+    three weighted 1-D sums back for the 15 flux components, the moments' contravariant transform
+    (15 per mode and field), the sparse modal derivative matrices, V_o and LIFT; about 100 per face
+    node for the Lax-Friedrichs flux.  Viscous: the nodal contravariant viscous flux (75 per node),
+    the modes of its four rows (V_o^-1 for each direction), and about 40 more per face node for the
+    central viscous flux."""
+    Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+    NF, Nt2, q2, q3 = 4 * Nfp, Nfp, Q * Q, Q ** 3
+    f = 2 * 5 * Np * Np + 2 * 5 * Q * Np + 2 * 5 * q2 * Nt2
+    f += q3 * (2 * 5 * (N + 1) + 30)
+    f += 2 * 15 * (N + 1) * q3 + 2 * 15 * Nt2 * q2 + 5 * Np * (2 * 3 * Q + 15)
+    f += 2 * 5 * MODAL_DERIVATIVE_NNZ[N] + 2 * 5 * Np * (Np + NF) + 100 * NF
     if viscous:
-        f += Ng * (18 * Np + 12) + 40 * 4 * Nfp
+        f += 75 * Np + 2 * 4 * 3 * Np * Np + 40 * NF
     return f
 
 

@@ -200,7 +200,7 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
       return fail(DG_ERR_UNSUPPORTED, "over-integration runs in the FP64 form with a perfect gas over the whole mesh");
     if ((g.mu > 0 || av) && m.oi_q <= m.N)
       return fail(DG_ERR_UNSUPPORTED, "viscous and AV fluxes need at least N + 1 points per direction over-integrated");
-    if (!dg::overint_fits(m.N, m.oi_q, g.mu > 0, av))
+    if (!dg::overint_fits(m.N, m.oi_q, m.oi_nnz, g.mu > 0, av))
       return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's viscous or AV work exceed a "
                                       "block's shared memory at this point count");
   }
@@ -555,19 +555,21 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
   if (q == 0) {
     cudaFree(d.oi_tab);
     d.oi_tab = nullptr;
-    d.oi_q = d.oi_ng = 0;
+    d.oi_q = d.oi_ng = d.oi_nnz = 0;
     return DG_OK;
   }
   if (q == DG_OVERINT_DEFAULT) q = (3 * d.N + 1) / 2;
-  if (!dg::overint_fits(d.N, q, false, false))
-    return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
   dg::OverintOps o;
   std::string err;
   if (!dg::build_overint_ops(d.N, mesh->ref_nodes.data(), q, o, err)) return fail(DG_ERR_INVALID_ARG, err);
-  // device layout: A | Aw | B | Bw | C | Cw | V_o^-T | Z^T | Dw^T (the kernel's order)
+  if (!dg::overint_fits(d.N, q, (int)o.Dh_val.size(), false, false))
+    return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
+  // device layout: A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx (the kernel's
+  // order; the small integers of the last two exact as doubles)
   std::vector<double> tab;
-  for (const std::vector<double>* t : {&o.A, &o.Aw, &o.B, &o.Bw, &o.C, &o.Cw, &o.VinvT, &o.ZT, &o.DwT})
+  for (const std::vector<double>* t : {&o.A, &o.Aw, &o.B, &o.Bw, &o.C, &o.Cw, &o.VinvT, &o.VoT, &o.Dh_val})
     tab.insert(tab.end(), t->begin(), t->end());
+  for (const std::vector<int>* t : {&o.Dh_ptr, &o.Dh_idx}) tab.insert(tab.end(), t->begin(), t->end());
   double* dev = nullptr;
   cudaError_t e = cudaMalloc((void**)&dev, sizeof(double) * tab.size());
   if (e == cudaSuccess) e = cudaMemcpy(dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
@@ -579,6 +581,7 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
   d.oi_tab = dev;
   d.oi_q = q;
   d.oi_ng = o.Ng;
+  d.oi_nnz = (int)o.Dh_val.size();
   return DG_OK;
 }
 

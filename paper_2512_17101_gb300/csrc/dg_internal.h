@@ -43,8 +43,11 @@ struct OverintOps {
   std::vector<double> B, Bw;        // [(N+1)(N+2)/2][q]: B_pq(b_j)
   std::vector<double> C, Cw;        // [Np][q]: C_pqr(c_k)
   std::vector<double> VinvT;        // [Np(j)][Np(n)]: (V_o^-1)[n][j], nodal values -> mode n
-  std::vector<double> ZT;           // [3][Np(n)][Np(i)]: (M^-1 D_a^T V_o^-T)[i][n], modal moments -> nodes
-  std::vector<double> DwT;          // [3][Np(j)][Np(i)]: (M^-1 D_a^T M)[i][j], weak form of a nodal flux
+  std::vector<double> VoT;          // [Np(n)][Np(i)]: V_o[i][n], modes -> nodal values
+  // the modal derivative matrices Dh_a = V_o^-1 D_a V_o by column n, zeros left out: entries
+  // Dh_ptr[n] .. Dh_ptr[n+1] - 1 hold Dh_a[m][n] in Dh_val with a Np + m in Dh_idx
+  std::vector<int> Dh_ptr, Dh_idx;
+  std::vector<double> Dh_val;
 };
 bool tet_quadrature(int q, std::vector<double>& rst, std::vector<double>& w, std::string& err);
 bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::string& err);
@@ -150,9 +153,10 @@ struct MeshDev {
   double* prim = nullptr;      // FP64 form, perfect gas: [3][K][Np] (1/rho, p, c) of the state being
                                // differentiated, written by the primitives pass before each stage
   // over-integration (dg_mesh_set_overint; oi_q = 0: off): the sum-factorised tables of
-  // OverintOps, A | Aw | B | Bw | C | Cw | V_o^-T | Z^T | Dw^T
+  // OverintOps, A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx (the last two
+  // as doubles), with oi_nnz entries in Dh
   double* oi_tab = nullptr;
-  int oi_q = 0, oi_ng = 0;
+  int oi_q = 0, oi_ng = 0, oi_nnz = 0;
 };
 
 // LSRK4 coefficients (Carpenter & Kennedy 1994, five stages, 2N storage).
@@ -181,7 +185,7 @@ cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cud
 // block's shared memory at order N.
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s);
-bool overint_fits(int N, int q, bool visc, bool av);
+bool overint_fits(int N, int q, int nnz, bool visc, bool av);
 cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
 // Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
 // flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.

@@ -13,13 +13,15 @@
 // and the orthonormal modes factor there, psi_pqr = A_p(a) B_pq(b) C_pqr(c), so the state at the
 // points is u = sum_p A_p sum_q B_pq sum_r C_pqr m_pqr with the modes m = V_o^-1 q, and the
 // moments y_n = sum_g w_g psi_n(g) F(g) run the same sums backwards (the weights split over the
-// three directions).  The weak-form operator on the moments is Z_a = M^-1 D_a^T V_o^-T, because
-// I = Psi V_o^-1.  The geometric factors are constant per element (affine tetrahedra), so the
-// moments are taken of the physical flux components and turned contravariant on the Np modes, not
-// on the q^3 points.  The diffusive fluxes (VISC, AV) are degree-N nodal fields, whose products
-// with the degree-N test functions the rule integrates exactly when q >= N + 1: their part is the
-// exact M^-1 D_a^T M applied to their nodal contravariant components (the host refuses fewer
-// points for them).
+// three directions).  The weak-form operator on the moments is M^-1 D_a^T V_o^-T = V_o Dh_a^T,
+// because I = Psi V_o^-1 and M^-1 = V_o V_o^T, with the modal derivative matrices
+// Dh_a = V_o^-1 D_a V_o, most of whose entries vanish (a mode's derivative has lower degree); they
+// are applied sparse, by column.  The geometric factors are constant per element (affine
+// tetrahedra), so the moments are taken of the physical flux components and turned contravariant
+// on the Np modes, not on the q^3 points.  The diffusive fluxes (VISC, AV) are degree-N nodal
+// fields, whose products with the test-function gradients the rule integrates exactly when
+// q >= N + 1: their part is the exact M^-1 D_a^T M = V_o Dh_a^T V_o^-1 on their nodal
+// contravariant components, so their modes join the moments (the host refuses fewer points).
 //
 // One persistent block per group of E elements keeps every intermediate in shared memory:
 //   A. the modes X = V_o^-1 q; the Lax-Friedrichs flux of the face traces (ghost states at
@@ -28,9 +30,10 @@
 //   B. T1[pq][k] = sum_r C_pqr(c_k) X_pqr                      C. T2[p][j][k] = sum_q B_pq(b_j) T1
 //   D. per point: the state sum_p A_p(a_i) T2, its Euler flux F_d -> F (no weight, physical axes)
 //   E. S1[p][j][k] = sum_i Aw_p(a_i) F[i][j][k]                 F. S2[pq][k] = sum_j Bw_pq(b_j) S1
-//   G. y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], then Y_a = sum_d (dr_a/dx_d) y_d
-//   H. rhs = sum_a Z_a Y_a - sum_a Dw_a D_a - LIFT (Fscale f*), then the RK update -> HBM
-// Buffers that are dead by then are reused: T2 and S1 share R2, X|T1 and S2 share R3, F and Y R1.
+//   G. y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], then Y_a = sum_d (dr_a/dx_d) y_d - V_o^-1 D_a
+//   G2. u = sum_a Dh_a^T Y_a (sparse)
+//   H. rhs = V_o u - LIFT (Fscale f*), then the RK update -> HBM
+// Buffers that are dead by then are reused: T2, S1 and u share R2, X|T1 and S2 share R3, F and Y R1.
 // All arithmetic is FP64.
 #include <algorithm>
 
@@ -49,26 +52,27 @@ struct OiLayout {
 };
 
 template <int N>
-__host__ __device__ inline OiLayout oi_layout(int q, bool diff) {
+__host__ __device__ inline OiLayout oi_layout(int q, int nnz, bool diff) {
   using O = Ord<N>;
   constexpr int Np = O::Np, Nt2 = (N + 1) * (N + 2) / 2;
   OiLayout L;
   L.tA = (N + 1) * q;
   L.tB = Nt2 * q;
   L.tC = Np * q;
-  L.tables = 2 * (L.tA + L.tB + L.tC) + Np * Np + 3 * Np * Np + (diff ? 3 * Np * Np : 0) + O::NF * Np;
+  L.tables = 2 * (L.tA + L.tB + L.tC) + 2 * Np * Np + nnz + O::NF * Np;
   const int q2 = q * q, q3 = q2 * q;
   L.r1 = 15 * (q3 > Np ? q3 : Np);
-  L.r2 = 15 * (N + 1) * q2;
+  L.r2 = 15 * (N + 1) * q2 > 5 * Np ? 15 * (N + 1) * q2 : 5 * Np;
   L.r3 = 5 * Np + 5 * Nt2 * q > 15 * Nt2 * q ? 5 * Np + 5 * Nt2 * q : 15 * Nt2 * q;
   L.per_elem = GS + 5 * Np + 5 * O::NF + L.r1 + L.r2 + L.r3 + (diff ? 15 * Np : 0);
-  L.ints = O::NF + 3 * Nt2 + (N + 1) + Np;  // fmask, pq -> (p, first mode, count), p -> first pq, mode -> pq
+  // fmask, pq -> (p, first mode, count), p -> first pq, mode -> pq, Dh column starts and rows
+  L.ints = O::NF + 3 * Nt2 + (N + 1) + Np + (Np + 1) + nnz;
   return L;
 }
 
 template <int N>
-inline size_t oi_smem(int q, int E, bool diff) {
-  const OiLayout L = oi_layout<N>(q, diff);
+inline size_t oi_smem(int q, int nnz, int E, bool diff) {
+  const OiLayout L = oi_layout<N>(q, nnz, diff);
   return sizeof(double) * ((size_t)L.tables + (size_t)E * L.per_elem) + sizeof(int) * (size_t)L.ints;
 }
 
@@ -83,12 +87,12 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
                                                       const double* __restrict__ geo_g,
                                                       const int32_t* __restrict__ vmapP, unsigned* __restrict__ status,
                                                       const GasParams gp, const BcParams bc, const int K,
-                                                      const int nq, const int E, const double a, const double b,
-                                                      const double dt) {
+                                                      const int nq, const int nnz, const int E, const double a,
+                                                      const double b, const double dt) {
   using O = Ord<N>;
   constexpr int Np = O::Np, NF = O::NF, Nt2 = (N + 1) * (N + 2) / 2;
   constexpr bool DIFF = VISC || AV;
-  const OiLayout L = oi_layout<N>(nq, DIFF);
+  const OiLayout L = oi_layout<N>(nq, nnz, DIFF);
   const int q2 = nq * nq, q3 = q2 * nq;
   const int lT1 = Nt2 * nq, lT2 = (N + 1) * q2;  // per-slab lengths of T1|S2 and T2|S1
   extern __shared__ double smem[];
@@ -99,9 +103,9 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   double* sC = sBw + L.tB;             // [Np][q], then Cw
   double* sCw = sC + L.tC;
   double* sVi = sCw + L.tC;            // [Np(j)][Np(n)]: (V_o^-1)[n][j]
-  double* sZ = sVi + Np * Np;          // [3][Np(n)][Np(i)]: Z_a[i][n]
-  double* sDw = sZ + 3 * Np * Np;      // DIFF: [3][Np(j)][Np(i)]: Dw_a[i][j]
-  double* sLT = sDw + (DIFF ? 3 * Np * Np : 0);  // [NF][Np]: LIFT[i][m] at [m][i]
+  double* sVo = sVi + Np * Np;         // [Np(n)][Np(i)]: V_o[i][n]
+  double* sDh = sVo + Np * Np;         // [nnz]: Dh_a[m][n] by column n
+  double* sLT = sDh + nnz;             // [NF][Np]: LIFT[i][m] at [m][i]
   double* sGeo = sLT + NF * Np;        // [E][GS]
   double* sQ = sGeo + E * GS;          // [5][E][Np]
   double* sG = sQ + 5 * E * Np;        // [5][E][NF]: Fscale n.G*
@@ -115,14 +119,17 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   int* sPQc = sPQn + Nt2;              // pq -> modes with this (p, q)
   int* sP0 = sPQc + Nt2;               // p -> first pq
   int* sNpq = sP0 + (N + 1);           // mode -> pq
+  int* sDp = sNpq + Np;                // [Np + 1]: Dh column starts
+  int* sDi = sDp + (Np + 1);           // [nnz]: a Np + m of each Dh entry
   double* sX = R3;
   double* sT1 = R3 + 5 * E * Np;
   const int tid = threadIdx.x, NT = blockDim.x;
   const size_t KNp = (size_t)K * Np;
 
   {
-    const int ntab = 2 * (L.tA + L.tB + L.tC) + 4 * Np * Np + (DIFF ? 3 * Np * Np : 0);
+    const int ntab = 2 * (L.tA + L.tB + L.tC) + 2 * Np * Np + nnz;
     for (int i = tid; i < ntab; i += NT) smem[i] = tab[i];
+    for (int i = tid; i < Np + 1 + nnz; i += NT) sDp[i] = (int)tab[ntab + i];  // Dh_ptr | Dh_idx
   }
   for (int i = tid; i < Np * NF; i += NT) {
     const int r = i / NF, m = i - r * NF;
@@ -347,7 +354,8 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
     }
     __syncthreads();
 
-    // ---- G: moments y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], contravariant Y_a (into R1) ----
+    // ---- G: moments y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], contravariant Y_a, less the modes of
+    //      the nodal contravariant diffusive flux (into R1) ----
     for (int it = tid; it < 5 * nn; it += NT) {
       const int n = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
       const double* w = sCw + n * nq;
@@ -361,39 +369,47 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
         y[d] = acc;
       }
       const double* G = sGeo + e * GS;
+      const bool dif = DIFF && ((AV && av_eps[e0 + e] > 0.0) || (VISC && v > 0));
 #pragma unroll
-      for (int ra = 0; ra < 3; ++ra)
-        R1[((5 * ra + v) * E + e) * Np + n] = fma(G[3 * ra], y[0], fma(G[3 * ra + 1], y[1], G[3 * ra + 2] * y[2]));
+      for (int ra = 0; ra < 3; ++ra) {
+        double ya = fma(G[3 * ra], y[0], fma(G[3 * ra + 1], y[1], G[3 * ra + 2] * y[2]));
+        if (dif) {
+          // the diffusive part, M^-1 D_a^T M D_a = V_o Dh_a^T (V_o^-1 D_a): its modes join the moments
+          const double* dd = sD + ((5 * ra + v) * E + e) * Np;
+          double acc = 0.0;
+#pragma unroll 4
+          for (int j = 0; j < Np; ++j) acc = fma(sVi[j * Np + n], dd[j], acc);
+          ya -= acc;
+        }
+        R1[((5 * ra + v) * E + e) * Np + n] = ya;
+      }
     }
     __syncthreads();
 
-    // ---- H: rhs = sum_a Z_a Y_a - sum_a Dw_a D_a - LIFT (Fscale f*), then the output or RK update ----
+    // ---- G2: modal divergence u[n] = sum_a sum_m Dh_a[m][n] Y_a[m] (into R2) ----
+    for (int it = tid; it < 5 * nn; it += NT) {
+      const int n = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      const double* Y = R1 + (v * E + e) * Np;  // Y_a at Y[a 5 E Np + m]
+      double acc = 0.0;
+      for (int x = sDp[n]; x < sDp[n + 1]; ++x) {
+        const int am = sDi[x], ra = am / Np, m = am - ra * Np;
+        acc = fma(sDh[x], Y[ra * 5 * E * Np + m], acc);
+      }
+      R2[(v * E + e) * Np + n] = acc;
+    }
+    __syncthreads();
+
+    // ---- H: rhs = V_o u - LIFT (Fscale f*), then the output or RK update ----
     for (int it = tid; it < 5 * nn; it += NT) {
       const int i = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
-      double acc = 0.0, acd = 0.0;
-#pragma unroll
-      for (int ra = 0; ra < 3; ++ra) {
-        const double* y = R1 + ((5 * ra + v) * E + e) * Np;
-        const double* Z = sZ + ra * Np * Np + i;
+      const double* u = R2 + (v * E + e) * Np;
+      double acc = 0.0, acl = 0.0;
 #pragma unroll 4
-        for (int n = 0; n < Np; ++n) acc = fma(Z[n * Np], y[n], acc);
-      }
-      if (DIFF) {
-        const bool on = AV && av_eps[e0 + e] > 0.0;
-        if (on || (VISC && v > 0)) {
-#pragma unroll
-          for (int ra = 0; ra < 3; ++ra) {
-            const double* dd = sD + ((5 * ra + v) * E + e) * Np;
-            const double* W = sDw + ra * Np * Np + i;
-#pragma unroll 4
-            for (int j = 0; j < Np; ++j) acd = fma(W[j * Np], dd[j], acd);
-          }
-        }
-      }
+      for (int n = 0; n < Np; ++n) acc = fma(sVo[n * Np + i], u[n], acc);
       const double* gq = sG + (v * E + e) * NF;
 #pragma unroll 4
-      for (int m = 0; m < NF; ++m) acd = fma(sLT[m * Np + i], gq[m], acd);
-      acc -= acd;
+      for (int m = 0; m < NF; ++m) acl = fma(sLT[m * Np + i], gq[m], acl);
+      acc -= acl;
       const size_t gi = v * KNp + base + e * Np + i;
       if (RK) {
         const double kk = (a != 0.0 ? a * kreg[gi] : 0.0) + dt * acc;
@@ -410,12 +426,12 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
 // an SM's shared memory, else one block with as many elements as fit; false when one element does
 // not.
 template <int N>
-bool oi_config(int nq, bool diff, int& E, int& bps, size_t& smem) {
+bool oi_config(int nq, int nnz, bool diff, int& E, int& bps, size_t& smem) {
   int dev = 0, per_sm = 0, per_block = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const OiLayout L = oi_layout<N>(nq, diff);
+  const OiLayout L = oi_layout<N>(nq, nnz, diff);
   for (bps = 2; bps >= 1; --bps) {
     const size_t budget = std::min((size_t)per_block, (size_t)per_sm / bps - 1024);
     const size_t fixed = sizeof(double) * L.tables + sizeof(int) * L.ints;
@@ -423,7 +439,7 @@ bool oi_config(int nq, bool diff, int& E, int& bps, size_t& smem) {
     E = (int)((budget - fixed) / (sizeof(double) * L.per_elem));
     E = std::min(E, 64);
     if (E >= (bps == 2 ? 2 : 1)) {
-      smem = oi_smem<N>(nq, E, diff);
+      smem = oi_smem<N>(nq, nnz, E, diff);
       return true;
     }
   }
@@ -435,7 +451,7 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
                         double b, double dt, cudaStream_t s) {
   int E = 0, bps = 0;
   size_t smem = 0;
-  if (!oi_config<N>(m.oi_q, VISC || AV, E, bps, smem)) return cudaErrorInvalidConfiguration;
+  if (!oi_config<N>(m.oi_q, m.oi_nnz, VISC || AV, E, bps, smem)) return cudaErrorInvalidConfiguration;
   cudaError_t e =
       cudaFuncSetAttribute(rhs_oi_kernel<N, VISC, AV, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -446,22 +462,22 @@ cudaError_t launch_oi_t(const MeshDev& m, const GasParams& g, const double* q, d
   const int groups = (m.K + E - 1) / E;
   const int blocks = std::min(groups, sms * bps);
   rhs_oi_kernel<N, VISC, AV, RK><<<blocks, NT, smem, s>>>(q, out, k, m.oi_tab, m.scratch, m.av_sig, m.av_eps, m.ops,
-                                                            m.fmask, m.geo, m.vmapP, m.status, g, m.bc, m.K, m.oi_q,
+                                                            m.fmask, m.geo, m.vmapP, m.status, g, m.bc, m.K, m.oi_q, m.oi_nnz,
                                                             E, a, b, dt);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool overint_fits(int N, int q, bool visc, bool av) {
+bool overint_fits(int N, int q, int nnz, bool visc, bool av) {
   int E = 0, bps = 0;
   size_t smem = 0;
   const bool diff = visc || av;
   switch (N) {
-    case 1: return oi_config<1>(q, diff, E, bps, smem);
-    case 2: return oi_config<2>(q, diff, E, bps, smem);
-    case 3: return oi_config<3>(q, diff, E, bps, smem);
-    case 4: return oi_config<4>(q, diff, E, bps, smem);
+    case 1: return oi_config<1>(q, nnz, diff, E, bps, smem);
+    case 2: return oi_config<2>(q, nnz, diff, E, bps, smem);
+    case 3: return oi_config<3>(q, nnz, diff, E, bps, smem);
+    case 4: return oi_config<4>(q, nnz, diff, E, bps, smem);
     default: return false;
   }
 }

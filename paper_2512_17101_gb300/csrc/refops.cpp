@@ -460,29 +460,38 @@ bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::
   out.VinvT.assign(Np * Np, 0.0);
   for (int n = 0; n < Np; ++n)
     for (int j = 0; j < Np; ++j) out.VinvT[j * Np + n] = (double)Voi[n * Np + j];
-  // ZT[a][n][i] = (Wt_a V_o^-T)[i][n] = sum_j Wt_a[i][j] Voi[n][j];  DwT[a][j][i] = (Wt_a M)[i][j]
-  std::vector<ld> Mm = Voi;  // M = V_o^-T V_o^-1
-  for (int i = 0; i < Np; ++i)
-    for (int j = 0; j < Np; ++j) {
-      ld acc = 0;
-      for (int n = 0; n < Np; ++n) acc += Voi[n * Np + i] * Voi[n * Np + j];
-      Mm[i * Np + j] = acc;
-    }
-  out.ZT.assign(3 * Np * Np, 0.0);
-  out.DwT.assign(3 * Np * Np, 0.0);
-  for (int a = 0; a < 3; ++a)
-    for (int i = 0; i < Np; ++i) {
-      for (int n = 0; n < Np; ++n) {
-        ld acc = 0;
-        for (int j = 0; j < Np; ++j) acc += WtL[a][i * Np + j] * Voi[n * Np + j];
-        out.ZT[(a * Np + n) * Np + i] = (double)acc;
+  // modal derivative matrices Dh_a = V_o^-1 D_a V_o (the derivative of mode n in the modes), stored
+  // by column n with their structural zeros left out: Z_a = M^-1 D_a^T V_o^-T = V_o Dh_a^T, so the
+  // moments reach the nodes as V_o (sum_a Dh_a^T y_a).  A mode's derivative has lower degree and a
+  // collapsed-coordinate structure, so most entries vanish; they sit at rounding level, the others
+  // at >= 1e-4 of the largest, and a value in between is refused as a failed construction.
+  out.VoT.assign(Np * Np, 0.0);
+  for (int n = 0; n < Np; ++n)
+    for (int i = 0; i < Np; ++i) out.VoT[n * Np + i] = (double)Vo[i * Np + n];
+  std::vector<ld> Dh[3];
+  ld dmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    Dh[a] = matmul(matmul(Voi, Dl[a], Np, Np, Np), Vo, Np, Np, Np);
+    for (const ld x : Dh[a]) dmax = std::max(dmax, fabsl(x));
+  }
+  out.Dh_ptr.assign(1, 0);
+  out.Dh_idx.clear();
+  out.Dh_val.clear();
+  for (int n = 0; n < Np; ++n) {
+    for (int a = 0; a < 3; ++a)
+      for (int m = 0; m < Np; ++m) {
+        const ld x = Dh[a][m * Np + n], r = fabsl(x) / dmax;
+        if (r > 1e-12L && r < 1e-6L) {
+          err = "the modal derivative matrices have no clear zero pattern";
+          return false;
+        }
+        if (r >= 1e-6L) {
+          out.Dh_idx.push_back(a * Np + m);
+          out.Dh_val.push_back((double)x);
+        }
       }
-      for (int j = 0; j < Np; ++j) {
-        ld acc = 0;
-        for (int k = 0; k < Np; ++k) acc += WtL[a][i * Np + k] * Mm[k * Np + j];
-        out.DwT[(a * Np + j) * Np + i] = (double)acc;
-      }
-    }
+    out.Dh_ptr.push_back((int)out.Dh_val.size());
+  }
   return true;
 }
 
