@@ -564,12 +564,12 @@ int dg_mesh_set_overint(dg_mesh mesh, int32_t q) {
   if (!dg::build_overint_ops(d.N, mesh->ref_nodes.data(), q, o, err)) return fail(DG_ERR_INVALID_ARG, err);
   if (!dg::overint_fits(d.N, q, (int)o.Dh_val.size(), false, false))
     return fail(DG_ERR_UNSUPPORTED, "the over-integration tables and one element's work exceed a block's shared memory");
-  // device layout: A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx (the kernel's
-  // order; the small integers of the last two exact as doubles)
+  // device layout: A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx | Dh_col (the
+  // kernel's order; the small integers of the last three exact as doubles)
   std::vector<double> tab;
   for (const std::vector<double>* t : {&o.A, &o.Aw, &o.B, &o.Bw, &o.C, &o.Cw, &o.VinvT, &o.VoT, &o.Dh_val})
     tab.insert(tab.end(), t->begin(), t->end());
-  for (const std::vector<int>* t : {&o.Dh_ptr, &o.Dh_idx}) tab.insert(tab.end(), t->begin(), t->end());
+  for (const std::vector<int>* t : {&o.Dh_ptr, &o.Dh_idx, &o.Dh_col}) tab.insert(tab.end(), t->begin(), t->end());
   double* dev = nullptr;
   cudaError_t e = cudaMalloc((void**)&dev, sizeof(double) * tab.size());
   if (e == cudaSuccess) e = cudaMemcpy(dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);

@@ -44,9 +44,10 @@ struct OverintOps {
   std::vector<double> C, Cw;        // [Np][q]: C_pqr(c_k)
   std::vector<double> VinvT;        // [Np(j)][Np(n)]: (V_o^-1)[n][j], nodal values -> mode n
   std::vector<double> VoT;          // [Np(n)][Np(i)]: V_o[i][n], modes -> nodal values
-  // the modal derivative matrices Dh_a = V_o^-1 D_a V_o by column n, zeros left out: entries
-  // Dh_ptr[n] .. Dh_ptr[n+1] - 1 hold Dh_a[m][n] in Dh_val with a Np + m in Dh_idx
-  std::vector<int> Dh_ptr, Dh_idx;
+  // the modal derivative matrices Dh_a = V_o^-1 D_a V_o by column, zeros left out, the columns in
+  // the order Dh_col (longest first): entries Dh_ptr[s] .. Dh_ptr[s+1] - 1 hold Dh_a[m][n] of
+  // column n = Dh_col[s] in Dh_val, with a Np + m in Dh_idx
+  std::vector<int> Dh_ptr, Dh_idx, Dh_col;
   std::vector<double> Dh_val;
 };
 bool tet_quadrature(int q, std::vector<double>& rst, std::vector<double>& w, std::string& err);
@@ -153,8 +154,8 @@ struct MeshDev {
   double* prim = nullptr;      // FP64 form, perfect gas: [3][K][Np] (1/rho, p, c) of the state being
                                // differentiated, written by the primitives pass before each stage
   // over-integration (dg_mesh_set_overint; oi_q = 0: off): the sum-factorised tables of
-  // OverintOps, A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx (the last two
-  // as doubles), with oi_nnz entries in Dh
+  // OverintOps, A | Aw | B | Bw | C | Cw | V_o^-T | V_o^T | Dh_val | Dh_ptr | Dh_idx | Dh_col (the
+  // last three as doubles), with oi_nnz entries in Dh
   double* oi_tab = nullptr;
   int oi_q = 0, oi_ng = 0, oi_nnz = 0;
 };

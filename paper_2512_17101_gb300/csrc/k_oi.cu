@@ -29,7 +29,8 @@
 //      diffusive flux -> sD
 //   B. T1[pq][k] = sum_r C_pqr(c_k) X_pqr                      C. T2[p][j][k] = sum_q B_pq(b_j) T1
 //   D. per point: the state sum_p A_p(a_i) T2, its Euler flux F_d -> F (no weight, physical axes)
-//   E. S1[p][j][k] = sum_i Aw_p(a_i) F[i][j][k]                 F. S2[pq][k] = sum_j Bw_pq(b_j) S1
+//   E. S1[p][j][k] = sum_i Aw_p(a_i) F[i][j][k] (folded by the Gauss-Legendre symmetry)
+//   F. S2[pq][k] = sum_j Bw_pq(b_j) S1
 //   G. y_d[n] = sum_k Cw_n(c_k) S2[pq(n)][k], then Y_a = sum_d (dr_a/dx_d) y_d - V_o^-1 D_a
 //   G2. u = sum_a Dh_a^T Y_a (sparse)
 //   H. rhs = V_o u - LIFT (Fscale f*), then the RK update -> HBM
@@ -44,6 +45,13 @@ namespace {
 
 using kern::GS;
 using kern::Ord;
+
+// x > 0 and not NaN (+inf included), decided on the bits so that the check costs no FP64 issue:
+// positive doubles order like their bit patterns, and NaNs lie above +inf.
+__device__ __forceinline__ bool oi_positive(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7FF0000000000000LL;
+}
 
 // Shared-memory plan in doubles: the tables once per block, then per element.
 struct OiLayout {
@@ -65,8 +73,8 @@ __host__ __device__ inline OiLayout oi_layout(int q, int nnz, bool diff) {
   L.r2 = 15 * (N + 1) * q2 > 5 * Np ? 15 * (N + 1) * q2 : 5 * Np;
   L.r3 = 5 * Np + 5 * Nt2 * q > 15 * Nt2 * q ? 5 * Np + 5 * Nt2 * q : 15 * Nt2 * q;
   L.per_elem = GS + 5 * Np + 5 * O::NF + L.r1 + L.r2 + L.r3 + (diff ? 15 * Np : 0);
-  // fmask, pq -> (p, first mode, count), p -> first pq, mode -> pq, Dh column starts and rows
-  L.ints = O::NF + 3 * Nt2 + (N + 1) + Np + (Np + 1) + nnz;
+  // fmask, pq -> (p, first mode, count), p -> first pq, mode -> pq, Dh column starts, rows, columns
+  L.ints = O::NF + 3 * Nt2 + (N + 1) + Np + (Np + 1) + nnz + Np;
   return L;
 }
 
@@ -121,6 +129,7 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   int* sNpq = sP0 + (N + 1);           // mode -> pq
   int* sDp = sNpq + Np;                // [Np + 1]: Dh column starts
   int* sDi = sDp + (Np + 1);           // [nnz]: a Np + m of each Dh entry
+  int* sDc = sDi + nnz;                // [Np]: the column n of each stored column, longest first
   double* sX = R3;
   double* sT1 = R3 + 5 * E * Np;
   const int tid = threadIdx.x, NT = blockDim.x;
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   {
     const int ntab = 2 * (L.tA + L.tB + L.tC) + 2 * Np * Np + nnz;
     for (int i = tid; i < ntab; i += NT) smem[i] = tab[i];
-    for (int i = tid; i < Np + 1 + nnz; i += NT) sDp[i] = (int)tab[ntab + i];  // Dh_ptr | Dh_idx
+    for (int i = tid; i < 2 * Np + 1 + nnz; i += NT) sDp[i] = (int)tab[ntab + i];  // Dh_ptr | Dh_idx | Dh_col
   }
   for (int i = tid; i < Np * NF; i += NT) {
     const int r = i / NF, m = i - r * NF;
@@ -185,7 +194,8 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
       const double irm = 1.0 / qm[0], irp = 1.0 / qp[0];
       const double pm = gm1 * (qm[4] - 0.5 * irm * (qm[1] * qm[1] + qm[2] * qm[2] + qm[3] * qm[3]));
       const double pp = gm1 * (qp[4] - 0.5 * irp * (qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]));
-      if (!(qp[0] > 0.0) || !(pp > 0.0) || !(qm[0] > 0.0) || !(pm > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      if (!oi_positive(qp[0]) || !oi_positive(pp) || !oi_positive(qm[0]) || !oi_positive(pm))
+        atomicOr(status, DG_STATUS_NONPHYSICAL);
       const double cm = sqrt(gp.gamma * pm * irm), cp = sqrt(gp.gamma * pp * irp);
       const double unm = (qm[1] * nx + qm[2] * ny + qm[3] * nz) * irm;
       const double unp = (qp[1] * nx + qp[2] * ny + qp[3] * nz) * irp;
@@ -316,29 +326,59 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
       }
       const double ir = 1.0 / qg[0];
       const double u[3] = {qg[1] * ir, qg[2] * ir, qg[3] * ir};
-      const double p = gm1 * (qg[4] - 0.5 * (qg[1] * u[0] + qg[2] * u[1] + qg[3] * u[2]));
-      if (!(qg[0] > 0.0) || !(p > 0.0)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      // rho u_c u_d, each product once: the flux's momentum block is symmetric
+      const double mxx = qg[1] * u[0], myy = qg[2] * u[1], mzz = qg[3] * u[2];
+      const double mxy = qg[1] * u[1], mxz = qg[1] * u[2], myz = qg[2] * u[2];
+      const double p = gm1 * fma(-0.5, mxx + myy + mzz, qg[4]);
+      if (!oi_positive(qg[0]) || !oi_positive(p)) atomicOr(status, DG_STATUS_NONPHYSICAL);
+      const double H = qg[4] + p;
       double* F = R1 + e * q3 + g;
       const int sl = E * q3;  // slab stride
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        F[(5 * d + 0) * sl] = qg[1 + d];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) F[(5 * d + 1 + c) * sl] = c == d ? fma(qg[1 + c], u[d], p) : qg[1 + c] * u[d];
-        F[(5 * d + 4) * sl] = u[d] * (qg[4] + p);
-      }
+      F[0 * sl] = qg[1];
+      F[1 * sl] = mxx + p;
+      F[2 * sl] = mxy;
+      F[3 * sl] = mxz;
+      F[4 * sl] = u[0] * H;
+      F[5 * sl] = qg[2];
+      F[6 * sl] = mxy;
+      F[7 * sl] = myy + p;
+      F[8 * sl] = myz;
+      F[9 * sl] = u[1] * H;
+      F[10 * sl] = qg[3];
+      F[11 * sl] = mxz;
+      F[12 * sl] = myz;
+      F[13 * sl] = mzz + p;
+      F[14 * sl] = u[2] * H;
     }
     __syncthreads();
 
-    // ---- E: S1[p][j][k] = sum_i Aw_p(a_i) F[(k q + j) q + i] (into R2) ----
-    for (int it = tid; it < 15 * nel * lT2; it += NT) {
-      const int idx = it % lT2, rest = it / lT2, e = rest % nel, s = rest / nel;
-      const int p = idx / q2, jk = idx - p * q2, j = jk / nq, k = jk - j * nq;
-      const double* f = R1 + (s * E + e) * q3 + (k * nq + j) * nq;
-      const double* w = sAw + p * nq;
-      double acc = 0.0;
-      for (int i = 0; i < nq; ++i) acc = fma(w[i], f[i], acc);
-      R2[(s * E + e) * lT2 + idx] = acc;
+    // ---- E: S1[p][j][k] = sum_i Aw_p(a_i) F[(k q + j) q + i] (into R2), one thread per line
+    //      (s, e, j, k) for every p, folded by the rule's symmetry Aw_p(a_(q-1-i)) = (-1)^p Aw_p(a_i):
+    //      even p take F_i + F_(q-1-i), odd p the difference, and odd p skip the middle point ----
+    {
+      const int h = nq >> 1;
+      for (int it = tid; it < 15 * nel * q2; it += NT) {
+        const int jk = it % q2, rest = it / q2, e = rest % nel, s = rest / nel;
+        const int j = jk / nq, k = jk - j * nq;
+        const double* f = R1 + (s * E + e) * q3 + (k * nq + j) * nq;
+        double acc[N + 1];
+#pragma unroll
+        for (int p = 0; p <= N; ++p) acc[p] = 0.0;
+        for (int i = 0; i < h; ++i) {
+          const double x = f[i], y = f[nq - 1 - i];
+          const double ev = x + y, od = x - y;
+#pragma unroll
+          for (int p = 0; p <= N; ++p) acc[p] = fma(sAw[p * nq + i], (p & 1) ? od : ev, acc[p]);
+        }
+        if (nq & 1) {
+          const double mid = f[h];
+#pragma unroll
+          for (int p = 0; p <= N; p += 2) acc[p] = fma(sAw[p * nq + h], mid, acc[p]);
+        }
+        double* o = R2 + (s * E + e) * lT2 + jk;  // S1 index (p q + j) q + k = p q^2 + jk
+#pragma unroll
+        for (int p = 0; p <= N; ++p) o[p * q2] = acc[p];
+      }
     }
     __syncthreads();
 
@@ -387,11 +427,14 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
     __syncthreads();
 
     // ---- G2: modal divergence u[n] = sum_a sum_m Dh_a[m][n] Y_a[m] (into R2) ----
+    // stored column c, then field and element, so that a warp's threads walk columns of similar
+    // length (the columns are stored longest first)
     for (int it = tid; it < 5 * nn; it += NT) {
-      const int n = it % Np, rest = it / Np, e = rest % nel, v = rest / nel;
+      const int c = it / (5 * nel), r = it - c * 5 * nel, v = r / nel, e = r - v * nel;
+      const int n = sDc[c];
       const double* Y = R1 + (v * E + e) * Np;  // Y_a at Y[a 5 E Np + m]
       double acc = 0.0;
-      for (int x = sDp[n]; x < sDp[n + 1]; ++x) {
+      for (int x = sDp[c]; x < sDp[c + 1]; ++x) {
         const int am = sDi[x], ra = am / Np, m = am - ra * Np;
         acc = fma(sDh[x], Y[ra * 5 * E * Np + m], acc);
       }

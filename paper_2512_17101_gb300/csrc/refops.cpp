@@ -474,24 +474,45 @@ bool build_overint_ops(int N, const double* nodes, int q, OverintOps& out, std::
     Dh[a] = matmul(matmul(Voi, Dl[a], Np, Np, Np), Vo, Np, Np, Np);
     for (const ld x : Dh[a]) dmax = std::max(dmax, fabsl(x));
   }
-  out.Dh_ptr.assign(1, 0);
-  out.Dh_idx.clear();
-  out.Dh_val.clear();
-  for (int n = 0; n < Np; ++n) {
+  // columns stored longest first, so that the threads of a warp walk columns of similar length
+  std::vector<int> len(Np, 0);
+  for (int n = 0; n < Np; ++n)
     for (int a = 0; a < 3; ++a)
       for (int m = 0; m < Np; ++m) {
-        const ld x = Dh[a][m * Np + n], r = fabsl(x) / dmax;
+        const ld r = fabsl(Dh[a][m * Np + n]) / dmax;
         if (r > 1e-12L && r < 1e-6L) {
           err = "the modal derivative matrices have no clear zero pattern";
           return false;
         }
-        if (r >= 1e-6L) {
+        len[n] += r >= 1e-6L;
+      }
+  out.Dh_col.resize(Np);
+  for (int n = 0; n < Np; ++n) out.Dh_col[n] = n;
+  std::stable_sort(out.Dh_col.begin(), out.Dh_col.end(), [&](int x, int y) { return len[x] > len[y]; });
+  out.Dh_ptr.assign(1, 0);
+  out.Dh_idx.clear();
+  out.Dh_val.clear();
+  for (const int n : out.Dh_col) {
+    for (int a = 0; a < 3; ++a)
+      for (int m = 0; m < Np; ++m) {
+        const ld x = Dh[a][m * Np + n];
+        if (fabsl(x) / dmax >= 1e-6L) {
           out.Dh_idx.push_back(a * Np + m);
           out.Dh_val.push_back((double)x);
         }
       }
     out.Dh_ptr.push_back((int)out.Dh_val.size());
   }
+  // A_p has the parity of p and the Gauss-Legendre rule is symmetric: Aw_p(a_(q-1-i)) =
+  // (-1)^p Aw_p(a_i), which the backward sum over i folds; check it holds to rounding
+  for (int p = 0; p <= N; ++p)
+    for (int i = 0; i < q; ++i) {
+      const ld x = Al[p * q + i] * gwa[i], y = Al[p * q + q - 1 - i] * gwa[q - 1 - i] * (p % 2 ? -1 : 1);
+      if (fabsl(x - y) > 1e-15L * (1 + fabsl(x))) {
+        err = "the Gauss-Legendre rule is not symmetric";
+        return false;
+      }
+    }
   return true;
 }
 
