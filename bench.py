@@ -661,7 +661,8 @@ def overint_flops_per_element(N, Q, viscous=False):
     """FP64 flops of one element in the sum-factorised over-integrated right-hand side (Q points
     per collapsed direction, Q^3 in all; an FMA counts two): the modes (V_o^-1 on 5 fields), the
     three 1-D sums to the points, per point the state's last sum and the Euler flux (about 30), the
-    three weighted 1-D sums back for the 15 flux components, the moments' contravariant transform
+    three weighted 1-D sums back for the 15 flux components (the first folded by the symmetry of
+    the Gauss-Legendre points), the moments' contravariant transform
     (15 per mode and field), the sparse modal derivative matrices, V_o and LIFT; about 100 per face
     node for the Lax-Friedrichs flux.  Viscous: the nodal contravariant viscous flux (75 per node),
     the modes of its four rows (V_o^-1 for each direction), and about 40 more per face node for the
@@ -670,7 +671,10 @@ def overint_flops_per_element(N, Q, viscous=False):
     NF, Nt2, q2, q3 = 4 * Nfp, Nfp, Q * Q, Q ** 3
     f = 2 * 5 * Np * Np + 2 * 5 * Q * Np + 2 * 5 * q2 * Nt2
     f += q3 * (2 * 5 * (N + 1) + 30)
-    f += 2 * 15 * (N + 1) * q3 + 2 * 15 * Nt2 * q2 + 5 * Np * (2 * 3 * Q + 15)
+    h = Q // 2  # the backward a-sum folds the symmetric Gauss-Legendre points: per line 2h sums, then
+    # h FMAs per mode p and the middle point for even p
+    f += 15 * q2 * (2 * h + 2 * (N + 1) * h + 2 * ((N + 2) // 2) * (Q % 2))
+    f += 2 * 15 * Nt2 * q2 + 5 * Np * (2 * 3 * Q + 15)
     f += 2 * 5 * MODAL_DERIVATIVE_NNZ[N] + 2 * 5 * Np * (Np + NF) + 100 * NF
     if viscous:
         f += 75 * Np + 2 * 4 * 3 * Np * Np + 40 * NF
