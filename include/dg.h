@@ -213,18 +213,22 @@ int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* st
 int dg_tet_quadrature(int32_t q, double* rst_host, double* w_host);
 
 /* Over-integration for later dg_rhs / dg_rk_stage calls on the mesh: q points per direction,
- * DG_OVERINT_DEFAULT for ceil(3N/2), 0 for the collocated strong form again.  Builds the tables
- * (the nodal basis at the points, the weights, M^-1 D_a^T) from the mesh's reference nodes and
- * copies them to the device (cudaMalloc; the mesh owns them).  Right-hand sides with it on run
- * in the FP64 form with a perfect gas (Euler or Navier-Stokes), periodic or with boundary faces,
- * over the whole mesh, with or without artificial viscosity (whose flux sigma = eps grad_h q, a
- * degree-N field, is integrated on the rule with G, and whose central face flux joins n.G*); the
- * mixed-precision and batched forms, a mixture, element ranges and prims_given are
- * DG_ERR_UNSUPPORTED then, and so is a viscous or AV right-hand side whose larger per-element work
+ * DG_OVERINT_DEFAULT for ceil(3N/2), 0 for the collocated strong form again.  Builds the
+ * sum-factorised tables in long double from the mesh's reference nodes (the collapsed-coordinate
+ * factors of the orthonormal modes at the rule's 1-D points, with and without the weights, V_o^-1,
+ * V_o and the modal derivative matrices V_o^-1 D_a V_o by column, their structural zeros left
+ * out) and copies them to the device (cudaMalloc; the mesh owns them).  Right-hand sides with it
+ * on run in the FP64 form with a perfect gas (Euler or Navier-Stokes), periodic or with boundary
+ * faces, over the whole mesh, with or without artificial viscosity (whose flux sigma =
+ * eps grad_h q, a degree-N field, is integrated with G, and whose central face flux joins n.G*).
+ * The viscous and AV fluxes, degree-N nodal fields, take their exact weak form, which the rule
+ * reproduces from q = N + 1 on: below that a viscous or AV right-hand side is DG_ERR_UNSUPPORTED.
+ * The mixed-precision and batched forms, a mixture, element ranges and prims_given are
+ * DG_ERR_UNSUPPORTED too, and so is a viscous or AV right-hand side whose larger per-element work
  * does not fit at this point count.  Errors:
- * DG_ERR_INVALID_ARG (host-only mesh, q below -1 or above DG_MAX_OVERINT_POINTS),
- * DG_ERR_UNSUPPORTED (the tables and one element's Euler work do not fit in a block's shared
- * memory), DG_ERR_CUDA, DG_ERR_OOM. */
+ * DG_ERR_INVALID_ARG (host-only mesh, q below -1 or above DG_MAX_OVERINT_POINTS, a table
+ * construction that fails its own checks), DG_ERR_UNSUPPORTED (the tables and one element's Euler
+ * work do not fit in a block's shared memory), DG_ERR_CUDA, DG_ERR_OOM. */
 int dg_mesh_set_overint(dg_mesh mesh, int32_t q);
 
 /* ---- partitioned meshes: halo exchange support -------------------------------------------

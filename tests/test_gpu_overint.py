@@ -202,3 +202,36 @@ def test_overint_refusals():
         mesh.set_overint(-2)
     dg.dg_rhs(mesh, gas, q, rhs)
     assert rel_err(rhs.cpu().numpy(), _want(d, q0)) <= TOL
+
+
+@pytest.mark.parametrize("av_on", [False, True])
+def test_overint_diffusive_fluxes_need_n_plus_one_points(av_on):
+    """The viscous and AV fluxes take the exact weak form of a degree-N nodal field, which the rule
+    reproduces only from N + 1 points per direction: with N points the right-hand side is
+    refused, with N + 1 it matches the oracle on that rule, and Euler still runs with N points."""
+    from paper_2512_17101_gb300 import capi
+    from tests.test_gpu_av import EPS0
+    N = 3
+    torch, dg, d, mesh, gas = _setup((3, 2, 2), N, SIDES["in_out_x_walls_y"], q=N, viscous=not av_on)
+    q0 = _smooth(d.xyz, seed=6)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    if av_on:
+        mesh.set_av(EPS0, -40.0, 1.0)  # a threshold far below the smooth state's indicator: eps0 everywhere
+    with pytest.raises(capi.DGError):
+        dg.dg_rhs(mesh, gas, q, rhs)
+    if not av_on:
+        euler = dg.Gas(model="perfect", gamma=1.4, R=1.0, mu=0.0, Pr=PR)
+        dg.dg_rhs(mesh, euler, q, rhs)
+        assert rel_err(rhs.cpu().numpy(), _want(d, q0, Q=N)) <= TOL
+    mesh.set_overint(N + 1)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    if av_on:
+        import oracle.av as av
+        eps = av.element_viscosity(d.ref, q0, EPS0, -40.0, 1.0)
+        assert (eps > 0).all()
+        want = oi.rhs_overint_av(d.ref, d.geo, d.conn, q0, GAS, eps, Q=N + 1, q_in=Q_IN)
+    else:
+        want = _want(d, q0, Q=N + 1, viscous=True)
+    assert rel_err(rhs.cpu().numpy(), want) <= TOL
+    assert mesh.status() == 0
