@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   double* sQ = sGeo + E * GS;          // [5][E][Np]
   double* sG = sQ + 5 * E * Np;        // [5][E][NF]: Fscale n.G*
   double* R1 = sG + 5 * E * NF;        // F [15][E][q3] (slab 5 d + v), then Y [15][E][Np] (slab 5 a + v)
-  double* R2 = R1 + E * L.r1;          // T2 [5][E][lT2], then S1 [15][E][lT2]
+  double* R2 = R1 + E * L.r1;          // T2 [5][E][lT2], then S1 [15][E][lT2], then u [5][E][Np]
   double* R3 = R2 + E * L.r2;          // X [5][E][Np] | T1 [5][E][lT1], then S2 [15][E][lT1]
   double* sD = R3 + E * L.r3;          // DIFF: [15][E][Np] contravariant diffusive flux (slab 5 a + v)
   int* sFm = reinterpret_cast<int*>(sD + (DIFF ? 15 * E * Np : 0));
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(512, 1) rhs_oi_kernel(const double* __restrict
   int* sPQc = sPQn + Nt2;              // pq -> modes with this (p, q)
   int* sP0 = sPQc + Nt2;               // p -> first pq
   int* sNpq = sP0 + (N + 1);           // mode -> pq
-  int* sDp = sNpq + Np;                // [Np + 1]: Dh column starts
+  int* sDp = sNpq + Np;                // [Np + 1]: starts of the stored Dh columns
   int* sDi = sDp + (Np + 1);           // [nnz]: a Np + m of each Dh entry
   int* sDc = sDi + nnz;                // [Np]: the column n of each stored column, longest first
   double* sX = R3;

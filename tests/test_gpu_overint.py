@@ -235,3 +235,17 @@ def test_overint_diffusive_fluxes_need_n_plus_one_points(av_on):
         want = _want(d, q0, Q=N + 1, viscous=True)
     assert rel_err(rhs.cpu().numpy(), want) <= TOL
     assert mesh.status() == 0
+
+
+@pytest.mark.parametrize("N,Q,viscous", [(2, 11, False), (3, 10, True), (4, 9, False), (4, 9, True)])
+def test_overint_largest_point_counts(N, Q, viscous):
+    """The largest point counts that fit: one element per block, even and odd Q (the folded
+    a-sum with and without a middle point), Q >= 2N, so that the rule is exact for the cubic
+    energy flux of a degree-N state too."""
+    torch, dg, d, mesh, gas = _setup((3, 2, 2), N, SIDES["in_out_x_walls_y"], q=Q, viscous=viscous)
+    q0 = _smooth(d.xyz, seed=7)
+    q = torch.tensor(q0, device="cuda")
+    rhs = torch.empty_like(q)
+    dg.dg_rhs(mesh, gas, q, rhs)
+    assert rel_err(rhs.cpu().numpy(), _want(d, q0, Q=Q, viscous=viscous)) <= TOL
+    assert mesh.status() == 0
