@@ -42,6 +42,7 @@ struct dg_hex_mesh_s {
   double* av_sig = nullptr;
   bool overint = false;             // dg_hex_set_overintegration
   std::vector<double> oi_I, oi_A, oi_B;  // [Q][M], [M][Q], [M][Q]
+  std::vector<double> oi_An, oi_Bn;      // [M][M]: A I and B I, the same contractions of a nodal field
   std::vector<double> modal;        // [M][M]: nodal values -> Legendre coefficients (GLL-weighted)
   std::vector<double> modal_norm;   // [M]: discrete norms of the Legendre polynomials
   unsigned* status = nullptr;
@@ -601,16 +602,17 @@ struct OiCfg {
   static constexpr int EPB = N == 1 ? 16 : (N == 2 ? 4 : (N == 3 ? 2 : 1));
   static constexpr int NT = 256;
   // doubles per element: nodal state, x-, y- and z-interpolated state, fluxes, volume and face terms;
-  // VISC or AV: the nodal diffusive flux (viscous and artificial) of one direction, five rows, and
-  // its Gauss-point values
-  static constexpr int PER = 5 * (Np + M * M * Q + M * Q * Q + 2 * Q * Q * Q + 2 * Np) + (VISC || AV ? 5 * (Np + Q * Q * Q) : 0);
+  // VISC or AV: the nodal diffusive flux (viscous and artificial) of one direction, five rows
+  static constexpr int PER = 5 * (Np + M * M * Q + M * Q * Q + 2 * Q * Q * Q + 2 * Np) + (VISC || AV ? 5 * Np : 0);
   static constexpr size_t SMEM = sizeof(double) * PER * EPB + sizeof(int) * 6 * EPB;
 };
 
 struct HexOI {
-  double I[40];  // [Q][M]
-  double A[40];  // [M][Q]
-  double B[40];  // [M][Q]
+  double I[40];   // [Q][M]
+  double A[40];   // [M][Q]
+  double B[40];   // [M][Q]
+  double An[25];  // [M][M]: A I = W^-1 D^T M_e, exact for a degree-N nodal field (Q >= N + 1)
+  double Bn[25];  // [M][M]: B I = W^-1 M_e
 };
 
 template <int N, bool RK, bool VISC, bool AV>
@@ -633,8 +635,7 @@ __global__ void __launch_bounds__(OiCfg<N, VISC, AV>::NT) hex_oi_kernel(const do
   double* acc = sF + 5 * EPB * Q3;      // [5][EPB][Np]       volume term
   double* sS = acc + 5 * EPB * Np;      // [5][EPB][Np]       face terms
   double* sFvN = sS + 5 * EPB * Np;     // DIF: [5][EPB][Np] the nodal diffusive flux along d, row by row
-  double* sV = sFvN + (DIF ? 5 * EPB * Np : 0);  // DIF: [5][EPB][Q][Q][Q] the same at the Gauss points
-  int(*sNb)[6] = reinterpret_cast<int(*)[6]>(sV + (DIF ? 5 * EPB * Q3 : 0));
+  int(*sNb)[6] = reinterpret_cast<int(*)[6]>(sFvN + (DIF ? 5 * EPB * Np : 0));
   const int tid = threadIdx.x;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int nel = (int)min((int64_t)EPB, K - e0);
@@ -699,9 +700,11 @@ __global__ void __launch_bounds__(OiCfg<N, VISC, AV>::NT) hex_oi_kernel(const do
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     if constexpr (DIF) {
-      // the diffusive flux along d at the Gauss points, row v: the viscous tau_(v-1)d or Q_d
-      // (VISC) plus the artificial sigma_dv where the element has eps > 0 (AV); three interpolation
-      // passes through the sA and sB scratch, as for the state
+      // the diffusive flux along d, row v: the viscous tau_(v-1)d or Q_d (VISC) plus the artificial
+      // sigma_dv where the element has eps > 0 (AV).  A degree-N nodal field is its own interpolant
+      // and the Q >= N + 1 Gauss points integrate its products with the test functions exactly, so
+      // its part of the volume term is (A I) (x) (B I) (x) (B I) on the nodes: three M x M passes
+      // through the sA and sB scratch instead of interpolating it to the Q^3 points.
       for (int t = tid; t < 5 * nn; t += NT) {
         const int v = t / nn, r = t - v * nn;
         double f = 0.0;
@@ -710,34 +713,38 @@ __global__ void __launch_bounds__(OiCfg<N, VISC, AV>::NT) hex_oi_kernel(const do
         sFvN[v * EPB * Np + r] = f;
       }
       __syncthreads();
-      for (int t = tid; t < 5 * nel * M2 * Q; t += NT) {
-        const int v = t / (nel * M2 * Q), r = t - v * nel * M2 * Q, el = r / (M2 * Q), s2 = r - el * M2 * Q;
-        const int kj = s2 / Q, qa = s2 - kj * Q;
+      const double* Xn = d == 0 ? op.An : op.Bn;
+      const double* Yn = d == 1 ? op.An : op.Bn;
+      const double* Zn = d == 2 ? op.An : op.Bn;
+      for (int t = tid; t < 5 * nn; t += NT) {  // along x: node (k M + j) M + i
+        const int v = t / nn, r = t - v * nn, el = r / Np, node = r - el * Np;
+        const int i = node % M, kj = node / M;
         const double* src = sFvN + v * EPB * Np + el * Np + kj * M;
         double c = 0.0;
 #pragma unroll
-        for (int i = 0; i < M; ++i) c = fma(op.I[qa * M + i], src[i], c);
-        sA[v * EPB * M2 * Q + el * M2 * Q + s2] = c;
+        for (int x = 0; x < M; ++x) c = fma(Xn[i * M + x], src[x], c);
+        sA[v * EPB * Np + r] = c;
       }
       __syncthreads();
-      for (int t = tid; t < 5 * nel * M * Q2; t += NT) {
-        const int v = t / (nel * M * Q2), r = t - v * nel * M * Q2, el = r / (M * Q2), s2 = r - el * M * Q2;
-        const int k = s2 / Q2, qb = (s2 / Q) % Q, qa = s2 % Q;
-        const double* src = sA + v * EPB * M2 * Q + el * M2 * Q + k * M * Q + qa;
+      for (int t = tid; t < 5 * nn; t += NT) {  // along y
+        const int v = t / nn, r = t - v * nn, el = r / Np, node = r - el * Np;
+        const int k = node / M2, j = (node / M) % M, i = node % M;
+        const double* src = sA + v * EPB * Np + el * Np + k * M2 + i;
         double c = 0.0;
 #pragma unroll
-        for (int j = 0; j < M; ++j) c = fma(op.I[qb * M + j], src[j * Q], c);
-        sB[v * EPB * M * Q2 + el * M * Q2 + s2] = c;
+        for (int x = 0; x < M; ++x) c = fma(Yn[j * M + x], src[x * M], c);
+        sB[v * EPB * Np + r] = c;
       }
       __syncthreads();
-      for (int t = tid; t < 5 * nel * Q3; t += NT) {
-        const int v = t / (nel * Q3), r = t - v * nel * Q3, el = r / Q3, s2 = r - el * Q3;
-        const int qc = s2 / Q2, qba = s2 - qc * Q2;
-        const double* src = sB + v * EPB * M * Q2 + el * M * Q2 + qba;
+      const double fac = -geo.dsc[d];
+      for (int t = tid; t < 5 * nn; t += NT) {  // along z, subtracted from the volume term (G = F - Fd)
+        const int v = t / nn, r = t - v * nn, el = r / Np, node = r - el * Np;
+        const int k = node / M2, ji = node - k * M2;
+        const double* src = sB + v * EPB * Np + el * Np + ji;
         double c = 0.0;
 #pragma unroll
-        for (int k = 0; k < M; ++k) c = fma(op.I[qc * M + k], src[k * Q2], c);
-        sV[v * EPB * Q3 + el * Q3 + s2] = c;
+        for (int x = 0; x < M; ++x) c = fma(Zn[k * M + x], src[x * M2], c);
+        acc[v * EPB * Np + r] = fma(-fac, c, acc[v * EPB * Np + r]);
       }
       __syncthreads();
     }
@@ -757,10 +764,6 @@ __global__ void __launch_bounds__(OiCfg<N, VISC, AV>::NT) hex_oi_kernel(const do
       sF[2 * EPB * Q3 + t] = qv[2] * ud + (d == 1 ? p : 0.0);
       sF[3 * EPB * Q3 + t] = qv[3] * ud + (d == 2 ? p : 0.0);
       sF[4 * EPB * Q3 + t] = ud * (qv[4] + p);
-      if constexpr (DIF) {  // G_d = F_d minus the diffusive flux
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sF[v * EPB * Q3 + t] -= sV[v * EPB * Q3 + t];
-      }
     }
     __syncthreads();
     // contraction along x: [Q][Q][Q] -> [Q][Q][M] (into the sB region)
@@ -1095,6 +1098,8 @@ cudaError_t launch_oi_t(const dg_hex_mesh_s& m, double gamma, const double* q, d
   for (size_t i = 0; i < m.oi_I.size(); ++i) op.I[i] = m.oi_I[i];
   for (size_t i = 0; i < m.oi_A.size(); ++i) op.A[i] = m.oi_A[i];
   for (size_t i = 0; i < m.oi_B.size(); ++i) op.B[i] = m.oi_B[i];
+  for (size_t i = 0; i < m.oi_An.size(); ++i) op.An[i] = m.oi_An[i];
+  for (size_t i = 0; i < m.oi_Bn.size(); ++i) op.Bn[i] = m.oi_Bn[i];
   const int64_t blocks = (m.K + C::EPB - 1) / C::EPB;
   hex_oi_kernel<N, RK, VISC, AV><<<(unsigned)blocks, C::NT, C::SMEM, s>>>(
       q, out, k, make_geo<N>(m, RK ? dt : 1.0), op, m.K, gamma, a, b, a != 0.0, m.status, m.fv_dev, m.av_sig, m.av_eps);
@@ -1466,6 +1471,21 @@ int dg_hex_set_overintegration(dg_hex_mesh m, int32_t enable) {
       for (int k = 0; k < M; ++k) id += I[(size_t)g * M + k] * (ld)m->D[(size_t)k * M + i];
       m->oi_A[(size_t)i * Q + g] = (double)(id * wg[g] / (ld)m->w[i]);
       m->oi_B[(size_t)i * Q + g] = (double)(I[(size_t)g * M + i] * wg[g] / (ld)m->w[i]);
+    }
+  // A I and B I: the contractions of a degree-N nodal field's interpolant, M x M
+  m->oi_An.assign((size_t)M * M, 0.0);
+  m->oi_Bn.assign((size_t)M * M, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      ld an = 0.0L, bn = 0.0L;
+      for (int g = 0; g < Q; ++g) {
+        ld id = 0.0L;
+        for (int k = 0; k < M; ++k) id += I[(size_t)g * M + k] * (ld)m->D[(size_t)k * M + i];
+        an += id * wg[g] * I[(size_t)g * M + j];
+        bn += I[(size_t)g * M + i] * wg[g] * I[(size_t)g * M + j];
+      }
+      m->oi_An[(size_t)i * M + j] = (double)(an / (ld)m->w[i]);
+      m->oi_Bn[(size_t)i * M + j] = (double)(bn / (ld)m->w[i]);
     }
   return DG_OK;
 }
