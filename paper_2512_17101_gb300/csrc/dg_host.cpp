@@ -241,10 +241,11 @@ int run_rhs(dg_mesh mesh, dg_gas gas, const double* q, double* out, double* k, d
         e = timed(mesh, DG_KERNEL_VISCOUS, s, [&] { return dg::launch_viscous_tc(m, g, q, s, opts->wait_polls); });
         if (e != cudaSuccess) return cuda_fail(e, "mixed viscous kernel");
       }
-      if (av) {  // the element viscosities and the AV flux in FP64, for the tensor-core right-hand side
+      if (av) {  // the element viscosities and the AV flux in FP32 arithmetic, for the tensor-core
+                 // right-hand side, which takes sigma as one of its FP32 terms
         e = timed(mesh, DG_KERNEL_AV, s, [&] {
-          cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s, m.av_list);
-          return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s) : e2;
+          cudaError_t e2 = dg::launch_av_sensor(m, q, m.av_eps, s, m.av_list, true);
+          return e2 == cudaSuccess ? dg::launch_av_flux(m, g, q, s, true) : e2;
         });
         if (e != cudaSuccess) return cuda_fail(e, "artificial-viscosity kernels");
       }

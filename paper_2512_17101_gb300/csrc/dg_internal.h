@@ -179,7 +179,9 @@ cudaError_t launch_rhs(const MeshDev& m, const GasParams& g, const double* q, do
 // Artificial viscosity (k_av.cu): element viscosities of q into eps [K]; the flux eps grad q into
 // m.av_sig (from m.av_eps); the right-hand side / RK stage with that flux added.
 // list (may be null): m.av_list, refilled with the elements whose eps > 0 for launch_av_flux.
-cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s, int* list = nullptr);
+// fp32: the arithmetic in FP32 (the mixed-precision form), else FP64; eps and sigma stay FP64 arrays.
+cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cudaStream_t s, int* list = nullptr,
+                             bool fp32 = false);
 // Over-integrated weak-form Euler or Navier-Stokes right-hand side / RK stage of a perfect gas
 // (k_oi.cu; Navier-Stokes reads the BR1 viscous flux in m.scratch, artificial viscosity the flux of
 // the AV pass in m.av_sig), and whether its tables and one element's work for Ng points fit in a
@@ -187,7 +189,7 @@ cudaError_t launch_av_sensor(const MeshDev& m, const double* q, double* eps, cud
 cudaError_t launch_rhs_overint(const MeshDev& m, const GasParams& g, const double* q, double* out, double* k,
                                bool rk, double a, double b, double dt, cudaStream_t s);
 bool overint_fits(int N, int q, int nnz, bool visc, bool av);
-cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s);
+cudaError_t launch_av_flux(const MeshDev& m, const GasParams& g, const double* q, cudaStream_t s, bool fp32 = false);
 // Mixture with viscosity (k_mixns.cu): BR1 gradients of (rho, rho u, T, Y_k) and the viscous
 // flux with species diffusion into m.mix_fv; the right-hand side / RK stage that subtracts it.
 cudaError_t launch_viscous_mixture(const MeshDev& m, const GasParams& g, const double* q, const double* T,
