@@ -202,9 +202,11 @@ int dg_av_viscosity(dg_mesh mesh, const double* q_dev, double* eps_dev, void* st
  * (1 - c)^2, so q^3 points with positive weights, exact for total degree 2q - 1; ceil(3N/2)
  * points integrate degree 3N - 1, a degree-N field's quadratic fluxes against the test
  * functions' gradients.  Navier-Stokes: the whole flux G = F - Fv is integrated on the rule, with
- * the nodal BR1 viscous flux Fv of the first pass interpolated to the points (a degree-N field,
- * so that part equals the collocated weak-form term), and the face flux gains minus the central
- * viscous flux with the walls' exterior viscous fluxes, as in the collocated form. */
+ * the nodal BR1 viscous flux Fv of the first pass interpolated to the points.  Fv is a degree-N
+ * field, so from q = N + 1 on the rule integrates that part exactly and it equals the collocated
+ * weak-form term; the library applies it in that exact form on the nodes.  The face flux gains
+ * minus the central viscous flux with the walls' exterior viscous fluxes, as in the collocated
+ * form. */
 
 /* Host only (no CUDA call): the rule with q points per direction (1..DG_MAX_OVERINT_POINTS) on the
  * reference tetrahedron, rst_host[q^3][3] and w_host[q^3] (caller-owned); point (k q + j) q + i
