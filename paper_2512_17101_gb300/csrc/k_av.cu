@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_sensor_kernel(const double* __r
 template <int N, typename R>
 constexpr size_t av_flux_smem() {
   using O = Ord<N>;
-  return sizeof(double) * O::EPB * GS + sizeof(R) * (O::OPS + 5 * O::NODES + 5 * O::EPB * O::NF) +
+  return sizeof(double) * O::EPB * GS + sizeof(R) * (O::OPS + 5 * O::NODES + 5 * O::EPB * O::NF + O::EPB * GS) +
          sizeof(int) * (O::NF + O::EPB);
 }
 
@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
   R* sOps = reinterpret_cast<R*>(sGeo + EPB * GS);
   R* sW = sOps + O::OPS;
   R* sJ = sW + W * NODES;
-  int* sFm = reinterpret_cast<int*>(sJ + W * EPB * NF);
+  R* sGr = sJ + W * EPB * NF;  // the geometry converted once per element, for the node loop
+  int* sFm = reinterpret_cast<int*>(sGr + EPB * GS);
   int* sE = sFm + NF;  // [EPB]: the group's element indices
 
   const int tid = threadIdx.x;
@@ -108,7 +109,11 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
   __syncthreads();  // the previous group's reads of sE, sGeo, sW and sJ are done
   if (tid < nel) sE[tid] = list[1 + g0 + tid];
   __syncthreads();
-  for (int i = tid; i < nel * GS; i += blockDim.x) sGeo[i] = geo_g[(size_t)sE[i / GS] * GS + i % GS];
+  for (int i = tid; i < nel * GS; i += blockDim.x) {
+    const double gv = geo_g[(size_t)sE[i / GS] * GS + i % GS];
+    sGeo[i] = gv;
+    sGr[i] = (R)gv;
+  }
 #pragma unroll
   for (int v = 0; v < W; ++v)
     for (int i = tid; i < nn; i += blockDim.x) sW[v * NODES + i] = (R)q[v * KNp + (size_t)sE[i / Np] * Np + i % Np];
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
 
   if (tid < nn) {
     const int e = tid / Np, i = tid - e * Np;
-    const double* G = sGeo + e * GS;
+    const R* G = sGr + e * GS;
     const R* Dr = sOps + i * Np;
     const R* Ds = sOps + Np * Np + i * Np;
     const R* Dt = sOps + 2 * Np * Np + i * Np;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
     for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int v = 0; v < W; ++v)
-        grad[d][v] = fma((R)G[d], dref[0][v], fma((R)G[3 + d], dref[1][v], (R)G[6 + d] * dref[2][v]));
+        grad[d][v] = fma(G[d], dref[0][v], fma(G[3 + d], dref[1][v], G[6 + d] * dref[2][v]));
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       R lf[W];
@@ -171,18 +176,18 @@ __global__ void __launch_bounds__(Ord<N>::NT) av_flux_kernel(
 #pragma unroll
         for (int v = 0; v < W; ++v) lf[v] = fma(l, sJ[v * EPB * NF + col], lf[v]);
       }
-      const R nf[3] = {(R)G[9 + 4 * f], (R)G[10 + 4 * f], (R)G[11 + 4 * f]};
+      const R nf[3] = {G[9 + 4 * f], G[10 + 4 * f], G[11 + 4 * f]};
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < W; ++v) grad[d][v] = fma(nf[d], lf[v], grad[d][v]);
     }
-    const double ee = eps[sE[e]];
+    const R ee = (R)eps[sE[e]];
     const size_t gi = (size_t)sE[e] * Np + i;
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = ee * (double)grad[d][v];
+      for (int v = 0; v < W; ++v) sig[(5 * d + v) * KNp + gi] = (double)(ee * grad[d][v]);
   }
   }
 }
